@@ -1,0 +1,209 @@
+/*
+ * gplhr.h -- C ABI of libgplhr, a GB300 (sm_103a) implementation of the GPLHR
+ * eigensolver: Generalized Preconditioned Locally Harmonic Residual method,
+ * Vecharynski, Yang & Xue, arXiv 1506.06829.
+ *
+ * Problem (Sec. 1, Eq. gevp):  A x = lambda B x,  A, B sparse n x n, B = I allowed.
+ * Wanted: the k eigenvalues nearest a shift sigma in C, a partial generalized
+ * Schur form A V = Q R_A, B V = Q R_B (Eq. gschur; B = I: A V = V R, Eq. schur),
+ * and eigenvectors x_j = V z_j.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex numbers are interleaved (re, im) pairs of double, as C99
+ *   double _Complex / std::complex<double> / torch.complex128.
+ * - Dense blocks are ROW-MAJOR n x w with a leading dimension ld >= w counted in
+ *   elements: element (i, j) sits at p[i * ld + j].  (Rows of a k-wide block are
+ *   contiguous so one sparse row gathers whole 16*k-byte block rows.)
+ * - Small k x k / s x s matrices are row-major with ld = number of columns.
+ * - "where" arguments: GPLHR_HOST (0) = pointer to host memory (pageable or
+ *   pinned), GPLHR_DEVICE (1) = pointer to device memory of the context's GPU.
+ * - Ownership: the library never keeps a caller pointer after a call returns;
+ *   inputs are copied, outputs are written into caller-allocated memory.
+ * - Errors: every call returns a gplhr_status; no exception, abort or exit
+ *   crosses the ABI.  gplhr_last_error() gives a one-line message for the
+ *   context (or the last failed create when called with NULL).
+ * - Streams: all device work of a context runs on the stream given in
+ *   gplhr_opts.stream (NULL = a stream the context creates).  Calls are
+ *   synchronous with respect to the host unless stated otherwise.
+ * - A context is not thread-safe; distinct contexts may be used concurrently.
+ */
+#ifndef GPLHR_H
+#define GPLHR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GPLHR_OK = 0,
+  GPLHR_EINVAL = 1,     /* invalid argument (sizes, pointers, CSR pattern, sigma)      */
+  GPLHR_ENOMEM = 2,     /* device or host allocation failed                            */
+  GPLHR_ECUDA = 3,      /* a CUDA runtime call failed (message has the CUDA error)     */
+  GPLHR_ENOTCONV = 4,   /* maxit reached before all k pairs met tol (results readable) */
+  GPLHR_ESINGULAR = 5,  /* singular (block-)Jacobi block, or orth() broke down twice   */
+  GPLHR_ENUMERIC = 6,   /* NaN/Inf met in the iteration                                */
+  GPLHR_ETIMEOUT = 7    /* a bounded device wait gave up                               */
+} gplhr_status;
+
+enum { GPLHR_HOST = 0, GPLHR_DEVICE = 1 };
+enum { GPLHR_R64 = 0, GPLHR_C128 = 1 };                 /* CSR value types            */
+enum {
+  GPLHR_PREC_NONE = 0,          /* T = I                                               */
+  GPLHR_PREC_JACOBI = 1,        /* T = diag(A - sigma B)^{-1}                          */
+  GPLHR_PREC_BLOCK_JACOBI = 2,  /* T = blockdiag of bs x bs diagonal blocks, inverted  */
+  GPLHR_PREC_CSR = 3            /* T given explicitly as a sparse matrix (C128)        */
+};
+enum { GPLHR_FP64 = 0 };                                 /* arithmetic of the iteration */
+
+/* Sparse matrix in CSR form (0-based, column indices sorted per row, no duplicates).
+ * rowptr has n+1 entries, colind and vals nnz entries; vals are double (GPLHR_R64) or
+ * interleaved complex double (GPLHR_C128).  on_device = 1 if the three arrays are
+ * device pointers.  The library copies what it needs during gplhr_create. */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int32_t* rowptr;
+  const int32_t* colind;
+  const void* vals;
+  int32_t dtype;
+  int32_t on_device;
+} gplhr_csr;
+
+/* Preconditioner T ~ (A - sigma B)^{-1} (Sec. 4).  JACOBI and BLOCK_JACOBI are built
+ * from A - sigma B inside gplhr_create; block_size bs >= 1 groups consecutive rows
+ * [b bs, (b+1) bs) (the last block is n mod bs wide when bs does not divide n).
+ * JACOBI with a constant diagonal (relative spread <= 1e-12) is T = I: every output
+ * of T goes through a projector and orth(), so a constant scaling of T leaves the
+ * iteration unchanged.  CSR: T is applied as a sparse product with matrix T_csr. */
+typedef struct {
+  int32_t kind;
+  int32_t block_size;
+  const gplhr_csr* T_csr;
+} gplhr_precond;
+
+/* Solver options.  Zero-initialised fields take the defaults in brackets. */
+typedef struct {
+  double tol;          /* [1e-8] backward error per pair, see gplhr_info.resid          */
+  int32_t maxit;       /* [500]  iteration cap (the paper's DNC limit, Sec. 5.1)        */
+  int32_t precision;   /* [GPLHR_FP64]                                                   */
+  int32_t no_lock;     /* [0]    1 disables soft locking (Sec. 3.6)                      */
+  int32_t reserved;
+  void* stream;        /* [NULL] cudaStream_t for all device work of the context        */
+} gplhr_opts;
+
+/* Per-solve report.  resid[j] (j < k) is the backward error of pair j,
+ *   ||A x_j - lambda_j B x_j|| / ((||A||_1 + |lambda_j| ||B||_1) ||x_j||),
+ * with x_j = V z_j from the triangular factors (Sec. 5.1 measures eigen-residuals
+ * of vectors made from the Schur basis).  Counters follow the paper's #mv / #prec
+ * (Sec. 5): n_spmm counts products of A (and of B when B != I) with one n x w block. */
+typedef struct {
+  int32_t iters;
+  int32_t nconv;        /* leading pairs meeting tol (locked in order)                 */
+  int32_t m;            /* current m after adaptation                                  */
+  int32_t n_orth_fallback; /* orth() calls that needed the shifted-Cholesky pass       */
+  int64_t n_spmm;
+  int64_t n_prec;
+  int64_t n_qz;
+  double resid[64];     /* first min(k, 64) residuals                                  */
+} gplhr_info;
+
+typedef struct gplhr_ctx gplhr_ctx;
+
+/* gplhr_create -- set up a GPLHR solve for the pencil (A, B) and shift sigma.
+ * Paper: Algorithm 2 inputs (Sec. 3.6): a regular pair (A, B), sigma not an
+ * eigenvalue, preconditioner T, block size k and expansion parameter m; the
+ * trial subspace has s = (m+3)k columns (Eq. trial_partial1) and the context
+ * allocates Z, U, AZ, BZ of n x s each (Sec. 3.6 storage remark).
+ * A: required; B: NULL means B = I.  1 <= k <= 32, 0 <= m <= 20, (m+2) k <= 80 (the
+ * widest orthonormalised block, held in one CTA's shared memory), (m+3) k <= n.
+ * Errors: EINVAL (sizes, pattern, sigma not finite), ESINGULAR (a Jacobi /
+ * block-Jacobi block of A - sigma B is singular), ENOMEM, ECUDA.
+ * On success *out owns all device memory of the solve; free with gplhr_destroy. */
+gplhr_status gplhr_create(const gplhr_csr* A, const gplhr_csr* B, double sigma_re,
+                          double sigma_im, int32_t k, int32_t m, const gplhr_precond* T,
+                          const gplhr_opts* opts, gplhr_ctx** out);
+
+/* gplhr_solve -- run Algorithm 2 from the start block V0 until every pair's
+ * residual is <= tol, or maxit iterations (then ENOTCONV; results readable).
+ * V0: n x k row-major (ld = k), complex (is_complex = 1) or real (0), on host or
+ * device per V0_where; NULL draws a Gaussian block from `seed` on the device.
+ * info may be NULL.  Steps 1-4 (initial orth + ordered QZ) are part of this call. */
+gplhr_status gplhr_solve(gplhr_ctx* ctx, const void* V0, int32_t V0_where, int32_t is_complex,
+                         uint64_t seed, gplhr_info* info);
+
+/* gplhr_start -- steps 1-4 of Algorithm 2 only (initial basis and factors), then
+ * gplhr_iterate -- exactly `niter` passes of the while loop of Algorithm 2 (steps
+ * 6-30) with the convergence/locking bookkeeping, stopping early only if all k pairs
+ * meet tol.  Together they equal gplhr_solve; they exist for timing and checks. */
+gplhr_status gplhr_start(gplhr_ctx* ctx, const void* V0, int32_t V0_where, int32_t is_complex,
+                         uint64_t seed);
+gplhr_status gplhr_iterate(gplhr_ctx* ctx, int32_t niter, gplhr_info* info);
+
+/* gplhr_vectors -- read the current (converged) results.  Any pointer may be NULL.
+ * alpha, beta, lambda: k complex each (diagonals of R_A, R_B and their ratio,
+ *   Sec. 2, Eq. gevp_mod; lambda = alpha/beta, +inf when beta = 0), in ascending
+ *   |lambda - sigma| order (footnote to Alg. 2 step 2).
+ * X: n x k eigenvectors x_j = V z_j, unit 2-norm (Sec. 2.1: eigenvectors from the
+ *   Schur basis), V, Q: n x k Schur bases (ld = k), RA, RB: k x k upper triangular
+ *   (B = I: RA is R with A V = V R, Eq. schur, and RB = I).
+ * resid: k backward errors recomputed with fresh products A X, B X (FP64).
+ * where selects host or device for X, V, Q, RA, RB (alpha/beta/lambda/resid are
+ * always host).  Errors: EINVAL if called before gplhr_start/solve. */
+gplhr_status gplhr_vectors(gplhr_ctx* ctx, double* alpha, double* beta, double* lambda,
+                           void* X, void* V, void* Q, void* RA, void* RB, double* resid,
+                           int32_t where);
+
+/* gplhr_destroy -- free everything the context owns.  NULL is a no-op. */
+void gplhr_destroy(gplhr_ctx* ctx);
+
+/* Message for the last failing call on ctx (or of the last failed gplhr_create when
+ * ctx is NULL).  The string stays valid until the next call on the same context. */
+const char* gplhr_last_error(const gplhr_ctx* ctx);
+
+/* ---------------------------------------------------------------------------------
+ * Step-level entry points: one building block of an iteration each, on device
+ * pointers of the context's GPU, on the context's stream, synchronous on return.
+ * They run the same kernels as gplhr_iterate and exist so that each step can be
+ * checked against the CPU oracle on its own.
+ * ------------------------------------------------------------------------------ */
+
+/* Sparse times block (the "matblock" products of Sec. 3.6, (m+1) per iteration):
+ * AX = A X and, if B != I and BX != NULL, BX = B X.  X, AX, BX: n x w, row-major. */
+gplhr_status gplhr_spmm(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t w, void* AX,
+                        int32_t ldax, void* BX, int32_t ldbx);
+
+/* Preconditioner Y = T X (Sec. 4; inside T_L of Eq. prec_gen).  Y may equal X. */
+gplhr_status gplhr_precond_apply(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t w,
+                                 void* Y, int32_t ldy);
+
+/* Gram product C = X^* Y (w_x x w_y, row-major, ld = w_y) over all n rows: the
+ * projections and the projected pencil U^* A Z, U^* B Z (Alg. 2 steps 8, 15, 19-24). */
+gplhr_status gplhr_gram(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t wx, const void* Y,
+                        int32_t ldy, int32_t wy, void* C);
+
+/* orth(X) in place (Alg. 1 footnote): X <- X R^{-1} with X = Q R the thin QR whose R
+ * has a real positive diagonal, by Cholesky QR applied twice (a shifted Cholesky
+ * first pass and a third pass when the Gram matrix is not numerically positive
+ * definite).  Rinv (w x w, may be NULL) receives R^{-1}. */
+gplhr_status gplhr_orth(gplhr_ctx* ctx, void* X, int32_t ldx, int32_t w, void* Rinv);
+
+/* Ordered complex QZ of a small pencil on the host (footnote to Alg. 2 step 2):
+ * Phi = YL RA YR^*, Psi = YL RB YR^* with |RA(j,j)/RB(j,j) - sigma| non-decreasing
+ * and RB(j,j) real >= 0.  All matrices s x s row-major complex, host memory.
+ * Phi/Psi are not modified.  No context or GPU needed.  Errors: EINVAL, ENOTCONV. */
+gplhr_status gplhr_ordqz(int32_t s, const double* Phi, const double* Psi, double sigma_re,
+                         double sigma_im, double* RA, double* RB, double* YL, double* YR);
+
+/* Q-free factors of Theorem 1 with Eqs. G1_fix, G2_fix: M_A = G2 G^{-1} R_A,
+ * M_B = I - G1 G^{-1} R_A, G = R_A G1 + R_B G2 (k x k row-major complex, host). */
+gplhr_status gplhr_mfactors(int32_t k, const double* RA, const double* RB, double* MA,
+                            double* MB);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPLHR_H */

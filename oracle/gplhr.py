@@ -16,7 +16,8 @@ CUDA path):
   and P carry only the k - q active columns; the active recurrence for S_l uses
   the trailing blocks M_A(q:, q:), M_B(q:, q:) (the correction of a locked
   column is zero, and M_A, M_B are upper triangular); the thick-restart block is
-  P = Z Ybar_R(:, k+1 : 2k-q).  m <- min(floor(m0 k/(k - q)), 20).
+  P = Z Ybar_R(:, k+1 : 2k-q), and when q grows P keeps its leading k - q columns
+  (the Schur vectors nearest sigma after V).  m <- min(floor(m0 k/(k - q)), 20).
 * Convergence (Sec. 5.1 measures eigen-residuals of vectors made from V): the
   eigenvector of the j-th pair is x_j = V z_j, z_j the eigenvector of the upper
   triangular pencil (R_A, R_B) for its j-th diagonal pair (alpha_j, beta_j),
@@ -167,6 +168,8 @@ def iterate(pen: Pencil, st: State) -> State:
         S_prev = Sl
     Sc = np.hstack(S)
     blocks = [W] + S
+    if P is not None:
+        P = P[:, :k - q]                                   # soft locking: k - q columns
     if P is not None and P.shape[1] > 0:                   # step 21
         P = P - V @ (V.conj().T @ P)
         P = P - W @ (W.conj().T @ P)

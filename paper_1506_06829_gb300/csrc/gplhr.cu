@@ -1,0 +1,1129 @@
+// libgplhr: host driver and C ABI of the GPLHR eigensolver (arXiv 1506.06829,
+// Algorithm 2) on one GPU.  Device kernels are in kernels.cuh; the small dense
+// QZ / Q-free factor algebra runs on the host (qz.cpp).
+//
+// Storage (Sec. 3.6: Z, U, AZ, BZ of n x s, s = (m+3)k): four n x s_max row-major
+// complex blocks with s_max = (m0+3)k.  Column layout of Z (and of AZ, BZ):
+//   [ V (k) | W (kk) | S_1 (kk) ... S_m (kk) | P (kk) ],  kk = k - q (soft locking),
+// and U = [ Q (k) | Qhat (s - k) ].  For B = I, BZ is Z itself.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/gplhr.h"
+#include "kernels.cuh"
+#include "qz.h"
+
+using gplhr::cd;
+using gplhr::SqMat;
+
+namespace {
+
+std::string g_create_error;
+
+struct DevCsr {
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  void* val = nullptr;
+  int dtype = GPLHR_R64;
+  int64_t nnz = 0;
+};
+
+struct Blk {  // row-major block view
+  double2* p;
+  int ld;
+};
+
+
+}  // namespace
+
+struct gplhr_ctx {
+  // problem
+  int n = 0, k = 0, m0 = 0, s_max = 0;
+  cd sigma;
+  bool hasB = false;
+  DevCsr A, B, Tcsr;
+  double normA = 1.0, normB = 1.0;
+  int prec = GPLHR_PREC_NONE, bs = 1;
+  double2* prec_data = nullptr;  // Jacobi diagonal or block-Jacobi inverse blocks
+  // options
+  double tol = 1e-8;
+  int maxit = 500;
+  bool lock = true;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 152;
+  // device buffers
+  double2 *Z = nullptr, *AZ = nullptr, *BZ = nullptr, *U = nullptr;
+  double2 *Pb = nullptr, *APb = nullptr, *BPb = nullptr;
+  double2 *Rw = nullptr, *Tw1 = nullptr, *Tw2 = nullptr;
+  double2 *dC1 = nullptr, *dC2 = nullptr, *dMBa = nullptr, *dMAa = nullptr;
+  double2 *dYR = nullptr, *dYL = nullptr, *dPhiPsi = nullptr, *dGram = nullptr, *dProjC = nullptr;
+  double2* dRinv = nullptr;  // 3 x s_max^2
+  double2* gram_part = nullptr;
+  size_t gram_part_elems = 0;
+  double* norm_part = nullptr;
+  double* d_norms = nullptr;
+  int* d_status = nullptr;    // [0..2] chol status of the passes of one orth call
+  int* d_diag = nullptr;      // [0] shifted-Cholesky fallbacks, [1] Cholesky failures
+  // pinned host staging
+  double2* h_small = nullptr;  // coefficient uploads
+  double2* h_phipsi = nullptr;
+  double* h_norms = nullptr;
+  int* h_diag = nullptr;
+  // iteration state (host side)
+  bool started = false;
+  bool hasP = false;
+  int q = 0, m = 0, it = 0;
+  SqMat RA, RB, MA, MB;
+  std::vector<double> resid;
+  int64_t n_spmm = 0, n_prec = 0, n_qz = 0;
+  std::string err;
+};
+
+namespace {
+
+#define CK(call)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                \
+      return GPLHR_ECUDA;                                                           \
+    }                                                                               \
+  } while (0)
+
+#define TRY(expr)                      \
+  do {                                 \
+    gplhr_status s_ = (expr);          \
+    if (s_ != GPLHR_OK) return s_;     \
+  } while (0)
+
+const double2 kOne = {1.0, 0.0};
+const double2 kMinusOne = {-1.0, 0.0};
+
+inline double2 d2(cd z) { return make_double2(z.real(), z.imag()); }
+
+int grid_for(size_t work, int per_cta, int cap) {
+  size_t g = (work + per_cta - 1) / per_cta;
+  if (g < 1) g = 1;
+  if (g > (size_t)cap) g = cap;
+  return (int)g;
+}
+
+// ------------------------------------------------------------------ launches --
+
+gplhr_status launch_spmm_one(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, Blk X, int w, Blk Y,
+                             Blk Y2) {
+  const int threads = 256;
+  const int grid = grid_for((size_t)ctx->n, threads / 32, ctx->num_sms * 16);
+  const bool has2 = M2 != nullptr;
+  gplhr::CsrDev<double> dr{M.rowptr, M.col, (const double*)M.val};
+  gplhr::CsrDev<double2> dc{M.rowptr, M.col, (const double2*)M.val};
+  if (!has2) {
+    gplhr::CsrDev<double> none{nullptr, nullptr, nullptr};
+    if (M.dtype == GPLHR_R64)
+      gplhr::spmm_kernel<double, double><<<grid, threads, 0, ctx->stream>>>(ctx->n, dr, none, 0, X.p, X.ld, w,
+                                                                            Y.p, Y.ld, nullptr, 0);
+    else
+      gplhr::spmm_kernel<double2, double><<<grid, threads, 0, ctx->stream>>>(ctx->n, dc, none, 0, X.p, X.ld, w,
+                                                                             Y.p, Y.ld, nullptr, 0);
+  } else {
+    gplhr::CsrDev<double> br{M2->rowptr, M2->col, (const double*)M2->val};
+    gplhr::CsrDev<double2> bc{M2->rowptr, M2->col, (const double2*)M2->val};
+    if (M.dtype == GPLHR_R64 && M2->dtype == GPLHR_R64)
+      gplhr::spmm_kernel<double, double><<<grid, threads, 0, ctx->stream>>>(ctx->n, dr, br, 1, X.p, X.ld, w, Y.p,
+                                                                            Y.ld, Y2.p, Y2.ld);
+    else if (M.dtype == GPLHR_R64)
+      gplhr::spmm_kernel<double, double2><<<grid, threads, 0, ctx->stream>>>(ctx->n, dr, bc, 1, X.p, X.ld, w, Y.p,
+                                                                             Y.ld, Y2.p, Y2.ld);
+    else if (M2->dtype == GPLHR_R64)
+      gplhr::spmm_kernel<double2, double><<<grid, threads, 0, ctx->stream>>>(ctx->n, dc, br, 1, X.p, X.ld, w, Y.p,
+                                                                             Y.ld, Y2.p, Y2.ld);
+    else
+      gplhr::spmm_kernel<double2, double2><<<grid, threads, 0, ctx->stream>>>(ctx->n, dc, bc, 1, X.p, X.ld, w,
+                                                                              Y.p, Y.ld, Y2.p, Y2.ld);
+  }
+  CK(cudaGetLastError());
+  return GPLHR_OK;
+}
+
+// AX = A X and (B != I) BX = B X
+gplhr_status spmm_AB(gplhr_ctx* ctx, Blk X, int w, Blk AX, Blk BX) {
+  if (w <= 0) return GPLHR_OK;
+  ctx->n_spmm += 1;
+  return launch_spmm_one(ctx, ctx->A, ctx->hasB ? &ctx->B : nullptr, X, w, AX, BX);
+}
+
+// C (wx x (wy0 + wy1), row-major) = X^* [Y0 Y1]
+gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy1, double2* C,
+                  const int* skip = nullptr) {
+  const int wy = wy0 + wy1;
+  const int nout = wx * wy;
+  if (nout == 0) return GPLHR_OK;
+  const int ntile = (nout + gplhr::GRAM_OUT_PER_CTA - 1) / gplhr::GRAM_OUT_PER_CTA;
+  int nchunk = std::max(1, (4 * ctx->num_sms) / ntile);
+  nchunk = std::min(nchunk, std::max(1, (ctx->n + gplhr::GRAM_ROWS - 1) / gplhr::GRAM_ROWS));
+  while ((size_t)nchunk * nout > ctx->gram_part_elems && nchunk > 1) nchunk /= 2;
+  int rows = (ctx->n + nchunk - 1) / nchunk;
+  rows = ((rows + gplhr::GRAM_ROWS - 1) / gplhr::GRAM_ROWS) * gplhr::GRAM_ROWS;
+  nchunk = (ctx->n + rows - 1) / rows;
+  dim3 grid(nchunk, ntile);
+  const size_t smem = (size_t)gplhr::GRAM_ROWS * (wx + wy) * sizeof(double2);
+  gplhr::gram_partial_kernel<<<grid, gplhr::GRAM_THREADS, smem, ctx->stream>>>(
+      ctx->n, rows, X.p, X.ld, wx, Y0.p, Y0.ld, wy0, Y1.p, Y1.ld, wy1, ctx->gram_part, skip);
+  CK(cudaGetLastError());
+  gplhr::gram_reduce_kernel<<<(nout + 255) / 256, 256, 0, ctx->stream>>>(nchunk, nout, ctx->gram_part, C, skip);
+  CK(cudaGetLastError());
+  return GPLHR_OK;
+}
+
+struct In {
+  Blk X;
+  int w;
+  const double2* C;
+  double2 alpha;
+};
+
+// Y(cols 0..c_split) / Y2 (cols c_split..c_store) = beta Y + sum alpha_t X_t C_t;
+// columns c_store..c only contribute |.|^2 sums (reduced into ctx->d_norms).
+gplhr_status combine(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, bool beta_one,
+                     const int* skip = nullptr, Blk Y2 = Blk{nullptr, 0}, int c_split = -1,
+                     int c_store = -1) {
+  if (c <= 0 || ctx->n == 0) return GPLHR_OK;
+  if (c_store < 0) c_store = c;
+  if (c_split < 0) c_split = c_store;
+  gplhr::CombArgs a{};
+  a.nin = (int)ins.size();
+  int wsum = 0;
+  for (int t = 0; t < a.nin; ++t) {
+    a.in[t] = gplhr::CombIn{ins[t].X.p, ins[t].X.ld, ins[t].w, ins[t].C, ins[t].alpha};
+    wsum += ins[t].w;
+  }
+  a.Y = Y.p;
+  a.ldy = Y.ld;
+  a.Y2 = Y2.p;
+  a.ldy2 = Y2.ld;
+  a.c = c;
+  a.c_split = c_split;
+  a.c_store = c_store;
+  a.beta_one = beta_one ? 1 : 0;
+  a.skip = skip;
+  const int rows_tile = gplhr::comb_rows_tile(c);
+  const int grid = grid_for((size_t)ctx->n, std::max(rows_tile, 64), 4 * ctx->num_sms);
+  const int rows_per_cta = (ctx->n + grid - 1) / grid;
+  a.normpart = c_store < c ? ctx->norm_part : nullptr;
+  const size_t smem = (size_t)(wsum * c + rows_tile * wsum + rows_tile * c) * sizeof(double2);
+  gplhr::combine_kernel<<<grid, gplhr::COMB_THREADS, smem, ctx->stream>>>(ctx->n, rows_per_cta, a);
+  CK(cudaGetLastError());
+  if (c_store < c) {
+    gplhr::norm_reduce_kernel<<<1, 128, 0, ctx->stream>>>(grid, c - c_store, ctx->norm_part, ctx->d_norms);
+    CK(cudaGetLastError());
+  }
+  return GPLHR_OK;
+}
+
+gplhr_status precond_apply(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
+  if (w <= 0) return GPLHR_OK;
+  ctx->n_prec += 1;
+  const int n = ctx->n;
+  switch (ctx->prec) {
+    case GPLHR_PREC_NONE: {
+      if (X.p != Y.p) {
+        gplhr::copy_block_kernel<<<grid_for((size_t)n * w, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+            n, w, X.p, X.ld, Y.p, Y.ld);
+        CK(cudaGetLastError());
+      }
+      return GPLHR_OK;
+    }
+    case GPLHR_PREC_JACOBI: {
+      gplhr::jacobi_kernel<<<grid_for((size_t)n * w, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+          n, w, ctx->prec_data, X.p, X.ld, Y.p, Y.ld);
+      CK(cudaGetLastError());
+      return GPLHR_OK;
+    }
+    case GPLHR_PREC_BLOCK_JACOBI: {
+      const int bs = ctx->bs;
+      const int nblocks = (n + bs - 1) / bs;
+      const int bpc = std::max(1, 1024 / (bs * w));
+      const int grid = (nblocks + bpc - 1) / bpc;
+      const size_t smem = (size_t)bpc * bs * w * sizeof(double2);
+      gplhr::block_jacobi_kernel<<<grid, gplhr::BJ_THREADS, smem, ctx->stream>>>(n, bs, w, ctx->prec_data, X.p,
+                                                                                X.ld, Y.p, Y.ld, bpc);
+      CK(cudaGetLastError());
+      return GPLHR_OK;
+    }
+    case GPLHR_PREC_CSR: {
+      if (X.p == Y.p) {  // out of place through a scratch block
+        TRY(launch_spmm_one(ctx, ctx->Tcsr, nullptr, X, w, Blk{ctx->Tw1, ctx->k}, Blk{nullptr, 0}));
+        gplhr::copy_block_kernel<<<grid_for((size_t)n * w, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+            n, w, ctx->Tw1, ctx->k, Y.p, Y.ld);
+        CK(cudaGetLastError());
+        return GPLHR_OK;
+      }
+      return launch_spmm_one(ctx, ctx->Tcsr, nullptr, X, w, Y, Blk{nullptr, 0});
+    }
+  }
+  ctx->err = "unknown preconditioner";
+  return GPLHR_EINVAL;
+}
+
+// X <- X - L (L^* X): one projection against the leading block L (wl columns).
+gplhr_status project_out(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w) {
+  if (wl <= 0 || w <= 0) return GPLHR_OK;
+  TRY(gram(ctx, L, wl, X, w, Blk{nullptr, 0}, 0, ctx->dProjC));
+  return combine(ctx, {In{L, wl, ctx->dProjC, kMinusOne}}, X, w, true);
+}
+
+struct Extra {  // a block transformed alongside X (e.g. A P with P): E -= EL C; E <- E R^{-1}
+  Blk E;
+  Blk EL;
+};
+
+// orth of X against the leading block L (wl cols): block classical Gram-Schmidt
+// twice interleaved with Cholesky QR twice,
+//     pass: X -= L (L^* X);  G = X^* X = R^* R;  X <- X R^{-1},
+// with a shifted Cholesky in the first pass when G is not numerically positive
+// definite, followed then by a third pass (shifted Cholesky QR3).  Extras follow X.
+gplhr_status orth_against(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w, const std::vector<Extra>& ex = {}) {
+  if (w <= 0) return GPLHR_OK;
+  const int smax2 = ctx->s_max * ctx->s_max;
+  for (int pass = 0; pass < 3; ++pass) {
+    const int* skip = pass == 2 ? ctx->d_status + 0 : nullptr;
+    if (wl > 0) {
+      TRY(gram(ctx, L, wl, X, w, Blk{nullptr, 0}, 0, ctx->dProjC, skip));
+      TRY(combine(ctx, {In{L, wl, ctx->dProjC, kMinusOne}}, X, w, true, skip));
+      for (const Extra& e : ex) TRY(combine(ctx, {In{e.EL, wl, ctx->dProjC, kMinusOne}}, e.E, w, true, skip));
+    }
+    TRY(gram(ctx, X, w, X, w, Blk{nullptr, 0}, 0, ctx->dGram, skip));
+    double2* Rinv = ctx->dRinv + (size_t)pass * smax2;
+    const size_t smem = (size_t)2 * w * w * sizeof(double2);
+    gplhr::chol_inv_kernel<<<1, 256, smem, ctx->stream>>>(w, (int64_t)ctx->n, ctx->dGram, Rinv,
+                                                          ctx->d_status + pass, skip, ctx->d_diag);
+    CK(cudaGetLastError());
+    TRY(combine(ctx, {In{X, w, Rinv, kOne}}, X, w, false, skip));
+    for (const Extra& e : ex) TRY(combine(ctx, {In{e.E, w, Rinv, kOne}}, e.E, w, false, skip));
+  }
+  return GPLHR_OK;
+}
+
+gplhr_status upload(gplhr_ctx* ctx, double2* dst, const double2* src, size_t elems) {
+  CK(cudaMemcpyAsync(dst, src, elems * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+  return GPLHR_OK;
+}
+
+// Pack a host matrix M (rows x cols of a SqMat, starting at (r0, c0)) into dst (row-major).
+void pack(double2* dst, const SqMat& M, int r0, int rows, int c0, int cols) {
+  for (int i = 0; i < rows; ++i)
+    for (int j = 0; j < cols; ++j) dst[(size_t)i * cols + j] = d2(M(r0 + i, c0 + j));
+}
+
+Blk blkZ(gplhr_ctx* c, int col) { return Blk{c->Z + col, c->s_max}; }
+Blk blkAZ(gplhr_ctx* c, int col) { return Blk{c->AZ + col, c->s_max}; }
+Blk blkBZ(gplhr_ctx* c, int col) { return Blk{(c->hasB ? c->BZ : c->Z) + col, c->s_max}; }
+Blk blkU(gplhr_ctx* c, int col) { return Blk{c->U + col, c->s_max}; }
+
+// Residual R = AV M_B - BV M_A (all k columns, into Rw) and the backward errors of
+// the pairs with x_j = V z_j (Sec. 5.1); host receives resid[].
+gplhr_status residuals(gplhr_ctx* ctx) {
+  const int k = ctx->k;
+  SqMat Ze = gplhr::tri_eigvecs(ctx->RA, ctx->RB);
+  double2* h1 = ctx->h_small;
+  double2* h2 = ctx->h_small + 2 * k * k;
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) {
+      h1[i * 2 * k + j] = d2(ctx->MB(i, j));
+      h2[i * 2 * k + j] = d2(ctx->MA(i, j));
+      h1[i * 2 * k + k + j] = d2(Ze(i, j) * ctx->RB(j, j));
+      h2[i * 2 * k + k + j] = d2(Ze(i, j) * ctx->RA(j, j));
+    }
+  TRY(upload(ctx, ctx->dC1, h1, 2 * k * k));
+  TRY(upload(ctx, ctx->dC2, h2, 2 * k * k));
+  TRY(combine(ctx, {In{blkAZ(ctx, 0), k, ctx->dC1, kOne}, In{blkBZ(ctx, 0), k, ctx->dC2, kMinusOne}},
+              Blk{ctx->Rw, k}, 2 * k, false, nullptr, Blk{nullptr, 0}, k, k));
+  CK(cudaMemcpyAsync(ctx->h_norms, ctx->d_norms, k * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_diag, ctx->d_diag, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->resid.assign(k, 0.0);
+  for (int j = 0; j < k; ++j) {
+    double zn = 0.0;
+    for (int i = 0; i <= j; ++i) zn += std::norm(Ze(i, j));
+    const double a = std::abs(ctx->RA(j, j)), b = std::abs(ctx->RB(j, j));
+    const double den = (b * ctx->normA + a * ctx->normB) * std::sqrt(zn);
+    ctx->resid[j] = std::sqrt(ctx->h_norms[j]) / den;
+    if (!std::isfinite(ctx->resid[j])) {
+      ctx->err = "non-finite residual";
+      return GPLHR_ENUMERIC;
+    }
+  }
+  if (ctx->h_diag[1] != 0) {
+    ctx->err = "orth(): Cholesky QR broke down even with the shifted first pass";
+    return GPLHR_ESINGULAR;
+  }
+  return GPLHR_OK;
+}
+
+// Host: sorted QZ of the s x s pencil in h_phipsi, returns Ybar_R, Ybar_L, Rbar_A, Rbar_B.
+gplhr_status host_qz(gplhr_ctx* ctx, int s, SqMat& RAb, SqMat& RBb, SqMat& YLb, SqMat& YRb) {
+  SqMat Phi(s), Psi(s);
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) {
+      const double2 a = ctx->h_phipsi[(size_t)i * 2 * s + j];
+      const double2 b = ctx->h_phipsi[(size_t)i * 2 * s + s + j];
+      Phi(i, j) = cd(a.x, a.y);
+      Psi(i, j) = cd(b.x, b.y);
+      if (!std::isfinite(a.x) || !std::isfinite(a.y) || !std::isfinite(b.x) || !std::isfinite(b.y)) {
+        ctx->err = "non-finite projected pencil";
+        return GPLHR_ENUMERIC;
+      }
+    }
+  ctx->n_qz += 1;
+  if (!gplhr::ordered_qz(Phi, Psi, ctx->sigma, RAb, RBb, YLb, YRb)) {
+    ctx->err = "QZ iteration did not converge";
+    return GPLHR_ENUMERIC;
+  }
+  return GPLHR_OK;
+}
+
+void set_factors(gplhr_ctx* ctx, const SqMat& RAb, const SqMat& RBb) {
+  const int k = ctx->k;
+  ctx->RA = SqMat(k);
+  ctx->RB = SqMat(k);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) {
+      ctx->RA(i, j) = RAb(i, j);
+      ctx->RB(i, j) = RBb(i, j);
+    }
+  gplhr::m_factors(ctx->RA, ctx->RB, ctx->MA, ctx->MB);
+}
+
+// Steps 1-4 of Algorithm 2.  Z[:, 0:k] must hold V0.
+gplhr_status start(gplhr_ctx* ctx) {
+  const int k = ctx->k;
+  ctx->it = 0;
+  ctx->q = 0;
+  ctx->m = ctx->m0;
+  ctx->hasP = false;
+  ctx->n_spmm = ctx->n_prec = ctx->n_qz = 0;
+  CK(cudaMemsetAsync(ctx->d_diag, 0, 2 * sizeof(int), ctx->stream));
+  TRY(orth_against(ctx, Blk{nullptr, 0}, 0, blkZ(ctx, 0), k));                // V = orth(V0)
+  TRY(spmm_AB(ctx, blkZ(ctx, 0), k, blkAZ(ctx, 0), blkBZ(ctx, 0)));        // AV, BV
+  const double2 ms = d2(-ctx->sigma);
+  gplhr::axpby_kernel<<<grid_for((size_t)ctx->n * k, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+      ctx->n, k, kOne, ctx->AZ, ctx->s_max, ms, blkBZ(ctx, 0).p, ctx->s_max, ctx->U, ctx->s_max);
+  CK(cudaGetLastError());
+  TRY(orth_against(ctx, Blk{nullptr, 0}, 0, blkU(ctx, 0), k));                // Q = orth((A - sigma B) V)
+  TRY(gram(ctx, blkU(ctx, 0), k, blkAZ(ctx, 0), k, blkBZ(ctx, 0), k, ctx->dPhiPsi));
+  CK(cudaMemcpyAsync(ctx->h_phipsi, ctx->dPhiPsi, (size_t)2 * k * k * sizeof(double2), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  SqMat RAb, RBb, YLb, YRb;
+  TRY(host_qz(ctx, k, RAb, RBb, YLb, YRb));
+  double2* hy = ctx->h_small + 6 * k * k;  // residuals() reuses the first 4 k^2 entries
+  double2* hl = hy + k * k;
+  pack(hy, YRb, 0, k, 0, k);
+  pack(hl, YLb, 0, k, 0, k);
+  TRY(upload(ctx, ctx->dYR, hy, k * k));
+  TRY(upload(ctx, ctx->dYL, hl, k * k));
+  // V <- V YR, AV <- AV YR, BV <- BV YR, Q <- Q YL (in place)
+  TRY(combine(ctx, {In{blkZ(ctx, 0), k, ctx->dYR, kOne}}, blkZ(ctx, 0), k, false));
+  TRY(combine(ctx, {In{blkAZ(ctx, 0), k, ctx->dYR, kOne}}, blkAZ(ctx, 0), k, false));
+  if (ctx->hasB) TRY(combine(ctx, {In{blkBZ(ctx, 0), k, ctx->dYR, kOne}}, blkBZ(ctx, 0), k, false));
+  TRY(combine(ctx, {In{blkU(ctx, 0), k, ctx->dYL, kOne}}, blkU(ctx, 0), k, false));
+  set_factors(ctx, RAb, RBb);
+  ctx->started = true;
+  return residuals(ctx);
+}
+
+// Convergence bookkeeping after residuals(): soft locking in order and m-adaptation.
+bool converged_update(gplhr_ctx* ctx) {
+  const int k = ctx->k;
+  bool all = true;
+  for (int j = 0; j < k; ++j) all = all && ctx->resid[j] <= ctx->tol;
+  if (all) return true;
+  if (ctx->lock) {
+    int lead = 0;
+    while (lead < k && ctx->resid[lead] <= ctx->tol) ++lead;
+    if (lead > ctx->q) {
+      ctx->q = lead;
+      ctx->m = std::min(ctx->m0 * k / (k - ctx->q), 20);
+    }
+  }
+  return false;
+}
+
+// One pass of the while loop of Algorithm 2 (steps 6-30).  Rw holds the residual.
+gplhr_status iterate_once(gplhr_ctx* ctx) {
+  const int k = ctx->k, q = ctx->q, kk = k - ctx->q, m = ctx->m;
+  const int sm = ctx->s_max;
+  const Blk V = blkZ(ctx, 0), Q = blkU(ctx, 0);
+  const Blk right = ctx->hasB ? Q : V;  // projector before T: (I - QQ^*), or (I - VV^*) if B = I
+  // steps 7-8 / 10: W = (I - VV^*) T (I - QQ^*) R, active columns q..k-1
+  Blk Ra{ctx->Rw + q, k};
+  TRY(project_out(ctx, right, k, Ra, kk));
+  TRY(precond_apply(ctx, Ra, kk, blkZ(ctx, k)));
+  TRY(orth_against(ctx, V, k, blkZ(ctx, k), kk));                           // step 12 (with (I - VV^*))
+  TRY(spmm_AB(ctx, blkZ(ctx, k), kk, blkAZ(ctx, k), blkBZ(ctx, k)));
+  // steps 13-20: Krylov-Arnoldi blocks S_l
+  if (m > 0) {
+    double2* hm = ctx->h_small + 4 * k * k;
+    for (int i = 0; i < kk; ++i)
+      for (int j = 0; j < kk; ++j) {
+        hm[i * kk + j] = d2(ctx->MB(q + i, q + j));
+        hm[kk * kk + i * kk + j] = d2(ctx->MA(q + i, q + j));
+      }
+    TRY(upload(ctx, ctx->dMBa, hm, 2 * kk * kk));
+  }
+  for (int l = 1; l <= m; ++l) {
+    const int prev = k + (l - 1) * kk, cur = k + l * kk;
+    Blk X{ctx->Rw, k};
+    TRY(combine(ctx, {In{blkAZ(ctx, prev), kk, ctx->dMBa, kOne},
+                      In{blkBZ(ctx, prev), kk, ctx->dMBa + kk * kk, kMinusOne}},
+                X, kk, false));
+    TRY(project_out(ctx, right, k, X, kk));
+    TRY(precond_apply(ctx, X, kk, blkZ(ctx, cur)));
+    TRY(orth_against(ctx, V, cur, blkZ(ctx, cur), kk));                      // against V, W, S_1..S_{l-1}
+    TRY(spmm_AB(ctx, blkZ(ctx, cur), kk, blkAZ(ctx, cur), blkBZ(ctx, cur)));
+  }
+  // step 21: P against V, W, S and orth; AP, BP follow by the same transforms
+  int sP = 0;
+  const int pslot = k + (m + 1) * kk;
+  if (ctx->hasP && kk > 0) {
+    const size_t nw = (size_t)ctx->n;
+    gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+        ctx->n, kk, ctx->Pb, k, ctx->Z + pslot, sm);
+    gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+        ctx->n, kk, ctx->APb, k, ctx->AZ + pslot, sm);
+    if (ctx->hasB)
+      gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+          ctx->n, kk, ctx->BPb, k, ctx->BZ + pslot, sm);
+    CK(cudaGetLastError());
+    std::vector<Extra> ex{Extra{blkAZ(ctx, pslot), blkAZ(ctx, 0)}};
+    if (ctx->hasB) ex.push_back(Extra{blkBZ(ctx, pslot), blkBZ(ctx, 0)});
+    TRY(orth_against(ctx, V, pslot, blkZ(ctx, pslot), kk, ex));
+    sP = kk;
+  }
+  const int s = pslot + sP;
+  const int sk = s - k;
+  // steps 23-24: Qhat = orth((A - sigma B) [W S P]) against Q;  U = [Q Qhat]
+  gplhr::axpby_kernel<<<grid_for((size_t)ctx->n * sk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+      ctx->n, sk, kOne, ctx->AZ + k, sm, d2(-ctx->sigma), blkBZ(ctx, k).p, sm, ctx->U + k, sm);
+  CK(cudaGetLastError());
+  TRY(orth_against(ctx, Q, k, blkU(ctx, k), sk));
+  // step 24: projected pencil (U^* A Z, U^* B Z)
+  TRY(gram(ctx, blkU(ctx, 0), s, blkAZ(ctx, 0), s, blkBZ(ctx, 0), s, ctx->dPhiPsi));
+  CK(cudaMemcpyAsync(ctx->h_phipsi, ctx->dPhiPsi, (size_t)2 * s * s * sizeof(double2), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  SqMat RAb, RBb, YLb, YRb;
+  TRY(host_qz(ctx, s, RAb, RBb, YLb, YRb));
+  // steps 25-28: V = Z Ybar_R(:, 1:k), P = Z Ybar_R(:, k+1:k+kk), Q = U Ybar_L(:, 1:k)
+  const int cv = k + kk;
+  double2* hy = ctx->h_small + 6 * k * k;
+  double2* hl = hy + (size_t)s * cv;
+  pack(hy, YRb, 0, s, 0, cv);
+  pack(hl, YLb, 0, s, 0, k);
+  TRY(upload(ctx, ctx->dYR, hy, (size_t)s * cv));
+  TRY(upload(ctx, ctx->dYL, hl, (size_t)s * k));
+  TRY(combine(ctx, {In{blkZ(ctx, 0), s, ctx->dYR, kOne}}, blkZ(ctx, 0), cv, false, nullptr, Blk{ctx->Pb, k}, k));
+  TRY(combine(ctx, {In{blkAZ(ctx, 0), s, ctx->dYR, kOne}}, blkAZ(ctx, 0), cv, false, nullptr, Blk{ctx->APb, k},
+              k));
+  if (ctx->hasB)
+    TRY(combine(ctx, {In{blkBZ(ctx, 0), s, ctx->dYR, kOne}}, blkBZ(ctx, 0), cv, false, nullptr,
+                Blk{ctx->BPb, k}, k));
+  TRY(combine(ctx, {In{blkU(ctx, 0), s, ctx->dYL, kOne}}, blkU(ctx, 0), k, false));
+  ctx->hasP = true;
+  // steps 29-30
+  set_factors(ctx, RAb, RBb);
+  ctx->it += 1;
+  return GPLHR_OK;
+}
+
+void fill_info(gplhr_ctx* ctx, gplhr_info* info) {
+  if (!info) return;
+  std::memset(info, 0, sizeof(*info));
+  info->iters = ctx->it;
+  int lead = 0;
+  while (lead < ctx->k && lead < (int)ctx->resid.size() && ctx->resid[lead] <= ctx->tol) ++lead;
+  info->nconv = lead;
+  info->m = ctx->m;
+  info->n_orth_fallback = ctx->h_diag ? ctx->h_diag[0] : 0;
+  info->n_spmm = ctx->n_spmm;
+  info->n_prec = ctx->n_prec;
+  info->n_qz = ctx->n_qz;
+  for (int j = 0; j < ctx->k && j < 64 && j < (int)ctx->resid.size(); ++j) info->resid[j] = ctx->resid[j];
+}
+
+gplhr_status run_iterations(gplhr_ctx* ctx, int niter, gplhr_info* info, bool* conv_out) {
+  bool conv = converged_update(ctx);
+  for (int i = 0; i < niter && !conv; ++i) {
+    TRY(iterate_once(ctx));
+    TRY(residuals(ctx));
+    conv = converged_update(ctx);
+  }
+  fill_info(ctx, info);
+  if (conv_out) *conv_out = conv;
+  return GPLHR_OK;
+}
+
+// ------------------------------------------------------------------ setup ----
+
+gplhr_status validate_csr(const gplhr_csr* M, int64_t n, std::string& err, std::vector<int>& rp,
+                          std::vector<int>& ci) {
+  if (!M || M->n != n || M->nnz < 0 || !M->rowptr || (M->nnz > 0 && (!M->colind || !M->vals))) {
+    err = "invalid CSR descriptor";
+    return GPLHR_EINVAL;
+  }
+  if (M->dtype != GPLHR_R64 && M->dtype != GPLHR_C128) {
+    err = "CSR dtype must be GPLHR_R64 or GPLHR_C128";
+    return GPLHR_EINVAL;
+  }
+  rp.resize(n + 1);
+  ci.resize(M->nnz);
+  if (M->on_device) {
+    if (cudaMemcpy(rp.data(), M->rowptr, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (M->nnz > 0 &&
+         cudaMemcpy(ci.data(), M->colind, M->nnz * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)) {
+      err = "cannot read device CSR arrays";
+      return GPLHR_ECUDA;
+    }
+  } else {
+    std::memcpy(rp.data(), M->rowptr, (n + 1) * sizeof(int));
+    if (M->nnz > 0) std::memcpy(ci.data(), M->colind, M->nnz * sizeof(int));
+  }
+  if (rp[0] != 0 || rp[n] != M->nnz) {
+    err = "CSR rowptr must start at 0 and end at nnz";
+    return GPLHR_EINVAL;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (rp[i + 1] < rp[i]) {
+      err = "CSR rowptr not monotone";
+      return GPLHR_EINVAL;
+    }
+    for (int j = rp[i]; j < rp[i + 1]; ++j) {
+      if (ci[j] < 0 || ci[j] >= n || (j > rp[i] && ci[j] <= ci[j - 1])) {
+        err = "CSR column indices out of range or not strictly increasing in a row";
+        return GPLHR_EINVAL;
+      }
+    }
+  }
+  return GPLHR_OK;
+}
+
+gplhr_status upload_csr(gplhr_ctx* ctx, const gplhr_csr* M, DevCsr& D, double* onenorm) {
+  std::vector<int> rp, ci;
+  gplhr_status st = validate_csr(M, ctx->n, ctx->err, rp, ci);
+  if (st != GPLHR_OK) return st;
+  const int64_t n = ctx->n, nnz = M->nnz;
+  const size_t vsz = M->dtype == GPLHR_C128 ? 16 : 8;
+  D.dtype = M->dtype;
+  D.nnz = nnz;
+  CK(cudaMalloc(&D.rowptr, (n + 1) * sizeof(int)));
+  CK(cudaMalloc(&D.col, std::max<int64_t>(nnz, 1) * sizeof(int)));
+  CK(cudaMalloc(&D.val, std::max<int64_t>(nnz, 1) * vsz));
+  CK(cudaMemcpy(D.rowptr, rp.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  if (nnz > 0) {
+    CK(cudaMemcpy(D.col, ci.data(), nnz * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(D.val, M->vals, nnz * vsz, M->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+  }
+  if (onenorm) {  // ||M||_1 = max column sum of |m_ij|, on the host copy
+    std::vector<double> vals(nnz * (vsz / 8));
+    if (nnz > 0) CK(cudaMemcpy(vals.data(), D.val, nnz * vsz, cudaMemcpyDeviceToHost));
+    std::vector<double> colsum(n, 0.0);
+    for (int64_t j = 0; j < nnz; ++j) {
+      const double a = vsz == 16 ? std::hypot(vals[2 * j], vals[2 * j + 1]) : std::fabs(vals[j]);
+      colsum[ci[j]] += a;
+    }
+    double mx = 0.0;
+    for (double v : colsum) mx = std::max(mx, v);
+    *onenorm = mx;
+  }
+  return GPLHR_OK;
+}
+
+template <typename VTA, typename VTB>
+void launch_prec_setup(gplhr_ctx* ctx, int kind, double2* out, int nblocks) {
+  gplhr::CsrDev<VTA> a{ctx->A.rowptr, ctx->A.col, (const VTA*)ctx->A.val};
+  gplhr::CsrDev<VTB> b{ctx->B.rowptr, ctx->B.col, (const VTB*)ctx->B.val};
+  const double2 sg = d2(ctx->sigma);
+  if (kind == GPLHR_PREC_JACOBI)
+    gplhr::jacobi_setup_kernel<VTA, VTB><<<(ctx->n + 255) / 256, 256, 0, ctx->stream>>>(ctx->n, a, b, ctx->hasB,
+                                                                                        sg, out);
+  else
+    gplhr::extract_blocks_kernel<VTA, VTB><<<(nblocks * ctx->bs + 255) / 256, 256, 0, ctx->stream>>>(
+        ctx->n, ctx->bs, a, b, ctx->hasB, sg, out, nblocks);
+}
+
+gplhr_status setup_preconditioner(gplhr_ctx* ctx, const gplhr_precond* T) {
+  ctx->prec = T ? T->kind : GPLHR_PREC_NONE;
+  if (ctx->prec == GPLHR_PREC_NONE) return GPLHR_OK;
+  if (ctx->prec == GPLHR_PREC_CSR) {
+    if (!T->T_csr || T->T_csr->dtype != GPLHR_C128) {
+      ctx->err = "CSR preconditioner needs a complex (GPLHR_C128) matrix";
+      return GPLHR_EINVAL;
+    }
+    return upload_csr(ctx, T->T_csr, ctx->Tcsr, nullptr);
+  }
+  if (ctx->prec != GPLHR_PREC_JACOBI && ctx->prec != GPLHR_PREC_BLOCK_JACOBI) {
+    ctx->err = "unknown preconditioner kind";
+    return GPLHR_EINVAL;
+  }
+  ctx->bs = ctx->prec == GPLHR_PREC_JACOBI ? 1 : T->block_size;
+  if (ctx->bs < 1 || ctx->bs > 32) {
+    ctx->err = "block-Jacobi block size must be in [1, 32]";
+    return GPLHR_EINVAL;
+  }
+  const int n = ctx->n, bs = ctx->bs;
+  const int nblocks = (n + bs - 1) / bs;
+  const size_t elems = ctx->prec == GPLHR_PREC_JACOBI ? (size_t)n : (size_t)nblocks * bs * bs;
+  CK(cudaMalloc(&ctx->prec_data, elems * sizeof(double2)));
+  const int ta = ctx->A.dtype, tb = ctx->hasB ? ctx->B.dtype : GPLHR_R64;
+  if (ta == GPLHR_R64 && tb == GPLHR_R64) launch_prec_setup<double, double>(ctx, ctx->prec, ctx->prec_data, nblocks);
+  else if (ta == GPLHR_R64) launch_prec_setup<double, double2>(ctx, ctx->prec, ctx->prec_data, nblocks);
+  else if (tb == GPLHR_R64) launch_prec_setup<double2, double>(ctx, ctx->prec, ctx->prec_data, nblocks);
+  else launch_prec_setup<double2, double2>(ctx, ctx->prec, ctx->prec_data, nblocks);
+  CK(cudaGetLastError());
+  if (ctx->prec == GPLHR_PREC_JACOBI) {
+    std::vector<double2> d(n);
+    CK(cudaMemcpyAsync(d.data(), ctx->prec_data, n * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    double amax = 0.0, spread = 0.0;
+    bool zero = false;
+    for (int i = 0; i < n; ++i) {
+      amax = std::max(amax, std::hypot(d[i].x, d[i].y));
+      spread = std::max(spread, std::hypot(d[i].x - d[0].x, d[i].y - d[0].y));
+      zero = zero || (d[i].x == 0.0 && d[i].y == 0.0);
+    }
+    if (amax == 0.0 || spread <= 1e-12 * amax) {  // constant diagonal: T is a multiple of I
+      ctx->prec = GPLHR_PREC_NONE;
+      cudaFree(ctx->prec_data);
+      ctx->prec_data = nullptr;
+      return GPLHR_OK;
+    }
+    if (zero) {
+      ctx->err = "Jacobi: zero diagonal entry of A - sigma B";
+      return GPLHR_ESINGULAR;
+    }
+    gplhr::reciprocal_kernel<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, ctx->prec_data);
+    CK(cudaGetLastError());
+    return GPLHR_OK;
+  }
+  int* dflag = ctx->d_status;
+  CK(cudaMemsetAsync(dflag, 0, sizeof(int), ctx->stream));
+  const int wpc = 4;
+  const size_t smem = (size_t)wpc * bs * 2 * bs * sizeof(double2);
+  gplhr::invert_blocks_kernel<<<(nblocks + wpc - 1) / wpc, 32 * wpc, smem, ctx->stream>>>(nblocks, bs,
+                                                                                         ctx->prec_data, dflag);
+  CK(cudaGetLastError());
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (flag != 0) {
+    ctx->err = "block-Jacobi: singular diagonal block " + std::to_string(flag - 1) + " of A - sigma B";
+    return GPLHR_ESINGULAR;
+  }
+  return GPLHR_OK;
+}
+
+void free_all(gplhr_ctx* c) {
+  auto F = [](void* p) {
+    if (p) cudaFree(p);
+  };
+  F(c->A.rowptr); F(c->A.col); F(c->A.val);
+  F(c->B.rowptr); F(c->B.col); F(c->B.val);
+  F(c->Tcsr.rowptr); F(c->Tcsr.col); F(c->Tcsr.val);
+  F(c->prec_data);
+  F(c->Z); F(c->AZ); F(c->BZ); F(c->U); F(c->Pb); F(c->APb); F(c->BPb);
+  F(c->Rw); F(c->Tw1); F(c->Tw2);
+  F(c->dC1); F(c->dC2); F(c->dMBa); F(c->dMAa); F(c->dYR); F(c->dYL); F(c->dPhiPsi); F(c->dGram);
+  F(c->dProjC); F(c->dRinv); F(c->gram_part); F(c->norm_part); F(c->d_norms); F(c->d_status); F(c->d_diag);
+  if (c->h_small) cudaFreeHost(c->h_small);
+  if (c->h_phipsi) cudaFreeHost(c->h_phipsi);
+  if (c->h_norms) cudaFreeHost(c->h_norms);
+  if (c->h_diag) cudaFreeHost(c->h_diag);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+gplhr_status allocate(gplhr_ctx* ctx) {
+  const size_t n = ctx->n, k = ctx->k, sm = ctx->s_max;
+  const size_t nb = n * sm * sizeof(double2);
+  CK(cudaMalloc(&ctx->Z, nb));
+  CK(cudaMalloc(&ctx->AZ, nb));
+  if (ctx->hasB) CK(cudaMalloc(&ctx->BZ, nb));
+  CK(cudaMalloc(&ctx->U, nb));
+  const size_t kb = n * k * sizeof(double2);
+  CK(cudaMalloc(&ctx->Pb, kb));
+  CK(cudaMalloc(&ctx->APb, kb));
+  if (ctx->hasB) CK(cudaMalloc(&ctx->BPb, kb));
+  CK(cudaMalloc(&ctx->Rw, kb));
+  CK(cudaMalloc(&ctx->Tw1, kb));
+  CK(cudaMalloc(&ctx->Tw2, kb));
+  CK(cudaMemset(ctx->Z, 0, nb));
+  CK(cudaMemset(ctx->AZ, 0, nb));
+  CK(cudaMemset(ctx->U, 0, nb));
+  if (ctx->hasB) CK(cudaMemset(ctx->BZ, 0, nb));
+  const size_t s2 = sm * sm * sizeof(double2);
+  CK(cudaMalloc(&ctx->dC1, 2 * k * k * sizeof(double2)));
+  CK(cudaMalloc(&ctx->dC2, 2 * k * k * sizeof(double2)));
+  CK(cudaMalloc(&ctx->dMBa, 2 * k * k * sizeof(double2)));
+  CK(cudaMalloc(&ctx->dMAa, k * k * sizeof(double2)));
+  CK(cudaMalloc(&ctx->dYR, 2 * s2));
+  CK(cudaMalloc(&ctx->dYL, 2 * s2));
+  CK(cudaMalloc(&ctx->dPhiPsi, 2 * s2));
+  CK(cudaMalloc(&ctx->dGram, 2 * s2));
+  CK(cudaMalloc(&ctx->dProjC, 2 * s2));
+  CK(cudaMalloc(&ctx->dRinv, 3 * s2));
+  ctx->gram_part_elems = (size_t)(4 * ctx->num_sms + 8) * gplhr::GRAM_OUT_PER_CTA;
+  ctx->gram_part_elems = std::max(ctx->gram_part_elems, 2 * sm * sm);
+  CK(cudaMalloc(&ctx->gram_part, ctx->gram_part_elems * sizeof(double2)));
+  CK(cudaMalloc(&ctx->norm_part, (size_t)(4 * ctx->num_sms + 8) * gplhr::COMB_MAX_NORMS * sizeof(double)));
+  CK(cudaMalloc(&ctx->d_norms, gplhr::COMB_MAX_NORMS * sizeof(double)));
+  CK(cudaMalloc(&ctx->d_status, 8 * sizeof(int)));
+  CK(cudaMalloc(&ctx->d_diag, 2 * sizeof(int)));
+  CK(cudaMemset(ctx->d_diag, 0, 2 * sizeof(int)));
+  CK(cudaMallocHost(&ctx->h_small, (8 * k * k + 4 * sm * sm) * sizeof(double2)));
+  CK(cudaMallocHost(&ctx->h_phipsi, 2 * s2));
+  CK(cudaMallocHost(&ctx->h_norms, gplhr::COMB_MAX_NORMS * sizeof(double)));
+  CK(cudaMallocHost(&ctx->h_diag, 2 * sizeof(int)));
+  ctx->h_diag[0] = ctx->h_diag[1] = 0;
+  return GPLHR_OK;
+}
+
+gplhr_status set_smem_limits(gplhr_ctx* ctx) {
+  const int big = 200 * 1024;
+  CK(cudaFuncSetAttribute(gplhr::combine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::block_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::invert_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  return GPLHR_OK;
+}
+
+gplhr_status load_V0(gplhr_ctx* ctx, const void* V0, int where, int is_complex, uint64_t seed) {
+  const int n = ctx->n, k = ctx->k;
+  if (!V0) {
+    gplhr::gaussian_block_kernel<<<grid_for((size_t)n * k, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+        n, k, seed, ctx->Z, ctx->s_max);
+    CK(cudaGetLastError());
+    return GPLHR_OK;
+  }
+  const cudaMemcpyKind kind = where == GPLHR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (is_complex) {
+    CK(cudaMemcpy2DAsync(ctx->Z, ctx->s_max * sizeof(double2), V0, k * sizeof(double2), k * sizeof(double2), n,
+                         kind, ctx->stream));
+  } else {
+    CK(cudaMemcpyAsync(ctx->Tw1, V0, (size_t)n * k * sizeof(double), kind, ctx->stream));
+    gplhr::real_to_complex_kernel<<<grid_for((size_t)n * k, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+        n, k, (const double*)ctx->Tw1, ctx->Z, ctx->s_max);
+    CK(cudaGetLastError());
+  }
+  return GPLHR_OK;
+}
+
+bool valid_block(const void* p, int ld, int w) { return p != nullptr && w >= 0 && ld >= w; }
+
+}  // namespace
+
+// ====================================================================== C ABI ==
+
+extern "C" {
+
+gplhr_status gplhr_create(const gplhr_csr* A, const gplhr_csr* B, double sigma_re, double sigma_im, int32_t k,
+                          int32_t m, const gplhr_precond* T, const gplhr_opts* opts, gplhr_ctx** out) {
+  if (!out) {
+    g_create_error = "out must not be NULL";
+    return GPLHR_EINVAL;
+  }
+  *out = nullptr;
+  if (!A || A->n < 1 || A->n > (int64_t)0x7fffffff / 2) {
+    g_create_error = "A must be a CSR matrix with 1 <= n < 2^30";
+    return GPLHR_EINVAL;
+  }
+  if (k < 1 || m < 0 || m > 20 || (int64_t)(m + 3) * k > A->n || !std::isfinite(sigma_re) ||
+      !std::isfinite(sigma_im) || (B && B->n != A->n) || k > 32 || (m + 2) * k > 80) {
+    g_create_error = "invalid sizes: need 1 <= k <= 32, 0 <= m <= 20, (m+2) k <= 80, (m+3) k <= n, finite sigma";
+    return GPLHR_EINVAL;
+  }
+  gplhr_ctx* ctx = new (std::nothrow) gplhr_ctx();
+  if (!ctx) {
+    g_create_error = "out of host memory";
+    return GPLHR_ENOMEM;
+  }
+  ctx->n = (int)A->n;
+  ctx->k = k;
+  ctx->m0 = m;
+  ctx->m = m;
+  ctx->s_max = (m + 3) * k;
+  ctx->sigma = cd(sigma_re, sigma_im);
+  ctx->hasB = B != nullptr;
+  if (opts) {
+    if (opts->tol > 0) ctx->tol = opts->tol;
+    if (opts->maxit > 0) ctx->maxit = opts->maxit;
+    ctx->lock = opts->no_lock == 0;
+    ctx->stream = (cudaStream_t)opts->stream;
+  }
+  auto fail = [&](gplhr_status st) {
+    g_create_error = ctx->err;
+    free_all(ctx);
+    delete ctx;
+    return st;
+  };
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    ctx->err = "no CUDA device";
+    return fail(GPLHR_ECUDA);
+  }
+  if (!ctx->stream) {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      ctx->err = "cudaStreamCreate failed";
+      return fail(GPLHR_ECUDA);
+    }
+    ctx->own_stream = true;
+  }
+  gplhr_status st;
+  if ((st = set_smem_limits(ctx)) != GPLHR_OK) return fail(st);
+  if ((st = upload_csr(ctx, A, ctx->A, &ctx->normA)) != GPLHR_OK) return fail(st);
+  if (ctx->hasB && (st = upload_csr(ctx, B, ctx->B, &ctx->normB)) != GPLHR_OK) return fail(st);
+  if ((st = allocate(ctx)) != GPLHR_OK) return fail(st);
+  if ((st = setup_preconditioner(ctx, T)) != GPLHR_OK) return fail(st);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    ctx->err = "setup failed on the device";
+    return fail(GPLHR_ECUDA);
+  }
+  *out = ctx;
+  return GPLHR_OK;
+}
+
+gplhr_status gplhr_start(gplhr_ctx* ctx, const void* V0, int32_t V0_where, int32_t is_complex, uint64_t seed) {
+  if (!ctx) return GPLHR_EINVAL;
+  TRY(load_V0(ctx, V0, V0_where, is_complex, seed));
+  return start(ctx);
+}
+
+gplhr_status gplhr_iterate(gplhr_ctx* ctx, int32_t niter, gplhr_info* info) {
+  if (!ctx) return GPLHR_EINVAL;
+  if (!ctx->started) {
+    ctx->err = "gplhr_iterate before gplhr_start";
+    return GPLHR_EINVAL;
+  }
+  bool conv = false;
+  return run_iterations(ctx, niter, info, &conv);
+}
+
+gplhr_status gplhr_solve(gplhr_ctx* ctx, const void* V0, int32_t V0_where, int32_t is_complex, uint64_t seed,
+                         gplhr_info* info) {
+  if (!ctx) return GPLHR_EINVAL;
+  TRY(gplhr_start(ctx, V0, V0_where, is_complex, seed));
+  bool conv = false;
+  TRY(run_iterations(ctx, ctx->maxit, info, &conv));
+  if (!conv) {
+    ctx->err = "maxit reached before all pairs met tol";
+    return GPLHR_ENOTCONV;
+  }
+  return GPLHR_OK;
+}
+
+gplhr_status gplhr_vectors(gplhr_ctx* ctx, double* alpha, double* beta, double* lambda, void* X, void* V,
+                           void* Q, void* RA, void* RB, double* resid, int32_t where) {
+  if (!ctx) return GPLHR_EINVAL;
+  if (!ctx->started) {
+    ctx->err = "gplhr_vectors before gplhr_start";
+    return GPLHR_EINVAL;
+  }
+  const int n = ctx->n, k = ctx->k;
+  const cudaMemcpyKind d2x = where == GPLHR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  for (int j = 0; j < k; ++j) {
+    const cd a = ctx->RA(j, j), b = ctx->RB(j, j);
+    if (alpha) { alpha[2 * j] = a.real(); alpha[2 * j + 1] = a.imag(); }
+    if (beta) { beta[2 * j] = b.real(); beta[2 * j + 1] = b.imag(); }
+    if (lambda) {
+      const cd l = std::abs(b) > 0 ? a / b : cd(INFINITY, 0.0);
+      lambda[2 * j] = l.real();
+      lambda[2 * j + 1] = l.imag();
+    }
+  }
+  if (V) CK(cudaMemcpy2DAsync(V, k * sizeof(double2), ctx->Z, ctx->s_max * sizeof(double2), k * sizeof(double2), n,
+                              d2x, ctx->stream));
+  if (Q) CK(cudaMemcpy2DAsync(Q, k * sizeof(double2), ctx->U, ctx->s_max * sizeof(double2), k * sizeof(double2), n,
+                              d2x, ctx->stream));
+  SqMat Rout = ctx->RA, RBout = ctx->RB;
+  if (!ctx->hasB) {  // B = I: R = M_A M_B^{-1} (A V M_B = V M_A, Eq. gschur2), RB = I
+    SqMat Minv = SqMat::eye(k);
+    // solve M_B^T-free: Rout = MA * inv(MB), MB upper triangular
+    for (int c = 0; c < k; ++c)
+      for (int i = k - 1; i >= 0; --i) {
+        cd acc = (i == c) ? cd(1.0) : cd(0.0);
+        for (int t = i + 1; t < k; ++t) acc -= ctx->MB(i, t) * Minv(t, c);
+        Minv(i, c) = acc / ctx->MB(i, i);
+      }
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) {
+        cd acc = 0.0;
+        for (int t = 0; t < k; ++t) acc += ctx->MA(i, t) * Minv(t, j);
+        Rout(i, j) = acc;
+      }
+    RBout = SqMat::eye(k);
+  }
+  std::vector<double2> hr(k * k);
+  if (RA) {
+    pack(hr.data(), Rout, 0, k, 0, k);
+    CK(cudaMemcpyAsync(RA, hr.data(), k * k * sizeof(double2),
+                       where == GPLHR_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  if (RB) {
+    pack(hr.data(), RBout, 0, k, 0, k);
+    CK(cudaMemcpyAsync(RB, hr.data(), k * k * sizeof(double2),
+                       where == GPLHR_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  if (X || resid) {
+    // x_j = V z_j / ||V z_j||; fresh products A X, B X for the residuals
+    SqMat Ze = gplhr::tri_eigvecs(ctx->RA, ctx->RB);
+    for (int j = 0; j < k; ++j) {
+      double zn = 0.0;
+      for (int i = 0; i < k; ++i) zn += std::norm(Ze(i, j));
+      zn = std::sqrt(zn);
+      for (int i = 0; i < k; ++i) Ze(i, j) /= zn;
+    }
+    double2* hz = ctx->h_small;
+    pack(hz, Ze, 0, k, 0, k);
+    TRY(upload(ctx, ctx->dC1, hz, k * k));
+    Blk Xb{ctx->Rw, k};
+    TRY(combine(ctx, {In{blkZ(ctx, 0), k, ctx->dC1, kOne}}, Xb, k, false));
+    if (resid) {
+      Blk AX{ctx->Tw1, k}, BX{ctx->hasB ? ctx->Tw2 : ctx->Rw, k};
+      TRY(launch_spmm_one(ctx, ctx->A, ctx->hasB ? &ctx->B : nullptr, Xb, k, AX, BX));
+      double2* hb = ctx->h_small + k * k;
+      double2* ha = ctx->h_small + 2 * k * k;
+      for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) {
+          hb[i * k + j] = i == j ? d2(ctx->RB(j, j)) : make_double2(0.0, 0.0);
+          ha[i * k + j] = i == j ? d2(ctx->RA(j, j)) : make_double2(0.0, 0.0);
+        }
+      TRY(upload(ctx, ctx->dC2, hb, 2 * k * k));
+      TRY(combine(ctx, {In{AX, k, ctx->dC2, kOne}, In{BX, k, ctx->dC2 + k * k, kMinusOne}}, Blk{nullptr, 0}, k,
+                  false, nullptr, Blk{nullptr, 0}, 0, 0));
+      std::vector<double> nrm(k);
+      CK(cudaMemcpyAsync(nrm.data(), ctx->d_norms, k * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      for (int j = 0; j < k; ++j) {
+        const double a = std::abs(ctx->RA(j, j)), b = std::abs(ctx->RB(j, j));
+        resid[j] = std::sqrt(nrm[j]) / (b * ctx->normA + a * ctx->normB);
+      }
+    }
+    if (X) CK(cudaMemcpyAsync(X, ctx->Rw, (size_t)n * k * sizeof(double2), d2x, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return GPLHR_OK;
+}
+
+void gplhr_destroy(gplhr_ctx* ctx) {
+  if (!ctx) return;
+  free_all(ctx);
+  delete ctx;
+}
+
+const char* gplhr_last_error(const gplhr_ctx* ctx) {
+  if (!ctx) return g_create_error.c_str();
+  return ctx->err.c_str();
+}
+
+gplhr_status gplhr_spmm(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t w, void* AX, int32_t ldax, void* BX,
+                        int32_t ldbx) {
+  if (!ctx || !valid_block(X, ldx, w) || !valid_block(AX, ldax, w) || (ctx->hasB && BX && ldbx < w))
+    return GPLHR_EINVAL;
+  const bool withB = ctx->hasB && BX;
+  TRY(launch_spmm_one(ctx, ctx->A, withB ? &ctx->B : nullptr, Blk{(double2*)X, ldx}, w, Blk{(double2*)AX, ldax},
+                      Blk{(double2*)BX, ldbx}));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return GPLHR_OK;
+}
+
+gplhr_status gplhr_precond_apply(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t w, void* Y, int32_t ldy) {
+  if (!ctx || !valid_block(X, ldx, w) || !valid_block(Y, ldy, w) || w > ctx->k) return GPLHR_EINVAL;
+  TRY(precond_apply(ctx, Blk{(double2*)X, ldx}, w, Blk{(double2*)Y, ldy}));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return GPLHR_OK;
+}
+
+gplhr_status gplhr_gram(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t wx, const void* Y, int32_t ldy,
+                        int32_t wy, void* C) {
+  if (!ctx || !valid_block(X, ldx, wx) || !valid_block(Y, ldy, wy) || !C || wx > ctx->s_max ||
+      wy > 2 * ctx->s_max)
+    return GPLHR_EINVAL;
+  TRY(gram(ctx, Blk{(double2*)X, ldx}, wx, Blk{(double2*)Y, ldy}, wy, Blk{nullptr, 0}, 0, (double2*)C));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return GPLHR_OK;
+}
+
+gplhr_status gplhr_orth(gplhr_ctx* ctx, void* X, int32_t ldx, int32_t w, void* Rinv) {
+  if (!ctx || !valid_block(X, ldx, w) || w > ctx->s_max) return GPLHR_EINVAL;
+  TRY(orth_against(ctx, Blk{nullptr, 0}, 0, Blk{(double2*)X, ldx}, w));
+  if (Rinv) {
+    // R^{-1} of the whole orth = Rinv_0 Rinv_1 (Rinv_2): accumulate on the host
+    const int smax2 = ctx->s_max * ctx->s_max;
+    std::vector<double2> h(3 * (size_t)smax2);
+    CK(cudaMemcpyAsync(h.data(), ctx->dRinv, 3 * smax2 * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    SqMat acc = SqMat::eye(w);
+    for (int p = 0; p < 3; ++p) {
+      SqMat Rp(w), t(w);
+      for (int i = 0; i < w; ++i)
+        for (int j = 0; j < w; ++j) Rp(i, j) = cd(h[p * smax2 + i * w + j].x, h[p * smax2 + i * w + j].y);
+      for (int i = 0; i < w; ++i)
+        for (int j = 0; j < w; ++j) {
+          cd s = 0.0;
+          for (int l = 0; l < w; ++l) s += acc(i, l) * Rp(l, j);
+          t(i, j) = s;
+        }
+      acc = t;
+    }
+    std::vector<double2> o(w * w);
+    pack(o.data(), acc, 0, w, 0, w);
+    CK(cudaMemcpy(Rinv, o.data(), w * w * sizeof(double2), cudaMemcpyHostToDevice));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return GPLHR_OK;
+}
+
+gplhr_status gplhr_ordqz(int32_t s, const double* Phi, const double* Psi, double sigma_re, double sigma_im,
+                         double* RA, double* RB, double* YL, double* YR) {
+  if (s < 0 || (s > 0 && (!Phi || !Psi || !RA || !RB || !YL || !YR))) return GPLHR_EINVAL;
+  SqMat P(s), S(s), ra, rb, yl, yr;
+  for (int i = 0; i < s * s; ++i) {
+    P.a[i] = cd(Phi[2 * i], Phi[2 * i + 1]);
+    S.a[i] = cd(Psi[2 * i], Psi[2 * i + 1]);
+  }
+  if (!gplhr::ordered_qz(P, S, cd(sigma_re, sigma_im), ra, rb, yl, yr)) return GPLHR_ENOTCONV;
+  for (int i = 0; i < s * s; ++i) {
+    RA[2 * i] = ra.a[i].real(); RA[2 * i + 1] = ra.a[i].imag();
+    RB[2 * i] = rb.a[i].real(); RB[2 * i + 1] = rb.a[i].imag();
+    YL[2 * i] = yl.a[i].real(); YL[2 * i + 1] = yl.a[i].imag();
+    YR[2 * i] = yr.a[i].real(); YR[2 * i + 1] = yr.a[i].imag();
+  }
+  return GPLHR_OK;
+}
+
+gplhr_status gplhr_mfactors(int32_t k, const double* RA, const double* RB, double* MA, double* MB) {
+  if (k < 0 || (k > 0 && (!RA || !RB || !MA || !MB))) return GPLHR_EINVAL;
+  SqMat ra(k), rb(k), ma, mb;
+  for (int i = 0; i < k * k; ++i) {
+    ra.a[i] = cd(RA[2 * i], RA[2 * i + 1]);
+    rb.a[i] = cd(RB[2 * i], RB[2 * i + 1]);
+  }
+  gplhr::m_factors(ra, rb, ma, mb);
+  for (int i = 0; i < k * k; ++i) {
+    MA[2 * i] = ma.a[i].real(); MA[2 * i + 1] = ma.a[i].imag();
+    MB[2 * i] = mb.a[i].real(); MB[2 * i + 1] = mb.a[i].imag();
+  }
+  return GPLHR_OK;
+}
+
+}  // extern "C"

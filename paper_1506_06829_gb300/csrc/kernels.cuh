@@ -1,0 +1,605 @@
+// Device kernels of the GPLHR block iteration (FP64 / complex128).
+//
+// Dense n x w blocks are row-major with leading dimension ld (elements): row i of
+// a block is w contiguous double2 values, so a sparse row gathers whole block rows
+// with coalesced 16*w-byte loads.  Small coefficient matrices (w x c) are row-major.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gplhr {
+
+// ----------------------------------------------------------------- complex ----
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// c + a * b
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+  c.x = fma(a.x, b.x, c.x);
+  c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y);
+  c.y = fma(a.y, b.x, c.y);
+  return c;
+}
+// c + conj(a) * b
+__device__ __forceinline__ double2 cfmaconj(double2 a, double2 b, double2 c) {
+  c.x = fma(a.x, b.x, c.x);
+  c.x = fma(a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y);
+  c.y = fma(-a.y, b.x, c.y);
+  return c;
+}
+// c + v * b for a real v
+__device__ __forceinline__ double2 rfma(double v, double2 b, double2 c) {
+  c.x = fma(v, b.x, c.x);
+  c.y = fma(v, b.y, c.y);
+  return c;
+}
+__device__ __forceinline__ double2 vfma(double v, double2 b, double2 c) { return rfma(v, b, c); }
+__device__ __forceinline__ double2 vfma(double2 v, double2 b, double2 c) { return cfma(v, b, c); }
+
+__device__ __forceinline__ double2 shfl_xor2(double2 v, int m) {
+  v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+  v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+  return v;
+}
+
+// ------------------------------------------------------------------- SpMM -----
+// Y = M X for up to two CSR matrices sharing the input block (A and B of the pencil).
+// One warp per row.  For a block width w <= 32 the warp is split into 32/wp
+// "slots" of wp = next power of two >= w lanes: lane (slot, c) accumulates column c
+// over the nonzeros slot, slot + nslot, ... of the row; the slots are then summed
+// with xor-shuffles.  Wider blocks are processed in chunks of 32 columns.
+template <typename VT>
+struct CsrDev {
+  const int* rowptr;
+  const int* col;
+  const VT* val;
+};
+
+template <typename VT>
+__device__ __forceinline__ void spmm_row(const CsrDev<VT>& M, int r, const double2* __restrict__ X,
+                                         int ldx, int c0, int cw, int wp, int lane,
+                                         double2* __restrict__ Y, int ldy) {
+  const int slot = lane / wp;
+  const int nslot = 32 / wp;
+  const int c = lane - slot * wp;
+  double2 acc = make_double2(0.0, 0.0);
+  const int j0 = M.rowptr[r], j1 = M.rowptr[r + 1];
+  if (c < cw) {
+    for (int j = j0 + slot; j < j1; j += nslot) {
+      const VT v = M.val[j];
+      const int cc = M.col[j];
+      acc = vfma(v, X[(size_t)cc * ldx + c0 + c], acc);
+    }
+  }
+  for (int off = wp; off < 32; off <<= 1) {
+    double2 o = shfl_xor2(acc, off);
+    acc = cadd(acc, o);
+  }
+  if (slot == 0 && c < cw) Y[(size_t)r * ldy + c0 + c] = acc;
+}
+
+template <typename VTA, typename VTB>
+__global__ void spmm_kernel(int n, CsrDev<VTA> A, CsrDev<VTB> B, int hasB,
+                            const double2* __restrict__ X, int ldx, int w,
+                            double2* __restrict__ AX, int ldax, double2* __restrict__ BX, int ldbx) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int r = warp; r < n; r += nwarps) {
+    for (int c0 = 0; c0 < w; c0 += 32) {
+      const int cw = min(32, w - c0);
+      int wp = 1;
+      while (wp < cw) wp <<= 1;
+      spmm_row(A, r, X, ldx, c0, cw, wp, lane, AX, ldax);
+      if (hasB) spmm_row(B, r, X, ldx, c0, cw, wp, lane, BX, ldbx);
+    }
+  }
+}
+
+// ------------------------------------------------------------------- Gram -----
+// Split-n Gram product: partial[b][i][j] = sum over rows of chunk b of conj(X[r][i]) Y[r][j],
+// where Y is the column concatenation of up to two blocks (Y0: wy0 cols, Y1: wy1 cols).
+// The grid is (nchunk, ntile): CTA (b, t) owns chunk b of rows and tile t of up to
+// GRAM_OUT_PER_CTA outputs (row-major over the wx x wy output).  Rows are staged
+// through shared memory GRAM_ROWS at a time.
+constexpr int GRAM_THREADS = 256;
+constexpr int GRAM_ACC = 8;  // outputs per thread
+constexpr int GRAM_OUT_PER_CTA = GRAM_THREADS * GRAM_ACC;
+constexpr int GRAM_ROWS = 16;
+
+__global__ void gram_partial_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, int ldx,
+                                    int wx, const double2* __restrict__ Y0, int ldy0, int wy0,
+                                    const double2* __restrict__ Y1, int ldy1, int wy1,
+                                    double2* __restrict__ partial, const int* skip) {
+  if (skip && *skip == 0) return;
+  extern __shared__ double2 sm[];
+  const int wy = wy0 + wy1;
+  double2* xs = sm;                         // GRAM_ROWS x wx
+  double2* ys = sm + GRAM_ROWS * wx;        // GRAM_ROWS x wy
+  const int nout = wx * wy;
+  const int tile0 = blockIdx.y * GRAM_OUT_PER_CTA;
+  const int r0 = blockIdx.x * rows_per_chunk;
+  const int r1 = min(n, r0 + rows_per_chunk);
+  double2 acc[GRAM_ACC];
+  int oi[GRAM_ACC], oj[GRAM_ACC];
+#pragma unroll
+  for (int t = 0; t < GRAM_ACC; ++t) {
+    acc[t] = make_double2(0.0, 0.0);
+    const int o = tile0 + threadIdx.x + t * GRAM_THREADS;
+    oi[t] = o < nout ? o / wy : -1;
+    oj[t] = o < nout ? o - (o / wy) * wy : 0;
+  }
+  for (int rb = r0; rb < r1; rb += GRAM_ROWS) {
+    const int nr = min(GRAM_ROWS, r1 - rb);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * wx; e += blockDim.x) {
+      const int rr = e / wx, cc = e - rr * wx;
+      xs[rr * wx + cc] = X[(size_t)(rb + rr) * ldx + cc];
+    }
+    for (int e = threadIdx.x; e < nr * wy; e += blockDim.x) {
+      const int rr = e / wy, cc = e - rr * wy;
+      ys[rr * wy + cc] = cc < wy0 ? Y0[(size_t)(rb + rr) * ldy0 + cc]
+                                  : Y1[(size_t)(rb + rr) * ldy1 + (cc - wy0)];
+    }
+    __syncthreads();
+    for (int rr = 0; rr < nr; ++rr) {
+#pragma unroll
+      for (int t = 0; t < GRAM_ACC; ++t) {
+        if (oi[t] >= 0) acc[t] = cfmaconj(xs[rr * wx + oi[t]], ys[rr * wy + oj[t]], acc[t]);
+      }
+    }
+  }
+  double2* out = partial + (size_t)blockIdx.x * nout;
+#pragma unroll
+  for (int t = 0; t < GRAM_ACC; ++t)
+    if (oi[t] >= 0) out[oi[t] * wy + oj[t]] = acc[t];
+}
+
+// C[o] = sum_b partial[b][o] in a fixed order (deterministic).
+__global__ void gram_reduce_kernel(int nchunk, int nout, const double2* __restrict__ partial,
+                                   double2* __restrict__ C, const int* skip) {
+  if (skip && *skip == 0) return;
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nout) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int b = 0; b < nchunk; ++b) s = cadd(s, partial[(size_t)b * nout + o]);
+  C[o] = s;
+}
+
+// ---------------------------------------------------------------- combine -----
+// Y[r][0:c] = beta * Y[r][0:c] + sum_t alpha_t * (X_t[r][0:w_t] C_t), C_t is w_t x c
+// row-major on the device.  Rows are staged in shared memory before any write, so
+// Y may alias the rows of any X_t (in-place block transforms such as X <- X R^{-1}).
+// Output columns [0, c_split) go to Y, columns [c_split, c_store) to Y2 (column
+// c - c_split of Y2), and columns [c_store, c) are not stored: their |.|^2 is summed
+// per CTA into normpart[blockIdx.x][col - c_store].  beta applies to stored columns.
+// With skip != null and *skip == 0 the kernel does nothing.
+constexpr int COMB_MAX_IN = 4;
+constexpr int COMB_MAX_NORMS = 128;
+struct CombIn {
+  const double2* X;
+  int ldx;
+  int w;
+  const double2* C;
+  double2 alpha;
+};
+struct CombArgs {
+  CombIn in[COMB_MAX_IN];
+  int nin;
+  double2* Y;
+  int ldy;
+  double2* Y2;
+  int ldy2;
+  int c;
+  int c_split;      // == c_store when there is no second output
+  int c_store;      // == c when nothing but stores
+  int beta_one;     // 1: Y += ..., 0: Y = ...
+  double* normpart; // [gridDim.x][c - c_store] or null
+  const int* skip;
+};
+constexpr int COMB_THREADS = 256;
+
+__host__ __device__ inline int comb_rows_tile(int c) { return c >= COMB_THREADS ? 1 : COMB_THREADS / c; }
+
+__device__ __forceinline__ double2* comb_out(const CombArgs& a, int r, int cc) {
+  return cc < a.c_split ? a.Y + (size_t)r * a.ldy + cc : a.Y2 + (size_t)r * a.ldy2 + (cc - a.c_split);
+}
+
+__global__ void combine_kernel(int n, int rows_per_cta, CombArgs a) {
+  if (a.skip && *a.skip == 0) return;
+  extern __shared__ double2 sm[];
+  // layout: C_0 .. C_{nin-1} (w_t x c each, pre-scaled by alpha_t), then the staged
+  // rows: rows_tile x (sum w_t) X values, then rows_tile x c old Y values (beta = 1)
+  int wsum = 0;
+  for (int t = 0; t < a.nin; ++t) wsum += a.in[t].w;
+  double2* cs = sm;
+  double2* xs = cs + wsum * a.c;
+  const int rows_tile = comb_rows_tile(a.c);
+  double2* ys = xs + rows_tile * wsum;
+  __shared__ double nsum[COMB_MAX_NORMS];
+  {
+    int off = 0;
+    for (int t = 0; t < a.nin; ++t) {
+      const int sz = a.in[t].w * a.c;
+      for (int e = threadIdx.x; e < sz; e += blockDim.x) cs[off + e] = cmul(a.in[t].alpha, a.in[t].C[e]);
+      off += sz;
+    }
+  }
+  const int nnorm = a.c - a.c_store;
+  for (int e = threadIdx.x; e < nnorm; e += blockDim.x) nsum[e] = 0.0;
+  const int r0 = blockIdx.x * rows_per_cta;
+  const int r1 = min(n, r0 + rows_per_cta);
+  for (int rb = r0; rb < r1; rb += rows_tile) {
+    const int nr = min(rows_tile, r1 - rb);
+    __syncthreads();
+    int off = 0;
+    for (int t = 0; t < a.nin; ++t) {
+      const int w = a.in[t].w;
+      for (int e = threadIdx.x; e < nr * w; e += blockDim.x) {
+        const int rr = e / w, cc = e - rr * w;
+        xs[rr * wsum + off + cc] = a.in[t].X[(size_t)(rb + rr) * a.in[t].ldx + cc];
+      }
+      off += w;
+    }
+    if (a.beta_one) {
+      for (int e = threadIdx.x; e < nr * a.c_store; e += blockDim.x) {
+        const int rr = e / a.c_store, cc = e - rr * a.c_store;
+        ys[rr * a.c + cc] = *comb_out(a, rb + rr, cc);
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * a.c; e += blockDim.x) {
+      const int rr = e / a.c, cc = e - rr * a.c;
+      double2 acc = (a.beta_one && cc < a.c_store) ? ys[rr * a.c + cc] : make_double2(0.0, 0.0);
+      const double2* xr = xs + rr * wsum;
+      for (int j = 0; j < wsum; ++j) acc = cfma(xr[j], cs[j * a.c + cc], acc);
+      if (cc < a.c_store) {
+        *comb_out(a, rb + rr, cc) = acc;
+      } else {
+        atomicAdd(&nsum[cc - a.c_store], acc.x * acc.x + acc.y * acc.y);
+      }
+    }
+  }
+  if (a.normpart) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < nnorm; e += blockDim.x)
+      a.normpart[(size_t)blockIdx.x * nnorm + e] = nsum[e];
+  }
+}
+
+// normout[j] = sum_b normpart[b][j]  (fixed order)
+__global__ void norm_reduce_kernel(int nb, int nc, const double* __restrict__ part,
+                                   double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nc) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(size_t)b * nc + j];
+  out[j] = s;
+}
+
+// Y = alpha X1 + beta X2 (elementwise, n x w)
+__global__ void axpby_kernel(int n, int w, double2 alpha, const double2* __restrict__ X1, int ld1,
+                             double2 beta, const double2* __restrict__ X2, int ld2,
+                             double2* __restrict__ Y, int ldy) {
+  const size_t total = (size_t)n * w;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / w), c = (int)(e - (size_t)r * w);
+    double2 v = cmul(alpha, X1[(size_t)r * ld1 + c]);
+    v = cfma(beta, X2[(size_t)r * ld2 + c], v);
+    Y[(size_t)r * ldy + c] = v;
+  }
+}
+
+// Copy an n x w block (any lds)
+__global__ void copy_block_kernel(int n, int w, const double2* __restrict__ X, int ldx,
+                                  double2* __restrict__ Y, int ldy) {
+  const size_t total = (size_t)n * w;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / w), c = (int)(e - (size_t)r * w);
+    Y[(size_t)r * ldy + c] = X[(size_t)r * ldx + c];
+  }
+}
+
+// Real n x w (row-major, ld = w) to complex block.
+__global__ void real_to_complex_kernel(int n, int w, const double* __restrict__ X,
+                                       double2* __restrict__ Y, int ldy) {
+  const size_t total = (size_t)n * w;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / w), c = (int)(e - (size_t)r * w);
+    Y[(size_t)r * ldy + c] = make_double2(X[e], 0.0);
+  }
+}
+
+// --------------------------------------------------------- preconditioners ----
+// Jacobi: Y[r][c] = d[r] X[r][c]
+__global__ void jacobi_kernel(int n, int w, const double2* __restrict__ d, const double2* __restrict__ X,
+                              int ldx, double2* __restrict__ Y, int ldy) {
+  const size_t total = (size_t)n * w;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / w), c = (int)(e - (size_t)r * w);
+    Y[(size_t)r * ldy + c] = cmul(d[r], X[(size_t)r * ldx + c]);
+  }
+}
+
+// Block-Jacobi: for block b (rows [b bs, b bs + nb_b)), Y_b = Tinv_b X_b with Tinv_b
+// stored as bs x bs row-major (a ragged last block is identity-padded).  One CTA
+// handles BJ_BLOCKS_PER_CTA consecutive blocks; X rows are staged in shared memory,
+// so Y may equal X.
+constexpr int BJ_THREADS = 256;
+__global__ void block_jacobi_kernel(int n, int bs, int w, const double2* __restrict__ Tinv,
+                                    const double2* __restrict__ X, int ldx,
+                                    double2* __restrict__ Y, int ldy, int blocks_per_cta) {
+  extern __shared__ double2 sm[];
+  double2* xs = sm;  // blocks_per_cta * bs rows x w
+  const int nblocks = (n + bs - 1) / bs;
+  const int b0 = blockIdx.x * blocks_per_cta;
+  const int b1 = min(nblocks, b0 + blocks_per_cta);
+  if (b0 >= b1) return;
+  const int rstart = b0 * bs;
+  const int rend = min(n, b1 * bs);
+  const int nrows = rend - rstart;
+  for (int e = threadIdx.x; e < nrows * w; e += blockDim.x) {
+    const int rr = e / w, cc = e - rr * w;
+    xs[rr * w + cc] = X[(size_t)(rstart + rr) * ldx + cc];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nrows * w; e += blockDim.x) {
+    const int rr = e / w, cc = e - rr * w;
+    const int blk = rr / bs, i = rr - blk * bs;
+    const int gb = b0 + blk;
+    const int rows_in_blk = min(bs, n - gb * bs);
+    const double2* T = Tinv + (size_t)gb * bs * bs + (size_t)i * bs;
+    double2 acc = make_double2(0.0, 0.0);
+    const double2* xb = xs + (size_t)blk * bs * w;
+    for (int j = 0; j < rows_in_blk; ++j) acc = cfma(T[j], xb[j * w + cc], acc);
+    Y[(size_t)(rstart + rr) * ldy + cc] = acc;
+  }
+}
+
+// Setup: extract the diagonal blocks of K = A - sigma B (B = I if hasB = 0) into
+// blocks[b] (bs x bs, identity-padded past n).  One thread per row.
+template <typename VTA, typename VTB>
+__global__ void extract_blocks_kernel(int n, int bs, CsrDev<VTA> A, CsrDev<VTB> B, int hasB,
+                                      double2 sigma, double2* __restrict__ blocks, int nblocks) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nblocks * bs) return;
+  const int b = r / bs, i = r - b * bs;
+  double2* row = blocks + (size_t)b * bs * bs + (size_t)i * bs;
+  for (int j = 0; j < bs; ++j) row[j] = make_double2(0.0, 0.0);
+  if (r >= n) {
+    row[i] = make_double2(1.0, 0.0);
+    return;
+  }
+  const int c0 = b * bs;
+  for (int jj = A.rowptr[r]; jj < A.rowptr[r + 1]; ++jj) {
+    const int cc = A.col[jj];
+    if (cc >= c0 && cc < c0 + bs) row[cc - c0] = vfma(A.val[jj], make_double2(1.0, 0.0), row[cc - c0]);
+  }
+  const double2 ms = make_double2(-sigma.x, -sigma.y);
+  if (hasB) {
+    for (int jj = B.rowptr[r]; jj < B.rowptr[r + 1]; ++jj) {
+      const int cc = B.col[jj];
+      if (cc >= c0 && cc < c0 + bs) {
+        double2 v = vfma(B.val[jj], make_double2(1.0, 0.0), make_double2(0.0, 0.0));
+        row[cc - c0] = cfma(ms, v, row[cc - c0]);
+      }
+    }
+  } else {
+    row[i] = cadd(row[i], ms);
+  }
+}
+
+// Setup: invert each bs x bs block in place by Gauss-Jordan elimination with partial
+// pivoting, one warp per block (bs <= 32) on a [bs][2 bs] shared-memory tableau.
+// flag[0] is set to 1 + block index of a block whose pivot vanishes.
+__global__ void invert_blocks_kernel(int nblocks, int bs, double2* __restrict__ blocks, int* flag) {
+  extern __shared__ double2 sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wpc = blockDim.x >> 5;
+  const int b = blockIdx.x * wpc + warp;
+  if (b >= nblocks) return;
+  double2* tab = sm + (size_t)warp * bs * 2 * bs;
+  double2* blk = blocks + (size_t)b * bs * bs;
+  const int w2 = 2 * bs;
+  for (int e = lane; e < bs * w2; e += 32) {
+    const int i = e / w2, j = e - i * w2;
+    tab[e] = j < bs ? blk[i * bs + j] : make_double2(j - bs == i ? 1.0 : 0.0, 0.0);
+  }
+  __syncwarp();
+  double scale = 0.0;
+  for (int e = 0; e < bs * bs; ++e) scale = fmax(scale, fabs(blk[e].x) + fabs(blk[e].y));
+  bool singular = false;
+  for (int p = 0; p < bs; ++p) {
+    // pivot search (every lane does it: bs <= 32 values)
+    int piv = p;
+    double best = -1.0;
+    for (int i = p; i < bs; ++i) {
+      const double v = hypot(tab[i * w2 + p].x, tab[i * w2 + p].y);
+      if (v > best) { best = v; piv = i; }
+    }
+    if (!(best > 1e-300 && best > 1e-14 * scale)) { singular = true; break; }
+    if (piv != p) {
+      for (int j = lane; j < w2; j += 32) {
+        double2 t = tab[p * w2 + j];
+        tab[p * w2 + j] = tab[piv * w2 + j];
+        tab[piv * w2 + j] = t;
+      }
+      __syncwarp();
+    }
+    const double2 d = tab[p * w2 + p];
+    const double dd = d.x * d.x + d.y * d.y;
+    const double2 inv = make_double2(d.x / dd, -d.y / dd);
+    __syncwarp();
+    for (int j = lane; j < w2; j += 32) tab[p * w2 + j] = cmul(inv, tab[p * w2 + j]);
+    __syncwarp();
+    // eliminate column p from all other rows: row i -= tab[i][p] * row p
+    for (int i = 0; i < bs; ++i) {
+      if (i == p) continue;
+      const double2 f = tab[i * w2 + p];
+      __syncwarp();
+      for (int j = lane; j < w2; j += 32) {
+        const double2 v = tab[p * w2 + j];
+        tab[i * w2 + j] = csub(tab[i * w2 + j], cmul(f, v));
+      }
+      __syncwarp();
+    }
+  }
+  if (singular) {
+    if (lane == 0) atomicCAS(flag, 0, 1 + b);
+    return;
+  }
+  for (int e = lane; e < bs * bs; e += 32) {
+    const int i = e / bs, j = e - i * bs;
+    blk[e] = tab[i * w2 + bs + j];
+  }
+}
+
+// Setup: Jacobi diagonal d[r] = 1 / (A[r][r] - sigma B[r][r]).
+template <typename VTA, typename VTB>
+__global__ void jacobi_setup_kernel(int n, CsrDev<VTA> A, CsrDev<VTB> B, int hasB, double2 sigma,
+                                    double2* __restrict__ d) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double2 v = make_double2(0.0, 0.0);
+  for (int jj = A.rowptr[r]; jj < A.rowptr[r + 1]; ++jj)
+    if (A.col[jj] == r) v = vfma(A.val[jj], make_double2(1.0, 0.0), v);
+  double2 bv = make_double2(hasB ? 0.0 : 1.0, 0.0);
+  if (hasB)
+    for (int jj = B.rowptr[r]; jj < B.rowptr[r + 1]; ++jj)
+      if (B.col[jj] == r) bv = vfma(B.val[jj], make_double2(1.0, 0.0), bv);
+  d[r] = csub(v, cmul(sigma, bv));
+}
+
+__global__ void reciprocal_kernel(int n, double2* __restrict__ d) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const double2 v = d[r];
+  const double dd = v.x * v.x + v.y * v.y;
+  d[r] = make_double2(v.x / dd, -v.y / dd);
+}
+
+// ------------------------------------------------------ Cholesky QR helpers ----
+// Single-CTA Cholesky of the Hermitian w x w Gram matrix G (row-major) and the
+// inverse of its upper triangular factor: G = R^* R, R(j,j) > 0, Rinv = R^{-1}.
+// If the factorisation breaks down (a pivot <= eps_rel * max diag), the kernel
+// retries once on G + shift I with shift = 11 (n w + w (w+1)) u ||G||_F (the shift of
+// shifted Cholesky QR, Fukaya et al. 2020) and sets status[0] = 1 (shift used);
+// status[0] = 2 if that fails too.  fallback_counter[0] counts shifted retries and
+// fallback_counter[1] final failures.  When `skip_if_zero` is non-null and *skip_if_zero
+// is 0, the kernel writes the identity and returns (used for the conditional third
+// pass of shifted Cholesky QR).
+__global__ void chol_inv_kernel(int w, int64_t n, const double2* __restrict__ G,
+                                double2* __restrict__ Rinv, int* status, const int* skip_if_zero,
+                                int* fallback_counter) {
+  extern __shared__ double2 sm[];
+  double2* a = sm;              // w x w working copy -> R (upper)
+  double2* inv = sm + w * w;    // w x w -> R^{-1}
+  __shared__ int fail;
+  __shared__ double shift;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (skip_if_zero && *skip_if_zero == 0) {
+    for (int e = tid; e < w * w; e += nt) {
+      const int i = e / w, j = e - i * w;
+      Rinv[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    }
+    return;
+  }
+  if (tid == 0) {
+    double f = 0.0;
+    for (int e = 0; e < w * w; ++e) f += G[e].x * G[e].x + G[e].y * G[e].y;
+    const double u = 1.1102230246251565e-16;
+    shift = 11.0 * ((double)n * w + (double)w * (w + 1)) * u * sqrt(f);
+    if (status) status[0] = 0;
+  }
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    __syncthreads();
+    for (int e = tid; e < w * w; e += nt) {
+      const int i = e / w, j = e - i * w;
+      double2 v = G[e];
+      if (i == j) v = make_double2(v.x + (attempt ? shift : 0.0), 0.0);
+      a[e] = v;
+    }
+    if (tid == 0) fail = 0;
+    __syncthreads();
+    double dmax = 0.0;
+    for (int i = 0; i < w; ++i) dmax = fmax(dmax, a[i * w + i].x);
+    for (int p = 0; p < w; ++p) {
+      const double piv = a[p * w + p].x;
+      if (!(piv > 1e-15 * dmax) || !(piv > 0.0)) {
+        if (tid == 0) fail = 1;
+      }
+      __syncthreads();
+      if (fail) break;
+      const double rp = sqrt(piv);
+      // scale row p (upper part) by 1/rp
+      for (int j = p + tid; j < w; j += nt) {
+        double2 v = a[p * w + j];
+        a[p * w + j] = j == p ? make_double2(rp, 0.0) : make_double2(v.x / rp, v.y / rp);
+      }
+      __syncthreads();
+      // trailing update a[i][j] -= conj(R[p][i]) R[p][j], i, j > p, j >= i
+      const int m = w - p - 1;
+      for (int e = tid; e < m * m; e += nt) {
+        const int i = p + 1 + e / m, j = p + 1 + e % m;
+        if (j < i) continue;
+        const double2 ri = a[p * w + i], rj = a[p * w + j];
+        double2 v = a[i * w + j];
+        v = cfmaconj(ri, make_double2(-rj.x, -rj.y), v);
+        a[i * w + j] = v;
+      }
+      __syncthreads();
+    }
+    if (!fail) break;
+    if (attempt == 0 && tid == 0 && status) status[0] = 1;
+    if (attempt == 0 && tid == 0 && fallback_counter) atomicAdd(fallback_counter, 1);
+    if (attempt == 1 && tid == 0 && status) status[0] = 2;
+    if (attempt == 1 && tid == 0 && fallback_counter) atomicAdd(fallback_counter + 1, 1);
+  }
+  __syncthreads();
+  // inverse of the upper triangular R: column c of inv solves R x = e_c (back substitution)
+  for (int c = tid; c < w; c += nt) {
+    for (int i = w - 1; i >= 0; --i) {
+      double2 acc = make_double2(i == c ? 1.0 : 0.0, 0.0);
+      for (int t = i + 1; t <= c; ++t) acc = csub(acc, cmul(a[i * w + t], inv[t * w + c]));
+      const double d = a[i * w + i].x;
+      inv[i * w + c] = i > c ? make_double2(0.0, 0.0) : make_double2(acc.x / d, acc.y / d);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < w * w; e += nt) {
+    const int i = e / w, j = e - i * w;
+    Rinv[e] = (j >= i) ? inv[e] : make_double2(0.0, 0.0);
+  }
+}
+
+// Counter-based Gaussian start block (used when no V0 is given): Box-Muller on
+// two uniforms from a 64-bit splitmix of (seed, element index).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+__global__ void gaussian_block_kernel(int n, int w, uint64_t seed, double2* __restrict__ Y, int ldy) {
+  const size_t total = (size_t)n * w;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t h1 = splitmix64(seed ^ (2 * e));
+    const uint64_t h2 = splitmix64(seed ^ (2 * e + 1));
+    const double u1 = ((h1 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    const double u2 = ((h2 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    const double g = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+    const int r = (int)(e / w), c = (int)(e - (size_t)r * w);
+    Y[(size_t)r * ldy + c] = make_double2(g, 0.0);
+  }
+}
+
+}  // namespace gplhr

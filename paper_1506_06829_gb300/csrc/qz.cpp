@@ -1,0 +1,399 @@
+// Host-side complex QZ with reordering, and the k x k Q-free factor algebra.
+//
+// The sorted QZ of the projected pencil (U^*AZ, U^*BZ) is what the paper's
+// harmonic Schur-Rayleigh-Ritz step needs (Sec. 3.4, footnote to Alg. 2 step 2):
+// the FULL generalized Schur form, ordered by distance of the eigenvalues to sigma.
+// Written from the published algorithms:
+//   * reduction to Hessenberg-triangular form by Givens rotations and the
+//     single-shift implicit QZ sweep of Moler & Stewart (1973);
+//   * reordering by swapping adjacent 1x1 diagonal blocks with one right and one
+//     left plane rotation (Van Dooren's direct swap for triangular pencils);
+//   * a final unit-phase scaling that makes the diagonal of RB real non-negative.
+#include "qz.h"
+
+#include <algorithm>
+#include <cmath>
+#include <limits>
+
+namespace gplhr {
+
+namespace {
+
+const double kEps = std::numeric_limits<double>::epsilon();
+
+// Plane rotation G = [[c, s], [-conj(s), c]] with c real >= 0 such that
+// G [f; g] = [r; 0].
+void givens(cd f, cd g, double& c, cd& s, cd& r) {
+  const double ag = std::abs(g);
+  if (ag == 0.0) {
+    c = 1.0;
+    s = 0.0;
+    r = f;
+    return;
+  }
+  const double af = std::abs(f);
+  if (af == 0.0) {
+    c = 0.0;
+    s = std::conj(g) / ag;
+    r = ag;
+    return;
+  }
+  const double nrm = std::hypot(af, ag);
+  const cd ph = f / af;
+  c = af / nrm;
+  s = ph * std::conj(g) / nrm;
+  r = ph * nrm;
+}
+
+// M <- G M on rows (i1, i2), columns [c0, c1).
+void rot_rows(SqMat& M, int i1, int i2, double c, cd s, int c0, int c1) {
+  for (int j = c0; j < c1; ++j) {
+    const cd x = M(i1, j), y = M(i2, j);
+    M(i1, j) = c * x + s * y;
+    M(i2, j) = -std::conj(s) * x + c * y;
+  }
+}
+
+// Y <- Y G^* on columns (j1, j2): the accumulation that keeps Y (G M) = Y_old M.
+void rot_left_accum(SqMat& Y, int j1, int j2, double c, cd s) {
+  for (int i = 0; i < Y.n; ++i) {
+    const cd x = Y(i, j1), y = Y(i, j2);
+    Y(i, j1) = c * x + std::conj(s) * y;
+    Y(i, j2) = -s * x + c * y;
+  }
+}
+
+// M <- M Zr on columns (j1, j2), rows [r0, r1), Zr = [[c, s], [-conj(s), c]].
+void rot_cols(SqMat& M, int j1, int j2, double c, cd s, int r0, int r1) {
+  for (int i = r0; i < r1; ++i) {
+    const cd x = M(i, j1), y = M(i, j2);
+    M(i, j1) = c * x - std::conj(s) * y;
+    M(i, j2) = s * x + c * y;
+  }
+}
+
+// Right rotation on columns (j1, j2) that zeroes the entry x = M(i, j1) against
+// y = M(i, j2): with (c, s, r) = givens(y, x), [x y] Zr = [0 r].
+void right_zeroing(cd x, cd y, double& c, cd& s) {
+  cd r;
+  givens(y, x, c, s, r);
+}
+
+double fro(const SqMat& M) {
+  double t = 0.0;
+  for (const cd& v : M.a) t += std::norm(v);
+  return std::sqrt(t);
+}
+
+// Eigenvalue of the 2x2 upper-Hessenberg/triangular pencil (H2, T2) nearest h22/t22.
+cd wilkinson_shift(cd h11, cd h12, cd h21, cd h22, cd t11, cd t12, cd t22) {
+  // det(H2 - l T2) = a l^2 + b l + c
+  const cd a = t11 * t22;
+  const cd b = -(h11 * t22 + h22 * t11 - h21 * t12);
+  const cd c = h11 * h22 - h12 * h21;
+  const double scale = std::abs(h22) + std::abs(h11) + std::abs(h21) + std::abs(h12);
+  const double tsc = std::abs(t11) * std::abs(t22);
+  if (tsc <= kEps * kEps * std::max(1.0, scale) || std::abs(a) == 0.0) {
+    return std::abs(t22) > 0 ? h22 / t22 : h22;
+  }
+  const cd disc = std::sqrt(b * b - 4.0 * a * c);
+  const cd l1 = (-b + disc) / (2.0 * a);
+  const cd l2 = (-b - disc) / (2.0 * a);
+  const cd ref = std::abs(t22) > 0 ? h22 / t22 : l1;
+  return std::abs(l1 - ref) <= std::abs(l2 - ref) ? l1 : l2;
+}
+
+// Reduce (H, T) to upper Hessenberg / upper triangular form, accumulating YL, YR.
+void hessenberg_triangular(SqMat& H, SqMat& T, SqMat& YL, SqMat& YR) {
+  const int n = H.n;
+  // T -> upper triangular by left rotations (a Givens QR).
+  for (int j = 0; j < n; ++j) {
+    for (int i = n - 1; i > j; --i) {
+      if (T(i, j) == cd(0.0)) continue;
+      double c;
+      cd s, r;
+      givens(T(i - 1, j), T(i, j), c, s, r);
+      rot_rows(T, i - 1, i, c, s, 0, n);
+      rot_rows(H, i - 1, i, c, s, 0, n);
+      rot_left_accum(YL, i - 1, i, c, s);
+      T(i, j) = 0.0;
+    }
+  }
+  // H -> upper Hessenberg, keeping T triangular.
+  for (int j = 0; j + 2 < n; ++j) {
+    for (int i = n - 1; i >= j + 2; --i) {
+      if (H(i, j) == cd(0.0)) continue;
+      double c;
+      cd s, r;
+      givens(H(i - 1, j), H(i, j), c, s, r);
+      rot_rows(H, i - 1, i, c, s, j, n);
+      rot_rows(T, i - 1, i, c, s, i - 1, n);
+      rot_left_accum(YL, i - 1, i, c, s);
+      H(i, j) = 0.0;
+      // fill T(i, i-1): zero it from the right on columns (i-1, i)
+      right_zeroing(T(i, i - 1), T(i, i), c, s);
+      rot_cols(T, i - 1, i, c, s, 0, i + 1);
+      rot_cols(H, i - 1, i, c, s, 0, n);
+      rot_cols(YR, i - 1, i, c, s, 0, n);
+      T(i, i - 1) = 0.0;
+    }
+  }
+}
+
+// Move a negligible T(j, j) (ilo <= j <= ihi) down to T(ihi, ihi) and deflate an
+// infinite eigenvalue by zeroing H(ihi, ihi-1).
+void chase_zero_down(SqMat& H, SqMat& T, SqMat& YL, SqMat& YR, int j, int ihi) {
+  const int n = H.n;
+  T(j, j) = 0.0;
+  for (int i = j; i < ihi; ++i) {
+    double c;
+    cd s, r;
+    givens(T(i, i + 1), T(i + 1, i + 1), c, s, r);
+    rot_rows(T, i, i + 1, c, s, i, n);
+    rot_rows(H, i, i + 1, c, s, std::max(i - 1, 0), n);
+    rot_left_accum(YL, i, i + 1, c, s);
+    T(i + 1, i + 1) = 0.0;
+    if (i > 0) {
+      // H(i+1, i-1) filled: zero it from the right on columns (i-1, i)
+      right_zeroing(H(i + 1, i - 1), H(i + 1, i), c, s);
+      rot_cols(H, i - 1, i, c, s, 0, std::min(i + 2, n));
+      rot_cols(T, i - 1, i, c, s, 0, i + 1);
+      rot_cols(YR, i - 1, i, c, s, 0, n);
+      H(i + 1, i - 1) = 0.0;
+    }
+  }
+  if (ihi > 0) {
+    double c;
+    cd s;
+    right_zeroing(H(ihi, ihi - 1), H(ihi, ihi), c, s);
+    rot_cols(H, ihi - 1, ihi, c, s, 0, ihi + 1);
+    rot_cols(T, ihi - 1, ihi, c, s, 0, ihi + 1);
+    rot_cols(YR, ihi - 1, ihi, c, s, 0, n);
+    H(ihi, ihi - 1) = 0.0;
+  }
+}
+
+// Single-shift QZ iterations until (H, T) is upper triangular.
+bool qz_iterate(SqMat& H, SqMat& T, SqMat& YL, SqMat& YR) {
+  const int n = H.n;
+  const double normH = fro(H), normT = fro(T);
+  const double atolH = kEps * std::max(normH, std::numeric_limits<double>::min());
+  const double atolT = kEps * std::max(normT, std::numeric_limits<double>::min());
+  int ihi = n - 1;
+  int since_deflation = 0;
+  int total = 0;
+  const int max_total = 60 * std::max(n, 1);
+  while (ihi > 0) {
+    // find the start of the active unreduced block
+    int ilo = ihi;
+    while (ilo > 0) {
+      const double h = std::abs(H(ilo, ilo - 1));
+      const double rel = kEps * (std::abs(H(ilo, ilo)) + std::abs(H(ilo - 1, ilo - 1)));
+      if (h <= atolH || h <= rel) {
+        H(ilo, ilo - 1) = 0.0;
+        break;
+      }
+      --ilo;
+    }
+    if (ilo == ihi) {
+      --ihi;
+      since_deflation = 0;
+      continue;
+    }
+    // a negligible diagonal entry of T in the active block: infinite eigenvalue
+    bool chased = false;
+    for (int j = ilo; j <= ihi; ++j) {
+      if (std::abs(T(j, j)) <= atolT) {
+        chase_zero_down(H, T, YL, YR, j, ihi);
+        chased = true;
+        break;
+      }
+    }
+    if (chased) continue;
+    if (++total > max_total) return false;
+    ++since_deflation;
+    cd mu;
+    if (since_deflation % 10 == 0) {
+      // exceptional shift
+      mu = H(ihi, ihi) / T(ihi, ihi) +
+           cd(0.75, 0.35) * std::abs(H(ihi, ihi - 1)) / std::abs(T(ihi - 1, ihi - 1));
+    } else {
+      mu = wilkinson_shift(H(ihi - 1, ihi - 1), H(ihi - 1, ihi), H(ihi, ihi - 1), H(ihi, ihi),
+                           T(ihi - 1, ihi - 1), T(ihi - 1, ihi), T(ihi, ihi));
+    }
+    // implicit single-shift sweep on [ilo, ihi]
+    double c;
+    cd s, r;
+    givens(H(ilo, ilo) - mu * T(ilo, ilo), H(ilo + 1, ilo), c, s, r);
+    rot_rows(H, ilo, ilo + 1, c, s, ilo, n);
+    rot_rows(T, ilo, ilo + 1, c, s, ilo, n);
+    rot_left_accum(YL, ilo, ilo + 1, c, s);
+    for (int j = ilo; j < ihi; ++j) {
+      // T(j+1, j) is the bulge: zero it from the right on columns (j, j+1)
+      right_zeroing(T(j + 1, j), T(j + 1, j + 1), c, s);
+      rot_cols(T, j, j + 1, c, s, 0, j + 2);
+      rot_cols(H, j, j + 1, c, s, 0, std::min(j + 3, n));
+      rot_cols(YR, j, j + 1, c, s, 0, n);
+      T(j + 1, j) = 0.0;
+      if (j + 2 <= ihi) {
+        // H(j+2, j) filled: zero it from the left on rows (j+1, j+2)
+        givens(H(j + 1, j), H(j + 2, j), c, s, r);
+        rot_rows(H, j + 1, j + 2, c, s, j, n);
+        rot_rows(T, j + 1, j + 2, c, s, j + 1, n);
+        rot_left_accum(YL, j + 1, j + 2, c, s);
+        H(j + 2, j) = 0.0;
+      }
+    }
+  }
+  return true;
+}
+
+// Swap the adjacent 1x1 diagonal pairs at (j, j+1) of the triangular pencil (A, B).
+void swap_adjacent(SqMat& A, SqMat& B, SqMat& YL, SqMat& YR, int j) {
+  const int n = A.n;
+  const cd a11 = A(j, j), a12 = A(j, j + 1), a22 = A(j + 1, j + 1);
+  const cd b11 = B(j, j), b12 = B(j, j + 1), b22 = B(j + 1, j + 1);
+  // right eigenvector x of the 2x2 pencil for the pair (a22, b22): (b22 A - a22 B) x = 0
+  const cd num = -(b22 * a12 - a22 * b12);
+  const cd den = b22 * a11 - a22 * b11;
+  const double nn = std::abs(num), nd = std::abs(den);
+  if (nd == 0.0 && nn == 0.0) return;  // identical pairs: nothing to swap
+  const double nrm = std::hypot(nn, nd);
+  double c;
+  cd s;
+  if (nn == 0.0) {
+    c = 0.0;
+    s = -std::conj(den) / nd;
+  } else {
+    const cd ph = num / nn;
+    c = nn / nrm;
+    s = -ph * std::conj(den) / nrm;
+  }
+  rot_cols(A, j, j + 1, c, s, 0, j + 2);
+  rot_cols(B, j, j + 1, c, s, 0, j + 2);
+  rot_cols(YR, j, j + 1, c, s, 0, n);
+  // first columns of A, B are now parallel in rows (j, j+1): zero row j+1 from the left
+  const double na = std::norm(A(j, j)) + std::norm(A(j + 1, j));
+  const double nb = std::norm(B(j, j)) + std::norm(B(j + 1, j));
+  cd r;
+  if (na >= nb)
+    givens(A(j, j), A(j + 1, j), c, s, r);
+  else
+    givens(B(j, j), B(j + 1, j), c, s, r);
+  rot_rows(A, j, j + 1, c, s, j, n);
+  rot_rows(B, j, j + 1, c, s, j, n);
+  rot_left_accum(YL, j, j + 1, c, s);
+  A(j + 1, j) = 0.0;
+  B(j + 1, j) = 0.0;
+}
+
+bool key_less(cd a1, cd b1, cd a2, cd b2, cd sigma) {
+  const double d1 = pair_distance(a1, b1, sigma), d2 = pair_distance(a2, b2, sigma);
+  if (d1 != d2) return d1 < d2;
+  if (!std::isfinite(d1)) return false;
+  const cd l1 = a1 / b1, l2 = a2 / b2;
+  if (l1.real() != l2.real()) return l1.real() < l2.real();
+  return l1.imag() < l2.imag();
+}
+
+}  // namespace
+
+double pair_distance(cd alpha, cd beta, cd sigma) {
+  const double ab = std::abs(beta);
+  if (ab == 0.0) return std::numeric_limits<double>::infinity();
+  return std::abs(alpha - sigma * beta) / ab;
+}
+
+bool ordered_qz(const SqMat& Phi, const SqMat& Psi, cd sigma, SqMat& RA, SqMat& RB, SqMat& YL,
+                SqMat& YR) {
+  const int n = Phi.n;
+  RA = Phi;
+  RB = Psi;
+  YL = SqMat::eye(n);
+  YR = SqMat::eye(n);
+  if (n == 0) return true;
+  hessenberg_triangular(RA, RB, YL, YR);
+  if (!qz_iterate(RA, RB, YL, YR)) return false;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j) {
+      RA(i, j) = 0.0;
+      RB(i, j) = 0.0;
+    }
+  // selection sort: bring the nearest remaining pair to position pos by adjacent swaps
+  for (int pos = 0; pos + 1 < n; ++pos) {
+    int best = pos;
+    for (int j = pos + 1; j < n; ++j)
+      if (key_less(RA(j, j), RB(j, j), RA(best, best), RB(best, best), sigma)) best = j;
+    for (int j = best - 1; j >= pos; --j) swap_adjacent(RA, RB, YL, YR, j);
+  }
+  // unit-phase scaling: RB(j, j) real >= 0
+  for (int j = 0; j < n; ++j) {
+    const double mag = std::abs(RB(j, j));
+    if (mag > 0.0) {
+      const cd t = std::conj(RB(j, j)) / mag;
+      for (int c = j; c < n; ++c) {
+        RA(j, c) *= t;
+        RB(j, c) *= t;
+      }
+      RB(j, j) = mag;
+      for (int i = 0; i < n; ++i) YL(i, j) *= std::conj(t);
+    }
+  }
+  return true;
+}
+
+void m_factors(const SqMat& RA, const SqMat& RB, SqMat& MA, SqMat& MB) {
+  const int k = RA.n;
+  std::vector<cd> g1(k), g2(k);
+  for (int j = 0; j < k; ++j) {
+    const cd a = RA(j, j), b = RB(j, j);
+    if (std::abs(a) < std::abs(b)) {  // Eqs. G1_fix, G2_fix, tau_j = 0
+      g1[j] = 0.0;
+      g2[j] = 1.0 / b;
+    } else {                          // tau_j = 1
+      g1[j] = (1.0 - b) / a;
+      g2[j] = 1.0;
+    }
+  }
+  SqMat G(k);
+  for (int i = 0; i < k; ++i)
+    for (int j = i; j < k; ++j) G(i, j) = RA(i, j) * g1[j] + RB(i, j) * g2[j];
+  // X = G^{-1} RA by back substitution (G upper triangular, unit diagonal in exact arithmetic)
+  SqMat X(k);
+  for (int c = 0; c < k; ++c) {
+    for (int i = k - 1; i >= 0; --i) {
+      cd acc = RA(i, c);
+      for (int t = i + 1; t < k; ++t) acc -= G(i, t) * X(t, c);
+      X(i, c) = acc / G(i, i);
+    }
+  }
+  MA = SqMat(k);
+  MB = SqMat(k);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) {
+      MA(i, j) = g2[i] * X(i, j);
+      MB(i, j) = (i == j ? cd(1.0) : cd(0.0)) - g1[i] * X(i, j);
+    }
+}
+
+SqMat tri_eigvecs(const SqMat& RA, const SqMat& RB) {
+  const int k = RA.n;
+  SqMat Zv(k);
+  const double nA = fro(RA), nB = fro(RB);
+  for (int j = 0; j < k; ++j) {
+    const cd a = RA(j, j), b = RB(j, j);
+    const double small =
+        kEps * std::max(std::abs(b) * nA + std::abs(a) * nB, std::numeric_limits<double>::min());
+    Zv(j, j) = 1.0;
+    for (int i = j - 1; i >= 0; --i) {
+      cd rhs = 0.0;
+      for (int t = i + 1; t <= j; ++t) rhs -= (b * RA(i, t) - a * RB(i, t)) * Zv(t, j);
+      cd piv = b * RA(i, i) - a * RB(i, i);
+      if (std::abs(piv) < small) piv = small;
+      Zv(i, j) = rhs / piv;
+    }
+  }
+  return Zv;
+}
+
+}  // namespace gplhr

@@ -1,0 +1,290 @@
+"""ctypes binding to libgplhr (``include/gplhr.h``): argument marshalling only.
+
+Every function keeps the C name and forwards to the library; all arithmetic of the
+eigensolver runs in the CUDA kernels and host C++ of ``libgplhr.so``.  PyTorch is
+used only for device memory (``torch.Tensor.data_ptr()``) and streams.
+
+Blocks are row-major complex128 (n x w); host CSR matrices come from SciPy.
+If ``libgplhr.so`` has not been built, importing works but the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgplhr.so")
+
+GPLHR_OK, GPLHR_EINVAL, GPLHR_ENOMEM, GPLHR_ECUDA = 0, 1, 2, 3
+GPLHR_ENOTCONV, GPLHR_ESINGULAR, GPLHR_ENUMERIC, GPLHR_ETIMEOUT = 4, 5, 6, 7
+GPLHR_HOST, GPLHR_DEVICE = 0, 1
+GPLHR_R64, GPLHR_C128 = 0, 1
+PREC = {"none": 0, "jacobi": 1, "block_jacobi": 2, "csr": 3}
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ESINGULAR",
+                6: "ENUMERIC", 7: "ETIMEOUT"}
+
+EXPORTED = ["gplhr_create", "gplhr_solve", "gplhr_start", "gplhr_iterate", "gplhr_vectors",
+            "gplhr_destroy", "gplhr_last_error", "gplhr_spmm", "gplhr_precond_apply",
+            "gplhr_gram", "gplhr_orth", "gplhr_ordqz", "gplhr_mfactors"]
+
+
+class Csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("colind", C.c_void_p), ("vals", C.c_void_p), ("dtype", C.c_int32),
+                ("on_device", C.c_int32)]
+
+
+class Precond(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("block_size", C.c_int32), ("T_csr", C.POINTER(Csr))]
+
+
+class Opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("precision", C.c_int32),
+                ("no_lock", C.c_int32), ("reserved", C.c_int32), ("stream", C.c_void_p)]
+
+
+class Info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("nconv", C.c_int32), ("m", C.c_int32),
+                ("n_orth_fallback", C.c_int32), ("n_spmm", C.c_int64), ("n_prec", C.c_int64),
+                ("n_qz", C.c_int64), ("resid", C.c_double * 64)]
+
+
+class GplhrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libgplhr.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_1506_06829_gb300.build`")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, u64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+    dp = C.POINTER(C.c_double)
+    L.gplhr_create.argtypes = [C.POINTER(Csr), C.POINTER(Csr), dbl, dbl, i32, i32,
+                               C.POINTER(Precond), C.POINTER(Opts), C.POINTER(vp)]
+    L.gplhr_solve.argtypes = [vp, vp, i32, i32, u64, C.POINTER(Info)]
+    L.gplhr_start.argtypes = [vp, vp, i32, i32, u64]
+    L.gplhr_iterate.argtypes = [vp, i32, C.POINTER(Info)]
+    L.gplhr_vectors.argtypes = [vp, dp, dp, dp, vp, vp, vp, vp, vp, dp, i32]
+    L.gplhr_destroy.argtypes = [vp]
+    L.gplhr_destroy.restype = None
+    L.gplhr_last_error.argtypes = [vp]
+    L.gplhr_last_error.restype = C.c_char_p
+    L.gplhr_spmm.argtypes = [vp, vp, i32, i32, vp, i32, vp, i32]
+    L.gplhr_precond_apply.argtypes = [vp, vp, i32, i32, vp, i32]
+    L.gplhr_gram.argtypes = [vp, vp, i32, i32, vp, i32, i32, vp]
+    L.gplhr_orth.argtypes = [vp, vp, i32, i32, vp]
+    L.gplhr_ordqz.argtypes = [i32, dp, dp, dbl, dbl, dp, dp, dp, dp]
+    L.gplhr_mfactors.argtypes = [i32, dp, dp, dp, dp]
+    for name in EXPORTED:
+        f = getattr(L, name)
+        if f.restype is C.c_int:  # default
+            f.restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int, ctx=None):
+    if status != GPLHR_OK:
+        msg = lib().gplhr_last_error(ctx)
+        raise GplhrError(status, msg.decode() if msg else "")
+    return status
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class _HostCsr:
+    """Keeps the numpy arrays of a host CSR descriptor alive."""
+
+    def __init__(self, M):
+        self.indptr = np.ascontiguousarray(M.indptr, dtype=np.int32)
+        self.indices = np.ascontiguousarray(M.indices, dtype=np.int32)
+        if np.iscomplexobj(M.data):
+            self.data = np.ascontiguousarray(M.data, dtype=np.complex128)
+            dt = GPLHR_C128
+        else:
+            self.data = np.ascontiguousarray(M.data, dtype=np.float64)
+            dt = GPLHR_R64
+        self.desc = Csr(M.shape[0], self.indices.size, self.indptr.ctypes.data,
+                        self.indices.ctypes.data, self.data.ctypes.data, dt, 0)
+
+
+# ------------------------------------------------------------------ C names ----
+
+def gplhr_create(A, B, sigma: complex, k: int, m: int, precond: str = "none",
+                 block_size: int = 1, T=None, tol: float = 1e-8, maxit: int = 500,
+                 lock: bool = True, stream: int = 0):
+    """Returns an opaque context handle (int).  A, B: SciPy CSR (B None = identity)."""
+    L = lib()
+    hA = _HostCsr(A)
+    hB = _HostCsr(B) if B is not None else None
+    hT = _HostCsr(T.astype(np.complex128)) if T is not None else None
+    pc = Precond(PREC[precond], block_size, C.pointer(hT.desc) if hT else None)
+    opts = Opts(tol, maxit, 0, 0 if lock else 1, 0, stream or None)
+    out = C.c_void_p()
+    st = L.gplhr_create(C.byref(hA.desc), C.byref(hB.desc) if hB else None, sigma.real,
+                        sigma.imag, k, m, C.byref(pc), C.byref(opts), C.byref(out))
+    _check(st, None)
+    return out.value
+
+
+def gplhr_destroy(ctx):
+    lib().gplhr_destroy(ctx)
+
+
+def gplhr_last_error(ctx=None) -> str:
+    msg = lib().gplhr_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def _v0_args(V0):
+    if V0 is None:
+        return None, GPLHR_HOST, 0, None
+    if hasattr(V0, "data_ptr"):           # torch tensor
+        where = GPLHR_DEVICE if V0.is_cuda else GPLHR_HOST
+        return V0.data_ptr(), where, int(V0.is_complex()), V0
+    arr = np.ascontiguousarray(V0)
+    if np.iscomplexobj(arr):
+        arr = arr.astype(np.complex128)
+    else:
+        arr = arr.astype(np.float64)
+    return arr.ctypes.data, GPLHR_HOST, int(np.iscomplexobj(arr)), arr
+
+
+def gplhr_solve(ctx, V0=None, seed: int = 0, allow_notconv: bool = False) -> Info:
+    p, where, cplx, keep = _v0_args(V0)
+    info = Info()
+    st = lib().gplhr_solve(ctx, p, where, cplx, seed, C.byref(info))
+    if not (allow_notconv and st == GPLHR_ENOTCONV):
+        _check(st, ctx)
+    del keep
+    return info
+
+
+def gplhr_start(ctx, V0=None, seed: int = 0):
+    p, where, cplx, keep = _v0_args(V0)
+    _check(lib().gplhr_start(ctx, p, where, cplx, seed), ctx)
+    del keep
+
+
+def gplhr_iterate(ctx, niter: int) -> Info:
+    info = Info()
+    _check(lib().gplhr_iterate(ctx, niter, C.byref(info)), ctx)
+    return info
+
+
+def gplhr_vectors(ctx, n: int, k: int):
+    """Host copies of (alpha, beta, lambda, X, V, Q, RA, RB, resid)."""
+    alpha = np.zeros(2 * k)
+    beta = np.zeros(2 * k)
+    lam = np.zeros(2 * k)
+    X = np.zeros((n, k), dtype=np.complex128)
+    V = np.zeros((n, k), dtype=np.complex128)
+    Q = np.zeros((n, k), dtype=np.complex128)
+    RA = np.zeros((k, k), dtype=np.complex128)
+    RB = np.zeros((k, k), dtype=np.complex128)
+    resid = np.zeros(k)
+    _check(lib().gplhr_vectors(ctx, _dptr(alpha), _dptr(beta), _dptr(lam), X.ctypes.data,
+                               V.ctypes.data, Q.ctypes.data, RA.ctypes.data, RB.ctypes.data,
+                               _dptr(resid), GPLHR_HOST), ctx)
+    c = lambda a: a[0::2] + 1j * a[1::2]
+    return dict(alpha=c(alpha), beta=c(beta), lam=c(lam), X=X, V=V, Q=Q, RA=RA, RB=RB,
+                resid=resid)
+
+
+def gplhr_spmm(ctx, X, AX, BX=None):
+    """Device tensors (n x w complex128, row-major, may be column slices)."""
+    w = X.shape[1]
+    _check(lib().gplhr_spmm(ctx, X.data_ptr(), X.stride(0), w, AX.data_ptr(), AX.stride(0),
+                            BX.data_ptr() if BX is not None else None,
+                            BX.stride(0) if BX is not None else 0), ctx)
+
+
+def gplhr_precond_apply(ctx, X, Y):
+    _check(lib().gplhr_precond_apply(ctx, X.data_ptr(), X.stride(0), X.shape[1], Y.data_ptr(),
+                                     Y.stride(0)), ctx)
+
+
+def gplhr_gram(ctx, X, Y, Cout):
+    _check(lib().gplhr_gram(ctx, X.data_ptr(), X.stride(0), X.shape[1], Y.data_ptr(),
+                            Y.stride(0), Y.shape[1], Cout.data_ptr()), ctx)
+
+
+def gplhr_orth(ctx, X, Rinv=None):
+    _check(lib().gplhr_orth(ctx, X.data_ptr(), X.stride(0), X.shape[1],
+                            Rinv.data_ptr() if Rinv is not None else None), ctx)
+
+
+def gplhr_ordqz(Phi: np.ndarray, Psi: np.ndarray, sigma: complex):
+    """Host ordered QZ of the C library (no GPU needed)."""
+    s = Phi.shape[0]
+    P = np.ascontiguousarray(Phi, dtype=np.complex128)
+    S = np.ascontiguousarray(Psi, dtype=np.complex128)
+    out = [np.zeros((s, s), dtype=np.complex128) for _ in range(4)]
+    st = lib().gplhr_ordqz(s, _dptr(P.view(np.float64)), _dptr(S.view(np.float64)),
+                           sigma.real, sigma.imag, *[_dptr(o.view(np.float64)) for o in out])
+    _check(st, None)
+    return tuple(out)  # RA, RB, YL, YR
+
+
+def gplhr_mfactors(RA: np.ndarray, RB: np.ndarray):
+    k = RA.shape[0]
+    a = np.ascontiguousarray(RA, dtype=np.complex128)
+    b = np.ascontiguousarray(RB, dtype=np.complex128)
+    MA = np.zeros((k, k), dtype=np.complex128)
+    MB = np.zeros((k, k), dtype=np.complex128)
+    _check(lib().gplhr_mfactors(k, _dptr(a.view(np.float64)), _dptr(b.view(np.float64)),
+                                _dptr(MA.view(np.float64)), _dptr(MB.view(np.float64))), None)
+    return MA, MB
+
+
+class GPLHR:
+    """Owning handle around a gplhr context (marshalling only)."""
+
+    def __init__(self, A, B, sigma, k, m, precond="none", block_size=1, T=None, tol=1e-8,
+                 maxit=500, lock=True, stream=0):
+        self.n, self.k = A.shape[0], k
+        self.ctx = gplhr_create(A, B, complex(sigma), k, m, precond, block_size, T, tol, maxit,
+                                lock, stream)
+
+    def solve(self, V0=None, seed=0, allow_notconv=False):
+        return gplhr_solve(self.ctx, V0, seed, allow_notconv)
+
+    def start(self, V0=None, seed=0):
+        gplhr_start(self.ctx, V0, seed)
+
+    def iterate(self, niter):
+        return gplhr_iterate(self.ctx, niter)
+
+    def vectors(self):
+        return gplhr_vectors(self.ctx, self.n, self.k)
+
+    def close(self):
+        if self.ctx:
+            gplhr_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

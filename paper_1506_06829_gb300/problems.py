@@ -171,10 +171,10 @@ def sym_pencil3d_eigs(N: int) -> np.ndarray:
     return lam.ravel()
 
 
-# Largest-modulus eigenvalue of the 64^3 pencil with gamma = (0.4, 0.2, 0.1),
-# frozen as a literal (real part; the imaginary part is below 1e-6 relative).
-# Written by ``tests/golden/make_config2_lambda_max.py``.
-CONFIG2_LAMBDA_MAX = None  # filled in below once computed
+# Largest-modulus eigenvalue of the 64^3 pencil with gamma = (0.4, 0.2, 0.1)
+# (ARPACK on B^{-1} A; its imaginary part came out exactly 0), frozen as a literal.
+# Written by ``python -m paper_1506_06829_gb300.lambda_max 64``.
+CONFIG2_LAMBDA_MAX = 1359896.7265743553
 
 
 def config2(N: int = 64, lambda_max: float | None = None) -> Problem:

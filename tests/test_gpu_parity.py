@@ -1,0 +1,306 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (FP64 throughout; derivation): a length-L complex dot product has a
+relative rounding error below ~L u with u = 2^-53 ~ 1.1e-16 (different summation
+orders on the two sides), so kernel-level results are compared at 1e-12 relative to
+the norms involved.  Whole solves compare what is unique: eigenvalues to 1e-8
+relative (the target stated for the method), subspaces by principal angles
+<= 1e-6, and every residual <= tol.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+torch = pytest.importorskip("torch")
+
+from oracle import gplhr as OG
+from oracle.precond import build as oracle_precond
+from paper_1506_06829_gb300 import gplhr as G
+from paper_1506_06829_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    G.lib()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128)).to(DEV)
+
+
+def _host(t):
+    return t.cpu().numpy()
+
+
+def _rand_block(rng, n, w):
+    return rng.standard_normal((n, w)) + 1j * rng.standard_normal((n, w))
+
+
+def _angle(X, Y):
+    return float(np.max(sla.subspace_angles(X, Y)))
+
+
+# ------------------------------------------------------------------ SpMM ----
+
+@pytest.mark.parametrize("case", ["generalized_real", "complex_A", "ragged_w5", "ragged_w3", "wide_w40"])
+def test_spmm_parity(case):
+    rng = np.random.default_rng(1)
+    if case in ("generalized_real", "ragged_w5", "wide_w40"):
+        N = 10
+        A, B = P.convdiff3d(N, (0.4, 0.2, 0.1)), P.mass3d(N)
+        k = {"generalized_real": 8, "ragged_w5": 5, "wide_w40": 8}[case]
+        w = {"generalized_real": 8, "ragged_w5": 5, "wide_w40": 8}[case]
+        m = 1
+    else:
+        pr = P.config3(20)
+        A, B = pr.A, None
+        k, w, m = (16, 16, 2) if case == "complex_A" else (3, 3, 1)
+    n = A.shape[0]
+    ctx = G.gplhr_create(A, B, 0.1 + 0.2j, k, m)
+    try:
+        wide = 40 if case == "wide_w40" else w
+        Xh = _rand_block(rng, n, wide)
+        # strided views: X is a column slice of a wider tensor
+        Xbig = _dev(np.hstack([Xh, _rand_block(rng, n, 3)]))
+        X = Xbig[:, :wide]
+        AX = torch.zeros((n, wide + 2), dtype=torch.complex128, device=DEV)
+        BX = torch.zeros((n, wide + 2), dtype=torch.complex128, device=DEV)
+        G.gplhr_spmm(ctx, X, AX[:, :wide], BX[:, :wide] if B is not None else None)
+        torch.cuda.synchronize()
+        ref = A @ Xh
+        got = _host(AX)[:, :wide]
+        assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
+        assert np.all(_host(AX)[:, wide:] == 0)              # no writes past the block
+        if B is not None:
+            refB = B @ Xh
+            assert np.linalg.norm(_host(BX)[:, :wide] - refB) <= 1e-13 * np.linalg.norm(refB)
+    finally:
+        G.gplhr_destroy(ctx)
+
+
+# ------------------------------------------------------------ precond ----
+
+@pytest.mark.parametrize("kind,bs,N,gen", [("block_jacobi", 8, 10, True), ("block_jacobi", 16, 10, True),
+                                          ("block_jacobi", 16, 24, False), ("jacobi", 1, 24, False),
+                                          ("block_jacobi", 7, 9, True)])
+def test_precond_parity(kind, bs, N, gen):
+    rng = np.random.default_rng(2)
+    if gen:
+        A, B = P.convdiff3d(N, (0.4, 0.2, 0.1)), P.mass3d(N)
+        sigma = 900.0 + 60.0j
+    else:
+        A, B = P.config3(N).A, None
+        sigma = -2.0 - 0.5j
+    n = A.shape[0]
+    k = 8
+    ctx = G.gplhr_create(A, B, sigma, k, 1, precond=kind, block_size=bs)
+    try:
+        Xh = _rand_block(rng, n, k)
+        X = _dev(Xh)
+        Y = torch.zeros_like(X)
+        G.gplhr_precond_apply(ctx, X, Y)
+        T = oracle_precond(A, B, sigma, kind, bs)
+        ref = T.apply(Xh)
+        assert np.linalg.norm(_host(Y) - ref) <= 1e-12 * np.linalg.norm(ref)
+        G.gplhr_precond_apply(ctx, X, X)                       # in place
+        assert np.linalg.norm(_host(X) - ref) <= 1e-12 * np.linalg.norm(ref)
+    finally:
+        G.gplhr_destroy(ctx)
+
+
+# ------------------------------------------------------------ Gram / orth --
+
+@pytest.mark.parametrize("n,wx,wy", [(5000, 24, 48), (777, 8, 8), (100003, 16, 32), (33, 3, 5)])
+def test_gram_parity(n, wx, wy):
+    rng = np.random.default_rng(3)
+    A = sp.identity(n, format="csr")
+    k, m = (8, 7) if n >= 80 else (3, 1)
+    ctx = G.gplhr_create(A, None, 0.5, k, m)
+    try:
+        Xh, Yh = _rand_block(rng, n, wx), _rand_block(rng, n, wy)
+        Cd = torch.zeros((wx, wy), dtype=torch.complex128, device=DEV)
+        G.gplhr_gram(ctx, _dev(Xh), _dev(Yh), Cd)
+        ref = Xh.conj().T @ Yh
+        assert np.linalg.norm(_host(Cd) - ref) <= 1e-13 * np.linalg.norm(Xh) * np.linalg.norm(Yh)
+    finally:
+        G.gplhr_destroy(ctx)
+
+
+@pytest.mark.parametrize("n,w,cond", [(3000, 8, 1e2), (20000, 24, 1e6), (4096, 16, 1e10)])
+def test_orth_parity(n, w, cond):
+    """orth() = the unique thin QR factor with a real positive R diagonal (oracle: Householder)."""
+    rng = np.random.default_rng(4)
+    Uq, _ = np.linalg.qr(_rand_block(rng, n, w))
+    Vq, _ = np.linalg.qr(_rand_block(rng, w, w))
+    Xh = Uq @ np.diag(np.logspace(0, -np.log10(cond), w)) @ Vq
+    A = sp.identity(n, format="csr")
+    ctx = G.gplhr_create(A, None, 0.5, 8, 7)
+    try:
+        X = _dev(Xh)
+        G.gplhr_orth(ctx, X)
+        Qg = _host(X)
+        assert np.linalg.norm(Qg.conj().T @ Qg - np.eye(w)) <= 1e-13 * w
+        ref = OG.orth(Xh)
+        # the factors are unique; the accuracy of Q itself degrades like u * cond(X)
+        assert np.linalg.norm(Qg - ref) <= max(1e-12, 1e-15 * cond) * np.sqrt(w)
+    finally:
+        G.gplhr_destroy(ctx)
+
+
+# ----------------------------------------------------------- whole solves --
+
+def _compare_solutions(res_o, vec_g, k, tol, lam_rtol=1e-8, ang_tol=1e-6):
+    lo, lg = res_o.lam, vec_g["lam"]
+    # every GPU eigenvalue matches an oracle one (multiset), and vice versa
+    for mu in lg:
+        assert np.min(np.abs(lo - mu)) <= lam_rtol * abs(mu), (mu, lo)
+    for mu in lo:
+        assert np.min(np.abs(lg - mu)) <= lam_rtol * abs(mu), (mu, lg)
+    assert _angle(vec_g["V"], res_o.V) <= ang_tol
+    assert np.max(vec_g["resid"]) <= tol
+
+
+def test_solve_parity_schroedinger_small():
+    pr = P.config3(24)
+    o = OG.solve(pr.A, None, pr.sigma, pr.start_block(), m=pr.m, tol=pr.tol, maxit=300,
+                 precond=pr.precond, block_size=pr.block_size)
+    assert o.converged
+    with G.GPLHR(pr.A, None, pr.sigma, pr.k, pr.m, pr.precond, pr.block_size, tol=pr.tol,
+                 maxit=300) as s:
+        info = s.solve(pr.start_block())
+        vec = s.vectors()
+    assert info.iters <= 2 * o.iters + 5
+    _compare_solutions(o, vec, pr.k, pr.tol)
+    ev = sla.eigvals(pr.A.toarray())
+    want = ev[np.argsort(np.abs(ev - pr.sigma))[:pr.k]]
+    for mu in want:
+        assert np.min(np.abs(vec["lam"] - mu)) <= 1e-8 * abs(mu)
+    V = vec["V"]
+    assert np.linalg.norm(V.conj().T @ V - np.eye(pr.k)) <= 1e-12
+    # A V = V R (Eq. schur) with the returned R
+    assert np.linalg.norm(pr.A @ V - V @ vec["RA"]) <= 1e-7 * OG.onenorm(pr.A)
+
+
+def test_solve_parity_generalized_exact_preconditioner():
+    """Generalized 3-D pencil with T = (A - sigma B)^{-1} given explicitly (CSR)."""
+    N = 6
+    A, B = P.convdiff3d(N, (0.4, 0.2, 0.1)), P.mass3d(N)
+    sigma = 300.0 + 40.0j
+    n, k = A.shape[0], 4
+    Tm = np.linalg.inv(A.toarray() - sigma * B.toarray())
+    Tcsr = sp.csr_matrix(Tm)
+    V0 = P.start_block(n, k, 77)
+    from oracle.precond import Preconditioner
+    To = Preconditioner("block_jacobi", blocks=[Tm], bs=n)
+    o = OG.solve(A, B, sigma, V0, m=1, tol=1e-10, maxit=100, T=To)
+    assert o.converged
+    with G.GPLHR(A, B, sigma, k, 1, "csr", T=Tcsr, tol=1e-10, maxit=100) as s:
+        s.solve(V0)
+        vec = s.vectors()
+    _compare_solutions(o, vec, k, 1e-10)
+    ev = sla.eigvals(A.toarray(), B.toarray())
+    want = ev[np.argsort(np.abs(ev - sigma))[:k]]
+    for mu in want:
+        assert np.min(np.abs(vec["lam"] - mu)) <= 1e-8 * abs(mu)
+    # partial generalized Schur form (Eq. gschur) and Prop. 3.2
+    V, Q = vec["V"], vec["Q"]
+    nA = OG.onenorm(A)
+    assert np.linalg.norm(A @ V - Q @ vec["RA"]) <= 1e-8 * nA
+    assert np.linalg.norm(B @ V - Q @ vec["RB"]) <= 1e-8 * nA
+    assert np.linalg.norm(Q.conj().T @ Q - np.eye(k)) <= 1e-12
+
+
+def test_one_step_parity_generalized_block_jacobi():
+    """Same start block, same number of iterations: the Ritz values and the nested
+    Schur subspaces of the GPU iterate equal the oracle's (orth and QZ bases differ
+    only by unitary factors that the harmonic projection removes)."""
+    N = 8
+    A, B = P.convdiff3d(N, (0.4, 0.2, 0.1)), P.mass3d(N)
+    lmax = 21295.965461059128           # dense eigvals of this 8^3 pencil
+    sigma = complex(0.3 * lmax, 0.05 * lmax)
+    n, k, m = A.shape[0], 8, 1
+    V0 = P.start_block(n, k, 1002)
+    T = oracle_precond(A, B, sigma, "block_jacobi", 8)
+    pen = OG.Pencil(A, B, sigma, T)
+    st = OG.init_state(pen, V0, m)
+    with G.GPLHR(A, B, sigma, k, m, "block_jacobi", 8, tol=1e-14, maxit=10, lock=False) as s:
+        s.start(V0)
+        for it in range(3):
+            st = OG.iterate(pen, st)
+            s.iterate(1)
+            vec = s.vectors()
+            lo = np.diag(st.RA) / np.diag(st.RB)
+            assert np.allclose(vec["lam"], lo, rtol=1e-9, atol=0), (it, vec["lam"], lo)
+            for j in range(1, k + 1):
+                assert _angle(vec["V"][:, :j], st.V[:, :j]) <= 1e-7, (it, j)
+
+
+def test_jacobi_constant_diagonal_is_identity_and_notconv_status():
+    """Config-1 shape (32 x 32 convection-diffusion, sigma at the spectrum's midpoint):
+    the constant Jacobi diagonal makes T = I; a short run returns ENOTCONV with the
+    results readable, like the paper's DNC."""
+    pr = P.config1()
+    with G.GPLHR(pr.A, None, pr.sigma, pr.k, pr.m, "jacobi", tol=pr.tol, maxit=5) as s:
+        with pytest.raises(G.GplhrError) as e:
+            s.solve(pr.start_block())
+        assert e.value.status == G.GPLHR_ENOTCONV
+        vec = s.vectors()
+        assert np.all(np.isfinite(vec["lam"]))
+        V = vec["V"]
+        assert np.linalg.norm(V.conj().T @ V - np.eye(pr.k)) <= 1e-12
+
+
+# -------------------------------------------------- full-size, sampled checks --
+
+@pytest.mark.parametrize("cfg", ["config2", "config3"])
+def test_full_size_sampled(cfg):
+    """Full-size workloads (n = 262144 / 65536) in the configuration the benchmark
+    times: after start + 2 iterations, (i) sampled rows of the SpMM against the
+    oracle's sparse rows, (ii) V, Q orthonormal, (iii) Prop. 3.2
+    (A - sigma B) V = Q (R_A - sigma R_B) with fresh products, (iv) the library's
+    residuals equal the oracle's residual formula on the returned vectors."""
+    pr = P.config2() if cfg == "config2" else P.config3()
+    n, k = pr.n, pr.k
+    rng = np.random.default_rng(5)
+    with G.GPLHR(pr.A, pr.B, pr.sigma, k, pr.m, pr.precond, pr.block_size, tol=pr.tol,
+                 maxit=10) as s:
+        s.start(pr.start_block())
+        s.iterate(2)
+        vec = s.vectors()
+        V, Q = vec["V"], vec["Q"]
+        # (i) sampled SpMM rows
+        Xh = _rand_block(rng, n, k)
+        AX = torch.zeros((n, k), dtype=torch.complex128, device=DEV)
+        BX = torch.zeros((n, k), dtype=torch.complex128, device=DEV)
+        G.gplhr_spmm(s.ctx, _dev(Xh), AX, BX if pr.B is not None else None)
+        rows = rng.choice(n, 200, replace=False)
+        refA = pr.A[rows] @ Xh
+        assert np.linalg.norm(_host(AX)[rows] - refA) <= 1e-13 * np.linalg.norm(refA)
+        if pr.B is not None:
+            refB = pr.B[rows] @ Xh
+            assert np.linalg.norm(_host(BX)[rows] - refB) <= 1e-13 * np.linalg.norm(refB)
+    assert np.linalg.norm(V.conj().T @ V - np.eye(k)) <= 1e-12
+    assert np.linalg.norm(Q.conj().T @ Q - np.eye(k)) <= 1e-12
+    Bm = sp.identity(n) if pr.B is None else pr.B
+    lhs = pr.A @ V - pr.sigma * (Bm @ V)
+    if pr.B is None:
+        # B = I: RA is R, and Q spans (A - sigma I) V; use the QZ form via Q^* (A - sigma) V
+        QR = Q @ (Q.conj().T @ lhs)
+    else:
+        QR = Q @ (vec["RA"] - pr.sigma * vec["RB"])
+    assert np.linalg.norm(lhs - QR) <= 1e-10 * np.linalg.norm(lhs)
+    X = vec["X"]
+    a, b = vec["alpha"], vec["beta"]
+    E = (pr.A @ X) * b[None, :] - (Bm @ X) * a[None, :]
+    ref = np.linalg.norm(E, axis=0) / ((np.abs(b) * OG.onenorm(pr.A)
+                                        + np.abs(a) * OG.onenorm(pr.B)) * np.linalg.norm(X, axis=0))
+    assert np.allclose(vec["resid"], ref, rtol=1e-6, atol=1e-15)
