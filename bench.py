@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the GPLHR hot path on one GB300 (or N replicas).
+
+Workload (default): the generalized 3-D convection-diffusion pencil, 64^3 grid
+(n = 262144), gamma = (0.4, 0.2, 0.1), B = M x M x M (27-point mass matrix),
+sigma = (0.3 + 0.05i) lambda_max, k = 8, m = 1, block-Jacobi 8 x 8 on A - sigma B,
+FP64 / complex128.  A "step" is one pass of the while loop of Algorithm 2
+(residual, projected preconditioning, Krylov-Arnoldi block, P block, test basis,
+projected pencil, sorted QZ, basis update) plus the convergence/locking check.
+
+value        seconds per GPLHR iteration, inputs resident in HBM (device time between
+             CUDA events on the library's stream; the host QZ inside each iteration
+             is part of it).  On this workload the k nearest eigenpairs are NOT
+             reached in practical time (the distances |lambda - sigma| of the
+             eigenvalues around Re sigma differ by ~1e-7 relative), so "seconds to k
+             eigenpairs" is reported on the complex-scaled Schroedinger workload
+             (256^2, k = 16, m = 2) under "solve".
+e2e          the same metric through the C ABI from HOST buffers: gplhr_create (CSR
+             upload, preconditioner set-up) + gplhr_solve from a host V0 for K
+             iterations + gplhr_vectors to host, divided by K.
+roofline     dominant kernel class by device time, achieved = algorithmic flops /
+             event time of its launches inside the timed region.
+cpu_baseline the CPU oracle (NumPy, FP64) on a bounded sample (3 iterations).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gplhr|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "s to k eigenpairs @1e-8 resid (FP64 vs mixed); SpMM+Gram HBM GB/s vs peak"
+FP64_PEAK_GFLOPS = 1250.0   # GB300 dense FP64 (profiling recipe table); probe measured 1203
+KCLASSES = ["spmm", "gram", "combine", "precond", "chol", "other"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gplhr", choices=["gplhr", "reference"])
+    ap.add_argument("--workload", default="config2", choices=["config2", "config3"])
+    ap.add_argument("--no-solve", action="store_true", help="skip the time-to-k-pairs solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def problem(name):
+    from paper_1506_06829_gb300 import problems as P
+    return P.config2() if name == "config2" else P.config3()
+
+
+def workload_config(pr, name):
+    return {
+        "workload": f"{pr.name} ({'generalized 3-D convection-diffusion, B = MxMxM' if name == 'config2' else 'complex-scaled 2-D Schroedinger, B = I'})",
+        "n": pr.n, "nnz_A": int(pr.A.nnz), "nnz_B": int(pr.B.nnz) if pr.B is not None else 0,
+        "k": pr.k, "m": pr.m, "precond": f"{pr.precond}_{pr.block_size}",
+        "sigma": [pr.sigma.real, pr.sigma.imag], "tol": pr.tol,
+        "l2": "working set Z, U, AZ, BZ = 4 x n x (m+3)k x 16 B > 129 MB L2; no flush",
+    }
+
+
+# ---------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle ----
+
+def oracle_iterations(pr, iters: int, warm: int = 0):
+    """Times `iters` oracle iterations (after `warm` untimed ones); returns s/iteration."""
+    from oracle import gplhr as OG
+    from oracle.precond import build
+    T = build(pr.A, pr.B, pr.sigma, pr.precond, pr.block_size)
+    pen = OG.Pencil(pr.A, pr.B, pr.sigma, T)
+    st = OG.init_state(pen, pr.start_block(), pr.m)
+    for _ in range(warm):
+        st = OG.iterate(pen, st)
+        OG.residuals(pen, st)
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        st = OG.iterate(pen, st)
+        OG.residuals(pen, st)      # the convergence check is part of a step
+    return (time.perf_counter() - t0) / iters
+
+
+def cpu_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max((d.get("num_threads", 1) for d in info), default=os.cpu_count())
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    pr = problem(args.workload)
+    K, W = max(1, args.steps), max(0, args.warmup)
+    spi = oracle_iterations(pr, K, W)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": spi, "unit": "s/iteration",
+        "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": spi * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic", "config": workload_config(pr, args.workload),
+        "cpu_baseline": {"value": spi, "unit": "s/iteration", "cores": cpu_threads(),
+                         "kind": "oracle", "sample": f"{K} timed iterations after {W} warm-up"},
+        "e2e": {"value": spi, "unit": "s/iteration", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------- GPU arm ----
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1506_06829_gb300 import gplhr as G
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    K, W = max(1, args.steps), max(3, args.warmup)
+    pr = problem(args.workload)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    stream = torch.cuda.Stream(device=dev)
+    solver = G.GPLHR(pr.A, pr.B, pr.sigma, pr.k, pr.m, pr.precond, pr.block_size, tol=pr.tol,
+                     maxit=10 ** 6, stream=stream.cuda_stream)
+    solver.start(pr.start_block())
+    solver.iterate(W)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    G.gplhr_profile(solver.ctx, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    it_before = solver.iterate(0).iters
+    ev0.record(stream)
+    info = solver.iterate(K)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    done = info.iters - it_before
+    if done != K:
+        raise RuntimeError(f"expected {K} iterations, ran {done} (converged early?)")
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    per_class = {}
+    total_launch = 0
+    for c in KCLASSES:
+        cms, nl, fl, by = G.gplhr_profile_read(solver.ctx, c)
+        per_class[c] = {"ms": cms, "launches": nl, "gflop": fl / 1e9, "gbyte": by / 1e9}
+        total_launch += nl
+    G.gplhr_profile(solver.ctx, False)
+    kern_ms = sum(v["ms"] for v in per_class.values())
+    dom = max(per_class, key=lambda c: per_class[c]["ms"])
+    d = per_class[dom]
+    achieved_gflops = d["gflop"] / (d["ms"] / 1e3) if d["ms"] > 0 else 0.0
+    achieved_gbs = d["gbyte"] / (d["ms"] / 1e3) if d["ms"] > 0 else 0.0
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    roofline = {
+        "kernel": dom, "bound": "alu", "achieved": achieved_gflops, "peak": FP64_PEAK_GFLOPS,
+        "unit": "GFLOP/s", "frac": achieved_gflops / FP64_PEAK_GFLOPS, "traffic": None,
+        "note": ("FP64 DFMA-bound: algorithmic flops (complex multiply-add = 8) / event time of the "
+                 f"{d['launches']} {dom} launches; its algorithmic bytes give {achieved_gbs:.0f} GB/s "
+                 f"= {achieved_gbs / hbm_peak:.3f} of the measured HBM copy bandwidth"),
+    }
+    spmm, gram = per_class["spmm"], per_class["gram"]
+    hbm = {c: {"GB/s": (per_class[c]["gbyte"] / (per_class[c]["ms"] / 1e3)) if per_class[c]["ms"] else 0.0}
+           for c in ("spmm", "gram")}
+    for c in hbm:
+        hbm[c]["frac_of_measured_peak"] = hbm[c]["GB/s"] / hbm_peak
+    s_per_iter = ms / 1e3 / K
+    value = s_per_iter / world          # whole-job: N replicas each ran K iterations
+    line = {
+        "metric": METRIC, "value": value, "unit": "s/iteration", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms / K, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": dict(workload_config(pr, args.workload), parallelism=f"replicas{world}"),
+        "roofline": roofline, "gpu_launches": total_launch,
+        "kernels": {c: {"share": per_class[c]["ms"] / kern_ms if kern_ms else 0.0,
+                        "ms_per_step": per_class[c]["ms"] / K,
+                        "launches_per_step": per_class[c]["launches"] / K} for c in KCLASSES},
+        "hbm_spmm_gram": hbm,
+        "clocks": clocks,
+    }
+    solver.close()
+
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e(pr, K, stream, G)
+    if rank == 0 and not args.no_solve:
+        line["solve"] = time_to_pairs(G, stream)
+    if rank == 0 and not args.no_cpu:
+        sample = 3
+        spi = oracle_iterations(pr, sample, 0)
+        line["cpu_baseline"] = {"value": spi, "unit": "s/iteration", "cores": cpu_threads(),
+                                "kind": "oracle", "sample": f"{sample} oracle iterations of this workload"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def e2e(pr, K, stream, G):
+    """create (host CSR) + solve from a host V0 for K iterations + vectors to host."""
+    import torch
+    V0 = pr.start_block()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = G.GPLHR(pr.A, pr.B, pr.sigma, pr.k, pr.m, pr.precond, pr.block_size, tol=pr.tol, maxit=K,
+                stream=stream.cuda_stream)
+    info = s.solve(V0, allow_notconv=True)
+    vec = s.vectors()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    s.close()
+    csr_bytes = sum(M.data.nbytes + M.indices.nbytes + M.indptr.nbytes
+                    for M in (pr.A, pr.B) if M is not None)
+    out_bytes = sum(vec[x].nbytes for x in ("X", "V", "Q", "RA", "RB"))
+    return {"value": dt / K, "unit": "s/iteration",
+            "h2d_bytes_per_step": (csr_bytes + V0.nbytes + info.h2d_bytes) / K,
+            "d2h_bytes_per_step": (out_bytes + info.d2h_bytes) / K,
+            "iterations": info.iters}
+
+
+def time_to_pairs(G, stream):
+    """Seconds to k eigenpairs at the residual target, complex-scaled Schroedinger 256^2."""
+    import torch
+    from paper_1506_06829_gb300 import problems as P
+    pr = P.config3()
+    s = G.GPLHR(pr.A, None, pr.sigma, pr.k, pr.m, pr.precond, pr.block_size, tol=pr.tol,
+                maxit=2000, stream=stream.cuda_stream)
+    V0 = torch.from_numpy(pr.start_block()).to("cuda")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    info = s.solve(V0, allow_notconv=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    vec = s.vectors()
+    s.close()
+    return {"workload": f"{pr.name} (complex-scaled Schroedinger, n = {pr.n}, k = {pr.k}, m = {pr.m}, "
+                        f"block-Jacobi {pr.block_size}, tol {pr.tol})",
+            "s_to_k_pairs": e0.elapsed_time(e1) / 1e3, "iterations": info.iters,
+            "converged": bool(info.nconv == pr.k), "max_resid": float(max(vec["resid"]))}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -108,6 +108,9 @@ typedef struct {
   int64_t n_spmm;
   int64_t n_prec;
   int64_t n_qz;
+  int64_t n_launch;     /* CUDA kernels launched (since create or gplhr_profile)       */
+  int64_t h2d_bytes;    /* host->device bytes moved by the iteration since start        */
+  int64_t d2h_bytes;    /* device->host bytes (projected pencil for the host QZ, norms) */
   double resid[64];     /* first min(k, 64) residuals                                  */
 } gplhr_info;
 
@@ -190,6 +193,18 @@ gplhr_status gplhr_gram(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t wx, 
  * first pass and a third pass when the Gram matrix is not numerically positive
  * definite).  Rinv (w x w, may be NULL) receives R^{-1}. */
 gplhr_status gplhr_orth(gplhr_ctx* ctx, void* X, int32_t ldx, int32_t w, void* Rinv);
+
+/* Instrumentation.  gplhr_profile(ctx, 1) clears the per-kernel-class counters and
+ * brackets every later launch section with CUDA events on the context's stream;
+ * gplhr_profile(ctx, 0) stops the timing (counters keep counting).
+ * gplhr_profile_read returns for kernel class kclass -- 0 SpMM, 1 Gram, 2 block
+ * combine (tall-skinny times small), 3 preconditioner, 4 small Cholesky, 5 other
+ * elementwise -- the summed event time (ms, while profiling), the kernel launches,
+ * and the ALGORITHMIC flops (complex multiply-add = 8, real x complex = 4) and bytes
+ * (each operand read once, each result written once) of those launches. */
+gplhr_status gplhr_profile(gplhr_ctx* ctx, int32_t enable);
+gplhr_status gplhr_profile_read(gplhr_ctx* ctx, int32_t kclass, double* ms, int64_t* launches,
+                                double* flops, double* bytes);
 
 /* Ordered complex QZ of a small pencil on the host (footnote to Alg. 2 step 2):
  * Phi = YL RA YR^*, Psi = YL RB YR^* with |RA(j,j)/RB(j,j) - sigma| non-decreasing

@@ -166,7 +166,7 @@ def iterate(pen: Pencil, st: State) -> State:
         Sl = orth(Sl)
         S.append(Sl)
         S_prev = Sl
-    Sc = np.hstack(S)
+    Sc = np.hstack(S) if S else np.zeros((pen.n, 0), dtype=np.complex128)
     blocks = [W] + S
     if P is not None:
         P = P[:, :k - q]                                   # soft locking: k - q columns

@@ -62,7 +62,7 @@ struct gplhr_ctx {
   // device buffers
   double2 *Z = nullptr, *AZ = nullptr, *BZ = nullptr, *U = nullptr;
   double2 *Pb = nullptr, *APb = nullptr, *BPb = nullptr;
-  double2 *Rw = nullptr, *Tw1 = nullptr, *Tw2 = nullptr;
+  double2 *Rw = nullptr, *Tw1 = nullptr, *Tw2 = nullptr, *Tw3 = nullptr;  // Rw holds the residual
   double2 *dC1 = nullptr, *dC2 = nullptr, *dMBa = nullptr, *dMAa = nullptr;
   double2 *dYR = nullptr, *dYL = nullptr, *dPhiPsi = nullptr, *dGram = nullptr, *dProjC = nullptr;
   double2* dRinv = nullptr;  // 3 x s_max^2
@@ -83,7 +83,14 @@ struct gplhr_ctx {
   int q = 0, m = 0, it = 0;
   SqMat RA, RB, MA, MB;
   std::vector<double> resid;
-  int64_t n_spmm = 0, n_prec = 0, n_qz = 0;
+  int64_t n_spmm = 0, n_prec = 0, n_qz = 0, n_launch = 0;
+  int64_t h2d_bytes = 0, d2h_bytes = 0;  // host<->device traffic of the iteration
+  // per-kernel-class accounting (always) and CUDA-event timing (when profiling)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_rec;  // (class, start event index); stop = start + 1
+  double k_flops[8] = {0}, k_bytes[8] = {0};
+  int64_t k_launch[8] = {0};
   std::string err;
 };
 
@@ -116,6 +123,31 @@ int grid_for(size_t work, int per_cta, int cap) {
   return (int)g;
 }
 
+// ----------------------------------------------------------- accounting ----
+// Kernel classes for the per-class report (gplhr_profile_read).
+enum { KC_SPMM = 0, KC_GRAM = 1, KC_COMBINE = 2, KC_PREC = 3, KC_CHOL = 4, KC_OTHER = 5, KC_N = 6 };
+
+// Opens a timed section of class c (one or more launches); returns its handle.
+int prof_begin(gplhr_ctx* ctx, int c, double flops, double bytes, int launches = 1) {
+  ctx->k_flops[c] += flops;
+  ctx->k_bytes[c] += bytes;
+  ctx->k_launch[c] += launches;
+  ctx->n_launch += launches;
+  if (!ctx->prof_on) return -1;
+  const int idx = (int)ctx->ev_rec.size() * 2;
+  while ((int)ctx->ev_pool.size() < idx + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    ctx->ev_pool.push_back(e);
+  }
+  cudaEventRecord(ctx->ev_pool[idx], ctx->stream);
+  ctx->ev_rec.emplace_back(c, idx);
+  return idx;
+}
+void prof_end(gplhr_ctx* ctx, int h) {
+  if (h >= 0) cudaEventRecord(ctx->ev_pool[h + 1], ctx->stream);
+}
+
 // ------------------------------------------------------------------ launches --
 
 gplhr_status launch_spmm_one(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, Blk X, int w, Blk Y,
@@ -123,6 +155,15 @@ gplhr_status launch_spmm_one(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, 
   const int threads = 256;
   const int grid = grid_for((size_t)ctx->n, threads / 32, ctx->num_sms * 16);
   const bool has2 = M2 != nullptr;
+  auto mat_cost = [&](const DevCsr& D, double& fl, double& by) {
+    const bool cplx = D.dtype == GPLHR_C128;
+    fl += (cplx ? 8.0 : 4.0) * (double)D.nnz * w;                 // real x complex = 2 FMA
+    by += (double)D.nnz * ((cplx ? 16.0 : 8.0) + 4.0) + 4.0 * (ctx->n + 1.0) + 16.0 * ctx->n * w;
+  };
+  double fl = 0.0, by = 16.0 * ctx->n * w;  // X read once
+  mat_cost(M, fl, by);
+  if (has2) mat_cost(*M2, fl, by);
+  const int ph = prof_begin(ctx, KC_SPMM, fl, by);
   gplhr::CsrDev<double> dr{M.rowptr, M.col, (const double*)M.val};
   gplhr::CsrDev<double2> dc{M.rowptr, M.col, (const double2*)M.val};
   if (!has2) {
@@ -149,6 +190,7 @@ gplhr_status launch_spmm_one(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, 
       gplhr::spmm_kernel<double2, double2><<<grid, threads, 0, ctx->stream>>>(ctx->n, dc, bc, 1, X.p, X.ld, w,
                                                                               Y.p, Y.ld, Y2.p, Y2.ld);
   }
+  prof_end(ctx, ph);
   CK(cudaGetLastError());
   return GPLHR_OK;
 }
@@ -175,10 +217,14 @@ gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy
   nchunk = (ctx->n + rows - 1) / rows;
   dim3 grid(nchunk, ntile);
   const size_t smem = (size_t)gplhr::GRAM_ROWS * (wx + wy) * sizeof(double2);
+  const bool self = X.p == Y0.p && wy1 == 0;
+  const double by = 16.0 * ctx->n * (self ? wx : wx + wy);
+  const int ph = prof_begin(ctx, KC_GRAM, 8.0 * ctx->n * wx * wy, by, 2);
   gplhr::gram_partial_kernel<<<grid, gplhr::GRAM_THREADS, smem, ctx->stream>>>(
       ctx->n, rows, X.p, X.ld, wx, Y0.p, Y0.ld, wy0, Y1.p, Y1.ld, wy1, ctx->gram_part, skip);
   CK(cudaGetLastError());
   gplhr::gram_reduce_kernel<<<(nout + 255) / 256, 256, 0, ctx->stream>>>(nchunk, nout, ctx->gram_part, C, skip);
+  prof_end(ctx, ph);
   CK(cudaGetLastError());
   return GPLHR_OK;
 }
@@ -219,18 +265,40 @@ gplhr_status combine(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, b
   const int rows_per_cta = (ctx->n + grid - 1) / grid;
   a.normpart = c_store < c ? ctx->norm_part : nullptr;
   const size_t smem = (size_t)(wsum * c + rows_tile * wsum + rows_tile * c) * sizeof(double2);
+  double by = 16.0 * ctx->n * (wsum + c_store * (beta_one ? 2.0 : 1.0));
+  const int ph = prof_begin(ctx, KC_COMBINE, 8.0 * ctx->n * wsum * c, by, c_store < c ? 2 : 1);
   gplhr::combine_kernel<<<grid, gplhr::COMB_THREADS, smem, ctx->stream>>>(ctx->n, rows_per_cta, a);
   CK(cudaGetLastError());
   if (c_store < c) {
     gplhr::norm_reduce_kernel<<<1, 128, 0, ctx->stream>>>(grid, c - c_store, ctx->norm_part, ctx->d_norms);
     CK(cudaGetLastError());
   }
+  prof_end(ctx, ph);
   return GPLHR_OK;
 }
+
+gplhr_status precond_apply_impl(gplhr_ctx* ctx, Blk X, int w, Blk Y);
 
 gplhr_status precond_apply(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
   if (w <= 0) return GPLHR_OK;
   ctx->n_prec += 1;
+  if (ctx->prec == GPLHR_PREC_CSR) return precond_apply_impl(ctx, X, w, Y);  // counted as SpMM
+  const double n = ctx->n;
+  double fl = 0.0, by = 32.0 * n * w;
+  if (ctx->prec == GPLHR_PREC_JACOBI) {
+    fl = 6.0 * n * w;
+    by += 16.0 * n;
+  } else if (ctx->prec == GPLHR_PREC_BLOCK_JACOBI) {
+    fl = 8.0 * n * ctx->bs * w;
+    by += 16.0 * ((n + ctx->bs - 1) / ctx->bs) * ctx->bs * ctx->bs;
+  }
+  const int ph = prof_begin(ctx, KC_PREC, fl, by, (ctx->prec == GPLHR_PREC_NONE && X.p == Y.p) ? 0 : 1);
+  gplhr_status st = precond_apply_impl(ctx, X, w, Y);
+  prof_end(ctx, ph);
+  return st;
+}
+
+gplhr_status precond_apply_impl(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
   const int n = ctx->n;
   switch (ctx->prec) {
     case GPLHR_PREC_NONE: {
@@ -303,8 +371,10 @@ gplhr_status orth_against(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w, const std
     TRY(gram(ctx, X, w, X, w, Blk{nullptr, 0}, 0, ctx->dGram, skip));
     double2* Rinv = ctx->dRinv + (size_t)pass * smax2;
     const size_t smem = (size_t)2 * w * w * sizeof(double2);
+    const int ph = prof_begin(ctx, KC_CHOL, 8.0 * w * w * w / 2.0, 48.0 * w * w);
     gplhr::chol_inv_kernel<<<1, 256, smem, ctx->stream>>>(w, (int64_t)ctx->n, ctx->dGram, Rinv,
                                                           ctx->d_status + pass, skip, ctx->d_diag);
+    prof_end(ctx, ph);
     CK(cudaGetLastError());
     TRY(combine(ctx, {In{X, w, Rinv, kOne}}, X, w, false, skip));
     for (const Extra& e : ex) TRY(combine(ctx, {In{e.E, w, Rinv, kOne}}, e.E, w, false, skip));
@@ -313,6 +383,7 @@ gplhr_status orth_against(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w, const std
 }
 
 gplhr_status upload(gplhr_ctx* ctx, double2* dst, const double2* src, size_t elems) {
+  ctx->h2d_bytes += (int64_t)(elems * sizeof(double2));
   CK(cudaMemcpyAsync(dst, src, elems * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
   return GPLHR_OK;
 }
@@ -346,6 +417,7 @@ gplhr_status residuals(gplhr_ctx* ctx) {
   TRY(upload(ctx, ctx->dC2, h2, 2 * k * k));
   TRY(combine(ctx, {In{blkAZ(ctx, 0), k, ctx->dC1, kOne}, In{blkBZ(ctx, 0), k, ctx->dC2, kMinusOne}},
               Blk{ctx->Rw, k}, 2 * k, false, nullptr, Blk{nullptr, 0}, k, k));
+  ctx->d2h_bytes += k * sizeof(double) + 2 * sizeof(int);
   CK(cudaMemcpyAsync(ctx->h_norms, ctx->d_norms, k * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(ctx->h_diag, ctx->d_diag, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -410,15 +482,18 @@ gplhr_status start(gplhr_ctx* ctx) {
   ctx->m = ctx->m0;
   ctx->hasP = false;
   ctx->n_spmm = ctx->n_prec = ctx->n_qz = 0;
+  ctx->h2d_bytes = ctx->d2h_bytes = 0;
   CK(cudaMemsetAsync(ctx->d_diag, 0, 2 * sizeof(int), ctx->stream));
   TRY(orth_against(ctx, Blk{nullptr, 0}, 0, blkZ(ctx, 0), k));                // V = orth(V0)
   TRY(spmm_AB(ctx, blkZ(ctx, 0), k, blkAZ(ctx, 0), blkBZ(ctx, 0)));        // AV, BV
   const double2 ms = d2(-ctx->sigma);
+  prof_begin(ctx, KC_OTHER, 8.0 * ctx->n * k, 48.0 * ctx->n * k);
   gplhr::axpby_kernel<<<grid_for((size_t)ctx->n * k, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
       ctx->n, k, kOne, ctx->AZ, ctx->s_max, ms, blkBZ(ctx, 0).p, ctx->s_max, ctx->U, ctx->s_max);
   CK(cudaGetLastError());
   TRY(orth_against(ctx, Blk{nullptr, 0}, 0, blkU(ctx, 0), k));                // Q = orth((A - sigma B) V)
   TRY(gram(ctx, blkU(ctx, 0), k, blkAZ(ctx, 0), k, blkBZ(ctx, 0), k, ctx->dPhiPsi));
+  ctx->d2h_bytes += (int64_t)2 * k * k * sizeof(double2);
   CK(cudaMemcpyAsync(ctx->h_phipsi, ctx->dPhiPsi, (size_t)2 * k * k * sizeof(double2), cudaMemcpyDeviceToHost,
                      ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -495,6 +570,7 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
   const int pslot = k + (m + 1) * kk;
   if (ctx->hasP && kk > 0) {
     const size_t nw = (size_t)ctx->n;
+    prof_begin(ctx, KC_OTHER, 0.0, 32.0 * ctx->n * kk * (ctx->hasB ? 3 : 2), ctx->hasB ? 3 : 2);
     gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
         ctx->n, kk, ctx->Pb, k, ctx->Z + pslot, sm);
     gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
@@ -511,12 +587,15 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
   const int s = pslot + sP;
   const int sk = s - k;
   // steps 23-24: Qhat = orth((A - sigma B) [W S P]) against Q;  U = [Q Qhat]
+  const int ph_ax = prof_begin(ctx, KC_OTHER, 8.0 * ctx->n * sk, 48.0 * ctx->n * sk);
   gplhr::axpby_kernel<<<grid_for((size_t)ctx->n * sk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
       ctx->n, sk, kOne, ctx->AZ + k, sm, d2(-ctx->sigma), blkBZ(ctx, k).p, sm, ctx->U + k, sm);
+  prof_end(ctx, ph_ax);
   CK(cudaGetLastError());
   TRY(orth_against(ctx, Q, k, blkU(ctx, k), sk));
   // step 24: projected pencil (U^* A Z, U^* B Z)
   TRY(gram(ctx, blkU(ctx, 0), s, blkAZ(ctx, 0), s, blkBZ(ctx, 0), s, ctx->dPhiPsi));
+  ctx->d2h_bytes += (int64_t)2 * s * s * sizeof(double2);
   CK(cudaMemcpyAsync(ctx->h_phipsi, ctx->dPhiPsi, (size_t)2 * s * s * sizeof(double2), cudaMemcpyDeviceToHost,
                      ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -556,6 +635,9 @@ void fill_info(gplhr_ctx* ctx, gplhr_info* info) {
   info->n_spmm = ctx->n_spmm;
   info->n_prec = ctx->n_prec;
   info->n_qz = ctx->n_qz;
+  info->n_launch = ctx->n_launch;
+  info->h2d_bytes = ctx->h2d_bytes;
+  info->d2h_bytes = ctx->d2h_bytes;
   for (int j = 0; j < ctx->k && j < 64 && j < (int)ctx->resid.size(); ++j) info->resid[j] = ctx->resid[j];
 }
 
@@ -739,9 +821,10 @@ void free_all(gplhr_ctx* c) {
   F(c->Tcsr.rowptr); F(c->Tcsr.col); F(c->Tcsr.val);
   F(c->prec_data);
   F(c->Z); F(c->AZ); F(c->BZ); F(c->U); F(c->Pb); F(c->APb); F(c->BPb);
-  F(c->Rw); F(c->Tw1); F(c->Tw2);
+  F(c->Rw); F(c->Tw1); F(c->Tw2); F(c->Tw3);
   F(c->dC1); F(c->dC2); F(c->dMBa); F(c->dMAa); F(c->dYR); F(c->dYL); F(c->dPhiPsi); F(c->dGram);
   F(c->dProjC); F(c->dRinv); F(c->gram_part); F(c->norm_part); F(c->d_norms); F(c->d_status); F(c->d_diag);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->h_small) cudaFreeHost(c->h_small);
   if (c->h_phipsi) cudaFreeHost(c->h_phipsi);
   if (c->h_norms) cudaFreeHost(c->h_norms);
@@ -763,6 +846,7 @@ gplhr_status allocate(gplhr_ctx* ctx) {
   CK(cudaMalloc(&ctx->Rw, kb));
   CK(cudaMalloc(&ctx->Tw1, kb));
   CK(cudaMalloc(&ctx->Tw2, kb));
+  CK(cudaMalloc(&ctx->Tw3, kb));
   CK(cudaMemset(ctx->Z, 0, nb));
   CK(cudaMemset(ctx->AZ, 0, nb));
   CK(cudaMemset(ctx->U, 0, nb));
@@ -995,10 +1079,11 @@ gplhr_status gplhr_vectors(gplhr_ctx* ctx, double* alpha, double* beta, double* 
     double2* hz = ctx->h_small;
     pack(hz, Ze, 0, k, 0, k);
     TRY(upload(ctx, ctx->dC1, hz, k * k));
-    Blk Xb{ctx->Rw, k};
+    // scratch only: Rw carries the residual into the next gplhr_iterate
+    Blk Xb{ctx->Tw3, k};
     TRY(combine(ctx, {In{blkZ(ctx, 0), k, ctx->dC1, kOne}}, Xb, k, false));
     if (resid) {
-      Blk AX{ctx->Tw1, k}, BX{ctx->hasB ? ctx->Tw2 : ctx->Rw, k};
+      Blk AX{ctx->Tw1, k}, BX{ctx->hasB ? ctx->Tw2 : ctx->Tw3, k};
       TRY(launch_spmm_one(ctx, ctx->A, ctx->hasB ? &ctx->B : nullptr, Xb, k, AX, BX));
       double2* hb = ctx->h_small + k * k;
       double2* ha = ctx->h_small + 2 * k * k;
@@ -1018,7 +1103,7 @@ gplhr_status gplhr_vectors(gplhr_ctx* ctx, double* alpha, double* beta, double* 
         resid[j] = std::sqrt(nrm[j]) / (b * ctx->normA + a * ctx->normB);
       }
     }
-    if (X) CK(cudaMemcpyAsync(X, ctx->Rw, (size_t)n * k * sizeof(double2), d2x, ctx->stream));
+    if (X) CK(cudaMemcpyAsync(X, ctx->Tw3, (size_t)n * k * sizeof(double2), d2x, ctx->stream));
   }
   CK(cudaStreamSynchronize(ctx->stream));
   return GPLHR_OK;
@@ -1090,6 +1175,37 @@ gplhr_status gplhr_orth(gplhr_ctx* ctx, void* X, int32_t ldx, int32_t w, void* R
     CK(cudaMemcpy(Rinv, o.data(), w * w * sizeof(double2), cudaMemcpyHostToDevice));
   }
   CK(cudaStreamSynchronize(ctx->stream));
+  return GPLHR_OK;
+}
+
+gplhr_status gplhr_profile(gplhr_ctx* ctx, int32_t enable) {
+  if (!ctx) return GPLHR_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->prof_on = enable != 0;
+  ctx->ev_rec.clear();
+  for (int c = 0; c < 8; ++c) {
+    ctx->k_flops[c] = ctx->k_bytes[c] = 0.0;
+    ctx->k_launch[c] = 0;
+  }
+  ctx->n_launch = 0;
+  return GPLHR_OK;
+}
+
+gplhr_status gplhr_profile_read(gplhr_ctx* ctx, int32_t kclass, double* ms, int64_t* launches, double* flops,
+                                double* bytes) {
+  if (!ctx || kclass < 0 || kclass >= KC_N) return GPLHR_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream));
+  double t = 0.0;
+  for (const auto& r : ctx->ev_rec) {
+    if (r.first != kclass) continue;
+    float e = 0.f;
+    CK(cudaEventElapsedTime(&e, ctx->ev_pool[r.second], ctx->ev_pool[r.second + 1]));
+    t += e;
+  }
+  if (ms) *ms = t;
+  if (launches) *launches = ctx->k_launch[kclass];
+  if (flops) *flops = ctx->k_flops[kclass];
+  if (bytes) *bytes = ctx->k_bytes[kclass];
   return GPLHR_OK;
 }
 

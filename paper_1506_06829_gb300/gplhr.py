@@ -27,7 +27,9 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5:
 
 EXPORTED = ["gplhr_create", "gplhr_solve", "gplhr_start", "gplhr_iterate", "gplhr_vectors",
             "gplhr_destroy", "gplhr_last_error", "gplhr_spmm", "gplhr_precond_apply",
-            "gplhr_gram", "gplhr_orth", "gplhr_ordqz", "gplhr_mfactors"]
+            "gplhr_gram", "gplhr_orth", "gplhr_ordqz", "gplhr_mfactors", "gplhr_profile",
+            "gplhr_profile_read"]
+KCLASS = {"spmm": 0, "gram": 1, "combine": 2, "precond": 3, "chol": 4, "other": 5}
 
 
 class Csr(C.Structure):
@@ -48,7 +50,8 @@ class Opts(C.Structure):
 class Info(C.Structure):
     _fields_ = [("iters", C.c_int32), ("nconv", C.c_int32), ("m", C.c_int32),
                 ("n_orth_fallback", C.c_int32), ("n_spmm", C.c_int64), ("n_prec", C.c_int64),
-                ("n_qz", C.c_int64), ("resid", C.c_double * 64)]
+                ("n_qz", C.c_int64), ("n_launch", C.c_int64), ("h2d_bytes", C.c_int64),
+                ("d2h_bytes", C.c_int64), ("resid", C.c_double * 64)]
 
 
 class GplhrError(RuntimeError):
@@ -87,6 +90,8 @@ def lib():
     L.gplhr_orth.argtypes = [vp, vp, i32, i32, vp]
     L.gplhr_ordqz.argtypes = [i32, dp, dp, dbl, dbl, dp, dp, dp, dp]
     L.gplhr_mfactors.argtypes = [i32, dp, dp, dp, dp]
+    L.gplhr_profile.argtypes = [vp, i32]
+    L.gplhr_profile_read.argtypes = [vp, i32, dp, C.POINTER(C.c_int64), dp, dp]
     for name in EXPORTED:
         f = getattr(L, name)
         if f.restype is C.c_int:  # default
@@ -249,6 +254,19 @@ def gplhr_mfactors(RA: np.ndarray, RB: np.ndarray):
     _check(lib().gplhr_mfactors(k, _dptr(a.view(np.float64)), _dptr(b.view(np.float64)),
                                 _dptr(MA.view(np.float64)), _dptr(MB.view(np.float64))), None)
     return MA, MB
+
+
+def gplhr_profile(ctx, enable: bool):
+    _check(lib().gplhr_profile(ctx, 1 if enable else 0), ctx)
+
+
+def gplhr_profile_read(ctx, kclass: str):
+    """(ms, launches, flops, bytes) of one kernel class."""
+    ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+    nl = C.c_int64()
+    _check(lib().gplhr_profile_read(ctx, KCLASS[kclass], C.byref(ms), C.byref(nl), C.byref(fl),
+                                    C.byref(by)), ctx)
+    return ms.value, nl.value, fl.value, by.value
 
 
 class GPLHR:
