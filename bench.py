@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-k-pairs solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--grid", type=int, default=0,
+                    help="grid side of a smaller copy of the generalized pencil (profiling captures); "
+                         "its lambda_max is scaled from the 64^3 value by ((N+1)/65)^2")
     return ap.parse_args()
 
 
@@ -63,8 +66,10 @@ def dist_env():
     return rank, world, local
 
 
-def problem(name):
+def problem(name, grid: int = 0):
     from paper_1506_06829_gb300 import problems as P
+    if name == "config2" and grid and grid != 64:
+        return P.config2(grid, lambda_max=P.CONFIG2_LAMBDA_MAX * ((grid + 1) / 65.0) ** 2)
     return P.config2() if name == "config2" else P.config3()
 
 
@@ -161,7 +166,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    pr = problem(args.workload)
+    pr = problem(args.workload, args.grid)
     K, W = max(1, args.steps), max(0, args.warmup)
     spi = oracle_iterations(pr, K, W)
     line = {
@@ -195,7 +200,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     K, W = max(1, args.steps), max(3, args.warmup)
-    pr = problem(args.workload)
+    pr = problem(args.workload, args.grid)
 
     def barrier():
         if world > 1:

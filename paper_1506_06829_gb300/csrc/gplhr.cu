@@ -202,13 +202,28 @@ gplhr_status spmm_AB(gplhr_ctx* ctx, Blk X, int w, Blk AX, Blk BX) {
   return launch_spmm_one(ctx, ctx->A, ctx->hasB ? &ctx->B : nullptr, X, w, AX, BX);
 }
 
-// C (wx x (wy0 + wy1), row-major) = X^* [Y0 Y1]
+// C (wx x (wy0 + wy1), row-major) = X^* [Y0 Y1].  herm: X^* X (only the upper
+// triangle is computed; the lower one is filled by conjugation).
+template <int ACC>
+void launch_gram_acc(gplhr_ctx* ctx, dim3 grid, size_t smem, int rows, Blk X, int wx, Blk Y0, int wy0,
+                     Blk Y1, int wy1, int herm, int nout, int G, int RG, const int* skip) {
+  gplhr::gram_partial_kernel<ACC><<<grid, gplhr::GRAM_THREADS, smem, ctx->stream>>>(
+      ctx->n, rows, X.p, X.ld, wx, Y0.p, Y0.ld, wy0, Y1.p, Y1.ld, wy1, herm, nout, G, RG, ctx->gram_part, skip);
+}
+
 gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy1, double2* C,
-                  const int* skip = nullptr) {
+                  const int* skip = nullptr, bool herm = false, bool count = true) {
   const int wy = wy0 + wy1;
-  const int nout = wx * wy;
+  if (herm && (wy1 != 0 || wy0 != wx)) herm = false;
+  const int nout = herm ? wx * (wx + 1) / 2 : wx * wy;
   if (nout == 0) return GPLHR_OK;
-  const int ntile = (nout + gplhr::GRAM_OUT_PER_CTA - 1) / gplhr::GRAM_OUT_PER_CTA;
+  // accumulators per thread and output groups per CTA tile
+  int acc = 8;
+  while (acc > 1 && (nout + acc - 1) / acc < 128) acc >>= 1;
+  const int groups = (nout + acc - 1) / acc;
+  const int G = std::min(groups, gplhr::GRAM_THREADS);
+  const int RG = gplhr::GRAM_THREADS / G;
+  const int ntile = (groups + G - 1) / G;
   int nchunk = std::max(1, (4 * ctx->num_sms) / ntile);
   nchunk = std::min(nchunk, std::max(1, (ctx->n + gplhr::GRAM_ROWS - 1) / gplhr::GRAM_ROWS));
   while ((size_t)nchunk * nout > ctx->gram_part_elems && nchunk > 1) nchunk /= 2;
@@ -216,14 +231,20 @@ gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy
   rows = ((rows + gplhr::GRAM_ROWS - 1) / gplhr::GRAM_ROWS) * gplhr::GRAM_ROWS;
   nchunk = (ctx->n + rows - 1) / rows;
   dim3 grid(nchunk, ntile);
-  const size_t smem = (size_t)gplhr::GRAM_ROWS * (wx + wy) * sizeof(double2);
+  const size_t smem =
+      std::max((size_t)gplhr::GRAM_ROWS * (wx + wy), (size_t)RG * G * acc) * sizeof(double2);
   const bool self = X.p == Y0.p && wy1 == 0;
   const double by = 16.0 * ctx->n * (self ? wx : wx + wy);
-  const int ph = prof_begin(ctx, KC_GRAM, 8.0 * ctx->n * wx * wy, by, 2);
-  gplhr::gram_partial_kernel<<<grid, gplhr::GRAM_THREADS, smem, ctx->stream>>>(
-      ctx->n, rows, X.p, X.ld, wx, Y0.p, Y0.ld, wy0, Y1.p, Y1.ld, wy1, ctx->gram_part, skip);
+  const int ph = prof_begin(ctx, KC_GRAM, count ? 8.0 * ctx->n * nout : 0.0, count ? by : 0.0, 2);
+  switch (acc) {
+    case 8: launch_gram_acc<8>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip); break;
+    case 4: launch_gram_acc<4>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip); break;
+    case 2: launch_gram_acc<2>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip); break;
+    default: launch_gram_acc<1>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip); break;
+  }
   CK(cudaGetLastError());
-  gplhr::gram_reduce_kernel<<<(nout + 255) / 256, 256, 0, ctx->stream>>>(nchunk, nout, ctx->gram_part, C, skip);
+  gplhr::gram_reduce_kernel<<<(nout + 255) / 256, 256, 0, ctx->stream>>>(nchunk, nout, wx, wy, herm ? 1 : 0,
+                                                                         ctx->gram_part, C, skip);
   prof_end(ctx, ph);
   CK(cudaGetLastError());
   return GPLHR_OK;
@@ -240,7 +261,7 @@ struct In {
 // columns c_store..c only contribute |.|^2 sums (reduced into ctx->d_norms).
 gplhr_status combine(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, bool beta_one,
                      const int* skip = nullptr, Blk Y2 = Blk{nullptr, 0}, int c_split = -1,
-                     int c_store = -1) {
+                     int c_store = -1, bool count = true) {
   if (c <= 0 || ctx->n == 0) return GPLHR_OK;
   if (c_store < 0) c_store = c;
   if (c_split < 0) c_split = c_store;
@@ -266,7 +287,8 @@ gplhr_status combine(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, b
   a.normpart = c_store < c ? ctx->norm_part : nullptr;
   const size_t smem = (size_t)(wsum * c + rows_tile * wsum + rows_tile * c) * sizeof(double2);
   double by = 16.0 * ctx->n * (wsum + c_store * (beta_one ? 2.0 : 1.0));
-  const int ph = prof_begin(ctx, KC_COMBINE, 8.0 * ctx->n * wsum * c, by, c_store < c ? 2 : 1);
+  const int ph = prof_begin(ctx, KC_COMBINE, count ? 8.0 * ctx->n * wsum * c : 0.0, count ? by : 0.0,
+                           c_store < c ? 2 : 1);
   gplhr::combine_kernel<<<grid, gplhr::COMB_THREADS, smem, ctx->stream>>>(ctx->n, rows_per_cta, a);
   CK(cudaGetLastError());
   if (c_store < c) {
@@ -362,13 +384,18 @@ gplhr_status orth_against(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w, const std
   if (w <= 0) return GPLHR_OK;
   const int smax2 = ctx->s_max * ctx->s_max;
   for (int pass = 0; pass < 3; ++pass) {
+    // the third pass runs only when the first Cholesky needed the shift (decided on the
+    // device); its work is not counted in the algorithmic totals
     const int* skip = pass == 2 ? ctx->d_status + 0 : nullptr;
+    const bool cnt = pass < 2;
+    const Blk none{nullptr, 0};
     if (wl > 0) {
-      TRY(gram(ctx, L, wl, X, w, Blk{nullptr, 0}, 0, ctx->dProjC, skip));
-      TRY(combine(ctx, {In{L, wl, ctx->dProjC, kMinusOne}}, X, w, true, skip));
-      for (const Extra& e : ex) TRY(combine(ctx, {In{e.EL, wl, ctx->dProjC, kMinusOne}}, e.E, w, true, skip));
+      TRY(gram(ctx, L, wl, X, w, none, 0, ctx->dProjC, skip, false, cnt));
+      TRY(combine(ctx, {In{L, wl, ctx->dProjC, kMinusOne}}, X, w, true, skip, none, -1, -1, cnt));
+      for (const Extra& e : ex)
+        TRY(combine(ctx, {In{e.EL, wl, ctx->dProjC, kMinusOne}}, e.E, w, true, skip, none, -1, -1, cnt));
     }
-    TRY(gram(ctx, X, w, X, w, Blk{nullptr, 0}, 0, ctx->dGram, skip));
+    TRY(gram(ctx, X, w, X, w, none, 0, ctx->dGram, skip, true, cnt));
     double2* Rinv = ctx->dRinv + (size_t)pass * smax2;
     const size_t smem = (size_t)2 * w * w * sizeof(double2);
     const int ph = prof_begin(ctx, KC_CHOL, 8.0 * w * w * w / 2.0, 48.0 * w * w);
@@ -376,8 +403,8 @@ gplhr_status orth_against(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w, const std
                                                           ctx->d_status + pass, skip, ctx->d_diag);
     prof_end(ctx, ph);
     CK(cudaGetLastError());
-    TRY(combine(ctx, {In{X, w, Rinv, kOne}}, X, w, false, skip));
-    for (const Extra& e : ex) TRY(combine(ctx, {In{e.E, w, Rinv, kOne}}, e.E, w, false, skip));
+    TRY(combine(ctx, {In{X, w, Rinv, kOne}}, X, w, false, skip, none, -1, -1, cnt));
+    for (const Extra& e : ex) TRY(combine(ctx, {In{e.E, w, Rinv, kOne}}, e.E, w, false, skip, none, -1, -1, cnt));
   }
   return GPLHR_OK;
 }
@@ -487,9 +514,10 @@ gplhr_status start(gplhr_ctx* ctx) {
   TRY(orth_against(ctx, Blk{nullptr, 0}, 0, blkZ(ctx, 0), k));                // V = orth(V0)
   TRY(spmm_AB(ctx, blkZ(ctx, 0), k, blkAZ(ctx, 0), blkBZ(ctx, 0)));        // AV, BV
   const double2 ms = d2(-ctx->sigma);
-  prof_begin(ctx, KC_OTHER, 8.0 * ctx->n * k, 48.0 * ctx->n * k);
+  const int ph = prof_begin(ctx, KC_OTHER, 8.0 * ctx->n * k, 48.0 * ctx->n * k);
   gplhr::axpby_kernel<<<grid_for((size_t)ctx->n * k, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
       ctx->n, k, kOne, ctx->AZ, ctx->s_max, ms, blkBZ(ctx, 0).p, ctx->s_max, ctx->U, ctx->s_max);
+  prof_end(ctx, ph);
   CK(cudaGetLastError());
   TRY(orth_against(ctx, Blk{nullptr, 0}, 0, blkU(ctx, 0), k));                // Q = orth((A - sigma B) V)
   TRY(gram(ctx, blkU(ctx, 0), k, blkAZ(ctx, 0), k, blkBZ(ctx, 0), k, ctx->dPhiPsi));
@@ -570,7 +598,7 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
   const int pslot = k + (m + 1) * kk;
   if (ctx->hasP && kk > 0) {
     const size_t nw = (size_t)ctx->n;
-    prof_begin(ctx, KC_OTHER, 0.0, 32.0 * ctx->n * kk * (ctx->hasB ? 3 : 2), ctx->hasB ? 3 : 2);
+    const int ph = prof_begin(ctx, KC_OTHER, 0.0, 32.0 * ctx->n * kk * (ctx->hasB ? 3 : 2), ctx->hasB ? 3 : 2);
     gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
         ctx->n, kk, ctx->Pb, k, ctx->Z + pslot, sm);
     gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
@@ -578,6 +606,7 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
     if (ctx->hasB)
       gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
           ctx->n, kk, ctx->BPb, k, ctx->BZ + pslot, sm);
+    prof_end(ctx, ph);
     CK(cudaGetLastError());
     std::vector<Extra> ex{Extra{blkAZ(ctx, pslot), blkAZ(ctx, 0)}};
     if (ctx->hasB) ex.push_back(Extra{blkBZ(ctx, pslot), blkBZ(ctx, 0)});
@@ -862,7 +891,7 @@ gplhr_status allocate(gplhr_ctx* ctx) {
   CK(cudaMalloc(&ctx->dGram, 2 * s2));
   CK(cudaMalloc(&ctx->dProjC, 2 * s2));
   CK(cudaMalloc(&ctx->dRinv, 3 * s2));
-  ctx->gram_part_elems = (size_t)(4 * ctx->num_sms + 8) * gplhr::GRAM_OUT_PER_CTA;
+  ctx->gram_part_elems = (size_t)(4 * ctx->num_sms + 8) * gplhr::GRAM_THREADS * 8;
   ctx->gram_part_elems = std::max(ctx->gram_part_elems, 2 * sm * sm);
   CK(cudaMalloc(&ctx->gram_part, ctx->gram_part_elems * sizeof(double2)));
   CK(cudaMalloc(&ctx->norm_part, (size_t)(4 * ctx->num_sms + 8) * gplhr::COMB_MAX_NORMS * sizeof(double)));
@@ -881,7 +910,10 @@ gplhr_status allocate(gplhr_ctx* ctx) {
 gplhr_status set_smem_limits(gplhr_ctx* ctx) {
   const int big = 200 * 1024;
   CK(cudaFuncSetAttribute(gplhr::combine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::block_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::invert_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));

@@ -101,73 +101,118 @@ __global__ void spmm_kernel(int n, CsrDev<VTA> A, CsrDev<VTB> B, int hasB,
 }
 
 // ------------------------------------------------------------------- Gram -----
-// Split-n Gram product: partial[b][i][j] = sum over rows of chunk b of conj(X[r][i]) Y[r][j],
-// where Y is the column concatenation of up to two blocks (Y0: wy0 cols, Y1: wy1 cols).
-// The grid is (nchunk, ntile): CTA (b, t) owns chunk b of rows and tile t of up to
-// GRAM_OUT_PER_CTA outputs (row-major over the wx x wy output).  Rows are staged
-// through shared memory GRAM_ROWS at a time.
+// Split-n Gram product over the rows:  partial[b][o] = sum over rows of chunk b of
+// conj(X[r][i_o]) Y[r][j_o], Y the column concatenation of Y0 (wy0 cols) and Y1.
+// Outputs o enumerate the wx x wy result row-major, or only its upper triangle
+// (i <= j) when herm = 1 (X^* X, whose lower triangle is the conjugate transpose).
+//
+// FP64 on GB300 issues at ~2 DFMA/clk/SM, so every issued DFMA must be useful:
+// thread g of a CTA owns ACC consecutive outputs (all valid except possibly in the
+// very last thread, which computes padding it then discards), and when the CTA has
+// fewer than 256 output groups the threads split the staged rows into RG row
+// groups whose partial sums are added in shared memory at the end.  The grid is
+// (nchunk, ntile): chunk b of rows, tile t of G*ACC outputs.
 constexpr int GRAM_THREADS = 256;
-constexpr int GRAM_ACC = 8;  // outputs per thread
-constexpr int GRAM_OUT_PER_CTA = GRAM_THREADS * GRAM_ACC;
 constexpr int GRAM_ROWS = 16;
 
-__global__ void gram_partial_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, int ldx,
-                                    int wx, const double2* __restrict__ Y0, int ldy0, int wy0,
-                                    const double2* __restrict__ Y1, int ldy1, int wy1,
-                                    double2* __restrict__ partial, const int* skip) {
+__device__ __forceinline__ void gram_index(int o, int wx, int wy, int herm, int& i, int& j) {
+  if (!herm) {
+    i = o / wy;
+    j = o - i * wy;
+    return;
+  }
+  // upper triangle, row-major: row i starts at i*wx - i*(i-1)/2
+  int r = 0, off = 0;
+  while (r + 1 < wx && off + (wx - r) <= o) {
+    off += wx - r;
+    ++r;
+  }
+  i = r;
+  j = r + (o - off);
+}
+
+template <int ACC>
+__global__ void __launch_bounds__(GRAM_THREADS)
+gram_partial_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, int ldx, int wx,
+                    const double2* __restrict__ Y0, int ldy0, int wy0, const double2* __restrict__ Y1,
+                    int ldy1, int wy1, int herm, int nout, int G, int RG, double2* __restrict__ partial,
+                    const int* skip) {
   if (skip && *skip == 0) return;
   extern __shared__ double2 sm[];
   const int wy = wy0 + wy1;
   double2* xs = sm;                         // GRAM_ROWS x wx
   double2* ys = sm + GRAM_ROWS * wx;        // GRAM_ROWS x wy
-  const int nout = wx * wy;
-  const int tile0 = blockIdx.y * GRAM_OUT_PER_CTA;
+  const int tid = threadIdx.x;
+  const int g = tid % G, rg = tid / G;
+  const int tile0 = blockIdx.y * G * ACC;
+  const int o0 = tile0 + g * ACC;
+  const bool active = rg < RG && o0 < nout;
   const int r0 = blockIdx.x * rows_per_chunk;
   const int r1 = min(n, r0 + rows_per_chunk);
-  double2 acc[GRAM_ACC];
-  int oi[GRAM_ACC], oj[GRAM_ACC];
+  double2 acc[ACC];
+  int oi[ACC], oj[ACC];
 #pragma unroll
-  for (int t = 0; t < GRAM_ACC; ++t) {
+  for (int t = 0; t < ACC; ++t) {
     acc[t] = make_double2(0.0, 0.0);
-    const int o = tile0 + threadIdx.x + t * GRAM_THREADS;
-    oi[t] = o < nout ? o / wy : -1;
-    oj[t] = o < nout ? o - (o / wy) * wy : 0;
+    const int o = min(o0 + t, nout - 1);
+    gram_index(o, wx, wy, herm, oi[t], oj[t]);
   }
   for (int rb = r0; rb < r1; rb += GRAM_ROWS) {
     const int nr = min(GRAM_ROWS, r1 - rb);
     __syncthreads();
-    for (int e = threadIdx.x; e < nr * wx; e += blockDim.x) {
+    for (int e = tid; e < nr * wx; e += blockDim.x) {
       const int rr = e / wx, cc = e - rr * wx;
       xs[rr * wx + cc] = X[(size_t)(rb + rr) * ldx + cc];
     }
-    for (int e = threadIdx.x; e < nr * wy; e += blockDim.x) {
+    for (int e = tid; e < nr * wy; e += blockDim.x) {
       const int rr = e / wy, cc = e - rr * wy;
       ys[rr * wy + cc] = cc < wy0 ? Y0[(size_t)(rb + rr) * ldy0 + cc]
                                   : Y1[(size_t)(rb + rr) * ldy1 + (cc - wy0)];
     }
     __syncthreads();
-    for (int rr = 0; rr < nr; ++rr) {
+    if (active) {
+      for (int rr = rg; rr < nr; rr += RG) {
+        const double2* xr = xs + rr * wx;
+        const double2* yr = ys + rr * wy;
 #pragma unroll
-      for (int t = 0; t < GRAM_ACC; ++t) {
-        if (oi[t] >= 0) acc[t] = cfmaconj(xs[rr * wx + oi[t]], ys[rr * wy + oj[t]], acc[t]);
+        for (int t = 0; t < ACC; ++t) acc[t] = cfmaconj(xr[oi[t]], yr[oj[t]], acc[t]);
       }
     }
   }
-  double2* out = partial + (size_t)blockIdx.x * nout;
+  // add the RG row-group partials: red[rg][g*ACC + t]
+  __syncthreads();
+  double2* red = sm;
+  const int per = G * ACC;
+  if (rg < RG) {
 #pragma unroll
-  for (int t = 0; t < GRAM_ACC; ++t)
-    if (oi[t] >= 0) out[oi[t] * wy + oj[t]] = acc[t];
+    for (int t = 0; t < ACC; ++t) red[rg * per + g * ACC + t] = acc[t];
+  }
+  __syncthreads();
+  double2* out = partial + (size_t)blockIdx.x * nout;
+  for (int e = tid; e < per; e += blockDim.x) {
+    const int o = tile0 + e;
+    if (o >= nout) break;
+    double2 s = red[e];
+    for (int q = 1; q < RG; ++q) s = cadd(s, red[q * per + e]);
+    out[o] = s;
+  }
 }
 
-// C[o] = sum_b partial[b][o] in a fixed order (deterministic).
-__global__ void gram_reduce_kernel(int nchunk, int nout, const double2* __restrict__ partial,
-                                   double2* __restrict__ C, const int* skip) {
+// C = sum_b partial[b] in a fixed order (deterministic); the output enumeration is
+// mapped back to (i, j) of the wx x wy result (row-major, ld = wy); with herm = 1 the
+// lower triangle is filled with the conjugate transpose.
+__global__ void gram_reduce_kernel(int nchunk, int nout, int wx, int wy, int herm,
+                                   const double2* __restrict__ partial, double2* __restrict__ C,
+                                   const int* skip) {
   if (skip && *skip == 0) return;
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= nout) return;
   double2 s = make_double2(0.0, 0.0);
   for (int b = 0; b < nchunk; ++b) s = cadd(s, partial[(size_t)b * nout + o]);
-  C[o] = s;
+  int i, j;
+  gram_index(o, wx, wy, herm, i, j);
+  C[i * wy + j] = s;
+  if (herm && i != j) C[j * wy + i] = make_double2(s.x, -s.y);
 }
 
 // ---------------------------------------------------------------- combine -----
