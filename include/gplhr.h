@@ -206,6 +206,26 @@ gplhr_status gplhr_profile(gplhr_ctx* ctx, int32_t enable);
 gplhr_status gplhr_profile_read(gplhr_ctx* ctx, int32_t kclass, double* ms, int64_t* launches,
                                 double* flops, double* bytes);
 
+/* Gram product C = X^* Y that allocates nothing, for callers that cannot call
+ * cudaMalloc: for instance code whose device memory is all owned by another
+ * allocator or memory pool, or a loop that must not take the implicit device
+ * synchronisation and latency of an allocation.  The paper has no counterpart: this
+ * is a library convenience around the Gram kernel of gplhr_gram.
+ * X: n x wx, Y: n x wy (row-major complex, device pointers, leading dimensions in
+ * elements), C: wx x wy row-major (ld = wy), device pointer; all are the caller's.
+ * Needs no context.  Limits: wx * wy <= 16384 and wx + wy <= 768, else EINVAL with a
+ * message in gplhr_last_error(NULL).  The kernel's scratch (partial sums over chunks
+ * of rows) is a fixed 4 MiB array in the library's device memory, held by every GPU
+ * that loads the library until the process exits; every call on a device shares it
+ * and leaves it holding its own partial sums, so calls that overlap on the GPU (two
+ * streams, or two threads) race and must be ordered by the caller.  The call is
+ * asynchronous on `stream` (NULL = the default stream): C is complete when the stream
+ * reaches this point.  The first call on a device (with that device current) also
+ * looks up the scratch array's device address and sets the kernels' shared-memory
+ * limit; make that first call before capturing `stream`.  Errors: EINVAL, ECUDA. */
+gplhr_status gplhr_gram_noalloc(int64_t n, const void* X, int32_t ldx, int32_t wx,
+                                const void* Y, int32_t ldy, int32_t wy, void* C, void* stream);
+
 /* Ordered complex QZ of a small pencil on the host (footnote to Alg. 2 step 2):
  * Phi = YL RA YR^*, Psi = YL RB YR^* with |RA(j,j)/RB(j,j) - sigma| non-decreasing
  * and RB(j,j) real >= 0.  All matrices s x s row-major complex, host memory.

@@ -10,8 +10,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <climits>
 #include <complex>
 #include <cstdio>
+#include <mutex>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -945,6 +947,61 @@ bool valid_block(const void* p, int ld, int w) { return p != nullptr && w >= 0 &
 
 }  // namespace
 
+// ------------------------------------------------------- allocation-free Gram --
+// Scratch of gplhr_gram_noalloc: the split-n partial sums of the Gram product live
+// in this file-scope device array (4 MiB) instead of memory from cudaMalloc.  Every
+// GPU that loads the library holds it until the process exits, and all calls on a
+// device share it.
+constexpr size_t kNoallocScratchElems = (size_t)1 << 18;  // double2 elements
+constexpr int kNoallocMaxOut = 16384;                     // wx * wy limit
+constexpr int kNoallocMaxCols = 768;                      // wx + wy limit (staged rows)
+static __device__ __align__(256) double2 g_noalloc_scratch[kNoallocScratchElems];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double2* g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
+int g_noalloc_sms[kNoallocMaxDevices] = {0};
+
+// Once per device, with that device current: the device address of the scratch array
+// (host code only has a host-side stand-in for the symbol, which must never be passed
+// to a kernel) and the shared-memory opt-in of the Gram kernels.
+gplhr_status noalloc_setup(double2** ptr, int* sms) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
+    g_create_error = "gplhr_gram_noalloc: no usable current CUDA device";
+    return GPLHR_ECUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      g_create_error = std::string("gplhr_gram_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+      return GPLHR_ECUDA;
+    }
+    int nsm = 0;
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int big = 200 * 1024;
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gplhr::gram_partial_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gplhr::gram_partial_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gplhr::gram_partial_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gplhr::gram_partial_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e != cudaSuccess) {
+      g_create_error = std::string("gplhr_gram_noalloc: device set-up: ") + cudaGetErrorString(e);
+      return GPLHR_ECUDA;
+    }
+    g_noalloc_sms[dev] = nsm;
+    g_noalloc_ptr[dev] = (double2*)p;
+  }
+  *ptr = g_noalloc_ptr[dev];
+  *sms = g_noalloc_sms[dev];
+  return GPLHR_OK;
+}
+
 // ====================================================================== C ABI ==
 
 extern "C" {
@@ -1238,6 +1295,72 @@ gplhr_status gplhr_profile_read(gplhr_ctx* ctx, int32_t kclass, double* ms, int6
   if (launches) *launches = ctx->k_launch[kclass];
   if (flops) *flops = ctx->k_flops[kclass];
   if (bytes) *bytes = ctx->k_bytes[kclass];
+  return GPLHR_OK;
+}
+
+gplhr_status gplhr_gram_noalloc(int64_t n, const void* X, int32_t ldx, int32_t wx, const void* Y, int32_t ldy,
+                                int32_t wy, void* C, void* stream) {
+  if (n < 1 || n > INT_MAX || wx < 1 || wy < 1 || ldx < wx || ldy < wy || !X || !Y || !C) {
+    g_create_error = "gplhr_gram_noalloc: need 1 <= n < 2^31, w >= 1, ld >= w, non-null pointers";
+    return GPLHR_EINVAL;
+  }
+  if ((int64_t)wx * wy > kNoallocMaxOut || wx + wy > kNoallocMaxCols) {
+    g_create_error = "gplhr_gram_noalloc: wx * wy must be <= 16384 and wx + wy <= 768 (fixed scratch size)";
+    return GPLHR_EINVAL;
+  }
+  double2* scratch = nullptr;
+  int nsm = 0;
+  gplhr_status st = noalloc_setup(&scratch, &nsm);
+  if (st != GPLHR_OK) return st;
+  const int nn = (int)n;
+  const int nout = wx * wy;
+  int acc = 8;
+  while (acc > 1 && (nout + acc - 1) / acc < 128) acc >>= 1;
+  const int groups = (nout + acc - 1) / acc;
+  const int G = std::min(groups, gplhr::GRAM_THREADS);
+  const int RG = gplhr::GRAM_THREADS / G;
+  const int ntile = (groups + G - 1) / G;
+  int nchunk = std::max(1, (4 * std::max(nsm, 1)) / ntile);
+  nchunk = std::min(nchunk, std::max(1, (nn + gplhr::GRAM_ROWS - 1) / gplhr::GRAM_ROWS));
+  nchunk = std::min<int>(nchunk, (int)(kNoallocScratchElems / nout));
+  int rows = (nn + nchunk - 1) / nchunk;
+  rows = ((rows + gplhr::GRAM_ROWS - 1) / gplhr::GRAM_ROWS) * gplhr::GRAM_ROWS;
+  nchunk = (nn + rows - 1) / rows;
+  const dim3 grid(nchunk, ntile);
+  const size_t smem =
+      std::max((size_t)gplhr::GRAM_ROWS * (wx + wy), (size_t)RG * G * acc) * sizeof(double2);
+  cudaStream_t strm = (cudaStream_t)stream;
+  const double2* Xp = (const double2*)X;
+  const double2* Yp = (const double2*)Y;
+  const double2* none = nullptr;
+  switch (acc) {
+    case 8:
+      gplhr::gram_partial_kernel<8><<<grid, gplhr::GRAM_THREADS, smem, strm>>>(
+          nn, rows, Xp, ldx, wx, Yp, ldy, wy, none, 0, 0, 0, nout, G, RG, scratch, nullptr);
+      break;
+    case 4:
+      gplhr::gram_partial_kernel<4><<<grid, gplhr::GRAM_THREADS, smem, strm>>>(
+          nn, rows, Xp, ldx, wx, Yp, ldy, wy, none, 0, 0, 0, nout, G, RG, scratch, nullptr);
+      break;
+    case 2:
+      gplhr::gram_partial_kernel<2><<<grid, gplhr::GRAM_THREADS, smem, strm>>>(
+          nn, rows, Xp, ldx, wx, Yp, ldy, wy, none, 0, 0, 0, nout, G, RG, scratch, nullptr);
+      break;
+    default:
+      gplhr::gram_partial_kernel<1><<<grid, gplhr::GRAM_THREADS, smem, strm>>>(
+          nn, rows, Xp, ldx, wx, Yp, ldy, wy, none, 0, 0, 0, nout, G, RG, scratch, nullptr);
+      break;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    gplhr::gram_reduce_kernel<<<(nout + 255) / 256, 256, 0, strm>>>(nchunk, nout, wx, wy, 0, scratch,
+                                                                   (double2*)C, nullptr);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    g_create_error = std::string("gplhr_gram_noalloc: launch: ") + cudaGetErrorString(e);
+    return GPLHR_ECUDA;
+  }
   return GPLHR_OK;
 }
 

@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5:
 EXPORTED = ["gplhr_create", "gplhr_solve", "gplhr_start", "gplhr_iterate", "gplhr_vectors",
             "gplhr_destroy", "gplhr_last_error", "gplhr_spmm", "gplhr_precond_apply",
             "gplhr_gram", "gplhr_orth", "gplhr_ordqz", "gplhr_mfactors", "gplhr_profile",
-            "gplhr_profile_read"]
+            "gplhr_profile_read", "gplhr_gram_noalloc"]
 KCLASS = {"spmm": 0, "gram": 1, "combine": 2, "precond": 3, "chol": 4, "other": 5}
 
 
@@ -91,6 +91,7 @@ def lib():
     L.gplhr_ordqz.argtypes = [i32, dp, dp, dbl, dbl, dp, dp, dp, dp]
     L.gplhr_mfactors.argtypes = [i32, dp, dp, dp, dp]
     L.gplhr_profile.argtypes = [vp, i32]
+    L.gplhr_gram_noalloc.argtypes = [i64, vp, i32, i32, vp, i32, i32, vp, vp]
     L.gplhr_profile_read.argtypes = [vp, i32, dp, C.POINTER(C.c_int64), dp, dp]
     for name in EXPORTED:
         f = getattr(L, name)
@@ -226,6 +227,13 @@ def gplhr_precond_apply(ctx, X, Y):
 def gplhr_gram(ctx, X, Y, Cout):
     _check(lib().gplhr_gram(ctx, X.data_ptr(), X.stride(0), X.shape[1], Y.data_ptr(),
                             Y.stride(0), Y.shape[1], Cout.data_ptr()), ctx)
+
+
+def gplhr_gram_noalloc(X, Y, Cout, stream: int = 0):
+    """C = X^* Y without any allocation (device tensors; asynchronous on `stream`)."""
+    _check(lib().gplhr_gram_noalloc(X.shape[0], X.data_ptr(), X.stride(0), X.shape[1],
+                                    Y.data_ptr(), Y.stride(0), Y.shape[1], Cout.data_ptr(),
+                                    stream or None), None)
 
 
 def gplhr_orth(ctx, X, Rinv=None):
