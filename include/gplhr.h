@@ -91,7 +91,10 @@ typedef struct {
   int32_t maxit;       /* [500]  iteration cap (the paper's DNC limit, Sec. 5.1)        */
   int32_t precision;   /* [GPLHR_FP64]                                                   */
   int32_t no_lock;     /* [0]    1 disables soft locking (Sec. 3.6)                      */
-  int32_t reserved;
+  int32_t products;    /* [0]    how AV, BV, AP, BP are formed: 1 = linear combinations of
+                          AZ, BZ (the paper's (m+1) sparse products per iteration), 2 =
+                          fresh sparse products of V and P ((m+3) per iteration), 0 = the
+                          one with fewer flops for this pencil                          */
   void* stream;        /* [NULL] cudaStream_t for all device work of the context        */
 } gplhr_opts;
 

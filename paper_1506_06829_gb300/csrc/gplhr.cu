@@ -58,6 +58,7 @@ struct gplhr_ctx {
   double tol = 1e-8;
   int maxit = 500;
   bool lock = true;
+  bool recompute = false;  // AV, BV, AP, BP by sparse products instead of combinations
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int num_sms = 152;
@@ -245,8 +246,8 @@ gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy
     default: launch_gram_acc<1>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip); break;
   }
   CK(cudaGetLastError());
-  gplhr::gram_reduce_kernel<<<(nout + 255) / 256, 256, 0, ctx->stream>>>(nchunk, nout, wx, wy, herm ? 1 : 0,
-                                                                         ctx->gram_part, C, skip);
+  gplhr::gram_reduce_kernel<<<(nout + gplhr::GRED_WARPS - 1) / gplhr::GRED_WARPS, 32 * gplhr::GRED_WARPS, 0,
+                               ctx->stream>>>(nchunk, nout, wx, wy, herm ? 1 : 0, ctx->gram_part, C, skip);
   prof_end(ctx, ph);
   CK(cudaGetLastError());
   return GPLHR_OK;
@@ -537,8 +538,12 @@ gplhr_status start(gplhr_ctx* ctx) {
   TRY(upload(ctx, ctx->dYL, hl, k * k));
   // V <- V YR, AV <- AV YR, BV <- BV YR, Q <- Q YL (in place)
   TRY(combine(ctx, {In{blkZ(ctx, 0), k, ctx->dYR, kOne}}, blkZ(ctx, 0), k, false));
-  TRY(combine(ctx, {In{blkAZ(ctx, 0), k, ctx->dYR, kOne}}, blkAZ(ctx, 0), k, false));
-  if (ctx->hasB) TRY(combine(ctx, {In{blkBZ(ctx, 0), k, ctx->dYR, kOne}}, blkBZ(ctx, 0), k, false));
+  if (ctx->recompute) {
+    TRY(spmm_AB(ctx, blkZ(ctx, 0), k, blkAZ(ctx, 0), blkBZ(ctx, 0)));
+  } else {
+    TRY(combine(ctx, {In{blkAZ(ctx, 0), k, ctx->dYR, kOne}}, blkAZ(ctx, 0), k, false));
+    if (ctx->hasB) TRY(combine(ctx, {In{blkBZ(ctx, 0), k, ctx->dYR, kOne}}, blkBZ(ctx, 0), k, false));
+  }
   TRY(combine(ctx, {In{blkU(ctx, 0), k, ctx->dYL, kOne}}, blkU(ctx, 0), k, false));
   set_factors(ctx, RAb, RBb);
   ctx->started = true;
@@ -600,19 +605,27 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
   const int pslot = k + (m + 1) * kk;
   if (ctx->hasP && kk > 0) {
     const size_t nw = (size_t)ctx->n;
-    const int ph = prof_begin(ctx, KC_OTHER, 0.0, 32.0 * ctx->n * kk * (ctx->hasB ? 3 : 2), ctx->hasB ? 3 : 2);
+    const int ncopy = ctx->recompute ? 1 : (ctx->hasB ? 3 : 2);
+    const int ph = prof_begin(ctx, KC_OTHER, 0.0, 32.0 * ctx->n * kk * ncopy, ncopy);
     gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
         ctx->n, kk, ctx->Pb, k, ctx->Z + pslot, sm);
-    gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-        ctx->n, kk, ctx->APb, k, ctx->AZ + pslot, sm);
-    if (ctx->hasB)
+    if (!ctx->recompute) {
       gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-          ctx->n, kk, ctx->BPb, k, ctx->BZ + pslot, sm);
+          ctx->n, kk, ctx->APb, k, ctx->AZ + pslot, sm);
+      if (ctx->hasB)
+        gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+            ctx->n, kk, ctx->BPb, k, ctx->BZ + pslot, sm);
+    }
     prof_end(ctx, ph);
     CK(cudaGetLastError());
-    std::vector<Extra> ex{Extra{blkAZ(ctx, pslot), blkAZ(ctx, 0)}};
-    if (ctx->hasB) ex.push_back(Extra{blkBZ(ctx, pslot), blkBZ(ctx, 0)});
-    TRY(orth_against(ctx, V, pslot, blkZ(ctx, pslot), kk, ex));
+    if (ctx->recompute) {
+      TRY(orth_against(ctx, V, pslot, blkZ(ctx, pslot), kk));
+      TRY(spmm_AB(ctx, blkZ(ctx, pslot), kk, blkAZ(ctx, pslot), blkBZ(ctx, pslot)));
+    } else {
+      std::vector<Extra> ex{Extra{blkAZ(ctx, pslot), blkAZ(ctx, 0)}};
+      if (ctx->hasB) ex.push_back(Extra{blkBZ(ctx, pslot), blkBZ(ctx, 0)});
+      TRY(orth_against(ctx, V, pslot, blkZ(ctx, pslot), kk, ex));
+    }
     sP = kk;
   }
   const int s = pslot + sP;
@@ -641,11 +654,16 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
   TRY(upload(ctx, ctx->dYR, hy, (size_t)s * cv));
   TRY(upload(ctx, ctx->dYL, hl, (size_t)s * k));
   TRY(combine(ctx, {In{blkZ(ctx, 0), s, ctx->dYR, kOne}}, blkZ(ctx, 0), cv, false, nullptr, Blk{ctx->Pb, k}, k));
-  TRY(combine(ctx, {In{blkAZ(ctx, 0), s, ctx->dYR, kOne}}, blkAZ(ctx, 0), cv, false, nullptr, Blk{ctx->APb, k},
-              k));
-  if (ctx->hasB)
-    TRY(combine(ctx, {In{blkBZ(ctx, 0), s, ctx->dYR, kOne}}, blkBZ(ctx, 0), cv, false, nullptr,
-                Blk{ctx->BPb, k}, k));
+  if (ctx->recompute) {
+    // AV, BV by fresh sparse products (AP, BP are formed after P's orth next iteration)
+    TRY(spmm_AB(ctx, blkZ(ctx, 0), k, blkAZ(ctx, 0), blkBZ(ctx, 0)));
+  } else {
+    TRY(combine(ctx, {In{blkAZ(ctx, 0), s, ctx->dYR, kOne}}, blkAZ(ctx, 0), cv, false, nullptr,
+                Blk{ctx->APb, k}, k));
+    if (ctx->hasB)
+      TRY(combine(ctx, {In{blkBZ(ctx, 0), s, ctx->dYR, kOne}}, blkBZ(ctx, 0), cv, false, nullptr,
+                  Blk{ctx->BPb, k}, k));
+  }
   TRY(combine(ctx, {In{blkU(ctx, 0), s, ctx->dYL, kOne}}, blkU(ctx, 0), k, false));
   ctx->hasP = true;
   // steps 29-30
@@ -1040,6 +1058,12 @@ gplhr_status gplhr_create(const gplhr_csr* A, const gplhr_csr* B, double sigma_r
     ctx->lock = opts->no_lock == 0;
     ctx->stream = (cudaStream_t)opts->stream;
   }
+  const int products = opts ? opts->products : 0;
+  if (products < 0 || products > 2) {
+    g_create_error = "opts.products must be 0, 1 or 2";
+    delete ctx;
+    return GPLHR_EINVAL;
+  }
   auto fail = [&](gplhr_status st) {
     g_create_error = ctx->err;
     free_all(ctx);
@@ -1065,6 +1089,14 @@ gplhr_status gplhr_create(const gplhr_csr* A, const gplhr_csr* B, double sigma_r
   if (ctx->hasB && (st = upload_csr(ctx, B, ctx->B, &ctx->normB)) != GPLHR_OK) return fail(st);
   if ((st = allocate(ctx)) != GPLHR_OK) return fail(st);
   if ((st = setup_preconditioner(ctx, T)) != GPLHR_OK) return fail(st);
+  {
+    // flops per block column: sparse products of one column vs an s-wide combination
+    const double spmm = ((ctx->A.dtype == GPLHR_C128 ? 8.0 : 4.0) * ctx->A.nnz +
+                         (ctx->hasB ? (ctx->B.dtype == GPLHR_C128 ? 8.0 : 4.0) * ctx->B.nnz : 0.0)) /
+                        ctx->n;
+    const double comb = 8.0 * ctx->s_max * (ctx->hasB ? 2.0 : 1.0);
+    ctx->recompute = products == 2 || (products == 0 && spmm < comb);
+  }
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
     ctx->err = "setup failed on the device";
     return fail(GPLHR_ECUDA);
@@ -1353,8 +1385,8 @@ gplhr_status gplhr_gram_noalloc(int64_t n, const void* X, int32_t ldx, int32_t w
   }
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
-    gplhr::gram_reduce_kernel<<<(nout + 255) / 256, 256, 0, strm>>>(nchunk, nout, wx, wy, 0, scratch,
-                                                                   (double2*)C, nullptr);
+    gplhr::gram_reduce_kernel<<<(nout + gplhr::GRED_WARPS - 1) / gplhr::GRED_WARPS, 32 * gplhr::GRED_WARPS, 0,
+                                 strm>>>(nchunk, nout, wx, wy, 0, scratch, (double2*)C, nullptr);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {

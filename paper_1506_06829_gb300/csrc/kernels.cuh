@@ -198,21 +198,27 @@ gram_partial_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, in
   }
 }
 
-// C = sum_b partial[b] in a fixed order (deterministic); the output enumeration is
+// C = sum_b partial[b] (deterministic): one warp per output, lane l adds the chunks
+// l, l+32, ... in order, then a fixed xor-shuffle tree.  The output enumeration is
 // mapped back to (i, j) of the wx x wy result (row-major, ld = wy); with herm = 1 the
 // lower triangle is filled with the conjugate transpose.
+constexpr int GRED_WARPS = 8;
 __global__ void gram_reduce_kernel(int nchunk, int nout, int wx, int wy, int herm,
                                    const double2* __restrict__ partial, double2* __restrict__ C,
                                    const int* skip) {
   if (skip && *skip == 0) return;
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int o = blockIdx.x * GRED_WARPS + (threadIdx.x >> 5);
   if (o >= nout) return;
   double2 s = make_double2(0.0, 0.0);
-  for (int b = 0; b < nchunk; ++b) s = cadd(s, partial[(size_t)b * nout + o]);
-  int i, j;
-  gram_index(o, wx, wy, herm, i, j);
-  C[i * wy + j] = s;
-  if (herm && i != j) C[j * wy + i] = make_double2(s.x, -s.y);
+  for (int b = lane; b < nchunk; b += 32) s = cadd(s, partial[(size_t)b * nout + o]);
+  for (int off = 16; off > 0; off >>= 1) s = cadd(s, shfl_xor2(s, off));
+  if (lane == 0) {
+    int i, j;
+    gram_index(o, wx, wy, herm, i, j);
+    C[i * wy + j] = s;
+    if (herm && i != j) C[j * wy + i] = make_double2(s.x, -s.y);
+  }
 }
 
 // ---------------------------------------------------------------- combine -----
@@ -557,18 +563,29 @@ __global__ void chol_inv_kernel(int w, int64_t n, const double2* __restrict__ G,
     }
     return;
   }
+  // G -> inv (as a staging copy) in parallel; ||G||_F by a block reduction
+  __shared__ double red[32];
+  double f = 0.0;
+  for (int e = tid; e < w * w; e += nt) {
+    const double2 v = G[e];
+    inv[e] = v;
+    f += v.x * v.x + v.y * v.y;
+  }
+  for (int off = 16; off > 0; off >>= 1) f += __shfl_xor_sync(0xffffffffu, f, off);
+  if ((tid & 31) == 0) red[tid >> 5] = f;
+  __syncthreads();
   if (tid == 0) {
-    double f = 0.0;
-    for (int e = 0; e < w * w; ++e) f += G[e].x * G[e].x + G[e].y * G[e].y;
+    double t = 0.0;
+    for (int q = 0; q < (nt + 31) / 32; ++q) t += red[q];
     const double u = 1.1102230246251565e-16;
-    shift = 11.0 * ((double)n * w + (double)w * (w + 1)) * u * sqrt(f);
+    shift = 11.0 * ((double)n * w + (double)w * (w + 1)) * u * sqrt(t);
     if (status) status[0] = 0;
   }
   for (int attempt = 0; attempt < 2; ++attempt) {
     __syncthreads();
     for (int e = tid; e < w * w; e += nt) {
       const int i = e / w, j = e - i * w;
-      double2 v = G[e];
+      double2 v = inv[e];
       if (i == j) v = make_double2(v.x + (attempt ? shift : 0.0), 0.0);
       a[e] = v;
     }
@@ -609,7 +626,8 @@ __global__ void chol_inv_kernel(int w, int64_t n, const double2* __restrict__ G,
     if (attempt == 1 && tid == 0 && fallback_counter) atomicAdd(fallback_counter + 1, 1);
   }
   __syncthreads();
-  // inverse of the upper triangular R: column c of inv solves R x = e_c (back substitution)
+  // inverse of the upper triangular R: column c of inv solves R x = e_c (back substitution);
+  // the staging copy of G in inv is dead from here on
   for (int c = tid; c < w; c += nt) {
     for (int i = w - 1; i >= 0; --i) {
       double2 acc = make_double2(i == c ? 1.0 : 0.0, 0.0);

@@ -44,7 +44,7 @@ class Precond(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("precision", C.c_int32),
-                ("no_lock", C.c_int32), ("reserved", C.c_int32), ("stream", C.c_void_p)]
+                ("no_lock", C.c_int32), ("products", C.c_int32), ("stream", C.c_void_p)]
 
 
 class Info(C.Structure):
@@ -130,16 +130,19 @@ class _HostCsr:
 
 # ------------------------------------------------------------------ C names ----
 
+PRODUCTS = {"auto": 0, "combine": 1, "spmm": 2}
+
+
 def gplhr_create(A, B, sigma: complex, k: int, m: int, precond: str = "none",
                  block_size: int = 1, T=None, tol: float = 1e-8, maxit: int = 500,
-                 lock: bool = True, stream: int = 0):
+                 lock: bool = True, stream: int = 0, products: str = "auto"):
     """Returns an opaque context handle (int).  A, B: SciPy CSR (B None = identity)."""
     L = lib()
     hA = _HostCsr(A)
     hB = _HostCsr(B) if B is not None else None
     hT = _HostCsr(T.astype(np.complex128)) if T is not None else None
     pc = Precond(PREC[precond], block_size, C.pointer(hT.desc) if hT else None)
-    opts = Opts(tol, maxit, 0, 0 if lock else 1, 0, stream or None)
+    opts = Opts(tol, maxit, 0, 0 if lock else 1, PRODUCTS[products], stream or None)
     out = C.c_void_p()
     st = L.gplhr_create(C.byref(hA.desc), C.byref(hB.desc) if hB else None, sigma.real,
                         sigma.imag, k, m, C.byref(pc), C.byref(opts), C.byref(out))
@@ -281,10 +284,10 @@ class GPLHR:
     """Owning handle around a gplhr context (marshalling only)."""
 
     def __init__(self, A, B, sigma, k, m, precond="none", block_size=1, T=None, tol=1e-8,
-                 maxit=500, lock=True, stream=0):
+                 maxit=500, lock=True, stream=0, products="auto"):
         self.n, self.k = A.shape[0], k
         self.ctx = gplhr_create(A, B, complex(sigma), k, m, precond, block_size, T, tol, maxit,
-                                lock, stream)
+                                lock, stream, products)
 
     def solve(self, V0=None, seed=0, allow_notconv=False):
         return gplhr_solve(self.ctx, V0, seed, allow_notconv)
