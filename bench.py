@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-k-pairs solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision runs")
     ap.add_argument("--grid", type=int, default=0,
                     help="grid side of a smaller copy of the generalized pencil (profiling captures); "
                          "its lambda_max is scaled from the 64^3 value by ((N+1)/65)^2")
@@ -207,40 +208,9 @@ def main():
             dist.barrier()
 
     stream = torch.cuda.Stream(device=dev)
-    solver = G.GPLHR(pr.A, pr.B, pr.sigma, pr.k, pr.m, pr.precond, pr.block_size, tol=pr.tol,
-                     maxit=10 ** 6, stream=stream.cuda_stream)
-    solver.start(pr.start_block())
-    solver.iterate(W)
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
-    barrier()
-    torch.cuda.synchronize()
-    G.gplhr_profile(solver.ctx, True)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    it_before = solver.iterate(0).iters
-    ev0.record(stream)
-    info = solver.iterate(K)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    done = info.iters - it_before
-    if done != K:
-        raise RuntimeError(f"expected {K} iterations, ran {done} (converged early?)")
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    per_class = {}
-    total_launch = 0
-    for c in KCLASSES:
-        cms, nl, fl, by = G.gplhr_profile_read(solver.ctx, c)
-        per_class[c] = {"ms": cms, "launches": nl, "gflop": fl / 1e9, "gbyte": by / 1e9}
-        total_launch += nl
-    G.gplhr_profile(solver.ctx, False)
+    run = timed_iterations(G, pr, K, W, stream, "fp64", barrier, local, world, dev)
+    ms, per_class, clocks = run["ms"], run["per_class"], run["clocks"]
+    total_launch = sum(v["launches"] for v in per_class.values())
     kern_ms = sum(v["ms"] for v in per_class.values())
     dom = max(per_class, key=lambda c: per_class[c]["ms"])
     d = per_class[dom]
@@ -278,12 +248,24 @@ def main():
         "hbm_spmm_gram": hbm,
         "clocks": clocks,
     }
-    solver.close()
+    if not args.no_mixed:
+        mrun = timed_iterations(G, pr, K, W, stream, "mixed", barrier, local, world, dev)
+        mcls = mrun["per_class"]
+        mk = sum(v["ms"] for v in mcls.values())
+        line["mixed"] = {
+            "value": mrun["ms"] / 1e3 / K / world, "unit": "s/iteration",
+            "ms_per_step": mrun["ms"] / K, "phase": "FP32 bulk (Cholesky-QR Grams, pencil, QZ in FP64)",
+            "kernels": {c: {"share": mcls[c]["ms"] / mk if mk else 0.0, "ms_per_step": mcls[c]["ms"] / K}
+                        for c in KCLASSES},
+            "speedup_vs_fp64": ms / mrun["ms"], "clocks": mrun["clocks"],
+        }
 
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e(pr, K, stream, G)
     if rank == 0 and not args.no_solve:
-        line["solve"] = time_to_pairs(G, stream)
+        line["solve"] = time_to_pairs(G, stream, "fp64")
+        if not args.no_mixed:
+            line["solve_mixed"] = time_to_pairs(G, stream, "mixed")
     if rank == 0 and not args.no_cpu:
         sample = 3
         spi = oracle_iterations(pr, sample, 0)
@@ -295,6 +277,50 @@ def main():
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def timed_iterations(G, pr, K, W, stream, precision, barrier, local, world, dev):
+    """K timed GPLHR iterations after W warm-up ones (CUDA events on the library stream),
+    with the library's per-kernel-class event timing over the same region."""
+    import torch
+    import torch.distributed as dist
+    extra = {"switch_tol": 1e-300, "stall_iters": -1} if precision == "mixed" else {}
+    solver = G.GPLHR(pr.A, pr.B, pr.sigma, pr.k, pr.m, pr.precond, pr.block_size, tol=pr.tol,
+                     maxit=10 ** 6, stream=stream.cuda_stream, precision=precision, **extra)
+    solver.start(pr.start_block())
+    solver.iterate(W)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    G.gplhr_profile(solver.ctx, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    it_before = solver.iterate(0).iters
+    ev0.record(stream)
+    info = solver.iterate(K)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    done = info.iters - it_before
+    if done != K:
+        raise RuntimeError(f"expected {K} iterations, ran {done} (converged early?)")
+    if precision == "mixed" and info.bulk != 1:
+        raise RuntimeError("mixed run left the FP32 bulk phase")
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    per_class = {}
+    for c in KCLASSES:
+        cms, nl, fl, by = G.gplhr_profile_read(solver.ctx, c)
+        per_class[c] = {"ms": cms, "launches": nl, "gflop": fl / 1e9, "gbyte": by / 1e9}
+    G.gplhr_profile(solver.ctx, False)
+    solver.close()
+    return {"ms": ms, "per_class": per_class, "clocks": clocks}
 
 
 def e2e(pr, K, stream, G):
@@ -319,13 +345,13 @@ def e2e(pr, K, stream, G):
             "iterations": info.iters}
 
 
-def time_to_pairs(G, stream):
+def time_to_pairs(G, stream, precision):
     """Seconds to k eigenpairs at the residual target, complex-scaled Schroedinger 256^2."""
     import torch
     from paper_1506_06829_gb300 import problems as P
     pr = P.config3()
     s = G.GPLHR(pr.A, None, pr.sigma, pr.k, pr.m, pr.precond, pr.block_size, tol=pr.tol,
-                maxit=2000, stream=stream.cuda_stream)
+                maxit=2000, stream=stream.cuda_stream, precision=precision)
     V0 = torch.from_numpy(pr.start_block()).to("cuda")
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -338,6 +364,7 @@ def time_to_pairs(G, stream):
     return {"workload": f"{pr.name} (complex-scaled Schroedinger, n = {pr.n}, k = {pr.k}, m = {pr.m}, "
                         f"block-Jacobi {pr.block_size}, tol {pr.tol})",
             "s_to_k_pairs": e0.elapsed_time(e1) / 1e3, "iterations": info.iters,
+            "precision": precision, "fp32_iterations": info.fp32_iters,
             "converged": bool(info.nconv == pr.k), "max_resid": float(max(vec["resid"]))}
 
 

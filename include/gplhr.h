@@ -57,7 +57,13 @@ enum {
   GPLHR_PREC_BLOCK_JACOBI = 2,  /* T = blockdiag of bs x bs diagonal blocks, inverted  */
   GPLHR_PREC_CSR = 3            /* T given explicitly as a sparse matrix (C128)        */
 };
-enum { GPLHR_FP64 = 0 };                                 /* arithmetic of the iteration */
+/* Arithmetic of the iteration.  MIXED: a bulk phase in which the sparse products, the
+ * preconditioner, the projections and block combinations compute in FP32 (complex64
+ * arithmetic with FP32 accumulation, on FP64 storage), while the Cholesky-QR Gram
+ * matrices, the projected pencil, its QZ and the small factors stay FP64; then FP64
+ * refinement iterations once the largest residual is below switch_tol or has not
+ * dropped by 10 % over stall_iters iterations.  Convergence is declared only in FP64. */
+enum { GPLHR_FP64 = 0, GPLHR_MIXED = 1 };
 
 /* Sparse matrix in CSR form (0-based, column indices sorted per row, no duplicates).
  * rowptr has n+1 entries, colind and vals nnz entries; vals are double (GPLHR_R64) or
@@ -96,6 +102,10 @@ typedef struct {
                           fresh sparse products of V and P ((m+3) per iteration), 0 = the
                           one with fewer flops for this pencil                          */
   void* stream;        /* [NULL] cudaStream_t for all device work of the context        */
+  double switch_tol;   /* [1e-5] MIXED: refine in FP64 once max residual < switch_tol   */
+  int32_t stall_iters; /* [5]    MIXED: ... or after this many iterations without a 10 %
+                          decrease of the max residual; < 0: never on a stall            */
+  int32_t reserved;
 } gplhr_opts;
 
 /* Per-solve report.  resid[j] (j < k) is the backward error of pair j,
@@ -108,6 +118,8 @@ typedef struct {
   int32_t nconv;        /* leading pairs meeting tol (locked in order)                 */
   int32_t m;            /* current m after adaptation                                  */
   int32_t n_orth_fallback; /* orth() calls that needed the shifted-Cholesky pass       */
+  int32_t fp32_iters;   /* iterations run in the FP32 bulk phase (GPLHR_MIXED)         */
+  int32_t bulk;         /* 1 while the iteration is still in the FP32 bulk phase        */
   int64_t n_spmm;
   int64_t n_prec;
   int64_t n_qz;

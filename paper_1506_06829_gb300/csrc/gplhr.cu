@@ -59,6 +59,13 @@ struct gplhr_ctx {
   int maxit = 500;
   bool lock = true;
   bool recompute = false;  // AV, BV, AP, BP by sparse products instead of combinations
+  bool mixed = false;      // mixed-precision mode requested
+  bool bulk32 = false;     // currently in the FP32 bulk phase
+  int fp32_iters = 0;      // iterations run in the bulk phase
+  double best_res = 1e300; // stall detection for the bulk phase
+  int since_best = 0;
+  double switch_tol = 1e-5;
+  int stall_iters = 5;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int num_sms = 152;
@@ -153,8 +160,16 @@ void prof_end(gplhr_ctx* ctx, int h) {
 
 // ------------------------------------------------------------------ launches --
 
-gplhr_status launch_spmm_one(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, Blk X, int w, Blk Y,
-                             Blk Y2) {
+template <typename T>
+gplhr_status launch_spmm_t(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, Blk X, int w, Blk Y, Blk Y2);
+
+gplhr_status launch_spmm_one(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, Blk X, int w, Blk Y, Blk Y2,
+                             bool fp32 = false) {
+  return fp32 ? launch_spmm_t<float>(ctx, M, M2, X, w, Y, Y2) : launch_spmm_t<double>(ctx, M, M2, X, w, Y, Y2);
+}
+
+template <typename T>
+gplhr_status launch_spmm_t(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, Blk X, int w, Blk Y, Blk Y2) {
   const int threads = 256;
   const int grid = grid_for((size_t)ctx->n, threads / 32, ctx->num_sms * 16);
   const bool has2 = M2 != nullptr;
@@ -172,25 +187,25 @@ gplhr_status launch_spmm_one(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, 
   if (!has2) {
     gplhr::CsrDev<double> none{nullptr, nullptr, nullptr};
     if (M.dtype == GPLHR_R64)
-      gplhr::spmm_kernel<double, double><<<grid, threads, 0, ctx->stream>>>(ctx->n, dr, none, 0, X.p, X.ld, w,
+      gplhr::spmm_kernel<double, double, T><<<grid, threads, 0, ctx->stream>>>(ctx->n, dr, none, 0, X.p, X.ld, w,
                                                                             Y.p, Y.ld, nullptr, 0);
     else
-      gplhr::spmm_kernel<double2, double><<<grid, threads, 0, ctx->stream>>>(ctx->n, dc, none, 0, X.p, X.ld, w,
+      gplhr::spmm_kernel<double2, double, T><<<grid, threads, 0, ctx->stream>>>(ctx->n, dc, none, 0, X.p, X.ld, w,
                                                                              Y.p, Y.ld, nullptr, 0);
   } else {
     gplhr::CsrDev<double> br{M2->rowptr, M2->col, (const double*)M2->val};
     gplhr::CsrDev<double2> bc{M2->rowptr, M2->col, (const double2*)M2->val};
     if (M.dtype == GPLHR_R64 && M2->dtype == GPLHR_R64)
-      gplhr::spmm_kernel<double, double><<<grid, threads, 0, ctx->stream>>>(ctx->n, dr, br, 1, X.p, X.ld, w, Y.p,
+      gplhr::spmm_kernel<double, double, T><<<grid, threads, 0, ctx->stream>>>(ctx->n, dr, br, 1, X.p, X.ld, w, Y.p,
                                                                             Y.ld, Y2.p, Y2.ld);
     else if (M.dtype == GPLHR_R64)
-      gplhr::spmm_kernel<double, double2><<<grid, threads, 0, ctx->stream>>>(ctx->n, dr, bc, 1, X.p, X.ld, w, Y.p,
+      gplhr::spmm_kernel<double, double2, T><<<grid, threads, 0, ctx->stream>>>(ctx->n, dr, bc, 1, X.p, X.ld, w, Y.p,
                                                                              Y.ld, Y2.p, Y2.ld);
     else if (M2->dtype == GPLHR_R64)
-      gplhr::spmm_kernel<double2, double><<<grid, threads, 0, ctx->stream>>>(ctx->n, dc, br, 1, X.p, X.ld, w, Y.p,
+      gplhr::spmm_kernel<double2, double, T><<<grid, threads, 0, ctx->stream>>>(ctx->n, dc, br, 1, X.p, X.ld, w, Y.p,
                                                                              Y.ld, Y2.p, Y2.ld);
     else
-      gplhr::spmm_kernel<double2, double2><<<grid, threads, 0, ctx->stream>>>(ctx->n, dc, bc, 1, X.p, X.ld, w,
+      gplhr::spmm_kernel<double2, double2, T><<<grid, threads, 0, ctx->stream>>>(ctx->n, dc, bc, 1, X.p, X.ld, w,
                                                                               Y.p, Y.ld, Y2.p, Y2.ld);
   }
   prof_end(ctx, ph);
@@ -202,20 +217,24 @@ gplhr_status launch_spmm_one(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, 
 gplhr_status spmm_AB(gplhr_ctx* ctx, Blk X, int w, Blk AX, Blk BX) {
   if (w <= 0) return GPLHR_OK;
   ctx->n_spmm += 1;
-  return launch_spmm_one(ctx, ctx->A, ctx->hasB ? &ctx->B : nullptr, X, w, AX, BX);
+  return launch_spmm_one(ctx, ctx->A, ctx->hasB ? &ctx->B : nullptr, X, w, AX, BX, ctx->bulk32);
 }
 
 // C (wx x (wy0 + wy1), row-major) = X^* [Y0 Y1].  herm: X^* X (only the upper
 // triangle is computed; the lower one is filled by conjugation).
 template <int ACC>
 void launch_gram_acc(gplhr_ctx* ctx, dim3 grid, size_t smem, int rows, Blk X, int wx, Blk Y0, int wy0,
-                     Blk Y1, int wy1, int herm, int nout, int G, int RG, const int* skip) {
-  gplhr::gram_partial_kernel<ACC><<<grid, gplhr::GRAM_THREADS, smem, ctx->stream>>>(
-      ctx->n, rows, X.p, X.ld, wx, Y0.p, Y0.ld, wy0, Y1.p, Y1.ld, wy1, herm, nout, G, RG, ctx->gram_part, skip);
+                     Blk Y1, int wy1, int herm, int nout, int G, int RG, const int* skip, bool fp32) {
+  if (fp32)
+    gplhr::gram_partial_kernel<ACC, float><<<grid, gplhr::GRAM_THREADS, smem, ctx->stream>>>(
+        ctx->n, rows, X.p, X.ld, wx, Y0.p, Y0.ld, wy0, Y1.p, Y1.ld, wy1, herm, nout, G, RG, ctx->gram_part, skip);
+  else
+    gplhr::gram_partial_kernel<ACC, double><<<grid, gplhr::GRAM_THREADS, smem, ctx->stream>>>(
+        ctx->n, rows, X.p, X.ld, wx, Y0.p, Y0.ld, wy0, Y1.p, Y1.ld, wy1, herm, nout, G, RG, ctx->gram_part, skip);
 }
 
 gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy1, double2* C,
-                  const int* skip = nullptr, bool herm = false, bool count = true) {
+                  const int* skip = nullptr, bool herm = false, bool count = true, bool fp32 = false) {
   const int wy = wy0 + wy1;
   if (herm && (wy1 != 0 || wy0 != wx)) herm = false;
   const int nout = herm ? wx * (wx + 1) / 2 : wx * wy;
@@ -240,10 +259,10 @@ gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy
   const double by = 16.0 * ctx->n * (self ? wx : wx + wy);
   const int ph = prof_begin(ctx, KC_GRAM, count ? 8.0 * ctx->n * nout : 0.0, count ? by : 0.0, 2);
   switch (acc) {
-    case 8: launch_gram_acc<8>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip); break;
-    case 4: launch_gram_acc<4>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip); break;
-    case 2: launch_gram_acc<2>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip); break;
-    default: launch_gram_acc<1>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip); break;
+    case 8: launch_gram_acc<8>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip, fp32); break;
+    case 4: launch_gram_acc<4>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip, fp32); break;
+    case 2: launch_gram_acc<2>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip, fp32); break;
+    default: launch_gram_acc<1>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip, fp32); break;
   }
   CK(cudaGetLastError());
   gplhr::gram_reduce_kernel<<<(nout + gplhr::GRED_WARPS - 1) / gplhr::GRED_WARPS, 32 * gplhr::GRED_WARPS, 0,
@@ -264,7 +283,9 @@ struct In {
 // columns c_store..c only contribute |.|^2 sums (reduced into ctx->d_norms).
 gplhr_status combine(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, bool beta_one,
                      const int* skip = nullptr, Blk Y2 = Blk{nullptr, 0}, int c_split = -1,
-                     int c_store = -1, bool count = true) {
+                     int c_store = -1, bool count = true, int fp32 = -1) {
+  // fp32 = -1: the current phase decides (FP32 in the bulk phase of the mixed mode)
+  const bool use32 = fp32 < 0 ? ctx->bulk32 : fp32 != 0;
   if (c <= 0 || ctx->n == 0) return GPLHR_OK;
   if (c_store < 0) c_store = c;
   if (c_split < 0) c_split = c_store;
@@ -288,14 +309,19 @@ gplhr_status combine(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, b
   const int grid = grid_for((size_t)ctx->n, std::max(rows_tile, 64), 4 * ctx->num_sms);
   const int rows_per_cta = (ctx->n + grid - 1) / grid;
   a.normpart = c_store < c ? ctx->norm_part : nullptr;
-  const size_t smem = (size_t)(wsum * c + rows_tile * wsum + rows_tile * c) * sizeof(double2);
+  const size_t smem =
+      (size_t)(wsum * c + rows_tile * wsum + rows_tile * c) * (use32 ? sizeof(float2) : sizeof(double2));
   double by = 16.0 * ctx->n * (wsum + c_store * (beta_one ? 2.0 : 1.0));
   const int ph = prof_begin(ctx, KC_COMBINE, count ? 8.0 * ctx->n * wsum * c : 0.0, count ? by : 0.0,
                            c_store < c ? 2 : 1);
-  gplhr::combine_kernel<<<grid, gplhr::COMB_THREADS, smem, ctx->stream>>>(ctx->n, rows_per_cta, a);
+  if (use32)
+    gplhr::combine_kernel<float><<<grid, gplhr::COMB_THREADS, smem, ctx->stream>>>(ctx->n, rows_per_cta, a);
+  else
+    gplhr::combine_kernel<double><<<grid, gplhr::COMB_THREADS, smem, ctx->stream>>>(ctx->n, rows_per_cta, a);
   CK(cudaGetLastError());
   if (c_store < c) {
-    gplhr::norm_reduce_kernel<<<1, 128, 0, ctx->stream>>>(grid, c - c_store, ctx->norm_part, ctx->d_norms);
+    const int nc = c - c_store;
+    gplhr::norm_reduce_kernel<<<(nc + 3) / 4, 128, 0, ctx->stream>>>(grid, nc, ctx->norm_part, ctx->d_norms);
     CK(cudaGetLastError());
   }
   prof_end(ctx, ph);
@@ -335,8 +361,11 @@ gplhr_status precond_apply_impl(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
       return GPLHR_OK;
     }
     case GPLHR_PREC_JACOBI: {
-      gplhr::jacobi_kernel<<<grid_for((size_t)n * w, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-          n, w, ctx->prec_data, X.p, X.ld, Y.p, Y.ld);
+      const int g = grid_for((size_t)n * w, 256, 8 * ctx->num_sms);
+      if (ctx->bulk32)
+        gplhr::jacobi_kernel<float><<<g, 256, 0, ctx->stream>>>(n, w, ctx->prec_data, X.p, X.ld, Y.p, Y.ld);
+      else
+        gplhr::jacobi_kernel<double><<<g, 256, 0, ctx->stream>>>(n, w, ctx->prec_data, X.p, X.ld, Y.p, Y.ld);
       CK(cudaGetLastError());
       return GPLHR_OK;
     }
@@ -346,20 +375,24 @@ gplhr_status precond_apply_impl(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
       const int bpc = std::max(1, 1024 / (bs * w));
       const int grid = (nblocks + bpc - 1) / bpc;
       const size_t smem = (size_t)bpc * bs * w * sizeof(double2);
-      gplhr::block_jacobi_kernel<<<grid, gplhr::BJ_THREADS, smem, ctx->stream>>>(n, bs, w, ctx->prec_data, X.p,
-                                                                                X.ld, Y.p, Y.ld, bpc);
+      if (ctx->bulk32)
+        gplhr::block_jacobi_kernel<float><<<grid, gplhr::BJ_THREADS, smem, ctx->stream>>>(
+            n, bs, w, ctx->prec_data, X.p, X.ld, Y.p, Y.ld, bpc);
+      else
+        gplhr::block_jacobi_kernel<double><<<grid, gplhr::BJ_THREADS, smem, ctx->stream>>>(
+            n, bs, w, ctx->prec_data, X.p, X.ld, Y.p, Y.ld, bpc);
       CK(cudaGetLastError());
       return GPLHR_OK;
     }
     case GPLHR_PREC_CSR: {
       if (X.p == Y.p) {  // out of place through a scratch block
-        TRY(launch_spmm_one(ctx, ctx->Tcsr, nullptr, X, w, Blk{ctx->Tw1, ctx->k}, Blk{nullptr, 0}));
+        TRY(launch_spmm_one(ctx, ctx->Tcsr, nullptr, X, w, Blk{ctx->Tw1, ctx->k}, Blk{nullptr, 0}, ctx->bulk32));
         gplhr::copy_block_kernel<<<grid_for((size_t)n * w, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
             n, w, ctx->Tw1, ctx->k, Y.p, Y.ld);
         CK(cudaGetLastError());
         return GPLHR_OK;
       }
-      return launch_spmm_one(ctx, ctx->Tcsr, nullptr, X, w, Y, Blk{nullptr, 0});
+      return launch_spmm_one(ctx, ctx->Tcsr, nullptr, X, w, Y, Blk{nullptr, 0}, ctx->bulk32);
     }
   }
   ctx->err = "unknown preconditioner";
@@ -369,7 +402,7 @@ gplhr_status precond_apply_impl(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
 // X <- X - L (L^* X): one projection against the leading block L (wl columns).
 gplhr_status project_out(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w) {
   if (wl <= 0 || w <= 0) return GPLHR_OK;
-  TRY(gram(ctx, L, wl, X, w, Blk{nullptr, 0}, 0, ctx->dProjC));
+  TRY(gram(ctx, L, wl, X, w, Blk{nullptr, 0}, 0, ctx->dProjC, nullptr, false, true, ctx->bulk32));
   return combine(ctx, {In{L, wl, ctx->dProjC, kMinusOne}}, X, w, true);
 }
 
@@ -393,7 +426,7 @@ gplhr_status orth_against(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w, const std
     const bool cnt = pass < 2;
     const Blk none{nullptr, 0};
     if (wl > 0) {
-      TRY(gram(ctx, L, wl, X, w, none, 0, ctx->dProjC, skip, false, cnt));
+      TRY(gram(ctx, L, wl, X, w, none, 0, ctx->dProjC, skip, false, cnt, ctx->bulk32));
       TRY(combine(ctx, {In{L, wl, ctx->dProjC, kMinusOne}}, X, w, true, skip, none, -1, -1, cnt));
       for (const Extra& e : ex)
         TRY(combine(ctx, {In{e.EL, wl, ctx->dProjC, kMinusOne}}, e.E, w, true, skip, none, -1, -1, cnt));
@@ -513,6 +546,10 @@ gplhr_status start(gplhr_ctx* ctx) {
   ctx->hasP = false;
   ctx->n_spmm = ctx->n_prec = ctx->n_qz = 0;
   ctx->h2d_bytes = ctx->d2h_bytes = 0;
+  ctx->bulk32 = ctx->mixed;
+  ctx->fp32_iters = 0;
+  ctx->best_res = 1e300;
+  ctx->since_best = 0;
   CK(cudaMemsetAsync(ctx->d_diag, 0, 2 * sizeof(int), ctx->stream));
   TRY(orth_against(ctx, Blk{nullptr, 0}, 0, blkZ(ctx, 0), k));                // V = orth(V0)
   TRY(spmm_AB(ctx, blkZ(ctx, 0), k, blkAZ(ctx, 0), blkBZ(ctx, 0)));        // AV, BV
@@ -550,9 +587,35 @@ gplhr_status start(gplhr_ctx* ctx) {
   return residuals(ctx);
 }
 
+// Mixed mode: leave the FP32 bulk phase once the largest residual is below switch_tol
+// or has not dropped by 10 % over stall_iters iterations (survey reading C14).  The
+// products AV, BV (and AP, BP when they are kept as combinations) are then formed again
+// in FP64, and the residuals recomputed in FP64.
+gplhr_status phase_update(gplhr_ctx* ctx) {
+  if (!ctx->bulk32) return GPLHR_OK;
+  double mx = 0.0;
+  for (double r : ctx->resid) mx = std::max(mx, r);
+  bool go = mx < ctx->switch_tol;
+  if (mx < 0.9 * ctx->best_res) {
+    ctx->best_res = mx;
+    ctx->since_best = 0;
+  } else if (++ctx->since_best >= ctx->stall_iters && ctx->stall_iters > 0) {
+    go = true;
+  }
+  if (!go) return GPLHR_OK;
+  ctx->bulk32 = false;
+  const int k = ctx->k;
+  TRY(spmm_AB(ctx, blkZ(ctx, 0), k, blkAZ(ctx, 0), blkBZ(ctx, 0)));
+  if (!ctx->recompute && ctx->hasP)
+    TRY(spmm_AB(ctx, Blk{ctx->Pb, k}, k, Blk{ctx->APb, k}, Blk{ctx->hasB ? ctx->BPb : ctx->Pb, k}));
+  return residuals(ctx);
+}
+
 // Convergence bookkeeping after residuals(): soft locking in order and m-adaptation.
+// Nothing converges or locks during the FP32 bulk phase.
 bool converged_update(gplhr_ctx* ctx) {
   const int k = ctx->k;
+  if (ctx->bulk32) return false;
   bool all = true;
   for (int j = 0; j < k; ++j) all = all && ctx->resid[j] <= ctx->tol;
   if (all) return true;
@@ -681,6 +744,8 @@ void fill_info(gplhr_ctx* ctx, gplhr_info* info) {
   info->nconv = lead;
   info->m = ctx->m;
   info->n_orth_fallback = ctx->h_diag ? ctx->h_diag[0] : 0;
+  info->fp32_iters = ctx->fp32_iters;
+  info->bulk = ctx->bulk32 ? 1 : 0;
   info->n_spmm = ctx->n_spmm;
   info->n_prec = ctx->n_prec;
   info->n_qz = ctx->n_qz;
@@ -691,10 +756,13 @@ void fill_info(gplhr_ctx* ctx, gplhr_info* info) {
 }
 
 gplhr_status run_iterations(gplhr_ctx* ctx, int niter, gplhr_info* info, bool* conv_out) {
+  TRY(phase_update(ctx));
   bool conv = converged_update(ctx);
   for (int i = 0; i < niter && !conv; ++i) {
+    if (ctx->bulk32) ctx->fp32_iters += 1;
     TRY(iterate_once(ctx));
     TRY(residuals(ctx));
+    TRY(phase_update(ctx));
     conv = converged_update(ctx);
   }
   fill_info(ctx, info);
@@ -929,13 +997,19 @@ gplhr_status allocate(gplhr_ctx* ctx) {
 
 gplhr_status set_smem_limits(gplhr_ctx* ctx) {
   const int big = 200 * 1024;
-  CK(cudaFuncSetAttribute(gplhr::combine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::combine_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::combine_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<8, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<4, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  CK(cudaFuncSetAttribute(gplhr::block_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::block_jacobi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::block_jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::invert_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   return GPLHR_OK;
 }
@@ -1057,6 +1131,14 @@ gplhr_status gplhr_create(const gplhr_csr* A, const gplhr_csr* B, double sigma_r
     if (opts->maxit > 0) ctx->maxit = opts->maxit;
     ctx->lock = opts->no_lock == 0;
     ctx->stream = (cudaStream_t)opts->stream;
+    ctx->mixed = opts->precision == GPLHR_MIXED;
+    if (opts->switch_tol > 0) ctx->switch_tol = opts->switch_tol;
+    if (opts->stall_iters != 0) ctx->stall_iters = opts->stall_iters;
+    if (opts->precision != GPLHR_FP64 && opts->precision != GPLHR_MIXED) {
+      g_create_error = "opts.precision must be GPLHR_FP64 or GPLHR_MIXED";
+      delete ctx;
+      return GPLHR_EINVAL;
+    }
   }
   const int products = opts ? opts->products : 0;
   if (products < 0 || products > 2) {
@@ -1202,7 +1284,8 @@ gplhr_status gplhr_vectors(gplhr_ctx* ctx, double* alpha, double* beta, double* 
     TRY(upload(ctx, ctx->dC1, hz, k * k));
     // scratch only: Rw carries the residual into the next gplhr_iterate
     Blk Xb{ctx->Tw3, k};
-    TRY(combine(ctx, {In{blkZ(ctx, 0), k, ctx->dC1, kOne}}, Xb, k, false));
+    const Blk none{nullptr, 0};
+    TRY(combine(ctx, {In{blkZ(ctx, 0), k, ctx->dC1, kOne}}, Xb, k, false, nullptr, none, -1, -1, true, 0));
     if (resid) {
       Blk AX{ctx->Tw1, k}, BX{ctx->hasB ? ctx->Tw2 : ctx->Tw3, k};
       TRY(launch_spmm_one(ctx, ctx->A, ctx->hasB ? &ctx->B : nullptr, Xb, k, AX, BX));
@@ -1214,8 +1297,8 @@ gplhr_status gplhr_vectors(gplhr_ctx* ctx, double* alpha, double* beta, double* 
           ha[i * k + j] = i == j ? d2(ctx->RA(j, j)) : make_double2(0.0, 0.0);
         }
       TRY(upload(ctx, ctx->dC2, hb, 2 * k * k));
-      TRY(combine(ctx, {In{AX, k, ctx->dC2, kOne}, In{BX, k, ctx->dC2 + k * k, kMinusOne}}, Blk{nullptr, 0}, k,
-                  false, nullptr, Blk{nullptr, 0}, 0, 0));
+      TRY(combine(ctx, {In{AX, k, ctx->dC2, kOne}, In{BX, k, ctx->dC2 + k * k, kMinusOne}}, none, k, false,
+                  nullptr, none, 0, 0, true, 0));
       std::vector<double> nrm(k);
       CK(cudaMemcpyAsync(nrm.data(), ctx->d_norms, k * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
       CK(cudaStreamSynchronize(ctx->stream));

@@ -46,6 +46,62 @@ __device__ __forceinline__ double2 shfl_xor2(double2 v, int m) {
   return v;
 }
 
+// Single-precision complex (the FP32 bulk phase of the mixed-precision mode computes
+// on GB300's FFMA pipe; storage stays complex128 and is converted on load and store).
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+  c.x = fmaf(a.x, b.x, c.x);
+  c.x = fmaf(-a.y, b.y, c.x);
+  c.y = fmaf(a.x, b.y, c.y);
+  c.y = fmaf(a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ float2 cfmaconj(float2 a, float2 b, float2 c) {
+  c.x = fmaf(a.x, b.x, c.x);
+  c.x = fmaf(a.y, b.y, c.x);
+  c.y = fmaf(a.x, b.y, c.y);
+  c.y = fmaf(-a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
+  v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+  v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+  return v;
+}
+
+// Compute-type traits: T = double (FP64) or float (FP32).
+template <typename T> struct Cx;
+template <> struct Cx<double> { using t = double2; };
+template <> struct Cx<float> { using t = float2; };
+template <typename T> using cplx = typename Cx<T>::t;
+
+template <typename T> __device__ __forceinline__ cplx<T> to_t(double2 v);
+template <> __device__ __forceinline__ double2 to_t<double>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 to_t<float>(double2 v) {
+  return make_float2((float)v.x, (float)v.y);
+}
+__device__ __forceinline__ double2 to_d(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d(float2 v) { return make_double2(v.x, v.y); }
+template <typename T> __device__ __forceinline__ cplx<T> czero() {
+  cplx<T> z;
+  z.x = 0;
+  z.y = 0;
+  return z;
+}
+// acc + v * x for a sparse-matrix value v (real double or complex double2)
+template <typename T> __device__ __forceinline__ cplx<T> mfma(double v, cplx<T> x, cplx<T> acc) {
+  const T r = (T)v;
+  acc.x = fma(r, x.x, acc.x);
+  acc.y = fma(r, x.y, acc.y);
+  return acc;
+}
+template <typename T> __device__ __forceinline__ cplx<T> mfma(double2 v, cplx<T> x, cplx<T> acc) {
+  return cfma(to_t<T>(v), x, acc);
+}
+
 // ------------------------------------------------------------------- SpMM -----
 // Y = M X for up to two CSR matrices sharing the input block (A and B of the pencil).
 // One warp per row.  For a block width w <= 32 the warp is split into 32/wp
@@ -59,30 +115,28 @@ struct CsrDev {
   const VT* val;
 };
 
-template <typename VT>
+template <typename VT, typename T>
 __device__ __forceinline__ void spmm_row(const CsrDev<VT>& M, int r, const double2* __restrict__ X,
                                          int ldx, int c0, int cw, int wp, int lane,
                                          double2* __restrict__ Y, int ldy) {
   const int slot = lane / wp;
   const int nslot = 32 / wp;
   const int c = lane - slot * wp;
-  double2 acc = make_double2(0.0, 0.0);
+  cplx<T> acc = czero<T>();
   const int j0 = M.rowptr[r], j1 = M.rowptr[r + 1];
   if (c < cw) {
     for (int j = j0 + slot; j < j1; j += nslot) {
       const VT v = M.val[j];
       const int cc = M.col[j];
-      acc = vfma(v, X[(size_t)cc * ldx + c0 + c], acc);
+      acc = mfma<T>(v, to_t<T>(X[(size_t)cc * ldx + c0 + c]), acc);
     }
   }
-  for (int off = wp; off < 32; off <<= 1) {
-    double2 o = shfl_xor2(acc, off);
-    acc = cadd(acc, o);
-  }
-  if (slot == 0 && c < cw) Y[(size_t)r * ldy + c0 + c] = acc;
+  for (int off = wp; off < 32; off <<= 1) acc = cadd(acc, shfl_xor2(acc, off));
+  if (slot == 0 && c < cw) Y[(size_t)r * ldy + c0 + c] = to_d(acc);
 }
 
-template <typename VTA, typename VTB>
+// T is the arithmetic (double, or float in the FP32 bulk phase); blocks stay complex128.
+template <typename VTA, typename VTB, typename T>
 __global__ void spmm_kernel(int n, CsrDev<VTA> A, CsrDev<VTB> B, int hasB,
                             const double2* __restrict__ X, int ldx, int w,
                             double2* __restrict__ AX, int ldax, double2* __restrict__ BX, int ldbx) {
@@ -94,8 +148,8 @@ __global__ void spmm_kernel(int n, CsrDev<VTA> A, CsrDev<VTB> B, int hasB,
       const int cw = min(32, w - c0);
       int wp = 1;
       while (wp < cw) wp <<= 1;
-      spmm_row(A, r, X, ldx, c0, cw, wp, lane, AX, ldax);
-      if (hasB) spmm_row(B, r, X, ldx, c0, cw, wp, lane, BX, ldbx);
+      spmm_row<VTA, T>(A, r, X, ldx, c0, cw, wp, lane, AX, ldax);
+      if (hasB) spmm_row<VTB, T>(B, r, X, ldx, c0, cw, wp, lane, BX, ldbx);
     }
   }
 }
@@ -131,17 +185,19 @@ __device__ __forceinline__ void gram_index(int o, int wx, int wy, int herm, int&
   j = r + (o - off);
 }
 
-template <int ACC>
+template <int ACC, typename T = double>
 __global__ void __launch_bounds__(GRAM_THREADS)
 gram_partial_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, int ldx, int wx,
                     const double2* __restrict__ Y0, int ldy0, int wy0, const double2* __restrict__ Y1,
                     int ldy1, int wy1, int herm, int nout, int G, int RG, double2* __restrict__ partial,
                     const int* skip) {
   if (skip && *skip == 0) return;
-  extern __shared__ double2 sm[];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  using C2 = cplx<T>;
+  C2* sm = reinterpret_cast<C2*>(smraw);
   const int wy = wy0 + wy1;
-  double2* xs = sm;                         // GRAM_ROWS x wx
-  double2* ys = sm + GRAM_ROWS * wx;        // GRAM_ROWS x wy
+  C2* xs = sm;                         // GRAM_ROWS x wx
+  C2* ys = sm + GRAM_ROWS * wx;        // GRAM_ROWS x wy
   const int tid = threadIdx.x;
   const int g = tid % G, rg = tid / G;
   const int tile0 = blockIdx.y * G * ACC;
@@ -149,11 +205,11 @@ gram_partial_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, in
   const bool active = rg < RG && o0 < nout;
   const int r0 = blockIdx.x * rows_per_chunk;
   const int r1 = min(n, r0 + rows_per_chunk);
-  double2 acc[ACC];
+  C2 acc[ACC];
   int oi[ACC], oj[ACC];
 #pragma unroll
   for (int t = 0; t < ACC; ++t) {
-    acc[t] = make_double2(0.0, 0.0);
+    acc[t] = czero<T>();
     const int o = min(o0 + t, nout - 1);
     gram_index(o, wx, wy, herm, oi[t], oj[t]);
   }
@@ -162,18 +218,18 @@ gram_partial_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, in
     __syncthreads();
     for (int e = tid; e < nr * wx; e += blockDim.x) {
       const int rr = e / wx, cc = e - rr * wx;
-      xs[rr * wx + cc] = X[(size_t)(rb + rr) * ldx + cc];
+      xs[rr * wx + cc] = to_t<T>(X[(size_t)(rb + rr) * ldx + cc]);
     }
     for (int e = tid; e < nr * wy; e += blockDim.x) {
       const int rr = e / wy, cc = e - rr * wy;
-      ys[rr * wy + cc] = cc < wy0 ? Y0[(size_t)(rb + rr) * ldy0 + cc]
-                                  : Y1[(size_t)(rb + rr) * ldy1 + (cc - wy0)];
+      ys[rr * wy + cc] = to_t<T>(cc < wy0 ? Y0[(size_t)(rb + rr) * ldy0 + cc]
+                                          : Y1[(size_t)(rb + rr) * ldy1 + (cc - wy0)]);
     }
     __syncthreads();
     if (active) {
       for (int rr = rg; rr < nr; rr += RG) {
-        const double2* xr = xs + rr * wx;
-        const double2* yr = ys + rr * wy;
+        const C2* xr = xs + rr * wx;
+        const C2* yr = ys + rr * wy;
 #pragma unroll
         for (int t = 0; t < ACC; ++t) acc[t] = cfmaconj(xr[oi[t]], yr[oj[t]], acc[t]);
       }
@@ -181,7 +237,7 @@ gram_partial_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, in
   }
   // add the RG row-group partials: red[rg][g*ACC + t]
   __syncthreads();
-  double2* red = sm;
+  C2* red = sm;
   const int per = G * ACC;
   if (rg < RG) {
 #pragma unroll
@@ -192,8 +248,8 @@ gram_partial_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, in
   for (int e = tid; e < per; e += blockDim.x) {
     const int o = tile0 + e;
     if (o >= nout) break;
-    double2 s = red[e];
-    for (int q = 1; q < RG; ++q) s = cadd(s, red[q * per + e]);
+    double2 s = to_d(red[e]);
+    for (int q = 1; q < RG; ++q) s = cadd(s, to_d(red[q * per + e]));
     out[o] = s;
   }
 }
@@ -260,23 +316,26 @@ __device__ __forceinline__ double2* comb_out(const CombArgs& a, int r, int cc) {
   return cc < a.c_split ? a.Y + (size_t)r * a.ldy + cc : a.Y2 + (size_t)r * a.ldy2 + (cc - a.c_split);
 }
 
+template <typename T = double>
 __global__ void combine_kernel(int n, int rows_per_cta, CombArgs a) {
   if (a.skip && *a.skip == 0) return;
-  extern __shared__ double2 sm[];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  using C2 = cplx<T>;
+  C2* sm = reinterpret_cast<C2*>(smraw);
   // layout: C_0 .. C_{nin-1} (w_t x c each, pre-scaled by alpha_t), then the staged
   // rows: rows_tile x (sum w_t) X values, then rows_tile x c old Y values (beta = 1)
   int wsum = 0;
   for (int t = 0; t < a.nin; ++t) wsum += a.in[t].w;
-  double2* cs = sm;
-  double2* xs = cs + wsum * a.c;
+  C2* cs = sm;
+  C2* xs = cs + wsum * a.c;
   const int rows_tile = comb_rows_tile(a.c);
-  double2* ys = xs + rows_tile * wsum;
+  C2* ys = xs + rows_tile * wsum;
   __shared__ double nsum[COMB_MAX_NORMS];
   {
     int off = 0;
     for (int t = 0; t < a.nin; ++t) {
       const int sz = a.in[t].w * a.c;
-      for (int e = threadIdx.x; e < sz; e += blockDim.x) cs[off + e] = cmul(a.in[t].alpha, a.in[t].C[e]);
+      for (int e = threadIdx.x; e < sz; e += blockDim.x) cs[off + e] = to_t<T>(cmul(a.in[t].alpha, a.in[t].C[e]));
       off += sz;
     }
   }
@@ -292,26 +351,27 @@ __global__ void combine_kernel(int n, int rows_per_cta, CombArgs a) {
       const int w = a.in[t].w;
       for (int e = threadIdx.x; e < nr * w; e += blockDim.x) {
         const int rr = e / w, cc = e - rr * w;
-        xs[rr * wsum + off + cc] = a.in[t].X[(size_t)(rb + rr) * a.in[t].ldx + cc];
+        xs[rr * wsum + off + cc] = to_t<T>(a.in[t].X[(size_t)(rb + rr) * a.in[t].ldx + cc]);
       }
       off += w;
     }
     if (a.beta_one) {
       for (int e = threadIdx.x; e < nr * a.c_store; e += blockDim.x) {
         const int rr = e / a.c_store, cc = e - rr * a.c_store;
-        ys[rr * a.c + cc] = *comb_out(a, rb + rr, cc);
+        ys[rr * a.c + cc] = to_t<T>(*comb_out(a, rb + rr, cc));
       }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < nr * a.c; e += blockDim.x) {
       const int rr = e / a.c, cc = e - rr * a.c;
-      double2 acc = (a.beta_one && cc < a.c_store) ? ys[rr * a.c + cc] : make_double2(0.0, 0.0);
-      const double2* xr = xs + rr * wsum;
+      C2 acc = (a.beta_one && cc < a.c_store) ? ys[rr * a.c + cc] : czero<T>();
+      const C2* xr = xs + rr * wsum;
       for (int j = 0; j < wsum; ++j) acc = cfma(xr[j], cs[j * a.c + cc], acc);
       if (cc < a.c_store) {
-        *comb_out(a, rb + rr, cc) = acc;
+        *comb_out(a, rb + rr, cc) = to_d(acc);
       } else {
-        atomicAdd(&nsum[cc - a.c_store], acc.x * acc.x + acc.y * acc.y);
+        const double2 v = to_d(acc);
+        atomicAdd(&nsum[cc - a.c_store], v.x * v.x + v.y * v.y);
       }
     }
   }
@@ -323,13 +383,16 @@ __global__ void combine_kernel(int n, int rows_per_cta, CombArgs a) {
 }
 
 // normout[j] = sum_b normpart[b][j]  (fixed order)
+// one warp per column, lane-strided then a fixed shuffle tree (deterministic)
 __global__ void norm_reduce_kernel(int nb, int nc, const double* __restrict__ part,
                                    double* __restrict__ out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (j >= nc) return;
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += part[(size_t)b * nc + j];
-  out[j] = s;
+  for (int b = lane; b < nb; b += 32) s += part[(size_t)b * nc + j];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) out[j] = s;
 }
 
 // Y = alpha X1 + beta X2 (elementwise, n x w)
@@ -370,13 +433,14 @@ __global__ void real_to_complex_kernel(int n, int w, const double* __restrict__ 
 
 // --------------------------------------------------------- preconditioners ----
 // Jacobi: Y[r][c] = d[r] X[r][c]
+template <typename T = double>
 __global__ void jacobi_kernel(int n, int w, const double2* __restrict__ d, const double2* __restrict__ X,
                               int ldx, double2* __restrict__ Y, int ldy) {
   const size_t total = (size_t)n * w;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / w), c = (int)(e - (size_t)r * w);
-    Y[(size_t)r * ldy + c] = cmul(d[r], X[(size_t)r * ldx + c]);
+    Y[(size_t)r * ldy + c] = to_d(cmul(to_t<T>(d[r]), to_t<T>(X[(size_t)r * ldx + c])));
   }
 }
 
@@ -385,11 +449,13 @@ __global__ void jacobi_kernel(int n, int w, const double2* __restrict__ d, const
 // handles BJ_BLOCKS_PER_CTA consecutive blocks; X rows are staged in shared memory,
 // so Y may equal X.
 constexpr int BJ_THREADS = 256;
+template <typename T = double>
 __global__ void block_jacobi_kernel(int n, int bs, int w, const double2* __restrict__ Tinv,
                                     const double2* __restrict__ X, int ldx,
                                     double2* __restrict__ Y, int ldy, int blocks_per_cta) {
-  extern __shared__ double2 sm[];
-  double2* xs = sm;  // blocks_per_cta * bs rows x w
+  extern __shared__ __align__(16) unsigned char smraw[];
+  using C2 = cplx<T>;
+  C2* xs = reinterpret_cast<C2*>(smraw);  // blocks_per_cta * bs rows x w
   const int nblocks = (n + bs - 1) / bs;
   const int b0 = blockIdx.x * blocks_per_cta;
   const int b1 = min(nblocks, b0 + blocks_per_cta);
@@ -399,7 +465,7 @@ __global__ void block_jacobi_kernel(int n, int bs, int w, const double2* __restr
   const int nrows = rend - rstart;
   for (int e = threadIdx.x; e < nrows * w; e += blockDim.x) {
     const int rr = e / w, cc = e - rr * w;
-    xs[rr * w + cc] = X[(size_t)(rstart + rr) * ldx + cc];
+    xs[rr * w + cc] = to_t<T>(X[(size_t)(rstart + rr) * ldx + cc]);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < nrows * w; e += blockDim.x) {
@@ -407,11 +473,11 @@ __global__ void block_jacobi_kernel(int n, int bs, int w, const double2* __restr
     const int blk = rr / bs, i = rr - blk * bs;
     const int gb = b0 + blk;
     const int rows_in_blk = min(bs, n - gb * bs);
-    const double2* T = Tinv + (size_t)gb * bs * bs + (size_t)i * bs;
-    double2 acc = make_double2(0.0, 0.0);
-    const double2* xb = xs + (size_t)blk * bs * w;
-    for (int j = 0; j < rows_in_blk; ++j) acc = cfma(T[j], xb[j * w + cc], acc);
-    Y[(size_t)(rstart + rr) * ldy + cc] = acc;
+    const double2* Tm = Tinv + (size_t)gb * bs * bs + (size_t)i * bs;
+    C2 acc = czero<T>();
+    const C2* xb = xs + (size_t)blk * bs * w;
+    for (int j = 0; j < rows_in_blk; ++j) acc = cfma(to_t<T>(Tm[j]), xb[j * w + cc], acc);
+    Y[(size_t)(rstart + rr) * ldy + cc] = to_d(acc);
   }
 }
 

@@ -44,12 +44,14 @@ class Precond(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("precision", C.c_int32),
-                ("no_lock", C.c_int32), ("products", C.c_int32), ("stream", C.c_void_p)]
+                ("no_lock", C.c_int32), ("products", C.c_int32), ("stream", C.c_void_p),
+                ("switch_tol", C.c_double), ("stall_iters", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Info(C.Structure):
     _fields_ = [("iters", C.c_int32), ("nconv", C.c_int32), ("m", C.c_int32),
-                ("n_orth_fallback", C.c_int32), ("n_spmm", C.c_int64), ("n_prec", C.c_int64),
+                ("n_orth_fallback", C.c_int32), ("fp32_iters", C.c_int32), ("bulk", C.c_int32),
+                ("n_spmm", C.c_int64), ("n_prec", C.c_int64),
                 ("n_qz", C.c_int64), ("n_launch", C.c_int64), ("h2d_bytes", C.c_int64),
                 ("d2h_bytes", C.c_int64), ("resid", C.c_double * 64)]
 
@@ -135,14 +137,16 @@ PRODUCTS = {"auto": 0, "combine": 1, "spmm": 2}
 
 def gplhr_create(A, B, sigma: complex, k: int, m: int, precond: str = "none",
                  block_size: int = 1, T=None, tol: float = 1e-8, maxit: int = 500,
-                 lock: bool = True, stream: int = 0, products: str = "auto"):
+                 lock: bool = True, stream: int = 0, products: str = "auto",
+                 precision: str = "fp64", switch_tol: float = 1e-5, stall_iters: int = 5):
     """Returns an opaque context handle (int).  A, B: SciPy CSR (B None = identity)."""
     L = lib()
     hA = _HostCsr(A)
     hB = _HostCsr(B) if B is not None else None
     hT = _HostCsr(T.astype(np.complex128)) if T is not None else None
     pc = Precond(PREC[precond], block_size, C.pointer(hT.desc) if hT else None)
-    opts = Opts(tol, maxit, 0, 0 if lock else 1, PRODUCTS[products], stream or None)
+    opts = Opts(tol, maxit, {"fp64": 0, "mixed": 1}[precision], 0 if lock else 1,
+                PRODUCTS[products], stream or None, switch_tol, stall_iters, 0)
     out = C.c_void_p()
     st = L.gplhr_create(C.byref(hA.desc), C.byref(hB.desc) if hB else None, sigma.real,
                         sigma.imag, k, m, C.byref(pc), C.byref(opts), C.byref(out))
@@ -284,10 +288,11 @@ class GPLHR:
     """Owning handle around a gplhr context (marshalling only)."""
 
     def __init__(self, A, B, sigma, k, m, precond="none", block_size=1, T=None, tol=1e-8,
-                 maxit=500, lock=True, stream=0, products="auto"):
+                 maxit=500, lock=True, stream=0, products="auto", precision="fp64",
+                 switch_tol=1e-5, stall_iters=5):
         self.n, self.k = A.shape[0], k
         self.ctx = gplhr_create(A, B, complex(sigma), k, m, precond, block_size, T, tol, maxit,
-                                lock, stream, products)
+                                lock, stream, products, precision, switch_tol, stall_iters)
 
     def solve(self, V0=None, seed=0, allow_notconv=False):
         return gplhr_solve(self.ctx, V0, seed, allow_notconv)

@@ -307,3 +307,63 @@ def test_full_size_sampled(cfg):
     ref = np.linalg.norm(E, axis=0) / ((np.abs(b) * OG.onenorm(pr.A)
                                         + np.abs(a) * OG.onenorm(pr.B)) * np.linalg.norm(X, axis=0))
     assert np.allclose(vec["resid"], ref, rtol=1e-6, atol=1e-15)
+
+
+# --------------------------------------------------------- mixed precision --
+
+def test_mixed_solve_schroedinger_small():
+    """GPLHR_MIXED: FP32 bulk phase, then FP64 refinement; the final answer meets the
+    same FP64 targets as the FP64 mode (eigenvalues vs the oracle, residuals <= tol)."""
+    pr = P.config3(24)
+    o = OG.solve(pr.A, None, pr.sigma, pr.start_block(), m=pr.m, tol=pr.tol, maxit=300,
+                 precond=pr.precond, block_size=pr.block_size)
+    with G.GPLHR(pr.A, None, pr.sigma, pr.k, pr.m, pr.precond, pr.block_size, tol=pr.tol,
+                 maxit=300, precision="mixed") as s:
+        info = s.solve(pr.start_block())
+        vec = s.vectors()
+    assert info.fp32_iters > 0 and info.bulk == 0
+    _compare_solutions(o, vec, pr.k, pr.tol)
+
+
+def test_mixed_solve_generalized_exact_preconditioner():
+    N = 6
+    A, B = P.convdiff3d(N, (0.4, 0.2, 0.1)), P.mass3d(N)
+    sigma = 300.0 + 40.0j
+    n, k = A.shape[0], 4
+    Tm = np.linalg.inv(A.toarray() - sigma * B.toarray())
+    V0 = P.start_block(n, k, 77)
+    from oracle.precond import Preconditioner
+    o = OG.solve(A, B, sigma, V0, m=1, tol=1e-10, maxit=100,
+                 T=Preconditioner("block_jacobi", blocks=[Tm], bs=n))
+    with G.GPLHR(A, B, sigma, k, 1, "csr", T=sp.csr_matrix(Tm), tol=1e-10, maxit=100,
+                 precision="mixed") as s:
+        info = s.solve(V0)
+        vec = s.vectors()
+    assert info.fp32_iters > 0
+    _compare_solutions(o, vec, k, 1e-10)
+
+
+@pytest.mark.parametrize("products", ["combine", "spmm"])
+def test_bulk_fp32_iterates_track_the_oracle(products):
+    """In the FP32 bulk phase the iterates follow the FP64 oracle's to FP32 accuracy:
+    Ritz values after each of 2 iterations agree to 1e-4 relative (u32 ~ 6e-8, times
+    the growth of two iterations on this non-normal pencil)."""
+    N = 8
+    A, B = P.convdiff3d(N, (0.4, 0.2, 0.1)), P.mass3d(N)
+    lmax = 21295.965461059128
+    sigma = complex(0.3 * lmax, 0.05 * lmax)
+    n, k, m = A.shape[0], 8, 1
+    V0 = P.start_block(n, k, 1002)
+    pen = OG.Pencil(A, B, sigma, oracle_precond(A, B, sigma, "block_jacobi", 8))
+    st = OG.init_state(pen, V0, m)
+    with G.GPLHR(A, B, sigma, k, m, "block_jacobi", 8, tol=1e-14, maxit=10, lock=False,
+                 products=products, precision="mixed", switch_tol=1e-30, stall_iters=-1) as s:
+        s.start(V0)
+        for it in range(2):
+            st = OG.iterate(pen, st)
+            info = s.iterate(1)
+            assert info.bulk == 1
+            vec = s.vectors()
+            lo = np.diag(st.RA) / np.diag(st.RB)
+            assert np.allclose(vec["lam"], lo, rtol=1e-4, atol=0), (it, vec["lam"], lo)
+            assert _angle(vec["V"], st.V) <= 1e-3
