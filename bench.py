@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision runs")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="arithmetic of the headline run (mixed: FP32 bulk phase held)")
     ap.add_argument("--grid", type=int, default=0,
                     help="grid side of a smaller copy of the generalized pencil (profiling captures); "
                          "its lambda_max is scaled from the 64^3 value by ((N+1)/65)^2")
@@ -208,7 +210,7 @@ def main():
             dist.barrier()
 
     stream = torch.cuda.Stream(device=dev)
-    run = timed_iterations(G, pr, K, W, stream, "fp64", barrier, local, world, dev)
+    run = timed_iterations(G, pr, K, W, stream, args.precision, barrier, local, world, dev)
     ms, per_class, clocks = run["ms"], run["per_class"], run["clocks"]
     total_launch = sum(v["launches"] for v in per_class.values())
     kern_ms = sum(v["ms"] for v in per_class.values())
@@ -239,8 +241,10 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "s/iteration", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-        "config": dict(workload_config(pr, args.workload), parallelism=f"replicas{world}"),
+        "vs_baseline": None, "dtype": "c128" if args.precision == "fp64" else "c64-bulk/c128",
+        "data": "synthetic",
+        "config": dict(workload_config(pr, args.workload), parallelism=f"replicas{world}",
+                       precision=args.precision),
         "roofline": roofline, "gpu_launches": total_launch,
         "kernels": {c: {"share": per_class[c]["ms"] / kern_ms if kern_ms else 0.0,
                         "ms_per_step": per_class[c]["ms"] / K,

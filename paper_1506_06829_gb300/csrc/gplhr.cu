@@ -33,6 +33,7 @@ struct DevCsr {
   int* rowptr = nullptr;
   int* col = nullptr;
   void* val = nullptr;
+  void* val32 = nullptr;  // FP32 copy of the values (mixed-precision mode)
   int dtype = GPLHR_R64;
   int64_t nnz = 0;
 };
@@ -54,6 +55,8 @@ struct gplhr_ctx {
   double normA = 1.0, normB = 1.0;
   int prec = GPLHR_PREC_NONE, bs = 1;
   double2* prec_data = nullptr;  // Jacobi diagonal or block-Jacobi inverse blocks
+  float2* prec32 = nullptr;      // FP32 copy of the block-Jacobi inverse blocks (mixed mode)
+  float2* X32 = nullptr;         // complex64 copy of a sparse product's input block (mixed mode)
   // options
   double tol = 1e-8;
   int maxit = 500;
@@ -163,9 +166,61 @@ void prof_end(gplhr_ctx* ctx, int h) {
 template <typename T>
 gplhr_status launch_spmm_t(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, Blk X, int w, Blk Y, Blk Y2);
 
+gplhr_status launch_spmm_f32(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, Blk X, int w, Blk Y, Blk Y2);
+
 gplhr_status launch_spmm_one(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, Blk X, int w, Blk Y, Blk Y2,
                              bool fp32 = false) {
-  return fp32 ? launch_spmm_t<float>(ctx, M, M2, X, w, Y, Y2) : launch_spmm_t<double>(ctx, M, M2, X, w, Y, Y2);
+  return fp32 ? launch_spmm_f32(ctx, M, M2, X, w, Y, Y2) : launch_spmm_t<double>(ctx, M, M2, X, w, Y, Y2);
+}
+
+// FP32 sparse products: the input block is converted to complex64 once (the
+// double -> float conversion runs on the FP64 pipe, and a gather touches each input
+// row once per nonzero), and the matrix values come from their FP32 copies.
+gplhr_status launch_spmm_f32(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, Blk X, int w, Blk Y, Blk Y2) {
+  if (!M.val32 || (M2 && !M2->val32) || !ctx->X32 || w > ctx->k) return launch_spmm_t<double>(ctx, M, M2, X, w, Y, Y2);
+  const int threads = 256;
+  const int grid = grid_for((size_t)ctx->n, threads / 32, ctx->num_sms * 16);
+  auto mat_cost = [&](const DevCsr& D, double& fl, double& by) {
+    const bool cplx = D.dtype == GPLHR_C128;
+    fl += (cplx ? 8.0 : 4.0) * (double)D.nnz * w;
+    by += (double)D.nnz * ((cplx ? 8.0 : 4.0) + 4.0) + 4.0 * (ctx->n + 1.0) + 16.0 * ctx->n * w;
+  };
+  double fl = 0.0, by = 16.0 * ctx->n * w + 8.0 * ctx->n * w;
+  mat_cost(M, fl, by);
+  if (M2) mat_cost(*M2, fl, by);
+  const int ph = prof_begin(ctx, KC_SPMM, fl, by, 2);
+  gplhr::to_c64_kernel<<<grid_for((size_t)ctx->n * w, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+      ctx->n, w, X.p, X.ld, ctx->X32);
+  gplhr::CsrDev<float> ar{M.rowptr, M.col, (const float*)M.val32};
+  gplhr::CsrDev<float2> ac{M.rowptr, M.col, (const float2*)M.val32};
+  const float2* X32 = ctx->X32;
+  if (!M2) {
+    gplhr::CsrDev<float> none{nullptr, nullptr, nullptr};
+    if (M.dtype == GPLHR_R64)
+      gplhr::spmm_kernel<float, float, float, float2><<<grid, threads, 0, ctx->stream>>>(
+          ctx->n, ar, none, 0, X32, w, w, Y.p, Y.ld, nullptr, 0);
+    else
+      gplhr::spmm_kernel<float2, float, float, float2><<<grid, threads, 0, ctx->stream>>>(
+          ctx->n, ac, none, 0, X32, w, w, Y.p, Y.ld, nullptr, 0);
+  } else {
+    gplhr::CsrDev<float> br{M2->rowptr, M2->col, (const float*)M2->val32};
+    gplhr::CsrDev<float2> bc{M2->rowptr, M2->col, (const float2*)M2->val32};
+    if (M.dtype == GPLHR_R64 && M2->dtype == GPLHR_R64)
+      gplhr::spmm_kernel<float, float, float, float2><<<grid, threads, 0, ctx->stream>>>(
+          ctx->n, ar, br, 1, X32, w, w, Y.p, Y.ld, Y2.p, Y2.ld);
+    else if (M.dtype == GPLHR_R64)
+      gplhr::spmm_kernel<float, float2, float, float2><<<grid, threads, 0, ctx->stream>>>(
+          ctx->n, ar, bc, 1, X32, w, w, Y.p, Y.ld, Y2.p, Y2.ld);
+    else if (M2->dtype == GPLHR_R64)
+      gplhr::spmm_kernel<float2, float, float, float2><<<grid, threads, 0, ctx->stream>>>(
+          ctx->n, ac, br, 1, X32, w, w, Y.p, Y.ld, Y2.p, Y2.ld);
+    else
+      gplhr::spmm_kernel<float2, float2, float, float2><<<grid, threads, 0, ctx->stream>>>(
+          ctx->n, ac, bc, 1, X32, w, w, Y.p, Y.ld, Y2.p, Y2.ld);
+  }
+  prof_end(ctx, ph);
+  CK(cudaGetLastError());
+  return GPLHR_OK;
 }
 
 template <typename T>
@@ -375,7 +430,10 @@ gplhr_status precond_apply_impl(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
       const int bpc = std::max(1, 1024 / (bs * w));
       const int grid = (nblocks + bpc - 1) / bpc;
       const size_t smem = (size_t)bpc * bs * w * sizeof(double2);
-      if (ctx->bulk32)
+      if (ctx->bulk32 && ctx->prec32)
+        gplhr::block_jacobi_kernel<float, float2><<<grid, gplhr::BJ_THREADS, smem, ctx->stream>>>(
+            n, bs, w, ctx->prec32, X.p, X.ld, Y.p, Y.ld, bpc);
+      else if (ctx->bulk32)
         gplhr::block_jacobi_kernel<float><<<grid, gplhr::BJ_THREADS, smem, ctx->stream>>>(
             n, bs, w, ctx->prec_data, X.p, X.ld, Y.p, Y.ld, bpc);
       else
@@ -929,14 +987,41 @@ gplhr_status setup_preconditioner(gplhr_ctx* ctx, const gplhr_precond* T) {
   return GPLHR_OK;
 }
 
+// FP32 copies used by the bulk phase of the mixed mode: matrix values, block-Jacobi
+// inverse blocks, and a complex64 staging block for the sparse products' input.
+gplhr_status to_fp32(gplhr_ctx* ctx, const void* src, size_t count, void** dst) {
+  std::vector<double> h(count);
+  std::vector<float> f(count);
+  CK(cudaMemcpy(h.data(), src, count * sizeof(double), cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < count; ++i) f[i] = (float)h[i];
+  CK(cudaMalloc(dst, std::max<size_t>(count, 1) * sizeof(float)));
+  CK(cudaMemcpy(*dst, f.data(), count * sizeof(float), cudaMemcpyHostToDevice));
+  return GPLHR_OK;
+}
+
+gplhr_status make_fp32_copies(gplhr_ctx* ctx) {
+  auto vals = [](const DevCsr& D) { return (size_t)D.nnz * (D.dtype == GPLHR_C128 ? 2 : 1); };
+  TRY(to_fp32(ctx, ctx->A.val, vals(ctx->A), &ctx->A.val32));
+  if (ctx->hasB) TRY(to_fp32(ctx, ctx->B.val, vals(ctx->B), &ctx->B.val32));
+  if (ctx->prec == GPLHR_PREC_CSR) TRY(to_fp32(ctx, ctx->Tcsr.val, vals(ctx->Tcsr), &ctx->Tcsr.val32));
+  if (ctx->prec == GPLHR_PREC_BLOCK_JACOBI) {
+    const size_t nb = (size_t)((ctx->n + ctx->bs - 1) / ctx->bs) * ctx->bs * ctx->bs;
+    void* p = nullptr;
+    TRY(to_fp32(ctx, ctx->prec_data, 2 * nb, &p));
+    ctx->prec32 = (float2*)p;
+  }
+  CK(cudaMalloc(&ctx->X32, (size_t)ctx->n * ctx->k * sizeof(float2)));
+  return GPLHR_OK;
+}
+
 void free_all(gplhr_ctx* c) {
   auto F = [](void* p) {
     if (p) cudaFree(p);
   };
-  F(c->A.rowptr); F(c->A.col); F(c->A.val);
-  F(c->B.rowptr); F(c->B.col); F(c->B.val);
-  F(c->Tcsr.rowptr); F(c->Tcsr.col); F(c->Tcsr.val);
-  F(c->prec_data);
+  F(c->A.rowptr); F(c->A.col); F(c->A.val); F(c->A.val32);
+  F(c->B.rowptr); F(c->B.col); F(c->B.val); F(c->B.val32);
+  F(c->Tcsr.rowptr); F(c->Tcsr.col); F(c->Tcsr.val); F(c->Tcsr.val32);
+  F(c->prec_data); F(c->prec32); F(c->X32);
   F(c->Z); F(c->AZ); F(c->BZ); F(c->U); F(c->Pb); F(c->APb); F(c->BPb);
   F(c->Rw); F(c->Tw1); F(c->Tw2); F(c->Tw3);
   F(c->dC1); F(c->dC2); F(c->dMBa); F(c->dMAa); F(c->dYR); F(c->dYL); F(c->dPhiPsi); F(c->dGram);
@@ -1010,6 +1095,8 @@ gplhr_status set_smem_limits(gplhr_ctx* ctx) {
   CK(cudaFuncSetAttribute(gplhr::chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::block_jacobi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::block_jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::block_jacobi_kernel<float, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          big));
   CK(cudaFuncSetAttribute(gplhr::invert_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   return GPLHR_OK;
 }
@@ -1171,6 +1258,7 @@ gplhr_status gplhr_create(const gplhr_csr* A, const gplhr_csr* B, double sigma_r
   if (ctx->hasB && (st = upload_csr(ctx, B, ctx->B, &ctx->normB)) != GPLHR_OK) return fail(st);
   if ((st = allocate(ctx)) != GPLHR_OK) return fail(st);
   if ((st = setup_preconditioner(ctx, T)) != GPLHR_OK) return fail(st);
+  if (ctx->mixed && (st = make_fp32_copies(ctx)) != GPLHR_OK) return fail(st);
   {
     // flops per block column: sparse products of one column vs an s-wide combination
     const double spmm = ((ctx->A.dtype == GPLHR_C128 ? 8.0 : 4.0) * ctx->A.nnz +

@@ -83,6 +83,9 @@ template <> __device__ __forceinline__ double2 to_t<double>(double2 v) { return 
 template <> __device__ __forceinline__ float2 to_t<float>(double2 v) {
   return make_float2((float)v.x, (float)v.y);
 }
+template <typename T> __device__ __forceinline__ cplx<T> to_t(float2 v);
+template <> __device__ __forceinline__ double2 to_t<double>(float2 v) { return make_double2(v.x, v.y); }
+template <> __device__ __forceinline__ float2 to_t<float>(float2 v) { return v; }
 __device__ __forceinline__ double2 to_d(double2 v) { return v; }
 __device__ __forceinline__ double2 to_d(float2 v) { return make_double2(v.x, v.y); }
 template <typename T> __device__ __forceinline__ cplx<T> czero() {
@@ -101,6 +104,15 @@ template <typename T> __device__ __forceinline__ cplx<T> mfma(double v, cplx<T> 
 template <typename T> __device__ __forceinline__ cplx<T> mfma(double2 v, cplx<T> x, cplx<T> acc) {
   return cfma(to_t<T>(v), x, acc);
 }
+template <typename T> __device__ __forceinline__ cplx<T> mfma(float v, cplx<T> x, cplx<T> acc) {
+  const T r = (T)v;
+  acc.x = fma(r, x.x, acc.x);
+  acc.y = fma(r, x.y, acc.y);
+  return acc;
+}
+template <typename T> __device__ __forceinline__ cplx<T> mfma(float2 v, cplx<T> x, cplx<T> acc) {
+  return cfma(to_t<T>(v), x, acc);
+}
 
 // ------------------------------------------------------------------- SpMM -----
 // Y = M X for up to two CSR matrices sharing the input block (A and B of the pencil).
@@ -115,30 +127,64 @@ struct CsrDev {
   const VT* val;
 };
 
-template <typename VT, typename T>
-__device__ __forceinline__ void spmm_row(const CsrDev<VT>& M, int r, const double2* __restrict__ X,
+__device__ __forceinline__ double shfl_val(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ float shfl_val(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ float2 shfl_val(float2 v, int src) {
+  v.x = __shfl_sync(0xffffffffu, v.x, src);
+  v.y = __shfl_sync(0xffffffffu, v.y, src);
+  return v;
+}
+__device__ __forceinline__ double2 shfl_val(double2 v, int src) {
+  v.x = __shfl_sync(0xffffffffu, v.x, src);
+  v.y = __shfl_sync(0xffffffffu, v.y, src);
+  return v;
+}
+template <typename VT> __device__ __forceinline__ VT zero_val();
+template <> __device__ __forceinline__ double zero_val<double>() { return 0.0; }
+template <> __device__ __forceinline__ double2 zero_val<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float zero_val<float>() { return 0.0f; }
+template <> __device__ __forceinline__ float2 zero_val<float2>() { return make_float2(0.0f, 0.0f); }
+
+// One CSR row times the block: the warp loads up to 32 (column, value) pairs of the
+// row with one coalesced access, then lane (slot, c) takes nonzero t + slot of each
+// group of nslot by shuffle and gathers X[col][c0 + c]; the gathers of consecutive
+// groups do not wait on index loads, and the loop is unrolled to keep several
+// 16*w-byte block rows in flight.  The slots are summed with xor-shuffles.
+template <typename VT, typename T, typename XT>
+__device__ __forceinline__ void spmm_row(const CsrDev<VT>& M, int r, const XT* __restrict__ X,
                                          int ldx, int c0, int cw, int wp, int lane,
                                          double2* __restrict__ Y, int ldy) {
   const int slot = lane / wp;
   const int nslot = 32 / wp;
   const int c = lane - slot * wp;
+  const bool colok = c < cw;
   cplx<T> acc = czero<T>();
   const int j0 = M.rowptr[r], j1 = M.rowptr[r + 1];
-  if (c < cw) {
-    for (int j = j0 + slot; j < j1; j += nslot) {
-      const VT v = M.val[j];
-      const int cc = M.col[j];
-      acc = mfma<T>(v, to_t<T>(X[(size_t)cc * ldx + c0 + c]), acc);
+  for (int base = j0; base < j1; base += 32) {
+    const int cnt = min(32, j1 - base);
+    int mycol = 0;
+    VT myval = zero_val<VT>();
+    if (lane < cnt) {
+      mycol = M.col[base + lane];
+      myval = M.val[base + lane];
+    }
+#pragma unroll 4
+    for (int t = 0; t < 32; t += nslot) {
+      if (t >= cnt) break;
+      const int src = t + slot;
+      const int cc = __shfl_sync(0xffffffffu, mycol, src & 31);
+      const VT v = shfl_val(myval, src & 31);
+      if (src < cnt && colok) acc = mfma<T>(v, to_t<T>(X[(size_t)cc * ldx + c0 + c]), acc);
     }
   }
   for (int off = wp; off < 32; off <<= 1) acc = cadd(acc, shfl_xor2(acc, off));
-  if (slot == 0 && c < cw) Y[(size_t)r * ldy + c0 + c] = to_d(acc);
+  if (slot == 0 && colok) Y[(size_t)r * ldy + c0 + c] = to_d(acc);
 }
 
 // T is the arithmetic (double, or float in the FP32 bulk phase); blocks stay complex128.
-template <typename VTA, typename VTB, typename T>
+template <typename VTA, typename VTB, typename T, typename XT = double2>
 __global__ void spmm_kernel(int n, CsrDev<VTA> A, CsrDev<VTB> B, int hasB,
-                            const double2* __restrict__ X, int ldx, int w,
+                            const XT* __restrict__ X, int ldx, int w,
                             double2* __restrict__ AX, int ldax, double2* __restrict__ BX, int ldbx) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -148,8 +194,8 @@ __global__ void spmm_kernel(int n, CsrDev<VTA> A, CsrDev<VTB> B, int hasB,
       const int cw = min(32, w - c0);
       int wp = 1;
       while (wp < cw) wp <<= 1;
-      spmm_row<VTA, T>(A, r, X, ldx, c0, cw, wp, lane, AX, ldax);
-      if (hasB) spmm_row<VTB, T>(B, r, X, ldx, c0, cw, wp, lane, BX, ldbx);
+      spmm_row<VTA, T, XT>(A, r, X, ldx, c0, cw, wp, lane, AX, ldax);
+      if (hasB) spmm_row<VTB, T, XT>(B, r, X, ldx, c0, cw, wp, lane, BX, ldbx);
     }
   }
 }
@@ -420,6 +466,17 @@ __global__ void copy_block_kernel(int n, int w, const double2* __restrict__ X, i
   }
 }
 
+// complex128 block -> complex64 block (ld = w), for the FP32 sparse products.
+__global__ void to_c64_kernel(int n, int w, const double2* __restrict__ X, int ldx, float2* __restrict__ Y) {
+  const size_t total = (size_t)n * w;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / w), c = (int)(e - (size_t)r * w);
+    const double2 v = X[(size_t)r * ldx + c];
+    Y[e] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
 // Real n x w (row-major, ld = w) to complex block.
 __global__ void real_to_complex_kernel(int n, int w, const double* __restrict__ X,
                                        double2* __restrict__ Y, int ldy) {
@@ -449,8 +506,8 @@ __global__ void jacobi_kernel(int n, int w, const double2* __restrict__ d, const
 // handles BJ_BLOCKS_PER_CTA consecutive blocks; X rows are staged in shared memory,
 // so Y may equal X.
 constexpr int BJ_THREADS = 256;
-template <typename T = double>
-__global__ void block_jacobi_kernel(int n, int bs, int w, const double2* __restrict__ Tinv,
+template <typename T = double, typename TT = double2>
+__global__ void block_jacobi_kernel(int n, int bs, int w, const TT* __restrict__ Tinv,
                                     const double2* __restrict__ X, int ldx,
                                     double2* __restrict__ Y, int ldy, int blocks_per_cta) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -473,7 +530,7 @@ __global__ void block_jacobi_kernel(int n, int bs, int w, const double2* __restr
     const int blk = rr / bs, i = rr - blk * bs;
     const int gb = b0 + blk;
     const int rows_in_blk = min(bs, n - gb * bs);
-    const double2* Tm = Tinv + (size_t)gb * bs * bs + (size_t)i * bs;
+    const TT* Tm = Tinv + (size_t)gb * bs * bs + (size_t)i * bs;
     C2 acc = czero<T>();
     const C2* xb = xs + (size_t)blk * bs * w;
     for (int j = 0; j < rows_in_blk; ++j) acc = cfma(to_t<T>(Tm[j]), xb[j * w + cc], acc);
