@@ -175,6 +175,24 @@ gplhr_status gplhr_vectors(gplhr_ctx* ctx, double* alpha, double* beta, double* 
                            void* X, void* V, void* Q, void* RA, void* RB, double* resid,
                            int32_t where);
 
+/* gplhr_grad -- gradient of a real loss of the k eigenvalues with respect to the stored
+ * values of A and B, on their CSR patterns (in the input order).  Uses the first-order
+ * perturbation of a simple eigenvalue (Sec. 2.1 gives the right and left Schur bases;
+ * the eigenvectors come from them):
+ *     d lambda_i = y_i^* (dA - lambda_i dB) x_i / (y_i^* B x_i),
+ * x_i the right eigenvector from `right` (solved on (A, B) at sigma) and y_i the left one
+ * from `left` (solved on (A^*, B^*) at conj(sigma), whose eigenvalues are conj(lambda));
+ * pairs are matched by nearest eigenvalue (EINVAL if a match is not unique within
+ * 1e-6 |lambda|).  G: 2k doubles on the host, G[2i] + i G[2i+1] = dL/dRe(lambda_i) +
+ * i dL/dIm(lambda_i), in the order gplhr_vectors reports for `right`.  Outputs
+ * dL/da for every stored entry of A (dA_vals, nnz(A) values) and of B (dB_vals, NULL if
+ * not wanted or B = I): doubles for a real matrix (the real part, i.e. the gradient
+ * with respect to real entries), interleaved complex (dL/dRe + i dL/dIm) for a complex
+ * one; host or device memory per `where`.  Both contexts must be on the current GPU,
+ * with equal n and k.  Errors: EINVAL, ENUMERIC (y^* B x = 0), ECUDA. */
+gplhr_status gplhr_grad(gplhr_ctx* right, gplhr_ctx* left, const double* G, void* dA_vals,
+                        void* dB_vals, int32_t where);
+
 /* gplhr_destroy -- free everything the context owns.  NULL is a no-op. */
 void gplhr_destroy(gplhr_ctx* ctx);
 

@@ -1304,6 +1304,28 @@ gplhr_status gplhr_solve(gplhr_ctx* ctx, const void* V0, int32_t V0_where, int32
   return GPLHR_OK;
 }
 
+namespace {
+// x_j = V z_j / ||V z_j|| (FP64) into ctx->Tw3 (n x k, ld = k); returns Ze normalised.
+gplhr_status eigvec_block(gplhr_ctx* ctx, SqMat* Ze_out) {
+  const int k = ctx->k;
+  SqMat Ze = gplhr::tri_eigvecs(ctx->RA, ctx->RB);
+  for (int j = 0; j < k; ++j) {
+    double zn = 0.0;
+    for (int i = 0; i < k; ++i) zn += std::norm(Ze(i, j));
+    zn = std::sqrt(zn);
+    for (int i = 0; i < k; ++i) Ze(i, j) /= zn;
+  }
+  double2* hz = ctx->h_small;
+  pack(hz, Ze, 0, k, 0, k);
+  TRY(upload(ctx, ctx->dC1, hz, k * k));
+  const Blk none{nullptr, 0};
+  TRY(combine(ctx, {In{blkZ(ctx, 0), k, ctx->dC1, kOne}}, Blk{ctx->Tw3, k}, k, false, nullptr, none, -1, -1, true,
+              0));
+  if (Ze_out) *Ze_out = Ze;
+  return GPLHR_OK;
+}
+}  // namespace
+
 gplhr_status gplhr_vectors(gplhr_ctx* ctx, double* alpha, double* beta, double* lambda, void* X, void* V,
                            void* Q, void* RA, void* RB, double* resid, int32_t where) {
   if (!ctx) return GPLHR_EINVAL;
@@ -1564,6 +1586,111 @@ gplhr_status gplhr_gram_noalloc(int64_t n, const void* X, int32_t ldx, int32_t w
     g_create_error = std::string("gplhr_gram_noalloc: launch: ") + cudaGetErrorString(e);
     return GPLHR_ECUDA;
   }
+  return GPLHR_OK;
+}
+
+gplhr_status gplhr_grad(gplhr_ctx* right, gplhr_ctx* left, const double* G, void* dA_vals, void* dB_vals,
+                        int32_t where) {
+  if (!right || !left || !G || (!dA_vals && !dB_vals)) {
+    g_create_error = "gplhr_grad: contexts, G and at least one output are required";
+    return GPLHR_EINVAL;
+  }
+  gplhr_ctx* ctx = right;
+  if (!right->started || !left->started || right->n != left->n || right->k != left->k ||
+      right->hasB != left->hasB || (dB_vals && !right->hasB)) {
+    ctx->err = "gplhr_grad: both contexts must be solved, with equal n, k and B kind (dB needs B != I)";
+    return GPLHR_EINVAL;
+  }
+  const int n = ctx->n, k = ctx->k;
+  // pair right lambda_i with the left eigenvalue mu_j ~ conj(lambda_i)
+  std::vector<cd> lam(k), mu(k);
+  for (int j = 0; j < k; ++j) {
+    lam[j] = right->RA(j, j) / right->RB(j, j);
+    mu[j] = left->RA(j, j) / left->RB(j, j);
+  }
+  std::vector<int> perm(k, -1);
+  for (int i = 0; i < k; ++i) {
+    int best = -1, nmatch = 0;
+    double bd = 1e300;
+    const double tol = 1e-6 * std::max(std::abs(lam[i]), 1e-300);
+    for (int j = 0; j < k; ++j) {
+      const double d = std::abs(std::conj(mu[j]) - lam[i]);
+      if (d <= tol) ++nmatch;
+      if (d < bd) { bd = d; best = j; }
+    }
+    if (bd > tol || nmatch != 1) {
+      ctx->err = "gplhr_grad: no unique left eigenvalue matches lambda_" + std::to_string(i);
+      return GPLHR_EINVAL;
+    }
+    perm[i] = best;
+  }
+  // right vectors X (right->Tw3), left vectors Y (left->Tw3), Y permuted into right->Tw2
+  TRY(eigvec_block(left, nullptr));
+  CK(cudaStreamSynchronize(left->stream));
+  TRY(eigvec_block(right, nullptr));
+  {
+    double2* hp = ctx->h_small + k * k;
+    for (int i = 0; i < k * k; ++i) hp[i] = make_double2(0.0, 0.0);
+    for (int i = 0; i < k; ++i) hp[perm[i] * k + i] = make_double2(1.0, 0.0);
+    TRY(upload(ctx, ctx->dC2, hp, k * k));
+    const Blk none{nullptr, 0};
+    TRY(combine(ctx, {In{Blk{left->Tw3, k}, k, ctx->dC2, kOne}}, Blk{ctx->Tw2, k}, k, false, nullptr, none, -1, -1,
+                true, 0));
+  }
+  const Blk X{ctx->Tw3, k}, Y{ctx->Tw2, k};
+  // d_i = y_i^* B x_i
+  Blk BX = X;
+  if (ctx->hasB) {
+    BX = Blk{ctx->Tw1, k};
+    TRY(launch_spmm_one(ctx, ctx->B, nullptr, X, k, BX, Blk{nullptr, 0}, false));
+  }
+  TRY(gram(ctx, Y, k, BX, k, Blk{nullptr, 0}, 0, ctx->dGram));
+  std::vector<double2> D(k * k);
+  CK(cudaMemcpyAsync(D.data(), ctx->dGram, k * k * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  double2* hc = ctx->h_small + 2 * k * k;
+  for (int i = 0; i < k; ++i) {
+    const cd d(D[i * k + i].x, D[i * k + i].y);
+    if (std::abs(d) == 0.0) {
+      ctx->err = "gplhr_grad: y_i^* B x_i = 0 (defective or badly paired eigenvalue)";
+      return GPLHR_ENUMERIC;
+    }
+    const cd a = cd(G[2 * i], G[2 * i + 1]) / std::conj(d);
+    hc[i] = d2(a);
+    hc[k + i] = d2(-std::conj(lam[i]) * a);
+  }
+  TRY(upload(ctx, ctx->dC1, hc, 2 * k));
+  auto scatter = [&](const DevCsr& M, const double2* coef, void* outp) -> gplhr_status {
+    const bool cplx = M.dtype == GPLHR_C128;
+    const size_t bytes = (size_t)M.nnz * (cplx ? 16 : 8);
+    void* dst = outp;
+    void* tmp = nullptr;
+    if (where != GPLHR_DEVICE) {
+      CK(cudaMalloc(&tmp, std::max<size_t>(bytes, 16)));
+      dst = tmp;
+    }
+    const int grid = grid_for((size_t)n, 8, ctx->num_sms * 16);
+    if (cplx)
+      gplhr::adjoint_scatter_kernel<double2><<<grid, 256, 0, ctx->stream>>>(n, M.rowptr, M.col, Y.p, Y.ld, X.p, X.ld,
+                                                                           k, coef, (double2*)dst);
+    else
+      gplhr::adjoint_scatter_kernel<double><<<grid, 256, 0, ctx->stream>>>(n, M.rowptr, M.col, Y.p, Y.ld, X.p, X.ld,
+                                                                          k, coef, (double*)dst);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && tmp) {
+      e = cudaMemcpyAsync(outp, tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    }
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) {
+      ctx->err = std::string("gplhr_grad: ") + cudaGetErrorString(e);
+      return GPLHR_ECUDA;
+    }
+    return GPLHR_OK;
+  };
+  if (dA_vals) TRY(scatter(ctx->A, ctx->dC1, dA_vals));
+  if (dB_vals) TRY(scatter(ctx->B, ctx->dC1 + k, dB_vals));
+  CK(cudaStreamSynchronize(ctx->stream));
   return GPLHR_OK;
 }
 

@@ -766,6 +766,36 @@ __global__ void chol_inv_kernel(int w, int64_t n, const double2* __restrict__ G,
   }
 }
 
+// ------------------------------------------------------------------ adjoint ----
+// Eigenvalue adjoint on the CSR pattern of a matrix M: for nonzero j = (p, q),
+//   out[j] = sum_i Y[p][i] conj(X[q][i]) coef[i]
+// (Y: left vectors, X: right vectors, paired by column; coef carries
+// G_i / conj(y_i^* B x_i), times -conj(lambda_i) for B).  OUT = double keeps the real
+// part (real matrices).  One warp per row, lanes over the row's nonzeros.
+__device__ __forceinline__ void store_out(double* o, double2 v) { *o = v.x; }
+__device__ __forceinline__ void store_out(double2* o, double2 v) { *o = v; }
+
+template <typename OUT>
+__global__ void adjoint_scatter_kernel(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                       const double2* __restrict__ Y, int ldy, const double2* __restrict__ X,
+                                       int ldx, int k, const double2* __restrict__ coef, OUT* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int p = warp; p < n; p += nwarps) {
+    const double2* yp = Y + (size_t)p * ldy;
+    for (int j = rowptr[p] + lane; j < rowptr[p + 1]; j += 32) {
+      const double2* xq = X + (size_t)col[j] * ldx;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int i = 0; i < k; ++i) {
+        const double2 t = cmul(yp[i], make_double2(xq[i].x, -xq[i].y));
+        acc = cfma(t, coef[i], acc);
+      }
+      store_out(out + j, acc);
+    }
+  }
+}
+
 // Counter-based Gaussian start block (used when no V0 is given): Box-Muller on
 // two uniforms from a 64-bit splitmix of (seed, element index).
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {

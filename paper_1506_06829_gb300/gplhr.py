@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5:
 EXPORTED = ["gplhr_create", "gplhr_solve", "gplhr_start", "gplhr_iterate", "gplhr_vectors",
             "gplhr_destroy", "gplhr_last_error", "gplhr_spmm", "gplhr_precond_apply",
             "gplhr_gram", "gplhr_orth", "gplhr_ordqz", "gplhr_mfactors", "gplhr_profile",
-            "gplhr_profile_read", "gplhr_gram_noalloc"]
+            "gplhr_profile_read", "gplhr_gram_noalloc", "gplhr_grad"]
 KCLASS = {"spmm": 0, "gram": 1, "combine": 2, "precond": 3, "chol": 4, "other": 5}
 
 
@@ -94,6 +94,7 @@ def lib():
     L.gplhr_mfactors.argtypes = [i32, dp, dp, dp, dp]
     L.gplhr_profile.argtypes = [vp, i32]
     L.gplhr_gram_noalloc.argtypes = [i64, vp, i32, i32, vp, i32, i32, vp, vp]
+    L.gplhr_grad.argtypes = [vp, vp, dp, vp, vp, i32]
     L.gplhr_profile_read.argtypes = [vp, i32, dp, C.POINTER(C.c_int64), dp, dp]
     for name in EXPORTED:
         f = getattr(L, name)
@@ -241,6 +242,17 @@ def gplhr_gram_noalloc(X, Y, Cout, stream: int = 0):
     _check(lib().gplhr_gram_noalloc(X.shape[0], X.data_ptr(), X.stride(0), X.shape[1],
                                     Y.data_ptr(), Y.stride(0), Y.shape[1], Cout.data_ptr(),
                                     stream or None), None)
+
+
+def gplhr_grad(right, left, G, dA=None, dB=None):
+    """dL/dA, dL/dB on the CSR patterns.  G: k complex (dL/dRe + i dL/dIm per eigenvalue).
+    dA / dB: numpy arrays (host) or torch tensors (device), real for a real matrix."""
+    g = np.ascontiguousarray(np.stack([np.real(G), np.imag(G)], axis=1).ravel(), dtype=np.float64)
+    outs = [x for x in (dA, dB) if x is not None]
+    on_dev = any(hasattr(x, "data_ptr") and x.is_cuda for x in outs)
+    ptr = lambda x: None if x is None else (x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data)
+    _check(lib().gplhr_grad(right, left, _dptr(g), ptr(dA), ptr(dB),
+                            GPLHR_DEVICE if on_dev else GPLHR_HOST), right)
 
 
 def gplhr_orth(ctx, X, Rinv=None):

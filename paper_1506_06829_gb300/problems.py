@@ -243,3 +243,61 @@ def csr_arrays(M: sp.csr_matrix):
     return (np.ascontiguousarray(M.indptr, dtype=np.int32),
             np.ascontiguousarray(M.indices, dtype=np.int32),
             np.ascontiguousarray(M.data))
+
+
+# ---------------------------------------------------------------------------
+# Differentiation workload: 2-D convection-diffusion with a per-edge field b_e
+# ---------------------------------------------------------------------------
+
+def edges2d(N: int):
+    """Interior edges (p, q = p + e_d) of the N x N grid, x edges first, then y edges."""
+    idx = np.arange(N * N).reshape(N, N)          # idx[j, i] = i + N j
+    ex = np.stack([idx[:, :-1].ravel(), idx[:, 1:].ravel()], axis=1)
+    ey = np.stack([idx[:-1, :].ravel(), idx[1:, :].ravel()], axis=1)
+    return np.concatenate([ex, ey], axis=0)
+
+
+def convdiff2d_edges(N: int, b: np.ndarray) -> sp.csr_matrix:
+    """5-point -Laplacian (4/h^2 diagonal, -1/h^2 neighbours, h = 1/(N+1)) plus a
+    central-difference convection term per interior edge e = (p, q): +b_e/(2h) at (p, q)
+    and -b_e/(2h) at (q, p).  Linear in b: A(b) = L + sum_e b_e E_e."""
+    h = 1.0 / (N + 1)
+    L = neg_laplacian2d(N, h)
+    E = edges2d(N)
+    c = b / (2.0 * h)
+    C = sp.coo_matrix((np.concatenate([c, -c]), (np.concatenate([E[:, 0], E[:, 1]]),
+                                                 np.concatenate([E[:, 1], E[:, 0]]))),
+                      shape=L.shape)
+    return _csr(L + C)
+
+
+def edge_jacobian(N: int, A: sp.csr_matrix) -> sp.csr_matrix:
+    """J (nnz(A) x n_edges) with dA.data / db = J: entry (p, q) of edge e gets +1/(2h),
+    entry (q, p) gets -1/(2h).  Maps a gradient on A's CSR values to one on b."""
+    h = 1.0 / (N + 1)
+    E = edges2d(N)
+    A = sp.csr_matrix(A)
+    pos = {}
+    for p in range(A.shape[0]):
+        for j in range(A.indptr[p], A.indptr[p + 1]):
+            pos[(p, int(A.indices[j]))] = j
+    rows, cols, vals = [], [], []
+    for e, (p, q) in enumerate(E):
+        rows += [pos[(int(p), int(q))], pos[(int(q), int(p))]]
+        cols += [e, e]
+        vals += [1.0 / (2.0 * h), -1.0 / (2.0 * h)]
+    return sp.csr_matrix((vals, (rows, cols)), shape=(A.nnz, E.shape[0]))
+
+
+def config5(N: int = 256) -> Problem:
+    """Per-edge convection field b_e ~ U[0.2, 0.6] (seed 1005) on the N x N 5-point
+    operator (n = 65536 at N = 256), B = I, k = 8 nearest sigma = 4/h^2 (the centre of
+    the spectrum), m = 1, FP64; gradient of sum Re(lambda_i) w.r.t. b."""
+    E = edges2d(N)
+    rng = np.random.default_rng(1005)
+    b = rng.uniform(0.2, 0.6, size=E.shape[0])
+    A = convdiff2d_edges(N, b)
+    h = 1.0 / (N + 1)
+    return Problem(f"convdiff2d_edges_{N}x{N}", A, None, complex(4.0 / (h * h), 0.0), k=8, m=1,
+                   precond="jacobi", block_size=1, tol=1e-8, seed=1005,
+                   meta={"N": N, "b": b})

@@ -1,0 +1,109 @@
+"""GPU parity of the eigenvalue adjoint (gplhr_grad) against the CPU oracle's adjoint,
+and of the torch.autograd path against finite differences.
+
+Tolerance: the adjoint is linear in x_i and y_i, which both solves deliver to their
+residual tolerance (1e-11 here) times the eigenvector condition; 1e-7 relative on the
+whole gradient vector is well above that and far below any formula error (a wrong sign,
+conjugation or index changes the result by O(1))."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+torch = pytest.importorskip("torch")
+
+from oracle.grad import eig_grad
+from paper_1506_06829_gb300 import gplhr as G
+from paper_1506_06829_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _dense_pairs(A, B, sigma, k):
+    Ad = A.toarray()
+    Bd = None if B is None else B.toarray()
+    w, vl, vr = sla.eig(Ad, Bd, left=True, right=True) if Bd is not None else sla.eig(Ad, left=True, right=True)
+    idx = np.argsort(np.abs(w - sigma))[:k]
+    return w[idx], vr[:, idx], vl[:, idx]
+
+
+def _exact_T(A, B, sigma):
+    n = A.shape[0]
+    Bd = np.eye(n) if B is None else B.toarray()
+    return sp.csr_matrix(np.linalg.inv(A.toarray() - sigma * Bd))
+
+
+@pytest.mark.parametrize("case", ["edges_real_B_I", "generalized_real", "complex_A"])
+def test_gplhr_grad_matches_oracle_adjoint(case):
+    if case == "edges_real_B_I":
+        pr = P.config5(8)
+        A, B, sigma, k = pr.A, None, pr.sigma + 3.0, 4
+    elif case == "generalized_real":
+        A, B = P.convdiff3d(6, (0.4, 0.2, 0.1)), P.mass3d(6)
+        sigma, k = 300.0 + 40.0j, 4
+    else:
+        A, B = P.schroedinger2d(10, 0.3), None
+        sigma, k = -2.0 - 0.5j, 5
+    n = A.shape[0]
+    V0 = P.start_block(n, k, 9)
+    AH = sp.csr_matrix(A.conj().T)
+    BH = None if B is None else sp.csr_matrix(B.conj().T)
+    with G.GPLHR(A, B, sigma, k, 1, "csr", T=_exact_T(A, B, sigma), tol=1e-11, maxit=100) as r, \
+         G.GPLHR(AH, BH, np.conj(sigma), k, 1, "csr", T=_exact_T(AH, BH, np.conj(sigma)), tol=1e-11,
+                 maxit=100) as l:
+        r.solve(V0)
+        l.solve(V0)
+        lam = r.vectors()["lam"]
+        Gv = np.linspace(1.0, 2.0, k) + 1j * np.linspace(-0.5, 0.5, k)
+        cplx = np.iscomplexobj(A.data)
+        dA = np.zeros(A.nnz, dtype=np.complex128 if cplx else np.float64)
+        dB = None if B is None else np.zeros(B.nnz)
+        G.gplhr_grad(r.ctx, l.ctx, Gv, dA, dB)
+        # device outputs as well
+        dA_dev = torch.zeros(A.nnz, dtype=torch.complex128 if cplx else torch.float64, device="cuda:0")
+        G.gplhr_grad(r.ctx, l.ctx, Gv, dA_dev, None)
+    lam_d, X, Y = _dense_pairs(A, B, sigma, k)
+    order = [int(np.argmin(np.abs(lam_d - l_))) for l_ in lam]
+    refA, refB = eig_grad(A, B, lam, X[:, order], Y[:, order], Gv)
+    assert np.linalg.norm(dA - refA) <= 1e-7 * np.linalg.norm(refA)
+    assert np.linalg.norm(dA_dev.cpu().numpy() - refA) <= 1e-7 * np.linalg.norm(refA)
+    if B is not None:
+        assert np.linalg.norm(dB - refB) <= 1e-7 * np.linalg.norm(refB)
+
+
+def test_autograd_edge_field_against_finite_differences():
+    """torch.autograd path on the per-edge field of an 8 x 8 copy of the differentiation
+    workload: d(sum Re lambda)/db against central differences (step 1e-6) on 12 edges."""
+    from paper_1506_06829_gb300.autograd import eigenvalues
+    N, k = 8, 4
+    pr = P.config5(N)
+    b = pr.meta["b"]
+    sigma = pr.sigma + 3.0
+    J = P.edge_jacobian(N, pr.A)
+    pattern = (pr.A.indptr, pr.A.indices, pr.n)
+    T = _exact_T(pr.A, None, sigma)
+    bt = torch.tensor(b, dtype=torch.float64, requires_grad=True)
+    Jt = torch.tensor(J.toarray())
+    L0 = torch.tensor(P.convdiff2d_edges(N, np.zeros_like(b)).data)   # b-independent part
+    for recompute in (False, True):
+        vals = L0 + Jt @ bt
+        lam = eigenvalues(vals, pattern, sigma, k, 1, precond="csr", T=T, tol=1e-11, maxit=100,
+                          recompute=recompute)
+        loss = lam.real.sum()
+        g, = torch.autograd.grad(loss, bt)
+        delta = 1e-6
+        for e in [0, 3, 11, 20, 33, 47, 55, 60, 71, 90, 101, 111]:
+            def L(bb):
+                ev = sla.eigvals(P.convdiff2d_edges(N, bb).toarray())
+                return np.sort(ev[np.argsort(np.abs(ev - sigma))[:k]].real).sum()
+            bp, bm = b.copy(), b.copy()
+            bp[e] += delta
+            bm[e] -= delta
+            fd = (L(bp) - L(bm)) / (2 * delta)
+            assert abs(g[e].item() - fd) <= 1e-5 * max(1.0, abs(fd)), (e, g[e].item(), fd)
