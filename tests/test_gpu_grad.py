@@ -48,8 +48,13 @@ def test_gplhr_grad_matches_oracle_adjoint(case):
         A, B = P.convdiff3d(6, (0.4, 0.2, 0.1)), P.mass3d(6)
         sigma, k = 300.0 + 40.0j, 4
     else:
-        A, B = P.schroedinger2d(10, 0.3), None
-        sigma, k = -2.0 - 0.5j, 5
+        # complex-scaled Schroedinger plus a seeded complex diagonal: the square's symmetry
+        # would otherwise give exact double eigenvalues, whose individual derivatives do
+        # not exist (gplhr_grad refuses them)
+        rng = np.random.default_rng(4)
+        A0 = P.schroedinger2d(10, 0.3)
+        A = sp.csr_matrix(A0 + sp.diags(rng.uniform(-2, 2, A0.shape[0]) + 1j * rng.uniform(-1, 1, A0.shape[0])))
+        B, sigma, k = None, -2.0 - 0.5j, 5
     n = A.shape[0]
     V0 = P.start_block(n, k, 9)
     AH = sp.csr_matrix(A.conj().T)
@@ -107,3 +112,18 @@ def test_autograd_edge_field_against_finite_differences():
             bm[e] -= delta
             fd = (L(bp) - L(bm)) / (2 * delta)
             assert abs(g[e].item() - fd) <= 1e-5 * max(1.0, abs(fd)), (e, g[e].item(), fd)
+
+
+def test_gplhr_grad_refuses_a_degenerate_eigenvalue():
+    """Exact double eigenvalues (square-domain symmetry): no unique left/right pairing."""
+    A = P.schroedinger2d(10, 0.3)
+    n, k = A.shape[0], 4
+    AH = sp.csr_matrix(A.conj().T)
+    V0 = P.start_block(n, k, 9)
+    with G.GPLHR(A, None, -2.0 - 0.5j, k, 1, "csr", T=_exact_T(A, None, -2.0 - 0.5j), tol=1e-11) as r, \
+         G.GPLHR(AH, None, -2.0 + 0.5j, k, 1, "csr", T=_exact_T(AH, None, -2.0 + 0.5j), tol=1e-11) as l:
+        r.solve(V0)
+        l.solve(V0)
+        with pytest.raises(G.GplhrError) as e:
+            G.gplhr_grad(r.ctx, l.ctx, np.ones(k, dtype=complex), np.zeros(A.nnz, dtype=complex))
+        assert e.value.status == G.GPLHR_EINVAL
