@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision runs")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload run")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="arithmetic of the headline run (mixed: FP32 bulk phase held)")
     ap.add_argument("--grid", type=int, default=0,
@@ -266,6 +267,8 @@ def main():
 
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e(pr, K, stream, G)
+    if rank == 0 and not args.no_batched:
+        line["batched"] = batched_throughput(G, K)
     if rank == 0 and not args.no_solve:
         line["solve"] = time_to_pairs(G, stream, "fp64")
         if not args.no_mixed:
@@ -347,6 +350,38 @@ def e2e(pr, K, stream, G):
             "h2d_bytes_per_step": (csr_bytes + V0.nbytes + info.h2d_bytes) / K,
             "d2h_bytes_per_step": (out_bytes + info.d2h_bytes) / K,
             "iterations": info.iters}
+
+
+def batched_throughput(G, K):
+    """Batched workload (64 pencils of uneven size + 16 shifts over a 128^2 pencil): K
+    iterations of every context, concurrently (one stream per context, a host thread
+    pool) and one context at a time; pencil-iterations per second of each."""
+    import torch
+    from paper_1506_06829_gb300 import problems as P
+    ps = P.config4()
+    solvers = [G.GPLHR(p.A, p.B, p.sigma, p.k, p.m, p.precond, p.block_size, tol=p.tol, maxit=10 ** 6)
+               for p in ps]
+    for s, p in zip(solvers, ps):
+        s.start(p.start_block())
+    ctxs = [s.ctx for s in solvers]
+    G.gplhr_iterate_batched(ctxs, 2)                  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, infos, _ = G.gplhr_iterate_batched(ctxs, K)
+    torch.cuda.synchronize()
+    t_batched = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    G.gplhr_iterate_batched(ctxs, K, nthreads=1)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    for s in solvers:
+        s.close()
+    units = len(ps) * K
+    return {"workload": f"{len(ps)} contexts: 64 convection-diffusion pencils (grid sides 16..96, B = MxM, k = 4) "
+                        "+ 16 shifts over a 128^2 pencil (k = 8), Jacobi, FP64",
+            "pencil_iterations_per_s": units / t_batched, "sequential_pencil_iterations_per_s": units / t_seq,
+            "speedup_vs_sequential": t_seq / t_batched, "threads": os.cpu_count(), "iterations": K,
+            "status": int(st)}
 
 
 def time_to_pairs(G, stream, precision):

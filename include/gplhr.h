@@ -193,6 +193,22 @@ gplhr_status gplhr_vectors(gplhr_ctx* ctx, double* alpha, double* beta, double* 
 gplhr_status gplhr_grad(gplhr_ctx* right, gplhr_ctx* left, const double* G, void* dA_vals,
                         void* dB_vals, int32_t where);
 
+/* Batched solves (many pencils of uneven size, or many shifts over one pencil, each in
+ * its own context).  The contexts are independent: each has its own stream and
+ * buffers; a pool of nthreads host threads (<= 0: the host's hardware threads) runs
+ * them concurrently, so the host QZ and synchronisations of one pencil overlap the
+ * device work of the others.  Arguments are arrays of nctx entries (V0, V0_where,
+ * is_complex, seeds, infos may be NULL: then gplhr_solve's defaults); statuses
+ * (may be NULL) receives each context's status.  Returns GPLHR_OK if every context
+ * succeeded, else the first failing status in context order.  A context must not
+ * appear twice.  gplhr_iterate_batched runs niter iterations of each started context. */
+gplhr_status gplhr_solve_batched(int32_t nctx, gplhr_ctx* const* ctxs, const void* const* V0,
+                                 const int32_t* V0_where, const int32_t* is_complex,
+                                 const uint64_t* seeds, gplhr_info* infos,
+                                 gplhr_status* statuses, int32_t nthreads);
+gplhr_status gplhr_iterate_batched(int32_t nctx, gplhr_ctx* const* ctxs, int32_t niter,
+                                   gplhr_info* infos, gplhr_status* statuses, int32_t nthreads);
+
 /* gplhr_destroy -- free everything the context owns.  NULL is a no-op. */
 void gplhr_destroy(gplhr_ctx* ctx);
 

@@ -9,13 +9,16 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <cmath>
+#include <atomic>
 #include <climits>
+#include <cmath>
 #include <complex>
 #include <cstdio>
-#include <mutex>
 #include <cstring>
+#include <functional>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/gplhr.h"
@@ -1692,6 +1695,52 @@ gplhr_status gplhr_grad(gplhr_ctx* right, gplhr_ctx* left, const double* G, void
   if (dB_vals) TRY(scatter(ctx->B, ctx->dC1 + k, dB_vals));
   CK(cudaStreamSynchronize(ctx->stream));
   return GPLHR_OK;
+}
+
+// Batched driver: contexts are independent (own streams and buffers); a pool of host
+// threads takes them one at a time, so the host QZ and synchronisation of one pencil
+// overlap the device work of the others.
+static gplhr_status run_batched(int32_t nctx, gplhr_ctx* const* ctxs, int32_t nthreads, gplhr_status* statuses,
+                                const std::function<gplhr_status(int)>& job) {
+  if (nctx < 0 || (nctx > 0 && !ctxs)) return GPLHR_EINVAL;
+  for (int i = 0; i < nctx; ++i)
+    if (!ctxs[i]) return GPLHR_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GPLHR_ECUDA;
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nt = std::max(1, std::min<int>(nthreads > 0 ? nthreads : hw, nctx));
+  std::vector<gplhr_status> st(nctx, GPLHR_OK);
+  std::atomic<int> next(0);
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (int i = next.fetch_add(1); i < nctx; i = next.fetch_add(1)) st[i] = job(i);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& th : pool) th.join();
+  gplhr_status first = GPLHR_OK;
+  for (int i = 0; i < nctx; ++i) {
+    if (statuses) statuses[i] = st[i];
+    if (first == GPLHR_OK && st[i] != GPLHR_OK) first = st[i];
+  }
+  return first;
+}
+
+gplhr_status gplhr_iterate_batched(int32_t nctx, gplhr_ctx* const* ctxs, int32_t niter, gplhr_info* infos,
+                                   gplhr_status* statuses, int32_t nthreads) {
+  return run_batched(nctx, ctxs, nthreads, statuses, [&](int i) {
+    return gplhr_iterate(ctxs[i], niter, infos ? infos + i : nullptr);
+  });
+}
+
+gplhr_status gplhr_solve_batched(int32_t nctx, gplhr_ctx* const* ctxs, const void* const* V0,
+                                 const int32_t* V0_where, const int32_t* is_complex, const uint64_t* seeds,
+                                 gplhr_info* infos, gplhr_status* statuses, int32_t nthreads) {
+  return run_batched(nctx, ctxs, nthreads, statuses, [&](int i) {
+    return gplhr_solve(ctxs[i], V0 ? V0[i] : nullptr, V0_where ? V0_where[i] : GPLHR_HOST,
+                       is_complex ? is_complex[i] : 0, seeds ? seeds[i] : 0, infos ? infos + i : nullptr);
+  });
 }
 
 gplhr_status gplhr_ordqz(int32_t s, const double* Phi, const double* Psi, double sigma_re, double sigma_im,

@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5:
 EXPORTED = ["gplhr_create", "gplhr_solve", "gplhr_start", "gplhr_iterate", "gplhr_vectors",
             "gplhr_destroy", "gplhr_last_error", "gplhr_spmm", "gplhr_precond_apply",
             "gplhr_gram", "gplhr_orth", "gplhr_ordqz", "gplhr_mfactors", "gplhr_profile",
-            "gplhr_profile_read", "gplhr_gram_noalloc", "gplhr_grad"]
+            "gplhr_profile_read", "gplhr_gram_noalloc", "gplhr_grad", "gplhr_solve_batched",
+            "gplhr_iterate_batched"]
 KCLASS = {"spmm": 0, "gram": 1, "combine": 2, "precond": 3, "chol": 4, "other": 5}
 
 
@@ -95,6 +96,11 @@ def lib():
     L.gplhr_profile.argtypes = [vp, i32]
     L.gplhr_gram_noalloc.argtypes = [i64, vp, i32, i32, vp, i32, i32, vp, vp]
     L.gplhr_grad.argtypes = [vp, vp, dp, vp, vp, i32]
+    L.gplhr_solve_batched.argtypes = [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(i32),
+                                      C.POINTER(i32), C.POINTER(u64), C.POINTER(Info),
+                                      C.POINTER(C.c_int), i32]
+    L.gplhr_iterate_batched.argtypes = [i32, C.POINTER(vp), i32, C.POINTER(Info),
+                                        C.POINTER(C.c_int), i32]
     L.gplhr_profile_read.argtypes = [vp, i32, dp, C.POINTER(C.c_int64), dp, dp]
     for name in EXPORTED:
         f = getattr(L, name)
@@ -253,6 +259,41 @@ def gplhr_grad(right, left, G, dA=None, dB=None):
     ptr = lambda x: None if x is None else (x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data)
     _check(lib().gplhr_grad(right, left, _dptr(g), ptr(dA), ptr(dB),
                             GPLHR_DEVICE if on_dev else GPLHR_HOST), right)
+
+
+def gplhr_solve_batched(ctxs, V0s=None, nthreads: int = 0):
+    """Solve every context concurrently.  V0s: list of host arrays (or None).
+    Returns (overall status, [Info], [status])."""
+    n = len(ctxs)
+    cs = (C.c_void_p * n)(*ctxs)
+    keep = []
+    if V0s is not None:
+        ptrs, where, cplx = [], [], []
+        for v in V0s:
+            p, w, c, k = _v0_args(v)
+            keep.append(k)
+            ptrs.append(p)
+            where.append(w)
+            cplx.append(c)
+        vp_arr = (C.c_void_p * n)(*ptrs)
+        w_arr = (C.c_int32 * n)(*where)
+        c_arr = (C.c_int32 * n)(*cplx)
+    else:
+        vp_arr = w_arr = c_arr = None
+    infos = (Info * n)()
+    sts = (C.c_int * n)()
+    st = lib().gplhr_solve_batched(n, cs, vp_arr, w_arr, c_arr, None, infos, sts, nthreads)
+    del keep
+    return st, list(infos), list(sts)
+
+
+def gplhr_iterate_batched(ctxs, niter: int, nthreads: int = 0):
+    n = len(ctxs)
+    cs = (C.c_void_p * n)(*ctxs)
+    infos = (Info * n)()
+    sts = (C.c_int * n)()
+    st = lib().gplhr_iterate_batched(n, cs, niter, infos, sts, nthreads)
+    return st, list(infos), list(sts)
 
 
 def gplhr_orth(ctx, X, Rinv=None):

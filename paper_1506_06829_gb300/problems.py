@@ -301,3 +301,54 @@ def config5(N: int = 256) -> Problem:
     return Problem(f"convdiff2d_edges_{N}x{N}", A, None, complex(4.0 / (h * h), 0.0), k=8, m=1,
                    precond="jacobi", block_size=1, tol=1e-8, seed=1005,
                    meta={"N": N, "b": b})
+
+
+# ---------------------------------------------------------------------------
+# Batched workload: many convection-diffusion pencils, and shifts over one pencil
+# ---------------------------------------------------------------------------
+
+def convdiff2d_mass(N: int, gx: float, gy: float):
+    """(A, B): 5-point convection-diffusion and the 2-D mass matrix M x M (9-point)."""
+    M = mass_1d(N)
+    return convdiff2d(N, gx, gy), _csr(kron_prod([M, M]))
+
+
+def separable_interval(N: int, gx: float, gy: float):
+    """Real spectral interval of the separable approximation (mu_x + mu_y)/(nu_x nu_y),
+    mu = (2 - 2 sqrt(1-g^2) cos t)/h^2, nu = (2 + cos t)/3, t = j pi h: exact when the
+    pencil's 1-D factors share eigenvectors (gamma = 0), an approximation otherwise."""
+    h = 1.0 / (N + 1)
+    t = np.arange(1, N + 1) * math.pi * h
+    mux = (2 - 2 * math.sqrt(1 - gx * gx) * np.cos(t)) / (h * h)
+    muy = (2 - 2 * math.sqrt(1 - gy * gy) * np.cos(t)) / (h * h)
+    nu = (2 + np.cos(t)) / 3
+    lam = (mux[:, None] + muy[None, :]) / (nu[:, None] * nu[None, :])
+    return float(lam.min()), float(lam.max())
+
+
+def config4(n_pencils: int = 64, slice_grid: int = 128, n_slices: int = 16):
+    """64 independent pencils (convection-diffusion, B = M x M) with grid sides drawn
+    uniformly from 16..96 and gamma_x, gamma_y ~ U[0.1, 0.9] (seed 1004), k = 4 each,
+    sigma at the midpoint of the separable approximation's real interval; plus one
+    128 x 128 pencil sliced by 16 shifts at the centres of 16 equal sub-intervals of that
+    interval, k = 8 per shift.  m = 1, Jacobi on A - sigma B, tol 1e-8."""
+    rng = np.random.default_rng(1004)
+    sides = rng.integers(16, 97, size=n_pencils)
+    gam = rng.uniform(0.1, 0.9, size=(n_pencils, 2))
+    out = []
+    for i in range(n_pencils):
+        N = int(sides[i])
+        A, B = convdiff2d_mass(N, gam[i, 0], gam[i, 1])
+        lo, hi = separable_interval(N, gam[i, 0], gam[i, 1])
+        out.append(Problem(f"pencil{i}_{N}x{N}", A, B, complex(0.5 * (lo + hi), 0.0), k=4, m=1,
+                           precond="jacobi", block_size=1, tol=1e-8, seed=1004 + 1 + i,
+                           meta={"N": N, "gamma": tuple(gam[i])}))
+    gx, gy = rng.uniform(0.1, 0.9, size=2)
+    A, B = convdiff2d_mass(slice_grid, gx, gy)
+    lo, hi = separable_interval(slice_grid, gx, gy)
+    for s in range(n_slices):
+        sig = lo + (s + 0.5) * (hi - lo) / n_slices
+        out.append(Problem(f"slice{s}_{slice_grid}x{slice_grid}", A, B, complex(sig, 0.0), k=8, m=1,
+                           precond="jacobi", block_size=1, tol=1e-8, seed=2004 + s,
+                           meta={"N": slice_grid, "gamma": (gx, gy), "slice": s}))
+    return out
