@@ -233,9 +233,15 @@ gplhr_status gplhr_precond_apply(gplhr_ctx* ctx, const void* X, int32_t ldx, int
                                  void* Y, int32_t ldy);
 
 /* Gram product C = X^* Y (w_x x w_y, row-major, ld = w_y) over all n rows: the
- * projections and the projected pencil U^* A Z, U^* B Z (Alg. 2 steps 8, 15, 19-24). */
+ * projections and the projected pencil U^* A Z, U^* B Z (Alg. 2 steps 8, 15, 19-24).
+ * arith: GPLHR_GRAM_FP64 (0) DFMA; GPLHR_GRAM_FP32 (1) FP32 arithmetic (the projection
+ * coefficients of the mixed mode's bulk phase); GPLHR_GRAM_EXACT32 (2) inputs rounded
+ * to FP32, every product formed exactly on the FP32 pipe and summed with compensation
+ * into FP64 (the Cholesky-QR Grams and pencil of the bulk phase, whose blocks hold
+ * FP32 values). */
+enum { GPLHR_GRAM_FP64 = 0, GPLHR_GRAM_FP32 = 1, GPLHR_GRAM_EXACT32 = 2 };
 gplhr_status gplhr_gram(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t wx, const void* Y,
-                        int32_t ldy, int32_t wy, void* C);
+                        int32_t ldy, int32_t wy, void* C, int32_t arith);
 
 /* orth(X) in place (Alg. 1 footnote): X <- X R^{-1} with X = Q R the thin QR whose R
  * has a real positive diagonal, by Cholesky QR applied twice (a shifted Cholesky

@@ -282,8 +282,11 @@ gplhr_status spmm_AB(gplhr_ctx* ctx, Blk X, int w, Blk AX, Blk BX) {
 // triangle is computed; the lower one is filled by conjugation).
 template <int ACC>
 void launch_gram_acc(gplhr_ctx* ctx, dim3 grid, size_t smem, int rows, Blk X, int wx, Blk Y0, int wy0,
-                     Blk Y1, int wy1, int herm, int nout, int G, int RG, const int* skip, bool fp32) {
-  if (fp32)
+                     Blk Y1, int wy1, int herm, int nout, int G, int RG, const int* skip, int mode) {
+  if (mode == 2)
+    gplhr::gram_partial_x32_kernel<ACC><<<grid, gplhr::GRAM_THREADS, smem, ctx->stream>>>(
+        ctx->n, rows, X.p, X.ld, wx, Y0.p, Y0.ld, wy0, Y1.p, Y1.ld, wy1, herm, nout, G, RG, ctx->gram_part, skip);
+  else if (mode == 1)
     gplhr::gram_partial_kernel<ACC, float><<<grid, gplhr::GRAM_THREADS, smem, ctx->stream>>>(
         ctx->n, rows, X.p, X.ld, wx, Y0.p, Y0.ld, wy0, Y1.p, Y1.ld, wy1, herm, nout, G, RG, ctx->gram_part, skip);
   else
@@ -291,8 +294,13 @@ void launch_gram_acc(gplhr_ctx* ctx, dim3 grid, size_t smem, int rows, Blk X, in
         ctx->n, rows, X.p, X.ld, wx, Y0.p, Y0.ld, wy0, Y1.p, Y1.ld, wy1, herm, nout, G, RG, ctx->gram_part, skip);
 }
 
+// fp32: FP32 arithmetic (projection coefficients in the bulk phase).  Otherwise an
+// FP64-accurate Gram: DFMA, or in the bulk phase (FP32-valued blocks) exact products
+// on the FP32 pipe with compensated accumulation (gram_partial_x32_kernel).
 gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy1, double2* C,
-                  const int* skip = nullptr, bool herm = false, bool count = true, bool fp32 = false) {
+                  const int* skip = nullptr, bool herm = false, bool count = true, bool fp32 = false,
+                  int force_mode = -1) {
+  const int mode = force_mode >= 0 ? force_mode : (fp32 ? 1 : (ctx->bulk32 ? 2 : 0));
   const int wy = wy0 + wy1;
   if (herm && (wy1 != 0 || wy0 != wx)) herm = false;
   const int nout = herm ? wx * (wx + 1) / 2 : wx * wy;
@@ -317,10 +325,10 @@ gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy
   const double by = 16.0 * ctx->n * (self ? wx : wx + wy);
   const int ph = prof_begin(ctx, KC_GRAM, count ? 8.0 * ctx->n * nout : 0.0, count ? by : 0.0, 2);
   switch (acc) {
-    case 8: launch_gram_acc<8>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip, fp32); break;
-    case 4: launch_gram_acc<4>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip, fp32); break;
-    case 2: launch_gram_acc<2>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip, fp32); break;
-    default: launch_gram_acc<1>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip, fp32); break;
+    case 8: launch_gram_acc<8>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip, mode); break;
+    case 4: launch_gram_acc<4>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip, mode); break;
+    case 2: launch_gram_acc<2>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip, mode); break;
+    default: launch_gram_acc<1>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip, mode); break;
   }
   CK(cudaGetLastError());
   gplhr::gram_reduce_kernel<<<(nout + gplhr::GRED_WARPS - 1) / gplhr::GRED_WARPS, 32 * gplhr::GRED_WARPS, 0,
@@ -341,7 +349,7 @@ struct In {
 // columns c_store..c only contribute |.|^2 sums (reduced into ctx->d_norms).
 gplhr_status combine(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, bool beta_one,
                      const int* skip = nullptr, Blk Y2 = Blk{nullptr, 0}, int c_split = -1,
-                     int c_store = -1, bool count = true, int fp32 = -1) {
+                     int c_store = -1, bool count = true, int fp32 = -1, bool upper = false) {
   // fp32 = -1: the current phase decides (FP32 in the bulk phase of the mixed mode)
   const bool use32 = fp32 < 0 ? ctx->bulk32 : fp32 != 0;
   if (c <= 0 || ctx->n == 0) return GPLHR_OK;
@@ -363,14 +371,16 @@ gplhr_status combine(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, b
   a.c_store = c_store;
   a.beta_one = beta_one ? 1 : 0;
   a.skip = skip;
-  const int rows_tile = gplhr::comb_rows_tile(c);
+  a.upper = (upper && !use32 && a.nin == 1 && ins[0].w == c && c_store == c && c_split == c) ? 1 : 0;
+  const int rows_tile = gplhr::comb_rows_tile(c, a.upper);
   const int grid = grid_for((size_t)ctx->n, std::max(rows_tile, 64), 4 * ctx->num_sms);
   const int rows_per_cta = (ctx->n + grid - 1) / grid;
   a.normpart = c_store < c ? ctx->norm_part : nullptr;
   const size_t smem =
       (size_t)(wsum * c + rows_tile * wsum + rows_tile * c) * (use32 ? sizeof(float2) : sizeof(double2));
   double by = 16.0 * ctx->n * (wsum + c_store * (beta_one ? 2.0 : 1.0));
-  const int ph = prof_begin(ctx, KC_COMBINE, count ? 8.0 * ctx->n * wsum * c : 0.0, count ? by : 0.0,
+  const double macs = a.upper ? 0.5 * c * (c + 1.0) : (double)wsum * c;
+  const int ph = prof_begin(ctx, KC_COMBINE, count ? 8.0 * ctx->n * macs : 0.0, count ? by : 0.0,
                            c_store < c ? 2 : 1);
   if (use32)
     gplhr::combine_kernel<float><<<grid, gplhr::COMB_THREADS, smem, ctx->stream>>>(ctx->n, rows_per_cta, a);
@@ -500,8 +510,9 @@ gplhr_status orth_against(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w, const std
                                                           ctx->d_status + pass, skip, ctx->d_diag);
     prof_end(ctx, ph);
     CK(cudaGetLastError());
-    TRY(combine(ctx, {In{X, w, Rinv, kOne}}, X, w, false, skip, none, -1, -1, cnt));
-    for (const Extra& e : ex) TRY(combine(ctx, {In{e.E, w, Rinv, kOne}}, e.E, w, false, skip, none, -1, -1, cnt));
+    TRY(combine(ctx, {In{X, w, Rinv, kOne}}, X, w, false, skip, none, -1, -1, cnt, -1, true));
+    for (const Extra& e : ex)
+      TRY(combine(ctx, {In{e.E, w, Rinv, kOne}}, e.E, w, false, skip, none, -1, -1, cnt, -1, true));
   }
   return GPLHR_OK;
 }
@@ -648,8 +659,10 @@ gplhr_status start(gplhr_ctx* ctx) {
   return residuals(ctx);
 }
 
-// Mixed mode: leave the FP32 bulk phase once the largest residual is below switch_tol
-// or has not dropped by 10 % over stall_iters iterations (survey reading C14).  The
+// Mixed mode: leave the FP32 bulk phase once the largest residual is below switch_tol,
+// or, within two decades of switch_tol, has not dropped by 10 % over stall_iters
+// iterations (survey reading C14, with the stall test restricted to where FP32 could
+// be the floor).  The
 // products AV, BV (and AP, BP when they are kept as combinations) are then formed again
 // in FP64, and the residuals recomputed in FP64.
 gplhr_status phase_update(gplhr_ctx* ctx) {
@@ -660,7 +673,9 @@ gplhr_status phase_update(gplhr_ctx* ctx) {
   if (mx < 0.9 * ctx->best_res) {
     ctx->best_res = mx;
     ctx->since_best = 0;
-  } else if (++ctx->since_best >= ctx->stall_iters && ctx->stall_iters > 0) {
+  } else if (mx < 100.0 * ctx->switch_tol && ++ctx->since_best >= ctx->stall_iters && ctx->stall_iters > 0) {
+    // a plateau within two decades of switch_tol may be the FP32 floor; higher up it is
+    // the method's own (irregular) convergence and the bulk phase continues
     go = true;
   }
   if (!go) return GPLHR_OK;
@@ -1091,6 +1106,10 @@ gplhr_status set_smem_limits(gplhr_ctx* ctx) {
   CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<4, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::gram_partial_x32_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::gram_partial_x32_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::gram_partial_x32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::gram_partial_x32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
@@ -1456,11 +1475,12 @@ gplhr_status gplhr_precond_apply(gplhr_ctx* ctx, const void* X, int32_t ldx, int
 }
 
 gplhr_status gplhr_gram(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t wx, const void* Y, int32_t ldy,
-                        int32_t wy, void* C) {
+                        int32_t wy, void* C, int32_t arith) {
   if (!ctx || !valid_block(X, ldx, wx) || !valid_block(Y, ldy, wy) || !C || wx > ctx->s_max ||
-      wy > 2 * ctx->s_max)
+      wy > 2 * ctx->s_max || arith < 0 || arith > 2)
     return GPLHR_EINVAL;
-  TRY(gram(ctx, Blk{(double2*)X, ldx}, wx, Blk{(double2*)Y, ldy}, wy, Blk{nullptr, 0}, 0, (double2*)C));
+  TRY(gram(ctx, Blk{(double2*)X, ldx}, wx, Blk{(double2*)Y, ldy}, wy, Blk{nullptr, 0}, 0, (double2*)C, nullptr,
+           false, true, false, arith));
   CK(cudaStreamSynchronize(ctx->stream));
   return GPLHR_OK;
 }

@@ -300,6 +300,109 @@ gram_partial_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, in
   }
 }
 
+// Gram of FP32-valued blocks with exact products (bulk phase of the mixed mode, whose
+// blocks hold FP32 values in complex128 storage).  Each real product a*b is formed
+// exactly as the float pair (p, e) = (a*b, fma(a, b, -a*b)) on the FP32 pipe; a tile of
+// rows is summed in a compensated float pair (TwoSum on the high parts, the low parts
+// and rounding errors added into a second float), and each tile's pair is added into
+// FP64 accumulators.  The FP64 pipe (about 2 DFMA per clock per SM on GB300) sees only
+// the conversions and the per-tile additions.
+// Error-free transformations written with the _rn intrinsics, which the compiler never
+// contracts into FMAs (a contracted a*b + s would break the exact product / TwoSum).
+__device__ __forceinline__ void two_sum_acc(float& sh, float& sl, float p, float pe) {
+  const float s = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, pe));
+}
+__device__ __forceinline__ void exact_prod_acc(float& sh, float& sl, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -p);  // exact: a*b = p + pe for float a, b
+  two_sum_acc(sh, sl, p, pe);
+}
+
+template <int ACC>
+__global__ void __launch_bounds__(GRAM_THREADS)
+gram_partial_x32_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, int ldx, int wx,
+                        const double2* __restrict__ Y0, int ldy0, int wy0, const double2* __restrict__ Y1,
+                        int ldy1, int wy1, int herm, int nout, int G, int RG, double2* __restrict__ partial,
+                        const int* skip) {
+  if (skip && *skip == 0) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* xs = reinterpret_cast<float2*>(smraw);  // GRAM_ROWS x wx
+  const int wy = wy0 + wy1;
+  float2* ys = xs + GRAM_ROWS * wx;                // GRAM_ROWS x wy
+  const int tid = threadIdx.x;
+  const int g = tid % G, rg = tid / G;
+  const int tile0 = blockIdx.y * G * ACC;
+  const int o0 = tile0 + g * ACC;
+  const bool active = rg < RG && o0 < nout;
+  const int r0 = blockIdx.x * rows_per_chunk;
+  const int r1 = min(n, r0 + rows_per_chunk);
+  double2 acc[ACC];
+  int oi[ACC], oj[ACC];
+#pragma unroll
+  for (int t = 0; t < ACC; ++t) {
+    acc[t] = make_double2(0.0, 0.0);
+    const int o = min(o0 + t, nout - 1);
+    gram_index(o, wx, wy, herm, oi[t], oj[t]);
+  }
+  for (int rb = r0; rb < r1; rb += GRAM_ROWS) {
+    const int nr = min(GRAM_ROWS, r1 - rb);
+    __syncthreads();
+    for (int e = tid; e < nr * wx; e += blockDim.x) {
+      const int rr = e / wx, cc = e - rr * wx;
+      xs[rr * wx + cc] = to_t<float>(X[(size_t)(rb + rr) * ldx + cc]);
+    }
+    for (int e = tid; e < nr * wy; e += blockDim.x) {
+      const int rr = e / wy, cc = e - rr * wy;
+      ys[rr * wy + cc] = to_t<float>(cc < wy0 ? Y0[(size_t)(rb + rr) * ldy0 + cc]
+                                              : Y1[(size_t)(rb + rr) * ldy1 + (cc - wy0)]);
+    }
+    __syncthreads();
+    if (active) {
+      float rh[ACC], rl[ACC], ih[ACC], il[ACC];
+#pragma unroll
+      for (int t = 0; t < ACC; ++t) rh[t] = rl[t] = ih[t] = il[t] = 0.0f;
+      for (int rr = rg; rr < nr; rr += RG) {
+        const float2* xr = xs + rr * wx;
+        const float2* yr = ys + rr * wy;
+#pragma unroll
+        for (int t = 0; t < ACC; ++t) {
+          const float2 a = xr[oi[t]], b = yr[oj[t]];
+          // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
+          exact_prod_acc(rh[t], rl[t], a.x, b.x);
+          exact_prod_acc(rh[t], rl[t], a.y, b.y);
+          exact_prod_acc(ih[t], il[t], a.x, b.y);
+          exact_prod_acc(ih[t], il[t], -a.y, b.x);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < ACC; ++t) {
+        acc[t].x += (double)rh[t] + (double)rl[t];
+        acc[t].y += (double)ih[t] + (double)il[t];
+      }
+    }
+  }
+  __syncthreads();
+  double2* red = reinterpret_cast<double2*>(smraw);
+  const int per = G * ACC;
+  if (rg < RG) {
+#pragma unroll
+    for (int t = 0; t < ACC; ++t) red[rg * per + g * ACC + t] = acc[t];
+  }
+  __syncthreads();
+  double2* out = partial + (size_t)blockIdx.x * nout;
+  for (int e = tid; e < per; e += blockDim.x) {
+    const int o = tile0 + e;
+    if (o >= nout) break;
+    double2 sum = red[e];
+    for (int q = 1; q < RG; ++q) sum = cadd(sum, red[q * per + e]);
+    out[o] = sum;
+  }
+}
+
 // C = sum_b partial[b] (deterministic): one warp per output, lane l adds the chunks
 // l, l+32, ... in order, then a fixed xor-shuffle tree.  The output enumeration is
 // mapped back to (i, j) of the wx x wy result (row-major, ld = wy); with herm = 1 the
@@ -353,10 +456,17 @@ struct CombArgs {
   int beta_one;     // 1: Y += ..., 0: Y = ...
   double* normpart; // [gridDim.x][c - c_store] or null
   const int* skip;
+  int upper;        // 1: single input whose C is upper triangular (X R^{-1}): sum j <= col
 };
 constexpr int COMB_THREADS = 256;
 
-__host__ __device__ inline int comb_rows_tile(int c) { return c >= COMB_THREADS ? 1 : COMB_THREADS / c; }
+// Rows staged per tile.  For the triangular form the tile is 32 rows and threads are
+// mapped column-major (a warp = 32 rows of one output column), so the loop bound j <= col
+// is uniform across each warp: no predicated-off DFMAs.
+__host__ __device__ inline int comb_rows_tile(int c, int upper = 0) {
+  if (upper) return 32;
+  return c >= COMB_THREADS ? 1 : COMB_THREADS / c;
+}
 
 __device__ __forceinline__ double2* comb_out(const CombArgs& a, int r, int cc) {
   return cc < a.c_split ? a.Y + (size_t)r * a.ldy + cc : a.Y2 + (size_t)r * a.ldy2 + (cc - a.c_split);
@@ -374,7 +484,7 @@ __global__ void combine_kernel(int n, int rows_per_cta, CombArgs a) {
   for (int t = 0; t < a.nin; ++t) wsum += a.in[t].w;
   C2* cs = sm;
   C2* xs = cs + wsum * a.c;
-  const int rows_tile = comb_rows_tile(a.c);
+  const int rows_tile = comb_rows_tile(a.c, a.upper);
   C2* ys = xs + rows_tile * wsum;
   __shared__ double nsum[COMB_MAX_NORMS];
   {
@@ -408,11 +518,21 @@ __global__ void combine_kernel(int n, int rows_per_cta, CombArgs a) {
       }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < nr * a.c; e += blockDim.x) {
-      const int rr = e / a.c, cc = e - rr * a.c;
+    const int nwork = a.upper ? rows_tile * a.c : nr * a.c;
+    for (int e = threadIdx.x; e < nwork; e += blockDim.x) {
+      int rr, cc;
+      if (a.upper) {
+        rr = e % rows_tile;
+        cc = e / rows_tile;
+        if (rr >= nr) continue;
+      } else {
+        rr = e / a.c;
+        cc = e - rr * a.c;
+      }
       C2 acc = (a.beta_one && cc < a.c_store) ? ys[rr * a.c + cc] : czero<T>();
       const C2* xr = xs + rr * wsum;
-      for (int j = 0; j < wsum; ++j) acc = cfma(xr[j], cs[j * a.c + cc], acc);
+      const int jend = a.upper ? cc + 1 : wsum;
+      for (int j = 0; j < jend; ++j) acc = cfma(xr[j], cs[j * a.c + cc], acc);
       if (cc < a.c_store) {
         *comb_out(a, rb + rr, cc) = to_d(acc);
       } else {

@@ -89,7 +89,7 @@ def lib():
     L.gplhr_last_error.restype = C.c_char_p
     L.gplhr_spmm.argtypes = [vp, vp, i32, i32, vp, i32, vp, i32]
     L.gplhr_precond_apply.argtypes = [vp, vp, i32, i32, vp, i32]
-    L.gplhr_gram.argtypes = [vp, vp, i32, i32, vp, i32, i32, vp]
+    L.gplhr_gram.argtypes = [vp, vp, i32, i32, vp, i32, i32, vp, i32]
     L.gplhr_orth.argtypes = [vp, vp, i32, i32, vp]
     L.gplhr_ordqz.argtypes = [i32, dp, dp, dbl, dbl, dp, dp, dp, dp]
     L.gplhr_mfactors.argtypes = [i32, dp, dp, dp, dp]
@@ -238,9 +238,12 @@ def gplhr_precond_apply(ctx, X, Y):
                                      Y.stride(0)), ctx)
 
 
-def gplhr_gram(ctx, X, Y, Cout):
+GRAM_ARITH = {"fp64": 0, "fp32": 1, "exact32": 2}
+
+
+def gplhr_gram(ctx, X, Y, Cout, arith: str = "fp64"):
     _check(lib().gplhr_gram(ctx, X.data_ptr(), X.stride(0), X.shape[1], Y.data_ptr(),
-                            Y.stride(0), Y.shape[1], Cout.data_ptr()), ctx)
+                            Y.stride(0), Y.shape[1], Cout.data_ptr(), GRAM_ARITH[arith]), ctx)
 
 
 def gplhr_gram_noalloc(X, Y, Cout, stream: int = 0):

