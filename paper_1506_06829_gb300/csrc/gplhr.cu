@@ -576,7 +576,7 @@ gplhr_status residuals(gplhr_ctx* ctx) {
 }
 
 // Host: sorted QZ of the s x s pencil in h_phipsi, returns Ybar_R, Ybar_L, Rbar_A, Rbar_B.
-gplhr_status host_qz(gplhr_ctx* ctx, int s, SqMat& RAb, SqMat& RBb, SqMat& YLb, SqMat& YRb) {
+gplhr_status host_qz(gplhr_ctx* ctx, int s, SqMat& RAb, SqMat& RBb, SqMat& YLb, SqMat& YRb, int nsort = -1) {
   SqMat Phi(s), Psi(s);
   for (int i = 0; i < s; ++i)
     for (int j = 0; j < s; ++j) {
@@ -590,7 +590,7 @@ gplhr_status host_qz(gplhr_ctx* ctx, int s, SqMat& RAb, SqMat& RBb, SqMat& YLb, 
       }
     }
   ctx->n_qz += 1;
-  if (!gplhr::ordered_qz(Phi, Psi, ctx->sigma, RAb, RBb, YLb, YRb)) {
+  if (!gplhr::ordered_qz(Phi, Psi, ctx->sigma, RAb, RBb, YLb, YRb, nsort)) {
     ctx->err = "QZ iteration did not converge";
     return GPLHR_ENUMERIC;
   }
@@ -783,9 +783,10 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
                      ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   SqMat RAb, RBb, YLb, YRb;
-  TRY(host_qz(ctx, s, RAb, RBb, YLb, YRb));
-  // steps 25-28: V = Z Ybar_R(:, 1:k), P = Z Ybar_R(:, k+1:k+kk), Q = U Ybar_L(:, 1:k)
+  // only the leading k + kk positions of the ordering are used (V and P)
   const int cv = k + kk;
+  TRY(host_qz(ctx, s, RAb, RBb, YLb, YRb, cv));
+  // steps 25-28: V = Z Ybar_R(:, 1:k), P = Z Ybar_R(:, k+1:k+kk), Q = U Ybar_L(:, 1:k)
   double2* hy = ctx->h_small + 6 * k * k;
   double2* hl = hy + (size_t)s * cv;
   pack(hy, YRb, 0, s, 0, cv);

@@ -55,11 +55,27 @@ void rot_rows(SqMat& M, int i1, int i2, double c, cd s, int c0, int c1) {
 }
 
 // Y <- Y G^* on columns (j1, j2): the accumulation that keeps Y (G M) = Y_old M.
-void rot_left_accum(SqMat& Y, int j1, int j2, double c, cd s) {
-  for (int i = 0; i < Y.n; ++i) {
-    const cd x = Y(i, j1), y = Y(i, j2);
-    Y(i, j1) = c * x + std::conj(s) * y;
-    Y(i, j2) = -s * x + c * y;
+// Y is held transposed (Yt(j, i) = Y(i, j)) so the two columns are contiguous rows.
+void rot_left_accum(SqMat& Yt, int j1, int j2, double c, cd s) {
+  cd* a = &Yt(j1, 0);
+  cd* b = &Yt(j2, 0);
+  const cd cs = std::conj(s);
+  for (int i = 0; i < Yt.n; ++i) {
+    const cd x = a[i], y = b[i];
+    a[i] = c * x + cs * y;
+    b[i] = -s * x + c * y;
+  }
+}
+
+// YR <- YR Zr on columns (j1, j2), YR held transposed like YL.
+void rot_right_accum(SqMat& Yt, int j1, int j2, double c, cd s) {
+  cd* a = &Yt(j1, 0);
+  cd* b = &Yt(j2, 0);
+  const cd cs = std::conj(s);
+  for (int i = 0; i < Yt.n; ++i) {
+    const cd x = a[i], y = b[i];
+    a[i] = c * x - cs * y;
+    b[i] = s * x + c * y;
   }
 }
 
@@ -134,7 +150,7 @@ void hessenberg_triangular(SqMat& H, SqMat& T, SqMat& YL, SqMat& YR) {
       right_zeroing(T(i, i - 1), T(i, i), c, s);
       rot_cols(T, i - 1, i, c, s, 0, i + 1);
       rot_cols(H, i - 1, i, c, s, 0, n);
-      rot_cols(YR, i - 1, i, c, s, 0, n);
+      rot_right_accum(YR, i - 1, i, c, s);
       T(i, i - 1) = 0.0;
     }
   }
@@ -158,7 +174,7 @@ void chase_zero_down(SqMat& H, SqMat& T, SqMat& YL, SqMat& YR, int j, int ihi) {
       right_zeroing(H(i + 1, i - 1), H(i + 1, i), c, s);
       rot_cols(H, i - 1, i, c, s, 0, std::min(i + 2, n));
       rot_cols(T, i - 1, i, c, s, 0, i + 1);
-      rot_cols(YR, i - 1, i, c, s, 0, n);
+      rot_right_accum(YR, i - 1, i, c, s);
       H(i + 1, i - 1) = 0.0;
     }
   }
@@ -168,7 +184,7 @@ void chase_zero_down(SqMat& H, SqMat& T, SqMat& YL, SqMat& YR, int j, int ihi) {
     right_zeroing(H(ihi, ihi - 1), H(ihi, ihi), c, s);
     rot_cols(H, ihi - 1, ihi, c, s, 0, ihi + 1);
     rot_cols(T, ihi - 1, ihi, c, s, 0, ihi + 1);
-    rot_cols(YR, ihi - 1, ihi, c, s, 0, n);
+    rot_right_accum(YR, ihi - 1, ihi, c, s);
     H(ihi, ihi - 1) = 0.0;
   }
 }
@@ -233,7 +249,7 @@ bool qz_iterate(SqMat& H, SqMat& T, SqMat& YL, SqMat& YR) {
       right_zeroing(T(j + 1, j), T(j + 1, j + 1), c, s);
       rot_cols(T, j, j + 1, c, s, 0, j + 2);
       rot_cols(H, j, j + 1, c, s, 0, std::min(j + 3, n));
-      rot_cols(YR, j, j + 1, c, s, 0, n);
+      rot_right_accum(YR, j, j + 1, c, s);
       T(j + 1, j) = 0.0;
       if (j + 2 <= ihi) {
         // H(j+2, j) filled: zero it from the left on rows (j+1, j+2)
@@ -271,7 +287,7 @@ void swap_adjacent(SqMat& A, SqMat& B, SqMat& YL, SqMat& YR, int j) {
   }
   rot_cols(A, j, j + 1, c, s, 0, j + 2);
   rot_cols(B, j, j + 1, c, s, 0, j + 2);
-  rot_cols(YR, j, j + 1, c, s, 0, n);
+  rot_right_accum(YR, j, j + 1, c, s);
   // first columns of A, B are now parallel in rows (j, j+1): zero row j+1 from the left
   const double na = std::norm(A(j, j)) + std::norm(A(j + 1, j));
   const double nb = std::norm(B(j, j)) + std::norm(B(j + 1, j));
@@ -305,26 +321,31 @@ double pair_distance(cd alpha, cd beta, cd sigma) {
 }
 
 bool ordered_qz(const SqMat& Phi, const SqMat& Psi, cd sigma, SqMat& RA, SqMat& RB, SqMat& YL,
-                SqMat& YR) {
+                SqMat& YR, int nsort) {
   const int n = Phi.n;
   RA = Phi;
   RB = Psi;
-  YL = SqMat::eye(n);
-  YR = SqMat::eye(n);
-  if (n == 0) return true;
-  hessenberg_triangular(RA, RB, YL, YR);
-  if (!qz_iterate(RA, RB, YL, YR)) return false;
+  SqMat YLt = SqMat::eye(n), YRt = SqMat::eye(n);  // transposed accumulators
+  if (n == 0) {
+    YL = YLt;
+    YR = YRt;
+    return true;
+  }
+  hessenberg_triangular(RA, RB, YLt, YRt);
+  if (!qz_iterate(RA, RB, YLt, YRt)) return false;
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < i; ++j) {
       RA(i, j) = 0.0;
       RB(i, j) = 0.0;
     }
-  // selection sort: bring the nearest remaining pair to position pos by adjacent swaps
-  for (int pos = 0; pos + 1 < n; ++pos) {
+  // selection sort of the leading nsort positions: bring the nearest remaining pair to
+  // position pos by adjacent swaps (positions past nsort keep the QZ's order)
+  const int npos = nsort < 0 ? n - 1 : std::min(nsort, n - 1);
+  for (int pos = 0; pos < npos; ++pos) {
     int best = pos;
     for (int j = pos + 1; j < n; ++j)
       if (key_less(RA(j, j), RB(j, j), RA(best, best), RB(best, best), sigma)) best = j;
-    for (int j = best - 1; j >= pos; --j) swap_adjacent(RA, RB, YL, YR, j);
+    for (int j = best - 1; j >= pos; --j) swap_adjacent(RA, RB, YLt, YRt, j);
   }
   // unit-phase scaling: RB(j, j) real >= 0
   for (int j = 0; j < n; ++j) {
@@ -336,9 +357,16 @@ bool ordered_qz(const SqMat& Phi, const SqMat& Psi, cd sigma, SqMat& RA, SqMat& 
         RB(j, c) *= t;
       }
       RB(j, j) = mag;
-      for (int i = 0; i < n; ++i) YL(i, j) *= std::conj(t);
+      for (int i = 0; i < n; ++i) YLt(j, i) *= std::conj(t);
     }
   }
+  YL = SqMat(n);
+  YR = SqMat(n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      YL(i, j) = YLt(j, i);
+      YR(i, j) = YRt(j, i);
+    }
   return true;
 }
 

@@ -23,10 +23,11 @@ struct SqMat {
 };
 
 // Ordered complex QZ (footnote to Alg. 2 step 2): Phi = YL RA YR^*, Psi = YL RB YR^*,
-// |RA(j,j)/RB(j,j) - sigma| non-decreasing, RB(j,j) real >= 0.
+// |RA(j,j)/RB(j,j) - sigma| non-decreasing over the leading nsort positions (< 0: all),
+// which hold the nsort pairs nearest sigma; RB(j,j) real >= 0.
 // Returns false if the QZ iteration did not converge.
 bool ordered_qz(const SqMat& Phi, const SqMat& Psi, cd sigma, SqMat& RA, SqMat& RB, SqMat& YL,
-                SqMat& YR);
+                SqMat& YR, int nsort = -1);
 
 // Theorem 1 with Eqs. G1_fix/G2_fix: MA = G2 G^{-1} RA, MB = I - G1 G^{-1} RA.
 void m_factors(const SqMat& RA, const SqMat& RB, SqMat& MA, SqMat& MB);
