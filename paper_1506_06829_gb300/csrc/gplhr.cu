@@ -319,8 +319,10 @@ gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy
   rows = ((rows + gplhr::GRAM_ROWS - 1) / gplhr::GRAM_ROWS) * gplhr::GRAM_ROWS;
   nchunk = (ctx->n + rows - 1) / rows;
   dim3 grid(nchunk, ntile);
-  const size_t smem =
-      std::max((size_t)gplhr::GRAM_ROWS * (wx + wy), (size_t)RG * G * acc) * sizeof(double2);
+  const size_t smem = mode == 2 ? std::max((size_t)gplhr::X32_ROWS * (wx + wy) * sizeof(float2),
+                                           (size_t)RG * G * acc * sizeof(double2))
+                                : std::max((size_t)gplhr::GRAM_ROWS * (wx + wy), (size_t)RG * G * acc) *
+                                      sizeof(double2);
   const bool self = X.p == Y0.p && wy1 == 0;
   const double by = 16.0 * ctx->n * (self ? wx : wx + wy);
   const int ph = prof_begin(ctx, KC_GRAM, count ? 8.0 * ctx->n * nout : 0.0, count ? by : 0.0, 2);

@@ -322,6 +322,11 @@ __device__ __forceinline__ void exact_prod_acc(float& sh, float& sl, float a, fl
   two_sum_acc(sh, sl, p, pe);
 }
 
+// Rows per staged tile of the exact-product Gram, and rows a thread sums in its float
+// pair between flushes to FP64 (compensated-sum error <= X32_FLUSH * 2^-48 * sum |p|).
+constexpr int X32_ROWS = 32;
+constexpr int X32_FLUSH = 32;
+
 template <int ACC>
 __global__ void __launch_bounds__(GRAM_THREADS)
 gram_partial_x32_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, int ldx, int wx,
@@ -330,9 +335,9 @@ gram_partial_x32_kernel(int n, int rows_per_chunk, const double2* __restrict__ X
                         const int* skip) {
   if (skip && *skip == 0) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* xs = reinterpret_cast<float2*>(smraw);  // GRAM_ROWS x wx
+  float2* xs = reinterpret_cast<float2*>(smraw);  // X32_ROWS x wx
   const int wy = wy0 + wy1;
-  float2* ys = xs + GRAM_ROWS * wx;                // GRAM_ROWS x wy
+  float2* ys = xs + X32_ROWS * wx;                 // X32_ROWS x wy
   const int tid = threadIdx.x;
   const int g = tid % G, rg = tid / G;
   const int tile0 = blockIdx.y * G * ACC;
@@ -348,8 +353,14 @@ gram_partial_x32_kernel(int n, int rows_per_chunk, const double2* __restrict__ X
     const int o = min(o0 + t, nout - 1);
     gram_index(o, wx, wy, herm, oi[t], oj[t]);
   }
-  for (int rb = r0; rb < r1; rb += GRAM_ROWS) {
-    const int nr = min(GRAM_ROWS, r1 - rb);
+  // float-pair accumulators, flushed to FP64 after about X32_FLUSH rows of this thread
+  float rh[ACC], rl[ACC], ih[ACC], il[ACC];
+#pragma unroll
+  for (int t = 0; t < ACC; ++t) rh[t] = rl[t] = ih[t] = il[t] = 0.0f;
+  const int tiles_per_flush = max(1, (X32_FLUSH * RG) / X32_ROWS);
+  int tile = 0;
+  for (int rb = r0; rb < r1; rb += X32_ROWS, ++tile) {
+    const int nr = min(X32_ROWS, r1 - rb);
     __syncthreads();
     for (int e = tid; e < nr * wx; e += blockDim.x) {
       const int rr = e / wx, cc = e - rr * wx;
@@ -362,9 +373,6 @@ gram_partial_x32_kernel(int n, int rows_per_chunk, const double2* __restrict__ X
     }
     __syncthreads();
     if (active) {
-      float rh[ACC], rl[ACC], ih[ACC], il[ACC];
-#pragma unroll
-      for (int t = 0; t < ACC; ++t) rh[t] = rl[t] = ih[t] = il[t] = 0.0f;
       for (int rr = rg; rr < nr; rr += RG) {
         const float2* xr = xs + rr * wx;
         const float2* yr = ys + rr * wy;
@@ -378,10 +386,13 @@ gram_partial_x32_kernel(int n, int rows_per_chunk, const double2* __restrict__ X
           exact_prod_acc(ih[t], il[t], -a.y, b.x);
         }
       }
+      if ((tile + 1) % tiles_per_flush == 0 || rb + X32_ROWS >= r1) {
 #pragma unroll
-      for (int t = 0; t < ACC; ++t) {
-        acc[t].x += (double)rh[t] + (double)rl[t];
-        acc[t].y += (double)ih[t] + (double)il[t];
+        for (int t = 0; t < ACC; ++t) {
+          acc[t].x += (double)rh[t] + (double)rl[t];
+          acc[t].y += (double)ih[t] + (double)il[t];
+          rh[t] = rl[t] = ih[t] = il[t] = 0.0f;
+        }
       }
     }
   }
