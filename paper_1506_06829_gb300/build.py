@@ -34,6 +34,11 @@ def _compile(src: str) -> str:
            "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")] + ARCH
     if src.endswith(".cu"):
         cmd += ["-Xptxas", "-warn-spills"]
+    else:
+        # host QZ: plain complex multiply/divide formulas, without the Inf/NaN recovery and
+        # overflow-avoiding scaling of the default ones (12-16 % faster); the QZ only sees
+        # finite pencils, non-finite ones are rejected before it, and entries far below 1e150
+        cmd += ["-Xcompiler", "-fcx-limited-range"]
     subprocess.run(cmd, check=True)
     return obj
 

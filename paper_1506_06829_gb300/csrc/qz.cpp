@@ -45,46 +45,66 @@ void givens(cd f, cd g, double& c, cd& s, cd& r) {
   r = ph * nrm;
 }
 
-// M <- G M on rows (i1, i2), columns [c0, c1).
+// The rotations below work on the interleaved (re, im) doubles directly so that the
+// compiler can vectorise them.
+
+// M <- G M on rows (i1, i2), columns [c0, c1): x' = c x + s y, y' = -conj(s) x + c y.
 void rot_rows(SqMat& M, int i1, int i2, double c, cd s, int c0, int c1) {
+  double* a = reinterpret_cast<double*>(&M(i1, 0));
+  double* b = reinterpret_cast<double*>(&M(i2, 0));
+  const double sr = s.real(), si = s.imag();
   for (int j = c0; j < c1; ++j) {
-    const cd x = M(i1, j), y = M(i2, j);
-    M(i1, j) = c * x + s * y;
-    M(i2, j) = -std::conj(s) * x + c * y;
+    const double xr = a[2 * j], xi = a[2 * j + 1], yr = b[2 * j], yi = b[2 * j + 1];
+    a[2 * j] = c * xr + sr * yr - si * yi;
+    a[2 * j + 1] = c * xi + sr * yi + si * yr;
+    b[2 * j] = -sr * xr - si * xi + c * yr;
+    b[2 * j + 1] = -sr * xi + si * xr + c * yi;
   }
 }
 
 // Y <- Y G^* on columns (j1, j2): the accumulation that keeps Y (G M) = Y_old M.
-// Y is held transposed (Yt(j, i) = Y(i, j)) so the two columns are contiguous rows.
+// Y is held transposed (Yt(j, i) = Y(i, j)) so the two columns are contiguous rows:
+// x' = c x + conj(s) y, y' = -s x + c y.
 void rot_left_accum(SqMat& Yt, int j1, int j2, double c, cd s) {
-  cd* a = &Yt(j1, 0);
-  cd* b = &Yt(j2, 0);
-  const cd cs = std::conj(s);
+  double* a = reinterpret_cast<double*>(&Yt(j1, 0));
+  double* b = reinterpret_cast<double*>(&Yt(j2, 0));
+  const double sr = s.real(), si = s.imag();
   for (int i = 0; i < Yt.n; ++i) {
-    const cd x = a[i], y = b[i];
-    a[i] = c * x + cs * y;
-    b[i] = -s * x + c * y;
+    const double xr = a[2 * i], xi = a[2 * i + 1], yr = b[2 * i], yi = b[2 * i + 1];
+    a[2 * i] = c * xr + sr * yr + si * yi;
+    a[2 * i + 1] = c * xi + sr * yi - si * yr;
+    b[2 * i] = -sr * xr + si * xi + c * yr;
+    b[2 * i + 1] = -sr * xi - si * xr + c * yi;
   }
 }
 
-// YR <- YR Zr on columns (j1, j2), YR held transposed like YL.
+// YR <- YR Zr on columns (j1, j2), YR held transposed like YL:
+// x' = c x - conj(s) y, y' = s x + c y.
 void rot_right_accum(SqMat& Yt, int j1, int j2, double c, cd s) {
-  cd* a = &Yt(j1, 0);
-  cd* b = &Yt(j2, 0);
-  const cd cs = std::conj(s);
+  double* a = reinterpret_cast<double*>(&Yt(j1, 0));
+  double* b = reinterpret_cast<double*>(&Yt(j2, 0));
+  const double sr = s.real(), si = s.imag();
   for (int i = 0; i < Yt.n; ++i) {
-    const cd x = a[i], y = b[i];
-    a[i] = c * x - cs * y;
-    b[i] = s * x + c * y;
+    const double xr = a[2 * i], xi = a[2 * i + 1], yr = b[2 * i], yi = b[2 * i + 1];
+    a[2 * i] = c * xr - sr * yr - si * yi;
+    a[2 * i + 1] = c * xi - sr * yi + si * yr;
+    b[2 * i] = sr * xr - si * xi + c * yr;
+    b[2 * i + 1] = sr * xi + si * xr + c * yi;
   }
 }
 
-// M <- M Zr on columns (j1, j2), rows [r0, r1), Zr = [[c, s], [-conj(s), c]].
+// M <- M Zr on columns (j1, j2), rows [r0, r1), Zr = [[c, s], [-conj(s), c]]:
+// x' = c x - conj(s) y, y' = s x + c y.
 void rot_cols(SqMat& M, int j1, int j2, double c, cd s, int r0, int r1) {
+  const double sr = s.real(), si = s.imag();
   for (int i = r0; i < r1; ++i) {
-    const cd x = M(i, j1), y = M(i, j2);
-    M(i, j1) = c * x - std::conj(s) * y;
-    M(i, j2) = s * x + c * y;
+    double* a = reinterpret_cast<double*>(&M(i, j1));
+    double* b = reinterpret_cast<double*>(&M(i, j2));
+    const double xr = a[0], xi = a[1], yr = b[0], yi = b[1];
+    a[0] = c * xr - sr * yr - si * yi;
+    a[1] = c * xi - sr * yi + si * yr;
+    b[0] = sr * xr - si * xi + c * yr;
+    b[1] = sr * xi + si * xr + c * yi;
   }
 }
 
