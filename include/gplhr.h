@@ -105,7 +105,10 @@ typedef struct {
   double switch_tol;   /* [1e-5] MIXED: refine in FP64 once max residual < switch_tol   */
   int32_t stall_iters; /* [5]    MIXED: ... or after this many iterations without a 10 %
                           decrease of the max residual; < 0: never on a stall            */
-  int32_t reserved;
+  int32_t pencil;      /* [0]    projected pencil: 0 = U^*BZ by a Gram product and
+                          U^*(A - sigma B)Z from the factors of U's construction (Prop. 3.2
+                          and the orthonormalisation of (A - sigma B)[W S P]); 1 = both
+                          U^*AZ and U^*BZ by Gram products (Alg. 2 step 24 as printed)   */
 } gplhr_opts;
 
 /* Per-solve report.  resid[j] (j < k) is the backward error of pair j,

@@ -82,6 +82,11 @@ struct gplhr_ctx {
   double2 *dC1 = nullptr, *dC2 = nullptr, *dMBa = nullptr, *dMAa = nullptr;
   double2 *dYR = nullptr, *dYL = nullptr, *dPhiPsi = nullptr, *dGram = nullptr, *dProjC = nullptr;
   double2* dRinv = nullptr;  // 3 x s_max^2
+  double2* dTrackC = nullptr;  // 3 x s_max^2: projection coefficients of each orth pass
+  double2* dTrackR = nullptr;  // 3 x s_max^2: Cholesky factors of each orth pass
+  double2* h_track = nullptr;  // pinned copies of the two above
+  int* h_status = nullptr;
+  bool factored = true;        // projected pencil from U's factors (one Gram)
   double2* gram_part = nullptr;
   size_t gram_part_elems = 0;
   double* norm_part = nullptr;
@@ -489,7 +494,11 @@ struct Extra {  // a block transformed alongside X (e.g. A P with P): E -= EL C;
 //     pass: X -= L (L^* X);  G = X^* X = R^* R;  X <- X R^{-1},
 // with a shifted Cholesky in the first pass when G is not numerically positive
 // definite, followed then by a third pass (shifted Cholesky QR3).  Extras follow X.
-gplhr_status orth_against(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w, const std::vector<Extra>& ex = {}) {
+// track: keep each pass's projection coefficients C_p (wl x w) in dTrackC and Cholesky
+// factor R_p (w x w) in dTrackR, so that X_0 = L (C_0 + C_1 R_0 [+ C_2 R_1 R_0])
+// + X_final (R_1 R_0 [R_2 R_1 R_0]) can be rebuilt on the host.
+gplhr_status orth_against(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w, const std::vector<Extra>& ex = {},
+                          bool track = false) {
   if (w <= 0) return GPLHR_OK;
   const int smax2 = ctx->s_max * ctx->s_max;
   for (int pass = 0; pass < 3; ++pass) {
@@ -500,6 +509,9 @@ gplhr_status orth_against(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w, const std
     const Blk none{nullptr, 0};
     if (wl > 0) {
       TRY(gram(ctx, L, wl, X, w, none, 0, ctx->dProjC, skip, false, cnt, ctx->bulk32));
+      if (track)
+        CK(cudaMemcpyAsync(ctx->dTrackC + (size_t)pass * smax2, ctx->dProjC, (size_t)wl * w * sizeof(double2),
+                           cudaMemcpyDeviceToDevice, ctx->stream));
       TRY(combine(ctx, {In{L, wl, ctx->dProjC, kMinusOne}}, X, w, true, skip, none, -1, -1, cnt));
       for (const Extra& e : ex)
         TRY(combine(ctx, {In{e.EL, wl, ctx->dProjC, kMinusOne}}, e.E, w, true, skip, none, -1, -1, cnt));
@@ -509,7 +521,8 @@ gplhr_status orth_against(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w, const std
     const size_t smem = (size_t)2 * w * w * sizeof(double2);
     const int ph = prof_begin(ctx, KC_CHOL, 8.0 * w * w * w / 2.0, 48.0 * w * w);
     gplhr::chol_inv_kernel<<<1, 256, smem, ctx->stream>>>(w, (int64_t)ctx->n, ctx->dGram, Rinv,
-                                                          ctx->d_status + pass, skip, ctx->d_diag);
+                                                          ctx->d_status + pass, skip, ctx->d_diag,
+                                                          track ? ctx->dTrackR + (size_t)pass * smax2 : nullptr);
     prof_end(ctx, ph);
     CK(cudaGetLastError());
     TRY(combine(ctx, {In{X, w, Rinv, kOne}}, X, w, false, skip, none, -1, -1, cnt, -1, true));
@@ -611,9 +624,10 @@ void set_factors(gplhr_ctx* ctx, const SqMat& RAb, const SqMat& RBb) {
   gplhr::m_factors(ctx->RA, ctx->RB, ctx->MA, ctx->MB);
 }
 
+gplhr_status start_steps(gplhr_ctx* ctx);
+
 // Steps 1-4 of Algorithm 2.  Z[:, 0:k] must hold V0.
 gplhr_status start(gplhr_ctx* ctx) {
-  const int k = ctx->k;
   ctx->it = 0;
   ctx->q = 0;
   ctx->m = ctx->m0;
@@ -625,6 +639,13 @@ gplhr_status start(gplhr_ctx* ctx) {
   ctx->best_res = 1e300;
   ctx->since_best = 0;
   CK(cudaMemsetAsync(ctx->d_diag, 0, 2 * sizeof(int), ctx->stream));
+  return start_steps(ctx);
+}
+
+// Steps 1-4 on the block in Z[:, 0:k]: V = orth(V), Q = orth((A - sigma B) V), ordered
+// QZ of (Q^*AV, Q^*BV), V <- V YR, Q <- Q YL, M_A, M_B; then the residuals.
+gplhr_status start_steps(gplhr_ctx* ctx) {
+  const int k = ctx->k;
   TRY(orth_against(ctx, Blk{nullptr, 0}, 0, blkZ(ctx, 0), k));                // V = orth(V0)
   TRY(spmm_AB(ctx, blkZ(ctx, 0), k, blkAZ(ctx, 0), blkBZ(ctx, 0)));        // AV, BV
   const double2 ms = d2(-ctx->sigma);
@@ -683,10 +704,13 @@ gplhr_status phase_update(gplhr_ctx* ctx) {
   if (!go) return GPLHR_OK;
   ctx->bulk32 = false;
   const int k = ctx->k;
-  TRY(spmm_AB(ctx, blkZ(ctx, 0), k, blkAZ(ctx, 0), blkBZ(ctx, 0)));
   if (!ctx->recompute && ctx->hasP)
     TRY(spmm_AB(ctx, Blk{ctx->Pb, k}, k, Blk{ctx->APb, k}, Blk{ctx->hasB ? ctx->BPb : ctx->Pb, k}));
-  return residuals(ctx);
+  // Steps 1-4 again, in FP64, from the current V: V and Q orthonormal to FP64 accuracy
+  // (the bulk phase leaves them orthonormal to FP32 accuracy only, and later iterations
+  // only rotate Q by unitary factors), AV, BV and the Schur factors consistent with them.
+  // P is kept.
+  return start_steps(ctx);
 }
 
 // Convergence bookkeeping after residuals(): soft locking in order and m-adaptation.
@@ -706,6 +730,93 @@ bool converged_update(gplhr_ctx* ctx) {
     }
   }
   return false;
+}
+
+// Projected pencil without a second Gram (step 24).  U = [Q Qhat] was built so that
+//   (A - sigma B) V       = Q (R_A - sigma R_B)                  (Prop. 3.2), and
+//   (A - sigma B) [W S P] = Q C + Qhat R,  C = C_0 + C_1 R_0 (+ C_2 R_1 R_0),
+//                                          R = R_1 R_0 (R_2 R_1 R_0)
+// from the passes of its orthonormalisation, so F = U^*(A - sigma B) Z is the block upper
+// triangular [[R_A - sigma R_B, C], [0, R]] and only Psi = U^* B Z needs a Gram product.
+// The QZ runs on (F, Psi), whose eigenvalues are lambda - sigma (sorted by modulus), and
+// Rbar_A = Rbar_F + sigma Rbar_Psi.
+gplhr_status factored_pencil_qz(gplhr_ctx* ctx, int s, int sk, SqMat& RAb, SqMat& RBb, SqMat& YLb, SqMat& YRb,
+                                int cv) {
+  const int k = ctx->k;
+  const int smax2 = ctx->s_max * ctx->s_max;
+  TRY(gram(ctx, blkU(ctx, 0), s, blkBZ(ctx, 0), s, Blk{nullptr, 0}, 0, ctx->dPhiPsi));
+  const size_t nC = (size_t)k * sk, nR = (size_t)sk * sk;
+  double2* hPsi = ctx->h_phipsi;
+  double2* hC = ctx->h_track;                // 3 x nC
+  double2* hR = ctx->h_track + 3 * nC;       // 3 x nR
+  CK(cudaMemcpyAsync(hPsi, ctx->dPhiPsi, (size_t)s * s * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+  for (int p = 0; p < 3; ++p) {
+    CK(cudaMemcpyAsync(hC + p * nC, ctx->dTrackC + (size_t)p * smax2, nC * sizeof(double2), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(hR + p * nR, ctx->dTrackR + (size_t)p * smax2, nR * sizeof(double2), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  }
+  CK(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  ctx->d2h_bytes += (int64_t)((size_t)s * s + 3 * (nC + nR)) * sizeof(double2) + sizeof(int);
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int passes = ctx->h_status[0] != 0 ? 3 : 2;
+  auto Cm = [&](int p) {
+    SqMat M(std::max(k, sk));
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < sk; ++j) M(i, j) = cd(hC[p * nC + i * sk + j].x, hC[p * nC + i * sk + j].y);
+    return M;
+  };
+  auto Rm = [&](int p) {
+    SqMat M(sk);
+    for (int i = 0; i < sk; ++i)
+      for (int j = 0; j < sk; ++j) M(i, j) = cd(hR[p * nR + i * sk + j].x, hR[p * nR + i * sk + j].y);
+    return M;
+  };
+  // C and R accumulated over the passes: X_0 = Q C + Qhat R
+  SqMat Cacc = Cm(0), Racc = Rm(0);
+  for (int p = 1; p < passes; ++p) {
+    SqMat Cp = Cm(p), Rp = Rm(p), Cn(std::max(k, sk)), Rn(sk);
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < sk; ++j) {
+        cd acc = Cacc(i, j);
+        for (int t = 0; t <= j; ++t) acc += Cp(i, t) * Racc(t, j);
+        Cn(i, j) = acc;
+      }
+    for (int i = 0; i < sk; ++i)
+      for (int j = i; j < sk; ++j) {
+        cd acc = 0.0;
+        for (int t = i; t <= j; ++t) acc += Rp(i, t) * Racc(t, j);
+        Rn(i, j) = acc;
+      }
+    Cacc = Cn;
+    Racc = Rn;
+  }
+  SqMat F(s), Psi(s);
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) {
+      const double2 b = hPsi[(size_t)i * s + j];
+      Psi(i, j) = cd(b.x, b.y);
+      if (!std::isfinite(b.x) || !std::isfinite(b.y)) {
+        ctx->err = "non-finite projected pencil";
+        return GPLHR_ENUMERIC;
+      }
+    }
+  for (int i = 0; i < k; ++i) {
+    for (int j = i; j < k; ++j) F(i, j) = ctx->RA(i, j) - ctx->sigma * ctx->RB(i, j);
+    for (int j = 0; j < sk; ++j) F(i, k + j) = Cacc(i, j);
+  }
+  for (int i = 0; i < sk; ++i)
+    for (int j = i; j < sk; ++j) F(k + i, k + j) = Racc(i, j);
+  ctx->n_qz += 1;
+  SqMat RFb;
+  if (!gplhr::ordered_qz(F, Psi, cd(0.0, 0.0), RFb, RBb, YLb, YRb, cv)) {
+    ctx->err = "QZ iteration did not converge";
+    return GPLHR_ENUMERIC;
+  }
+  RAb = SqMat(s);
+  for (int i = 0; i < s; ++i)
+    for (int j = i; j < s; ++j) RAb(i, j) = RFb(i, j) + ctx->sigma * RBb(i, j);
+  return GPLHR_OK;
 }
 
 // One pass of the while loop of Algorithm 2 (steps 6-30).  Rw holds the residual.
@@ -777,17 +888,21 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
       ctx->n, sk, kOne, ctx->AZ + k, sm, d2(-ctx->sigma), blkBZ(ctx, k).p, sm, ctx->U + k, sm);
   prof_end(ctx, ph_ax);
   CK(cudaGetLastError());
-  TRY(orth_against(ctx, Q, k, blkU(ctx, k), sk));
-  // step 24: projected pencil (U^* A Z, U^* B Z)
-  TRY(gram(ctx, blkU(ctx, 0), s, blkAZ(ctx, 0), s, blkBZ(ctx, 0), s, ctx->dPhiPsi));
-  ctx->d2h_bytes += (int64_t)2 * s * s * sizeof(double2);
-  CK(cudaMemcpyAsync(ctx->h_phipsi, ctx->dPhiPsi, (size_t)2 * s * s * sizeof(double2), cudaMemcpyDeviceToHost,
-                     ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
+  TRY(orth_against(ctx, Q, k, blkU(ctx, k), sk, {}, ctx->factored));
   SqMat RAb, RBb, YLb, YRb;
   // only the leading k + kk positions of the ordering are used (V and P)
   const int cv = k + kk;
-  TRY(host_qz(ctx, s, RAb, RBb, YLb, YRb, cv));
+  if (ctx->factored) {
+    TRY(factored_pencil_qz(ctx, s, sk, RAb, RBb, YLb, YRb, cv));
+  } else {
+    // step 24: projected pencil (U^* A Z, U^* B Z) by two Gram products
+    TRY(gram(ctx, blkU(ctx, 0), s, blkAZ(ctx, 0), s, blkBZ(ctx, 0), s, ctx->dPhiPsi));
+    ctx->d2h_bytes += (int64_t)2 * s * s * sizeof(double2);
+    CK(cudaMemcpyAsync(ctx->h_phipsi, ctx->dPhiPsi, (size_t)2 * s * s * sizeof(double2), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    TRY(host_qz(ctx, s, RAb, RBb, YLb, YRb, cv));
+  }
   // steps 25-28: V = Z Ybar_R(:, 1:k), P = Z Ybar_R(:, k+1:k+kk), Q = U Ybar_L(:, 1:k)
   double2* hy = ctx->h_small + 6 * k * k;
   double2* hl = hy + (size_t)s * cv;
@@ -1046,12 +1161,14 @@ void free_all(gplhr_ctx* c) {
   F(c->Z); F(c->AZ); F(c->BZ); F(c->U); F(c->Pb); F(c->APb); F(c->BPb);
   F(c->Rw); F(c->Tw1); F(c->Tw2); F(c->Tw3);
   F(c->dC1); F(c->dC2); F(c->dMBa); F(c->dMAa); F(c->dYR); F(c->dYL); F(c->dPhiPsi); F(c->dGram);
-  F(c->dProjC); F(c->dRinv); F(c->gram_part); F(c->norm_part); F(c->d_norms); F(c->d_status); F(c->d_diag);
+  F(c->dProjC); F(c->dRinv); F(c->dTrackC); F(c->dTrackR); F(c->gram_part); F(c->norm_part); F(c->d_norms); F(c->d_status); F(c->d_diag);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->h_small) cudaFreeHost(c->h_small);
   if (c->h_phipsi) cudaFreeHost(c->h_phipsi);
   if (c->h_norms) cudaFreeHost(c->h_norms);
   if (c->h_diag) cudaFreeHost(c->h_diag);
+  if (c->h_track) cudaFreeHost(c->h_track);
+  if (c->h_status) cudaFreeHost(c->h_status);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -1085,6 +1202,10 @@ gplhr_status allocate(gplhr_ctx* ctx) {
   CK(cudaMalloc(&ctx->dGram, 2 * s2));
   CK(cudaMalloc(&ctx->dProjC, 2 * s2));
   CK(cudaMalloc(&ctx->dRinv, 3 * s2));
+  CK(cudaMalloc(&ctx->dTrackC, 3 * s2));
+  CK(cudaMalloc(&ctx->dTrackR, 3 * s2));
+  CK(cudaMallocHost(&ctx->h_track, 6 * s2));
+  CK(cudaMallocHost(&ctx->h_status, 4 * sizeof(int)));
   ctx->gram_part_elems = (size_t)(4 * ctx->num_sms + 8) * gplhr::GRAM_THREADS * 8;
   ctx->gram_part_elems = std::max(ctx->gram_part_elems, 2 * sm * sm);
   CK(cudaMalloc(&ctx->gram_part, ctx->gram_part_elems * sizeof(double2)));
@@ -1246,6 +1367,7 @@ gplhr_status gplhr_create(const gplhr_csr* A, const gplhr_csr* B, double sigma_r
     ctx->mixed = opts->precision == GPLHR_MIXED;
     if (opts->switch_tol > 0) ctx->switch_tol = opts->switch_tol;
     if (opts->stall_iters != 0) ctx->stall_iters = opts->stall_iters;
+    ctx->factored = opts->pencil == 0;
     if (opts->precision != GPLHR_FP64 && opts->precision != GPLHR_MIXED) {
       g_create_error = "opts.precision must be GPLHR_FP64 or GPLHR_MIXED";
       delete ctx;

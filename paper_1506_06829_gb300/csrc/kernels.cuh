@@ -798,12 +798,12 @@ __global__ void reciprocal_kernel(int n, double2* __restrict__ d) {
 // retries once on G + shift I with shift = 11 (n w + w (w+1)) u ||G||_F (the shift of
 // shifted Cholesky QR, Fukaya et al. 2020) and sets status[0] = 1 (shift used);
 // status[0] = 2 if that fails too.  fallback_counter[0] counts shifted retries and
-// fallback_counter[1] final failures.  When `skip_if_zero` is non-null and *skip_if_zero
+// fallback_counter[1] final failures.  Rout (may be null) receives R itself.  When `skip_if_zero` is non-null and *skip_if_zero
 // is 0, the kernel writes the identity and returns (used for the conditional third
 // pass of shifted Cholesky QR).
 __global__ void chol_inv_kernel(int w, int64_t n, const double2* __restrict__ G,
                                 double2* __restrict__ Rinv, int* status, const int* skip_if_zero,
-                                int* fallback_counter) {
+                                int* fallback_counter, double2* __restrict__ Rout) {
   extern __shared__ double2 sm[];
   double2* a = sm;              // w x w working copy -> R (upper)
   double2* inv = sm + w * w;    // w x w -> R^{-1}
@@ -894,6 +894,7 @@ __global__ void chol_inv_kernel(int w, int64_t n, const double2* __restrict__ G,
   for (int e = tid; e < w * w; e += nt) {
     const int i = e / w, j = e - i * w;
     Rinv[e] = (j >= i) ? inv[e] : make_double2(0.0, 0.0);
+    if (Rout) Rout[e] = (j >= i) ? a[e] : make_double2(0.0, 0.0);
   }
 }
 

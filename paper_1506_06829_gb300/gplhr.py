@@ -46,7 +46,7 @@ class Precond(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("precision", C.c_int32),
                 ("no_lock", C.c_int32), ("products", C.c_int32), ("stream", C.c_void_p),
-                ("switch_tol", C.c_double), ("stall_iters", C.c_int32), ("reserved", C.c_int32)]
+                ("switch_tol", C.c_double), ("stall_iters", C.c_int32), ("pencil", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -145,7 +145,8 @@ PRODUCTS = {"auto": 0, "combine": 1, "spmm": 2}
 def gplhr_create(A, B, sigma: complex, k: int, m: int, precond: str = "none",
                  block_size: int = 1, T=None, tol: float = 1e-8, maxit: int = 500,
                  lock: bool = True, stream: int = 0, products: str = "auto",
-                 precision: str = "fp64", switch_tol: float = 1e-5, stall_iters: int = 5):
+                 precision: str = "fp64", switch_tol: float = 1e-5, stall_iters: int = 5,
+                 pencil: str = "factored"):
     """Returns an opaque context handle (int).  A, B: SciPy CSR (B None = identity)."""
     L = lib()
     hA = _HostCsr(A)
@@ -153,7 +154,8 @@ def gplhr_create(A, B, sigma: complex, k: int, m: int, precond: str = "none",
     hT = _HostCsr(T.astype(np.complex128)) if T is not None else None
     pc = Precond(PREC[precond], block_size, C.pointer(hT.desc) if hT else None)
     opts = Opts(tol, maxit, {"fp64": 0, "mixed": 1}[precision], 0 if lock else 1,
-                PRODUCTS[products], stream or None, switch_tol, stall_iters, 0)
+                PRODUCTS[products], stream or None, switch_tol, stall_iters,
+                {"factored": 0, "gram": 1}[pencil])
     out = C.c_void_p()
     st = L.gplhr_create(C.byref(hA.desc), C.byref(hB.desc) if hB else None, sigma.real,
                         sigma.imag, k, m, C.byref(pc), C.byref(opts), C.byref(out))
@@ -345,10 +347,10 @@ class GPLHR:
 
     def __init__(self, A, B, sigma, k, m, precond="none", block_size=1, T=None, tol=1e-8,
                  maxit=500, lock=True, stream=0, products="auto", precision="fp64",
-                 switch_tol=1e-5, stall_iters=5):
+                 switch_tol=1e-5, stall_iters=5, pencil="factored"):
         self.n, self.k = A.shape[0], k
         self.ctx = gplhr_create(A, B, complex(sigma), k, m, precond, block_size, T, tol, maxit,
-                                lock, stream, products, precision, switch_tol, stall_iters)
+                                lock, stream, products, precision, switch_tol, stall_iters, pencil)
 
     def solve(self, V0=None, seed=0, allow_notconv=False):
         return gplhr_solve(self.ctx, V0, seed, allow_notconv)

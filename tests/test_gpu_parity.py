@@ -169,14 +169,14 @@ def _compare_solutions(res_o, vec_g, k, tol, lam_rtol=1e-8, ang_tol=1e-6):
     assert np.max(vec_g["resid"]) <= tol
 
 
-@pytest.mark.parametrize("products", ["combine", "spmm"])
-def test_solve_parity_schroedinger_small(products):
+@pytest.mark.parametrize("products,pencil", [("combine", "gram"), ("spmm", "factored"), ("spmm", "gram")])
+def test_solve_parity_schroedinger_small(products, pencil):
     pr = P.config3(24)
     o = OG.solve(pr.A, None, pr.sigma, pr.start_block(), m=pr.m, tol=pr.tol, maxit=300,
                  precond=pr.precond, block_size=pr.block_size)
     assert o.converged
     with G.GPLHR(pr.A, None, pr.sigma, pr.k, pr.m, pr.precond, pr.block_size, tol=pr.tol,
-                 maxit=300, products=products) as s:
+                 maxit=300, products=products, pencil=pencil) as s:
         info = s.solve(pr.start_block())
         vec = s.vectors()
     assert info.iters <= 2 * o.iters + 5
@@ -220,8 +220,9 @@ def test_solve_parity_generalized_exact_preconditioner():
     assert np.linalg.norm(Q.conj().T @ Q - np.eye(k)) <= 1e-12
 
 
-@pytest.mark.parametrize("products", ["combine", "spmm"])
-def test_one_step_parity_generalized_block_jacobi(products):
+@pytest.mark.parametrize("products,pencil", [("combine", "gram"), ("spmm", "gram"), ("combine", "factored"),
+                                            ("spmm", "factored")])
+def test_one_step_parity_generalized_block_jacobi(products, pencil):
     """Same start block, same number of iterations: the Ritz values and the nested
     Schur subspaces of the GPU iterate equal the oracle's (orth and QZ bases differ
     only by unitary factors that the harmonic projection removes)."""
@@ -235,7 +236,7 @@ def test_one_step_parity_generalized_block_jacobi(products):
     pen = OG.Pencil(A, B, sigma, T)
     st = OG.init_state(pen, V0, m)
     with G.GPLHR(A, B, sigma, k, m, "block_jacobi", 8, tol=1e-14, maxit=10, lock=False,
-                 products=products) as s:
+                 products=products, pencil=pencil) as s:
         s.start(V0)
         for it in range(3):
             st = OG.iterate(pen, st)
