@@ -263,10 +263,11 @@ class Result:
 
 def solve(A, B, sigma, V0, m: int = 1, tol: float = 1e-8, maxit: int = 500,
           precond: str = "none", block_size: int = 1, T: Preconditioner | None = None,
-          lock: bool = True, callback=None) -> Result:
-    """Run Algorithm 2 until all k pairs meet ``tol`` or ``maxit`` iterations."""
+          lock: bool = True, callback=None, inner_steps: int = 0) -> Result:
+    """Run Algorithm 2 until all k pairs meet ``tol`` or ``maxit`` iterations.
+    inner_steps > 0: T is that many block GMRES steps preconditioned by ``precond``."""
     if T is None:
-        T = build_precond(A, B, sigma, precond, block_size)
+        T = build_precond(A, B, sigma, precond, block_size, inner_steps)
     pen = Pencil(A, B, sigma, T)
     st = init_state(pen, V0, m)
     k = st.k

@@ -47,7 +47,18 @@ def shifted(A: sp.spmatrix, B, sigma: complex) -> sp.csr_matrix:
     return sp.csr_matrix(A.astype(np.complex128) - sigma * Bm.astype(np.complex128))
 
 
-def build(A, B, sigma: complex, kind: str, bs: int = 1) -> Preconditioner:
+def build(A, B, sigma: complex, kind: str, bs: int = 1, inner_steps: int = 0):
+    """The preconditioner of kind (with block size bs); inner_steps > 0 wraps it as the
+    basic preconditioner T0 of that many block GMRES steps on (A - sigma B) w = r
+    (oracle.gmres)."""
+    T0 = _build(A, B, sigma, kind, bs)
+    if inner_steps > 0:
+        from .gmres import BlockGmres
+        return BlockGmres(shifted(A, B, sigma), T0, inner_steps)
+    return T0
+
+
+def _build(A, B, sigma: complex, kind: str, bs: int = 1) -> Preconditioner:
     if kind == "none":
         return Preconditioner("identity")
     K = shifted(A, B, sigma)
