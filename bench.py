@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision runs")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload run")
+    ap.add_argument("--inner-steps", type=int, default=4,
+                    help="block GMRES steps of the inner-solve preconditioner in the extra "
+                         "time-to-pairs runs (0 = skip them)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="arithmetic of the headline run (mixed: FP32 bulk phase held)")
     ap.add_argument("--grid", type=int, default=0,
@@ -273,6 +276,10 @@ def main():
         line["solve"] = time_to_pairs(G, stream, "fp64")
         if not args.no_mixed:
             line["solve_mixed"] = time_to_pairs(G, stream, "mixed")
+        if args.inner_steps > 0:
+            line["solve_gmres"] = time_to_pairs(G, stream, "fp64", args.inner_steps)
+            if not args.no_mixed:
+                line["solve_gmres_mixed"] = time_to_pairs(G, stream, "mixed", args.inner_steps)
     if rank == 0 and not args.no_cpu:
         sample = 3
         spi = oracle_iterations(pr, sample, 0)
@@ -384,13 +391,14 @@ def batched_throughput(G, K):
             "status": int(st)}
 
 
-def time_to_pairs(G, stream, precision):
-    """Seconds to k eigenpairs at the residual target, complex-scaled Schroedinger 256^2."""
+def time_to_pairs(G, stream, precision, inner_steps=0):
+    """Seconds to k eigenpairs at the residual target, complex-scaled Schroedinger 256^2
+    (inner_steps > 0: T = that many block GMRES steps around the block-Jacobi T0)."""
     import torch
     from paper_1506_06829_gb300 import problems as P
     pr = P.config3()
     s = G.GPLHR(pr.A, None, pr.sigma, pr.k, pr.m, pr.precond, pr.block_size, tol=pr.tol,
-                maxit=2000, stream=stream.cuda_stream, precision=precision)
+                maxit=2000, stream=stream.cuda_stream, precision=precision, inner_steps=inner_steps)
     V0 = torch.from_numpy(pr.start_block()).to("cuda")
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -403,7 +411,8 @@ def time_to_pairs(G, stream, precision):
     return {"workload": f"{pr.name} (complex-scaled Schroedinger, n = {pr.n}, k = {pr.k}, m = {pr.m}, "
                         f"block-Jacobi {pr.block_size}, tol {pr.tol})",
             "s_to_k_pairs": e0.elapsed_time(e1) / 1e3, "iterations": info.iters,
-            "precision": precision, "fp32_iterations": info.fp32_iters,
+            "precision": precision, "fp32_iterations": info.fp32_iters, "inner_gmres_steps": inner_steps,
+            "sparse_products": info.n_spmm, "preconditioner_applications": info.n_prec,
             "converged": bool(info.nconv == pr.k), "max_resid": float(max(vec["resid"]))}
 
 

@@ -84,11 +84,19 @@ typedef struct {
  * [b bs, (b+1) bs) (the last block is n mod bs wide when bs does not divide n).
  * JACOBI with a constant diagonal (relative spread <= 1e-12) is T = I: every output
  * of T goes through a projector and orth(), so a constant scaling of T leaves the
- * iteration unchanged.  CSR: T is applied as a sparse product with matrix T_csr. */
+ * iteration unchanged.  CSR: T is applied as a sparse product with matrix T_csr.
+ * inner_steps s > 0 (Sec. 4, an inner solve as T): T R = T0 Y*, s steps of block GMRES
+ * on (A - sigma B) W = R with zero start, right-preconditioned by the preconditioner T0
+ * that kind / block_size / T_csr describe: Y* minimises ||R - (A - sigma B) T0 Y||_F
+ * over the block Krylov space span{R, ((A - sigma B) T0) R, ...} of s blocks (block
+ * Arnoldi on the device, the small least-squares problem on the host).  Needs
+ * s <= 32 and s k <= 384 (EINVAL otherwise); each application of T costs s sparse
+ * products with A and B and s applications of T0. */
 typedef struct {
   int32_t kind;
   int32_t block_size;
   const gplhr_csr* T_csr;
+  int32_t inner_steps;
 } gplhr_precond;
 
 /* Solver options.  Zero-initialised fields take the defaults in brackets. */
@@ -130,6 +138,8 @@ typedef struct {
   int64_t h2d_bytes;    /* host->device bytes moved by the iteration since start        */
   int64_t d2h_bytes;    /* device->host bytes (projected pencil for the host QZ, norms) */
   double resid[64];     /* first min(k, 64) residuals                                  */
+  int64_t n_inner;      /* inner block GMRES steps (T.inner_steps per application of T;
+                           their sparse products are counted in n_spmm)                 */
 } gplhr_info;
 
 typedef struct gplhr_ctx gplhr_ctx;

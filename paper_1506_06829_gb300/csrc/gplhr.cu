@@ -86,7 +86,18 @@ struct gplhr_ctx {
   double2* dTrackR = nullptr;  // 3 x s_max^2: Cholesky factors of each orth pass
   double2* h_track = nullptr;  // pinned copies of the two above
   int* h_status = nullptr;
+  size_t trk = 0;              // stride of the passes in dTrackC (>= s_max^2)
   bool factored = true;        // projected pencil from U's factors (one Gram)
+  // inner block GMRES (T = gm_steps steps on (A - sigma B) W = R, right-preconditioned
+  // by the basic preconditioner prec)
+  int gm_steps = 0;
+  double2* gmV = nullptr;      // n x (gm_steps + 1) k, ld (gm_steps + 1) k: block Krylov basis
+  double2 *gmT = nullptr, *gmAX = nullptr, *gmBX = nullptr;  // n x k
+  double2* gmY = nullptr;      // gm_steps k x k: least-squares solution
+  double2* h_gm = nullptr;     // pinned, per step: tracks C (3 trk) and R (3 k^2)
+  int* h_gm_status = nullptr;  // pinned, per step: Cholesky status of its first pass
+  double2* h_gmY = nullptr;    // pinned staging of gmY
+  int64_t n_inner = 0;         // inner GMRES steps run
   double2* gram_part = nullptr;
   size_t gram_part_elems = 0;
   double* norm_part = nullptr;
@@ -132,6 +143,7 @@ namespace {
     if (s_ != GPLHR_OK) return s_;     \
   } while (0)
 
+const size_t kCombSmemMax = 200 * 1024;  // dynamic shared memory opted into per CTA
 const double2 kOne = {1.0, 0.0};
 const double2 kMinusOne = {-1.0, 0.0};
 
@@ -171,105 +183,108 @@ void prof_end(gplhr_ctx* ctx, int h) {
 
 // ------------------------------------------------------------------ launches --
 
-template <typename T>
-gplhr_status launch_spmm_t(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, Blk X, int w, Blk Y, Blk Y2);
-
+gplhr_status launch_spmm_f64(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, Blk X, int w, Blk Y, Blk Y2);
 gplhr_status launch_spmm_f32(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, Blk X, int w, Blk Y, Blk Y2);
-
 gplhr_status launch_spmm_one(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, Blk X, int w, Blk Y, Blk Y2,
                              bool fp32 = false) {
-  return fp32 ? launch_spmm_f32(ctx, M, M2, X, w, Y, Y2) : launch_spmm_t<double>(ctx, M, M2, X, w, Y, Y2);
+  return fp32 ? launch_spmm_f32(ctx, M, M2, X, w, Y, Y2) : launch_spmm_f64(ctx, M, M2, X, w, Y, Y2);
+}
+
+// One launch of the row-group SpMM for a block of w <= 32 V columns: G lanes per row,
+// the power of two >= ceil(w / V), at least 4.
+template <typename T, int V, typename VTA, typename VTB>
+void launch_spmm_g(gplhr_ctx* ctx, gplhr::CsrDev<VTA> a, gplhr::CsrDev<VTB> b, int hasB,
+                   const gplhr::cplx<T>* X, int ldx, int w, double2* Y, int ldy, double2* Y2, int ldy2) {
+  int G = 4;
+  while (G * V < w) G <<= 1;
+  const int rows_per_cta = (gplhr::SPMM_THREADS / 32) * (32 / G);
+  const int grid = grid_for((size_t)ctx->n, rows_per_cta, 8 * ctx->num_sms);
+  const int nt = gplhr::SPMM_THREADS;
+  switch (G) {
+    case 4:
+      gplhr::spmm_kernel<VTA, VTB, T, 4, V><<<grid, nt, 0, ctx->stream>>>(ctx->n, a, b, hasB, X, ldx, w, Y, ldy, Y2, ldy2);
+      break;
+    case 8:
+      gplhr::spmm_kernel<VTA, VTB, T, 8, V><<<grid, nt, 0, ctx->stream>>>(ctx->n, a, b, hasB, X, ldx, w, Y, ldy, Y2, ldy2);
+      break;
+    case 16:
+      gplhr::spmm_kernel<VTA, VTB, T, 16, V><<<grid, nt, 0, ctx->stream>>>(ctx->n, a, b, hasB, X, ldx, w, Y, ldy, Y2,
+                                                                         ldy2);
+      break;
+    default:
+      gplhr::spmm_kernel<VTA, VTB, T, 32, V><<<grid, nt, 0, ctx->stream>>>(ctx->n, a, b, hasB, X, ldx, w, Y, ldy, Y2,
+                                                                         ldy2);
+      break;
+  }
+}
+
+// Dispatch on the value types of M (and M2): real or complex values, stored as VR / VC.
+template <typename T, int V, typename VR, typename VC>
+void launch_spmm_types(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, const void* mval, const void* m2val,
+                       const gplhr::cplx<T>* X, int ldx, int w, double2* Y, int ldy, double2* Y2, int ldy2) {
+  gplhr::CsrDev<VR> ar{M.rowptr, M.col, (const VR*)mval};
+  gplhr::CsrDev<VC> ac{M.rowptr, M.col, (const VC*)mval};
+  if (!M2) {
+    if (M.dtype == GPLHR_R64)
+      launch_spmm_g<T, V>(ctx, ar, ar, 0, X, ldx, w, Y, ldy, nullptr, 0);
+    else
+      launch_spmm_g<T, V>(ctx, ac, ac, 0, X, ldx, w, Y, ldy, nullptr, 0);
+    return;
+  }
+  gplhr::CsrDev<VR> br{M2->rowptr, M2->col, (const VR*)m2val};
+  gplhr::CsrDev<VC> bc{M2->rowptr, M2->col, (const VC*)m2val};
+  if (M.dtype == GPLHR_R64 && M2->dtype == GPLHR_R64)
+    launch_spmm_g<T, V>(ctx, ar, br, 1, X, ldx, w, Y, ldy, Y2, ldy2);
+  else if (M.dtype == GPLHR_R64)
+    launch_spmm_g<T, V>(ctx, ar, bc, 1, X, ldx, w, Y, ldy, Y2, ldy2);
+  else if (M2->dtype == GPLHR_R64)
+    launch_spmm_g<T, V>(ctx, ac, br, 1, X, ldx, w, Y, ldy, Y2, ldy2);
+  else
+    launch_spmm_g<T, V>(ctx, ac, bc, 1, X, ldx, w, Y, ldy, Y2, ldy2);
+}
+
+// Algorithmic flops and bytes of one sparse product: values (vb bytes real, 2 vb
+// complex) and int32 indices read once, row pointers once, the output written once
+// (complex128).  The caller adds the reads of the input block.
+void spmm_cost(gplhr_ctx* ctx, const DevCsr& D, int w, double vb, double& fl, double& by) {
+  const bool cplx = D.dtype == GPLHR_C128;
+  fl += (cplx ? 8.0 : 4.0) * (double)D.nnz * w;  // real x complex = 2 FMA
+  by += (double)D.nnz * ((cplx ? 2.0 : 1.0) * vb + 4.0) + 4.0 * (ctx->n + 1.0) + 16.0 * ctx->n * w;
 }
 
 // FP32 sparse products: the input block is converted to complex64 once (the
 // double -> float conversion runs on the FP64 pipe, and a gather touches each input
-// row once per nonzero), and the matrix values come from their FP32 copies.
+// row once per nonzero), into rows of even length (16-byte aligned for the two-column
+// loads), and the matrix values come from their FP32 copies.
 gplhr_status launch_spmm_f32(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, Blk X, int w, Blk Y, Blk Y2) {
-  if (!M.val32 || (M2 && !M2->val32) || !ctx->X32 || w > ctx->k) return launch_spmm_t<double>(ctx, M, M2, X, w, Y, Y2);
-  const int threads = 256;
-  const int grid = grid_for((size_t)ctx->n, threads / 32, ctx->num_sms * 16);
-  auto mat_cost = [&](const DevCsr& D, double& fl, double& by) {
-    const bool cplx = D.dtype == GPLHR_C128;
-    fl += (cplx ? 8.0 : 4.0) * (double)D.nnz * w;
-    by += (double)D.nnz * ((cplx ? 8.0 : 4.0) + 4.0) + 4.0 * (ctx->n + 1.0) + 16.0 * ctx->n * w;
-  };
-  double fl = 0.0, by = 16.0 * ctx->n * w + 8.0 * ctx->n * w;
-  mat_cost(M, fl, by);
-  if (M2) mat_cost(*M2, fl, by);
+  if (!M.val32 || (M2 && !M2->val32) || !ctx->X32 || w > ctx->k) return launch_spmm_f64(ctx, M, M2, X, w, Y, Y2);
+  const int ld32 = (w + 1) & ~1;
+  // the conversion reads 16 and writes 8 bytes per element; the products read 8
+  double fl = 0.0, by = (16.0 + 8.0 + 8.0) * ctx->n * w;
+  spmm_cost(ctx, M, w, 4.0, fl, by);
+  if (M2) spmm_cost(ctx, *M2, w, 4.0, fl, by);
   const int ph = prof_begin(ctx, KC_SPMM, fl, by, 2);
   gplhr::to_c64_kernel<<<grid_for((size_t)ctx->n * w, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-      ctx->n, w, X.p, X.ld, ctx->X32);
-  gplhr::CsrDev<float> ar{M.rowptr, M.col, (const float*)M.val32};
-  gplhr::CsrDev<float2> ac{M.rowptr, M.col, (const float2*)M.val32};
-  const float2* X32 = ctx->X32;
-  if (!M2) {
-    gplhr::CsrDev<float> none{nullptr, nullptr, nullptr};
-    if (M.dtype == GPLHR_R64)
-      gplhr::spmm_kernel<float, float, float, float2><<<grid, threads, 0, ctx->stream>>>(
-          ctx->n, ar, none, 0, X32, w, w, Y.p, Y.ld, nullptr, 0);
-    else
-      gplhr::spmm_kernel<float2, float, float, float2><<<grid, threads, 0, ctx->stream>>>(
-          ctx->n, ac, none, 0, X32, w, w, Y.p, Y.ld, nullptr, 0);
-  } else {
-    gplhr::CsrDev<float> br{M2->rowptr, M2->col, (const float*)M2->val32};
-    gplhr::CsrDev<float2> bc{M2->rowptr, M2->col, (const float2*)M2->val32};
-    if (M.dtype == GPLHR_R64 && M2->dtype == GPLHR_R64)
-      gplhr::spmm_kernel<float, float, float, float2><<<grid, threads, 0, ctx->stream>>>(
-          ctx->n, ar, br, 1, X32, w, w, Y.p, Y.ld, Y2.p, Y2.ld);
-    else if (M.dtype == GPLHR_R64)
-      gplhr::spmm_kernel<float, float2, float, float2><<<grid, threads, 0, ctx->stream>>>(
-          ctx->n, ar, bc, 1, X32, w, w, Y.p, Y.ld, Y2.p, Y2.ld);
-    else if (M2->dtype == GPLHR_R64)
-      gplhr::spmm_kernel<float2, float, float, float2><<<grid, threads, 0, ctx->stream>>>(
-          ctx->n, ac, br, 1, X32, w, w, Y.p, Y.ld, Y2.p, Y2.ld);
-    else
-      gplhr::spmm_kernel<float2, float2, float, float2><<<grid, threads, 0, ctx->stream>>>(
-          ctx->n, ac, bc, 1, X32, w, w, Y.p, Y.ld, Y2.p, Y2.ld);
+      ctx->n, w, X.p, X.ld, ctx->X32, ld32);
+  for (int c0 = 0; c0 < w; c0 += 64) {
+    const int wc = std::min(64, w - c0);
+    launch_spmm_types<float, 2, float, float2>(ctx, M, M2, M.val32, M2 ? M2->val32 : nullptr, ctx->X32 + c0, ld32,
+                                               wc, Y.p + c0, Y.ld, M2 ? Y2.p + c0 : nullptr, Y2.ld);
   }
   prof_end(ctx, ph);
   CK(cudaGetLastError());
   return GPLHR_OK;
 }
 
-template <typename T>
-gplhr_status launch_spmm_t(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, Blk X, int w, Blk Y, Blk Y2) {
-  const int threads = 256;
-  const int grid = grid_for((size_t)ctx->n, threads / 32, ctx->num_sms * 16);
-  const bool has2 = M2 != nullptr;
-  auto mat_cost = [&](const DevCsr& D, double& fl, double& by) {
-    const bool cplx = D.dtype == GPLHR_C128;
-    fl += (cplx ? 8.0 : 4.0) * (double)D.nnz * w;                 // real x complex = 2 FMA
-    by += (double)D.nnz * ((cplx ? 16.0 : 8.0) + 4.0) + 4.0 * (ctx->n + 1.0) + 16.0 * ctx->n * w;
-  };
-  double fl = 0.0, by = 16.0 * ctx->n * w;  // X read once
-  mat_cost(M, fl, by);
-  if (has2) mat_cost(*M2, fl, by);
-  const int ph = prof_begin(ctx, KC_SPMM, fl, by);
-  gplhr::CsrDev<double> dr{M.rowptr, M.col, (const double*)M.val};
-  gplhr::CsrDev<double2> dc{M.rowptr, M.col, (const double2*)M.val};
-  if (!has2) {
-    gplhr::CsrDev<double> none{nullptr, nullptr, nullptr};
-    if (M.dtype == GPLHR_R64)
-      gplhr::spmm_kernel<double, double, T><<<grid, threads, 0, ctx->stream>>>(ctx->n, dr, none, 0, X.p, X.ld, w,
-                                                                            Y.p, Y.ld, nullptr, 0);
-    else
-      gplhr::spmm_kernel<double2, double, T><<<grid, threads, 0, ctx->stream>>>(ctx->n, dc, none, 0, X.p, X.ld, w,
-                                                                             Y.p, Y.ld, nullptr, 0);
-  } else {
-    gplhr::CsrDev<double> br{M2->rowptr, M2->col, (const double*)M2->val};
-    gplhr::CsrDev<double2> bc{M2->rowptr, M2->col, (const double2*)M2->val};
-    if (M.dtype == GPLHR_R64 && M2->dtype == GPLHR_R64)
-      gplhr::spmm_kernel<double, double, T><<<grid, threads, 0, ctx->stream>>>(ctx->n, dr, br, 1, X.p, X.ld, w, Y.p,
-                                                                            Y.ld, Y2.p, Y2.ld);
-    else if (M.dtype == GPLHR_R64)
-      gplhr::spmm_kernel<double, double2, T><<<grid, threads, 0, ctx->stream>>>(ctx->n, dr, bc, 1, X.p, X.ld, w, Y.p,
-                                                                             Y.ld, Y2.p, Y2.ld);
-    else if (M2->dtype == GPLHR_R64)
-      gplhr::spmm_kernel<double2, double, T><<<grid, threads, 0, ctx->stream>>>(ctx->n, dc, br, 1, X.p, X.ld, w, Y.p,
-                                                                             Y.ld, Y2.p, Y2.ld);
-    else
-      gplhr::spmm_kernel<double2, double2, T><<<grid, threads, 0, ctx->stream>>>(ctx->n, dc, bc, 1, X.p, X.ld, w,
-                                                                              Y.p, Y.ld, Y2.p, Y2.ld);
+gplhr_status launch_spmm_f64(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, Blk X, int w, Blk Y, Blk Y2) {
+  double fl = 0.0, by = 16.0 * ctx->n * w;  // the block, read once for both products
+  spmm_cost(ctx, M, w, 8.0, fl, by);
+  if (M2) spmm_cost(ctx, *M2, w, 8.0, fl, by);
+  const int ph = prof_begin(ctx, KC_SPMM, fl, by, (w + 31) / 32);
+  for (int c0 = 0; c0 < w; c0 += 32) {
+    const int wc = std::min(32, w - c0);
+    launch_spmm_types<double, 1, double, double2>(ctx, M, M2, M.val, M2 ? M2->val : nullptr, X.p + c0, X.ld, wc,
+                                                  Y.p + c0, Y.ld, M2 ? Y2.p + c0 : nullptr, Y2.ld);
   }
   prof_end(ctx, ph);
   CK(cudaGetLastError());
@@ -379,12 +394,19 @@ gplhr_status combine(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, b
   a.beta_one = beta_one ? 1 : 0;
   a.skip = skip;
   a.upper = (upper && !use32 && a.nin == 1 && ins[0].w == c && c_store == c && c_split == c) ? 1 : 0;
-  const int rows_tile = gplhr::comb_rows_tile(c, a.upper);
+  int rows_tile = gplhr::comb_rows_tile(c, a.upper);
+  const size_t esz = use32 ? sizeof(float2) : sizeof(double2);
+  auto smem_of = [&](int rt) { return (size_t)(wsum * c + rt * wsum + rt * c) * esz; };
+  while (!a.upper && rows_tile > 1 && smem_of(rows_tile) > kCombSmemMax) rows_tile /= 2;
+  if (smem_of(rows_tile) > kCombSmemMax) {
+    ctx->err = "combine: coefficient block too large for shared memory";
+    return GPLHR_EINVAL;
+  }
+  a.rows_tile = rows_tile;
   const int grid = grid_for((size_t)ctx->n, std::max(rows_tile, 64), 4 * ctx->num_sms);
   const int rows_per_cta = (ctx->n + grid - 1) / grid;
   a.normpart = c_store < c ? ctx->norm_part : nullptr;
-  const size_t smem =
-      (size_t)(wsum * c + rows_tile * wsum + rows_tile * c) * (use32 ? sizeof(float2) : sizeof(double2));
+  const size_t smem = smem_of(rows_tile);
   double by = 16.0 * ctx->n * (wsum + c_store * (beta_one ? 2.0 : 1.0));
   const double macs = a.upper ? 0.5 * c * (c + 1.0) : (double)wsum * c;
   const int ph = prof_begin(ctx, KC_COMBINE, count ? 8.0 * ctx->n * macs : 0.0, count ? by : 0.0,
@@ -405,9 +427,10 @@ gplhr_status combine(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, b
 
 gplhr_status precond_apply_impl(gplhr_ctx* ctx, Blk X, int w, Blk Y);
 
-gplhr_status precond_apply(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
-  if (w <= 0) return GPLHR_OK;
-  ctx->n_prec += 1;
+gplhr_status gmres_apply(gplhr_ctx* ctx, Blk X, int w, Blk Y);
+
+// The basic preconditioner T0 (Jacobi, block-Jacobi, CSR or I).
+gplhr_status precond_apply_t0(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
   if (ctx->prec == GPLHR_PREC_CSR) return precond_apply_impl(ctx, X, w, Y);  // counted as SpMM
   const double n = ctx->n;
   double fl = 0.0, by = 32.0 * n * w;
@@ -422,6 +445,13 @@ gplhr_status precond_apply(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
   gplhr_status st = precond_apply_impl(ctx, X, w, Y);
   prof_end(ctx, ph);
   return st;
+}
+
+// Y = T X: T0, or the inner block GMRES around it.
+gplhr_status precond_apply(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
+  if (w <= 0) return GPLHR_OK;
+  ctx->n_prec += 1;
+  return ctx->gm_steps > 0 ? gmres_apply(ctx, X, w, Y) : precond_apply_t0(ctx, X, w, Y);
 }
 
 gplhr_status precond_apply_impl(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
@@ -510,7 +540,7 @@ gplhr_status orth_against(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w, const std
     if (wl > 0) {
       TRY(gram(ctx, L, wl, X, w, none, 0, ctx->dProjC, skip, false, cnt, ctx->bulk32));
       if (track)
-        CK(cudaMemcpyAsync(ctx->dTrackC + (size_t)pass * smax2, ctx->dProjC, (size_t)wl * w * sizeof(double2),
+        CK(cudaMemcpyAsync(ctx->dTrackC + (size_t)pass * ctx->trk, ctx->dProjC, (size_t)wl * w * sizeof(double2),
                            cudaMemcpyDeviceToDevice, ctx->stream));
       TRY(combine(ctx, {In{L, wl, ctx->dProjC, kMinusOne}}, X, w, true, skip, none, -1, -1, cnt));
       for (const Extra& e : ex)
@@ -530,6 +560,114 @@ gplhr_status orth_against(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w, const std
       TRY(combine(ctx, {In{e.E, w, Rinv, kOne}}, e.E, w, false, skip, none, -1, -1, cnt, -1, true));
   }
   return GPLHR_OK;
+}
+
+// Accumulated factors of one tracked orth_against call from its passes' coefficients C_p
+// (wl x w) and Cholesky factors R_p (w x w): X_0 = L C + X_final R with
+// C = C_0 + C_1 R_0 [+ C_2 R_1 R_0] and R = R_1 R_0 [R_2 R_1 R_0].
+void accumulate_tracks(const double2* hC, size_t strideC, const double2* hR, size_t strideR, int passes, int wl,
+                       int w, std::vector<cd>& C, std::vector<cd>& R) {
+  auto c_of = [&](int p, int i, int j) { const double2 v = hC[p * strideC + (size_t)i * w + j]; return cd(v.x, v.y); };
+  auto r_of = [&](int p, int i, int j) { const double2 v = hR[p * strideR + (size_t)i * w + j]; return cd(v.x, v.y); };
+  C.assign((size_t)wl * w, cd(0.0, 0.0));
+  R.assign((size_t)w * w, cd(0.0, 0.0));
+  for (int i = 0; i < wl; ++i)
+    for (int j = 0; j < w; ++j) C[(size_t)i * w + j] = c_of(0, i, j);
+  for (int i = 0; i < w; ++i)
+    for (int j = i; j < w; ++j) R[(size_t)i * w + j] = r_of(0, i, j);
+  for (int p = 1; p < passes; ++p) {
+    std::vector<cd> Cn((size_t)wl * w), Rn((size_t)w * w, cd(0.0, 0.0));
+    for (int i = 0; i < wl; ++i)
+      for (int j = 0; j < w; ++j) {
+        cd acc = C[(size_t)i * w + j];
+        for (int t = 0; t <= j; ++t) acc += c_of(p, i, t) * R[(size_t)t * w + j];
+        Cn[(size_t)i * w + j] = acc;
+      }
+    for (int i = 0; i < w; ++i)
+      for (int j = i; j < w; ++j) {
+        cd acc = 0.0;
+        for (int t = i; t <= j; ++t) acc += r_of(p, i, t) * R[(size_t)t * w + j];
+        Rn[(size_t)i * w + j] = acc;
+      }
+    C.swap(Cn);
+    R.swap(Rn);
+  }
+}
+
+// T R by s steps of block GMRES on K W = R, K = A - sigma B, zero start, right-
+// preconditioned by T0 (Sec. 4): block Arnoldi K T0 V_j = V_{j+1} H(:, j) with the
+// orthogonalisation of the sparse products (block CGS2 + Cholesky QR, tracked), then
+// Y = argmin ||E_1 B_0 - H Y||_F (R = V_1 B_0) on the host, and T R = T0 (V_s Y).
+gplhr_status gmres_apply(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
+  const int s = ctx->gm_steps, k = ctx->k, n = ctx->n;
+  const int ldv = (s + 1) * k;
+  const int smax2 = ctx->s_max * ctx->s_max;
+  const size_t per = 3 * ctx->trk + 3 * (size_t)k * k;  // pinned doubles2 per step
+  auto Vb = [&](int j) { return Blk{ctx->gmV + (size_t)j * w, ldv}; };
+  auto stash = [&](int j, int wl) -> gplhr_status {
+    double2* h = ctx->h_gm + (size_t)j * per;
+    for (int p = 0; p < 3; ++p) {
+      if (wl > 0)
+        CK(cudaMemcpyAsync(h + p * ctx->trk, ctx->dTrackC + p * ctx->trk, (size_t)wl * w * sizeof(double2),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(h + 3 * ctx->trk + (size_t)p * k * k, ctx->dTrackR + (size_t)p * smax2,
+                         (size_t)w * w * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaMemcpyAsync(ctx->h_gm_status + j, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->d2h_bytes += (int64_t)(3 * ((size_t)wl * w + (size_t)w * w)) * sizeof(double2) + sizeof(int);
+    return GPLHR_OK;
+  };
+  gplhr::copy_block_kernel<<<grid_for((size_t)n * w, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+      n, w, X.p, X.ld, Vb(0).p, ldv);
+  CK(cudaGetLastError());
+  TRY(orth_against(ctx, Blk{nullptr, 0}, 0, Vb(0), w, {}, true));
+  TRY(stash(0, 0));
+  const Blk t{ctx->gmT, k}, ax{ctx->gmAX, k}, bx{ctx->gmBX, k};
+  const double2 msig = make_double2(-ctx->sigma.real(), -ctx->sigma.imag());
+  for (int j = 1; j <= s; ++j) {
+    TRY(precond_apply_t0(ctx, Vb(j - 1), w, t));
+    TRY(spmm_AB(ctx, t, w, ax, bx));
+    const Blk b = ctx->hasB ? bx : t;
+    const int ph = prof_begin(ctx, KC_OTHER, 8.0 * n * w, 48.0 * n * w);
+    gplhr::axpby_kernel<<<grid_for((size_t)n * w, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+        n, w, kOne, ax.p, ax.ld, msig, b.p, b.ld, Vb(j).p, ldv);
+    prof_end(ctx, ph);
+    CK(cudaGetLastError());
+    TRY(orth_against(ctx, Blk{ctx->gmV, ldv}, j * w, Vb(j), w, {}, true));
+    TRY(stash(j, j * w));
+  }
+  ctx->n_inner += s;
+  CK(cudaStreamSynchronize(ctx->stream));
+  // H ((s + 1) w x s w), block column j - 1 = [C_j; R_j] of step j; E = [B_0; 0]
+  const int M = (s + 1) * w, N = s * w;
+  std::vector<cd> H((size_t)M * N, cd(0.0, 0.0)), E((size_t)M * w, cd(0.0, 0.0)), C, R, Ys;
+  for (int j = 0; j <= s; ++j) {
+    const double2* h = ctx->h_gm + (size_t)j * per;
+    const int passes = ctx->h_gm_status[j] != 0 ? 3 : 2;
+    const int wl = j * w;
+    accumulate_tracks(h, ctx->trk, h + 3 * ctx->trk, (size_t)k * k, passes, wl, w, C, R);
+    for (int a = 0; a < w * w; ++a)
+      if (!std::isfinite(R[a].real()) || !std::isfinite(R[a].imag())) {
+        ctx->err = "non-finite Krylov basis in the inner GMRES";
+        return GPLHR_ENUMERIC;
+      }
+    if (j == 0) {
+      for (int i = 0; i < w; ++i)
+        for (int c = 0; c < w; ++c) E[(size_t)i * w + c] = R[(size_t)i * w + c];
+      continue;
+    }
+    const int col0 = (j - 1) * w;
+    for (int i = 0; i < wl; ++i)
+      for (int c = 0; c < w; ++c) H[(size_t)i * N + col0 + c] = C[(size_t)i * w + c];
+    for (int i = 0; i < w; ++i)
+      for (int c = 0; c < w; ++c) H[(size_t)(wl + i) * N + col0 + c] = R[(size_t)i * w + c];
+  }
+  gplhr::least_squares(H, M, N, E, w, Ys);
+  for (int i = 0; i < N * w; ++i) ctx->h_gmY[i] = make_double2(Ys[i].real(), Ys[i].imag());
+  CK(cudaMemcpyAsync(ctx->gmY, ctx->h_gmY, (size_t)N * w * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+  ctx->h2d_bytes += (int64_t)N * w * sizeof(double2);
+  TRY(combine(ctx, {In{Blk{ctx->gmV, ldv}, N, ctx->gmY, kOne}}, t, w, false));
+  return precond_apply_t0(ctx, t, w, Y);
 }
 
 gplhr_status upload(gplhr_ctx* ctx, double2* dst, const double2* src, size_t elems) {
@@ -632,7 +770,7 @@ gplhr_status start(gplhr_ctx* ctx) {
   ctx->q = 0;
   ctx->m = ctx->m0;
   ctx->hasP = false;
-  ctx->n_spmm = ctx->n_prec = ctx->n_qz = 0;
+  ctx->n_spmm = ctx->n_prec = ctx->n_qz = ctx->n_inner = 0;
   ctx->h2d_bytes = ctx->d2h_bytes = 0;
   ctx->bulk32 = ctx->mixed;
   ctx->fp32_iters = 0;
@@ -751,7 +889,7 @@ gplhr_status factored_pencil_qz(gplhr_ctx* ctx, int s, int sk, SqMat& RAb, SqMat
   double2* hR = ctx->h_track + 3 * nC;       // 3 x nR
   CK(cudaMemcpyAsync(hPsi, ctx->dPhiPsi, (size_t)s * s * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
   for (int p = 0; p < 3; ++p) {
-    CK(cudaMemcpyAsync(hC + p * nC, ctx->dTrackC + (size_t)p * smax2, nC * sizeof(double2), cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(hC + p * nC, ctx->dTrackC + (size_t)p * ctx->trk, nC * sizeof(double2), cudaMemcpyDeviceToHost,
                        ctx->stream));
     CK(cudaMemcpyAsync(hR + p * nR, ctx->dTrackR + (size_t)p * smax2, nR * sizeof(double2), cudaMemcpyDeviceToHost,
                        ctx->stream));
@@ -942,6 +1080,7 @@ void fill_info(gplhr_ctx* ctx, gplhr_info* info) {
   info->bulk = ctx->bulk32 ? 1 : 0;
   info->n_spmm = ctx->n_spmm;
   info->n_prec = ctx->n_prec;
+  info->n_inner = ctx->n_inner;
   info->n_qz = ctx->n_qz;
   info->n_launch = ctx->n_launch;
   info->h2d_bytes = ctx->h2d_bytes;
@@ -1146,7 +1285,7 @@ gplhr_status make_fp32_copies(gplhr_ctx* ctx) {
     TRY(to_fp32(ctx, ctx->prec_data, 2 * nb, &p));
     ctx->prec32 = (float2*)p;
   }
-  CK(cudaMalloc(&ctx->X32, (size_t)ctx->n * ctx->k * sizeof(float2)));
+  CK(cudaMalloc(&ctx->X32, (size_t)ctx->n * ((ctx->k + 1) & ~1) * sizeof(float2)));
   return GPLHR_OK;
 }
 
@@ -1162,6 +1301,10 @@ void free_all(gplhr_ctx* c) {
   F(c->Rw); F(c->Tw1); F(c->Tw2); F(c->Tw3);
   F(c->dC1); F(c->dC2); F(c->dMBa); F(c->dMAa); F(c->dYR); F(c->dYL); F(c->dPhiPsi); F(c->dGram);
   F(c->dProjC); F(c->dRinv); F(c->dTrackC); F(c->dTrackR); F(c->gram_part); F(c->norm_part); F(c->d_norms); F(c->d_status); F(c->d_diag);
+  F(c->gmV); F(c->gmT); F(c->gmAX); F(c->gmBX); F(c->gmY);
+  if (c->h_gm) cudaFreeHost(c->h_gm);
+  if (c->h_gm_status) cudaFreeHost(c->h_gm_status);
+  if (c->h_gmY) cudaFreeHost(c->h_gmY);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->h_small) cudaFreeHost(c->h_small);
   if (c->h_phipsi) cudaFreeHost(c->h_phipsi);
@@ -1200,9 +1343,10 @@ gplhr_status allocate(gplhr_ctx* ctx) {
   CK(cudaMalloc(&ctx->dYL, 2 * s2));
   CK(cudaMalloc(&ctx->dPhiPsi, 2 * s2));
   CK(cudaMalloc(&ctx->dGram, 2 * s2));
-  CK(cudaMalloc(&ctx->dProjC, 2 * s2));
+  ctx->trk = std::max(sm * sm, (size_t)ctx->gm_steps * k * k);
+  CK(cudaMalloc(&ctx->dProjC, std::max(2 * s2, ctx->trk * sizeof(double2))));
   CK(cudaMalloc(&ctx->dRinv, 3 * s2));
-  CK(cudaMalloc(&ctx->dTrackC, 3 * s2));
+  CK(cudaMalloc(&ctx->dTrackC, 3 * ctx->trk * sizeof(double2)));
   CK(cudaMalloc(&ctx->dTrackR, 3 * s2));
   CK(cudaMallocHost(&ctx->h_track, 6 * s2));
   CK(cudaMallocHost(&ctx->h_status, 4 * sizeof(int)));
@@ -1219,11 +1363,22 @@ gplhr_status allocate(gplhr_ctx* ctx) {
   CK(cudaMallocHost(&ctx->h_norms, gplhr::COMB_MAX_NORMS * sizeof(double)));
   CK(cudaMallocHost(&ctx->h_diag, 2 * sizeof(int)));
   ctx->h_diag[0] = ctx->h_diag[1] = 0;
+  if (ctx->gm_steps > 0) {
+    const size_t gs = ctx->gm_steps;
+    CK(cudaMalloc(&ctx->gmV, n * (gs + 1) * k * sizeof(double2)));
+    CK(cudaMalloc(&ctx->gmT, kb));
+    CK(cudaMalloc(&ctx->gmAX, kb));
+    if (ctx->hasB) CK(cudaMalloc(&ctx->gmBX, kb));
+    CK(cudaMalloc(&ctx->gmY, gs * k * k * sizeof(double2)));
+    CK(cudaMallocHost(&ctx->h_gm, (gs + 1) * (3 * ctx->trk + 3 * k * k) * sizeof(double2)));
+    CK(cudaMallocHost(&ctx->h_gm_status, (gs + 1) * sizeof(int)));
+    CK(cudaMallocHost(&ctx->h_gmY, gs * k * k * sizeof(double2)));
+  }
   return GPLHR_OK;
 }
 
 gplhr_status set_smem_limits(gplhr_ctx* ctx) {
-  const int big = 200 * 1024;
+  const int big = (int)kCombSmemMax;
   CK(cudaFuncSetAttribute(gplhr::combine_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::combine_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::gram_partial_kernel<8, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
@@ -1373,6 +1528,12 @@ gplhr_status gplhr_create(const gplhr_csr* A, const gplhr_csr* B, double sigma_r
       delete ctx;
       return GPLHR_EINVAL;
     }
+  }
+  ctx->gm_steps = T ? T->inner_steps : 0;
+  if (ctx->gm_steps < 0 || ctx->gm_steps > 32 || ctx->gm_steps * k > 384) {
+    g_create_error = "T.inner_steps must be in [0, 32] with inner_steps * k <= 384";
+    delete ctx;
+    return GPLHR_EINVAL;
   }
   const int products = opts ? opts->products : 0;
   if (products < 0 || products > 2) {

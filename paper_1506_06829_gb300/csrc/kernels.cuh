@@ -116,10 +116,14 @@ template <typename T> __device__ __forceinline__ cplx<T> mfma(float2 v, cplx<T> 
 
 // ------------------------------------------------------------------- SpMM -----
 // Y = M X for up to two CSR matrices sharing the input block (A and B of the pencil).
-// One warp per row.  For a block width w <= 32 the warp is split into 32/wp
-// "slots" of wp = next power of two >= w lanes: lane (slot, c) accumulates column c
-// over the nonzeros slot, slot + nslot, ... of the row; the slots are then summed
-// with xor-shuffles.  Wider blocks are processed in chunks of 32 columns.
+// A warp works on 32/G rows at once, a group of G lanes per row; lane c of a group
+// holds V consecutive columns of the block (c V .. c V + V - 1), so the group's gather
+// of one block row X[col, :] is one coalesced 16 G-byte access (complex128, V = 1, or
+// complex64, V = 2).  The group first loads up to 32 (column, value) pairs of its row,
+// spread over its lanes, then walks them in batches of 8: column indices by shuffle,
+// 8 independent block-row gathers in flight per lane, then the multiply-adds.  A row
+// longer than 32 entries takes several rounds (a warp runs as many rounds as its
+// longest row needs).  Each output row is written once, by its group.
 template <typename VT>
 struct CsrDev {
   const int* rowptr;
@@ -145,58 +149,95 @@ template <> __device__ __forceinline__ double2 zero_val<double2>() { return make
 template <> __device__ __forceinline__ float zero_val<float>() { return 0.0f; }
 template <> __device__ __forceinline__ float2 zero_val<float2>() { return make_float2(0.0f, 0.0f); }
 
-// One CSR row times the block: the warp loads up to 32 (column, value) pairs of the
-// row with one coalesced access, then lane (slot, c) takes nonzero t + slot of each
-// group of nslot by shuffle and gathers X[col][c0 + c]; the gathers of consecutive
-// groups do not wait on index loads, and the loop is unrolled to keep several
-// 16*w-byte block rows in flight.  The slots are summed with xor-shuffles.
-template <typename VT, typename T, typename XT>
-__device__ __forceinline__ void spmm_row(const CsrDev<VT>& M, int r, const XT* __restrict__ X,
-                                         int ldx, int c0, int cw, int wp, int lane,
-                                         double2* __restrict__ Y, int ldy) {
-  const int slot = lane / wp;
-  const int nslot = 32 / wp;
-  const int c = lane - slot * wp;
-  const bool colok = c < cw;
-  cplx<T> acc = czero<T>();
-  const int j0 = M.rowptr[r], j1 = M.rowptr[r + 1];
-  for (int base = j0; base < j1; base += 32) {
-    const int cnt = min(32, j1 - base);
-    int mycol = 0;
-    VT myval = zero_val<VT>();
-    if (lane < cnt) {
-      mycol = M.col[base + lane];
-      myval = M.val[base + lane];
-    }
-#pragma unroll 4
-    for (int t = 0; t < 32; t += nslot) {
-      if (t >= cnt) break;
-      const int src = t + slot;
-      const int cc = __shfl_sync(0xffffffffu, mycol, src & 31);
-      const VT v = shfl_val(myval, src & 31);
-      if (src < cnt && colok) acc = mfma<T>(v, to_t<T>(X[(size_t)cc * ldx + c0 + c]), acc);
-    }
-  }
-  for (int off = wp; off < 32; off <<= 1) acc = cadd(acc, shfl_xor2(acc, off));
-  if (slot == 0 && colok) Y[(size_t)r * ldy + c0 + c] = to_d(acc);
+// V consecutive complex values of the block row at p (V = 2: one 16-byte load).
+template <typename T, int V>
+__device__ __forceinline__ void load_xv(const cplx<T>* __restrict__ p, cplx<T> (&x)[V]);
+template <> __device__ __forceinline__ void load_xv<double, 1>(const double2* __restrict__ p, double2 (&x)[1]) {
+  x[0] = __ldg(p);
+}
+template <> __device__ __forceinline__ void load_xv<float, 2>(const float2* __restrict__ p, float2 (&x)[2]) {
+  const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+  x[0] = make_float2(q.x, q.y);
+  x[1] = make_float2(q.z, q.w);
 }
 
-// T is the arithmetic (double, or float in the FP32 bulk phase); blocks stay complex128.
-template <typename VTA, typename VTB, typename T, typename XT = double2>
-__global__ void spmm_kernel(int n, CsrDev<VTA> A, CsrDev<VTB> B, int hasB,
-                            const XT* __restrict__ X, int ldx, int w,
-                            double2* __restrict__ AX, int ldax, double2* __restrict__ BX, int ldbx) {
+constexpr int SPMM_THREADS = 256;
+constexpr int SPMM_BATCH = 8;
+
+template <typename VT, typename T, int G, int V>
+__device__ __forceinline__ void spmm_group_row(const CsrDev<VT>& M, int r, int n, const cplx<T>* __restrict__ X,
+                                               int ldx, int w, int c, int lane, double2* __restrict__ Y, int ldy) {
+  constexpr int PER = 32 / G;  // (column, value) pairs each lane loads per round
+  const bool active = r < n;
+  const int j0 = active ? M.rowptr[r] : 0;
+  const int j1 = active ? M.rowptr[r + 1] : 0;
+  const int c0 = c * V;
+  const bool colok = c0 < w;
+  const int gbase = lane & ~(G - 1);
+  cplx<T> acc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) acc[v] = czero<T>();
+  for (int base = j0; __any_sync(0xffffffffu, base < j1); base += 32) {
+    const int cnt = max(0, min(32, j1 - base));
+    const int wcnt = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
+    int colr[PER];
+    VT valr[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = c + G * q;
+      colr[q] = e < cnt ? M.col[base + e] : 0;
+      valr[q] = e < cnt ? M.val[base + e] : zero_val<VT>();
+    }
+#pragma unroll
+    for (int tb = 0; tb < 32; tb += SPMM_BATCH) {
+      if (tb >= wcnt) break;
+      int cc[SPMM_BATCH];
+      VT vv[SPMM_BATCH];
+#pragma unroll
+      for (int u = 0; u < SPMM_BATCH; ++u) {
+        const int t = tb + u;
+        cc[u] = __shfl_sync(0xffffffffu, colr[t / G], gbase + t % G);
+        vv[u] = shfl_val(valr[t / G], gbase + t % G);
+      }
+      cplx<T> xv[SPMM_BATCH][V];
+#pragma unroll
+      for (int u = 0; u < SPMM_BATCH; ++u) {
+        if (tb + u < cnt && colok) {
+          load_xv<T, V>(X + (size_t)cc[u] * ldx + c0, xv[u]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < V; ++v) xv[u][v] = czero<T>();
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < SPMM_BATCH; ++u)
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = mfma<T>(vv[u], xv[u][v], acc[v]);
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+      if (c0 + v < w) Y[(size_t)r * ldy + c0 + v] = to_d(acc[v]);
+  }
+}
+
+// T is the arithmetic (double, or float in the FP32 bulk phase; X is then the
+// complex64 copy of the block); the outputs are complex128.  Requires w <= G V; with
+// V = 2 the rows of X must be 16-byte aligned (ldx even).
+template <typename VTA, typename VTB, typename T, int G, int V>
+__global__ void __launch_bounds__(SPMM_THREADS) spmm_kernel(int n, CsrDev<VTA> A, CsrDev<VTB> B, int hasB,
+                                                            const cplx<T>* __restrict__ X, int ldx, int w,
+                                                            double2* __restrict__ AX, int ldax,
+                                                            double2* __restrict__ BX, int ldbx) {
+  constexpr int RPW = 32 / G;
   const int lane = threadIdx.x & 31;
+  const int g = lane / G, c = lane - g * G;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int r = warp; r < n; r += nwarps) {
-    for (int c0 = 0; c0 < w; c0 += 32) {
-      const int cw = min(32, w - c0);
-      int wp = 1;
-      while (wp < cw) wp <<= 1;
-      spmm_row<VTA, T, XT>(A, r, X, ldx, c0, cw, wp, lane, AX, ldax);
-      if (hasB) spmm_row<VTB, T, XT>(B, r, X, ldx, c0, cw, wp, lane, BX, ldbx);
-    }
+  for (int rb = warp * RPW; rb < n; rb += nwarps * RPW) {
+    spmm_group_row<VTA, T, G, V>(A, rb + g, n, X, ldx, w, c, lane, AX, ldax);
+    if (hasB) spmm_group_row<VTB, T, G, V>(B, rb + g, n, X, ldx, w, c, lane, BX, ldbx);
   }
 }
 
@@ -468,12 +509,14 @@ struct CombArgs {
   double* normpart; // [gridDim.x][c - c_store] or null
   const int* skip;
   int upper;        // 1: single input whose C is upper triangular (X R^{-1}): sum j <= col
+  int rows_tile;    // rows staged per tile (comb_rows_tile, halved on the host while the
+                    // staging would not fit in shared memory)
 };
 constexpr int COMB_THREADS = 256;
 
-// Rows staged per tile.  For the triangular form the tile is 32 rows and threads are
-// mapped column-major (a warp = 32 rows of one output column), so the loop bound j <= col
-// is uniform across each warp: no predicated-off DFMAs.
+// Rows staged per tile (at most).  For the triangular form the tile is 32 rows and
+// threads are mapped column-major (a warp = 32 rows of one output column), so the loop
+// bound j <= col is uniform across each warp: no predicated-off DFMAs.
 __host__ __device__ inline int comb_rows_tile(int c, int upper = 0) {
   if (upper) return 32;
   return c >= COMB_THREADS ? 1 : COMB_THREADS / c;
@@ -495,7 +538,7 @@ __global__ void combine_kernel(int n, int rows_per_cta, CombArgs a) {
   for (int t = 0; t < a.nin; ++t) wsum += a.in[t].w;
   C2* cs = sm;
   C2* xs = cs + wsum * a.c;
-  const int rows_tile = comb_rows_tile(a.c, a.upper);
+  const int rows_tile = a.rows_tile;
   C2* ys = xs + rows_tile * wsum;
   __shared__ double nsum[COMB_MAX_NORMS];
   {
@@ -598,13 +641,14 @@ __global__ void copy_block_kernel(int n, int w, const double2* __restrict__ X, i
 }
 
 // complex128 block -> complex64 block (ld = w), for the FP32 sparse products.
-__global__ void to_c64_kernel(int n, int w, const double2* __restrict__ X, int ldx, float2* __restrict__ Y) {
+__global__ void to_c64_kernel(int n, int w, const double2* __restrict__ X, int ldx, float2* __restrict__ Y,
+                              int ldy) {
   const size_t total = (size_t)n * w;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / w), c = (int)(e - (size_t)r * w);
     const double2 v = X[(size_t)r * ldx + c];
-    Y[e] = make_float2((float)v.x, (float)v.y);
+    Y[(size_t)r * ldy + c] = make_float2((float)v.x, (float)v.y);
   }
 }
 

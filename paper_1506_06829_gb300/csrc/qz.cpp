@@ -444,4 +444,48 @@ SqMat tri_eigvecs(const SqMat& RA, const SqMat& RB) {
   return Zv;
 }
 
+void least_squares(std::vector<cd>& H, int M, int N, std::vector<cd>& E, int r, std::vector<cd>& Y) {
+  std::vector<cd> v(M);
+  for (int j = 0; j < N; ++j) {
+    // Householder reflector I - 2 v v^* mapping H(j:, j) to a multiple of e_1
+    double nx = 0.0;
+    for (int i = j; i < M; ++i) nx += std::norm(H[(size_t)i * N + j]);
+    nx = std::sqrt(nx);
+    if (nx == 0.0) continue;
+    const cd x0 = H[(size_t)j * N + j];
+    const cd ph = std::abs(x0) > 0.0 ? x0 / std::abs(x0) : cd(1.0, 0.0);
+    const cd alpha = -ph * nx;
+    double nv = 0.0;
+    for (int i = j; i < M; ++i) {
+      v[i] = H[(size_t)i * N + j] - (i == j ? alpha : cd(0.0, 0.0));
+      nv += std::norm(v[i]);
+    }
+    nv = std::sqrt(nv);
+    if (nv == 0.0) continue;
+    for (int i = j; i < M; ++i) v[i] /= nv;
+    for (int c = j; c < N; ++c) {
+      cd d = 0.0;
+      for (int i = j; i < M; ++i) d += std::conj(v[i]) * H[(size_t)i * N + c];
+      for (int i = j; i < M; ++i) H[(size_t)i * N + c] -= 2.0 * v[i] * d;
+    }
+    for (int c = 0; c < r; ++c) {
+      cd d = 0.0;
+      for (int i = j; i < M; ++i) d += std::conj(v[i]) * E[(size_t)i * r + c];
+      for (int i = j; i < M; ++i) E[(size_t)i * r + c] -= 2.0 * v[i] * d;
+    }
+  }
+  double dmax = 0.0;
+  for (int j = 0; j < N; ++j) dmax = std::max(dmax, std::abs(H[(size_t)j * N + j]));
+  Y.assign((size_t)N * r, cd(0.0, 0.0));
+  for (int j = N - 1; j >= 0; --j) {
+    const cd d = H[(size_t)j * N + j];
+    if (!(std::abs(d) > 1e-14 * dmax)) continue;
+    for (int c = 0; c < r; ++c) {
+      cd acc = E[(size_t)j * r + c];
+      for (int t = j + 1; t < N; ++t) acc -= H[(size_t)j * N + t] * Y[(size_t)t * r + c];
+      Y[(size_t)j * r + c] = acc / d;
+    }
+  }
+}
+
 }  // namespace gplhr

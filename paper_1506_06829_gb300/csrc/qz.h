@@ -39,4 +39,9 @@ SqMat tri_eigvecs(const SqMat& RA, const SqMat& RB);
 // Distance of the pair (alpha, beta) to sigma: |alpha - sigma beta| / |beta| (inf if beta = 0).
 double pair_distance(cd alpha, cd beta, cd sigma);
 
+// Least squares min ||E - H Y||_F for a dense row-major H (M x N, M >= N) and E (M x r),
+// by Householder QR; Y (N x r, row-major).  A column whose R diagonal is at most
+// 1e-14 times the largest is dropped (its row of Y is zero).  H and E are overwritten.
+void least_squares(std::vector<cd>& H, int M, int N, std::vector<cd>& E, int r, std::vector<cd>& Y);
+
 }  // namespace gplhr

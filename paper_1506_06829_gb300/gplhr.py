@@ -40,7 +40,8 @@ class Csr(C.Structure):
 
 
 class Precond(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("block_size", C.c_int32), ("T_csr", C.POINTER(Csr))]
+    _fields_ = [("kind", C.c_int32), ("block_size", C.c_int32), ("T_csr", C.POINTER(Csr)),
+                ("inner_steps", C.c_int32)]
 
 
 class Opts(C.Structure):
@@ -54,7 +55,7 @@ class Info(C.Structure):
                 ("n_orth_fallback", C.c_int32), ("fp32_iters", C.c_int32), ("bulk", C.c_int32),
                 ("n_spmm", C.c_int64), ("n_prec", C.c_int64),
                 ("n_qz", C.c_int64), ("n_launch", C.c_int64), ("h2d_bytes", C.c_int64),
-                ("d2h_bytes", C.c_int64), ("resid", C.c_double * 64)]
+                ("d2h_bytes", C.c_int64), ("resid", C.c_double * 64), ("n_inner", C.c_int64)]
 
 
 class GplhrError(RuntimeError):
@@ -146,13 +147,15 @@ def gplhr_create(A, B, sigma: complex, k: int, m: int, precond: str = "none",
                  block_size: int = 1, T=None, tol: float = 1e-8, maxit: int = 500,
                  lock: bool = True, stream: int = 0, products: str = "auto",
                  precision: str = "fp64", switch_tol: float = 1e-5, stall_iters: int = 5,
-                 pencil: str = "factored"):
-    """Returns an opaque context handle (int).  A, B: SciPy CSR (B None = identity)."""
+                 pencil: str = "factored", inner_steps: int = 0):
+    """Returns an opaque context handle (int).  A, B: SciPy CSR (B None = identity).
+    inner_steps > 0: T = that many block GMRES steps on (A - sigma B) W = R,
+    right-preconditioned by `precond`."""
     L = lib()
     hA = _HostCsr(A)
     hB = _HostCsr(B) if B is not None else None
     hT = _HostCsr(T.astype(np.complex128)) if T is not None else None
-    pc = Precond(PREC[precond], block_size, C.pointer(hT.desc) if hT else None)
+    pc = Precond(PREC[precond], block_size, C.pointer(hT.desc) if hT else None, inner_steps)
     opts = Opts(tol, maxit, {"fp64": 0, "mixed": 1}[precision], 0 if lock else 1,
                 PRODUCTS[products], stream or None, switch_tol, stall_iters,
                 {"factored": 0, "gram": 1}[pencil])
@@ -347,10 +350,11 @@ class GPLHR:
 
     def __init__(self, A, B, sigma, k, m, precond="none", block_size=1, T=None, tol=1e-8,
                  maxit=500, lock=True, stream=0, products="auto", precision="fp64",
-                 switch_tol=1e-5, stall_iters=5, pencil="factored"):
+                 switch_tol=1e-5, stall_iters=5, pencil="factored", inner_steps=0):
         self.n, self.k = A.shape[0], k
         self.ctx = gplhr_create(A, B, complex(sigma), k, m, precond, block_size, T, tol, maxit,
-                                lock, stream, products, precision, switch_tol, stall_iters, pencil)
+                                lock, stream, products, precision, switch_tol, stall_iters, pencil,
+                                inner_steps)
 
     def solve(self, V0=None, seed=0, allow_notconv=False):
         return gplhr_solve(self.ctx, V0, seed, allow_notconv)

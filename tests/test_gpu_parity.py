@@ -413,3 +413,41 @@ def test_bulk_phase_gram_is_fp64_accurate_on_fp32_values():
     V, Q = vec["V"], vec["Q"]
     assert np.linalg.norm(V.conj().T @ V - np.eye(pr.k)) <= 1e-5    # FP32 updates of V
     assert np.linalg.norm(Q.conj().T @ Q - np.eye(pr.k)) <= 1e-5
+
+
+@pytest.mark.parametrize("arith", ["fp32", "exact32"])
+def test_fp32_conversion_is_round_to_nearest_even(arith):
+    """With Y = I the FP32 Gram returns C = X^* exactly (products with 1 and 0, sums of one
+    nonzero term), so C holds the kernels' FP64 -> FP32 conversion of every entry of X:
+    bit-exact against IEEE round-to-nearest-even (numpy's cast, FP32 subnormals kept) on
+    random values over FP32's exponent range, exact ties, near-ties, carries into the
+    exponent and underflow."""
+    rng = np.random.default_rng(12)
+    n, wx = 80, 40
+    vals = np.ldexp(rng.uniform(1.0, 2.0, 2 * n * wx), rng.integers(-125, 127, 2 * n * wx))
+    vals *= rng.choice([-1.0, 1.0], vals.size)
+    special = []
+    for e in (-100, -3, 0, 1, 17, 100):
+        one = 2.0 ** e
+        ulp = 2.0 ** (e - 23)
+        special += [one + ulp / 2, one + 1.5 * ulp, one + ulp / 2 + 2.0 ** (e - 52), one + ulp / 2 - 2.0 ** (e - 52),
+                    2 * one - 2.0 ** (e - 30), -(one + ulp / 2), -(2 * one - 2.0 ** (e - 52)), one + ulp]
+    special += [0.0, -0.0, 2.0 ** -126, 2.0 ** -127, -3.0e-40, 1.0e-300, 2.0 ** -126 * (1 - 2.0 ** -30),
+                float(np.finfo(np.float32).max), -float(np.finfo(np.float32).max)]
+    vals[:len(special)] = special
+    Xh = (vals[0::2] + 1j * vals[1::2]).reshape(n, wx)
+    A = sp.identity(n, format="csr")
+    ctx = G.gplhr_create(A, None, 0.5, 8, 7)
+    try:
+        Cd = torch.zeros((wx, n), dtype=torch.complex128, device=DEV)
+        G.gplhr_gram(ctx, _dev(Xh), _dev(np.eye(n, dtype=np.complex128)), Cd, arith)
+        C = _host(Cd)
+    finally:
+        G.gplhr_destroy(ctx)
+    f32 = lambda x: x.astype(np.float32).astype(np.float64)
+    want_re, want_im = f32(Xh.real.T), -f32(Xh.imag.T)
+    got_re, got_im = C.real, C.imag
+    assert np.array_equal(got_re, want_re), np.argwhere(got_re != want_re)[:5]
+    # the conjugate of a zero imaginary part may carry either sign after the sum
+    assert np.array_equal(np.abs(got_im), np.abs(want_im)) and \
+        np.array_equal(got_im[want_im != 0], want_im[want_im != 0])
