@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision runs")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload run")
-    ap.add_argument("--inner-steps", type=int, default=4,
+    ap.add_argument("--inner-steps", type=int, default=8,
                     help="block GMRES steps of the inner-solve preconditioner in the extra "
                          "time-to-pairs runs (0 = skip them)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
