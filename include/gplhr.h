@@ -117,6 +117,11 @@ typedef struct {
                           U^*(A - sigma B)Z from the factors of U's construction (Prop. 3.2
                           and the orthonormalisation of (A - sigma B)[W S P]); 1 = both
                           U^*AZ and U^*BZ by Gram products (Alg. 2 step 24 as printed)   */
+  int32_t fp64_gemm;   /* [0]    FP64 block combinations: 0 = on the tensor cores (tcgen05,
+                          each double split into 8 integer digits of 7 bits, exact FP32
+                          accumulation of digit products, error ~2^-53 max|x| sum|c| like
+                          a DFMA product) where the shape allows (<= 32 input and output
+                          columns), DFMA otherwise; 1 = DFMA only                         */
 } gplhr_opts;
 
 /* Per-solve report.  resid[j] (j < k) is the backward error of pair j,
@@ -255,6 +260,18 @@ gplhr_status gplhr_precond_apply(gplhr_ctx* ctx, const void* X, int32_t ldx, int
 enum { GPLHR_GRAM_FP64 = 0, GPLHR_GRAM_FP32 = 1, GPLHR_GRAM_EXACT32 = 2 };
 gplhr_status gplhr_gram(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t wx, const void* Y,
                         int32_t ldy, int32_t wy, void* C, int32_t arith);
+
+/* Block combination Y = X C (beta = 0) or Y = Y + X C (beta = 1): the basis update of
+ * Alg. 2 steps 25-28 (V = Z Y_R, Q = U Y_L, P = Z Ybar_R(:, k+1:2k)) and every projection
+ * X - L (L^* X) of the iteration.  X: n x w (ld >= w), C: w x c row-major, Y: n x c
+ * (ld >= c), all complex128 on the device; Y must not overlap X unless Y == X with
+ * c == w and ldy == ldx (in place, beta = 0).  arith: GPLHR_COMBINE_AUTO (0) the
+ * context's choice (tensor cores for <= 32 input and output columns unless
+ * opts.fp64_gemm = 1), GPLHR_COMBINE_DFMA (1).  EINVAL for w or c outside [1, 2 s_max].
+ * Synchronises the context's stream. */
+enum { GPLHR_COMBINE_AUTO = 0, GPLHR_COMBINE_DFMA = 1 };
+gplhr_status gplhr_combine(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t w, const void* C,
+                           int32_t c, void* Y, int32_t ldy, int32_t beta, int32_t arith);
 
 /* orth(X) in place (Alg. 1 footnote): X <- X R^{-1} with X = Q R the thin QR whose R
  * has a real positive diagonal, by Cholesky QR applied twice (a shifted Cholesky

@@ -24,6 +24,7 @@
 #include "../../include/gplhr.h"
 #include "kernels.cuh"
 #include "qz.h"
+#include "tc.cuh"
 
 using gplhr::cd;
 using gplhr::SqMat;
@@ -103,7 +104,9 @@ struct gplhr_ctx {
   double* norm_part = nullptr;
   double* d_norms = nullptr;
   int* d_status = nullptr;    // [0..2] chol status of the passes of one orth call
-  int* d_diag = nullptr;      // [0] shifted-Cholesky fallbacks, [1] Cholesky failures
+  int* d_diag = nullptr;      // [0] shifted-Cholesky fallbacks, [1] Cholesky failures,
+                              // [2] tensor-core waits that gave up
+  bool tc = true;             // FP64 combinations on the tensor cores where supported
   // pinned host staging
   double2* h_small = nullptr;  // coefficient uploads
   double2* h_phipsi = nullptr;
@@ -367,6 +370,39 @@ struct In {
   double2 alpha;
 };
 
+// The combination on the tensor cores (FP64 by integer digits, tc.cuh): one persistent
+// CTA per SM (more when shared and tensor memory allow), 128 rows per tile.
+gplhr_status combine_tc(gplhr_ctx* ctx, gplhr::CombArgs a, int wsum, int c, int c_store, bool beta_one,
+                        bool count) {
+  gplhr::TcCombArgs t{};
+  t.a = a;
+  t.a.upper = 0;
+  t.kp = ((2 * wsum + 15) / 16) * 16;
+  t.np = ((2 * c + 15) / 16) * 16;
+  t.tmem_cols = 32;
+  while (t.tmem_cols < gplhr::TC_DIAG * t.np) t.tmem_cols <<= 1;
+  t.err = ctx->d_diag + 2;
+  const size_t smem = (size_t)gplhr::TC_DIGITS * (gplhr::TC_ROWS + t.np) * t.kp * sizeof(uint16_t) +
+                      2 * t.np * sizeof(int);
+  // at most 4 per SM: the per-CTA norm partials are sized for 4 CTAs per SM
+  const int per_sm = std::max(1, std::min({(int)((227 * 1024) / (smem + 4096)), 512 / t.tmem_cols, 4}));
+  const int ntiles = (ctx->n + gplhr::TC_ROWS - 1) / gplhr::TC_ROWS;
+  const int grid = std::min(ntiles, per_sm * ctx->num_sms);
+  t.a.normpart = c_store < c ? ctx->norm_part : nullptr;
+  const double by = 16.0 * ctx->n * (wsum + c_store * (beta_one ? 2.0 : 1.0));
+  const int ph = prof_begin(ctx, KC_COMBINE, count ? 8.0 * ctx->n * (double)wsum * c : 0.0, count ? by : 0.0,
+                            c_store < c ? 2 : 1);
+  gplhr::tc_combine_kernel<<<grid, gplhr::TC_THREADS, smem, ctx->stream>>>(ctx->n, t);
+  CK(cudaGetLastError());
+  if (c_store < c) {
+    const int nc = c - c_store;
+    gplhr::norm_reduce_kernel<<<(nc + 3) / 4, 128, 0, ctx->stream>>>(grid, nc, ctx->norm_part, ctx->d_norms);
+    CK(cudaGetLastError());
+  }
+  prof_end(ctx, ph);
+  return GPLHR_OK;
+}
+
 // Y(cols 0..c_split) / Y2 (cols c_split..c_store) = beta Y + sum alpha_t X_t C_t;
 // columns c_store..c only contribute |.|^2 sums (reduced into ctx->d_norms).
 gplhr_status combine(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, bool beta_one,
@@ -394,6 +430,8 @@ gplhr_status combine(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, b
   a.beta_one = beta_one ? 1 : 0;
   a.skip = skip;
   a.upper = (upper && !use32 && a.nin == 1 && ins[0].w == c && c_store == c && c_split == c) ? 1 : 0;
+  if (!use32 && ctx->tc && wsum <= gplhr::TC_KMAX / 2 && c <= gplhr::TC_NMAX / 2 && ctx->n >= 4 * gplhr::TC_ROWS)
+    return combine_tc(ctx, a, wsum, c, c_store, beta_one, count);
   int rows_tile = gplhr::comb_rows_tile(c, a.upper);
   const size_t esz = use32 ? sizeof(float2) : sizeof(double2);
   auto smem_of = [&](int rt) { return (size_t)(wsum * c + rt * wsum + rt * c) * esz; };
@@ -707,7 +745,7 @@ gplhr_status residuals(gplhr_ctx* ctx) {
               Blk{ctx->Rw, k}, 2 * k, false, nullptr, Blk{nullptr, 0}, k, k));
   ctx->d2h_bytes += k * sizeof(double) + 2 * sizeof(int);
   CK(cudaMemcpyAsync(ctx->h_norms, ctx->d_norms, k * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->h_diag, ctx->d_diag, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_diag, ctx->d_diag, 3 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->resid.assign(k, 0.0);
   for (int j = 0; j < k; ++j) {
@@ -724,6 +762,10 @@ gplhr_status residuals(gplhr_ctx* ctx) {
   if (ctx->h_diag[1] != 0) {
     ctx->err = "orth(): Cholesky QR broke down even with the shifted first pass";
     return GPLHR_ESINGULAR;
+  }
+  if (ctx->h_diag[2] != 0) {
+    ctx->err = "tensor-core product: wait for completion gave up";
+    return GPLHR_ETIMEOUT;
   }
   return GPLHR_OK;
 }
@@ -776,7 +818,7 @@ gplhr_status start(gplhr_ctx* ctx) {
   ctx->fp32_iters = 0;
   ctx->best_res = 1e300;
   ctx->since_best = 0;
-  CK(cudaMemsetAsync(ctx->d_diag, 0, 2 * sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_diag, 0, 3 * sizeof(int), ctx->stream));
   return start_steps(ctx);
 }
 
@@ -1356,13 +1398,13 @@ gplhr_status allocate(gplhr_ctx* ctx) {
   CK(cudaMalloc(&ctx->norm_part, (size_t)(4 * ctx->num_sms + 8) * gplhr::COMB_MAX_NORMS * sizeof(double)));
   CK(cudaMalloc(&ctx->d_norms, gplhr::COMB_MAX_NORMS * sizeof(double)));
   CK(cudaMalloc(&ctx->d_status, 8 * sizeof(int)));
-  CK(cudaMalloc(&ctx->d_diag, 2 * sizeof(int)));
-  CK(cudaMemset(ctx->d_diag, 0, 2 * sizeof(int)));
+  CK(cudaMalloc(&ctx->d_diag, 3 * sizeof(int)));
+  CK(cudaMemset(ctx->d_diag, 0, 3 * sizeof(int)));
   CK(cudaMallocHost(&ctx->h_small, (8 * k * k + 4 * sm * sm) * sizeof(double2)));
   CK(cudaMallocHost(&ctx->h_phipsi, 2 * s2));
   CK(cudaMallocHost(&ctx->h_norms, gplhr::COMB_MAX_NORMS * sizeof(double)));
-  CK(cudaMallocHost(&ctx->h_diag, 2 * sizeof(int)));
-  ctx->h_diag[0] = ctx->h_diag[1] = 0;
+  CK(cudaMallocHost(&ctx->h_diag, 3 * sizeof(int)));
+  ctx->h_diag[0] = ctx->h_diag[1] = ctx->h_diag[2] = 0;
   if (ctx->gm_steps > 0) {
     const size_t gs = ctx->gm_steps;
     CK(cudaMalloc(&ctx->gmV, n * (gs + 1) * k * sizeof(double2)));
@@ -1399,6 +1441,7 @@ gplhr_status set_smem_limits(gplhr_ctx* ctx) {
   CK(cudaFuncSetAttribute(gplhr::block_jacobi_kernel<float, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           big));
   CK(cudaFuncSetAttribute(gplhr::invert_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::tc_combine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   return GPLHR_OK;
 }
 
@@ -1523,6 +1566,7 @@ gplhr_status gplhr_create(const gplhr_csr* A, const gplhr_csr* B, double sigma_r
     if (opts->switch_tol > 0) ctx->switch_tol = opts->switch_tol;
     if (opts->stall_iters != 0) ctx->stall_iters = opts->stall_iters;
     ctx->factored = opts->pencil == 0;
+    ctx->tc = opts->fp64_gemm == 0;
     if (opts->precision != GPLHR_FP64 && opts->precision != GPLHR_MIXED) {
       g_create_error = "opts.precision must be GPLHR_FP64 or GPLHR_MIXED";
       delete ctx;
@@ -1768,6 +1812,27 @@ gplhr_status gplhr_gram(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t wx, 
   TRY(gram(ctx, Blk{(double2*)X, ldx}, wx, Blk{(double2*)Y, ldy}, wy, Blk{nullptr, 0}, 0, (double2*)C, nullptr,
            false, true, false, arith));
   CK(cudaStreamSynchronize(ctx->stream));
+  return GPLHR_OK;
+}
+
+gplhr_status gplhr_combine(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t w, const void* C, int32_t c,
+                           void* Y, int32_t ldy, int32_t beta, int32_t arith) {
+  if (!ctx || !valid_block(X, ldx, w) || !valid_block(Y, ldy, c) || !C || w < 1 || c < 1 || w > 2 * ctx->s_max ||
+      c > 2 * ctx->s_max || arith < 0 || arith > 1 || beta < 0 || beta > 1 ||
+      (X == Y && (c != w || ldy != ldx || beta != 0)))
+    return GPLHR_EINVAL;
+  const bool tc = ctx->tc;
+  ctx->tc = tc && arith == GPLHR_COMBINE_AUTO;
+  const gplhr_status st = combine(ctx, {In{Blk{(double2*)X, ldx}, w, (const double2*)C, kOne}},
+                                  Blk{(double2*)Y, ldy}, c, beta != 0, nullptr, Blk{nullptr, 0}, -1, -1, true, 0);
+  ctx->tc = tc;
+  TRY(st);
+  CK(cudaMemcpyAsync(ctx->h_diag, ctx->d_diag, 3 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->h_diag[2] != 0) {
+    ctx->err = "tensor-core product: wait for completion gave up";
+    return GPLHR_ETIMEOUT;
+  }
   return GPLHR_OK;
 }
 

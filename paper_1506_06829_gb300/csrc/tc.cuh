@@ -1,0 +1,377 @@
+// FP64 block combination Y = beta Y + sum_t alpha_t X_t C_t on GB300's tensor cores
+// (tcgen05, bf16 operands, FP32 accumulators in tensor memory), accurate to FP64 working
+// precision by splitting every double into small integer digits.
+//
+// Scheme (per tile of 128 rows; K' = 2 sum w_t real columns, N' = 2 c real columns):
+// * complex to real: a row of [X_0 X_1 ...] is the K' doubles (Re, Im, Re, Im, ...),
+//   C' (K' x N') = [[Re c, Im c], [-Im c, Re c]] per complex entry, so Y' = X' C' is the
+//   interleaved complex result;
+// * row r of X' shares one exponent bound T_r (every |x| < 2^(T_r + 1)); each x becomes
+//   the integer S = round(x 2^(54 - T_r)), |S| <= 2^55, written in 7 balanced base-256
+//   digits, S = sum_{a=0..6} s_a 256^(6 - a) with s_1..s_6 in [-128, 127] and
+//   |s_0| <= 128 (exact in bf16); column n of C' likewise with its bound G_n;
+// * the tensor core forms the digit diagonals D_d = sum_{a + b = d} X'_a C'_b for
+//   d = 0..7 (34 digit-pair products).  |s_a s_b| <= 2^14, at most 7 pairs per diagonal
+//   and K' <= 64, so |D_d| < 7 2^20: every FP32 partial sum is an exact integer;
+// * y = 2^(T_r + G_n - 68) Z, Z = sum_d D_d 256^(7 - d) formed exactly in 128-bit
+//   integers and rounded once to double (nearest, ties to even).
+// Error per output: input rounding <= 2^-55 (max_k |x_rk| sum_k |c_kn| + K' max_k |x_rk|
+// max_k |c_kn|), the dropped pairs a + b >= 8 (weight <= 2^-62 K' 2^(T_r + G_n) in all),
+// and the final rounding: at most (K'/4 + 2) u max_k |x_rk| sum_k |c_kn| with u = 2^-53,
+// a quarter of the classical bound K' u sum_k |x_rk| |c_kn| <= K' u max|x| sum|c| of a
+// DFMA dot product.  Results below 2^-1022 (subnormal) take a second rounding.
+#pragma once
+#include <climits>
+#include <cstdint>
+
+namespace gplhr {
+
+// ------------------------------------------------------------- tcgen05 PTX --
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory operand descriptor, K-major without swizzle: core matrices of 8 rows x
+// 16 bytes stored as 128 contiguous bytes; lbo = byte step between cores along K, sbo =
+// between cores along M (or N).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
+}
+// Instruction descriptor, kind::f16: bf16 A and B (both K-major), f32 accumulator, M x N.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          int accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(mbar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ------------------------------------------------------------ digit algebra --
+constexpr int TC_DIGITS = 7;     // balanced base-256 digits of a 55-bit integer
+constexpr int TC_DIAG = 8;       // accumulated digit diagonals a + b = 0..7
+constexpr int TC_ROWS = 128;     // rows per tile = tensor-memory lanes (M)
+constexpr int TC_THREADS = 256;  // two threads per row: each loads half of the row
+constexpr int TC_KMAX = 64;      // K' per tile (complex inputs: 32 columns)
+constexpr int TC_NMAX = 64;      // N' (complex outputs: 32 columns)
+constexpr int TC_NOEXP = -100000;
+
+// Exponent bound of a double: |v| < 2^(e + 1) with e = ee + 52, |v| = M 2^ee; the
+// largest finite bound for Inf / NaN (their rows and columns come out as NaN).
+__device__ __forceinline__ int tc_top(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int eb = (int)((b >> 52) & 0x7FF);
+  if ((b << 1) == 0) return TC_NOEXP;
+  return (eb ? eb - 1075 : -1074) + 52;
+}
+__device__ __forceinline__ bool tc_nonfinite(double v) {
+  return (((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FF) == 0x7FF;
+}
+
+// The digits of v against the exponent bound T (T >= tc_top(v)) as floats holding small
+// integers: F = round(|v| 2^(54 - T)) < 2^55 (half up); F + 0x808080808080 carries the
+// balancing, so digit a >= 1 is byte (6 - a) of that sum minus 128 and digit 0 its
+// bits 48..55; every digit takes v's sign.
+__device__ __forceinline__ void tc_digits(double v, int T, float (&f)[TC_DIGITS]) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int eb = (int)((b >> 52) & 0x7FF);
+  const unsigned long long M =
+      eb == 0x7FF ? 0ull : ((b & 0x000FFFFFFFFFFFFFull) | (eb ? (1ull << 52) : 0ull));
+  const int sh = (eb ? eb - 1075 : -1074) + 54 - T;  // <= 2
+  unsigned long long F = 0;
+  if (sh >= 0)
+    F = M << (sh & 3);
+  else if (sh > -60)
+    F = (M + (1ull << (-sh - 1))) >> (-sh);
+  const unsigned long long S = F + 0x0000808080808080ull;
+  const uint32_t lo = (uint32_t)S, hi = (uint32_t)(S >> 32);
+  const float sg = (b >> 63) ? -1.0f : 1.0f;
+  // 0x4B0000xx as a float is 2^23 + xx; sg (2^23 + xx) - sg (2^23 + 128) is exact
+  const float m0 = sg * 8388608.0f, m1 = sg * 8388736.0f;
+  f[0] = fmaf(sg, __uint_as_float(__byte_perm(hi, 0x4B000000u, 0x7442)), -m0);
+  f[1] = fmaf(sg, __uint_as_float(__byte_perm(hi, 0x4B000000u, 0x7441)), -m1);
+  f[2] = fmaf(sg, __uint_as_float(__byte_perm(hi, 0x4B000000u, 0x7440)), -m1);
+  f[3] = fmaf(sg, __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7443)), -m1);
+  f[4] = fmaf(sg, __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7442)), -m1);
+  f[5] = fmaf(sg, __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7441)), -m1);
+  f[6] = fmaf(sg, __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7440)), -m1);
+}
+
+// Two bf16 halves packed from floats that hold bf16-exact values (their top 16 bits).
+__device__ __forceinline__ uint32_t tc_pack2(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+
+// 2^p Z for a signed 128-bit integer Z, rounded once to the nearest double (ties to
+// even); a result below 2^-1022 is rounded a second time to the subnormal grid.
+__device__ __forceinline__ double tc_i128_ldexp(__int128 z, int p) {
+  if (z == 0) return 0.0;
+  const bool neg = z < 0;
+  unsigned __int128 m = neg ? (unsigned __int128)(-z) : (unsigned __int128)z;
+  const uint64_t mh = (uint64_t)(m >> 64), ml = (uint64_t)m;
+  const int lz = mh ? __clzll((long long)mh) : 64 + __clzll((long long)ml);
+  m <<= lz;  // leading one at bit 127
+  const uint64_t top = (uint64_t)(m >> 64);
+  const bool sticky = (uint64_t)m != 0;
+  uint64_t mant = top >> 11;  // 53 bits
+  const uint64_t rb = top & 0x7FF;
+  if (rb > 0x400 || (rb == 0x400 && (sticky || (mant & 1)))) ++mant;
+  int e = 127 - lz + p;  // exponent of the leading one
+  if (mant >> 53) {
+    mant >>= 1;
+    ++e;
+  }
+  const uint64_t sgn = neg ? (1ull << 63) : 0ull;
+  if (e > 1023) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull));
+  if (e >= -1022) return __longlong_as_double((long long)(sgn | ((uint64_t)(e + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+  const double d = scalbn((double)mant, e - 52);
+  return neg ? -d : d;
+}
+
+// Exact integer value of an FP32 accumulator holding an integer of magnitude < 2^24.
+__device__ __forceinline__ int tc_f2i(uint32_t u) { return __float2int_rn(__uint_as_float(u)); }
+
+struct TcCombArgs {
+  CombArgs a;
+  int kp;          // K' padded to a multiple of 16 (<= TC_KMAX)
+  int np;          // N' padded to a multiple of 16 (<= TC_NMAX)
+  int tmem_cols;   // power of two >= max(32, TC_DIAG np)
+  int* err;        // set to 1 if a wait on the tensor core gave up
+};
+
+__device__ __forceinline__ int tc_off(int row, int k, int KC) {  // element offset in a core-matrix tile
+  return ((row >> 3) * KC + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
+}
+
+// The value of C' at (kk, nn): stacked alpha_t C_t, complex entries as 2 x 2 real blocks.
+__device__ __forceinline__ double tc_cval(const CombArgs& a, int wsum, int kk, int nn) {
+  const int j = kk >> 1, p = kk & 1, l = nn >> 1, q = nn & 1;
+  if (j >= wsum || l >= a.c) return 0.0;
+  int t = 0, jj = j;
+  while (jj >= a.in[t].w) {
+    jj -= a.in[t].w;
+    ++t;
+  }
+  const double2 cv = cmul(a.in[t].alpha, a.in[t].C[(size_t)jj * a.c + l]);
+  return p == 0 ? (q == 0 ? cv.x : cv.y) : (q == 0 ? -cv.y : cv.x);
+}
+
+// One persistent CTA per (SM, slot); 128 rows per tile, thread (r, h) = (tid % 128,
+// tid / 128) loads and splits the row's k-chunks kc = h, h + 2, ... (8 reals each) and
+// writes the output column groups nb = 8 h, 8 h + 16, ...  Warp w reads tensor-memory
+// lanes 32 (w % 4) .. +31, which hold rows 32 (w % 4) .. +31 of the tile.
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_combine_kernel(int n, TcCombArgs ta) {
+  const CombArgs& a = ta.a;
+  if (a.skip && *a.skip == 0) return;
+  extern __shared__ __align__(128) unsigned char tc_smem[];
+  const int kp = ta.kp, np = ta.np, KC = kp >> 3;
+  uint16_t* sA = reinterpret_cast<uint16_t*>(tc_smem);         // TC_DIGITS x 128 x kp
+  uint16_t* sB = sA + TC_DIGITS * TC_ROWS * kp;                // TC_DIGITS x np x kp
+  int* sG = reinterpret_cast<int*>(sB + TC_DIGITS * np * kp);  // np column exponents
+  int* sBadC = sG + np;                                        // np non-finite flags
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t taddr_s;
+  __shared__ double nsum[COMB_MAX_NORMS];
+  __shared__ const double2* colp[TC_KMAX / 2];
+  __shared__ int coll[TC_KMAX / 2];
+  __shared__ int sT[2][TC_ROWS];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int rl = tid & (TC_ROWS - 1), h = tid >> 7;
+  int wsum = 0;
+  for (int t = 0; t < a.nin; ++t) wsum += a.in[t].w;
+  const int nnorm = a.c - a.c_store;
+  for (int e = tid; e < nnorm; e += TC_THREADS) nsum[e] = 0.0;
+  if (tid < TC_KMAX / 2) {  // where input column j of the stacked row lives
+    const double2* p = nullptr;
+    int ld = 0;
+    if (tid < wsum) {
+      int t = 0, jj = tid;
+      while (jj >= a.in[t].w) {
+        jj -= a.in[t].w;
+        ++t;
+      }
+      p = a.in[t].X + jj;
+      ld = a.in[t].ldx;
+    }
+    colp[tid] = p;
+    coll[tid] = ld;
+  }
+  // B operand (C' digits): column exponents, then the digits of all kp x np entries
+  if (tid < np) {
+    int G = TC_NOEXP, bad = 0;
+    for (int kk = 0; kk < kp; ++kk) {
+      const double v = tc_cval(a, wsum, kk, tid);
+      G = max(G, tc_top(v));
+      bad |= tc_nonfinite(v);
+    }
+    sG[tid] = G;
+    sBadC[tid] = bad;
+  }
+  __syncthreads();
+  for (int e = tid; e < kp * np; e += TC_THREADS) {
+    const int nn = e / kp, kk = e - nn * kp;
+    float dg[TC_DIGITS];
+    tc_digits(tc_cval(a, wsum, kk, nn), sG[nn], dg);
+#pragma unroll
+    for (int d = 0; d < TC_DIGITS; ++d)
+      sB[d * np * kp + tc_off(nn, kk, KC)] = (uint16_t)(__float_as_uint(dg[d]) >> 16);
+  }
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
+                 "r"(ta.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = taddr_s;
+  const uint32_t idesc = umma_idesc_bf16(TC_ROWS, np);
+  const uint32_t a_slice = TC_ROWS * kp * 2, b_slice = np * kp * 2;  // bytes
+  const uint32_t sA_addr = smem_u32(sA), sB_addr = smem_u32(sB);
+  const int ntiles = (n + TC_ROWS - 1) / TC_ROWS;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+  bool ok = true;
+  uint32_t parity = 0;
+  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, parity ^= 1) {
+    const int r = tile * TC_ROWS + rl;
+    const bool valid = r < n;
+    // this thread's k-chunks of the row: 4 complex values each, in registers
+    double xv[TC_KMAX / 2];
+    int T = TC_NOEXP, bad = 0;
+#pragma unroll
+    for (int i = 0; i < TC_KMAX / 16; ++i) {
+      const int kc = 2 * i + h;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = kc * 4 + u;
+        double2 v = make_double2(0.0, 0.0);
+        if (valid && kc < KC && j < wsum) v = colp[j][(size_t)r * coll[j]];
+        xv[8 * i + 2 * u] = v.x;
+        xv[8 * i + 2 * u + 1] = v.y;
+        T = max(T, max(tc_top(v.x), tc_top(v.y)));
+        bad |= tc_nonfinite(v.x) | tc_nonfinite(v.y);
+      }
+    }
+    sT[h][rl] = T;
+    __syncthreads();
+    T = max(sT[0][rl], sT[1][rl]);
+    __syncthreads();
+    sT[h][rl] = bad;
+    // A operand: 8 consecutive k of one digit per 16-byte store
+#pragma unroll
+    for (int i = 0; i < TC_KMAX / 16; ++i) {
+      const int kc = 2 * i + h;
+      if (kc < KC) {
+        float dg[8][TC_DIGITS];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) tc_digits(xv[8 * i + u], T, dg[u]);
+#pragma unroll
+        for (int d = 0; d < TC_DIGITS; ++d) {
+          uint4 w;
+          w.x = tc_pack2(dg[0][d], dg[1][d]);
+          w.y = tc_pack2(dg[2][d], dg[3][d]);
+          w.z = tc_pack2(dg[4][d], dg[5][d]);
+          w.w = tc_pack2(dg[6][d], dg[7][d]);
+          *reinterpret_cast<uint4*>(sA + d * TC_ROWS * kp + tc_off(rl, kc * 8, KC)) = w;
+        }
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+    bad = sT[0][rl] | sT[1][rl];
+    if (tid == 0) {
+      tc_fence_after();
+      for (int ks = 0; ks < kp / 16; ++ks)
+        for (int da = 0; da < TC_DIGITS; ++da)
+          for (int db = 0; db < TC_DIGITS && da + db < TC_DIAG; ++db) {
+            const int d = da + db, first_da = d > TC_DIGITS - 1 ? d - (TC_DIGITS - 1) : 0;
+            const uint64_t ad = umma_desc(sA_addr + da * a_slice + ks * 256, 128, KC * 128);
+            const uint64_t bd = umma_desc(sB_addr + db * b_slice + ks * 256, 128, KC * 128);
+            umma_bf16(tmem + (uint32_t)(d * np), ad, bd, idesc, (ks > 0 || da > first_da) ? 1 : 0);
+          }
+      umma_commit(&mbar);
+    }
+    // wait for the products (bounded)
+    bool done = false;
+    for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(&mbar, parity);
+    if (!__syncthreads_and(done)) {  // the same decision in every thread
+      if (tid == 0) atomicExch(ta.err, 1);
+      ok = false;
+      break;
+    }
+    tc_fence_after();
+    for (int nb = 8 * h; nb < np; nb += 16) {
+      uint32_t acc[TC_DIAG][8];
+#pragma unroll
+      for (int d = 0; d < TC_DIAG; ++d) tmem_ld8(tmem + lane_base + (uint32_t)(d * np + nb), acc[d]);
+      tmem_wait_ld();
+      if (!valid) continue;
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        const int nn = nb + u, l = nn >> 1;
+        if (l >= a.c) continue;
+        double yv[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          long long hi = 0, lo = 0;
+#pragma unroll
+          for (int d = 0; d < 4; ++d) hi = hi * 256 + tc_f2i(acc[d][u + q]);
+#pragma unroll
+          for (int d = 4; d < 8; ++d) lo = lo * 256 + tc_f2i(acc[d][u + q]);
+          const __int128 z = ((__int128)hi << 32) + lo;
+          yv[q] = tc_i128_ldexp(z, T + sG[nn + q] - 68);
+          if (bad || sBadC[nn + q]) yv[q] = __longlong_as_double(0x7FF8000000000000ll);
+        }
+        double2 y = make_double2(yv[0], yv[1]);
+        if (l < a.c_store) {
+          double2* dst = comb_out(a, r, l);
+          if (a.beta_one) {
+            const double2 o = *dst;
+            y.x += o.x;
+            y.y += o.y;
+          }
+          *dst = y;
+        } else {
+          atomicAdd(&nsum[l - a.c_store], y.x * y.x + y.y * y.y);
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ta.tmem_cols)
+                              : "memory");
+  if (a.normpart)
+    for (int e = tid; e < nnorm; e += TC_THREADS) a.normpart[(size_t)blockIdx.x * nnorm + e] = nsum[e];
+}
+
+}  // namespace gplhr

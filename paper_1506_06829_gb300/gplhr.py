@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5:
 
 EXPORTED = ["gplhr_create", "gplhr_solve", "gplhr_start", "gplhr_iterate", "gplhr_vectors",
             "gplhr_destroy", "gplhr_last_error", "gplhr_spmm", "gplhr_precond_apply",
-            "gplhr_gram", "gplhr_orth", "gplhr_ordqz", "gplhr_mfactors", "gplhr_profile",
+            "gplhr_gram", "gplhr_combine", "gplhr_orth", "gplhr_ordqz", "gplhr_mfactors", "gplhr_profile",
             "gplhr_profile_read", "gplhr_gram_noalloc", "gplhr_grad", "gplhr_solve_batched",
             "gplhr_iterate_batched"]
 KCLASS = {"spmm": 0, "gram": 1, "combine": 2, "precond": 3, "chol": 4, "other": 5}
@@ -47,7 +47,8 @@ class Precond(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("precision", C.c_int32),
                 ("no_lock", C.c_int32), ("products", C.c_int32), ("stream", C.c_void_p),
-                ("switch_tol", C.c_double), ("stall_iters", C.c_int32), ("pencil", C.c_int32)]
+                ("switch_tol", C.c_double), ("stall_iters", C.c_int32), ("pencil", C.c_int32),
+                ("fp64_gemm", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -92,6 +93,7 @@ def lib():
     L.gplhr_precond_apply.argtypes = [vp, vp, i32, i32, vp, i32]
     L.gplhr_gram.argtypes = [vp, vp, i32, i32, vp, i32, i32, vp, i32]
     L.gplhr_orth.argtypes = [vp, vp, i32, i32, vp]
+    L.gplhr_combine.argtypes = [vp, vp, i32, i32, vp, i32, vp, i32, i32, i32]
     L.gplhr_ordqz.argtypes = [i32, dp, dp, dbl, dbl, dp, dp, dp, dp]
     L.gplhr_mfactors.argtypes = [i32, dp, dp, dp, dp]
     L.gplhr_profile.argtypes = [vp, i32]
@@ -147,7 +149,7 @@ def gplhr_create(A, B, sigma: complex, k: int, m: int, precond: str = "none",
                  block_size: int = 1, T=None, tol: float = 1e-8, maxit: int = 500,
                  lock: bool = True, stream: int = 0, products: str = "auto",
                  precision: str = "fp64", switch_tol: float = 1e-5, stall_iters: int = 5,
-                 pencil: str = "factored", inner_steps: int = 0):
+                 pencil: str = "factored", inner_steps: int = 0, fp64_gemm: str = "tensor"):
     """Returns an opaque context handle (int).  A, B: SciPy CSR (B None = identity).
     inner_steps > 0: T = that many block GMRES steps on (A - sigma B) W = R,
     right-preconditioned by `precond`."""
@@ -158,7 +160,7 @@ def gplhr_create(A, B, sigma: complex, k: int, m: int, precond: str = "none",
     pc = Precond(PREC[precond], block_size, C.pointer(hT.desc) if hT else None, inner_steps)
     opts = Opts(tol, maxit, {"fp64": 0, "mixed": 1}[precision], 0 if lock else 1,
                 PRODUCTS[products], stream or None, switch_tol, stall_iters,
-                {"factored": 0, "gram": 1}[pencil])
+                {"factored": 0, "gram": 1}[pencil], {"tensor": 0, "dfma": 1}[fp64_gemm])
     out = C.c_void_p()
     st = L.gplhr_create(C.byref(hA.desc), C.byref(hB.desc) if hB else None, sigma.real,
                         sigma.imag, k, m, C.byref(pc), C.byref(opts), C.byref(out))
@@ -244,6 +246,13 @@ def gplhr_precond_apply(ctx, X, Y):
 
 
 GRAM_ARITH = {"fp64": 0, "fp32": 1, "exact32": 2}
+
+
+def gplhr_combine(ctx, X, C, Y, beta: bool = False, arith: str = "auto"):
+    """Y = X C (or Y + X C); device complex128 tensors, C (w x c) row-major."""
+    _check(lib().gplhr_combine(ctx, X.data_ptr(), X.stride(0), X.shape[1], C.data_ptr(), Y.shape[1],
+                               Y.data_ptr(), Y.stride(0), 1 if beta else 0,
+                               {"auto": 0, "dfma": 1}[arith]), ctx)
 
 
 def gplhr_gram(ctx, X, Y, Cout, arith: str = "fp64"):
@@ -350,11 +359,12 @@ class GPLHR:
 
     def __init__(self, A, B, sigma, k, m, precond="none", block_size=1, T=None, tol=1e-8,
                  maxit=500, lock=True, stream=0, products="auto", precision="fp64",
-                 switch_tol=1e-5, stall_iters=5, pencil="factored", inner_steps=0):
+                 switch_tol=1e-5, stall_iters=5, pencil="factored", inner_steps=0,
+                 fp64_gemm="tensor"):
         self.n, self.k = A.shape[0], k
         self.ctx = gplhr_create(A, B, complex(sigma), k, m, precond, block_size, T, tol, maxit,
                                 lock, stream, products, precision, switch_tol, stall_iters, pencil,
-                                inner_steps)
+                                inner_steps, fp64_gemm)
 
     def solve(self, V0=None, seed=0, allow_notconv=False):
         return gplhr_solve(self.ctx, V0, seed, allow_notconv)

@@ -451,3 +451,106 @@ def test_fp32_conversion_is_round_to_nearest_even(arith):
     # the conjugate of a zero imaginary part may carry either sign after the sum
     assert np.array_equal(np.abs(got_im), np.abs(want_im)) and \
         np.array_equal(got_im[want_im != 0], want_im[want_im != 0])
+
+
+# ------------------------------------------------- block combination (a11) --
+def _dot2_product(X, C):
+    """X C for complex128 X (n x w), C (w x c) in twice the working precision, rounded
+    once (Ogita, Rump and Oishi's Dot2: error-free products by Veltkamp splitting and
+    error-free sums, |error| <= u |XC| + 2 (K' u)^2 sum |x'||c'|), through the real form
+    X' = (Re x, Im x) per column, C' = [[Re c, Im c], [-Im c, Re c]] per entry."""
+    n, w = X.shape
+    c = C.shape[1]
+    Xr = np.empty((n, 2 * w))
+    Xr[:, 0::2], Xr[:, 1::2] = X.real, X.imag
+    Cr = np.empty((2 * w, 2 * c))
+    Cr[0::2, 0::2], Cr[0::2, 1::2], Cr[1::2, 0::2], Cr[1::2, 1::2] = C.real, C.imag, -C.imag, C.real
+
+    def split(a):
+        t = a * 134217729.0
+        hi = t - (t - a)
+        return hi, a - hi
+
+    s = np.zeros((n, 2 * c))
+    comp = np.zeros((n, 2 * c))
+    for k in range(2 * w):
+        a, b = Xr[:, k:k + 1], Cr[k:k + 1, :]
+        p = a * b
+        ah, al = split(a)
+        bh, bl = split(b)
+        e = al * bl - (((p - ah * bh) - al * bh) - ah * bl)
+        t = s + p
+        z = t - s
+        q = (s - (t - z)) + (p - z)
+        s = t
+        comp += q + e
+    y = s + comp
+    return y[:, 0::2] + 1j * y[:, 1::2]
+
+
+
+@pytest.mark.parametrize("n,w,c,beta", [(5000, 8, 8, False), (100003, 32, 16, True), (4099, 17, 5, False),
+                                        (2048, 32, 32, True), (777, 24, 40, False)])
+def test_combine_tensor_and_dfma_match_fp64(n, w, c, beta):
+    """Y = X C (+ Y) on the tensor cores (integer digits, FP32 accumulation) and by DFMA
+    against numpy's FP64 product.  Rows span 1e-30 .. 1e30 and include zero rows, C has
+    a zero column.  In the real form (K' = 2w terms per output, x' = Re/Im of x, c' of C)
+    the digit scheme errs by at most (K'/4 + 2) u max_k |x'_rk| sum_k |c'_kn| (u = 2^-53:
+    the input digits' rounding, the dropped digit pairs and one final rounding), a DFMA
+    dot product by at most (K' + 1) u (sum_k |x'_rk| |c'_kn| + |y_old|).  (777 rows,
+    40 columns: the DFMA path, outside the tensor-core shapes.)"""
+    rng = np.random.default_rng(40 + w)
+    Xh = _rand_block(rng, n, w) * np.exp(rng.uniform(-69, 69, size=n))[:, None]
+    Xh[::97] = 0.0
+    Ch = _rand_block(rng, w, c) * np.exp(rng.uniform(-3, 3, size=(w, c)))
+    Ch[:, min(2, c - 1)] = 0.0
+    Y0 = _rand_block(rng, n, c)
+    xy = _dot2_product(Xh, Ch)
+    ref = xy + (Y0 if beta else 0.0)
+    u, K = 2.0 ** -53, 2 * w
+    xmax = np.maximum(np.abs(Xh.real), np.abs(Xh.imag)).max(axis=1)[:, None]
+    csum = (np.abs(Ch.real) + np.abs(Ch.imag)).sum(axis=0)[None, :]
+    # the reference's own rounding (one of X C, one of the sum with Y), and beta's
+    slack = u * np.maximum(np.abs(xy.real), np.abs(xy.imag)) * 1.01
+    # beta = 1: the tensor-core path adds Y to its rounded product (one more rounding);
+    # the DFMA path starts its accumulator at Y, so every one of its K' roundings may
+    # carry |Y| as well
+    y0max = np.maximum(np.abs(Y0.real), np.abs(Y0.imag))
+    yold = {"auto": 2.0 * u * np.maximum(np.abs(ref.real), np.abs(ref.imag)) if beta else 0.0,
+            "dfma": (K + 1) * u * y0max if beta else 0.0}
+    A = sp.identity(n, format="csr")
+    ctx = G.gplhr_create(A, None, 0.5, 8, 2)
+    try:
+        for arith, fac in (("auto", K / 4 + 2), ("dfma", K + 1)):
+            bound = fac * u * xmax * csum + slack + yold[arith]
+            Y = _dev(Y0)
+            G.gplhr_combine(ctx, _dev(Xh), _dev(Ch), Y, beta, arith)
+            got = _host(Y)
+            err = np.maximum(np.abs(got.real - ref.real), np.abs(got.imag - ref.imag))
+            assert np.all(err <= bound), (arith, np.max(err / np.maximum(bound, 1e-300)))
+    finally:
+        G.gplhr_destroy(ctx)
+
+
+def test_combine_in_place_and_nonfinite():
+    """In place (Y = X, the X R^-1 step) on both paths, and a NaN in one row of X gives
+    NaN in that row only."""
+    rng = np.random.default_rng(5)
+    n, w = 3000, 16
+    Xh = _rand_block(rng, n, w)
+    Ch = np.triu(_rand_block(rng, w, w))
+    A = sp.identity(n, format="csr")
+    ctx = G.gplhr_create(A, None, 0.5, 8, 2)
+    try:
+        for arith in ("auto", "dfma"):
+            X = _dev(Xh)
+            G.gplhr_combine(ctx, X, _dev(Ch), X, False, arith)
+            assert np.allclose(_host(X), Xh @ Ch, rtol=0, atol=1e-13 * np.abs(Xh @ Ch).max())
+            Xn = Xh.copy()
+            Xn[123, 4] = np.nan
+            Y = torch.zeros((n, w), dtype=torch.complex128, device=DEV)
+            G.gplhr_combine(ctx, _dev(Xn), _dev(Ch), Y, False, arith)
+            bad = ~np.isfinite(_host(Y)).all(axis=1)
+            assert bad[123] and bad.sum() == 1, (arith, np.flatnonzero(bad)[:5])
+    finally:
+        G.gplhr_destroy(ctx)
