@@ -382,8 +382,8 @@ gplhr_status combine_tc(gplhr_ctx* ctx, gplhr::CombArgs a, int wsum, int c, int 
   t.tmem_cols = 32;
   while (t.tmem_cols < gplhr::TC_DIAG * t.np) t.tmem_cols <<= 1;
   t.err = ctx->d_diag + 2;
-  const size_t smem = (size_t)gplhr::TC_DIGITS * (gplhr::TC_ROWS + t.np) * t.kp * sizeof(uint16_t) +
-                      2 * t.np * sizeof(int);
+  const size_t smem = ((size_t)gplhr::TC_DIGITS * gplhr::TC_ROWS + (size_t)gplhr::TC_DIAG * t.np) * t.kp *
+                          sizeof(uint16_t) + 2 * t.np * sizeof(int);
   // at most 4 per SM: the per-CTA norm partials are sized for 4 CTAs per SM
   const int per_sm = std::max(1, std::min({(int)((227 * 1024) / (smem + 4096)), 512 / t.tmem_cols, 4}));
   const int ntiles = (ctx->n + gplhr::TC_ROWS - 1) / gplhr::TC_ROWS;

@@ -11,10 +11,13 @@
 //   digits, S = sum_{a=0..6} s_a 256^(6 - a) with s_1..s_6 in [-128, 127] and
 //   |s_0| <= 128 (exact in bf16); column n of C' likewise with its bound G_n;
 // * the tensor core forms the digit diagonals D_d = sum_{a + b = d} X'_a C'_b for
-//   d = 0..7 (34 digit-pair products).  |s_a s_b| <= 2^14, at most 7 pairs per diagonal
-//   and K' <= 64, so |D_d| < 7 2^20: every FP32 partial sum is an exact integer;
-// * y = 2^(T_r + G_n - 68) Z, Z = sum_d D_d 256^(7 - d) formed exactly in 128-bit
-//   integers and rounded once to double (nearest, ties to even).
+//   d = 0..7 (34 digit-pair products).  The 7 digit planes of C' and a zero plane are
+//   stacked along N, so one MMA of X'_a against planes b = 0..7-a, written at accumulator
+//   column a N', lands each product X'_a C'_b on diagonal a + b: 7 MMAs per K step (N
+//   split at 256).  |s_a s_b| <= 2^14, at most 7 pairs per diagonal and K' <= 64, so
+//   |D_d| < 7 2^20: every FP32 partial sum is an exact integer;
+// * y = 2^(T_r + G_n - 68) Z, Z = sum_d D_d 256^(7 - d) formed exactly in 96-bit
+//   integer arithmetic and rounded once to double (nearest, ties to even).
 // Error per output: input rounding <= 2^-55 (max_k |x_rk| sum_k |c_kn| + K' max_k |x_rk|
 // max_k |c_kn|), the dropped pairs a + b >= 8 (weight <= 2^-62 K' 2^(T_r + G_n) in all),
 // and the final rounding: at most (K'/4 + 2) u max_k |x_rk| sum_k |c_kn| with u = 2^-53,
@@ -126,28 +129,43 @@ __device__ __forceinline__ uint32_t tc_pack2(float lo, float hi) {
   return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 
-// 2^p Z for a signed 128-bit integer Z, rounded once to the nearest double (ties to
-// even); a result below 2^-1022 is rounded a second time to the subnormal grid.
-__device__ __forceinline__ double tc_i128_ldexp(__int128 z, int p) {
-  if (z == 0) return 0.0;
-  const bool neg = z < 0;
-  unsigned __int128 m = neg ? (unsigned __int128)(-z) : (unsigned __int128)z;
-  const uint64_t mh = (uint64_t)(m >> 64), ml = (uint64_t)m;
-  const int lz = mh ? __clzll((long long)mh) : 64 + __clzll((long long)ml);
-  m <<= lz;  // leading one at bit 127
-  const uint64_t top = (uint64_t)(m >> 64);
-  const bool sticky = (uint64_t)m != 0;
-  uint64_t mant = top >> 11;  // 53 bits
-  const uint64_t rb = top & 0x7FF;
-  if (rb > 0x400 || (rb == 0x400 && (sticky || (mant & 1)))) ++mant;
-  int e = 127 - lz + p;  // exponent of the leading one
-  if (mant >> 53) {
-    mant >>= 1;
-    ++e;
+// 2^p (hi 2^32 + lo) for |hi|, |lo| < 2^48, rounded once to the nearest double (ties
+// to even), in integer arithmetic; a result below 2^-1022 takes a second rounding to the
+// subnormal grid.
+__device__ __forceinline__ double tc_round96(long long hi, long long lo, int p) {
+  long long zh = hi + (lo >> 32);  // value = zh 2^32 + zl, zl in [0, 2^32)
+  uint32_t zl = (uint32_t)lo;
+  const bool neg = zh < 0;
+  if (neg) {  // 96-bit negation
+    zh = -zh - (zl != 0u ? 1 : 0);
+    zl = 0u - zl;
   }
+  const uint64_t uh = (uint64_t)zh;  // < 2^49
+  if (uh == 0 && zl == 0) return 0.0;
+  uint64_t mant;  // 53 bits, leading one at bit 52
+  int e;          // exponent of the leading one
+  if (uh < (1ull << 21)) {  // below 2^53: exact
+    const uint64_t v = (uh << 32) | zl;
+    const int lz = __clzll((long long)v);
+    mant = v << (lz - 11);
+    e = 63 - lz;
+  } else {
+    const int L = 64 - __clzll((long long)uh);  // 22..49 bits above zl
+    const int sh = L - 21;                       // 1..28 bits of zl dropped
+    mant = (uh << (32 - sh)) | (zl >> sh);
+    const uint32_t rem = zl << (32 - sh);        // the dropped bits, left-aligned
+    if (rem > 0x80000000u || (rem == 0x80000000u && (mant & 1))) ++mant;
+    e = L + 31;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++e;
+    }
+  }
+  e += p;
   const uint64_t sgn = neg ? (1ull << 63) : 0ull;
   if (e > 1023) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull));
-  if (e >= -1022) return __longlong_as_double((long long)(sgn | ((uint64_t)(e + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+  if (e >= -1022)
+    return __longlong_as_double((long long)(sgn | ((uint64_t)(e + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
   const double d = scalbn((double)mant, e - 52);
   return neg ? -d : d;
 }
@@ -184,14 +202,14 @@ __device__ __forceinline__ double tc_cval(const CombArgs& a, int wsum, int kk, i
 // tid / 128) loads and splits the row's k-chunks kc = h, h + 2, ... (8 reals each) and
 // writes the output column groups nb = 8 h, 8 h + 16, ...  Warp w reads tensor-memory
 // lanes 32 (w % 4) .. +31, which hold rows 32 (w % 4) .. +31 of the tile.
-__global__ void __launch_bounds__(TC_THREADS, 1) tc_combine_kernel(int n, TcCombArgs ta) {
+__global__ void __launch_bounds__(TC_THREADS, 2) tc_combine_kernel(int n, TcCombArgs ta) {
   const CombArgs& a = ta.a;
   if (a.skip && *a.skip == 0) return;
   extern __shared__ __align__(128) unsigned char tc_smem[];
   const int kp = ta.kp, np = ta.np, KC = kp >> 3;
   uint16_t* sA = reinterpret_cast<uint16_t*>(tc_smem);         // TC_DIGITS x 128 x kp
-  uint16_t* sB = sA + TC_DIGITS * TC_ROWS * kp;                // TC_DIGITS x np x kp
-  int* sG = reinterpret_cast<int*>(sB + TC_DIGITS * np * kp);  // np column exponents
+  uint16_t* sB = sA + TC_DIGITS * TC_ROWS * kp;                // 8 np x kp: plane b, column n
+  int* sG = reinterpret_cast<int*>(sB + TC_DIAG * np * kp);    // at row b np + n; plane 7 zero
   int* sBadC = sG + np;                                        // np non-finite flags
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t taddr_s;
@@ -238,7 +256,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_combine_kernel(int n, TcComb
     tc_digits(tc_cval(a, wsum, kk, nn), sG[nn], dg);
 #pragma unroll
     for (int d = 0; d < TC_DIGITS; ++d)
-      sB[d * np * kp + tc_off(nn, kk, KC)] = (uint16_t)(__float_as_uint(dg[d]) >> 16);
+      sB[tc_off(d * np + nn, kk, KC)] = (uint16_t)(__float_as_uint(dg[d]) >> 16);
+    sB[tc_off(TC_DIGITS * np + nn, kk, KC)] = 0;
   }
   if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
   if (warp == 0) {
@@ -252,8 +271,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_combine_kernel(int n, TcComb
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = taddr_s;
-  const uint32_t idesc = umma_idesc_bf16(TC_ROWS, np);
-  const uint32_t a_slice = TC_ROWS * kp * 2, b_slice = np * kp * 2;  // bytes
+  const uint32_t a_slice = TC_ROWS * kp * 2;  // bytes
   const uint32_t sA_addr = smem_u32(sA), sB_addr = smem_u32(sB);
   const int ntiles = (n + TC_ROWS - 1) / TC_ROWS;
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
@@ -308,14 +326,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_combine_kernel(int n, TcComb
     bad = sT[0][rl] | sT[1][rl];
     if (tid == 0) {
       tc_fence_after();
+      // plane da of X' against C' planes 0 .. 7 - da (stack rows 0 .. (8 - da) np) at
+      // accumulator column da np; the first MMA (ks = 0, da = 0, all 8 planes)
+      // initialises every diagonal
       for (int ks = 0; ks < kp / 16; ++ks)
-        for (int da = 0; da < TC_DIGITS; ++da)
-          for (int db = 0; db < TC_DIGITS && da + db < TC_DIAG; ++db) {
-            const int d = da + db, first_da = d > TC_DIGITS - 1 ? d - (TC_DIGITS - 1) : 0;
-            const uint64_t ad = umma_desc(sA_addr + da * a_slice + ks * 256, 128, KC * 128);
-            const uint64_t bd = umma_desc(sB_addr + db * b_slice + ks * 256, 128, KC * 128);
-            umma_bf16(tmem + (uint32_t)(d * np), ad, bd, idesc, (ks > 0 || da > first_da) ? 1 : 0);
+        for (int da = 0; da < TC_DIGITS; ++da) {
+          const uint64_t ad = umma_desc(sA_addr + da * a_slice + ks * 256, 128, KC * 128);
+          const int ntot = (TC_DIAG - da) * np;
+          for (int c0 = 0; c0 < ntot; c0 += 256) {
+            const int nc = min(256, ntot - c0);
+            const uint64_t bd = umma_desc(sB_addr + (uint32_t)(c0 >> 3) * (uint32_t)(KC * 128) + ks * 256, 128, KC * 128);
+            umma_bf16(tmem + (uint32_t)(da * np + c0), ad, bd, umma_idesc_bf16(TC_ROWS, nc), (ks > 0 || da > 0) ? 1 : 0);
           }
+        }
       umma_commit(&mbar);
     }
     // wait for the products (bounded)
@@ -340,13 +363,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_combine_kernel(int n, TcComb
         double yv[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          long long hi = 0, lo = 0;
-#pragma unroll
-          for (int d = 0; d < 4; ++d) hi = hi * 256 + tc_f2i(acc[d][u + q]);
-#pragma unroll
-          for (int d = 4; d < 8; ++d) lo = lo * 256 + tc_f2i(acc[d][u + q]);
-          const __int128 z = ((__int128)hi << 32) + lo;
-          yv[q] = tc_i128_ldexp(z, T + sG[nn + q] - 68);
+          const long long hi = (long long)tc_f2i(acc[0][u + q]) * 16777216ll +
+                               (long long)tc_f2i(acc[1][u + q]) * 65536ll +
+                               (long long)tc_f2i(acc[2][u + q]) * 256ll + (long long)tc_f2i(acc[3][u + q]);
+          const long long lo = (long long)tc_f2i(acc[4][u + q]) * 16777216ll +
+                               (long long)tc_f2i(acc[5][u + q]) * 65536ll +
+                               (long long)tc_f2i(acc[6][u + q]) * 256ll + (long long)tc_f2i(acc[7][u + q]);
+          yv[q] = tc_round96(hi, lo, T + sG[nn + q] - 68);
           if (bad || sBadC[nn + q]) yv[q] = __longlong_as_double(0x7FF8000000000000ll);
         }
         double2 y = make_double2(yv[0], yv[1]);
