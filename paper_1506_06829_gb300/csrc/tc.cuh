@@ -69,6 +69,11 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -200,7 +205,7 @@ __device__ __forceinline__ double tc_cval(const CombArgs& a, int wsum, int kk, i
 
 // One persistent CTA per (SM, slot); 128 rows per tile, thread (r, h) = (tid % 128,
 // tid / 128) loads and splits the row's k-chunks kc = h, h + 2, ... (8 reals each) and
-// writes the output column groups nb = 8 h, 8 h + 16, ...  Warp w reads tensor-memory
+// writes the output column groups nb = 4 h, 4 h + 8, ...  Warp w reads tensor-memory
 // lanes 32 (w % 4) .. +31, which hold rows 32 (w % 4) .. +31 of the tile.
 __global__ void __launch_bounds__(TC_THREADS, 2) tc_combine_kernel(int n, TcCombArgs ta) {
   const CombArgs& a = ta.a;
@@ -280,6 +285,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_combine_kernel(int n, TcComb
   for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, parity ^= 1) {
     const int r = tile * TC_ROWS + rl;
     const bool valid = r < n;
+    {  // this row of the CTA's next tile into L2 while this tile is processed
+      const int r2 = r + gridDim.x * TC_ROWS;
+      if (h == 0 && r2 < n)
+        for (int t = 0; t < a.nin; ++t)
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.in[t].X + (size_t)r2 * a.in[t].ldx),
+                       "r"((uint32_t)(a.in[t].w * 16))
+                       : "memory");
+    }
     // this thread's k-chunks of the row: 4 complex values each, in registers
     double xv[TC_KMAX / 2];
     int T = TC_NOEXP, bad = 0;
@@ -307,18 +320,20 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_combine_kernel(int n, TcComb
     for (int i = 0; i < TC_KMAX / 16; ++i) {
       const int kc = 2 * i + h;
       if (kc < KC) {
-        float dg[8][TC_DIGITS];
+        // two values at a time (few live registers, so the compiler can interleave)
+        uint32_t wv[TC_DIGITS][4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) tc_digits(xv[8 * i + u], T, dg[u]);
+        for (int q = 0; q < 4; ++q) {
+          float d0[TC_DIGITS], d1[TC_DIGITS];
+          tc_digits(xv[8 * i + 2 * q], T, d0);
+          tc_digits(xv[8 * i + 2 * q + 1], T, d1);
 #pragma unroll
-        for (int d = 0; d < TC_DIGITS; ++d) {
-          uint4 w;
-          w.x = tc_pack2(dg[0][d], dg[1][d]);
-          w.y = tc_pack2(dg[2][d], dg[3][d]);
-          w.z = tc_pack2(dg[4][d], dg[5][d]);
-          w.w = tc_pack2(dg[6][d], dg[7][d]);
-          *reinterpret_cast<uint4*>(sA + d * TC_ROWS * kp + tc_off(rl, kc * 8, KC)) = w;
+          for (int d = 0; d < TC_DIGITS; ++d) wv[d][q] = tc_pack2(d0[d], d1[d]);
         }
+#pragma unroll
+        for (int d = 0; d < TC_DIGITS; ++d)
+          *reinterpret_cast<uint4*>(sA + d * TC_ROWS * kp + tc_off(rl, kc * 8, KC)) =
+              make_uint4(wv[d][0], wv[d][1], wv[d][2], wv[d][3]);
       }
     }
     fence_async_smem();
@@ -350,14 +365,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_combine_kernel(int n, TcComb
       break;
     }
     tc_fence_after();
-    for (int nb = 8 * h; nb < np; nb += 16) {
-      uint32_t acc[TC_DIAG][8];
+    for (int nb = 4 * h; nb < np; nb += 8) {  // groups of 4 real columns, alternating halves
+      uint32_t acc[TC_DIAG][4];
 #pragma unroll
-      for (int d = 0; d < TC_DIAG; ++d) tmem_ld8(tmem + lane_base + (uint32_t)(d * np + nb), acc[d]);
+      for (int d = 0; d < TC_DIAG; ++d) tmem_ld4(tmem + lane_base + (uint32_t)(d * np + nb), acc[d]);
       tmem_wait_ld();
       if (!valid) continue;
 #pragma unroll
-      for (int u = 0; u < 8; u += 2) {
+      for (int u = 0; u < 4; u += 2) {
         const int nn = nb + u, l = nn >> 1;
         if (l >= a.c) continue;
         double yv[2];
