@@ -237,7 +237,7 @@ def main():
     }
     spmm, gram = per_class["spmm"], per_class["gram"]
     hbm = {c: {"GB/s": (per_class[c]["gbyte"] / (per_class[c]["ms"] / 1e3)) if per_class[c]["ms"] else 0.0}
-           for c in ("spmm", "gram")}
+           for c in ("spmm", "gram", "combine")}
     for c in hbm:
         hbm[c]["frac_of_measured_peak"] = hbm[c]["GB/s"] / hbm_peak
     s_per_iter = ms / 1e3 / K
