@@ -362,33 +362,43 @@ def e2e(pr, K, stream, G):
 def batched_throughput(G, K):
     """Batched workload (64 pencils of uneven size + 16 shifts over a 128^2 pencil): K
     iterations of every context, concurrently (one stream per context, a host thread
-    pool) and one context at a time; pencil-iterations per second of each."""
+    pool) and one context at a time; pencil-iterations per second of each, with kernel
+    launches and with each iteration's device segments replayed from CUDA graphs."""
     import torch
     from paper_1506_06829_gb300 import problems as P
     ps = P.config4()
-    solvers = [G.GPLHR(p.A, p.B, p.sigma, p.k, p.m, p.precond, p.block_size, tol=p.tol, maxit=10 ** 6)
-               for p in ps]
-    for s, p in zip(solvers, ps):
-        s.start(p.start_block())
-    ctxs = [s.ctx for s in solvers]
-    G.gplhr_iterate_batched(ctxs, 2)                  # warm-up
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st, infos, _ = G.gplhr_iterate_batched(ctxs, K)
-    torch.cuda.synchronize()
-    t_batched = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    G.gplhr_iterate_batched(ctxs, K, nthreads=1)
-    torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
-    for s in solvers:
-        s.close()
+
+    def run(graphs):
+        solvers = [G.GPLHR(p.A, p.B, p.sigma, p.k, p.m, p.precond, p.block_size, tol=p.tol, maxit=10 ** 6,
+                           graphs=graphs) for p in ps]
+        for s, p in zip(solvers, ps):
+            s.start(p.start_block())
+        ctxs = [s.ctx for s in solvers]
+        G.gplhr_iterate_batched(ctxs, 2)                  # warm-up (and graph capture)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, infos, _ = G.gplhr_iterate_batched(ctxs, K)
+        torch.cuda.synchronize()
+        t_batched = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        G.gplhr_iterate_batched(ctxs, K, nthreads=1)
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+        for s in solvers:
+            s.close()
+        return t_batched, t_seq, int(st)
+
     units = len(ps) * K
+    tb, ts, st = run(False)
+    gb, gs, gst = run(True)
     return {"workload": f"{len(ps)} contexts: 64 convection-diffusion pencils (grid sides 16..96, B = MxM, k = 4) "
                         "+ 16 shifts over a 128^2 pencil (k = 8), Jacobi, FP64",
-            "pencil_iterations_per_s": units / t_batched, "sequential_pencil_iterations_per_s": units / t_seq,
-            "speedup_vs_sequential": t_seq / t_batched, "threads": os.cpu_count(), "iterations": K,
-            "status": int(st)}
+            "pencil_iterations_per_s": units / gb, "sequential_pencil_iterations_per_s": units / gs,
+            "speedup_vs_sequential": gs / gb,
+            "without_graphs": {"pencil_iterations_per_s": units / tb,
+                               "sequential_pencil_iterations_per_s": units / ts, "status": st},
+            "graphs": "each iteration's three device segments replayed from CUDA graphs",
+            "threads": os.cpu_count(), "iterations": K, "status": gst}
 
 
 def time_to_pairs(G, stream, precision, inner_steps=0):

@@ -118,10 +118,19 @@ typedef struct {
                           and the orthonormalisation of (A - sigma B)[W S P]); 1 = both
                           U^*AZ and U^*BZ by Gram products (Alg. 2 step 24 as printed)   */
   int32_t fp64_gemm;   /* [0]    FP64 block combinations: 0 = on the tensor cores (tcgen05,
-                          each double split into 8 integer digits of 7 bits, exact FP32
-                          accumulation of digit products, error ~2^-53 max|x| sum|c| like
-                          a DFMA product) where the shape allows (<= 32 input and output
-                          columns), DFMA otherwise; 1 = DFMA only                         */
+                          each double split into 7 balanced 8-bit integer digits, exact
+                          FP32 accumulation of digit-pair products, error at most
+                          (K'/4 + 2) 2^-53 max|x| sum|c| over K' real terms, below the
+                          DFMA bound) where the shape allows (<= 32 input and output
+                          columns, n >= 512), DFMA otherwise; 1 = DFMA only               */
+  int32_t graphs;      /* [0]    1 = capture the device work of each iteration between its
+                          host round trips (three segments) in CUDA graphs on first use
+                          and replay them afterwards: one graph launch instead of tens of
+                          kernel launches per segment, for small pencils where launch
+                          overhead dominates.  A graph is kept per state that fixes the
+                          launch sequence (locked pairs, m, P present, precision phase).
+                          Not used while gplhr_profile timing is on or with inner GMRES
+                          steps (their least squares runs on the host inside T).          */
 } gplhr_opts;
 
 /* Per-solve report.  resid[j] (j < k) is the backward error of pair j,

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -126,6 +127,18 @@ struct gplhr_ctx {
   std::vector<std::pair<int, int>> ev_rec;  // (class, start event index); stop = start + 1
   double k_flops[8] = {0}, k_bytes[8] = {0};
   int64_t k_launch[8] = {0};
+  // CUDA graphs of an iteration's device segments (opts.graphs), keyed by the state
+  // that fixes their launch sequence, with the accounting each replay adds
+  struct Counters {
+    double k_flops[8], k_bytes[8];
+    int64_t k_launch[8], n_launch, n_spmm, n_prec, h2d, d2h;
+  };
+  struct SegGraph {
+    cudaGraphExec_t exec;
+    Counters delta;
+  };
+  bool graphs = false;
+  std::map<uint64_t, SegGraph> seg_graphs;
   std::string err;
 };
 
@@ -182,6 +195,86 @@ int prof_begin(gplhr_ctx* ctx, int c, double flops, double bytes, int launches =
 }
 void prof_end(gplhr_ctx* ctx, int h) {
   if (h >= 0) cudaEventRecord(ctx->ev_pool[h + 1], ctx->stream);
+}
+
+gplhr_ctx::Counters snap_counters(const gplhr_ctx* ctx) {
+  gplhr_ctx::Counters c;
+  for (int i = 0; i < 8; ++i) {
+    c.k_flops[i] = ctx->k_flops[i];
+    c.k_bytes[i] = ctx->k_bytes[i];
+    c.k_launch[i] = ctx->k_launch[i];
+  }
+  c.n_launch = ctx->n_launch;
+  c.n_spmm = ctx->n_spmm;
+  c.n_prec = ctx->n_prec;
+  c.h2d = ctx->h2d_bytes;
+  c.d2h = ctx->d2h_bytes;
+  return c;
+}
+
+// Device work of one segment of an iteration (a run of launches and copies between two
+// host round trips), issued by `issue` on the context's stream.  With opts.graphs the
+// first run for a given key is captured into a CUDA graph, which later runs replay;
+// every kernel argument of the segment must then be fixed by the key, and the small
+// coefficient matrices reach the device through pinned staging buffers that the host
+// fills before the segment runs (the graph's copies read them when it executes).
+gplhr_status run_segment(gplhr_ctx* ctx, uint64_t key, const std::function<gplhr_status()>& issue) {
+  if (!ctx->graphs || ctx->prof_on || ctx->gm_steps > 0) return issue();
+  auto it = ctx->seg_graphs.find(key);
+  if (it != ctx->seg_graphs.end()) {
+    CK(cudaGraphLaunch(it->second.exec, ctx->stream));
+    const gplhr_ctx::Counters& d = it->second.delta;
+    for (int i = 0; i < 8; ++i) {
+      ctx->k_flops[i] += d.k_flops[i];
+      ctx->k_bytes[i] += d.k_bytes[i];
+      ctx->k_launch[i] += d.k_launch[i];
+    }
+    ctx->n_launch += d.n_launch;
+    ctx->n_spmm += d.n_spmm;
+    ctx->n_prec += d.n_prec;
+    ctx->h2d_bytes += d.h2d;
+    ctx->d2h_bytes += d.d2h;
+    return GPLHR_OK;
+  }
+  const gplhr_ctx::Counters c0 = snap_counters(ctx);
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  const gplhr_status st = issue();
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+  if (st != GPLHR_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    ctx->err = std::string("stream capture of an iteration segment: ") + cudaGetErrorString(e);
+    return GPLHR_ECUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  CK(ei);
+  const gplhr_ctx::Counters c1 = snap_counters(ctx);
+  gplhr_ctx::Counters d;
+  for (int i = 0; i < 8; ++i) {
+    d.k_flops[i] = c1.k_flops[i] - c0.k_flops[i];
+    d.k_bytes[i] = c1.k_bytes[i] - c0.k_bytes[i];
+    d.k_launch[i] = c1.k_launch[i] - c0.k_launch[i];
+  }
+  d.n_launch = c1.n_launch - c0.n_launch;
+  d.n_spmm = c1.n_spmm - c0.n_spmm;
+  d.n_prec = c1.n_prec - c0.n_prec;
+  d.h2d = c1.h2d - c0.h2d;
+  d.d2h = c1.d2h - c0.d2h;
+  ctx->seg_graphs[key] = gplhr_ctx::SegGraph{ex, d};
+  CK(cudaGraphLaunch(ex, ctx->stream));  // the capture recorded the work; run it (counted once above)
+  return GPLHR_OK;
+}
+
+// Key of a segment's launch sequence: segment id and the iteration state it depends on.
+uint64_t seg_key(int seg, int q, int m, int kk, int s, int flags) {
+  return (uint64_t)seg | ((uint64_t)(q & 0xFF) << 4) | ((uint64_t)(m & 0xFF) << 12) | ((uint64_t)(kk & 0xFF) << 20) |
+         ((uint64_t)(s & 0xFFFF) << 28) | ((uint64_t)(flags & 0xFF) << 44);
 }
 
 // ------------------------------------------------------------------ launches --
@@ -739,13 +832,16 @@ gplhr_status residuals(gplhr_ctx* ctx) {
       h1[i * 2 * k + k + j] = d2(Ze(i, j) * ctx->RB(j, j));
       h2[i * 2 * k + k + j] = d2(Ze(i, j) * ctx->RA(j, j));
     }
-  TRY(upload(ctx, ctx->dC1, h1, 2 * k * k));
-  TRY(upload(ctx, ctx->dC2, h2, 2 * k * k));
-  TRY(combine(ctx, {In{blkAZ(ctx, 0), k, ctx->dC1, kOne}, In{blkBZ(ctx, 0), k, ctx->dC2, kMinusOne}},
-              Blk{ctx->Rw, k}, 2 * k, false, nullptr, Blk{nullptr, 0}, k, k));
-  ctx->d2h_bytes += k * sizeof(double) + 2 * sizeof(int);
-  CK(cudaMemcpyAsync(ctx->h_norms, ctx->d_norms, k * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->h_diag, ctx->d_diag, 3 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  TRY(run_segment(ctx, seg_key(3, 0, 0, 0, 0, ctx->bulk32 ? 1 : 0), [&]() -> gplhr_status {
+    TRY(upload(ctx, ctx->dC1, h1, 2 * k * k));
+    TRY(upload(ctx, ctx->dC2, h2, 2 * k * k));
+    TRY(combine(ctx, {In{blkAZ(ctx, 0), k, ctx->dC1, kOne}, In{blkBZ(ctx, 0), k, ctx->dC2, kMinusOne}},
+                Blk{ctx->Rw, k}, 2 * k, false, nullptr, Blk{nullptr, 0}, k, k));
+    ctx->d2h_bytes += k * sizeof(double) + 3 * sizeof(int);
+    CK(cudaMemcpyAsync(ctx->h_norms, ctx->d_norms, k * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_diag, ctx->d_diag, 3 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    return GPLHR_OK;
+  }));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->resid.assign(k, 0.0);
   for (int j = 0; j < k; ++j) {
@@ -920,16 +1016,17 @@ bool converged_update(gplhr_ctx* ctx) {
 // triangular [[R_A - sigma R_B, C], [0, R]] and only Psi = U^* B Z needs a Gram product.
 // The QZ runs on (F, Psi), whose eigenvalues are lambda - sigma (sorted by modulus), and
 // Rbar_A = Rbar_F + sigma Rbar_Psi.
-gplhr_status factored_pencil_qz(gplhr_ctx* ctx, int s, int sk, SqMat& RAb, SqMat& RBb, SqMat& YLb, SqMat& YRb,
-                                int cv) {
+// Device part: Psi = U^* B Z and the tracked factors of U's construction, copied to the
+// pinned host buffers (the caller synchronises before factored_pencil_qz).
+gplhr_status factored_pencil_issue(gplhr_ctx* ctx, int s, int sk) {
   const int k = ctx->k;
   const int smax2 = ctx->s_max * ctx->s_max;
   TRY(gram(ctx, blkU(ctx, 0), s, blkBZ(ctx, 0), s, Blk{nullptr, 0}, 0, ctx->dPhiPsi));
   const size_t nC = (size_t)k * sk, nR = (size_t)sk * sk;
-  double2* hPsi = ctx->h_phipsi;
   double2* hC = ctx->h_track;                // 3 x nC
   double2* hR = ctx->h_track + 3 * nC;       // 3 x nR
-  CK(cudaMemcpyAsync(hPsi, ctx->dPhiPsi, (size_t)s * s * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_phipsi, ctx->dPhiPsi, (size_t)s * s * sizeof(double2), cudaMemcpyDeviceToHost,
+                     ctx->stream));
   for (int p = 0; p < 3; ++p) {
     CK(cudaMemcpyAsync(hC + p * nC, ctx->dTrackC + (size_t)p * ctx->trk, nC * sizeof(double2), cudaMemcpyDeviceToHost,
                        ctx->stream));
@@ -938,7 +1035,17 @@ gplhr_status factored_pencil_qz(gplhr_ctx* ctx, int s, int sk, SqMat& RAb, SqMat
   }
   CK(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   ctx->d2h_bytes += (int64_t)((size_t)s * s + 3 * (nC + nR)) * sizeof(double2) + sizeof(int);
-  CK(cudaStreamSynchronize(ctx->stream));
+  return GPLHR_OK;
+}
+
+// Host part (after the synchronisation): the pencil (F, Psi) and its sorted QZ.
+gplhr_status factored_pencil_qz(gplhr_ctx* ctx, int s, int sk, SqMat& RAb, SqMat& RBb, SqMat& YLb, SqMat& YRb,
+                                int cv) {
+  const int k = ctx->k;
+  const size_t nC = (size_t)k * sk, nR = (size_t)sk * sk;
+  double2* hPsi = ctx->h_phipsi;
+  double2* hC = ctx->h_track;
+  double2* hR = ctx->h_track + 3 * nC;
   const int passes = ctx->h_status[0] != 0 ? 3 : 2;
   auto Cm = [&](int p) {
     SqMat M(std::max(k, sk));
@@ -1005,13 +1112,14 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
   const int sm = ctx->s_max;
   const Blk V = blkZ(ctx, 0), Q = blkU(ctx, 0);
   const Blk right = ctx->hasB ? Q : V;  // projector before T: (I - QQ^*), or (I - VV^*) if B = I
-  // steps 7-8 / 10: W = (I - VV^*) T (I - QQ^*) R, active columns q..k-1
-  Blk Ra{ctx->Rw + q, k};
-  TRY(project_out(ctx, right, k, Ra, kk));
-  TRY(precond_apply(ctx, Ra, kk, blkZ(ctx, k)));
-  TRY(orth_against(ctx, V, k, blkZ(ctx, k), kk));                           // step 12 (with (I - VV^*))
-  TRY(spmm_AB(ctx, blkZ(ctx, k), kk, blkAZ(ctx, k), blkBZ(ctx, k)));
-  // steps 13-20: Krylov-Arnoldi blocks S_l
+  const bool withP = ctx->hasP && kk > 0;
+  const int pslot = k + (m + 1) * kk;
+  const int sP = withP ? kk : 0;
+  const int s = pslot + sP;
+  const int sk = s - k;
+  const int cv = k + kk;  // only the leading k + kk positions of the ordering are used (V and P)
+  const int flags = (ctx->bulk32 ? 1 : 0) | (ctx->recompute ? 2 : 0) | (ctx->factored ? 4 : 0) | (withP ? 8 : 0);
+  // host staging of segment A: M_B, M_A of the active pairs for the S-recurrence
   if (m > 0) {
     double2* hm = ctx->h_small + 4 * k * k;
     for (int i = 0; i < kk; ++i)
@@ -1019,89 +1127,95 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
         hm[i * kk + j] = d2(ctx->MB(q + i, q + j));
         hm[kk * kk + i * kk + j] = d2(ctx->MA(q + i, q + j));
       }
-    TRY(upload(ctx, ctx->dMBa, hm, 2 * kk * kk));
   }
-  for (int l = 1; l <= m; ++l) {
-    const int prev = k + (l - 1) * kk, cur = k + l * kk;
-    Blk X{ctx->Rw, k};
-    TRY(combine(ctx, {In{blkAZ(ctx, prev), kk, ctx->dMBa, kOne},
-                      In{blkBZ(ctx, prev), kk, ctx->dMBa + kk * kk, kMinusOne}},
-                X, kk, false));
-    TRY(project_out(ctx, right, k, X, kk));
-    TRY(precond_apply(ctx, X, kk, blkZ(ctx, cur)));
-    TRY(orth_against(ctx, V, cur, blkZ(ctx, cur), kk));                      // against V, W, S_1..S_{l-1}
-    TRY(spmm_AB(ctx, blkZ(ctx, cur), kk, blkAZ(ctx, cur), blkBZ(ctx, cur)));
-  }
-  // step 21: P against V, W, S and orth; AP, BP follow by the same transforms
-  int sP = 0;
-  const int pslot = k + (m + 1) * kk;
-  if (ctx->hasP && kk > 0) {
-    const size_t nw = (size_t)ctx->n;
-    const int ncopy = ctx->recompute ? 1 : (ctx->hasB ? 3 : 2);
-    const int ph = prof_begin(ctx, KC_OTHER, 0.0, 32.0 * ctx->n * kk * ncopy, ncopy);
-    gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-        ctx->n, kk, ctx->Pb, k, ctx->Z + pslot, sm);
-    if (!ctx->recompute) {
+  // segment A: steps 7-24 up to the copies of the projected pencil to the host
+  TRY(run_segment(ctx, seg_key(1, q, m, kk, s, flags), [&]() -> gplhr_status {
+    // steps 7-8 / 10: W = (I - VV^*) T (I - QQ^*) R, active columns q..k-1
+    Blk Ra{ctx->Rw + q, k};
+    TRY(project_out(ctx, right, k, Ra, kk));
+    TRY(precond_apply(ctx, Ra, kk, blkZ(ctx, k)));
+    TRY(orth_against(ctx, V, k, blkZ(ctx, k), kk));  // step 12 (with (I - VV^*))
+    TRY(spmm_AB(ctx, blkZ(ctx, k), kk, blkAZ(ctx, k), blkBZ(ctx, k)));
+    // steps 13-20: Krylov-Arnoldi blocks S_l
+    if (m > 0) TRY(upload(ctx, ctx->dMBa, ctx->h_small + 4 * k * k, 2 * kk * kk));
+    for (int l = 1; l <= m; ++l) {
+      const int prev = k + (l - 1) * kk, cur = k + l * kk;
+      Blk X{ctx->Rw, k};
+      TRY(combine(ctx, {In{blkAZ(ctx, prev), kk, ctx->dMBa, kOne},
+                        In{blkBZ(ctx, prev), kk, ctx->dMBa + kk * kk, kMinusOne}},
+                  X, kk, false));
+      TRY(project_out(ctx, right, k, X, kk));
+      TRY(precond_apply(ctx, X, kk, blkZ(ctx, cur)));
+      TRY(orth_against(ctx, V, cur, blkZ(ctx, cur), kk));  // against V, W, S_1..S_{l-1}
+      TRY(spmm_AB(ctx, blkZ(ctx, cur), kk, blkAZ(ctx, cur), blkBZ(ctx, cur)));
+    }
+    // step 21: P against V, W, S and orth; AP, BP follow by the same transforms
+    if (withP) {
+      const size_t nw = (size_t)ctx->n;
+      const int ncopy = ctx->recompute ? 1 : (ctx->hasB ? 3 : 2);
+      const int ph = prof_begin(ctx, KC_OTHER, 0.0, 32.0 * ctx->n * kk * ncopy, ncopy);
       gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-          ctx->n, kk, ctx->APb, k, ctx->AZ + pslot, sm);
-      if (ctx->hasB)
+          ctx->n, kk, ctx->Pb, k, ctx->Z + pslot, sm);
+      if (!ctx->recompute) {
         gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-            ctx->n, kk, ctx->BPb, k, ctx->BZ + pslot, sm);
+            ctx->n, kk, ctx->APb, k, ctx->AZ + pslot, sm);
+        if (ctx->hasB)
+          gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+              ctx->n, kk, ctx->BPb, k, ctx->BZ + pslot, sm);
+      }
+      prof_end(ctx, ph);
+      CK(cudaGetLastError());
+      if (ctx->recompute) {
+        TRY(orth_against(ctx, V, pslot, blkZ(ctx, pslot), kk));
+        TRY(spmm_AB(ctx, blkZ(ctx, pslot), kk, blkAZ(ctx, pslot), blkBZ(ctx, pslot)));
+      } else {
+        std::vector<Extra> ex{Extra{blkAZ(ctx, pslot), blkAZ(ctx, 0)}};
+        if (ctx->hasB) ex.push_back(Extra{blkBZ(ctx, pslot), blkBZ(ctx, 0)});
+        TRY(orth_against(ctx, V, pslot, blkZ(ctx, pslot), kk, ex));
+      }
     }
-    prof_end(ctx, ph);
+    // steps 23-24: Qhat = orth((A - sigma B) [W S P]) against Q;  U = [Q Qhat]
+    const int ph_ax = prof_begin(ctx, KC_OTHER, 8.0 * ctx->n * sk, 48.0 * ctx->n * sk);
+    gplhr::axpby_kernel<<<grid_for((size_t)ctx->n * sk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+        ctx->n, sk, kOne, ctx->AZ + k, sm, d2(-ctx->sigma), blkBZ(ctx, k).p, sm, ctx->U + k, sm);
+    prof_end(ctx, ph_ax);
     CK(cudaGetLastError());
-    if (ctx->recompute) {
-      TRY(orth_against(ctx, V, pslot, blkZ(ctx, pslot), kk));
-      TRY(spmm_AB(ctx, blkZ(ctx, pslot), kk, blkAZ(ctx, pslot), blkBZ(ctx, pslot)));
-    } else {
-      std::vector<Extra> ex{Extra{blkAZ(ctx, pslot), blkAZ(ctx, 0)}};
-      if (ctx->hasB) ex.push_back(Extra{blkBZ(ctx, pslot), blkBZ(ctx, 0)});
-      TRY(orth_against(ctx, V, pslot, blkZ(ctx, pslot), kk, ex));
-    }
-    sP = kk;
-  }
-  const int s = pslot + sP;
-  const int sk = s - k;
-  // steps 23-24: Qhat = orth((A - sigma B) [W S P]) against Q;  U = [Q Qhat]
-  const int ph_ax = prof_begin(ctx, KC_OTHER, 8.0 * ctx->n * sk, 48.0 * ctx->n * sk);
-  gplhr::axpby_kernel<<<grid_for((size_t)ctx->n * sk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-      ctx->n, sk, kOne, ctx->AZ + k, sm, d2(-ctx->sigma), blkBZ(ctx, k).p, sm, ctx->U + k, sm);
-  prof_end(ctx, ph_ax);
-  CK(cudaGetLastError());
-  TRY(orth_against(ctx, Q, k, blkU(ctx, k), sk, {}, ctx->factored));
-  SqMat RAb, RBb, YLb, YRb;
-  // only the leading k + kk positions of the ordering are used (V and P)
-  const int cv = k + kk;
-  if (ctx->factored) {
-    TRY(factored_pencil_qz(ctx, s, sk, RAb, RBb, YLb, YRb, cv));
-  } else {
+    TRY(orth_against(ctx, Q, k, blkU(ctx, k), sk, {}, ctx->factored));
+    if (ctx->factored) return factored_pencil_issue(ctx, s, sk);
     // step 24: projected pencil (U^* A Z, U^* B Z) by two Gram products
     TRY(gram(ctx, blkU(ctx, 0), s, blkAZ(ctx, 0), s, blkBZ(ctx, 0), s, ctx->dPhiPsi));
     ctx->d2h_bytes += (int64_t)2 * s * s * sizeof(double2);
     CK(cudaMemcpyAsync(ctx->h_phipsi, ctx->dPhiPsi, (size_t)2 * s * s * sizeof(double2), cudaMemcpyDeviceToHost,
                        ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    return GPLHR_OK;
+  }));
+  CK(cudaStreamSynchronize(ctx->stream));
+  SqMat RAb, RBb, YLb, YRb;
+  if (ctx->factored)
+    TRY(factored_pencil_qz(ctx, s, sk, RAb, RBb, YLb, YRb, cv));
+  else
     TRY(host_qz(ctx, s, RAb, RBb, YLb, YRb, cv));
-  }
   // steps 25-28: V = Z Ybar_R(:, 1:k), P = Z Ybar_R(:, k+1:k+kk), Q = U Ybar_L(:, 1:k)
   double2* hy = ctx->h_small + 6 * k * k;
   double2* hl = hy + (size_t)s * cv;
   pack(hy, YRb, 0, s, 0, cv);
   pack(hl, YLb, 0, s, 0, k);
-  TRY(upload(ctx, ctx->dYR, hy, (size_t)s * cv));
-  TRY(upload(ctx, ctx->dYL, hl, (size_t)s * k));
-  TRY(combine(ctx, {In{blkZ(ctx, 0), s, ctx->dYR, kOne}}, blkZ(ctx, 0), cv, false, nullptr, Blk{ctx->Pb, k}, k));
-  if (ctx->recompute) {
-    // AV, BV by fresh sparse products (AP, BP are formed after P's orth next iteration)
-    TRY(spmm_AB(ctx, blkZ(ctx, 0), k, blkAZ(ctx, 0), blkBZ(ctx, 0)));
-  } else {
-    TRY(combine(ctx, {In{blkAZ(ctx, 0), s, ctx->dYR, kOne}}, blkAZ(ctx, 0), cv, false, nullptr,
-                Blk{ctx->APb, k}, k));
-    if (ctx->hasB)
-      TRY(combine(ctx, {In{blkBZ(ctx, 0), s, ctx->dYR, kOne}}, blkBZ(ctx, 0), cv, false, nullptr,
-                  Blk{ctx->BPb, k}, k));
-  }
-  TRY(combine(ctx, {In{blkU(ctx, 0), s, ctx->dYL, kOne}}, blkU(ctx, 0), k, false));
+  TRY(run_segment(ctx, seg_key(2, q, m, kk, s, flags), [&]() -> gplhr_status {
+    TRY(upload(ctx, ctx->dYR, hy, (size_t)s * cv));
+    TRY(upload(ctx, ctx->dYL, hl, (size_t)s * k));
+    TRY(combine(ctx, {In{blkZ(ctx, 0), s, ctx->dYR, kOne}}, blkZ(ctx, 0), cv, false, nullptr, Blk{ctx->Pb, k}, k));
+    if (ctx->recompute) {
+      // AV, BV by fresh sparse products (AP, BP are formed after P's orth next iteration)
+      TRY(spmm_AB(ctx, blkZ(ctx, 0), k, blkAZ(ctx, 0), blkBZ(ctx, 0)));
+    } else {
+      TRY(combine(ctx, {In{blkAZ(ctx, 0), s, ctx->dYR, kOne}}, blkAZ(ctx, 0), cv, false, nullptr,
+                  Blk{ctx->APb, k}, k));
+      if (ctx->hasB)
+        TRY(combine(ctx, {In{blkBZ(ctx, 0), s, ctx->dYR, kOne}}, blkBZ(ctx, 0), cv, false, nullptr,
+                    Blk{ctx->BPb, k}, k));
+    }
+    return combine(ctx, {In{blkU(ctx, 0), s, ctx->dYL, kOne}}, blkU(ctx, 0), k, false);
+  }));
   ctx->hasP = true;
   // steps 29-30
   set_factors(ctx, RAb, RBb);
@@ -1567,6 +1681,7 @@ gplhr_status gplhr_create(const gplhr_csr* A, const gplhr_csr* B, double sigma_r
     if (opts->stall_iters != 0) ctx->stall_iters = opts->stall_iters;
     ctx->factored = opts->pencil == 0;
     ctx->tc = opts->fp64_gemm == 0;
+    ctx->graphs = opts->graphs != 0;
     if (opts->precision != GPLHR_FP64 && opts->precision != GPLHR_MIXED) {
       g_create_error = "opts.precision must be GPLHR_FP64 or GPLHR_MIXED";
       delete ctx;
@@ -1777,6 +1892,8 @@ gplhr_status gplhr_vectors(gplhr_ctx* ctx, double* alpha, double* beta, double* 
 
 void gplhr_destroy(gplhr_ctx* ctx) {
   if (!ctx) return;
+  for (auto& g : ctx->seg_graphs) cudaGraphExecDestroy(g.second.exec);
+  ctx->seg_graphs.clear();
   free_all(ctx);
   delete ctx;
 }
