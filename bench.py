@@ -254,6 +254,7 @@ def main():
                         "ms_per_step": per_class[c]["ms"] / K,
                         "launches_per_step": per_class[c]["launches"] / K} for c in KCLASSES},
         "hbm_spmm_gram": hbm,
+        "spmm_autotune": run["spmm_autotune"],
         "clocks": clocks,
     }
     if not args.no_mixed:
@@ -300,7 +301,11 @@ def timed_iterations(G, pr, K, W, stream, precision, barrier, local, world, dev)
     import torch.distributed as dist
     extra = {"switch_tol": 1e-300, "stall_iters": -1} if precision == "mixed" else {}
     solver = G.GPLHR(pr.A, pr.B, pr.sigma, pr.k, pr.m, pr.precond, pr.block_size, tol=pr.tol,
-                     maxit=10 ** 6, stream=stream.cuda_stream, precision=precision, **extra)
+                     maxit=10 ** 6, stream=stream.cuda_stream, precision=precision, autotune=True, **extra)
+    tuned = {}
+    for w in sorted({pr.k, max(1, pr.k // 2), 1}):
+        t, g, us, ud = G.gplhr_spmm_shape(solver.ctx, w, precision == "mixed")
+        tuned[str(w)] = {"threads": t, "ctas_per_sm": g, "us": us, "us_default_256x8": ud}
     solver.start(pr.start_block())
     solver.iterate(W)
     torch.cuda.synchronize()
@@ -334,7 +339,7 @@ def timed_iterations(G, pr, K, W, stream, precision, barrier, local, world, dev)
         per_class[c] = {"ms": cms, "launches": nl, "gflop": fl / 1e9, "gbyte": by / 1e9}
     G.gplhr_profile(solver.ctx, False)
     solver.close()
-    return {"ms": ms, "per_class": per_class, "clocks": clocks}
+    return {"ms": ms, "per_class": per_class, "clocks": clocks, "spmm_autotune": tuned}
 
 
 def e2e(pr, K, stream, G):
@@ -370,7 +375,7 @@ def batched_throughput(G, K):
 
     def run(graphs):
         solvers = [G.GPLHR(p.A, p.B, p.sigma, p.k, p.m, p.precond, p.block_size, tol=p.tol, maxit=10 ** 6,
-                           graphs=graphs) for p in ps]
+                           graphs=graphs, autotune=graphs) for p in ps]
         for s, p in zip(solvers, ps):
             s.start(p.start_block())
         ctxs = [s.ctx for s in solvers]
@@ -397,7 +402,8 @@ def batched_throughput(G, K):
             "speedup_vs_sequential": gs / gb,
             "without_graphs": {"pencil_iterations_per_s": units / tb,
                                "sequential_pencil_iterations_per_s": units / ts, "status": st},
-            "graphs": "each iteration's three device segments replayed from CUDA graphs",
+            "graphs": "each iteration's three device segments replayed from CUDA graphs; SpMM launch shapes "
+                      "autotuned per pencil",
             "threads": os.cpu_count(), "iterations": K, "status": gst}
 
 

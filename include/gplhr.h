@@ -131,6 +131,11 @@ typedef struct {
                           launch sequence (locked pairs, m, P present, precision phase).
                           Not used while gplhr_profile timing is on or with inner GMRES
                           steps (their least squares runs on the host inside T).          */
+  int32_t autotune;    /* [0]    1 = time the SpMM launch shapes (threads per CTA 64/128/256,
+                          grid cap 2..64 CTAs per SM) on this pencil's A and B at create,
+                          for each lane-group width the block widths 1..k select (and in
+                          the FP32 bulk phase), and use the fastest; gplhr_spmm_shape
+                          reports the choice.  Results do not depend on it.                */
 } gplhr_opts;
 
 /* Per-solve report.  resid[j] (j < k) is the backward error of pair j,
@@ -281,6 +286,15 @@ gplhr_status gplhr_gram(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t wx, 
 enum { GPLHR_COMBINE_AUTO = 0, GPLHR_COMBINE_DFMA = 1 };
 gplhr_status gplhr_combine(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t w, const void* C,
                            int32_t c, void* Y, int32_t ldy, int32_t beta, int32_t arith);
+
+/* Launch shape the context uses for sparse products of a w-column block (fp32 = 1: the
+ * FP32 bulk phase, w <= 64; else w <= 32): threads per CTA, grid cap in CTAs per SM and,
+ * when opts.autotune measured them, the time of one A (and B) product in microseconds
+ * with that shape and with the default shape (256 threads, 8 CTAs per SM); 0 otherwise.
+ * Any output pointer may be NULL.  EINVAL for w out of range.  The paper has no
+ * counterpart: a launch-configuration query of this implementation. */
+gplhr_status gplhr_spmm_shape(gplhr_ctx* ctx, int32_t w, int32_t fp32, int32_t* threads, int32_t* grid_per_sm,
+                              double* us, double* us_default);
 
 /* orth(X) in place (Alg. 1 footnote): X <- X R^{-1} with X = Q R the thin QR whose R
  * has a real positive diagonal, by Cholesky QR applied twice (a shifted Cholesky

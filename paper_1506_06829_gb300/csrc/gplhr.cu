@@ -139,6 +139,17 @@ struct gplhr_ctx {
   };
   bool graphs = false;
   std::map<uint64_t, SegGraph> seg_graphs;
+  // SpMM launch shape per (group width G, columns per lane V): threads per CTA and the
+  // grid cap in multiples of the SM count; the defaults, or the fastest candidate
+  // measured at create time (opts.autotune)
+  struct SpmmShape {
+    int threads = 256, gridmul = 8;
+    double us = 0.0;          // measured time of the chosen shape (autotune), microseconds
+    double us_default = 0.0;  // measured time of the default shape 256 / 8
+  };
+  bool autotune = false;
+  std::map<int, SpmmShape> spmm_shape;  // key 4 G + V
+  const SpmmShape* spmm_force = nullptr;  // candidate being measured
   std::string err;
 };
 
@@ -210,6 +221,19 @@ gplhr_ctx::Counters snap_counters(const gplhr_ctx* ctx) {
   c.h2d = ctx->h2d_bytes;
   c.d2h = ctx->d2h_bytes;
   return c;
+}
+
+void restore_counters(gplhr_ctx* ctx, const gplhr_ctx::Counters& c) {
+  for (int i = 0; i < 8; ++i) {
+    ctx->k_flops[i] = c.k_flops[i];
+    ctx->k_bytes[i] = c.k_bytes[i];
+    ctx->k_launch[i] = c.k_launch[i];
+  }
+  ctx->n_launch = c.n_launch;
+  ctx->n_spmm = c.n_spmm;
+  ctx->n_prec = c.n_prec;
+  ctx->h2d_bytes = c.h2d;
+  ctx->d2h_bytes = c.d2h;
 }
 
 // Device work of one segment of an iteration (a run of launches and copies between two
@@ -293,9 +317,16 @@ void launch_spmm_g(gplhr_ctx* ctx, gplhr::CsrDev<VTA> a, gplhr::CsrDev<VTB> b, i
                    const gplhr::cplx<T>* X, int ldx, int w, double2* Y, int ldy, double2* Y2, int ldy2) {
   int G = 4;
   while (G * V < w) G <<= 1;
-  const int rows_per_cta = (gplhr::SPMM_THREADS / 32) * (32 / G);
-  const int grid = grid_for((size_t)ctx->n, rows_per_cta, 8 * ctx->num_sms);
-  const int nt = gplhr::SPMM_THREADS;
+  gplhr_ctx::SpmmShape sh;
+  if (ctx->spmm_force) {
+    sh = *ctx->spmm_force;
+  } else {
+    const auto it = ctx->spmm_shape.find(4 * G + V);
+    if (it != ctx->spmm_shape.end()) sh = it->second;
+  }
+  const int rows_per_cta = (sh.threads / 32) * (32 / G);
+  const int grid = grid_for((size_t)ctx->n, rows_per_cta, sh.gridmul * ctx->num_sms);
+  const int nt = sh.threads;
   switch (G) {
     case 4:
       gplhr::spmm_kernel<VTA, VTB, T, 4, V><<<grid, nt, 0, ctx->stream>>>(ctx->n, a, b, hasB, X, ldx, w, Y, ldy, Y2, ldy2);
@@ -385,6 +416,65 @@ gplhr_status launch_spmm_f64(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, 
   prof_end(ctx, ph);
   CK(cudaGetLastError());
   return GPLHR_OK;
+}
+
+// SpMM autotuner: for every group width G that the iteration's block widths 1..k
+// select (in FP64, V = 1, and in the FP32 bulk phase, V = 2), time each launch shape
+// (64, 128 or 256 threads per CTA; grid capped at 2, 4, 8, 16 or 64 CTAs per SM) on the
+// context's own A (and B), 3 runs after a warm-up, CUDA events on its stream, and keep
+// the fastest.  Every shape computes each row in the same lane group, so results do not
+// depend on the choice.  The library's counters are left as they were.
+gplhr_status autotune_spmm(gplhr_ctx* ctx) {
+  const gplhr_ctx::Counters c0 = snap_counters(ctx);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  gplhr_status st = GPLHR_OK;
+  const int threads[3] = {64, 128, 256}, gridmul[5] = {2, 4, 8, 16, 64};
+  CK(cudaMemsetAsync(ctx->Z, 0, (size_t)ctx->n * ctx->s_max * sizeof(double2), ctx->stream));
+  for (int V = 1; V <= (ctx->mixed ? 2 : 1) && st == GPLHR_OK; ++V) {
+    for (int G = 4; G <= 32 && st == GPLHR_OK; G <<= 1) {
+      const int wlo = G == 4 ? 1 : (G / 2) * V + 1;
+      const int w = std::min(G * V, ctx->k);
+      if (w < wlo) continue;
+      gplhr_ctx::SpmmShape best;
+      best.us = 1e30;
+      for (int ti = 0; ti < 3 && st == GPLHR_OK; ++ti)
+        for (int gi = 0; gi < 5 && st == GPLHR_OK; ++gi) {
+          gplhr_ctx::SpmmShape cand;
+          cand.threads = threads[ti];
+          cand.gridmul = gridmul[gi];
+          ctx->spmm_force = &cand;
+          float ms = 0.0f;
+          for (int rep = 0; rep < 4 && st == GPLHR_OK; ++rep) {
+            if (rep == 1) cudaEventRecord(e0, ctx->stream);
+            st = launch_spmm_one(ctx, ctx->A, ctx->hasB ? &ctx->B : nullptr, Blk{ctx->Z, ctx->s_max}, w,
+                                 Blk{ctx->AZ, ctx->s_max}, Blk{ctx->hasB ? ctx->BZ : nullptr, ctx->s_max}, V == 2);
+          }
+          ctx->spmm_force = nullptr;
+          if (st != GPLHR_OK) break;
+          cudaEventRecord(e1, ctx->stream);
+          if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            ctx->err = "SpMM autotuning: event timing failed";
+            st = GPLHR_ECUDA;
+            break;
+          }
+          const double us = 1e3 * ms / 3.0;
+          if (cand.threads == 256 && cand.gridmul == 8) best.us_default = us;
+          if (us < best.us) {
+            const double ud = best.us_default;
+            best = cand;
+            best.us = us;
+            best.us_default = ud;
+          }
+        }
+      if (st == GPLHR_OK) ctx->spmm_shape[4 * G + V] = best;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  restore_counters(ctx, c0);
+  return st;
 }
 
 // AX = A X and (B != I) BX = B X
@@ -1682,6 +1772,7 @@ gplhr_status gplhr_create(const gplhr_csr* A, const gplhr_csr* B, double sigma_r
     ctx->factored = opts->pencil == 0;
     ctx->tc = opts->fp64_gemm == 0;
     ctx->graphs = opts->graphs != 0;
+    ctx->autotune = opts->autotune != 0;
     if (opts->precision != GPLHR_FP64 && opts->precision != GPLHR_MIXED) {
       g_create_error = "opts.precision must be GPLHR_FP64 or GPLHR_MIXED";
       delete ctx;
@@ -1734,6 +1825,7 @@ gplhr_status gplhr_create(const gplhr_csr* A, const gplhr_csr* B, double sigma_r
     const double comb = 8.0 * ctx->s_max * (ctx->hasB ? 2.0 : 1.0);
     ctx->recompute = products == 2 || (products == 0 && spmm < comb);
   }
+  if (ctx->autotune && (st = autotune_spmm(ctx)) != GPLHR_OK) return fail(st);
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
     ctx->err = "setup failed on the device";
     return fail(GPLHR_ECUDA);
@@ -1950,6 +2042,22 @@ gplhr_status gplhr_combine(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t w
     ctx->err = "tensor-core product: wait for completion gave up";
     return GPLHR_ETIMEOUT;
   }
+  return GPLHR_OK;
+}
+
+gplhr_status gplhr_spmm_shape(gplhr_ctx* ctx, int32_t w, int32_t fp32, int32_t* threads, int32_t* grid_per_sm,
+                              double* us, double* us_default) {
+  if (!ctx || w < 1 || w > 32 * (fp32 ? 2 : 1)) return GPLHR_EINVAL;
+  const int V = fp32 ? 2 : 1;
+  int G = 4;
+  while (G * V < w) G <<= 1;
+  gplhr_ctx::SpmmShape sh;
+  const auto it = ctx->spmm_shape.find(4 * G + V);
+  if (it != ctx->spmm_shape.end()) sh = it->second;
+  if (threads) *threads = sh.threads;
+  if (grid_per_sm) *grid_per_sm = sh.gridmul;
+  if (us) *us = sh.us;
+  if (us_default) *us_default = sh.us_default;
   return GPLHR_OK;
 }
 
