@@ -26,6 +26,16 @@ CUDA path):
   i.e. ||A x - lambda B x|| / ((||A||_1 + |lambda| ||B||_1) ||x||) <= tol.
   Locking is in order: q = number of leading pairs that pass (never decreasing).
   The iteration stops when all k pairs pass.
+* Search directions P (Sec. 3.5; the paper compares the options in Table 2):
+  "thick" is P = Z Ybar_R(:, k+1:2k) (Eq. P1, the default); "lobpcg" is
+  P = V^(i) - V^(i-1) C (Eq. P_lobpcg) with C = I, since the paper leaves C open and
+  every invertible C gives the same trial subspace once P is orthogonalised against
+  V^(i) (span{V, V - V_old C} = span{V, V_old}); "previous" is P = V^(i-1), the other
+  option the paper names with the same subspace; "none" drops P (Eq. trial_partial).
+  Under soft locking a lobpcg / previous P keeps the columns of the active pairs
+  q..k-1, a thick P its leading k - q columns.
+* The right projector before T (Table 3) can be omitted: T_L = (I - VV^*) T instead of
+  (I - VV^*) T (I - QQ^*) (or (I - VV^*) T (I - VV^*) when B = I).
 """
 from __future__ import annotations
 
@@ -100,6 +110,9 @@ class State:
     m: int
     m0: int
     it: int = 0
+    p_mode: str = "thick"         # "thick" | "lobpcg" | "previous" | "none"
+    right_proj: bool = True       # projector before T (Table 3)
+    lobpcg_C: np.ndarray | None = None   # C of Eq. P_lobpcg (None: identity)
 
     @property
     def k(self) -> int:
@@ -112,8 +125,11 @@ class State:
             RA=self.RA.copy(), RB=self.RB.copy(), MA=self.MA.copy(), MB=self.MB.copy())
 
 
-def init_state(pen: Pencil, V0: np.ndarray, m: int) -> State:
+def init_state(pen: Pencil, V0: np.ndarray, m: int, p_mode: str = "thick", right_proj: bool = True,
+               lobpcg_C: np.ndarray | None = None) -> State:
     """Steps 1-4 of Algorithm 2."""
+    if p_mode not in ("thick", "lobpcg", "previous", "none"):
+        raise ValueError(f"unknown p_mode {p_mode!r}")
     V = orth(np.asarray(V0, dtype=np.complex128))
     AV = pen.Amul(V)
     BV = pen.Bmul(V)
@@ -122,7 +138,8 @@ def init_state(pen: Pencil, V0: np.ndarray, m: int) -> State:
     V = V @ YR
     Q = Q @ YL
     MA, MB, _ = m_factors(RA, RB)
-    return State(V, Q, None, RA, RB, MA, MB, q=0, m=m, m0=m)
+    return State(V, Q, None, RA, RB, MA, MB, q=0, m=m, m0=m, p_mode=p_mode, right_proj=right_proj,
+                 lobpcg_C=lobpcg_C)
 
 
 def iterate(pen: Pencil, st: State) -> State:
@@ -140,8 +157,8 @@ def iterate(pen: Pencil, st: State) -> State:
 
     proj_right = proj_Q if generalized else proj_V
 
-    def T_L(X):  # projected preconditioner, Eqs. prec_gen / prec
-        return proj_V(pen.Tmul(proj_right(X)))
+    def T_L(X):  # projected preconditioner, Eqs. prec_gen / prec (right projector optional)
+        return proj_V(pen.Tmul(proj_right(X) if st.right_proj else X))
 
     AV = pen.Amul(V)
     BV = pen.Bmul(V)
@@ -168,8 +185,8 @@ def iterate(pen: Pencil, st: State) -> State:
         S_prev = Sl
     Sc = np.hstack(S) if S else np.zeros((pen.n, 0), dtype=np.complex128)
     blocks = [W] + S
-    if P is not None:
-        P = P[:, :k - q]                                   # soft locking: k - q columns
+    if P is not None:                                      # soft locking: k - q columns
+        P = P[:, q:] if st.p_mode in ("lobpcg", "previous") else P[:, :k - q]
     if P is not None and P.shape[1] > 0:                   # step 21
         P = P - V @ (V.conj().T @ P)
         P = P - W @ (W.conj().T @ P)
@@ -192,9 +209,17 @@ def iterate(pen: Pencil, st: State) -> State:
     YL = YLb[:, :k]
     RA = RAb[:k, :k]
     RB = RBb[:k, :k]
+    V_old = V
     V = Z @ YR                                             # steps 26-27
     Q = U @ YL
-    P = Z @ YRb[:, k:k + kk]                               # step 28 (thick restart)
+    if st.p_mode == "thick":
+        P = Z @ YRb[:, k:k + kk]                           # step 28 (thick restart, Eq. P1)
+    elif st.p_mode == "lobpcg":                            # Eq. P_lobpcg, all k columns
+        P = V - (V_old if st.lobpcg_C is None else V_old @ st.lobpcg_C)
+    elif st.p_mode == "previous":
+        P = V_old.copy()
+    else:
+        P = None
     MA, MB, _ = m_factors(RA, RB)                          # steps 29-30
     return dataclasses.replace(st, V=V, Q=Q, P=P, RA=RA, RB=RB, MA=MA, MB=MB,
                                it=st.it + 1)
@@ -263,13 +288,16 @@ class Result:
 
 def solve(A, B, sigma, V0, m: int = 1, tol: float = 1e-8, maxit: int = 500,
           precond: str = "none", block_size: int = 1, T: Preconditioner | None = None,
-          lock: bool = True, callback=None, inner_steps: int = 0) -> Result:
+          lock: bool = True, callback=None, inner_steps: int = 0, p_mode: str = "thick",
+          right_proj: bool = True, lobpcg_C: np.ndarray | None = None) -> Result:
     """Run Algorithm 2 until all k pairs meet ``tol`` or ``maxit`` iterations.
-    inner_steps > 0: T is that many block GMRES steps preconditioned by ``precond``."""
+    inner_steps > 0: T is that many block GMRES steps preconditioned by ``precond``.
+    p_mode, right_proj, lobpcg_C: the variants of Sec. 3.5 and Tables 2-3 (module
+    docstring)."""
     if T is None:
         T = build_precond(A, B, sigma, precond, block_size, inner_steps)
     pen = Pencil(A, B, sigma, T)
-    st = init_state(pen, V0, m)
+    st = init_state(pen, V0, m, p_mode, right_proj, lobpcg_C)
     k = st.k
     hist = []
     res = residuals(pen, st)
