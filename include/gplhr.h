@@ -136,6 +136,14 @@ typedef struct {
                           for each lane-group width the block widths 1..k select (and in
                           the FP32 bulk phase), and use the fastest; gplhr_spmm_shape
                           reports the choice.  Results do not depend on it.                */
+  int32_t p_mode;      /* [0]    search directions P (Sec. 3.5, the paper's Table 2): 0 = thick
+                          restart P = Z Ybar_R(:, k+1:2k) (Eq. P1); 1 = LOBPCG style
+                          P = V - V_prev (Eq. P_lobpcg with C = I: every invertible C gives
+                          the same trial subspace); 2 = no P, (m + 2) k trial columns.
+                          EINVAL otherwise.                                                */
+  int32_t no_right_proj; /* [0]  1 = omit the projector applied before T (T_L = (I - VV^*) T
+                          instead of (I - VV^*) T (I - QQ^*), or (I - VV^*) T (I - VV^*) when
+                          B = I): the variant the paper compares in its Table 3.            */
 } gplhr_opts;
 
 /* Per-solve report.  resid[j] (j < k) is the backward error of pair j,

@@ -90,6 +90,9 @@ struct gplhr_ctx {
   int* h_status = nullptr;
   size_t trk = 0;              // stride of the passes in dTrackC (>= s_max^2)
   bool factored = true;        // projected pencil from U's factors (one Gram)
+  int p_mode = 0;              // search directions P: 0 thick restart (Eq. P1), 1 LOBPCG
+                               // style V - V_old (Eq. P_lobpcg, C = I), 2 none
+  bool right_proj = true;      // projector before T (Table 3)
   // inner block GMRES (T = gm_steps steps on (A - sigma B) W = R, right-preconditioned
   // by the basic preconditioner prec)
   int gm_steps = 0;
@@ -1202,13 +1205,17 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
   const int sm = ctx->s_max;
   const Blk V = blkZ(ctx, 0), Q = blkU(ctx, 0);
   const Blk right = ctx->hasB ? Q : V;  // projector before T: (I - QQ^*), or (I - VV^*) if B = I
-  const bool withP = ctx->hasP && kk > 0;
+  const bool withP = ctx->hasP && kk > 0 && ctx->p_mode != 2;
+  const bool lob = ctx->p_mode == 1;
+  const int poff = lob ? q : 0;  // a LOBPCG-style P keeps its columns at V's positions
   const int pslot = k + (m + 1) * kk;
   const int sP = withP ? kk : 0;
   const int s = pslot + sP;
   const int sk = s - k;
-  const int cv = k + kk;  // only the leading k + kk positions of the ordering are used (V and P)
-  const int flags = (ctx->bulk32 ? 1 : 0) | (ctx->recompute ? 2 : 0) | (ctx->factored ? 4 : 0) | (withP ? 8 : 0);
+  // only the leading k + kk positions of the ordering are used (V and a thick P)
+  const int cv = ctx->p_mode == 0 ? k + kk : k;
+  const int flags = (ctx->bulk32 ? 1 : 0) | (ctx->recompute ? 2 : 0) | (ctx->factored ? 4 : 0) | (withP ? 8 : 0) |
+                    (ctx->p_mode << 4) | (ctx->right_proj ? 0 : 64);
   // host staging of segment A: M_B, M_A of the active pairs for the S-recurrence
   if (m > 0) {
     double2* hm = ctx->h_small + 4 * k * k;
@@ -1222,7 +1229,7 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
   TRY(run_segment(ctx, seg_key(1, q, m, kk, s, flags), [&]() -> gplhr_status {
     // steps 7-8 / 10: W = (I - VV^*) T (I - QQ^*) R, active columns q..k-1
     Blk Ra{ctx->Rw + q, k};
-    TRY(project_out(ctx, right, k, Ra, kk));
+    if (ctx->right_proj) TRY(project_out(ctx, right, k, Ra, kk));
     TRY(precond_apply(ctx, Ra, kk, blkZ(ctx, k)));
     TRY(orth_against(ctx, V, k, blkZ(ctx, k), kk));  // step 12 (with (I - VV^*))
     TRY(spmm_AB(ctx, blkZ(ctx, k), kk, blkAZ(ctx, k), blkBZ(ctx, k)));
@@ -1234,7 +1241,7 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
       TRY(combine(ctx, {In{blkAZ(ctx, prev), kk, ctx->dMBa, kOne},
                         In{blkBZ(ctx, prev), kk, ctx->dMBa + kk * kk, kMinusOne}},
                   X, kk, false));
-      TRY(project_out(ctx, right, k, X, kk));
+      if (ctx->right_proj) TRY(project_out(ctx, right, k, X, kk));
       TRY(precond_apply(ctx, X, kk, blkZ(ctx, cur)));
       TRY(orth_against(ctx, V, cur, blkZ(ctx, cur), kk));  // against V, W, S_1..S_{l-1}
       TRY(spmm_AB(ctx, blkZ(ctx, cur), kk, blkAZ(ctx, cur), blkBZ(ctx, cur)));
@@ -1245,13 +1252,13 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
       const int ncopy = ctx->recompute ? 1 : (ctx->hasB ? 3 : 2);
       const int ph = prof_begin(ctx, KC_OTHER, 0.0, 32.0 * ctx->n * kk * ncopy, ncopy);
       gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-          ctx->n, kk, ctx->Pb, k, ctx->Z + pslot, sm);
+          ctx->n, kk, ctx->Pb + poff, k, ctx->Z + pslot, sm);
       if (!ctx->recompute) {
         gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-            ctx->n, kk, ctx->APb, k, ctx->AZ + pslot, sm);
+            ctx->n, kk, ctx->APb + poff, k, ctx->AZ + pslot, sm);
         if (ctx->hasB)
           gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-              ctx->n, kk, ctx->BPb, k, ctx->BZ + pslot, sm);
+              ctx->n, kk, ctx->BPb + poff, k, ctx->BZ + pslot, sm);
       }
       prof_end(ctx, ph);
       CK(cudaGetLastError());
@@ -1293,6 +1300,17 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
   TRY(run_segment(ctx, seg_key(2, q, m, kk, s, flags), [&]() -> gplhr_status {
     TRY(upload(ctx, ctx->dYR, hy, (size_t)s * cv));
     TRY(upload(ctx, ctx->dYL, hl, (size_t)s * k));
+    const int nb = (int)grid_for((size_t)ctx->n * k, 256, 8 * ctx->num_sms);
+    if (lob) {  // V_old (and A V_old, B V_old) into the P buffers before the update
+      const int ph = prof_begin(ctx, KC_OTHER, 0.0, 32.0 * ctx->n * k, 1);
+      gplhr::copy_block_kernel<<<nb, 256, 0, ctx->stream>>>(ctx->n, k, ctx->Z, sm, ctx->Pb, k);
+      if (!ctx->recompute) {
+        gplhr::copy_block_kernel<<<nb, 256, 0, ctx->stream>>>(ctx->n, k, ctx->AZ, sm, ctx->APb, k);
+        if (ctx->hasB) gplhr::copy_block_kernel<<<nb, 256, 0, ctx->stream>>>(ctx->n, k, ctx->BZ, sm, ctx->BPb, k);
+      }
+      prof_end(ctx, ph);
+      CK(cudaGetLastError());
+    }
     TRY(combine(ctx, {In{blkZ(ctx, 0), s, ctx->dYR, kOne}}, blkZ(ctx, 0), cv, false, nullptr, Blk{ctx->Pb, k}, k));
     if (ctx->recompute) {
       // AV, BV by fresh sparse products (AP, BP are formed after P's orth next iteration)
@@ -1304,9 +1322,23 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
         TRY(combine(ctx, {In{blkBZ(ctx, 0), s, ctx->dYR, kOne}}, blkBZ(ctx, 0), cv, false, nullptr,
                     Blk{ctx->BPb, k}, k));
     }
-    return combine(ctx, {In{blkU(ctx, 0), s, ctx->dYL, kOne}}, blkU(ctx, 0), k, false);
+    TRY(combine(ctx, {In{blkU(ctx, 0), s, ctx->dYL, kOne}}, blkU(ctx, 0), k, false));
+    if (lob) {  // Eq. P_lobpcg with C = I: P = V - V_old (A P, B P likewise)
+      const int ph = prof_begin(ctx, KC_OTHER, 8.0 * ctx->n * k, 48.0 * ctx->n * k, 1);
+      gplhr::axpby_kernel<<<nb, 256, 0, ctx->stream>>>(ctx->n, k, kOne, ctx->Z, sm, kMinusOne, ctx->Pb, k, ctx->Pb, k);
+      if (!ctx->recompute) {
+        gplhr::axpby_kernel<<<nb, 256, 0, ctx->stream>>>(ctx->n, k, kOne, ctx->AZ, sm, kMinusOne, ctx->APb, k,
+                                                         ctx->APb, k);
+        if (ctx->hasB)
+          gplhr::axpby_kernel<<<nb, 256, 0, ctx->stream>>>(ctx->n, k, kOne, ctx->BZ, sm, kMinusOne, ctx->BPb, k,
+                                                           ctx->BPb, k);
+      }
+      prof_end(ctx, ph);
+      CK(cudaGetLastError());
+    }
+    return GPLHR_OK;
   }));
-  ctx->hasP = true;
+  ctx->hasP = ctx->p_mode != 2;
   // steps 29-30
   set_factors(ctx, RAb, RBb);
   ctx->it += 1;
@@ -1773,6 +1805,13 @@ gplhr_status gplhr_create(const gplhr_csr* A, const gplhr_csr* B, double sigma_r
     ctx->tc = opts->fp64_gemm == 0;
     ctx->graphs = opts->graphs != 0;
     ctx->autotune = opts->autotune != 0;
+    ctx->right_proj = opts->no_right_proj == 0;
+    if (opts->p_mode < 0 || opts->p_mode > 2) {
+      g_create_error = "opts.p_mode must be 0 (thick), 1 (LOBPCG style) or 2 (none)";
+      delete ctx;
+      return GPLHR_EINVAL;
+    }
+    ctx->p_mode = opts->p_mode;
     if (opts->precision != GPLHR_FP64 && opts->precision != GPLHR_MIXED) {
       g_create_error = "opts.precision must be GPLHR_FP64 or GPLHR_MIXED";
       delete ctx;

@@ -30,6 +30,7 @@ EXPORTED = ["gplhr_create", "gplhr_solve", "gplhr_start", "gplhr_iterate", "gplh
             "gplhr_gram", "gplhr_combine", "gplhr_orth", "gplhr_ordqz", "gplhr_mfactors", "gplhr_profile",
             "gplhr_profile_read", "gplhr_gram_noalloc", "gplhr_grad", "gplhr_solve_batched",
             "gplhr_iterate_batched", "gplhr_spmm_shape"]
+P_MODES = {"thick": 0, "lobpcg": 1, "none": 2}
 KCLASS = {"spmm": 0, "gram": 1, "combine": 2, "precond": 3, "chol": 4, "other": 5}
 
 
@@ -48,7 +49,8 @@ class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("precision", C.c_int32),
                 ("no_lock", C.c_int32), ("products", C.c_int32), ("stream", C.c_void_p),
                 ("switch_tol", C.c_double), ("stall_iters", C.c_int32), ("pencil", C.c_int32),
-                ("fp64_gemm", C.c_int32), ("graphs", C.c_int32), ("autotune", C.c_int32)]
+                ("fp64_gemm", C.c_int32), ("graphs", C.c_int32), ("autotune", C.c_int32),
+                ("p_mode", C.c_int32), ("no_right_proj", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -151,7 +153,8 @@ def gplhr_create(A, B, sigma: complex, k: int, m: int, precond: str = "none",
                  lock: bool = True, stream: int = 0, products: str = "auto",
                  precision: str = "fp64", switch_tol: float = 1e-5, stall_iters: int = 5,
                  pencil: str = "factored", inner_steps: int = 0, fp64_gemm: str = "tensor",
-                 graphs: bool = False, autotune: bool = False):
+                 graphs: bool = False, autotune: bool = False, p_mode: str = "thick",
+                 right_proj: bool = True):
     """Returns an opaque context handle (int).  A, B: SciPy CSR (B None = identity).
     inner_steps > 0: T = that many block GMRES steps on (A - sigma B) W = R,
     right-preconditioned by `precond`."""
@@ -163,7 +166,7 @@ def gplhr_create(A, B, sigma: complex, k: int, m: int, precond: str = "none",
     opts = Opts(tol, maxit, {"fp64": 0, "mixed": 1}[precision], 0 if lock else 1,
                 PRODUCTS[products], stream or None, switch_tol, stall_iters,
                 {"factored": 0, "gram": 1}[pencil], {"tensor": 0, "dfma": 1}[fp64_gemm],
-                1 if graphs else 0, 1 if autotune else 0)
+                1 if graphs else 0, 1 if autotune else 0, P_MODES[p_mode], 0 if right_proj else 1)
     out = C.c_void_p()
     st = L.gplhr_create(C.byref(hA.desc), C.byref(hB.desc) if hB else None, sigma.real,
                         sigma.imag, k, m, C.byref(pc), C.byref(opts), C.byref(out))
@@ -372,11 +375,11 @@ class GPLHR:
     def __init__(self, A, B, sigma, k, m, precond="none", block_size=1, T=None, tol=1e-8,
                  maxit=500, lock=True, stream=0, products="auto", precision="fp64",
                  switch_tol=1e-5, stall_iters=5, pencil="factored", inner_steps=0,
-                 fp64_gemm="tensor", graphs=False, autotune=False):
+                 fp64_gemm="tensor", graphs=False, autotune=False, p_mode="thick", right_proj=True):
         self.n, self.k = A.shape[0], k
         self.ctx = gplhr_create(A, B, complex(sigma), k, m, precond, block_size, T, tol, maxit,
                                 lock, stream, products, precision, switch_tol, stall_iters, pencil,
-                                inner_steps, fp64_gemm, graphs, autotune)
+                                inner_steps, fp64_gemm, graphs, autotune, p_mode, right_proj)
 
     def solve(self, V0=None, seed=0, allow_notconv=False):
         return gplhr_solve(self.ctx, V0, seed, allow_notconv)

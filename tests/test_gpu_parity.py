@@ -554,3 +554,54 @@ def test_combine_in_place_and_nonfinite():
             assert bad[123] and bad.sum() == 1, (arith, np.flatnonzero(bad)[:5])
     finally:
         G.gplhr_destroy(ctx)
+
+
+# ------------------------------------- search directions and projector (Tables 2-3) --
+
+@pytest.mark.parametrize("p_mode,right_proj,products", [("lobpcg", True, "combine"), ("lobpcg", True, "spmm"),
+                                                        ("none", True, "combine"), ("thick", False, "combine"),
+                                                        ("lobpcg", False, "spmm")])
+def test_variant_iterates_follow_oracle(p_mode, right_proj, products):
+    """The P-block variants (Eq. P_lobpcg with C = I, no P) and the variant without the
+    projector before T, iterate by iterate against the oracle on the generalized
+    block-Jacobi pencil: Ritz values and nested Schur subspaces."""
+    N = 8
+    A, B = P.convdiff3d(N, (0.4, 0.2, 0.1)), P.mass3d(N)
+    lmax = 21295.965461059128           # dense eigvals of this 8^3 pencil
+    sigma = complex(0.3 * lmax, 0.05 * lmax)
+    n, k, m = A.shape[0], 8, 1
+    V0 = P.start_block(n, k, 1002)
+    T = oracle_precond(A, B, sigma, "block_jacobi", 8)
+    pen = OG.Pencil(A, B, sigma, T)
+    st = OG.init_state(pen, V0, m, p_mode=p_mode, right_proj=right_proj)
+    with G.GPLHR(A, B, sigma, k, m, "block_jacobi", 8, tol=1e-14, maxit=10, lock=False,
+                 products=products, p_mode=p_mode, right_proj=right_proj) as s:
+        s.start(V0)
+        for it in range(3):
+            st = OG.iterate(pen, st)
+            s.iterate(1)
+            vec = s.vectors()
+            lo = np.diag(st.RA) / np.diag(st.RB)
+            assert np.allclose(vec["lam"], lo, rtol=1e-9, atol=0), (it, vec["lam"], lo)
+            for j in range(1, k + 1):
+                assert _angle(vec["V"][:, :j], st.V[:, :j]) <= 1e-7, (it, j)
+
+
+@pytest.mark.parametrize("p_mode", ["lobpcg", "none"])
+def test_variant_solve_with_locking(p_mode):
+    """Whole solves with soft locking (P columns of the active pairs) against the oracle
+    and dense LAPACK, complex-scaled Schroedinger 24^2."""
+    pr = P.config3(24)
+    o = OG.solve(pr.A, None, pr.sigma, pr.start_block(), m=pr.m, tol=pr.tol, maxit=400,
+                 precond=pr.precond, block_size=pr.block_size, p_mode=p_mode)
+    assert o.converged
+    with G.GPLHR(pr.A, None, pr.sigma, pr.k, pr.m, pr.precond, pr.block_size, tol=pr.tol,
+                 maxit=400, p_mode=p_mode) as s:
+        info = s.solve(pr.start_block())
+        vec = s.vectors()
+    assert info.iters <= 2 * o.iters + 5
+    _compare_solutions(o, vec, pr.k, pr.tol)
+    ev = sla.eigvals(pr.A.toarray())
+    want = ev[np.argsort(np.abs(ev - pr.sigma))[:pr.k]]
+    for mu in want:
+        assert np.min(np.abs(vec["lam"] - mu)) <= 1e-8 * abs(mu)
