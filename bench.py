@@ -273,6 +273,7 @@ def main():
         line["e2e"] = e2e(pr, K, stream, G)
     if rank == 0 and not args.no_batched:
         line["batched"] = batched_throughput(G, K)
+        line["small"] = small_pencil_iterations(G, K)
     if rank == 0 and not args.no_solve:
         line["solve"] = time_to_pairs(G, stream, "fp64")
         if not args.no_mixed:
@@ -362,6 +363,30 @@ def e2e(pr, K, stream, G):
             "h2d_bytes_per_step": (csr_bytes + V0.nbytes + info.h2d_bytes) / K,
             "d2h_bytes_per_step": (out_bytes + info.d2h_bytes) / K,
             "iterations": info.iters}
+
+
+def small_pencil_iterations(G, K):
+    """32 x 32 convection-diffusion (n = 1024, k = 4, m = 1, sigma at the centre of the
+    spectrum, T = I): seconds per iteration, launch- and latency-bound at this size,
+    with kernel launches and with the iteration's segments replayed from CUDA graphs.
+    (The k pairs nearest this interior shift are not reached in practical time: the
+    eigenvector condition numbers are ~1e9.)"""
+    import torch
+    from paper_1506_06829_gb300 import problems as P
+    pr = P.config1()
+    out = {"workload": "convdiff2d_32x32 (n = 1024, k = 4, m = 1, sigma = 4/h^2, T = I)", "unit": "s/iteration"}
+    for graphs in (False, True):
+        s = G.GPLHR(pr.A, None, pr.sigma, pr.k, pr.m, pr.precond, pr.block_size, tol=1e-300, maxit=10 ** 6,
+                    graphs=graphs, autotune=graphs)
+        s.start(pr.start_block())
+        s.iterate(3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.iterate(K)
+        torch.cuda.synchronize()
+        out["graphs" if graphs else "launches"] = (time.perf_counter() - t0) / K
+        s.close()
+    return out
 
 
 def batched_throughput(G, K):
