@@ -40,6 +40,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "s to k eigenpairs @1e-8 resid (FP64 vs mixed); SpMM+Gram HBM GB/s vs peak"
 FP64_PEAK_GFLOPS = 1250.0   # GB300 dense FP64 (profiling recipe table); probe measured 1203
+GRAM_TRAFFIC_64CUBED = 62.4e6   # bytes per gram_partial launch, ncu, 64^3 FP64 workload
 KCLASSES = ["spmm", "gram", "combine", "precond", "chol", "other"]
 
 
@@ -228,9 +229,14 @@ def main():
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    # DRAM bytes per Gram launch (mean over one iteration's 54 launches) from one ncu
+    # capture of this workload in FP64 (profiles/gram_traffic_convdiff3d_64cubed.md);
+    # reported only for that workload and kernel
+    traffic = (GRAM_TRAFFIC_64CUBED if dom == "gram" and args.workload == "config2" and args.grid is None
+               and args.precision == "fp64" else None)
     roofline = {
         "kernel": dom, "bound": "alu", "achieved": achieved_gflops, "peak": FP64_PEAK_GFLOPS,
-        "unit": "GFLOP/s", "frac": achieved_gflops / FP64_PEAK_GFLOPS, "traffic": None,
+        "unit": "GFLOP/s", "frac": achieved_gflops / FP64_PEAK_GFLOPS, "traffic": traffic,
         "note": ("FP64 DFMA-bound: algorithmic flops (complex multiply-add = 8) / event time of the "
                  f"{d['launches']} {dom} launches; its algorithmic bytes give {achieved_gbs:.0f} GB/s "
                  f"= {achieved_gbs / hbm_peak:.3f} of the measured HBM copy bandwidth"),
