@@ -232,7 +232,7 @@ def main():
     # DRAM bytes per Gram launch (mean over one iteration's 54 launches) from one ncu
     # capture of this workload in FP64 (profiles/gram_traffic_convdiff3d_64cubed.md);
     # reported only for that workload and kernel
-    traffic = (GRAM_TRAFFIC_64CUBED if dom == "gram" and args.workload == "config2" and args.grid is None
+    traffic = (GRAM_TRAFFIC_64CUBED if dom == "gram" and args.workload == "config2" and not args.grid
                and args.precision == "fp64" else None)
     roofline = {
         "kernel": dom, "bound": "alu", "achieved": achieved_gflops, "peak": FP64_PEAK_GFLOPS,
