@@ -36,6 +36,13 @@ CUDA path):
   q..k-1, a thick P its leading k - q columns.
 * The right projector before T (Table 3) can be omitted: T_L = (I - VV^*) T instead of
   (I - VV^*) T (I - QQ^*) (or (I - VV^*) T (I - VV^*) when B = I).
+* Deflation (Sec. 3.6, last paragraph): given k1 computed right and left Schur vectors
+  V1, Q1, further ones come from GPLHR on the deflated pair ((I - Q1 Q1^*) A (I - V1 V1^*),
+  (I - Q1 Q1^*) B (I - V1 V1^*)), or (I - V1 V1^*) A (I - V1 V1^*) with B = I.  That pair
+  is singular on span(V1) (both maps vanish there), so the trial subspace must stay
+  orthogonal to V1: the paper is silent on how, and the reading here deflates T too,
+  T_d = (I - V1 V1^*) T (I - Q1 Q1^*) ((I - V1 V1^*) T (I - V1 V1^*) with B = I), and
+  projects the start block.  Residual norms keep ||A||_1, ||B||_1 of the original pair.
 """
 from __future__ import annotations
 
@@ -72,29 +79,40 @@ def onenorm(M) -> float:
 class Pencil:
     """(A, B, sigma, T) with B = None meaning B = I."""
 
-    def __init__(self, A, B, sigma: complex, T: Preconditioner):
+    def __init__(self, A, B, sigma: complex, T: Preconditioner, deflate=None):
         self.A = sp.csr_matrix(A).astype(np.complex128)
         self.B = None if B is None else sp.csr_matrix(B).astype(np.complex128)
         self.sigma = complex(sigma)
         self.T = T
+        # deflation basis (V1, Q1); Q1 is ignored (taken as V1) when B = I
+        self.V1 = self.Q1 = None
+        if deflate is not None:
+            self.V1 = np.asarray(deflate[0], dtype=np.complex128)
+            self.Q1 = self.V1 if self.B is None else np.asarray(deflate[1], dtype=np.complex128)
         self.n = self.A.shape[0]
         self.normA = onenorm(self.A)
         self.normB = onenorm(self.B)
         self.n_mv = 0       # products with A (and with B when B != I), column blocks
         self.n_prec = 0     # applications of T, column blocks
 
+    def _pv(self, X):
+        return X if self.V1 is None else X - self.V1 @ (self.V1.conj().T @ X)
+
+    def _pq(self, X):
+        return X if self.Q1 is None else X - self.Q1 @ (self.Q1.conj().T @ X)
+
     def Amul(self, X):
         self.n_mv += 1
-        return self.A @ X
+        return self._pq(self.A @ self._pv(X))
 
     def Bmul(self, X):
         if self.B is None:
             return X.copy()
-        return self.B @ X
+        return self._pq(self.B @ self._pv(X))
 
     def Tmul(self, X):
         self.n_prec += 1
-        return self.T.apply(X)
+        return self._pv(self.T.apply(self._pq(X)))
 
 
 @dataclasses.dataclass
@@ -253,9 +271,9 @@ def tri_eigvecs(RA: np.ndarray, RB: np.ndarray) -> np.ndarray:
 def residuals(pen: Pencil, st: State, AV=None, BV=None) -> np.ndarray:
     """Backward-error residual of each of the k pairs (see module docstring)."""
     if AV is None:
-        AV = pen.A @ st.V
+        AV = pen._pq(pen.A @ pen._pv(st.V))
     if BV is None:
-        BV = st.V if pen.B is None else pen.B @ st.V
+        BV = st.V if pen.B is None else pen._pq(pen.B @ pen._pv(st.V))
     Zv = tri_eigvecs(st.RA, st.RB)
     a = np.diag(st.RA)
     b = np.diag(st.RB)
@@ -289,15 +307,17 @@ class Result:
 def solve(A, B, sigma, V0, m: int = 1, tol: float = 1e-8, maxit: int = 500,
           precond: str = "none", block_size: int = 1, T: Preconditioner | None = None,
           lock: bool = True, callback=None, inner_steps: int = 0, p_mode: str = "thick",
-          right_proj: bool = True, lobpcg_C: np.ndarray | None = None) -> Result:
+          right_proj: bool = True, lobpcg_C: np.ndarray | None = None, deflate=None) -> Result:
     """Run Algorithm 2 until all k pairs meet ``tol`` or ``maxit`` iterations.
     inner_steps > 0: T is that many block GMRES steps preconditioned by ``precond``.
     p_mode, right_proj, lobpcg_C: the variants of Sec. 3.5 and Tables 2-3 (module
-    docstring)."""
+    docstring).  deflate = (V1, Q1): solve the deflated pair (module docstring)."""
+    if deflate is not None and inner_steps > 0:
+        raise ValueError("deflation with an inner GMRES preconditioner is not supported")
     if T is None:
         T = build_precond(A, B, sigma, precond, block_size, inner_steps)
-    pen = Pencil(A, B, sigma, T)
-    st = init_state(pen, V0, m, p_mode, right_proj, lobpcg_C)
+    pen = Pencil(A, B, sigma, T, deflate)
+    st = init_state(pen, pen._pv(np.asarray(V0, dtype=np.complex128)), m, p_mode, right_proj, lobpcg_C)
     k = st.k
     hist = []
     res = residuals(pen, st)
