@@ -304,6 +304,22 @@ gplhr_status gplhr_combine(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t w
 gplhr_status gplhr_spmm_shape(gplhr_ctx* ctx, int32_t w, int32_t fp32, int32_t* threads, int32_t* grid_per_sm,
                               double* us, double* us_default);
 
+/* gplhr_set_deflation -- compute further Schur vectors by deflation (Sec. 3.6, last
+ * paragraph): with V1, Q1 the k1 right and left generalized Schur vectors found by an
+ * earlier solve (n x k1 row-major complex128, ld k1; orthonormal columns), later starts
+ * and solves of this context run GPLHR on the deflated pair
+ *     ((I - Q1 Q1^*) A (I - V1 V1^*), (I - Q1 Q1^*) B (I - V1 V1^*)),
+ * or (I - V1 V1^*) A (I - V1 V1^*) when B = I (Q1 is then ignored and may be NULL).  The
+ * deflated pair is singular on span(V1), so T is deflated alike,
+ * (I - V1 V1^*) T (I - Q1 Q1^*), and the start block is projected: the trial subspace stays
+ * orthogonal to V1.  The new block (V2, Q2, R_A2, R_B2 from gplhr_vectors) extends the
+ * partial Schur form: A [V1 V2] = [Q1 Q2] [[R_A1, Q1^* A V2], [0, R_A2]], likewise B.
+ * Residuals are those of the deflated pair, normalised by ||A||_1, ||B||_1.  The library
+ * copies V1, Q1 (where = HOST or DEVICE); k1 = 0 removes the deflation.  EINVAL for
+ * k1 > 256, k1 + (m+3)k > n, k1 k > 2 ((m+3)k)^2, missing bases, or with inner GMRES
+ * steps (opts: T.inner_steps > 0). */
+gplhr_status gplhr_set_deflation(gplhr_ctx* ctx, const void* V1, const void* Q1, int32_t k1, int32_t where);
+
 /* orth(X) in place (Alg. 1 footnote): X <- X R^{-1} with X = Q R the thin QR whose R
  * has a real positive diagonal, by Cholesky QR applied twice (a shifted Cholesky
  * first pass and a third pass when the Gram matrix is not numerically positive

@@ -90,6 +90,11 @@ struct gplhr_ctx {
   int* h_status = nullptr;
   size_t trk = 0;              // stride of the passes in dTrackC (>= s_max^2)
   bool factored = true;        // projected pencil from U's factors (one Gram)
+  // deflation basis (gplhr_set_deflation): k1 right / left Schur vectors already computed;
+  // the iteration then runs on ((I - Q1 Q1^*) A (I - V1 V1^*), (I - Q1 Q1^*) B (I - V1 V1^*))
+  double2* dV1 = nullptr;
+  double2* dQ1 = nullptr;
+  int k1 = 0;
   int p_mode = 0;              // search directions P: 0 thick restart (Eq. P1), 1 LOBPCG
                                // style V - V_old (Eq. P_lobpcg, C = I), 2 none
   bool right_proj = true;      // projector before T (Table 3)
@@ -480,11 +485,27 @@ gplhr_status autotune_spmm(gplhr_ctx* ctx) {
   return st;
 }
 
-// AX = A X and (B != I) BX = B X
+gplhr_status project_out(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w);
+
+// Products with the pencil the iteration runs on: A X and (B != I) B X, or with a
+// deflation basis (V1, Q1) the deflated maps (I - Q1 Q1^*) A (I - V1 V1^*) X and
+// (I - Q1 Q1^*) B (I - V1 V1^*) X (Q1 = V1 when B = I).  X is projected in place.
+gplhr_status pair_products(gplhr_ctx* ctx, Blk X, int w, Blk AX, Blk BX, bool fp32) {
+  if (ctx->k1 > 0) TRY(project_out(ctx, Blk{ctx->dV1, ctx->k1}, ctx->k1, X, w));
+  TRY(launch_spmm_one(ctx, ctx->A, ctx->hasB ? &ctx->B : nullptr, X, w, AX, BX, fp32));
+  if (ctx->k1 > 0) {
+    const Blk L{ctx->hasB ? ctx->dQ1 : ctx->dV1, ctx->k1};
+    TRY(project_out(ctx, L, ctx->k1, AX, w));
+    if (ctx->hasB) TRY(project_out(ctx, L, ctx->k1, BX, w));
+  }
+  return GPLHR_OK;
+}
+
+// AX = A X and (B != I) BX = B X (deflated pair when a deflation basis is set)
 gplhr_status spmm_AB(gplhr_ctx* ctx, Blk X, int w, Blk AX, Blk BX) {
   if (w <= 0) return GPLHR_OK;
   ctx->n_spmm += 1;
-  return launch_spmm_one(ctx, ctx->A, ctx->hasB ? &ctx->B : nullptr, X, w, AX, BX, ctx->bulk32);
+  return pair_products(ctx, X, w, AX, BX, ctx->bulk32);
 }
 
 // C (wx x (wy0 + wy1), row-major) = X^* [Y0 Y1].  herm: X^* X (only the upper
@@ -675,6 +696,11 @@ gplhr_status precond_apply_t0(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
 gplhr_status precond_apply(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
   if (w <= 0) return GPLHR_OK;
   ctx->n_prec += 1;
+  if (ctx->k1 > 0) {  // deflated T: (I - V1 V1^*) T (I - Q1 Q1^*), X projected in place
+    TRY(project_out(ctx, Blk{ctx->hasB ? ctx->dQ1 : ctx->dV1, ctx->k1}, ctx->k1, X, w));
+    TRY(precond_apply_t0(ctx, X, w, Y));
+    return project_out(ctx, Blk{ctx->dV1, ctx->k1}, ctx->k1, Y, w);
+  }
   return ctx->gm_steps > 0 ? gmres_apply(ctx, X, w, Y) : precond_apply_t0(ctx, X, w, Y);
 }
 
@@ -1015,6 +1041,7 @@ gplhr_status start(gplhr_ctx* ctx) {
 // QZ of (Q^*AV, Q^*BV), V <- V YR, Q <- Q YL, M_A, M_B; then the residuals.
 gplhr_status start_steps(gplhr_ctx* ctx) {
   const int k = ctx->k;
+  if (ctx->k1 > 0) TRY(project_out(ctx, Blk{ctx->dV1, ctx->k1}, ctx->k1, blkZ(ctx, 0), k));  // deflation
   TRY(orth_against(ctx, Blk{nullptr, 0}, 0, blkZ(ctx, 0), k));                // V = orth(V0)
   TRY(spmm_AB(ctx, blkZ(ctx, 0), k, blkAZ(ctx, 0), blkBZ(ctx, 0)));        // AV, BV
   const double2 ms = d2(-ctx->sigma);
@@ -1571,6 +1598,7 @@ void free_all(gplhr_ctx* c) {
   auto F = [](void* p) {
     if (p) cudaFree(p);
   };
+  F(c->dV1); F(c->dQ1);
   F(c->A.rowptr); F(c->A.col); F(c->A.val); F(c->A.val32);
   F(c->B.rowptr); F(c->B.col); F(c->B.val); F(c->B.val32);
   F(c->Tcsr.rowptr); F(c->Tcsr.col); F(c->Tcsr.val); F(c->Tcsr.val32);
@@ -1996,7 +2024,7 @@ gplhr_status gplhr_vectors(gplhr_ctx* ctx, double* alpha, double* beta, double* 
     TRY(combine(ctx, {In{blkZ(ctx, 0), k, ctx->dC1, kOne}}, Xb, k, false, nullptr, none, -1, -1, true, 0));
     if (resid) {
       Blk AX{ctx->Tw1, k}, BX{ctx->hasB ? ctx->Tw2 : ctx->Tw3, k};
-      TRY(launch_spmm_one(ctx, ctx->A, ctx->hasB ? &ctx->B : nullptr, Xb, k, AX, BX));
+      TRY(pair_products(ctx, Xb, k, AX, BX, false));
       double2* hb = ctx->h_small + k * k;
       double2* ha = ctx->h_small + 2 * k * k;
       for (int i = 0; i < k; ++i)
@@ -2097,6 +2125,39 @@ gplhr_status gplhr_spmm_shape(gplhr_ctx* ctx, int32_t w, int32_t fp32, int32_t* 
   if (grid_per_sm) *grid_per_sm = sh.gridmul;
   if (us) *us = sh.us;
   if (us_default) *us_default = sh.us_default;
+  return GPLHR_OK;
+}
+
+gplhr_status gplhr_set_deflation(gplhr_ctx* ctx, const void* V1, const void* Q1, int32_t k1, int32_t where) {
+  if (!ctx) return GPLHR_EINVAL;
+  if (k1 < 0 || k1 > 256 || (k1 > 0 && (!V1 || (ctx->hasB && !Q1))) || (where != GPLHR_HOST && where != GPLHR_DEVICE) ||
+      (int64_t)k1 + ctx->s_max > ctx->n || (size_t)k1 * ctx->k > (size_t)2 * ctx->s_max * ctx->s_max) {
+    ctx->err = "gplhr_set_deflation: need 0 <= k1 <= 256, k1 + (m+3)k <= n, k1 k <= 2 ((m+3)k)^2, V1 (and Q1 "
+               "when B != I) given, where HOST or DEVICE";
+    return GPLHR_EINVAL;
+  }
+  if (ctx->gm_steps > 0 && k1 > 0) {
+    ctx->err = "gplhr_set_deflation: not available with inner GMRES steps";
+    return GPLHR_EINVAL;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (auto& g : ctx->seg_graphs) cudaGraphExecDestroy(g.second.exec);  // launch sequences change
+  ctx->seg_graphs.clear();
+  if (ctx->dV1) cudaFree(ctx->dV1);
+  if (ctx->dQ1) cudaFree(ctx->dQ1);
+  ctx->dV1 = ctx->dQ1 = nullptr;
+  ctx->k1 = 0;
+  if (k1 == 0) return GPLHR_OK;
+  const size_t bytes = (size_t)ctx->n * k1 * sizeof(double2);
+  const cudaMemcpyKind kind = where == GPLHR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMalloc(&ctx->dV1, bytes));
+  CK(cudaMemcpyAsync(ctx->dV1, V1, bytes, kind, ctx->stream));
+  if (ctx->hasB) {
+    CK(cudaMalloc(&ctx->dQ1, bytes));
+    CK(cudaMemcpyAsync(ctx->dQ1, Q1, bytes, kind, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->k1 = k1;
   return GPLHR_OK;
 }
 

@@ -29,7 +29,7 @@ EXPORTED = ["gplhr_create", "gplhr_solve", "gplhr_start", "gplhr_iterate", "gplh
             "gplhr_destroy", "gplhr_last_error", "gplhr_spmm", "gplhr_precond_apply",
             "gplhr_gram", "gplhr_combine", "gplhr_orth", "gplhr_ordqz", "gplhr_mfactors", "gplhr_profile",
             "gplhr_profile_read", "gplhr_gram_noalloc", "gplhr_grad", "gplhr_solve_batched",
-            "gplhr_iterate_batched", "gplhr_spmm_shape"]
+            "gplhr_iterate_batched", "gplhr_spmm_shape", "gplhr_set_deflation"]
 P_MODES = {"thick": 0, "lobpcg": 1, "none": 2}
 KCLASS = {"spmm": 0, "gram": 1, "combine": 2, "precond": 3, "chol": 4, "other": 5}
 
@@ -97,6 +97,7 @@ def lib():
     L.gplhr_orth.argtypes = [vp, vp, i32, i32, vp]
     L.gplhr_combine.argtypes = [vp, vp, i32, i32, vp, i32, vp, i32, i32, i32]
     L.gplhr_spmm_shape.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(i32), dp, dp]
+    L.gplhr_set_deflation.argtypes = [vp, vp, vp, i32, i32]
     L.gplhr_ordqz.argtypes = [i32, dp, dp, dbl, dbl, dp, dp, dp, dp]
     L.gplhr_mfactors.argtypes = [i32, dp, dp, dp, dp]
     L.gplhr_profile.argtypes = [vp, i32]
@@ -259,6 +260,24 @@ def gplhr_combine(ctx, X, C, Y, beta: bool = False, arith: str = "auto"):
     _check(lib().gplhr_combine(ctx, X.data_ptr(), X.stride(0), X.shape[1], C.data_ptr(), Y.shape[1],
                                Y.data_ptr(), Y.stride(0), 1 if beta else 0,
                                {"auto": 0, "dfma": 1}[arith]), ctx)
+
+
+def gplhr_set_deflation(ctx, V1, Q1=None):
+    """Deflate the V1 (n x k1) / Q1 Schur vectors found earlier; host arrays or device
+    tensors (complex128).  V1 = None removes the deflation."""
+    if V1 is None:
+        _check(lib().gplhr_set_deflation(ctx, None, None, 0, GPLHR_HOST), ctx)
+        return
+    dev = hasattr(V1, "data_ptr")
+    if dev:
+        k1 = V1.shape[1]
+        _check(lib().gplhr_set_deflation(ctx, V1.data_ptr(), Q1.data_ptr() if Q1 is not None else None, k1,
+                                         GPLHR_DEVICE), ctx)
+        return
+    V = np.ascontiguousarray(V1, dtype=np.complex128)
+    Q = None if Q1 is None else np.ascontiguousarray(Q1, dtype=np.complex128)
+    _check(lib().gplhr_set_deflation(ctx, V.ctypes.data, None if Q is None else Q.ctypes.data, V.shape[1],
+                                     GPLHR_HOST), ctx)
 
 
 def gplhr_spmm_shape(ctx, w: int, fp32: bool = False):
