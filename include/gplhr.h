@@ -144,6 +144,14 @@ typedef struct {
   int32_t no_right_proj; /* [0]  1 = omit the projector applied before T (T_L = (I - VV^*) T
                           instead of (I - VV^*) T (I - QQ^*), or (I - VV^*) T (I - VV^*) when
                           B = I): the variant the paper compares in its Table 3.            */
+  int32_t variant;     /* [0]    0 = GPLHR on Schur vectors (Alg. 2); 1 = GPLHR-EIG (Alg. 3,
+                          Appendix A): eigenvector iterate X with unit columns, eigenvalues
+                          the Rayleigh quotients x^* A x / x^* B x, projected pair solved by
+                          its eigenvectors; P of step 27 (p_mode 0) or of step 25 (p_mode 1);
+                          all k pairs converge together (no locking).  FP64 only, with the
+                          projector before T, no deflation, no gplhr_grad.  gplhr_vectors
+                          then fills alpha, beta, lambda, X and resid and zero-fills V, Q,
+                          RA, RB.  EINVAL for other values or combinations.               */
 } gplhr_opts;
 
 /* Per-solve report.  resid[j] (j < k) is the backward error of pair j,

@@ -95,6 +95,11 @@ struct gplhr_ctx {
   double2* dV1 = nullptr;
   double2* dQ1 = nullptr;
   int k1 = 0;
+  // GPLHR-EIG (Algorithm 3): eigenvector iterate X (unit columns), A X, B X, and the
+  // Rayleigh-quotient factors alpha_j = x_j^* A x_j, beta_j = x_j^* B x_j
+  bool eig = false;
+  double2 *eX = nullptr, *eAX = nullptr, *eBX = nullptr;
+  std::vector<cd> ea, eb;
   int p_mode = 0;              // search directions P: 0 thick restart (Eq. P1), 1 LOBPCG
                                // style V - V_old (Eq. P_lobpcg, C = I), 2 none
   bool right_proj = true;      // projector before T (Table 3)
@@ -1022,7 +1027,10 @@ void set_factors(gplhr_ctx* ctx, const SqMat& RAb, const SqMat& RBb) {
 gplhr_status start_steps(gplhr_ctx* ctx);
 
 // Steps 1-4 of Algorithm 2.  Z[:, 0:k] must hold V0.
+gplhr_status eig_start(gplhr_ctx* ctx);
+
 gplhr_status start(gplhr_ctx* ctx) {
+  if (ctx->eig) return eig_start(ctx);
   ctx->it = 0;
   ctx->q = 0;
   ctx->m = ctx->m0;
@@ -1393,7 +1401,10 @@ void fill_info(gplhr_ctx* ctx, gplhr_info* info) {
   for (int j = 0; j < ctx->k && j < 64 && j < (int)ctx->resid.size(); ++j) info->resid[j] = ctx->resid[j];
 }
 
+gplhr_status eig_run(gplhr_ctx* ctx, int niter, gplhr_info* info, bool* conv_out);
+
 gplhr_status run_iterations(gplhr_ctx* ctx, int niter, gplhr_info* info, bool* conv_out) {
+  if (ctx->eig) return eig_run(ctx, niter, info, conv_out);
   TRY(phase_update(ctx));
   bool conv = converged_update(ctx);
   for (int i = 0; i < niter && !conv; ++i) {
@@ -1402,6 +1413,218 @@ gplhr_status run_iterations(gplhr_ctx* ctx, int niter, gplhr_info* info, bool* c
     TRY(residuals(ctx));
     TRY(phase_update(ctx));
     conv = converged_update(ctx);
+  }
+  fill_info(ctx, info);
+  if (conv_out) *conv_out = conv;
+  return GPLHR_OK;
+}
+
+// ------------------------------------------------------------ GPLHR-EIG ------
+// Algorithm 3 (Appendix A): the eigenvector-based variant.  The iterate X has unit
+// columns; its Rayleigh quotients alpha_j / beta_j (bilinear forms x^* A x, x^* B x) are
+// the eigenvalue approximations; the trial and test subspaces are built as in Algorithm 2
+// with diag(beta), diag(alpha) in place of M_B, M_A; the projected pair is solved by its
+// eigenvectors (ordered complex QZ, back substitution on the leading 2k block), which
+// give X = Z Y(:, 1:k) and P (step 25, LOBPCG style, or step 27, thick restart).
+
+// Upload the k x 2k row-major matrices [diag(d), diag(d)] of the two coefficient vectors
+// (residual stored and its column norms taken in one combination).
+gplhr_status eig_upload_diag2(gplhr_ctx* ctx, double2* dst, const std::vector<cd>& d, double2* stage) {
+  const int k = ctx->k;
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < 2 * k; ++j) stage[i * 2 * k + j] = (j % k == i) ? d2(d[i]) : make_double2(0.0, 0.0);
+  return upload(ctx, dst, stage, (size_t)2 * k * k);
+}
+
+// Step 28 (and steps 1-2): x_j <- x_j / ||x_j||, A X, B X, alpha, beta, Q <- (A - sigma B) X
+// (U's first k columns), the residual R = A X diag(beta) - B X diag(alpha) into Rw with
+// its column norms; the host receives alpha, beta and the backward errors.
+gplhr_status eig_refresh(gplhr_ctx* ctx) {
+  const int k = ctx->k, sm = ctx->s_max;
+  const Blk none{nullptr, 0};
+  const Blk X{ctx->eX, k}, AX{ctx->eAX, k}, BX{ctx->hasB ? ctx->eBX : ctx->eX, k};
+  TRY(gram(ctx, X, k, X, k, none, 0, ctx->dGram));
+  std::vector<double2> G((size_t)k * k);
+  CK(cudaMemcpyAsync(G.data(), ctx->dGram, (size_t)k * k * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  double2* hs = ctx->h_small;
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) {
+      const double nj = std::sqrt(G[(size_t)j * k + j].x);
+      hs[i * k + j] = make_double2(i == j && nj > 0.0 ? 1.0 / nj : 0.0, 0.0);
+    }
+  TRY(upload(ctx, ctx->dC1, hs, (size_t)k * k));
+  TRY(combine(ctx, {In{X, k, ctx->dC1, kOne}}, X, k, false, nullptr, none, -1, -1, true, 0));
+  TRY(spmm_AB(ctx, X, k, AX, ctx->hasB ? BX : none));
+  TRY(gram(ctx, X, k, AX, k, BX, k, ctx->dPhiPsi));
+  std::vector<double2> H((size_t)k * 2 * k);
+  CK(cudaMemcpyAsync(H.data(), ctx->dPhiPsi, H.size() * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->ea.assign(k, cd(0.0, 0.0));
+  ctx->eb.assign(k, cd(0.0, 0.0));
+  for (int j = 0; j < k; ++j) {
+    ctx->ea[j] = cd(H[(size_t)j * 2 * k + j].x, H[(size_t)j * 2 * k + j].y);
+    ctx->eb[j] = cd(H[(size_t)j * 2 * k + k + j].x, H[(size_t)j * 2 * k + k + j].y);
+  }
+  const int ph = prof_begin(ctx, KC_OTHER, 8.0 * ctx->n * k, 48.0 * ctx->n * k);
+  gplhr::axpby_kernel<<<grid_for((size_t)ctx->n * k, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+      ctx->n, k, kOne, ctx->eAX, k, d2(-ctx->sigma), BX.p, k, ctx->U, sm);
+  prof_end(ctx, ph);
+  CK(cudaGetLastError());
+  TRY(eig_upload_diag2(ctx, ctx->dC1, ctx->eb, ctx->h_small));
+  TRY(eig_upload_diag2(ctx, ctx->dC2, ctx->ea, ctx->h_small + 2 * k * k));
+  TRY(combine(ctx, {In{AX, k, ctx->dC1, kOne}, In{BX, k, ctx->dC2, kMinusOne}}, Blk{ctx->Rw, k}, 2 * k, false,
+              nullptr, none, k, k));
+  CK(cudaMemcpyAsync(ctx->h_norms, ctx->d_norms, k * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_diag, ctx->d_diag, 3 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->resid.assign(k, 0.0);
+  for (int j = 0; j < k; ++j) {
+    const double den = std::abs(ctx->eb[j]) * ctx->normA + std::abs(ctx->ea[j]) * ctx->normB;
+    ctx->resid[j] = std::sqrt(ctx->h_norms[j]) / den;
+    if (!std::isfinite(ctx->resid[j])) {
+      ctx->err = "non-finite residual";
+      return GPLHR_ENUMERIC;
+    }
+  }
+  if (ctx->h_diag[1] != 0) {
+    ctx->err = "orth(): Cholesky QR broke down even with the shifted first pass";
+    return GPLHR_ESINGULAR;
+  }
+  if (ctx->h_diag[2] != 0) {
+    ctx->err = "tensor-core product: wait for completion gave up";
+    return GPLHR_ETIMEOUT;
+  }
+  return GPLHR_OK;
+}
+
+gplhr_status eig_start(gplhr_ctx* ctx) {
+  const int k = ctx->k;
+  ctx->it = 0;
+  ctx->q = 0;
+  ctx->m = ctx->m0;
+  ctx->hasP = false;
+  ctx->n_spmm = ctx->n_prec = ctx->n_qz = ctx->n_inner = 0;
+  ctx->h2d_bytes = ctx->d2h_bytes = 0;
+  ctx->bulk32 = false;
+  CK(cudaMemsetAsync(ctx->d_diag, 0, 3 * sizeof(int), ctx->stream));
+  gplhr::copy_block_kernel<<<grid_for((size_t)ctx->n * k, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+      ctx->n, k, ctx->Z, ctx->s_max, ctx->eX, k);
+  CK(cudaGetLastError());
+  TRY(eig_refresh(ctx));
+  ctx->started = true;
+  return GPLHR_OK;
+}
+
+gplhr_status eig_iterate_once(gplhr_ctx* ctx) {
+  const int k = ctx->k, m = ctx->m0, sm = ctx->s_max;
+  const Blk none{nullptr, 0};
+  const Blk V = blkZ(ctx, 0), Q = blkU(ctx, 0);
+  const Blk right = ctx->hasB ? Q : V;
+  // step 4: V = orth(X), Q = orth((A - sigma B) X)
+  gplhr::copy_block_kernel<<<grid_for((size_t)ctx->n * k, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+      ctx->n, k, ctx->eX, k, ctx->Z, sm);
+  CK(cudaGetLastError());
+  TRY(orth_against(ctx, none, 0, V, k));
+  TRY(orth_against(ctx, none, 0, Q, k));
+  TRY(spmm_AB(ctx, V, k, blkAZ(ctx, 0), blkBZ(ctx, 0)));  // A V, B V: the pencil's first k columns
+  // steps 5-10: W from the residual A X diag(beta) - B X diag(alpha) (in Rw)
+  Blk R{ctx->Rw, k};
+  TRY(project_out(ctx, right, k, R, k));
+  TRY(precond_apply(ctx, R, k, blkZ(ctx, k)));
+  TRY(orth_against(ctx, V, k, blkZ(ctx, k), k));
+  TRY(spmm_AB(ctx, blkZ(ctx, k), k, blkAZ(ctx, k), blkBZ(ctx, k)));
+  // steps 11-18
+  if (m > 0) {
+    double2* hm = ctx->h_small + 4 * k * k;
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) {
+        hm[i * k + j] = i == j ? d2(ctx->eb[i]) : make_double2(0.0, 0.0);
+        hm[k * k + i * k + j] = i == j ? d2(ctx->ea[i]) : make_double2(0.0, 0.0);
+      }
+    TRY(upload(ctx, ctx->dMBa, hm, 2 * k * k));
+  }
+  for (int l = 1; l <= m; ++l) {
+    const int prev = l * k, cur = (l + 1) * k;
+    TRY(combine(ctx, {In{blkAZ(ctx, prev), k, ctx->dMBa, kOne}, In{blkBZ(ctx, prev), k, ctx->dMBa + k * k, kMinusOne}},
+                R, k, false));
+    TRY(project_out(ctx, right, k, R, k));
+    TRY(precond_apply(ctx, R, k, blkZ(ctx, cur)));
+    TRY(orth_against(ctx, V, cur, blkZ(ctx, cur), k));
+    TRY(spmm_AB(ctx, blkZ(ctx, cur), k, blkAZ(ctx, cur), blkBZ(ctx, cur)));
+  }
+  // step 19: P against V, W, S, orth; A P, B P by sparse products
+  const int pslot = (m + 2) * k;
+  int s = pslot;
+  if (ctx->hasP) {
+    gplhr::copy_block_kernel<<<grid_for((size_t)ctx->n * k, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+        ctx->n, k, ctx->Pb, k, ctx->Z + pslot, sm);
+    CK(cudaGetLastError());
+    TRY(orth_against(ctx, V, pslot, blkZ(ctx, pslot), k));
+    TRY(spmm_AB(ctx, blkZ(ctx, pslot), k, blkAZ(ctx, pslot), blkBZ(ctx, pslot)));
+    s += k;
+  }
+  const int sk = s - k;
+  // steps 20-22: Qhat = orth((A - sigma B) [W S P]) against Q; U = [Q Qhat]
+  const int ph = prof_begin(ctx, KC_OTHER, 8.0 * ctx->n * sk, 48.0 * ctx->n * sk);
+  gplhr::axpby_kernel<<<grid_for((size_t)ctx->n * sk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+      ctx->n, sk, kOne, ctx->AZ + k, sm, d2(-ctx->sigma), blkBZ(ctx, k).p, sm, ctx->U + k, sm);
+  prof_end(ctx, ph);
+  CK(cudaGetLastError());
+  TRY(orth_against(ctx, Q, k, blkU(ctx, k), sk));
+  // step 23: eigenvectors of (U^* A Z, U^* B Z) nearest sigma
+  TRY(gram(ctx, blkU(ctx, 0), s, blkAZ(ctx, 0), s, blkBZ(ctx, 0), s, ctx->dPhiPsi));
+  ctx->d2h_bytes += (int64_t)2 * s * s * sizeof(double2);
+  CK(cudaMemcpyAsync(ctx->h_phipsi, ctx->dPhiPsi, (size_t)2 * s * s * sizeof(double2), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  SqMat RAb, RBb, YLb, YRb;
+  TRY(host_qz(ctx, s, RAb, RBb, YLb, YRb, 2 * k));
+  SqMat RA2(2 * k), RB2(2 * k);
+  for (int i = 0; i < 2 * k; ++i)
+    for (int j = 0; j < 2 * k; ++j) {
+      RA2(i, j) = RAb(i, j);
+      RB2(i, j) = RBb(i, j);
+    }
+  const SqMat Zt = gplhr::tri_eigvecs(RA2, RB2);
+  // Y = Ybar_R(:, 1:2k) Zt, unit columns; staged as Y(:, 1:k) and Y(:, k+1:2k), s x k each
+  double2* hy = ctx->h_small + 6 * k * k;
+  double2* hp = hy + (size_t)s * k;
+  for (int j = 0; j < 2 * k; ++j) {
+    std::vector<cd> col(s, cd(0.0, 0.0));
+    double nrm = 0.0;
+    for (int i = 0; i < s; ++i) {
+      cd acc(0.0, 0.0);
+      for (int t = 0; t <= j; ++t) acc += YRb(i, t) * Zt(t, j);
+      col[i] = acc;
+      nrm += std::norm(acc);
+    }
+    nrm = std::sqrt(nrm);
+    for (int i = 0; i < s; ++i) (j < k ? hy : hp)[(size_t)i * k + (j % k)] = d2(col[i] / nrm);
+  }
+  TRY(upload(ctx, ctx->dYR, hy, (size_t)s * k));
+  TRY(upload(ctx, ctx->dYL, hp, (size_t)s * k));
+  // steps 24-27: X = Z Y(:, 1:k); P = [W S P] Y(k+1:s, 1:k) (step 25) or Z Y(:, k+1:2k) (27)
+  TRY(combine(ctx, {In{blkZ(ctx, 0), s, ctx->dYR, kOne}}, Blk{ctx->eX, k}, k, false));
+  if (ctx->p_mode == 1)
+    TRY(combine(ctx, {In{blkZ(ctx, k), sk, ctx->dYR + (size_t)k * k, kOne}}, Blk{ctx->Pb, k}, k, false));
+  else
+    TRY(combine(ctx, {In{blkZ(ctx, 0), s, ctx->dYL, kOne}}, Blk{ctx->Pb, k}, k, false));
+  ctx->hasP = true;
+  ctx->it += 1;
+  return eig_refresh(ctx);  // step 28
+}
+
+gplhr_status eig_run(gplhr_ctx* ctx, int niter, gplhr_info* info, bool* conv_out) {
+  auto all = [&]() {
+    for (double r : ctx->resid)
+      if (!(r <= ctx->tol)) return false;
+    return !ctx->resid.empty();
+  };
+  bool conv = all();
+  for (int i = 0; i < niter && !conv; ++i) {
+    TRY(eig_iterate_once(ctx));
+    conv = all();
   }
   fill_info(ctx, info);
   if (conv_out) *conv_out = conv;
@@ -1598,7 +1821,7 @@ void free_all(gplhr_ctx* c) {
   auto F = [](void* p) {
     if (p) cudaFree(p);
   };
-  F(c->dV1); F(c->dQ1);
+  F(c->dV1); F(c->dQ1); F(c->eX); F(c->eAX); F(c->eBX);
   F(c->A.rowptr); F(c->A.col); F(c->A.val); F(c->A.val32);
   F(c->B.rowptr); F(c->B.col); F(c->B.val); F(c->B.val32);
   F(c->Tcsr.rowptr); F(c->Tcsr.col); F(c->Tcsr.val); F(c->Tcsr.val32);
@@ -1840,6 +2063,14 @@ gplhr_status gplhr_create(const gplhr_csr* A, const gplhr_csr* B, double sigma_r
       return GPLHR_EINVAL;
     }
     ctx->p_mode = opts->p_mode;
+    ctx->eig = opts->variant == 1;
+    if (opts->variant < 0 || opts->variant > 1 ||
+        (ctx->eig && (opts->precision != GPLHR_FP64 || opts->p_mode == 2 || opts->no_right_proj != 0))) {
+      g_create_error = "opts.variant must be 0 (Schur vectors, Alg. 2) or 1 (eigenvectors, Alg. 3); the "
+                       "eigenvector variant runs in FP64 with p_mode 0 or 1 and the projector before T";
+      delete ctx;
+      return GPLHR_EINVAL;
+    }
     if (opts->precision != GPLHR_FP64 && opts->precision != GPLHR_MIXED) {
       g_create_error = "opts.precision must be GPLHR_FP64 or GPLHR_MIXED";
       delete ctx;
@@ -1882,6 +2113,14 @@ gplhr_status gplhr_create(const gplhr_csr* A, const gplhr_csr* B, double sigma_r
   if ((st = upload_csr(ctx, A, ctx->A, &ctx->normA)) != GPLHR_OK) return fail(st);
   if (ctx->hasB && (st = upload_csr(ctx, B, ctx->B, &ctx->normB)) != GPLHR_OK) return fail(st);
   if ((st = allocate(ctx)) != GPLHR_OK) return fail(st);
+  if (ctx->eig) {
+    const size_t bytes = (size_t)ctx->n * ctx->k * sizeof(double2);
+    if (cudaMalloc(&ctx->eX, bytes) != cudaSuccess || cudaMalloc(&ctx->eAX, bytes) != cudaSuccess ||
+        (ctx->hasB && cudaMalloc(&ctx->eBX, bytes) != cudaSuccess)) {
+      ctx->err = "cudaMalloc failed (eigenvector variant buffers)";
+      return fail(GPLHR_ENOMEM);
+    }
+  }
   if ((st = setup_preconditioner(ctx, T)) != GPLHR_OK) return fail(st);
   if (ctx->mixed && (st = make_fp32_copies(ctx)) != GPLHR_OK) return fail(st);
   {
@@ -1952,6 +2191,39 @@ gplhr_status eigvec_block(gplhr_ctx* ctx, SqMat* Ze_out) {
 }
 }  // namespace
 
+// GPLHR-EIG results: the Rayleigh-quotient pairs, X, the residuals of the last refresh;
+// the Schur-form outputs (V, Q, RA, RB) are zero-filled (the variant keeps no Schur form).
+gplhr_status eig_vectors(gplhr_ctx* ctx, double* alpha, double* beta, double* lambda, void* X, void* V, void* Q,
+                         void* RA, void* RB, double* resid, int32_t where) {
+  const int n = ctx->n, k = ctx->k;
+  for (int j = 0; j < k; ++j) {
+    const cd a = ctx->ea[j], b = ctx->eb[j];
+    if (alpha) { alpha[2 * j] = a.real(); alpha[2 * j + 1] = a.imag(); }
+    if (beta) { beta[2 * j] = b.real(); beta[2 * j + 1] = b.imag(); }
+    if (lambda) {
+      const cd l = std::abs(b) > 0 ? a / b : cd(INFINITY, 0.0);
+      lambda[2 * j] = l.real();
+      lambda[2 * j + 1] = l.imag();
+    }
+    if (resid) resid[j] = ctx->resid[j];
+  }
+  const size_t bytes = (size_t)n * k * sizeof(double2), rbytes = (size_t)k * k * sizeof(double2);
+  if (X)
+    CK(cudaMemcpyAsync(X, ctx->eX, bytes, where == GPLHR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  void* outs[4] = {V, Q, RA, RB};
+  const size_t sizes[4] = {bytes, bytes, rbytes, rbytes};
+  for (int i = 0; i < 4; ++i)
+    if (outs[i]) {
+      if (where == GPLHR_DEVICE)
+        CK(cudaMemsetAsync(outs[i], 0, sizes[i], ctx->stream));
+      else
+        std::memset(outs[i], 0, sizes[i]);
+    }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return GPLHR_OK;
+}
+
 gplhr_status gplhr_vectors(gplhr_ctx* ctx, double* alpha, double* beta, double* lambda, void* X, void* V,
                            void* Q, void* RA, void* RB, double* resid, int32_t where) {
   if (!ctx) return GPLHR_EINVAL;
@@ -1959,6 +2231,7 @@ gplhr_status gplhr_vectors(gplhr_ctx* ctx, double* alpha, double* beta, double* 
     ctx->err = "gplhr_vectors before gplhr_start";
     return GPLHR_EINVAL;
   }
+  if (ctx->eig) return eig_vectors(ctx, alpha, beta, lambda, X, V, Q, RA, RB, resid, where);
   const int n = ctx->n, k = ctx->k;
   const cudaMemcpyKind d2x = where == GPLHR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   for (int j = 0; j < k; ++j) {
@@ -2136,8 +2409,8 @@ gplhr_status gplhr_set_deflation(gplhr_ctx* ctx, const void* V1, const void* Q1,
                "when B != I) given, where HOST or DEVICE";
     return GPLHR_EINVAL;
   }
-  if (ctx->gm_steps > 0 && k1 > 0) {
-    ctx->err = "gplhr_set_deflation: not available with inner GMRES steps";
+  if ((ctx->gm_steps > 0 || ctx->eig) && k1 > 0) {
+    ctx->err = "gplhr_set_deflation: not available with inner GMRES steps or the eigenvector variant";
     return GPLHR_EINVAL;
   }
   CK(cudaStreamSynchronize(ctx->stream));
@@ -2295,7 +2568,7 @@ gplhr_status gplhr_grad(gplhr_ctx* right, gplhr_ctx* left, const double* G, void
     return GPLHR_EINVAL;
   }
   gplhr_ctx* ctx = right;
-  if (!right->started || !left->started || right->n != left->n || right->k != left->k ||
+  if (!right->started || !left->started || right->eig || left->eig || right->n != left->n || right->k != left->k ||
       right->hasB != left->hasB || (dB_vals && !right->hasB)) {
     ctx->err = "gplhr_grad: both contexts must be solved, with equal n, k and B kind (dB needs B != I)";
     return GPLHR_EINVAL;

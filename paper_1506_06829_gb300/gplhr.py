@@ -50,7 +50,7 @@ class Opts(C.Structure):
                 ("no_lock", C.c_int32), ("products", C.c_int32), ("stream", C.c_void_p),
                 ("switch_tol", C.c_double), ("stall_iters", C.c_int32), ("pencil", C.c_int32),
                 ("fp64_gemm", C.c_int32), ("graphs", C.c_int32), ("autotune", C.c_int32),
-                ("p_mode", C.c_int32), ("no_right_proj", C.c_int32)]
+                ("p_mode", C.c_int32), ("no_right_proj", C.c_int32), ("variant", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -155,7 +155,7 @@ def gplhr_create(A, B, sigma: complex, k: int, m: int, precond: str = "none",
                  precision: str = "fp64", switch_tol: float = 1e-5, stall_iters: int = 5,
                  pencil: str = "factored", inner_steps: int = 0, fp64_gemm: str = "tensor",
                  graphs: bool = False, autotune: bool = False, p_mode: str = "thick",
-                 right_proj: bool = True):
+                 right_proj: bool = True, variant: str = "schur"):
     """Returns an opaque context handle (int).  A, B: SciPy CSR (B None = identity).
     inner_steps > 0: T = that many block GMRES steps on (A - sigma B) W = R,
     right-preconditioned by `precond`."""
@@ -167,7 +167,8 @@ def gplhr_create(A, B, sigma: complex, k: int, m: int, precond: str = "none",
     opts = Opts(tol, maxit, {"fp64": 0, "mixed": 1}[precision], 0 if lock else 1,
                 PRODUCTS[products], stream or None, switch_tol, stall_iters,
                 {"factored": 0, "gram": 1}[pencil], {"tensor": 0, "dfma": 1}[fp64_gemm],
-                1 if graphs else 0, 1 if autotune else 0, P_MODES[p_mode], 0 if right_proj else 1)
+                1 if graphs else 0, 1 if autotune else 0, P_MODES[p_mode], 0 if right_proj else 1,
+                {"schur": 0, "eig": 1}[variant])
     out = C.c_void_p()
     st = L.gplhr_create(C.byref(hA.desc), C.byref(hB.desc) if hB else None, sigma.real,
                         sigma.imag, k, m, C.byref(pc), C.byref(opts), C.byref(out))
@@ -394,11 +395,12 @@ class GPLHR:
     def __init__(self, A, B, sigma, k, m, precond="none", block_size=1, T=None, tol=1e-8,
                  maxit=500, lock=True, stream=0, products="auto", precision="fp64",
                  switch_tol=1e-5, stall_iters=5, pencil="factored", inner_steps=0,
-                 fp64_gemm="tensor", graphs=False, autotune=False, p_mode="thick", right_proj=True):
+                 fp64_gemm="tensor", graphs=False, autotune=False, p_mode="thick", right_proj=True,
+                 variant="schur"):
         self.n, self.k = A.shape[0], k
         self.ctx = gplhr_create(A, B, complex(sigma), k, m, precond, block_size, T, tol, maxit,
                                 lock, stream, products, precision, switch_tol, stall_iters, pencil,
-                                inner_steps, fp64_gemm, graphs, autotune, p_mode, right_proj)
+                                inner_steps, fp64_gemm, graphs, autotune, p_mode, right_proj, variant)
 
     def solve(self, V0=None, seed=0, allow_notconv=False):
         return gplhr_solve(self.ctx, V0, seed, allow_notconv)
