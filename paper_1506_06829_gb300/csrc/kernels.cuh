@@ -899,10 +899,11 @@ __global__ void chol_inv_kernel(int w, int64_t n, const double2* __restrict__ G,
       __syncthreads();
       if (fail) break;
       const double rp = sqrt(piv);
+      const double rpi = 1.0 / rp;  // one division per pivot (FP64 division is a long sequence)
       // scale row p (upper part) by 1/rp
       for (int j = p + tid; j < w; j += nt) {
         double2 v = a[p * w + j];
-        a[p * w + j] = j == p ? make_double2(rp, 0.0) : make_double2(v.x / rp, v.y / rp);
+        a[p * w + j] = j == p ? make_double2(rp, 0.0) : make_double2(v.x * rpi, v.y * rpi);
       }
       __syncthreads();
       // trailing update a[i][j] -= conj(R[p][i]) R[p][j], i, j > p, j >= i
@@ -925,13 +926,17 @@ __global__ void chol_inv_kernel(int w, int64_t n, const double2* __restrict__ G,
   }
   __syncthreads();
   // inverse of the upper triangular R: column c of inv solves R x = e_c (back substitution);
-  // the staging copy of G in inv is dead from here on
+  // the staging copy of G in inv is dead from here on.  The w reciprocals of the diagonal
+  // first, in parallel.
+  __shared__ double dinv[256];
+  for (int i = tid; i < w; i += nt) dinv[i] = 1.0 / a[i * w + i].x;
+  __syncthreads();
   for (int c = tid; c < w; c += nt) {
     for (int i = w - 1; i >= 0; --i) {
       double2 acc = make_double2(i == c ? 1.0 : 0.0, 0.0);
       for (int t = i + 1; t <= c; ++t) acc = csub(acc, cmul(a[i * w + t], inv[t * w + c]));
-      const double d = a[i * w + i].x;
-      inv[i * w + c] = i > c ? make_double2(0.0, 0.0) : make_double2(acc.x / d, acc.y / d);
+      const double d = dinv[i];
+      inv[i * w + c] = i > c ? make_double2(0.0, 0.0) : make_double2(acc.x * d, acc.y * d);
     }
   }
   __syncthreads();
