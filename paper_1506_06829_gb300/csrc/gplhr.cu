@@ -853,7 +853,20 @@ void accumulate_tracks(const double2* hC, size_t strideC, const double2* hR, siz
 // preconditioned by T0 (Sec. 4): block Arnoldi K T0 V_j = V_{j+1} H(:, j) with the
 // orthogonalisation of the sparse products (block CGS2 + Cholesky QR, tracked), then
 // Y = argmin ||E_1 B_0 - H Y||_F (R = V_1 B_0) on the host, and T R = T0 (V_s Y).
+gplhr_status gmres_apply_impl(gplhr_ctx* ctx, Blk X, int w, Blk Y);
+
+// In the mixed mode the inner solve runs in FP32 in every phase: T is a preconditioner,
+// whose accuracy sets the outer convergence rate but not the accuracy reached (residuals,
+// projections, pencil and refinement of the outer iteration keep their own precision).
 gplhr_status gmres_apply(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
+  const bool saved = ctx->bulk32;
+  if (ctx->mixed) ctx->bulk32 = true;
+  const gplhr_status st = gmres_apply_impl(ctx, X, w, Y);
+  ctx->bulk32 = saved;
+  return st;
+}
+
+gplhr_status gmres_apply_impl(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
   const int s = ctx->gm_steps, k = ctx->k, n = ctx->n;
   const int ldv = (s + 1) * k;
   const int smax2 = ctx->s_max * ctx->s_max;
