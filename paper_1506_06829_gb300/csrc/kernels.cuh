@@ -845,6 +845,23 @@ __global__ void reciprocal_kernel(int n, double2* __restrict__ d) {
 // fallback_counter[1] final failures.  Rout (may be null) receives R itself.  When `skip_if_zero` is non-null and *skip_if_zero
 // is 0, the kernel writes the identity and returns (used for the conditional third
 // pass of shifted Cholesky QR).
+// 1 / sqrt(a) for a finite a > 0: the exponent is scaled by a power of 4 into [1, 4) in
+// the bits (exact), an FP32 seed is refined by two Newton-Raphson steps for the reciprocal
+// square root, y <- y (3 - a y^2) / 2 (each step doubles the correct bits: ~23 -> 46 -> 92),
+// and the scaling is undone.  Accurate to a few ulp; on GB300 a dependent FP64 operation
+// takes ~70 cycles, and this chain is about half as long as sqrt followed by a division.
+__device__ __forceinline__ double rsqrt_newton(double a) {
+  const long long b = __double_as_longlong(a);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;         // a = f 2^e, f in [1, 2) (normal a)
+  const int h = e >> 1;                                   // floor(e / 2)
+  const double as = __longlong_as_double(b - ((long long)(2 * h) << 52));  // a 2^(-2h) in [1, 4)
+  double y = (double)rsqrtf((float)as);
+  const double ha = 0.5 * as;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) y = y * fma(-ha * y, y, 1.5);
+  return __longlong_as_double(__double_as_longlong(y) - ((long long)h << 52));  // y 2^(-h)
+}
+
 __global__ void chol_inv_kernel(int w, int64_t n, const double2* __restrict__ G,
                                 double2* __restrict__ Rinv, int* status, const int* skip_if_zero,
                                 int* fallback_counter, double2* __restrict__ Rout) {
@@ -852,7 +869,7 @@ __global__ void chol_inv_kernel(int w, int64_t n, const double2* __restrict__ G,
   double2* a = sm;              // w x w working copy -> R (upper)
   double2* inv = sm + w * w;    // w x w -> R^{-1}
   __shared__ int fail;
-  __shared__ double shift;
+  __shared__ double shift, piv_r, piv_ri;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (skip_if_zero && *skip_if_zero == 0) {
     for (int e = tid; e < w * w; e += nt) {
@@ -890,16 +907,23 @@ __global__ void chol_inv_kernel(int w, int64_t n, const double2* __restrict__ G,
     if (tid == 0) fail = 0;
     __syncthreads();
     double dmax = 0.0;
-    for (int i = 0; i < w; ++i) dmax = fmax(dmax, a[i * w + i].x);
+    if (tid == 0)
+      for (int i = 0; i < w; ++i) dmax = fmax(dmax, a[i * w + i].x);
     for (int p = 0; p < w; ++p) {
-      const double piv = a[p * w + p].x;
-      if (!(piv > 1e-15 * dmax) || !(piv > 0.0)) {
-        if (tid == 0) fail = 1;
+      // one thread takes the pivot's square root and reciprocal (GB300's FP64 pipe is
+      // narrow: the same sequence in every thread costs thousands of cycles per pivot)
+      if (tid == 0) {
+        const double piv = a[p * w + p].x;
+        if (!(piv > 1e-15 * dmax) || !(piv > 0.0) || !(piv <= 1e300) || !(piv >= 1e-300)) {
+          fail = 1;
+        } else {
+          piv_ri = rsqrt_newton(piv);
+          piv_r = piv * piv_ri;
+        }
       }
       __syncthreads();
       if (fail) break;
-      const double rp = sqrt(piv);
-      const double rpi = 1.0 / rp;  // one division per pivot (FP64 division is a long sequence)
+      const double rp = piv_r, rpi = piv_ri;
       // scale row p (upper part) by 1/rp
       for (int j = p + tid; j < w; j += nt) {
         double2 v = a[p * w + j];
@@ -925,19 +949,30 @@ __global__ void chol_inv_kernel(int w, int64_t n, const double2* __restrict__ G,
     if (attempt == 1 && tid == 0 && fallback_counter) atomicAdd(fallback_counter + 1, 1);
   }
   __syncthreads();
-  // inverse of the upper triangular R: column c of inv solves R x = e_c (back substitution);
-  // the staging copy of G in inv is dead from here on.  The w reciprocals of the diagonal
-  // first, in parallel.
+  // inverse of the upper triangular R by right-looking back substitution: inv starts as I;
+  // for t = w-1 .. 0, row t of inv is final once scaled by 1/R(t,t), and its multiples
+  // R(i,t) inv(t, :) are taken from the rows i < t, all entries in parallel (chain depth
+  // ~2w dependent operations instead of ~w^2/2 per column).  The staging copy of G in inv
+  // is dead from here on.
+  for (int e = tid; e < w * w; e += nt) {
+    const int i = e / w, j = e - i * w;
+    inv[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
   __shared__ double dinv[256];
   for (int i = tid; i < w; i += nt) dinv[i] = 1.0 / a[i * w + i].x;
   __syncthreads();
-  for (int c = tid; c < w; c += nt) {
-    for (int i = w - 1; i >= 0; --i) {
-      double2 acc = make_double2(i == c ? 1.0 : 0.0, 0.0);
-      for (int t = i + 1; t <= c; ++t) acc = csub(acc, cmul(a[i * w + t], inv[t * w + c]));
-      const double d = dinv[i];
-      inv[i * w + c] = i > c ? make_double2(0.0, 0.0) : make_double2(acc.x * d, acc.y * d);
+  for (int t = w - 1; t >= 0; --t) {
+    for (int c = t + tid; c < w; c += nt) {
+      const double2 v = inv[t * w + c];
+      inv[t * w + c] = make_double2(v.x * dinv[t], v.y * dinv[t]);
     }
+    __syncthreads();
+    const int wc = w - t;  // columns t .. w-1
+    for (int e = tid; e < t * wc; e += nt) {
+      const int i = e / wc, c = t + (e - i * wc);
+      inv[i * w + c] = csub(inv[i * w + c], cmul(a[i * w + t], inv[t * w + c]));
+    }
+    __syncthreads();
   }
   __syncthreads();
   for (int e = tid; e < w * w; e += nt) {
