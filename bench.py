@@ -40,8 +40,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "s to k eigenpairs @1e-8 resid (FP64 vs mixed); SpMM+Gram HBM GB/s vs peak"
 FP64_PEAK_GFLOPS = 1250.0   # GB300 dense FP64 (profiling recipe table); probe measured 1203
-GRAM_TRAFFIC_64CUBED = 62.4e6   # bytes per gram_partial launch, ncu, 64^3 FP64 workload
-KCLASSES = ["spmm", "gram", "combine", "precond", "chol", "other"]
+# DRAM bytes per launch (means over one iteration's launches) of this workload in FP64, from
+# one-pass ncu captures (profiles/gram_traffic_convdiff3d_64cubed.md)
+GRAM_TRAFFIC_64CUBED = 52.6e6        # gram_partial_kernel (DFMA), 46 launches
+COMBINE_TC_TRAFFIC_64CUBED = 68.6e6  # tc_combine_kernel, 31 launches
+KCLASSES = ["spmm", "gram", "combine", "precond", "chol", "other", "gram_tc", "combine_tc"]
+TENSOR_CLASSES = ("gram_tc", "combine_tc")   # FP64 by integer digits on the tensor cores
 
 
 def parse():
@@ -229,21 +233,30 @@ def main():
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    # DRAM bytes per Gram launch (mean over one iteration's 54 launches) from one ncu
-    # capture of this workload in FP64 (profiles/gram_traffic_convdiff3d_64cubed.md);
-    # reported only for that workload and kernel
-    traffic = (GRAM_TRAFFIC_64CUBED if dom == "gram" and args.workload == "config2" and not args.grid
-               and args.precision == "fp64" else None)
-    roofline = {
-        "kernel": dom, "bound": "alu", "achieved": achieved_gflops, "peak": FP64_PEAK_GFLOPS,
-        "unit": "GFLOP/s", "frac": achieved_gflops / FP64_PEAK_GFLOPS, "traffic": traffic,
-        "note": ("FP64 DFMA-bound: algorithmic flops (complex multiply-add = 8) / event time of the "
-                 f"{d['launches']} {dom} launches; its algorithmic bytes give {achieved_gbs:.0f} GB/s "
-                 f"= {achieved_gbs / hbm_peak:.3f} of the measured HBM copy bandwidth"),
-    }
+    default_full = args.workload == "config2" and not args.grid and args.precision == "fp64"
+    if dom in TENSOR_CLASSES:
+        roofline = {
+            "kernel": dom, "bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved_gbs / hbm_peak,
+            "traffic": COMBINE_TC_TRAFFIC_64CUBED if dom == "combine_tc" and default_full else None,
+            "note": (f"FP64 by integer digits on the tensor cores: algorithmic bytes / event time of the "
+                     f"{d['launches']} {dom} launches (of measured copy bandwidth); the kernel is bound by "
+                     f"its integer work (digit split, exact rounding), the tensor pipe is mostly idle; "
+                     f"FP64-equivalent {achieved_gflops:.0f} GFLOP/s vs the {FP64_PEAK_GFLOPS:.0f} of DFMA"),
+        }
+    else:
+        roofline = {
+            "kernel": dom, "bound": "alu", "achieved": achieved_gflops, "peak": FP64_PEAK_GFLOPS,
+            "unit": "GFLOP/s", "frac": achieved_gflops / FP64_PEAK_GFLOPS, "traffic": None,
+            "note": ("FP64 DFMA-bound: algorithmic flops (complex multiply-add = 8) / event time of the "
+                     f"{d['launches']} {dom} launches; its algorithmic bytes give {achieved_gbs:.0f} GB/s "
+                     f"= {achieved_gbs / hbm_peak:.3f} of the measured HBM copy bandwidth"),
+        }
+        if dom == "gram" and default_full:
+            roofline["traffic"] = GRAM_TRAFFIC_64CUBED
     spmm, gram = per_class["spmm"], per_class["gram"]
     hbm = {c: {"GB/s": (per_class[c]["gbyte"] / (per_class[c]["ms"] / 1e3)) if per_class[c]["ms"] else 0.0}
-           for c in ("spmm", "gram", "combine")}
+           for c in ("spmm", "gram", "combine", "gram_tc", "combine_tc")}
     for c in hbm:
         hbm[c]["frac_of_measured_peak"] = hbm[c]["GB/s"] / hbm_peak
     s_per_iter = ms / 1e3 / K

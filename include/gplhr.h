@@ -286,8 +286,12 @@ gplhr_status gplhr_precond_apply(gplhr_ctx* ctx, const void* X, int32_t ldx, int
  * coefficients of the mixed mode's bulk phase); GPLHR_GRAM_EXACT32 (2) inputs rounded
  * to FP32, every product formed exactly on the FP32 pipe and summed with compensation
  * into FP64 (the Cholesky-QR Grams and pencil of the bulk phase, whose blocks hold
- * FP32 values). */
-enum { GPLHR_GRAM_FP64 = 0, GPLHR_GRAM_FP32 = 1, GPLHR_GRAM_EXACT32 = 2 };
+ * FP32 values); GPLHR_GRAM_TENSOR (3) the FP64 product as the iteration forms it: on the
+ * tensor cores (each double split into 7 integer digits against a per-column exponent
+ * over 128-row windows, exact FP32 accumulation of digit products, one rounding per
+ * window, FP64 sums of the windows) when wx <= 128, wy <= 32, wx wy >= 400, n >= 2048
+ * and opts.fp64_gemm = 0, else DFMA.  EINVAL for wx > max((m+3)k, 128) or wy > 2 (m+3)k. */
+enum { GPLHR_GRAM_FP64 = 0, GPLHR_GRAM_FP32 = 1, GPLHR_GRAM_EXACT32 = 2, GPLHR_GRAM_TENSOR = 3 };
 gplhr_status gplhr_gram(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t wx, const void* Y,
                         int32_t ldy, int32_t wy, void* C, int32_t arith);
 
@@ -337,9 +341,11 @@ gplhr_status gplhr_orth(gplhr_ctx* ctx, void* X, int32_t ldx, int32_t w, void* R
 /* Instrumentation.  gplhr_profile(ctx, 1) clears the per-kernel-class counters and
  * brackets every later launch section with CUDA events on the context's stream;
  * gplhr_profile(ctx, 0) stops the timing (counters keep counting).
- * gplhr_profile_read returns for kernel class kclass -- 0 SpMM, 1 Gram, 2 block
- * combine (tall-skinny times small), 3 preconditioner, 4 small Cholesky, 5 other
- * elementwise -- the summed event time (ms, while profiling), the kernel launches,
+ * gplhr_profile_read returns for kernel class kclass -- 0 SpMM, 1 Gram (DFMA, FP32 or
+ * exact-FP32 arithmetic), 2 block combine (tall-skinny times small; DFMA or FP32), 3
+ * preconditioner, 4 small Cholesky, 5 other elementwise, 6 Gram on the tensor cores, 7
+ * block combine on the tensor cores -- the summed event time (ms, while profiling), the
+ * kernel launches,
  * and the ALGORITHMIC flops (complex multiply-add = 8, real x complex = 4) and bytes
  * (each operand read once, each result written once) of those launches. */
 gplhr_status gplhr_profile(gplhr_ctx* ctx, int32_t enable);

@@ -198,7 +198,8 @@ int grid_for(size_t work, int per_cta, int cap) {
 
 // ----------------------------------------------------------- accounting ----
 // Kernel classes for the per-class report (gplhr_profile_read).
-enum { KC_SPMM = 0, KC_GRAM = 1, KC_COMBINE = 2, KC_PREC = 3, KC_CHOL = 4, KC_OTHER = 5, KC_N = 6 };
+enum { KC_SPMM = 0, KC_GRAM = 1, KC_COMBINE = 2, KC_PREC = 3, KC_CHOL = 4, KC_OTHER = 5, KC_GRAM_TC = 6,
+       KC_COMBINE_TC = 7, KC_N = 8 };
 
 // Opens a timed section of class c (one or more launches); returns its handle.
 int prof_begin(gplhr_ctx* ctx, int c, double flops, double bytes, int launches = 1) {
@@ -532,11 +533,63 @@ void launch_gram_acc(gplhr_ctx* ctx, dim3 grid, size_t smem, int rows, Blk X, in
 // fp32: FP32 arithmetic (projection coefficients in the bulk phase).  Otherwise an
 // FP64-accurate Gram: DFMA, or in the bulk phase (FP32-valued blocks) exact products
 // on the FP32 pipe with compensated accumulation (gram_partial_x32_kernel).
+// FP64 Gram product on the tensor cores (tc.cuh): one persistent CTA per SM over 128-row
+// windows, partials reduced deterministically.  Shapes: wx <= 128, wy <= 32, with the
+// accumulators of all M tiles in tensor memory.
+bool gram_tc_fits(const gplhr_ctx* ctx, int wx, int wy) {
+  const int np = ((2 * wy + 15) / 16) * 16, mt = (2 * wx + 127) / 128;
+  return ctx->tc && wx <= gplhr::TG_AMAX && wy <= gplhr::TG_BMAX && mt * gplhr::TC_DIAG * np <= 512 &&
+         ctx->n >= 2048 && wx * wy >= 400 &&
+         (size_t)std::min(ctx->num_sms, (ctx->n + gplhr::TG_WIN - 1) / gplhr::TG_WIN) * wx * wy <=
+             ctx->gram_part_elems;
+}
+
+gplhr_status gram_tc(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy1, double2* C, const int* skip,
+                     int nout_count, bool count) {
+  gplhr::TcGramArgs t{};
+  const int wy = wy0 + wy1;
+  t.n = ctx->n;
+  t.X = X.p;
+  t.ldx = X.ld;
+  t.wx = wx;
+  t.Y0 = Y0.p;
+  t.ldy0 = Y0.ld;
+  t.wy0 = wy0;
+  t.Y1 = Y1.p;
+  t.ldy1 = Y1.ld;
+  t.wy1 = wy1;
+  t.partial = ctx->gram_part;
+  t.skip = skip;
+  t.err = ctx->d_diag + 2;
+  t.np = ((2 * wy + 15) / 16) * 16;
+  t.mt = (2 * wx + 127) / 128;
+  t.tmem_cols = 32;
+  while (t.tmem_cols < t.mt * gplhr::TC_DIAG * t.np) t.tmem_cols <<= 1;
+  const int nwin = (ctx->n + gplhr::TG_WIN - 1) / gplhr::TG_WIN;
+  const int grid = std::min(ctx->num_sms, nwin);
+  const bool self = X.p == Y0.p && wy1 == 0;
+  const double by = 16.0 * ctx->n * (self ? wx : wx + wy);
+  const int ph = prof_begin(ctx, KC_GRAM_TC, count ? 8.0 * ctx->n * nout_count : 0.0, count ? by : 0.0, 2);
+  gplhr::tc_gram_kernel<<<grid, gplhr::TG_THREADS, gplhr::tg_smem_bytes(t.mt, t.np), ctx->stream>>>(t);
+  CK(cudaGetLastError());
+  const int nout = wx * wy;
+  gplhr::gram_reduce_kernel<<<(nout + gplhr::GRED_WARPS - 1) / gplhr::GRED_WARPS, 32 * gplhr::GRED_WARPS, 0,
+                               ctx->stream>>>(grid, nout, wx, wy, 0, ctx->gram_part, C, skip);
+  prof_end(ctx, ph);
+  CK(cudaGetLastError());
+  return GPLHR_OK;
+}
+
 gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy1, double2* C,
                   const int* skip = nullptr, bool herm = false, bool count = true, bool fp32 = false,
                   int force_mode = -1) {
   const int mode = force_mode >= 0 ? force_mode : (fp32 ? 1 : (ctx->bulk32 ? 2 : 0));
   const int wy = wy0 + wy1;
+  if (mode == 0 && force_mode < 0 && gram_tc_fits(ctx, wx, wy)) {
+    // (a Hermitian request gets the full product; the algorithmic count stays the half)
+    const bool h = herm && wy1 == 0 && wy0 == wx;
+    return gram_tc(ctx, X, wx, Y0, wy0, Y1, wy1, C, skip, h ? wx * (wx + 1) / 2 : wx * wy, count);
+  }
   if (herm && (wy1 != 0 || wy0 != wx)) herm = false;
   const int nout = herm ? wx * (wx + 1) / 2 : wx * wy;
   if (nout == 0) return GPLHR_OK;
@@ -602,7 +655,7 @@ gplhr_status combine_tc(gplhr_ctx* ctx, gplhr::CombArgs a, int wsum, int c, int 
   const int grid = std::min(ntiles, per_sm * ctx->num_sms);
   t.a.normpart = c_store < c ? ctx->norm_part : nullptr;
   const double by = 16.0 * ctx->n * (wsum + c_store * (beta_one ? 2.0 : 1.0));
-  const int ph = prof_begin(ctx, KC_COMBINE, count ? 8.0 * ctx->n * (double)wsum * c : 0.0, count ? by : 0.0,
+  const int ph = prof_begin(ctx, KC_COMBINE_TC, count ? 8.0 * ctx->n * (double)wsum * c : 0.0, count ? by : 0.0,
                             c_store < c ? 2 : 1);
   gplhr::tc_combine_kernel<<<grid, gplhr::TC_THREADS, smem, ctx->stream>>>(ctx->n, t);
   CK(cudaGetLastError());
@@ -1942,6 +1995,8 @@ gplhr_status set_smem_limits(gplhr_ctx* ctx) {
                           big));
   CK(cudaFuncSetAttribute(gplhr::invert_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::tc_combine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)gplhr::tg_smem_bytes(2, 64)));
   return GPLHR_OK;
 }
 
@@ -2368,11 +2423,15 @@ gplhr_status gplhr_precond_apply(gplhr_ctx* ctx, const void* X, int32_t ldx, int
 
 gplhr_status gplhr_gram(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t wx, const void* Y, int32_t ldy,
                         int32_t wy, void* C, int32_t arith) {
-  if (!ctx || !valid_block(X, ldx, wx) || !valid_block(Y, ldy, wy) || !C || wx > ctx->s_max ||
-      wy > 2 * ctx->s_max || arith < 0 || arith > 2)
+  if (!ctx || !valid_block(X, ldx, wx) || !valid_block(Y, ldy, wy) || !C || wx > std::max(ctx->s_max, 128) ||
+      wy > 2 * ctx->s_max || arith < 0 || arith > 3)
     return GPLHR_EINVAL;
-  TRY(gram(ctx, Blk{(double2*)X, ldx}, wx, Blk{(double2*)Y, ldy}, wy, Blk{nullptr, 0}, 0, (double2*)C, nullptr,
-           false, true, false, arith));
+  const bool saved = ctx->bulk32;
+  if (arith == 3) ctx->bulk32 = false;  // the FP64 product, on the tensor cores where the shape allows
+  const gplhr_status st = gram(ctx, Blk{(double2*)X, ldx}, wx, Blk{(double2*)Y, ldy}, wy, Blk{nullptr, 0}, 0,
+                               (double2*)C, nullptr, false, true, false, arith == 3 ? -1 : arith);
+  ctx->bulk32 = saved;
+  TRY(st);
   CK(cudaStreamSynchronize(ctx->stream));
   return GPLHR_OK;
 }

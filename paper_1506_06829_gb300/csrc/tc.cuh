@@ -412,4 +412,262 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_combine_kernel(int n, TcComb
     for (int e = tid; e < nnorm; e += TC_THREADS) a.normpart[(size_t)blockIdx.x * nnorm + e] = nsum[e];
 }
 
+// ------------------------------------------------ Gram products on the tensor cores --
+// C = X^* [Y0 Y1] (wx x wy, wy = wy0 + wy1) with the digit scheme of the combination, the
+// contraction now over the rows.  Real form: X' (n x 2wx) and Y' (n x 2wy) hold the real
+// and imaginary parts as columns; G = X'^T Y' gives the four real products of every
+// complex pair, Re C(j,l) = G(2j,2l) + G(2j+1,2l+1), Im C(j,l) = G(2j,2l+1) - G(2j+1,2l).
+// * The rows are taken in windows of 128.  Every real column c of X' and of Y' gets its
+//   exponent bound E_c over the window's rows (a first pass); each value becomes the
+//   integer round(v 2^(54 - E_c)) in 7 balanced base-256 digits.
+// * A = X'^T (M = real column of X, up to two 128-row tiles; K = row), B = Y'^T with the
+//   digit planes stacked along N as in the combination; per 16-row K step 7 MMAs per M
+//   tile.  Over a window |D_d| <= 7 * 128 * 2^14 < 2^24: exact FP32 accumulation.
+// * After a window every G entry is formed exactly and rounded once to double
+//   (2^(E_m + E_n - 68) Z), then added to FP64 accumulators in registers; the CTA's
+//   partial C goes to partial[blockIdx.x][j wy + l] for the deterministic reduction.
+// Error: per window as for the combination, plus one FP64 addition per window.
+constexpr int TG_WIN = 128;   // rows per window (exact accumulation bound)
+constexpr int TG_SUB = 32;    // rows per shared-memory pass (two 16-row K steps)
+constexpr int TG_THREADS = 256;
+constexpr int TG_AMAX = 128;  // complex columns of X (2 M tiles)
+constexpr int TG_BMAX = 32;   // complex columns of [Y0 Y1]
+
+struct TcGramArgs {
+  int n;
+  const double2* X;
+  int ldx, wx;
+  const double2* Y0;
+  int ldy0, wy0;
+  const double2* Y1;
+  int ldy1, wy1;
+  double2* partial;  // [gridDim.x][wx * (wy0 + wy1)]
+  const int* skip;   // nothing happens when non-null and *skip == 0
+  int* err;          // set to 1 if a wait on the tensor core gave up
+  int np;            // 2 (wy0 + wy1) rounded up to a multiple of 16 (<= 64)
+  int mt;            // M tiles: 2 wx <= 128 mt (1 or 2; 2 needs np <= 32)
+  int tmem_cols;     // power of two >= mt * 8 * np
+};
+
+// Dynamic shared memory: A digits (7 planes x mt x 128 x TG_SUB) and B digits (8 planes x
+// np x TG_SUB), bf16.
+__host__ __device__ constexpr size_t tg_smem_bytes(int mt, int np) {
+  return (size_t)TC_DIGITS * mt * 128 * TG_SUB * 2 + (size_t)TC_DIAG * np * TG_SUB * 2;
+}
+
+__global__ void __launch_bounds__(TG_THREADS, 1) tc_gram_kernel(TcGramArgs ta) {
+  if (ta.skip && *ta.skip == 0) return;
+  extern __shared__ __align__(1024) unsigned char tg_smem[];
+  const int np = ta.np, mt = ta.mt, wx = ta.wx, wy = ta.wy0 + ta.wy1, n = ta.n;
+  constexpr int KC = TG_SUB / 8;
+  uint16_t* sA = reinterpret_cast<uint16_t*>(tg_smem);           // [7][mt][128 x TG_SUB]
+  uint16_t* sB = sA + (size_t)TC_DIGITS * mt * 128 * TG_SUB;     // [8 np x TG_SUB]
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t taddr_s;
+  __shared__ int sE[2 * TG_AMAX], sF[2 * TG_BMAX], sBadE[2 * TG_AMAX], sBadF[2 * TG_BMAX];
+  __shared__ const double2* colY[TG_BMAX];
+  __shared__ int ldY[TG_BMAX];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid < wy) {
+    colY[tid] = tid < ta.wy0 ? ta.Y0 + tid : ta.Y1 + (tid - ta.wy0);
+    ldY[tid] = tid < ta.wy0 ? ta.ldy0 : ta.ldy1;
+  }
+  // zero digits once: padding rows of A and B and B's zero plane are never rewritten
+  {
+    const size_t words = tg_smem_bytes(mt, np) / 16;
+    for (size_t e = tid; e < words; e += TG_THREADS) reinterpret_cast<uint4*>(tg_smem)[e] = make_uint4(0, 0, 0, 0);
+  }
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
+                 "r"(ta.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = taddr_s;
+  // this thread's accumulators: one M row, CP consecutive real columns of Y'
+  const int half = tid >> 7;                      // warps 0-3 / 4-7
+  const int tile = mt == 2 ? half : 0;            // M tile of this thread's TMEM lanes
+  const int CP = mt == 2 ? np : np / 2;           // real columns per thread (<= 32)
+  const int col0 = mt == 2 ? 0 : half * (np / 2);
+  const int mrow = tile * 128 + (warp & 3) * 32 + lane;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+  double acc[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) acc[q] = 0.0;
+  bool bad_row = false;
+  uint32_t bad_cols = 0;
+  const int nwin = (n + TG_WIN - 1) / TG_WIN;
+  const int W = wx + wy, R = TG_THREADS / W;
+  uint32_t parity = 0;
+  bool ok = true;
+  for (int win = blockIdx.x; win < nwin && ok; win += gridDim.x) {
+    const int r0 = win * TG_WIN, nr = min(TG_WIN, n - r0);
+    // pass 1: exponent bound of every real column over the window's rows
+    for (int c = tid; c < 2 * TG_AMAX; c += TG_THREADS) { sE[c] = TC_NOEXP; sBadE[c] = 0; }
+    if (tid < 2 * TG_BMAX) { sF[tid] = TC_NOEXP; sBadF[tid] = 0; }
+    __syncthreads();
+    if (tid < R * W) {
+      const int col = tid % W, rg = tid / W;
+      int tre = TC_NOEXP, tim = TC_NOEXP, bre = 0, bim = 0;
+      const double2* base = col < wx ? ta.X + col : colY[col - wx];
+      const size_t ld = col < wx ? (size_t)ta.ldx : (size_t)ldY[col - wx];
+      for (int r = rg; r < nr; r += R) {
+        const double2 v = base[(size_t)(r0 + r) * ld];
+        tre = max(tre, tc_top(v.x));
+        tim = max(tim, tc_top(v.y));
+        bre |= tc_nonfinite(v.x);
+        bim |= tc_nonfinite(v.y);
+      }
+      int* E = col < wx ? sE + 2 * col : sF + 2 * (col - wx);
+      int* Bf = col < wx ? sBadE + 2 * col : sBadF + 2 * (col - wx);
+      atomicMax(E, tre);
+      atomicMax(E + 1, tim);
+      if (bre) atomicOr(Bf, 1);
+      if (bim) atomicOr(Bf + 1, 1);
+    }
+    __syncthreads();
+    for (int sc = 0; sc < TG_WIN / TG_SUB && ok; ++sc) {
+      const int rs = r0 + sc * TG_SUB;
+      // A digits: task (group g of 8 rows, complex column j), 2 real columns of X'
+      for (int a = tid; a < 4 * wx; a += TG_THREADS) {
+        const int j = a % wx, g = a / wx;
+        double re[8], im[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int r = rs + 8 * g + u;
+          const double2 v = r < n ? ta.X[(size_t)r * ta.ldx + j] : make_double2(0.0, 0.0);
+          re[u] = v.x;
+          im[u] = v.y;
+        }
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          const int m = 2 * j + p, T = sE[m];
+          uint32_t wv[TC_DIGITS][4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float d0[TC_DIGITS], d1[TC_DIGITS];
+            tc_digits(p ? im[2 * q] : re[2 * q], T, d0);
+            tc_digits(p ? im[2 * q + 1] : re[2 * q + 1], T, d1);
+#pragma unroll
+            for (int d = 0; d < TC_DIGITS; ++d) wv[d][q] = tc_pack2(d0[d], d1[d]);
+          }
+          const int t = m >> 7, ml = m & 127;
+#pragma unroll
+          for (int d = 0; d < TC_DIGITS; ++d)
+            *reinterpret_cast<uint4*>(sA + ((size_t)(d * mt + t) * 128 * TG_SUB) + tc_off(ml, 8 * g, KC)) =
+                make_uint4(wv[d][0], wv[d][1], wv[d][2], wv[d][3]);
+        }
+      }
+      // B digits: task (group g, complex column l), planes stacked along N
+      for (int b = tid; b < 4 * wy; b += TG_THREADS) {
+        const int l = b % wy, g = b / wy;
+        double re[8], im[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int r = rs + 8 * g + u;
+          const double2 v = r < n ? colY[l][(size_t)r * ldY[l]] : make_double2(0.0, 0.0);
+          re[u] = v.x;
+          im[u] = v.y;
+        }
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          const int nn = 2 * l + p, T = sF[nn];
+          uint32_t wv[TC_DIGITS][4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float d0[TC_DIGITS], d1[TC_DIGITS];
+            tc_digits(p ? im[2 * q] : re[2 * q], T, d0);
+            tc_digits(p ? im[2 * q + 1] : re[2 * q + 1], T, d1);
+#pragma unroll
+            for (int d = 0; d < TC_DIGITS; ++d) wv[d][q] = tc_pack2(d0[d], d1[d]);
+          }
+#pragma unroll
+          for (int d = 0; d < TC_DIGITS; ++d)
+            *reinterpret_cast<uint4*>(sB + tc_off(d * np + nn, 8 * g, KC)) =
+                make_uint4(wv[d][0], wv[d][1], wv[d][2], wv[d][3]);
+        }
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+        for (int ks = 0; ks < TG_SUB / 16; ++ks)
+          for (int t = 0; t < mt; ++t)
+            for (int da = 0; da < TC_DIGITS; ++da) {
+              const uint64_t ad = umma_desc(a0 + (uint32_t)((da * mt + t) * 128 * TG_SUB * 2) + ks * 256, 128, KC * 128);
+              const int ntot = (TC_DIAG - da) * np;
+              for (int c0 = 0; c0 < ntot; c0 += 256) {
+                const int nc = min(256, ntot - c0);
+                const uint64_t bd = umma_desc(b0 + (uint32_t)(c0 >> 3) * (KC * 128) + ks * 256, 128, KC * 128);
+                umma_bf16(tmem + (uint32_t)(t * TC_DIAG * np + da * np + c0), ad, bd, umma_idesc_bf16(128, nc),
+                          (sc > 0 || ks > 0 || da > 0) ? 1 : 0);
+              }
+            }
+        umma_commit(&mbar);
+      }
+      bool done = false;
+      for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(&mbar, parity);
+      parity ^= 1;
+      if (!__syncthreads_and(done)) {
+        if (tid == 0) atomicExch(ta.err, 1);
+        ok = false;
+      }
+      tc_fence_after();
+    }
+    if (!ok) break;
+    // flush: every G entry of the window exactly, rounded once, into the FP64 accumulators
+    const bool vrow = mrow < 2 * wx;
+    if (vrow && sBadE[mrow]) bad_row = true;
+#pragma unroll
+    for (int g4 = 0; g4 < 8; ++g4) {
+      if (4 * g4 < CP) {
+        uint32_t dg[TC_DIAG][4];
+#pragma unroll
+        for (int d = 0; d < TC_DIAG; ++d)
+          tmem_ld4(tmem + lane_base + (uint32_t)(tile * TC_DIAG * np + d * np + col0 + 4 * g4), dg[d]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = 4 * g4 + u, nn = col0 + q;
+          if (!vrow || nn >= 2 * wy) continue;
+          if (sBadF[nn]) bad_cols |= 1u << q;
+          const long long hi = (long long)tc_f2i(dg[0][u]) * 16777216ll + (long long)tc_f2i(dg[1][u]) * 65536ll +
+                               (long long)tc_f2i(dg[2][u]) * 256ll + (long long)tc_f2i(dg[3][u]);
+          const long long lo = (long long)tc_f2i(dg[4][u]) * 16777216ll + (long long)tc_f2i(dg[5][u]) * 65536ll +
+                               (long long)tc_f2i(dg[6][u]) * 256ll + (long long)tc_f2i(dg[7][u]);
+          acc[q] += tc_round96(hi, lo, sE[mrow] + sF[nn] - 68);
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();  // the next window's first products overwrite the accumulators
+  }
+  // complex result from the four real products (rows 2j, 2j+1 are adjacent lanes)
+  const bool ev = (lane & 1) == 0;
+  const int j = mrow >> 1;
+  const bool pbad = __shfl_down_sync(0xffffffffu, (int)bad_row, 1) != 0;
+  const double qnan = __longlong_as_double(0x7FF8000000000000ll);
+#pragma unroll
+  for (int q = 0; q < 32; q += 2) {
+    const double o0 = __shfl_down_sync(0xffffffffu, acc[q], 1);
+    const double o1 = __shfl_down_sync(0xffffffffu, acc[q + 1], 1);
+    const int l = (col0 + q) >> 1;
+    if (ev && q < CP && j < wx && l < wy) {
+      double2 v = make_double2(acc[q] + o1, acc[q + 1] - o0);
+      if (bad_row || pbad || ((bad_cols >> q) & 3u)) v = make_double2(qnan, qnan);
+      ta.partial[(size_t)blockIdx.x * wx * wy + (size_t)j * wy + l] = v;
+    }
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ta.tmem_cols)
+                              : "memory");
+}
+
 }  // namespace gplhr

@@ -31,7 +31,8 @@ EXPORTED = ["gplhr_create", "gplhr_solve", "gplhr_start", "gplhr_iterate", "gplh
             "gplhr_profile_read", "gplhr_gram_noalloc", "gplhr_grad", "gplhr_solve_batched",
             "gplhr_iterate_batched", "gplhr_spmm_shape", "gplhr_set_deflation"]
 P_MODES = {"thick": 0, "lobpcg": 1, "none": 2}
-KCLASS = {"spmm": 0, "gram": 1, "combine": 2, "precond": 3, "chol": 4, "other": 5}
+KCLASS = {"spmm": 0, "gram": 1, "combine": 2, "precond": 3, "chol": 4, "other": 5, "gram_tc": 6,
+          "combine_tc": 7}
 
 
 class Csr(C.Structure):
@@ -253,7 +254,7 @@ def gplhr_precond_apply(ctx, X, Y):
                                      Y.stride(0)), ctx)
 
 
-GRAM_ARITH = {"fp64": 0, "fp32": 1, "exact32": 2}
+GRAM_ARITH = {"fp64": 0, "fp32": 1, "exact32": 2, "tensor": 3}
 
 
 def gplhr_combine(ctx, X, C, Y, beta: bool = False, arith: str = "auto"):

@@ -605,3 +605,85 @@ def test_variant_solve_with_locking(p_mode):
     want = ev[np.argsort(np.abs(ev - pr.sigma))[:pr.k]]
     for mu in want:
         assert np.min(np.abs(vec["lam"] - mu)) <= 1e-8 * abs(mu)
+
+
+# ------------------------------------------------------ Gram on the tensor cores (a9) --
+
+def _gram_window_bound(Xh, Yh, nwin_cta):
+    """Bound on |C - X^* Y| per real part for the tensor-core Gram: per 128-row window w
+    and real columns m of X', n of Y' the digit rounding and dropped pairs stay below
+    2^-53 (max_w|x'_m| sum_w|y'_n| + max_w|y'_n| sum_w|x'_m| + max_w|x'_m| max_w|y'_n|),
+    the window's rounding below u |G_w|; the FP64 sums over a CTA's windows and the
+    reduction over CTAs add (nwin_cta + 160) u sum_r |x'_rm||y'_rn|.  Re C and Im C each
+    add two real entries."""
+    n = Xh.shape[0]
+    u = 2.0 ** -53
+
+    def real(Z):
+        R = np.empty((Z.shape[0], 2 * Z.shape[1]))
+        R[:, 0::2], R[:, 1::2] = np.abs(Z.real), np.abs(Z.imag)
+        return R
+
+    Xr, Yr = real(Xh), real(Yh)
+    Bm = np.zeros((Xr.shape[1], Yr.shape[1]))
+    for r0 in range(0, n, 128):
+        xs, ys = Xr[r0:r0 + 128], Yr[r0:r0 + 128]
+        mx, my = xs.max(axis=0), ys.max(axis=0)
+        sx, sy = xs.sum(axis=0), ys.sum(axis=0)
+        Bm += 2 * u * (np.outer(mx, sy) + np.outer(sx, my) + np.outer(mx, my))
+    Bm += (nwin_cta + 160) * u * (Xr.T @ Yr)
+    # Re C(j,l) uses (2j,2l), (2j+1,2l+1); Im C uses (2j,2l+1), (2j+1,2l)
+    bre = Bm[0::2, 0::2] + Bm[1::2, 1::2]
+    bim = Bm[0::2, 1::2] + Bm[1::2, 0::2]
+    return bre, bim
+
+
+@pytest.mark.parametrize("n,wx,wy,self_", [(5000, 32, 32, False), (100003, 128, 16, False), (20000, 64, 32, False),
+                                           (2048, 24, 24, False), (30001, 24, 24, True)])
+def test_gram_tensor_matches_twice_precision(n, wx, wy, self_):
+    """C = X^* Y on the tensor cores (GPLHR_GRAM_TENSOR) against a twice-working-
+    precision product, with rows spread over 1e-30..1e30, zero rows and a zero column,
+    within the digit scheme's per-window bound."""
+    rng = np.random.default_rng(70 + wx + wy)
+    Xh = _rand_block(rng, n, wx) * np.exp(rng.uniform(-69, 69, size=n))[:, None]
+    Xh[::113] = 0.0
+    Xh[:, min(3, wx - 1)] = 0.0
+    Yh = Xh.copy() if self_ else _rand_block(rng, n, wy) * np.exp(rng.uniform(-5, 5, size=n))[:, None]
+    ref = _dot2_product(Xh.conj().T.copy(), Yh)
+    A = sp.identity(n, format="csr")
+    ctx = G.gplhr_create(A, None, 0.5, 16, 2)
+    try:
+        X, Y = _dev(Xh), (None if self_ else _dev(Yh))
+        C = torch.zeros((wx, wy), dtype=torch.complex128, device=DEV)
+        G.gplhr_gram(ctx, X, X if self_ else Y, C, "tensor")
+        got = _host(C)
+    finally:
+        G.gplhr_destroy(ctx)
+    nwin_cta = -(-(-(-n // 128)) // 152)
+    bre, bim = _gram_window_bound(Xh, Yh, nwin_cta)
+    u = 2.0 ** -53
+    ere = np.abs(got.real - ref.real) - u * np.abs(ref.real)
+    eim = np.abs(got.imag - ref.imag) - u * np.abs(ref.imag)
+    assert np.all(ere <= bre) and np.all(eim <= bim), (np.max(ere / np.maximum(bre, 1e-300)),
+                                                      np.max(eim / np.maximum(bim, 1e-300)))
+
+
+def test_gram_tensor_nonfinite():
+    rng = np.random.default_rng(9)
+    n, wx, wy = 4096, 32, 16
+    Xh, Yh = _rand_block(rng, n, wx), _rand_block(rng, n, wy)
+    Xh[700, 5] = np.nan
+    Yh[3000, 2] = np.inf
+    A = sp.identity(n, format="csr")
+    ctx = G.gplhr_create(A, None, 0.5, 16, 2)
+    try:
+        C = torch.zeros((wx, wy), dtype=torch.complex128, device=DEV)
+        G.gplhr_gram(ctx, _dev(Xh), _dev(Yh), C, "tensor")
+        got = _host(C)
+    finally:
+        G.gplhr_destroy(ctx)
+    bad = ~np.isfinite(got)
+    want = np.zeros_like(bad)
+    want[5, :] = True
+    want[:, 2] = True
+    assert np.array_equal(bad, want)
