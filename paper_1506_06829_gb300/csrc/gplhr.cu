@@ -580,11 +580,82 @@ gplhr_status gram_tc(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int
   return GPLHR_OK;
 }
 
+// Narrow FP64 Gram products on the tensor cores (tc.cuh, tc_gram_narrow_kernel): digit
+// planes stacked along M and N, one pipelined CTA per SM over 128-row windows.
+struct TnShape {
+  int mt, np, ts, cols;
+  size_t smem;
+};
+bool gram_tn_fits(const gplhr_ctx* ctx, int wx, int wy, bool self, TnShape* sh = nullptr) {
+  if (!ctx->tc || ctx->n < 2048 || wx < 1 || wy < 1 || wx > gplhr::TN_XMAX || wy > gplhr::TN_YMAX ||
+      (self ? wx : wx + wy) > 4 * gplhr::TN_TASKS)
+    return false;
+  TnShape t;
+  t.mt = (14 * wx + 127) / 128;
+  t.np = ((2 * wy + 15) / 16) * 16;
+  const int buf = t.mt * 7 * t.np;
+  if (buf > 512) return false;
+  t.ts = 2 * buf <= 512 ? 2 : 1;
+  t.cols = 32;
+  while (t.cols < t.ts * buf) t.cols <<= 1;
+  t.smem = gplhr::tn_smem_bytes(t.mt, t.np, wx, wy);
+  if (t.smem > kCombSmemMax) return false;
+  if ((size_t)std::min(ctx->num_sms, (ctx->n + gplhr::TN_WIN - 1) / gplhr::TN_WIN) * wx * wy > ctx->gram_part_elems)
+    return false;
+  if (sh) *sh = t;
+  return true;
+}
+
+gplhr_status gram_tn(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy1, double2* C, const int* skip,
+                     int nout_count, bool count, bool self, const TnShape& sh) {
+  gplhr::TcGramNArgs t{};
+  const int wy = wy0 + wy1;
+  t.n = ctx->n;
+  t.X = X.p;
+  t.ldx = X.ld;
+  t.wx = wx;
+  t.Y0 = Y0.p;
+  t.ldy0 = Y0.ld;
+  t.wy0 = wy0;
+  t.Y1 = Y1.p;
+  t.ldy1 = Y1.ld;
+  t.wy1 = wy1;
+  t.self = self ? 1 : 0;
+  t.partial = ctx->gram_part;
+  t.skip = skip;
+  t.err = ctx->d_diag + 2;
+  t.mt = sh.mt;
+  t.np = sh.np;
+  t.ts = sh.ts;
+  t.tmem_cols = sh.cols;
+  const int nwin = (ctx->n + gplhr::TN_WIN - 1) / gplhr::TN_WIN;
+  const int grid = std::min(ctx->num_sms, nwin);
+  const double by = 16.0 * ctx->n * (self ? wx : wx + wy);
+  const int ph = prof_begin(ctx, KC_GRAM_TC, count ? 8.0 * ctx->n * nout_count : 0.0, count ? by : 0.0, 2);
+  if ((self ? wx : wx + wy) <= 16)
+    gplhr::tc_gram_narrow_kernel<4><<<grid, gplhr::TN_THREADS, sh.smem, ctx->stream>>>(t);
+  else
+    gplhr::tc_gram_narrow_kernel<8><<<grid, gplhr::TN_THREADS, sh.smem, ctx->stream>>>(t);
+  CK(cudaGetLastError());
+  const int nout = wx * wy;
+  gplhr::gram_reduce_kernel<<<(nout + gplhr::GRED_WARPS - 1) / gplhr::GRED_WARPS, 32 * gplhr::GRED_WARPS, 0,
+                               ctx->stream>>>(grid, nout, wx, wy, 0, ctx->gram_part, C, skip);
+  prof_end(ctx, ph);
+  CK(cudaGetLastError());
+  return GPLHR_OK;
+}
+
 gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy1, double2* C,
                   const int* skip = nullptr, bool herm = false, bool count = true, bool fp32 = false,
                   int force_mode = -1) {
   const int mode = force_mode >= 0 ? force_mode : (fp32 ? 1 : (ctx->bulk32 ? 2 : 0));
   const int wy = wy0 + wy1;
+  const bool self = X.p == Y0.p && X.ld == Y0.ld && wy0 == wx && wy1 == 0;
+  TnShape tn;
+  if (mode == 0 && force_mode < 0 && gram_tn_fits(ctx, wx, wy, self, &tn)) {
+    const bool h = herm && self;
+    return gram_tn(ctx, X, wx, Y0, wy0, Y1, wy1, C, skip, h ? wx * (wx + 1) / 2 : wx * wy, count, self, tn);
+  }
   if (mode == 0 && force_mode < 0 && gram_tc_fits(ctx, wx, wy)) {
     // (a Hermitian request gets the full product; the algorithmic count stays the half)
     const bool h = herm && wy1 == 0 && wy0 == wx;
@@ -611,7 +682,6 @@ gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy
                                            (size_t)RG * G * acc * sizeof(double2))
                                 : std::max((size_t)gplhr::GRAM_ROWS * (wx + wy), (size_t)RG * G * acc) *
                                       sizeof(double2);
-  const bool self = X.p == Y0.p && wy1 == 0;
   const double by = 16.0 * ctx->n * (self ? wx : wx + wy);
   const int ph = prof_begin(ctx, KC_GRAM, count ? 8.0 * ctx->n * nout : 0.0, count ? by : 0.0, 2);
   switch (acc) {
@@ -636,7 +706,8 @@ struct In {
 };
 
 // The combination on the tensor cores (FP64 by integer digits, tc.cuh): one persistent
-// CTA per SM (more when shared and tensor memory allow), 128 rows per tile.
+// pipelined CTA per SM, 128 rows per tile; two digit stages and two accumulator buffers
+// where shared and tensor memory allow.
 gplhr_status combine_tc(gplhr_ctx* ctx, gplhr::CombArgs a, int wsum, int c, int c_store, bool beta_one,
                         bool count) {
   gplhr::TcCombArgs t{};
@@ -644,20 +715,24 @@ gplhr_status combine_tc(gplhr_ctx* ctx, gplhr::CombArgs a, int wsum, int c, int 
   t.a.upper = 0;
   t.kp = ((2 * wsum + 15) / 16) * 16;
   t.np = ((2 * c + 15) / 16) * 16;
+  t.ds = gplhr::tc_comb_smem_bytes(t.kp, t.np, 2) <= kCombSmemMax ? 2 : 1;
+  t.ts = 2 * gplhr::TC_DIAG * t.np <= 512 ? 2 : 1;
   t.tmem_cols = 32;
-  while (t.tmem_cols < gplhr::TC_DIAG * t.np) t.tmem_cols <<= 1;
+  while (t.tmem_cols < t.ts * gplhr::TC_DIAG * t.np) t.tmem_cols <<= 1;
   t.err = ctx->d_diag + 2;
-  const size_t smem = ((size_t)gplhr::TC_DIGITS * gplhr::TC_ROWS + (size_t)gplhr::TC_DIAG * t.np) * t.kp *
-                          sizeof(uint16_t) + 2 * t.np * sizeof(int);
-  // at most 4 per SM: the per-CTA norm partials are sized for 4 CTAs per SM
-  const int per_sm = std::max(1, std::min({(int)((227 * 1024) / (smem + 4096)), 512 / t.tmem_cols, 4}));
+  const size_t smem = gplhr::tc_comb_smem_bytes(t.kp, t.np, t.ds);
   const int ntiles = (ctx->n + gplhr::TC_ROWS - 1) / gplhr::TC_ROWS;
-  const int grid = std::min(ntiles, per_sm * ctx->num_sms);
+  const int grid = std::min(ntiles, ctx->num_sms);
   t.a.normpart = c_store < c ? ctx->norm_part : nullptr;
   const double by = 16.0 * ctx->n * (wsum + c_store * (beta_one ? 2.0 : 1.0));
   const int ph = prof_begin(ctx, KC_COMBINE_TC, count ? 8.0 * ctx->n * (double)wsum * c : 0.0, count ? by : 0.0,
                             c_store < c ? 2 : 1);
-  gplhr::tc_combine_kernel<<<grid, gplhr::TC_THREADS, smem, ctx->stream>>>(ctx->n, t);
+  switch (t.kp / 8) {
+    case 2: gplhr::tc_combine_kernel<2><<<grid, gplhr::TC_PIPE_THREADS, smem, ctx->stream>>>(ctx->n, t); break;
+    case 4: gplhr::tc_combine_kernel<4><<<grid, gplhr::TC_PIPE_THREADS, smem, ctx->stream>>>(ctx->n, t); break;
+    case 6: gplhr::tc_combine_kernel<6><<<grid, gplhr::TC_PIPE_THREADS, smem, ctx->stream>>>(ctx->n, t); break;
+    default: gplhr::tc_combine_kernel<8><<<grid, gplhr::TC_PIPE_THREADS, smem, ctx->stream>>>(ctx->n, t); break;
+  }
   CK(cudaGetLastError());
   if (c_store < c) {
     const int nc = c - c_store;
@@ -1994,9 +2069,14 @@ gplhr_status set_smem_limits(gplhr_ctx* ctx) {
   CK(cudaFuncSetAttribute(gplhr::block_jacobi_kernel<float, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           big));
   CK(cudaFuncSetAttribute(gplhr::invert_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  CK(cudaFuncSetAttribute(gplhr::tc_combine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::tc_combine_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::tc_combine_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::tc_combine_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::tc_combine_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)gplhr::tg_smem_bytes(2, 64)));
+  CK(cudaFuncSetAttribute(gplhr::tc_gram_narrow_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::tc_gram_narrow_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   return GPLHR_OK;
 }
 

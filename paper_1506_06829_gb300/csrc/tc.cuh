@@ -55,12 +55,16 @@ __device__ __forceinline__ void umma_commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
                : "memory");
 }
+// One test of the phase; a thread whose phase is not complete sleeps until it completes
+// or for at most TC_WAIT_NS (it does not spin and take issue slots from working warps).
+constexpr uint32_t TC_WAIT_NS = 20000;
+constexpr int TC_WAIT_TRIES = 1 << 16;  // at most ~1.3 s in all
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
   uint32_t done;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(done)
-      : "r"(smem_u32(mbar)), "r"(parity)
+      : "r"(smem_u32(mbar)), "r"(parity), "r"(TC_WAIT_NS)
       : "memory");
   return done != 0;
 }
@@ -135,8 +139,11 @@ __device__ __forceinline__ uint32_t tc_pack2(float lo, float hi) {
 }
 
 // 2^p (hi 2^32 + lo) for |hi|, |lo| < 2^48, rounded once to the nearest double (ties
-// to even), in integer arithmetic; a result below 2^-1022 takes a second rounding to the
-// subnormal grid.
+// to even); a result below 2^-1022 takes a second rounding to the subnormal grid.
+// The magnitude (< 2^81) is brought to at most 63 bits: exactly when it is below 2^63,
+// else shifted right by s with the dropped bits collapsed into a sticky lowest bit; the
+// integer-to-double conversion then rounds once (the sticky bit lies below its rounding
+// point), and 2^(s + p) is applied to the exponent field, exactly while it stays normal.
 __device__ __forceinline__ double tc_round96(long long hi, long long lo, int p) {
   long long zh = hi + (lo >> 32);  // value = zh 2^32 + zl, zl in [0, 2^32)
   uint32_t zl = (uint32_t)lo;
@@ -146,45 +153,81 @@ __device__ __forceinline__ double tc_round96(long long hi, long long lo, int p) 
     zl = 0u - zl;
   }
   const uint64_t uh = (uint64_t)zh;  // < 2^49
-  if (uh == 0 && zl == 0) return 0.0;
-  uint64_t mant;  // 53 bits, leading one at bit 52
-  int e;          // exponent of the leading one
-  if (uh < (1ull << 21)) {  // below 2^53: exact
-    const uint64_t v = (uh << 32) | zl;
-    const int lz = __clzll((long long)v);
-    mant = v << (lz - 11);
-    e = 63 - lz;
+  uint64_t W;
+  int s = 0;
+  if (uh < (1ull << 31)) {
+    W = (uh << 32) | zl;
   } else {
-    const int L = 64 - __clzll((long long)uh);  // 22..49 bits above zl
-    const int sh = L - 21;                       // 1..28 bits of zl dropped
-    mant = (uh << (32 - sh)) | (zl >> sh);
-    const uint32_t rem = zl << (32 - sh);        // the dropped bits, left-aligned
-    if (rem > 0x80000000u || (rem == 0x80000000u && (mant & 1))) ++mant;
-    e = L + 31;
-    if (mant >> 53) {
-      mant >>= 1;
-      ++e;
-    }
+    s = 33 - __clzll((long long)uh);  // 1..18: the magnitude has 63 + s bits
+    W = (uh << (32 - s)) | (zl >> s) | ((zl << (32 - s)) != 0u ? 1ull : 0ull);
   }
-  e += p;
-  const uint64_t sgn = neg ? (1ull << 63) : 0ull;
-  if (e > 1023) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull));
-  if (e >= -1022)
-    return __longlong_as_double((long long)(sgn | ((uint64_t)(e + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
-  const double d = scalbn((double)mant, e - 52);
-  return neg ? -d : d;
+  if (W == 0) return 0.0;
+  unsigned long long bits = (unsigned long long)__double_as_longlong(__ull2double_rn(W));
+  const int e = s + p;
+  const int nb = (int)(bits >> 52) + e;  // the result's biased exponent
+  if (nb >= 1 && nb <= 2046)
+    bits += (unsigned long long)(long long)e << 52;
+  else if (nb > 2046)
+    bits = 0x7FF0000000000000ull;
+  else
+    bits = (unsigned long long)__double_as_longlong(scalbn(__longlong_as_double((long long)bits), e));
+  return __longlong_as_double((long long)(bits | (neg ? (1ull << 63) : 0ull)));
+}
+
+// The eight digit diagonals D_0..D_7 of the combination (FP32 accumulators holding
+// integers of magnitude <= 7 2^20, K' <= 64) as Z = hi 2^32 + lo = sum_d D_d 256^(7 - d):
+// pairs first in 32 bits (|256 D_2k + D_2k+1| < 2^31), then two 48-bit halves.
+__device__ __forceinline__ void tc_diag_sum(const uint32_t (&D)[TC_DIAG], long long& hi, long long& lo) {
+  int P[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) P[k] = __float2int_rn(__uint_as_float(D[2 * k])) * 256 + __float2int_rn(__uint_as_float(D[2 * k + 1]));
+  hi = (long long)P[0] * 65536ll + (long long)P[1];
+  lo = (long long)P[2] * 65536ll + (long long)P[3];
 }
 
 // Exact integer value of an FP32 accumulator holding an integer of magnitude < 2^24.
 __device__ __forceinline__ int tc_f2i(uint32_t u) { return __float2int_rn(__uint_as_float(u)); }
 
+// Named barrier over the first `count` threads of the CTA (barrier 0 is __syncthreads),
+// with an AND vote: every participating thread gets the same answer.
+__device__ __forceinline__ bool bar_and(int id, int count, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.b32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(count)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
+}
+// Bounded wait for the phase of the given parity: false after the iteration limit, or
+// as soon as another role has raised *abort.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  for (int it = 0; it < TC_WAIT_TRIES; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+  }
+  return false;
+}
+
 struct TcCombArgs {
   CombArgs a;
   int kp;          // K' padded to a multiple of 16 (<= TC_KMAX)
   int np;          // N' padded to a multiple of 16 (<= TC_NMAX)
-  int tmem_cols;   // power of two >= max(32, TC_DIAG np)
-  int* err;        // set to 1 if a wait on the tensor core gave up
+  int ds;          // A digit stages in shared memory (1 or 2)
+  int ts;          // accumulator buffers in tensor memory (1 or 2)
+  int tmem_cols;   // power of two >= max(32, ts TC_DIAG np)
+  int* err;        // set to 1 if a wait gave up
 };
+
+__host__ __device__ constexpr size_t tc_comb_smem_bytes(int kp, int np, int ds) {
+  return (size_t)ds * TC_DIGITS * TC_ROWS * kp * 2 + (size_t)TC_DIAG * np * kp * 2;
+}
 
 __device__ __forceinline__ int tc_off(int row, int k, int KC) {  // element offset in a core-matrix tile
   return ((row >> 3) * KC + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
@@ -203,31 +246,54 @@ __device__ __forceinline__ double tc_cval(const CombArgs& a, int wsum, int kk, i
   return p == 0 ? (q == 0 ? cv.x : cv.y) : (q == 0 ? -cv.y : cv.x);
 }
 
-// One persistent CTA per (SM, slot); 128 rows per tile, thread (r, h) = (tid % 128,
-// tid / 128) loads and splits the row's k-chunks kc = h, h + 2, ... (8 reals each) and
-// writes the output column groups nb = 4 h, 4 h + 8, ...  Warp w reads tensor-memory
-// lanes 32 (w % 4) .. +31, which hold rows 32 (w % 4) .. +31 of the tile.
-__global__ void __launch_bounds__(TC_THREADS, 2) tc_combine_kernel(int n, TcCombArgs ta) {
+// The combination as a pipeline of two roles in one persistent CTA per SM, so that the
+// loads and digit splitting of one tile, the MMAs of the tile before and the epilogue of
+// the one before that run at the same time (tile i uses A stage i % ds and accumulator
+// buffer i % ts; mbarriers pass the stages and buffers between the roles):
+// * warps 0-7 (digits): thread (row, half) = (tid % 128, tid / 128) loads the row's
+//   k-chunks kc = half, half + 2, ... (4 complex values each); the two halves agree on
+//   the row's exponent bound (named barrier 1); once the stage is free the row's digits
+//   are written to it, 8 consecutive k of one digit per 16-byte store.  When all are
+//   written, thread 0 waits for the buffer to be free and issues the MMAs: plane da of
+//   X' against C' planes 0 .. 7 - da (stack rows 0 .. (8 - da) np) at accumulator
+//   column da np; the first MMA (ks = 0, da = 0, all 8 planes) initialises every
+//   diagonal; commits free the stage and fill the buffer;
+// * warps 8-15 (epilogue): warp 8 + 4 e + q reads tensor-memory lanes 32 q .. 32 q + 31
+//   (rows 32 q .. of the tile) and the column groups nb = 4 e, 4 e + 8, ...; it forms,
+//   rounds and stores those outputs, then frees the buffer.
+// 16 warps, so that every SM sub-partition holds 4 of them and each thread may use 128
+// registers.  The row exponent bounds and non-finite flags go through a ring of TC_RING
+// slots (a slot is rewritten only after its tile's buffer was freed: TC_RING >= ds + ts).
+// Every wait has an iteration limit; a role that gives up raises the abort flag, which
+// ends the other role's waits; thread 0 waits (bounded) for its last products, and the CTA
+// frees its tensor memory and returns with *err = 1.
+constexpr int TC_DWARPS = 8, TC_EWARPS = 8;
+constexpr int TC_PIPE_THREADS = (TC_DWARPS + TC_EWARPS) * 32;
+constexpr int TC_RING = 4;
+
+template <int KC>  // K' / 8 (2, 4, 6 or 8)
+__global__ void __launch_bounds__(TC_PIPE_THREADS, 1) tc_combine_kernel(int n, TcCombArgs ta) {
   const CombArgs& a = ta.a;
   if (a.skip && *a.skip == 0) return;
   extern __shared__ __align__(128) unsigned char tc_smem[];
-  const int kp = ta.kp, np = ta.np, KC = kp >> 3;
-  uint16_t* sA = reinterpret_cast<uint16_t*>(tc_smem);         // TC_DIGITS x 128 x kp
-  uint16_t* sB = sA + TC_DIGITS * TC_ROWS * kp;                // 8 np x kp: plane b, column n
-  int* sG = reinterpret_cast<int*>(sB + TC_DIAG * np * kp);    // at row b np + n; plane 7 zero
-  int* sBadC = sG + np;                                        // np non-finite flags
-  __shared__ __align__(8) uint64_t mbar;
+  constexpr int kp = 8 * KC;
+  const int np = ta.np, ds = ta.ds, ts = ta.ts;
+  uint16_t* sB = reinterpret_cast<uint16_t*>(tc_smem);        // 8 np x kp: plane b, column n at row b np + n
+  uint16_t* sA = sB + TC_DIAG * np * kp;                       // ds stages of TC_DIGITS x 128 x kp
+  __shared__ __align__(8) uint64_t bar_dempty[2], bar_tfull[2], bar_tempty[2], bar_row[TC_RING];
   __shared__ uint32_t taddr_s;
+  __shared__ volatile int abort_s;
   __shared__ double nsum[COMB_MAX_NORMS];
   __shared__ const double2* colp[TC_KMAX / 2];
   __shared__ int coll[TC_KMAX / 2];
-  __shared__ int sT[2][TC_ROWS];
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int rl = tid & (TC_ROWS - 1), h = tid >> 7;
+  __shared__ int sG[TC_NMAX], sBadC[TC_NMAX];
+  __shared__ int sX[2][2][TC_ROWS], sXb[2][2][TC_ROWS];       // exponent exchange between the halves
+  __shared__ int sRowT[TC_RING][TC_ROWS], sRowBad[TC_RING][TC_ROWS];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int wsum = 0;
   for (int t = 0; t < a.nin; ++t) wsum += a.in[t].w;
   const int nnorm = a.c - a.c_store;
-  for (int e = tid; e < nnorm; e += TC_THREADS) nsum[e] = 0.0;
+  for (int e = tid; e < nnorm; e += TC_PIPE_THREADS) nsum[e] = 0.0;
   if (tid < TC_KMAX / 2) {  // where input column j of the stacked row lives
     const double2* p = nullptr;
     int ld = 0;
@@ -254,8 +320,17 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_combine_kernel(int n, TcComb
     sG[tid] = G;
     sBadC[tid] = bad;
   }
+  if (tid == 0) {
+    abort_s = 0;
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bar_dempty[i], 1);
+      mbar_init(&bar_tfull[i], 1);
+      mbar_init(&bar_tempty[i], TC_EWARPS * 32);
+    }
+    for (int i = 0; i < TC_RING; ++i) mbar_init(&bar_row[i], TC_ROWS);
+  }
   __syncthreads();
-  for (int e = tid; e < kp * np; e += TC_THREADS) {
+  for (int e = tid; e < kp * np; e += TC_PIPE_THREADS) {
     const int nn = e / kp, kk = e - nn * kp;
     float dg[TC_DIGITS];
     tc_digits(tc_cval(a, wsum, kk, nn), sG[nn], dg);
@@ -264,7 +339,6 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_combine_kernel(int n, TcComb
       sB[tc_off(d * np + nn, kk, KC)] = (uint16_t)(__float_as_uint(dg[d]) >> 16);
     sB[tc_off(TC_DIGITS * np + nn, kk, KC)] = 0;
   }
-  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
                  "r"(ta.tmem_cols)
@@ -276,140 +350,201 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_combine_kernel(int n, TcComb
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = taddr_s;
-  const uint32_t a_slice = TC_ROWS * kp * 2;  // bytes
-  const uint32_t sA_addr = smem_u32(sA), sB_addr = smem_u32(sB);
+  const uint32_t a_slice = TC_ROWS * kp * 2;              // bytes per digit plane
+  const uint32_t a_stage = TC_DIGITS * a_slice;           // bytes per stage
   const int ntiles = (n + TC_ROWS - 1) / TC_ROWS;
-  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-  bool ok = true;
-  uint32_t parity = 0;
-  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, parity ^= 1) {
-    const int r = tile * TC_ROWS + rl;
-    const bool valid = r < n;
-    {  // this row of the CTA's next tile into L2 while this tile is processed
-      const int r2 = r + gridDim.x * TC_ROWS;
-      if (h == 0 && r2 < n)
-        for (int t = 0; t < a.nin; ++t)
-          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.in[t].X + (size_t)r2 * a.in[t].ldx),
-                       "r"((uint32_t)(a.in[t].w * 16))
-                       : "memory");
-    }
-    // this thread's k-chunks of the row: 4 complex values each, in registers
-    double xv[TC_KMAX / 2];
-    int T = TC_NOEXP, bad = 0;
-#pragma unroll
-    for (int i = 0; i < TC_KMAX / 16; ++i) {
-      const int kc = 2 * i + h;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = kc * 4 + u;
-        double2 v = make_double2(0.0, 0.0);
-        if (valid && kc < KC && j < wsum) v = colp[j][(size_t)r * coll[j]];
-        xv[8 * i + 2 * u] = v.x;
-        xv[8 * i + 2 * u + 1] = v.y;
-        T = max(T, max(tc_top(v.x), tc_top(v.y)));
-        bad |= tc_nonfinite(v.x) | tc_nonfinite(v.y);
+
+  if (warp < TC_DWARPS) {
+    // ------------------------------------------------------------ digits role --
+    const int rl = tid & (TC_ROWS - 1), h = tid >> 7;
+    const uint32_t sA_addr = smem_u32(sA), sB_addr = smem_u32(sB);
+    int it = 0, last_b = -1;
+    uint32_t last_v = 0;
+    bool mma_ok = true;  // thread 0: its last wait for a buffer succeeded
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+      const int s = it % ds;
+      const uint32_t u = (uint32_t)(it / ds);
+      const int r = tile * TC_ROWS + rl;
+      const bool valid = r < n;
+      if (h == 0) {  // into L2: this row of the next tile's inputs, this row's old outputs
+        const int r2 = r + gridDim.x * TC_ROWS;
+        if (r2 < n)
+          for (int t = 0; t < a.nin; ++t)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.in[t].X + (size_t)r2 * a.in[t].ldx),
+                         "r"((uint32_t)(a.in[t].w * 16))
+                         : "memory");
+        if (valid && a.beta_one) {
+          if (a.c_split > 0)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.Y + (size_t)r * a.ldy),
+                         "r"((uint32_t)(a.c_split * 16))
+                         : "memory");
+          if (a.c_store > a.c_split)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.Y2 + (size_t)r * a.ldy2),
+                         "r"((uint32_t)((a.c_store - a.c_split) * 16))
+                         : "memory");
+        }
       }
-    }
-    sT[h][rl] = T;
-    __syncthreads();
-    T = max(sT[0][rl], sT[1][rl]);
-    __syncthreads();
-    sT[h][rl] = bad;
-    // A operand: 8 consecutive k of one digit per 16-byte store
+      double xv[4 * KC];
+      int T = TC_NOEXP, bad = 0;
 #pragma unroll
-    for (int i = 0; i < TC_KMAX / 16; ++i) {
-      const int kc = 2 * i + h;
-      if (kc < KC) {
-        // two values at a time (few live registers, so the compiler can interleave)
-        uint32_t wv[TC_DIGITS][4];
+      for (int i = 0; i < KC / 2; ++i) {
+        const int kc = 2 * i + h;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float d0[TC_DIGITS], d1[TC_DIGITS];
-          tc_digits(xv[8 * i + 2 * q], T, d0);
-          tc_digits(xv[8 * i + 2 * q + 1], T, d1);
-#pragma unroll
-          for (int d = 0; d < TC_DIGITS; ++d) wv[d][q] = tc_pack2(d0[d], d1[d]);
+        for (int uu = 0; uu < 4; ++uu) {
+          const int j = kc * 4 + uu;
+          double2 v = make_double2(0.0, 0.0);
+          if (valid && j < wsum) v = colp[j][(size_t)r * coll[j]];
+          xv[8 * i + 2 * uu] = v.x;
+          xv[8 * i + 2 * uu + 1] = v.y;
+          T = max(T, max(tc_top(v.x), tc_top(v.y)));
+          bad |= tc_nonfinite(v.x) | tc_nonfinite(v.y);
         }
-#pragma unroll
-        for (int d = 0; d < TC_DIGITS; ++d)
-          *reinterpret_cast<uint4*>(sA + d * TC_ROWS * kp + tc_off(rl, kc * 8, KC)) =
-              make_uint4(wv[d][0], wv[d][1], wv[d][2], wv[d][3]);
       }
-    }
-    fence_async_smem();
-    __syncthreads();
-    bad = sT[0][rl] | sT[1][rl];
-    if (tid == 0) {
-      tc_fence_after();
-      // plane da of X' against C' planes 0 .. 7 - da (stack rows 0 .. (8 - da) np) at
-      // accumulator column da np; the first MMA (ks = 0, da = 0, all 8 planes)
-      // initialises every diagonal
-      for (int ks = 0; ks < kp / 16; ++ks)
-        for (int da = 0; da < TC_DIGITS; ++da) {
-          const uint64_t ad = umma_desc(sA_addr + da * a_slice + ks * 256, 128, KC * 128);
-          const int ntot = (TC_DIAG - da) * np;
-          for (int c0 = 0; c0 < ntot; c0 += 256) {
-            const int nc = min(256, ntot - c0);
-            const uint64_t bd = umma_desc(sB_addr + (uint32_t)(c0 >> 3) * (uint32_t)(KC * 128) + ks * 256, 128, KC * 128);
-            umma_bf16(tmem + (uint32_t)(da * np + c0), ad, bd, umma_idesc_bf16(TC_ROWS, nc), (ks > 0 || da > 0) ? 1 : 0);
-          }
+      sX[it & 1][h][rl] = T;
+      sXb[it & 1][h][rl] = bad;
+      // both halves' bounds, and the stage free (the same decision in every thread)
+      bool ok = bar_and(1, TC_DWARPS * 32, true);
+      T = max(sX[it & 1][0][rl], sX[it & 1][1][rl]);
+      bad = sXb[it & 1][0][rl] | sXb[it & 1][1][rl];
+      ok = bar_and(1, TC_DWARPS * 32, mma_ok && mbar_wait_bounded(&bar_dempty[s], (u & 1) ^ 1, &abort_s));
+      if (!ok) {
+        if (tid == 0) {
+          abort_s = 1;
+          atomicExch(ta.err, 1);
         }
-      umma_commit(&mbar);
-    }
-    // wait for the products (bounded)
-    bool done = false;
-    for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(&mbar, parity);
-    if (!__syncthreads_and(done)) {  // the same decision in every thread
-      if (tid == 0) atomicExch(ta.err, 1);
-      ok = false;
-      break;
-    }
-    tc_fence_after();
-    for (int nb = 4 * h; nb < np; nb += 8) {  // groups of 4 real columns, alternating halves
-      uint32_t acc[TC_DIAG][4];
+        break;
+      }
+      if (h == 0) {
+        const int slot = it % TC_RING;
+        sRowT[slot][rl] = T;
+        sRowBad[slot][rl] = bad;
+        mbar_arrive(&bar_row[slot]);
+      }
+      uint16_t* sAs = sA + (size_t)s * (a_stage / 2);
 #pragma unroll
-      for (int d = 0; d < TC_DIAG; ++d) tmem_ld4(tmem + lane_base + (uint32_t)(d * np + nb), acc[d]);
-      tmem_wait_ld();
-      if (!valid) continue;
+      for (int i = 0; i < KC / 2; ++i) {
+        const int kc = 2 * i + h;
+        {
+          uint32_t wv[TC_DIGITS][4];
 #pragma unroll
-      for (int u = 0; u < 4; u += 2) {
-        const int nn = nb + u, l = nn >> 1;
-        if (l >= a.c) continue;
-        double yv[2];
+          for (int q = 0; q < 4; ++q) {
+            float d0[TC_DIGITS], d1[TC_DIGITS];
+            tc_digits(xv[8 * i + 2 * q], T, d0);
+            tc_digits(xv[8 * i + 2 * q + 1], T, d1);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const long long hi = (long long)tc_f2i(acc[0][u + q]) * 16777216ll +
-                               (long long)tc_f2i(acc[1][u + q]) * 65536ll +
-                               (long long)tc_f2i(acc[2][u + q]) * 256ll + (long long)tc_f2i(acc[3][u + q]);
-          const long long lo = (long long)tc_f2i(acc[4][u + q]) * 16777216ll +
-                               (long long)tc_f2i(acc[5][u + q]) * 65536ll +
-                               (long long)tc_f2i(acc[6][u + q]) * 256ll + (long long)tc_f2i(acc[7][u + q]);
-          yv[q] = tc_round96(hi, lo, T + sG[nn + q] - 68);
-          if (bad || sBadC[nn + q]) yv[q] = __longlong_as_double(0x7FF8000000000000ll);
-        }
-        double2 y = make_double2(yv[0], yv[1]);
-        if (l < a.c_store) {
-          double2* dst = comb_out(a, r, l);
-          if (a.beta_one) {
-            const double2 o = *dst;
-            y.x += o.x;
-            y.y += o.y;
+            for (int d = 0; d < TC_DIGITS; ++d) wv[d][q] = tc_pack2(d0[d], d1[d]);
           }
-          *dst = y;
+#pragma unroll
+          for (int d = 0; d < TC_DIGITS; ++d)
+            *reinterpret_cast<uint4*>(sAs + d * TC_ROWS * kp + tc_off(rl, kc * 8, KC)) =
+                make_uint4(wv[d][0], wv[d][1], wv[d][2], wv[d][3]);
+        }
+      }
+      fence_async_smem();
+      bar_and(1, TC_DWARPS * 32, true);  // the stage is complete
+      if (tid == 0) {
+        const int b = it % ts;
+        const uint32_t v = (uint32_t)(it / ts);
+        mma_ok = mbar_wait_bounded(&bar_tempty[b], (v & 1) ^ 1, &abort_s);
+        if (mma_ok) {
+          tc_fence_after();
+          const uint32_t a0 = sA_addr + (uint32_t)s * a_stage;
+          const uint32_t d0 = tmem + (uint32_t)(b * TC_DIAG * np);
+          for (int ks = 0; ks < kp / 16; ++ks)
+            for (int da = 0; da < TC_DIGITS; ++da) {
+              const uint64_t ad = umma_desc(a0 + da * a_slice + ks * 256, 128, KC * 128);
+              const int ntot = (TC_DIAG - da) * np;
+              for (int c0 = 0; c0 < ntot; c0 += 256) {
+                const int nc = min(256, ntot - c0);
+                const uint64_t bd =
+                    umma_desc(sB_addr + (uint32_t)(c0 >> 3) * (uint32_t)(KC * 128) + ks * 256, 128, KC * 128);
+                umma_bf16(d0 + (uint32_t)(da * np + c0), ad, bd, umma_idesc_bf16(TC_ROWS, nc),
+                          (ks > 0 || da > 0) ? 1 : 0);
+              }
+            }
+          umma_commit(&bar_dempty[s]);
+          umma_commit(&bar_tfull[b]);
+          last_b = b;
+          last_v = v;
         } else {
-          atomicAdd(&nsum[l - a.c_store], y.x * y.x + y.y * y.y);
+          abort_s = 1;
+          atomicExch(ta.err, 1);
         }
       }
     }
-    tc_fence_before();
-    __syncthreads();
+    if (tid == 0 && last_b >= 0) {  // the last products complete before the tensor memory is freed
+      volatile int never = 0;
+      if (!mbar_wait_bounded(&bar_tfull[last_b], last_v & 1, &never)) atomicExch(ta.err, 1);
+    }
+  } else if (warp < TC_DWARPS + TC_EWARPS) {
+    // ---------------------------------------------------------- epilogue role --
+    const int ew = warp - TC_DWARPS, q4 = warp & 3, eh = ew >> 2;
+    const int row_in = q4 * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+      const int b = it % ts, slot = it % TC_RING;
+      const uint32_t v = (uint32_t)(it / ts);
+      bool ok = mbar_wait_bounded(&bar_row[slot], (uint32_t)(it / TC_RING) & 1, &abort_s) &&
+                mbar_wait_bounded(&bar_tfull[b], v & 1, &abort_s);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) {
+          abort_s = 1;
+          atomicExch(ta.err, 1);
+        }
+        break;
+      }
+      tc_fence_after();
+      const int r = tile * TC_ROWS + row_in;
+      const bool valid = r < n;
+      const int T = sRowT[slot][row_in], bad = sRowBad[slot][row_in];
+      const uint32_t tb = tmem + lane_base + (uint32_t)(b * TC_DIAG * np);
+      for (int nb = 4 * eh; nb < np; nb += 8) {  // groups of 4 real columns, alternating halves
+        uint32_t acc[TC_DIAG][4];
+#pragma unroll
+        for (int d = 0; d < TC_DIAG; ++d) tmem_ld4(tb + (uint32_t)(d * np + nb), acc[d]);
+        tmem_wait_ld();
+        if (!valid) continue;
+#pragma unroll
+        for (int uu = 0; uu < 4; uu += 2) {
+          const int nn = nb + uu, l = nn >> 1;
+          if (l >= a.c) continue;
+          double yv[2];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            uint32_t dg[TC_DIAG];
+#pragma unroll
+            for (int d = 0; d < TC_DIAG; ++d) dg[d] = acc[d][uu + q];
+            long long hi, lo;
+            tc_diag_sum(dg, hi, lo);
+            yv[q] = tc_round96(hi, lo, T + sG[nn + q] - 68);
+            if (bad || sBadC[nn + q]) yv[q] = __longlong_as_double(0x7FF8000000000000ll);
+          }
+          double2 y = make_double2(yv[0], yv[1]);
+          if (l < a.c_store) {
+            double2* dst = comb_out(a, r, l);
+            if (a.beta_one) {
+              const double2 o = *dst;
+              y.x += o.x;
+              y.y += o.y;
+            }
+            *dst = y;
+          } else {
+            atomicAdd(&nsum[l - a.c_store], y.x * y.x + y.y * y.y);
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&bar_tempty[b]);
+    }
   }
   __syncthreads();
   tc_fence_after();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ta.tmem_cols)
                               : "memory");
   if (a.normpart)
-    for (int e = tid; e < nnorm; e += TC_THREADS) a.normpart[(size_t)blockIdx.x * nnorm + e] = nsum[e];
+    for (int e = tid; e < nnorm; e += TC_PIPE_THREADS) a.normpart[(size_t)blockIdx.x * nnorm + e] = nsum[e];
 }
 
 // ------------------------------------------------ Gram products on the tensor cores --
@@ -612,7 +747,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tc_gram_kernel(TcGramArgs ta) {
         umma_commit(&mbar);
       }
       bool done = false;
-      for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(&mbar, parity);
+      for (int it = 0; it < TC_WAIT_TRIES && !done; ++it) done = mbar_try_wait(&mbar, parity);
       parity ^= 1;
       if (!__syncthreads_and(done)) {
         if (tid == 0) atomicExch(ta.err, 1);
@@ -662,6 +797,366 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tc_gram_kernel(TcGramArgs ta) {
       double2 v = make_double2(acc[q] + o1, acc[q + 1] - o0);
       if (bad_row || pbad || ((bad_cols >> q) & 3u)) v = make_double2(qnan, qnan);
       ta.partial[(size_t)blockIdx.x * wx * wy + (size_t)j * wy + l] = v;
+    }
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ta.tmem_cols)
+                              : "memory");
+}
+
+// ------------------------------------------- narrow Gram products, pipelined --
+// C = X^* [Y0 Y1] for narrow blocks (wx <= 24, wy <= 16), the digit scheme of the
+// combination with the contraction over the rows, laid out so that nothing is padded:
+// * A = the 7 digit planes of X' stacked along M: lane L = a (2 wx) + m holds plane a of
+//   real column m (mt = ceil(14 wx / 128) tiles of 128 lanes); B = the 7 planes of Y'
+//   stacked along N: row b np + n.  One MMA per 16-row K step and M tile forms every
+//   plane product P_ab(m, n) = sum_r X'_a(r, m) Y'_b(r, n) at lane (a, m), column b np + n.
+// * Rows go in windows of 128 with per-column exponent bounds (a first pass over the
+//   window; |P_ab| <= 128 2^14 = 2^21, exact in FP32).  After a window the diagonals
+//   D_d(m, n) = sum_{a+b=d} P_ab(m, n), d = 0..7, are summed across lanes in shared
+//   memory with integer additions (each P_ab taken exactly to int32), which are exact
+//   and so independent of their order; every G(m, n) is then formed and rounded once (tc_round96) and added to
+//   FP64 accumulators, and the CTA's partial C goes to partial[blockIdx.x][j wy + l].
+// * Pipeline: warps 0-7 (digits) take a window in two halves of 64 rows (one shared-
+//   memory stage each): task (row pair, complex column) = two loads, then the exponent
+//   pass (shared atomicMax over the window), then the digits of its half; thread 0
+//   issues the half's MMAs into accumulator buffer (window % ts).  Warps 8-11 (epilogue)
+//   read the buffer (warp 8 + q: lanes 32 q .. 32 q + 31 of every tile), free it, and
+//   form the window's products.  X^* X (self) splits X once and writes both operands.
+// Every wait has an iteration limit, as in the combination.
+constexpr int TN_WIN = 128;
+constexpr int TN_HALF = 64;
+constexpr int TN_DWARPS = 8, TN_EWARPS = 4;
+constexpr int TN_THREADS = (TN_DWARPS + TN_EWARPS) * 32;
+constexpr int TN_XMAX = 24, TN_YMAX = 16;
+constexpr int TN_TASKS = 8;                          // tasks per digits thread, at most: 64 W <= 256 TN_TASKS
+constexpr int TN_OUT = (TN_XMAX * TN_YMAX + TN_EWARPS * 32 - 1) / (TN_EWARPS * 32);
+constexpr int TN_RING = 4;
+
+struct TcGramNArgs {
+  int n;
+  const double2* X;
+  int ldx, wx;
+  const double2* Y0;
+  int ldy0, wy0;
+  const double2* Y1;
+  int ldy1, wy1;
+  int self;          // Y0 == X, wy1 == 0
+  double2* partial;  // [gridDim.x][wx * (wy0 + wy1)]
+  const int* skip;
+  int* err;
+  int mt;            // M tiles: 14 wx <= 128 mt (<= 3)
+  int np;            // 2 wy rounded up to 16 (16 or 32)
+  int ts;            // accumulator buffers (1 or 2)
+  int tmem_cols;     // power of two >= ts mt 7 np
+};
+
+// Shared memory: two stages of (A: mt x 128 lanes, B: 7 np rows) x 64 rows of bf16, then
+// the diagonal sums: 8 x 2 wx x (2 wy + 1) int32.
+__host__ __device__ constexpr size_t tn_stage_bytes(int mt, int np) {
+  return ((size_t)mt * 128 + 7 * (size_t)np) * TN_HALF * 2;
+}
+__host__ __device__ constexpr size_t tn_smem_bytes(int mt, int np, int wx, int wy) {
+  return 2 * tn_stage_bytes(mt, np) + (size_t)TC_DIAG * 2 * wx * (2 * wy + 1) * 4;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+// The digits thread's tasks of the window at row r0: t = tid + 256 i -> (row pair t / W,
+// complex column t % W of [X Y0 Y1]); rows beyond n read as zero.
+template <int NT>
+__device__ __forceinline__ void tn_load(const TcGramNArgs& ta, int r0, int tid, int W, double (&v)[NT][4]) {
+  const int wx = ta.wx;
+#pragma unroll
+  for (int i = 0; i < NT; ++i) {
+    const int t = tid + 256 * i, rp = t / W, j = t - rp * W;
+    double2 x0 = make_double2(0.0, 0.0), x1 = x0;
+    if (rp < TN_WIN / 2) {
+      const int r = r0 + 2 * rp;
+      const double2* base;
+      size_t ld;
+      if (j < wx) {
+        base = ta.X + j;
+        ld = (size_t)ta.ldx;
+      } else if (j - wx < ta.wy0) {
+        base = ta.Y0 + (j - wx);
+        ld = (size_t)ta.ldy0;
+      } else {
+        base = ta.Y1 + (j - wx - ta.wy0);
+        ld = (size_t)ta.ldy1;
+      }
+      if (r < ta.n) x0 = base[(size_t)r * ld];
+      if (r + 1 < ta.n) x1 = base[(size_t)(r + 1) * ld];
+    }
+    v[i][0] = x0.x;
+    v[i][1] = x1.x;
+    v[i][2] = x0.y;
+    v[i][3] = x1.y;
+  }
+}
+
+template <int NT>  // tasks per digits thread (4: W <= 16 loaded columns, 8: W <= 32)
+__global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNArgs ta) {
+  if (ta.skip && *ta.skip == 0) return;
+  extern __shared__ __align__(1024) unsigned char tn_smem[];
+  const int n = ta.n, wx = ta.wx, wy = ta.wy0 + ta.wy1, mt = ta.mt, np = ta.np, ts = ta.ts;
+  const int W = ta.self ? wx : wx + wy;              // complex columns loaded per row
+  const int MX = 2 * wx, NY = 2 * wy, SP = NY + 1;   // real columns; diagonal-sum row stride
+  const size_t stage = tn_stage_bytes(mt, np);
+  uint16_t* sA0 = reinterpret_cast<uint16_t*>(tn_smem);                       // stage h: + h stage
+  int* sD = reinterpret_cast<int*>(tn_smem + 2 * stage);                      // [8][MX][SP]
+  __shared__ __align__(8) uint64_t bar_dempty[2], bar_tfull[2], bar_tempty[2], bar_exp[TN_RING];
+  __shared__ uint32_t taddr_s;
+  __shared__ volatile int abort_s;
+  __shared__ int sE[TN_RING][2 * (TN_XMAX + TN_YMAX)], sBad[TN_RING][2 * (TN_XMAX + TN_YMAX)];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  {  // zero the stages (padding lanes and rows stay zero) and the diagonal sums
+    const size_t words = tn_smem_bytes(mt, np, wx, wy) / 4;
+    for (size_t e = tid; e < words; e += TN_THREADS) reinterpret_cast<uint32_t*>(tn_smem)[e] = 0u;
+  }
+  if (tid == 0) {
+    abort_s = 0;
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bar_dempty[i], 1);
+      mbar_init(&bar_tfull[i], 1);
+      mbar_init(&bar_tempty[i], TN_EWARPS * 32);
+    }
+    for (int i = 0; i < TN_RING; ++i) mbar_init(&bar_exp[i], TN_DWARPS * 32);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
+                 "r"(ta.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = taddr_s;
+  const int nwin = (n + TN_WIN - 1) / TN_WIN;
+  const int bufcols = mt * 7 * np;
+  const int ncol = ta.self ? MX : MX + NY;  // real columns with an exponent (Y' after X')
+
+  if (warp < TN_DWARPS) {
+    // ------------------------------------------------------------ digits role --
+    const uint32_t sbase = smem_u32(tn_smem);
+    const uint32_t idesc = umma_idesc_bf16(128, 7 * np);
+    int it = 0, last_b = -1;
+    uint32_t last_v = 0;
+    bool mma_ok = true;
+    constexpr bool PF = NT <= 4;  // the next window's values are loaded one window ahead
+    double v[NT][4], vn[PF ? NT : 1][4];
+    for (int win = blockIdx.x; win < nwin; win += gridDim.x, ++it) {
+      const int slot = it % TN_RING;
+      if constexpr (PF) {
+        if (it == 0)
+          tn_load<NT>(ta, win * TN_WIN, tid, W, v);
+        else
+#pragma unroll
+          for (int i = 0; i < NT; ++i)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[i][c] = vn[i][c];
+        if (win + (int)gridDim.x < nwin) tn_load<NT>(ta, (win + gridDim.x) * TN_WIN, tid, W, vn);
+      } else {
+        tn_load<NT>(ta, win * TN_WIN, tid, W, v);
+      }
+      // the first stage free (the previous window's first-half products done): the
+      // exponent slot of this window is then free too (its epilogue is four windows back)
+      bool ok = bar_and(1, TN_DWARPS * 32, mma_ok && mbar_wait_bounded(&bar_dempty[0], (it & 1) ^ 1, &abort_s));
+      if (!ok) {
+        if (tid == 0) {
+          abort_s = 1;
+          atomicExch(ta.err, 1);
+        }
+        break;
+      }
+      for (int c = tid; c < ncol; c += TN_DWARPS * 32) {
+        sE[slot][c] = TC_NOEXP;
+        sBad[slot][c] = 0;
+      }
+      bar_and(1, TN_DWARPS * 32, true);
+#pragma unroll
+      for (int i = 0; i < NT; ++i) {
+        const int t = tid + 256 * i, rp = t / W, j = t - rp * W;
+        if (rp < TN_WIN / 2) {
+          const int c = (j < wx ? 2 * j : MX + 2 * (j - wx));  // real columns c (Re), c + 1 (Im)
+          const int tre = max(tc_top(v[i][0]), tc_top(v[i][1])), tim = max(tc_top(v[i][2]), tc_top(v[i][3]));
+          if (tre > TC_NOEXP) atomicMax(&sE[slot][c], tre);
+          if (tim > TC_NOEXP) atomicMax(&sE[slot][c + 1], tim);
+          if (tc_nonfinite(v[i][0]) | tc_nonfinite(v[i][1])) sBad[slot][c] = 1;
+          if (tc_nonfinite(v[i][2]) | tc_nonfinite(v[i][3])) sBad[slot][c + 1] = 1;
+        }
+      }
+      bar_and(1, TN_DWARPS * 32, true);
+      mbar_arrive(&bar_exp[slot]);
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1) {
+          ok = bar_and(1, TN_DWARPS * 32, mma_ok && mbar_wait_bounded(&bar_dempty[1], (it & 1) ^ 1, &abort_s));
+          if (!ok) break;
+        }
+        uint16_t* sA = sA0 + (size_t)h * (stage / 2);
+        uint16_t* sB = sA + (size_t)mt * 128 * TN_HALF;
+#pragma unroll
+        for (int i = 0; i < NT; ++i) {
+          const int t = tid + 256 * i, rp = t / W, j = t - rp * W;
+          if (rp < TN_WIN / 2 && (rp >> 5) == h) {
+            const int kk = 2 * (rp & 31);  // row within the half (even)
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {  // Re, Im
+              const int c = (j < wx ? 2 * j : MX + 2 * (j - wx)) + p;
+              float d0[TC_DIGITS], d1[TC_DIGITS];
+              const int T = sE[slot][c];
+              tc_digits(v[i][2 * p], T, d0);
+              tc_digits(v[i][2 * p + 1], T, d1);
+              if (j < wx) {
+#pragma unroll
+                for (int a = 0; a < TC_DIGITS; ++a) {
+                  const int L = a * MX + c;
+                  *reinterpret_cast<uint32_t*>(sA + (size_t)(L >> 7) * 128 * TN_HALF + tc_off(L & 127, kk, 8)) =
+                      tc_pack2(d0[a], d1[a]);
+                }
+              }
+              if (j >= wx || ta.self) {
+                const int nn = j < wx ? c : c - MX;
+#pragma unroll
+                for (int b = 0; b < TC_DIGITS; ++b)
+                  *reinterpret_cast<uint32_t*>(sB + tc_off(b * np + nn, kk, 8)) = tc_pack2(d0[b], d1[b]);
+              }
+            }
+          }
+        }
+        fence_async_smem();
+        bar_and(1, TN_DWARPS * 32, true);
+        if (tid == 0) {
+          const int b = it % ts;
+          const uint32_t vv = (uint32_t)(it / ts);
+          if (h == 0) mma_ok = mbar_wait_bounded(&bar_tempty[b], (vv & 1) ^ 1, &abort_s);
+          if (mma_ok) {
+            tc_fence_after();
+            const uint32_t a0 = sbase + (uint32_t)(h * stage);
+            const uint32_t b0 = a0 + (uint32_t)(mt * 128 * TN_HALF * 2);
+            for (int ks = 0; ks < TN_HALF / 16; ++ks)
+              for (int t = 0; t < mt; ++t)
+                umma_bf16(tmem + (uint32_t)(b * bufcols + t * 7 * np),
+                          umma_desc(a0 + (uint32_t)(t * 128 * TN_HALF * 2) + ks * 256, 128, 8 * 128),
+                          umma_desc(b0 + ks * 256, 128, 8 * 128), idesc, (h > 0 || ks > 0) ? 1 : 0);
+            umma_commit(&bar_dempty[h]);
+            if (h == 1) {
+              umma_commit(&bar_tfull[b]);
+              last_b = b;
+              last_v = vv;
+            }
+          } else {
+            abort_s = 1;
+            atomicExch(ta.err, 1);
+          }
+        }
+      }
+      if (!ok) {
+        if (tid == 0) {
+          abort_s = 1;
+          atomicExch(ta.err, 1);
+        }
+        break;
+      }
+    }
+    if (tid == 0 && last_b >= 0) {
+      volatile int never = 0;
+      if (!mbar_wait_bounded(&bar_tfull[last_b], last_v & 1, &never)) atomicExch(ta.err, 1);
+    }
+  } else {
+    // ---------------------------------------------------------- epilogue role --
+    const int etid = tid - TN_DWARPS * 32, q4 = warp & 3;
+    const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
+    double acc[TN_OUT][4];
+    uint32_t badmask = 0;
+#pragma unroll
+    for (int i = 0; i < TN_OUT; ++i)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][q] = 0.0;
+    int it = 0;
+    for (int win = blockIdx.x; win < nwin; win += gridDim.x, ++it) {
+      const int b = it % ts, slot = it % TN_RING;
+      const uint32_t vv = (uint32_t)(it / ts);
+      bool ok = mbar_wait_bounded(&bar_exp[slot], (uint32_t)(it / TN_RING) & 1, &abort_s) &&
+                mbar_wait_bounded(&bar_tfull[b], vv & 1, &abort_s);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) {
+          abort_s = 1;
+          atomicExch(ta.err, 1);
+        }
+        break;
+      }
+      tc_fence_after();
+      // plane products -> diagonal sums (exact integer additions)
+      for (int t = 0; t < mt; ++t) {
+        const int L = t * 128 + q4 * 32 + lane, a = L / MX, m = L - a * MX;
+        const bool vl = a < TC_DIGITS;
+        for (int bp = 0; bp < TC_DIGITS; ++bp) {
+          for (int n0 = 0; n0 < np; n0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(tmem + lane_base + (uint32_t)(b * bufcols + t * 7 * np + bp * np + n0), r);
+            tmem_wait_ld();
+            if (vl && a + bp < TC_DIAG) {
+              int* dst = sD + ((size_t)(a + bp) * MX + m) * SP + n0;
+              // |P_ab| <= 2^21: 1.5 2^23 + P is exact and its low bits are P + 2^22
+#pragma unroll
+              for (int u = 0; u < 16; ++u)
+                if (n0 + u < NY) atomicAdd(dst + u, __float_as_int(__uint_as_float(r[u]) + 12582912.0f) - 0x4B400000);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&bar_tempty[b]);
+      bar_and(2, TN_EWARPS * 32, true);
+      // this thread's outputs: every G(m, n) of the window, rounded once, into FP64
+#pragma unroll
+      for (int i = 0; i < TN_OUT; ++i) {
+        const int o = etid + TN_EWARPS * 32 * i;
+        if (o < wx * wy) {
+          const int j = o / wy, l = o - j * wy;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int m = 2 * j + (q >> 1), nn = 2 * l + (q & 1);
+            const int cy = ta.self ? nn : MX + nn;
+            int* src = sD + (size_t)m * SP + nn;
+            long long hi = 0, lo = 0;
+#pragma unroll
+            for (int d = 0; d < TC_DIAG; ++d) {
+              const long long Dd = (long long)src[(size_t)d * MX * SP];
+              src[(size_t)d * MX * SP] = 0;
+              if (d < 4)
+                hi += Dd << (8 * (3 - d));
+              else
+                lo += Dd << (8 * (7 - d));
+            }
+            acc[i][q] += tc_round96(hi, lo, sE[slot][m] + sE[slot][cy] - 68);
+            if (sBad[slot][m] | sBad[slot][cy]) badmask |= 1u << (4 * i + q);
+          }
+        }
+      }
+      bar_and(2, TN_EWARPS * 32, true);  // the sums are zero again
+    }
+    // G(2j, 2l) = Re x Re, (2j, 2l+1) = Re x Im, (2j+1, 2l) = Im x Re, (2j+1, 2l+1) = Im x Im
+#pragma unroll
+    for (int i = 0; i < TN_OUT; ++i) {
+      const int o = etid + TN_EWARPS * 32 * i;
+      if (o < wx * wy) {
+        double2 cz = make_double2(acc[i][0] + acc[i][3], acc[i][1] - acc[i][2]);
+        if ((badmask >> (4 * i)) & 0xFu) cz = make_double2(__longlong_as_double(0x7FF8000000000000ll),
+                                                           __longlong_as_double(0x7FF8000000000000ll));
+        ta.partial[(size_t)blockIdx.x * wx * wy + o] = cz;
+      }
     }
   }
   __syncthreads();

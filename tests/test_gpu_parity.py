@@ -638,12 +638,18 @@ def _gram_window_bound(Xh, Yh, nwin_cta):
     return bre, bim
 
 
-@pytest.mark.parametrize("n,wx,wy,self_", [(5000, 32, 32, False), (100003, 128, 16, False), (20000, 64, 32, False),
-                                           (2048, 24, 24, False), (30001, 24, 24, True)])
+@pytest.mark.parametrize("n,wx,wy,self_", [
+    # wide products (tc_gram_kernel)
+    (5000, 32, 32, False), (100003, 128, 16, False), (20000, 64, 32, False), (2048, 24, 24, False),
+    (30001, 24, 24, True),
+    # narrow products (tc_gram_narrow_kernel: planes stacked along M and N)
+    (4096, 8, 8, False), (100003, 8, 8, True), (20000, 24, 8, False), (30001, 16, 16, False),
+    (2048, 3, 5, False), (9000, 1, 1, True), (7001, 24, 1, False), (12345, 5, 16, False), (65536, 24, 24, True)])
 def test_gram_tensor_matches_twice_precision(n, wx, wy, self_):
     """C = X^* Y on the tensor cores (GPLHR_GRAM_TENSOR) against a twice-working-
     precision product, with rows spread over 1e-30..1e30, zero rows and a zero column,
-    within the digit scheme's per-window bound."""
+    within the digit scheme's per-window bound; wide and narrow shapes, ragged last
+    windows, self products."""
     rng = np.random.default_rng(70 + wx + wy)
     Xh = _rand_block(rng, n, wx) * np.exp(rng.uniform(-69, 69, size=n))[:, None]
     Xh[::113] = 0.0
@@ -668,22 +674,27 @@ def test_gram_tensor_matches_twice_precision(n, wx, wy, self_):
                                                       np.max(eim / np.maximum(bim, 1e-300)))
 
 
-def test_gram_tensor_nonfinite():
+@pytest.mark.parametrize("wx,wy,self_", [(32, 16, False), (8, 8, False), (12, 12, True)])
+def test_gram_tensor_nonfinite(wx, wy, self_):
+    """A NaN in X (an Inf in Y) makes exactly its row (column) of C NaN."""
     rng = np.random.default_rng(9)
-    n, wx, wy = 4096, 32, 16
-    Xh, Yh = _rand_block(rng, n, wx), _rand_block(rng, n, wy)
+    n = 4096
+    Xh = _rand_block(rng, n, wx)
+    Yh = Xh if self_ else _rand_block(rng, n, wy)
     Xh[700, 5] = np.nan
-    Yh[3000, 2] = np.inf
+    if not self_:
+        Yh[3000, 2] = np.inf
     A = sp.identity(n, format="csr")
     ctx = G.gplhr_create(A, None, 0.5, 16, 2)
     try:
         C = torch.zeros((wx, wy), dtype=torch.complex128, device=DEV)
-        G.gplhr_gram(ctx, _dev(Xh), _dev(Yh), C, "tensor")
+        X = _dev(Xh)
+        G.gplhr_gram(ctx, X, X if self_ else _dev(Yh), C, "tensor")
         got = _host(C)
     finally:
         G.gplhr_destroy(ctx)
     bad = ~np.isfinite(got)
     want = np.zeros_like(bad)
     want[5, :] = True
-    want[:, 2] = True
+    want[:, 5 if self_ else 2] = True
     assert np.array_equal(bad, want)
