@@ -606,8 +606,9 @@ bool gram_tn_fits(const gplhr_ctx* ctx, int wx, int wy, bool self, TnShape* sh =
   return true;
 }
 
+// trans: X and Y0 were swapped by the caller (C = (Y0^* X)^*), the reduction writes C.
 gplhr_status gram_tn(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy1, double2* C, const int* skip,
-                     int nout_count, bool count, bool self, const TnShape& sh) {
+                     int nout_count, bool count, bool self, const TnShape& sh, bool trans = false) {
   gplhr::TcGramNArgs t{};
   const int wy = wy0 + wy1;
   t.n = ctx->n;
@@ -639,7 +640,7 @@ gplhr_status gram_tn(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int
   CK(cudaGetLastError());
   const int nout = wx * wy;
   gplhr::gram_reduce_kernel<<<(nout + gplhr::GRED_WARPS - 1) / gplhr::GRED_WARPS, 32 * gplhr::GRED_WARPS, 0,
-                               ctx->stream>>>(grid, nout, wx, wy, 0, ctx->gram_part, C, skip);
+                               ctx->stream>>>(grid, nout, wx, wy, trans ? 2 : 0, ctx->gram_part, C, skip);
   prof_end(ctx, ph);
   CK(cudaGetLastError());
   return GPLHR_OK;
@@ -656,6 +657,8 @@ gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy
     const bool h = herm && self;
     return gram_tn(ctx, X, wx, Y0, wy0, Y1, wy1, C, skip, h ? wx * (wx + 1) / 2 : wx * wy, count, self, tn);
   }
+  if (mode == 0 && force_mode < 0 && wy1 == 0 && !self && gram_tn_fits(ctx, wy0, wx, false, &tn))
+    return gram_tn(ctx, Y0, wy0, X, wx, Blk{nullptr, 0}, 0, C, skip, wx * wy, count, false, tn, true);
   if (mode == 0 && force_mode < 0 && gram_tc_fits(ctx, wx, wy)) {
     // (a Hermitian request gets the full product; the algorithmic count stays the half)
     const bool h = herm && wy1 == 0 && wy0 == wx;

@@ -471,6 +471,11 @@ __global__ void gram_reduce_kernel(int nchunk, int nout, int wx, int wy, int her
   for (int b = lane; b < nchunk; b += 32) s = cadd(s, partial[(size_t)b * nout + o]);
   for (int off = 16; off > 0; off >>= 1) s = cadd(s, shfl_xor2(s, off));
   if (lane == 0) {
+    if (herm == 2) {  // the partials hold the transposed product: C(j, i) = conj(partial (i, j))
+      const int i = o / wy, j = o - i * wy;
+      C[j * wx + i] = make_double2(s.x, -s.y);
+      return;
+    }
     int i, j;
     gram_index(o, wx, wy, herm, i, j);
     C[i * wy + j] = s;

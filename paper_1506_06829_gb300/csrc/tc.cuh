@@ -820,15 +820,17 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tc_gram_kernel(TcGramArgs ta) {
 //   FP64 accumulators, and the CTA's partial C goes to partial[blockIdx.x][j wy + l].
 // * Pipeline: warps 0-7 (digits) take a window in two halves of 64 rows (one shared-
 //   memory stage each): task (row pair, complex column) = two loads, then the exponent
-//   pass (shared atomicMax over the window), then the digits of its half; thread 0
-//   issues the half's MMAs into accumulator buffer (window % ts).  Warps 8-11 (epilogue)
-//   read the buffer (warp 8 + q: lanes 32 q .. 32 q + 31 of every tile), free it, and
-//   form the window's products.  X^* X (self) splits X once and writes both operands.
+//   pass (shared atomicMax over the window), then the digits of its half, and the half
+//   is marked full.  Warp 12 (one thread) issues each full half's MMAs into accumulator
+//   buffer (window % ts), so that the digit warps never wait for the issue.  Warps 8-11
+//   (epilogue) read the buffer (warp 8 + q: lanes 32 q .. 32 q + 31 of every tile), free
+//   it, and form the window's products.  X^* X (self) splits X once and writes both
+//   operands.  13 warps: at most 4 per SM sub-partition, 128 registers per thread.
 // Every wait has an iteration limit, as in the combination.
 constexpr int TN_WIN = 128;
 constexpr int TN_HALF = 64;
 constexpr int TN_DWARPS = 8, TN_EWARPS = 4;
-constexpr int TN_THREADS = (TN_DWARPS + TN_EWARPS) * 32;
+constexpr int TN_THREADS = (TN_DWARPS + TN_EWARPS + 1) * 32;
 constexpr int TN_XMAX = 24, TN_YMAX = 16;
 constexpr int TN_TASKS = 8;                          // tasks per digits thread, at most: 64 W <= 256 TN_TASKS
 constexpr int TN_OUT = (TN_XMAX * TN_YMAX + TN_EWARPS * 32 - 1) / (TN_EWARPS * 32);
@@ -869,36 +871,44 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr));
 }
 
+// Rows r, r + 1 of complex column j of [X Y0 Y1] as (Re r, Re r+1, Im r, Im r+1); rows
+// beyond n read as zero.
+__device__ __forceinline__ void tn_load1(const TcGramNArgs& ta, int r, int j, double (&v)[4]) {
+  const int wx = ta.wx;
+  const double2* base;
+  size_t ld;
+  if (j < wx) {
+    base = ta.X + j;
+    ld = (size_t)ta.ldx;
+  } else if (j - wx < ta.wy0) {
+    base = ta.Y0 + (j - wx);
+    ld = (size_t)ta.ldy0;
+  } else {
+    base = ta.Y1 + (j - wx - ta.wy0);
+    ld = (size_t)ta.ldy1;
+  }
+  double2 x0 = make_double2(0.0, 0.0), x1 = x0;
+  if (r < ta.n) x0 = base[(size_t)r * ld];
+  if (r + 1 < ta.n) x1 = base[(size_t)(r + 1) * ld];
+  v[0] = x0.x;
+  v[1] = x1.x;
+  v[2] = x0.y;
+  v[3] = x1.y;
+}
+
 // The digits thread's tasks of the window at row r0: t = tid + 256 i -> (row pair t / W,
-// complex column t % W of [X Y0 Y1]); rows beyond n read as zero.
+// complex column t % W).
 template <int NT>
 __device__ __forceinline__ void tn_load(const TcGramNArgs& ta, int r0, int tid, int W, double (&v)[NT][4]) {
-  const int wx = ta.wx;
 #pragma unroll
   for (int i = 0; i < NT; ++i) {
     const int t = tid + 256 * i, rp = t / W, j = t - rp * W;
-    double2 x0 = make_double2(0.0, 0.0), x1 = x0;
     if (rp < TN_WIN / 2) {
-      const int r = r0 + 2 * rp;
-      const double2* base;
-      size_t ld;
-      if (j < wx) {
-        base = ta.X + j;
-        ld = (size_t)ta.ldx;
-      } else if (j - wx < ta.wy0) {
-        base = ta.Y0 + (j - wx);
-        ld = (size_t)ta.ldy0;
-      } else {
-        base = ta.Y1 + (j - wx - ta.wy0);
-        ld = (size_t)ta.ldy1;
-      }
-      if (r < ta.n) x0 = base[(size_t)r * ld];
-      if (r + 1 < ta.n) x1 = base[(size_t)(r + 1) * ld];
+      tn_load1(ta, r0 + 2 * rp, j, v[i]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[i][c] = 0.0;
     }
-    v[i][0] = x0.x;
-    v[i][1] = x1.x;
-    v[i][2] = x0.y;
-    v[i][3] = x1.y;
   }
 }
 
@@ -912,7 +922,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
   const size_t stage = tn_stage_bytes(mt, np);
   uint16_t* sA0 = reinterpret_cast<uint16_t*>(tn_smem);                       // stage h: + h stage
   int* sD = reinterpret_cast<int*>(tn_smem + 2 * stage);                      // [8][MX][SP]
-  __shared__ __align__(8) uint64_t bar_dempty[2], bar_tfull[2], bar_tempty[2], bar_exp[TN_RING];
+  __shared__ __align__(8) uint64_t bar_dfull[2], bar_dempty[2], bar_tfull[2], bar_tempty[2], bar_exp[TN_RING];
   __shared__ uint32_t taddr_s;
   __shared__ volatile int abort_s;
   __shared__ int sE[TN_RING][2 * (TN_XMAX + TN_YMAX)], sBad[TN_RING][2 * (TN_XMAX + TN_YMAX)];
@@ -924,6 +934,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
   if (tid == 0) {
     abort_s = 0;
     for (int i = 0; i < 2; ++i) {
+      mbar_init(&bar_dfull[i], TN_DWARPS * 32);
       mbar_init(&bar_dempty[i], 1);
       mbar_init(&bar_tfull[i], 1);
       mbar_init(&bar_tempty[i], TN_EWARPS * 32);
@@ -947,30 +958,14 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
 
   if (warp < TN_DWARPS) {
     // ------------------------------------------------------------ digits role --
-    const uint32_t sbase = smem_u32(tn_smem);
-    const uint32_t idesc = umma_idesc_bf16(128, 7 * np);
-    int it = 0, last_b = -1;
-    uint32_t last_v = 0;
-    bool mma_ok = true;
-    constexpr bool PF = NT <= 4;  // the next window's values are loaded one window ahead
-    double v[NT][4], vn[PF ? NT : 1][4];
+    int it = 0;
     for (int win = blockIdx.x; win < nwin; win += gridDim.x, ++it) {
-      const int slot = it % TN_RING;
-      if constexpr (PF) {
-        if (it == 0)
-          tn_load<NT>(ta, win * TN_WIN, tid, W, v);
-        else
-#pragma unroll
-          for (int i = 0; i < NT; ++i)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) v[i][c] = vn[i][c];
-        if (win + (int)gridDim.x < nwin) tn_load<NT>(ta, (win + gridDim.x) * TN_WIN, tid, W, vn);
-      } else {
-        tn_load<NT>(ta, win * TN_WIN, tid, W, v);
-      }
+      const int slot = it % TN_RING, r0 = win * TN_WIN;
+      double v[NT][4];  // this window's values, for the exponent pass (reloaded for the digits)
+      tn_load<NT>(ta, r0, tid, W, v);
       // the first stage free (the previous window's first-half products done): the
       // exponent slot of this window is then free too (its epilogue is four windows back)
-      bool ok = bar_and(1, TN_DWARPS * 32, mma_ok && mbar_wait_bounded(&bar_dempty[0], (it & 1) ^ 1, &abort_s));
+      bool ok = bar_and(1, TN_DWARPS * 32, mbar_wait_bounded(&bar_dempty[0], (it & 1) ^ 1, &abort_s));
       if (!ok) {
         if (tid == 0) {
           abort_s = 1;
@@ -999,7 +994,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
       mbar_arrive(&bar_exp[slot]);
       for (int h = 0; h < 2; ++h) {
         if (h == 1) {
-          ok = bar_and(1, TN_DWARPS * 32, mma_ok && mbar_wait_bounded(&bar_dempty[1], (it & 1) ^ 1, &abort_s));
+          ok = bar_and(1, TN_DWARPS * 32, mbar_wait_bounded(&bar_dempty[1], (it & 1) ^ 1, &abort_s));
           if (!ok) break;
         }
         uint16_t* sA = sA0 + (size_t)h * (stage / 2);
@@ -1009,13 +1004,15 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
           const int t = tid + 256 * i, rp = t / W, j = t - rp * W;
           if (rp < TN_WIN / 2 && (rp >> 5) == h) {
             const int kk = 2 * (rp & 31);  // row within the half (even)
+            double vv[4];
+            tn_load1(ta, r0 + 2 * rp, j, vv);
 #pragma unroll
             for (int p = 0; p < 2; ++p) {  // Re, Im
               const int c = (j < wx ? 2 * j : MX + 2 * (j - wx)) + p;
               float d0[TC_DIGITS], d1[TC_DIGITS];
               const int T = sE[slot][c];
-              tc_digits(v[i][2 * p], T, d0);
-              tc_digits(v[i][2 * p + 1], T, d1);
+              tc_digits(vv[2 * p], T, d0);
+              tc_digits(vv[2 * p + 1], T, d1);
               if (j < wx) {
 #pragma unroll
                 for (int a = 0; a < TC_DIGITS; ++a) {
@@ -1034,31 +1031,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
           }
         }
         fence_async_smem();
-        bar_and(1, TN_DWARPS * 32, true);
-        if (tid == 0) {
-          const int b = it % ts;
-          const uint32_t vv = (uint32_t)(it / ts);
-          if (h == 0) mma_ok = mbar_wait_bounded(&bar_tempty[b], (vv & 1) ^ 1, &abort_s);
-          if (mma_ok) {
-            tc_fence_after();
-            const uint32_t a0 = sbase + (uint32_t)(h * stage);
-            const uint32_t b0 = a0 + (uint32_t)(mt * 128 * TN_HALF * 2);
-            for (int ks = 0; ks < TN_HALF / 16; ++ks)
-              for (int t = 0; t < mt; ++t)
-                umma_bf16(tmem + (uint32_t)(b * bufcols + t * 7 * np),
-                          umma_desc(a0 + (uint32_t)(t * 128 * TN_HALF * 2) + ks * 256, 128, 8 * 128),
-                          umma_desc(b0 + ks * 256, 128, 8 * 128), idesc, (h > 0 || ks > 0) ? 1 : 0);
-            umma_commit(&bar_dempty[h]);
-            if (h == 1) {
-              umma_commit(&bar_tfull[b]);
-              last_b = b;
-              last_v = vv;
-            }
-          } else {
-            abort_s = 1;
-            atomicExch(ta.err, 1);
-          }
-        }
+        mbar_arrive(&bar_dfull[h]);
       }
       if (!ok) {
         if (tid == 0) {
@@ -1068,9 +1041,46 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
         break;
       }
     }
-    if (tid == 0 && last_b >= 0) {
-      volatile int never = 0;
-      if (!mbar_wait_bounded(&bar_tfull[last_b], last_v & 1, &never)) atomicExch(ta.err, 1);
+  } else if (warp == TN_DWARPS + TN_EWARPS) {
+    // --------------------------------------------------------------- MMA role --
+    if (lane == 0) {
+      const uint32_t sbase = smem_u32(tn_smem);
+      const uint32_t idesc = umma_idesc_bf16(128, 7 * np);
+      int it = 0, last_b = -1;
+      uint32_t last_v = 0;
+      for (int win = blockIdx.x; win < nwin; win += gridDim.x, ++it) {
+        const int b = it % ts;
+        const uint32_t vv = (uint32_t)(it / ts);
+        bool ok = true;
+        for (int h = 0; h < 2 && ok; ++h) {
+          ok = mbar_wait_bounded(&bar_dfull[h], it & 1, &abort_s) &&
+               (h == 1 || mbar_wait_bounded(&bar_tempty[b], (vv & 1) ^ 1, &abort_s));
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t a0 = sbase + (uint32_t)(h * stage);
+          const uint32_t b0 = a0 + (uint32_t)(mt * 128 * TN_HALF * 2);
+          for (int ks = 0; ks < TN_HALF / 16; ++ks)
+            for (int t = 0; t < mt; ++t)
+              umma_bf16(tmem + (uint32_t)(b * bufcols + t * 7 * np),
+                        umma_desc(a0 + (uint32_t)(t * 128 * TN_HALF * 2) + ks * 256, 128, 8 * 128),
+                        umma_desc(b0 + ks * 256, 128, 8 * 128), idesc, (h > 0 || ks > 0) ? 1 : 0);
+          umma_commit(&bar_dempty[h]);
+          if (h == 1) {
+            umma_commit(&bar_tfull[b]);
+            last_b = b;
+            last_v = vv;
+          }
+        }
+        if (!ok) {
+          abort_s = 1;
+          atomicExch(ta.err, 1);
+          break;
+        }
+      }
+      if (last_b >= 0) {  // the last products complete before the tensor memory is freed
+        volatile int never = 0;
+        if (!mbar_wait_bounded(&bar_tfull[last_b], last_v & 1, &never)) atomicExch(ta.err, 1);
+      }
     }
   } else {
     // ---------------------------------------------------------- epilogue role --
