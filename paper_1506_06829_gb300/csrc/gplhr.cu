@@ -646,6 +646,56 @@ gplhr_status gram_tn(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int
   return GPLHR_OK;
 }
 
+// Wide FP64 Gram products on the tensor cores (tc.cuh, tc_gram_wide_kernel): wx <= 64,
+// wy <= 32, one pipelined CTA per SM over 128-row windows.
+const size_t kTwSmemMax = 212 * 1024;  // dynamic shared memory opted into by the wide Gram
+bool gram_tw_fits(const gplhr_ctx* ctx, int wx, int wy, bool self) {
+  if (!ctx->tc || ctx->n < 2048 || wx < 1 || wy < 1 || wx > gplhr::TW_XMAX || wy > gplhr::TW_YMAX ||
+      wx * wy < 128)
+    return false;
+  const int np = ((2 * wy + 15) / 16) * 16;
+  if (gplhr::tw_smem_bytes(np, wx, wy) > kTwSmemMax) return false;
+  (void)self;
+  return (size_t)std::min(ctx->num_sms, (ctx->n + gplhr::TW_WIN - 1) / gplhr::TW_WIN) * wx * wy <=
+         ctx->gram_part_elems;
+}
+
+gplhr_status gram_tw(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy1, double2* C, const int* skip,
+                     int nout_count, bool count, bool self) {
+  gplhr::TcGramWArgs t{};
+  const int wy = wy0 + wy1;
+  t.n = ctx->n;
+  t.X = X.p;
+  t.ldx = X.ld;
+  t.wx = wx;
+  t.Y0 = Y0.p;
+  t.ldy0 = Y0.ld;
+  t.wy0 = wy0;
+  t.Y1 = Y1.p;
+  t.ldy1 = Y1.ld;
+  t.wy1 = wy1;
+  t.self = self ? 1 : 0;
+  t.partial = ctx->gram_part;
+  t.skip = skip;
+  t.err = ctx->d_diag + 2;
+  t.np = ((2 * wy + 15) / 16) * 16;
+  t.ts = 2 * gplhr::TC_DIAG * t.np <= 512 ? 2 : 1;
+  t.tmem_cols = 32;
+  while (t.tmem_cols < t.ts * gplhr::TC_DIAG * t.np) t.tmem_cols <<= 1;
+  const int nwin = (ctx->n + gplhr::TW_WIN - 1) / gplhr::TW_WIN;
+  const int grid = std::min(ctx->num_sms, nwin);
+  const double by = 16.0 * ctx->n * (self ? wx : wx + wy);
+  const int ph = prof_begin(ctx, KC_GRAM_TC, count ? 8.0 * ctx->n * nout_count : 0.0, count ? by : 0.0, 2);
+  gplhr::tc_gram_wide_kernel<<<grid, gplhr::TW_THREADS, gplhr::tw_smem_bytes(t.np, wx, wy), ctx->stream>>>(t);
+  CK(cudaGetLastError());
+  const int nout = wx * wy;
+  gplhr::gram_reduce_kernel<<<(nout + gplhr::GRED_WARPS - 1) / gplhr::GRED_WARPS, 32 * gplhr::GRED_WARPS, 0,
+                               ctx->stream>>>(grid, nout, wx, wy, 0, ctx->gram_part, C, skip);
+  prof_end(ctx, ph);
+  CK(cudaGetLastError());
+  return GPLHR_OK;
+}
+
 gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy1, double2* C,
                   const int* skip = nullptr, bool herm = false, bool count = true, bool fp32 = false,
                   int force_mode = -1) {
@@ -659,6 +709,10 @@ gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy
   }
   if (mode == 0 && force_mode < 0 && wy1 == 0 && !self && gram_tn_fits(ctx, wy0, wx, false, &tn))
     return gram_tn(ctx, Y0, wy0, X, wx, Blk{nullptr, 0}, 0, C, skip, wx * wy, count, false, tn, true);
+  if (mode == 0 && force_mode < 0 && gram_tw_fits(ctx, wx, wy, self)) {
+    const bool h = herm && self;
+    return gram_tw(ctx, X, wx, Y0, wy0, Y1, wy1, C, skip, h ? wx * (wx + 1) / 2 : wx * wy, count, self);
+  }
   if (mode == 0 && force_mode < 0 && gram_tc_fits(ctx, wx, wy)) {
     // (a Hermitian request gets the full product; the algorithmic count stays the half)
     const bool h = herm && wy1 == 0 && wy0 == wx;
@@ -2078,6 +2132,8 @@ gplhr_status set_smem_limits(gplhr_ctx* ctx) {
   CK(cudaFuncSetAttribute(gplhr::tc_combine_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)gplhr::tg_smem_bytes(2, 64)));
+  CK(cudaFuncSetAttribute(gplhr::tc_gram_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)kTwSmemMax));
   CK(cudaFuncSetAttribute(gplhr::tc_gram_narrow_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::tc_gram_narrow_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   return GPLHR_OK;

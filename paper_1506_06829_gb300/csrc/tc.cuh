@@ -1175,4 +1175,334 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
                               : "memory");
 }
 
+// ---------------------------------------------- wide Gram products, pipelined --
+// C = X^* [Y0 Y1] for wx <= 64, wy <= 32 (2 wx real columns on the 128 tensor-memory
+// lanes, N' = 2 wy): the combination's layout with the contraction over the rows.
+// * A = X'^T, one 128-lane slab per digit plane; B = Y'^T with its 7 digit planes and a
+//   zero plane stacked along N (row b np + n).  Per 16-row K step, plane a of A against B
+//   planes 0 .. 7 - a, written at accumulator column a np, lands every product on its
+//   diagonal: the MMAs form D_d(m, n), d = 0..7, directly (|D_d| <= 7 2^21 over a 128-row
+//   window: exact in FP32).
+// * Windows of 128 rows with per-column exponent bounds (a first pass over the window),
+//   written to shared memory in four stages of 32 rows (two stage buffers).
+// * Roles: warps 0-5 (digits, 192 threads) run the exponent pass and write the stages;
+//   warp 14 (one thread) issues each full stage's MMAs; warps 6-13 (epilogue: two per
+//   lane quarter, each half of the column groups) form every G(m, n) of the window,
+//   round it once (tc_round96) and add it to an FP64 accumulator in shared memory that
+//   the thread owns.  At the end the CTA's complex partial C goes to
+//   partial[blockIdx.x][j wy + l].  15 warps: 128 registers per thread.
+// Every wait has an iteration limit, as in the combination.
+constexpr int TW_WIN = 128, TW_STAGE = 32;
+constexpr int TW_DWARPS = 6, TW_EWARPS = 8;
+constexpr int TW_THREADS = (TW_DWARPS + TW_EWARPS + 1) * 32;
+constexpr int TW_XMAX = 64, TW_YMAX = 32;
+constexpr int TW_RING = 4;
+
+struct TcGramWArgs {
+  int n;
+  const double2* X;
+  int ldx, wx;
+  const double2* Y0;
+  int ldy0, wy0;
+  const double2* Y1;
+  int ldy1, wy1;
+  int self;          // Y0 == X, wy1 == 0
+  double2* partial;  // [gridDim.x][wx * (wy0 + wy1)]
+  const int* skip;
+  int* err;
+  int np;            // 2 wy rounded up to 16 (<= 64)
+  int ts;            // accumulator buffers (1 or 2)
+  int tmem_cols;     // power of two >= ts 8 np
+};
+
+__host__ __device__ constexpr size_t tw_stage_bytes(int np) {
+  return ((size_t)TC_DIGITS * 128 + (size_t)TC_DIAG * np) * TW_STAGE * 2;
+}
+// two stages, then the FP64 accumulators [2 wx][2 wy] and their non-finite flags
+__host__ __device__ constexpr size_t tw_smem_bytes(int np, int wx, int wy) {
+  return 2 * tw_stage_bytes(np) + (size_t)4 * wx * wy * 8 + (size_t)4 * wx * wy;
+}
+
+__global__ void __launch_bounds__(TW_THREADS, 1) tc_gram_wide_kernel(TcGramWArgs ta) {
+  if (ta.skip && *ta.skip == 0) return;
+  extern __shared__ __align__(1024) unsigned char tw_smem[];
+  const int n = ta.n, wx = ta.wx, wy = ta.wy0 + ta.wy1, np = ta.np, ts = ta.ts;
+  const int W = ta.self ? wx : wx + wy;
+  const int MX = 2 * wx, NY = 2 * wy;
+  const size_t stage = tw_stage_bytes(np);
+  double* sAcc = reinterpret_cast<double*>(tw_smem + 2 * stage);             // [MX][NY]
+  unsigned char* sBadAcc = reinterpret_cast<unsigned char*>(sAcc + (size_t)MX * NY);
+  __shared__ __align__(8) uint64_t bar_dfull[2], bar_dempty[2], bar_tfull[2], bar_tempty[2], bar_exp[TW_RING];
+  __shared__ uint32_t taddr_s;
+  __shared__ volatile int abort_s;
+  __shared__ int sE[TW_RING][2 * (TW_XMAX + TW_YMAX)], sBad[TW_RING][2 * (TW_XMAX + TW_YMAX)];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  {  // zero the stages (padding lanes, rows and the zero plane stay zero) and the accumulators
+    const size_t words = tw_smem_bytes(np, wx, wy) / 4;
+    for (size_t e = tid; e < words; e += TW_THREADS) reinterpret_cast<uint32_t*>(tw_smem)[e] = 0u;
+  }
+  if (tid == 0) {
+    abort_s = 0;
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bar_dfull[i], TW_DWARPS * 32);
+      mbar_init(&bar_dempty[i], 1);
+      mbar_init(&bar_tfull[i], 1);
+      mbar_init(&bar_tempty[i], TW_EWARPS * 32);
+    }
+    for (int i = 0; i < TW_RING; ++i) mbar_init(&bar_exp[i], TW_DWARPS * 32);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
+                 "r"(ta.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = taddr_s;
+  const int nwin = (n + TW_WIN - 1) / TW_WIN;
+  const int ncol = ta.self ? MX : MX + NY;
+  constexpr int DT = TW_DWARPS * 32;
+
+  if (warp < TW_DWARPS) {
+    // ------------------------------------------------------------ digits role --
+    int it = 0;
+    for (int win = blockIdx.x; win < nwin; win += gridDim.x, ++it) {
+      const int slot = it % TW_RING, r0 = win * TW_WIN, nr = min(TW_WIN, n - r0);
+      // the exponent slot is free once the previous window's first stage was consumed
+      // (that window's MMAs began after the epilogue of the one before it had finished)
+      bool ok = bar_and(1, DT, mbar_wait_bounded(&bar_dempty[0], ((uint32_t)(2 * it) & 1u) ^ 1u, &abort_s));
+      if (!ok) {
+        if (tid == 0) {
+          abort_s = 1;
+          atomicExch(ta.err, 1);
+        }
+        break;
+      }
+      for (int c = tid; c < ncol; c += DT) {
+        sE[slot][c] = TC_NOEXP;
+        sBad[slot][c] = 0;
+      }
+      bar_and(1, DT, true);
+      {  // exponent pass: thread (column j, row phase) over rows rg, rg + R, ...
+        const int R = DT / W;
+        if (tid < R * W) {
+          const int j = tid % W, rg = tid / W;
+          const double2* base;
+          size_t ld;
+          if (j < wx) {
+            base = ta.X + j;
+            ld = (size_t)ta.ldx;
+          } else if (j - wx < ta.wy0) {
+            base = ta.Y0 + (j - wx);
+            ld = (size_t)ta.ldy0;
+          } else {
+            base = ta.Y1 + (j - wx - ta.wy0);
+            ld = (size_t)ta.ldy1;
+          }
+          int tre = TC_NOEXP, tim = TC_NOEXP, bre = 0, bim = 0;
+#pragma unroll 8
+          for (int r = rg; r < nr; r += R) {
+            const double2 v = base[(size_t)(r0 + r) * ld];
+            tre = max(tre, tc_top(v.x));
+            tim = max(tim, tc_top(v.y));
+            bre |= tc_nonfinite(v.x);
+            bim |= tc_nonfinite(v.y);
+          }
+          const int c = j < wx ? 2 * j : MX + 2 * (j - wx);
+          if (tre > TC_NOEXP) atomicMax(&sE[slot][c], tre);
+          if (tim > TC_NOEXP) atomicMax(&sE[slot][c + 1], tim);
+          if (bre) sBad[slot][c] = 1;
+          if (bim) sBad[slot][c + 1] = 1;
+        }
+      }
+      bar_and(1, DT, true);
+      mbar_arrive(&bar_exp[slot]);
+      for (int sc = 0; sc < TW_WIN / TW_STAGE; ++sc) {
+        const int st = sc & 1;
+        const uint32_t u = (uint32_t)(2 * it + (sc >> 1));
+        if (sc > 0) {
+          ok = bar_and(1, DT, mbar_wait_bounded(&bar_dempty[st], (u & 1) ^ 1, &abort_s));
+          if (!ok) break;
+        }
+        uint16_t* sA = reinterpret_cast<uint16_t*>(tw_smem + st * stage);
+        uint16_t* sB = sA + (size_t)TC_DIGITS * 128 * TW_STAGE;
+        // tasks: (row pair, complex column), 16 W of them
+        for (int t = tid; t < (TW_STAGE / 2) * W; t += DT) {
+          const int rp = t / W, j = t - rp * W;
+          const int kk = 2 * rp, r = r0 + sc * TW_STAGE + kk;
+          double vv[4];
+          {
+            const double2* base;
+            size_t ld;
+            if (j < wx) {
+              base = ta.X + j;
+              ld = (size_t)ta.ldx;
+            } else if (j - wx < ta.wy0) {
+              base = ta.Y0 + (j - wx);
+              ld = (size_t)ta.ldy0;
+            } else {
+              base = ta.Y1 + (j - wx - ta.wy0);
+              ld = (size_t)ta.ldy1;
+            }
+            double2 x0 = make_double2(0.0, 0.0), x1 = x0;
+            if (r < n) x0 = base[(size_t)r * ld];
+            if (r + 1 < n) x1 = base[(size_t)(r + 1) * ld];
+            vv[0] = x0.x;
+            vv[1] = x1.x;
+            vv[2] = x0.y;
+            vv[3] = x1.y;
+          }
+#pragma unroll
+          for (int p = 0; p < 2; ++p) {
+            const int c = (j < wx ? 2 * j : MX + 2 * (j - wx)) + p;
+            float d0[TC_DIGITS], d1[TC_DIGITS];
+            const int T = sE[slot][c];
+            tc_digits(vv[2 * p], T, d0);
+            tc_digits(vv[2 * p + 1], T, d1);
+            if (j < wx) {
+#pragma unroll
+              for (int a = 0; a < TC_DIGITS; ++a)
+                *reinterpret_cast<uint32_t*>(sA + (size_t)a * 128 * TW_STAGE + tc_off(c, kk, TW_STAGE / 8)) =
+                    tc_pack2(d0[a], d1[a]);
+            }
+            if (j >= wx || ta.self) {
+              const int nn = j < wx ? c : c - MX;
+#pragma unroll
+              for (int b = 0; b < TC_DIGITS; ++b)
+                *reinterpret_cast<uint32_t*>(sB + tc_off(b * np + nn, kk, TW_STAGE / 8)) = tc_pack2(d0[b], d1[b]);
+            }
+          }
+        }
+        fence_async_smem();
+        mbar_arrive(&bar_dfull[st]);
+      }
+      if (!ok) {
+        if (tid == 0) {
+          abort_s = 1;
+          atomicExch(ta.err, 1);
+        }
+        break;
+      }
+    }
+  } else if (warp == TW_DWARPS + TW_EWARPS) {
+    // --------------------------------------------------------------- MMA role --
+    if (lane == 0) {
+      const uint32_t sbase = smem_u32(tw_smem);
+      constexpr uint32_t KCB = (TW_STAGE / 8) * 128;  // bytes between 8-row groups
+      int it = 0, last_b = -1;
+      uint32_t last_v = 0;
+      for (int win = blockIdx.x; win < nwin; win += gridDim.x, ++it) {
+        const int b = it % ts;
+        const uint32_t vv = (uint32_t)(it / ts);
+        bool ok = true;
+        for (int sc = 0; sc < TW_WIN / TW_STAGE && ok; ++sc) {
+          const int st = sc & 1;
+          const uint32_t u = (uint32_t)(2 * it + (sc >> 1));
+          ok = mbar_wait_bounded(&bar_dfull[st], u & 1, &abort_s) &&
+               (sc > 0 || mbar_wait_bounded(&bar_tempty[b], (vv & 1) ^ 1, &abort_s));
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t a0 = sbase + (uint32_t)(st * stage);
+          const uint32_t b0 = a0 + (uint32_t)(TC_DIGITS * 128 * TW_STAGE * 2);
+          for (int ks = 0; ks < TW_STAGE / 16; ++ks)
+            for (int da = 0; da < TC_DIGITS; ++da) {
+              const uint64_t ad = umma_desc(a0 + (uint32_t)(da * 128 * TW_STAGE * 2) + ks * 256, 128, KCB);
+              const int ntot = (TC_DIAG - da) * np;
+              for (int c0 = 0; c0 < ntot; c0 += 256) {
+                const int nc = min(256, ntot - c0);
+                const uint64_t bd = umma_desc(b0 + (uint32_t)(c0 >> 3) * KCB + ks * 256, 128, KCB);
+                umma_bf16(tmem + (uint32_t)(b * TC_DIAG * np + da * np + c0), ad, bd, umma_idesc_bf16(128, nc),
+                          (sc > 0 || ks > 0 || da > 0) ? 1 : 0);
+              }
+            }
+          umma_commit(&bar_dempty[st]);
+          if (sc == TW_WIN / TW_STAGE - 1) {
+            umma_commit(&bar_tfull[b]);
+            last_b = b;
+            last_v = vv;
+          }
+        }
+        if (!ok) {
+          abort_s = 1;
+          atomicExch(ta.err, 1);
+          break;
+        }
+      }
+      if (last_b >= 0) {  // the last products complete before the tensor memory is freed
+        volatile int never = 0;
+        if (!mbar_wait_bounded(&bar_tfull[last_b], last_v & 1, &never)) atomicExch(ta.err, 1);
+      }
+    }
+  } else {
+    // ---------------------------------------------------------- epilogue role --
+    const int ew = warp - TW_DWARPS, q4 = warp & 3, eh = ew >> 2;
+    const int m = q4 * 32 + lane;  // this thread's lane: real column m of X'
+    const bool vm = m < MX;
+    const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
+    int it = 0;
+    for (int win = blockIdx.x; win < nwin; win += gridDim.x, ++it) {
+      const int b = it % ts, slot = it % TW_RING;
+      const uint32_t vv = (uint32_t)(it / ts);
+      bool ok = mbar_wait_bounded(&bar_exp[slot], (uint32_t)(it / TW_RING) & 1, &abort_s) &&
+                mbar_wait_bounded(&bar_tfull[b], vv & 1, &abort_s);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) {
+          abort_s = 1;
+          atomicExch(ta.err, 1);
+        }
+        break;
+      }
+      tc_fence_after();
+      const int Em = vm ? sE[slot][m] : 0;
+      const int bm = vm ? sBad[slot][m] : 0;
+      const uint32_t tb = tmem + lane_base + (uint32_t)(b * TC_DIAG * np);
+      for (int nb = 4 * eh; nb < np; nb += 8) {
+        uint32_t acc[TC_DIAG][4];
+#pragma unroll
+        for (int d = 0; d < TC_DIAG; ++d) tmem_ld4(tb + (uint32_t)(d * np + nb), acc[d]);
+        tmem_wait_ld();
+        if (!vm) continue;
+#pragma unroll
+        for (int uu = 0; uu < 4; ++uu) {
+          const int nn = nb + uu;
+          if (nn >= NY) continue;
+          const int cy = ta.self ? nn : MX + nn;
+          long long hi = 0, lo = 0;
+#pragma unroll
+          for (int d = 0; d < TC_DIAG; ++d) {
+            const long long Dd = (long long)__float2int_rn(__uint_as_float(acc[d][uu]));
+            if (d < 4)
+              hi += Dd << (8 * (3 - d));
+            else
+              lo += Dd << (8 * (7 - d));
+          }
+          sAcc[(size_t)m * NY + nn] += tc_round96(hi, lo, Em + sE[slot][cy] - 68);
+          if (bm | sBad[slot][cy]) sBadAcc[(size_t)m * NY + nn] = 1;
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&bar_tempty[b]);
+    }
+    bar_and(2, TW_EWARPS * 32, true);
+    // G(2j, 2l) = Re x Re, (2j, 2l+1) = Re x Im, (2j+1, 2l) = Im x Re, (2j+1, 2l+1) = Im x Im
+    const int etid = tid - TW_DWARPS * 32;
+    for (int o = etid; o < wx * wy; o += TW_EWARPS * 32) {
+      const int j = o / wy, l = o - j * wy;
+      const size_t i00 = (size_t)(2 * j) * NY + 2 * l, i10 = i00 + NY;
+      double2 cz = make_double2(sAcc[i00] + sAcc[i10 + 1], sAcc[i00 + 1] - sAcc[i10]);
+      if (sBadAcc[i00] | sBadAcc[i00 + 1] | sBadAcc[i10] | sBadAcc[i10 + 1])
+        cz = make_double2(__longlong_as_double(0x7FF8000000000000ll), __longlong_as_double(0x7FF8000000000000ll));
+      ta.partial[(size_t)blockIdx.x * wx * wy + o] = cz;
+    }
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ta.tmem_cols)
+                              : "memory");
+}
+
 }  // namespace gplhr

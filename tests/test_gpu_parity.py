@@ -639,9 +639,10 @@ def _gram_window_bound(Xh, Yh, nwin_cta):
 
 
 @pytest.mark.parametrize("n,wx,wy,self_", [
-    # wide products (tc_gram_kernel)
+    # wide products (tc_gram_wide_kernel; wx > 64 or large outputs: tc_gram_kernel)
     (5000, 32, 32, False), (100003, 128, 16, False), (20000, 64, 32, False), (2048, 24, 24, False),
-    (30001, 24, 24, True),
+    (30001, 24, 24, True), (40000, 32, 32, True), (10007, 48, 20, False), (3000, 17, 30, False),
+    (2049, 64, 16, False),
     # narrow products (tc_gram_narrow_kernel: planes stacked along M and N)
     (4096, 8, 8, False), (100003, 8, 8, True), (20000, 24, 8, False), (30001, 16, 16, False),
     (2048, 3, 5, False), (9000, 1, 1, True), (7001, 24, 1, False), (12345, 5, 16, False), (65536, 24, 24, True),
@@ -676,7 +677,8 @@ def test_gram_tensor_matches_twice_precision(n, wx, wy, self_):
                                                       np.max(eim / np.maximum(bim, 1e-300)))
 
 
-@pytest.mark.parametrize("wx,wy,self_", [(32, 16, False), (8, 8, False), (12, 12, True)])
+@pytest.mark.parametrize("wx,wy,self_", [(32, 16, False), (8, 8, False), (12, 12, True), (24, 24, True),
+                                         (100, 16, False)])
 def test_gram_tensor_nonfinite(wx, wy, self_):
     """A NaN in X (an Inf in Y) makes exactly its row (column) of C NaN."""
     rng = np.random.default_rng(9)
