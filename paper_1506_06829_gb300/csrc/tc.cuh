@@ -500,14 +500,14 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) tc_combine_kernel(int n, T
       const bool valid = r < n;
       const int T = sRowT[slot][row_in], bad = sRowBad[slot][row_in];
       const uint32_t tb = tmem + lane_base + (uint32_t)(b * TC_DIAG * np);
-      for (int nb = 4 * eh; nb < np; nb += 8) {  // groups of 4 real columns, alternating halves
-        uint32_t acc[TC_DIAG][4];
+      for (int nb = 8 * eh; nb < np; nb += 16) {  // chunks of 8 real columns, alternating halves
+        uint32_t acc[TC_DIAG][8];
 #pragma unroll
-        for (int d = 0; d < TC_DIAG; ++d) tmem_ld4(tb + (uint32_t)(d * np + nb), acc[d]);
+        for (int d = 0; d < TC_DIAG; ++d) tmem_ld8(tb + (uint32_t)(d * np + nb), acc[d]);
         tmem_wait_ld();
         if (!valid) continue;
 #pragma unroll
-        for (int uu = 0; uu < 4; uu += 2) {
+        for (int uu = 0; uu < 8; uu += 2) {
           const int nn = nb + uu, l = nn >> 1;
           if (l >= a.c) continue;
           double yv[2];
@@ -1111,17 +1111,25 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
       for (int t = 0; t < mt; ++t) {
         const int L = t * 128 + q4 * 32 + lane, a = L / MX, m = L - a * MX;
         const bool vl = a < TC_DIGITS;
-        for (int bp = 0; bp < TC_DIGITS; ++bp) {
+        for (int bp0 = 0; bp0 < TC_DIGITS; bp0 += 2) {  // two planes of 16 columns per round trip
           for (int n0 = 0; n0 < np; n0 += 16) {
-            uint32_t r[16];
-            tmem_ld16(tmem + lane_base + (uint32_t)(b * bufcols + t * 7 * np + bp * np + n0), r);
-            tmem_wait_ld();
-            if (vl && a + bp < TC_DIAG) {
-              int* dst = sD + ((size_t)(a + bp) * MX + m) * SP + n0;
-              // |P_ab| <= 2^21: 1.5 2^23 + P is exact and its low bits are P + 2^22
+            uint32_t r[2][16];
 #pragma unroll
-              for (int u = 0; u < 16; ++u)
-                if (n0 + u < NY) atomicAdd(dst + u, __float_as_int(__uint_as_float(r[u]) + 12582912.0f) - 0x4B400000);
+            for (int e = 0; e < 2; ++e)
+              if (bp0 + e < TC_DIGITS)
+                tmem_ld16(tmem + lane_base + (uint32_t)(b * bufcols + t * 7 * np + (bp0 + e) * np + n0), r[e]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const int bp = bp0 + e;
+              if (bp < TC_DIGITS && vl && a + bp < TC_DIAG) {
+                int* dst = sD + ((size_t)(a + bp) * MX + m) * SP + n0;
+                // |P_ab| <= 2^21: 1.5 2^23 + P is exact and its low bits are P + 2^22
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                  if (n0 + u < NY)
+                    atomicAdd(dst + u, __float_as_int(__uint_as_float(r[e][u]) + 12582912.0f) - 0x4B400000);
+              }
             }
           }
         }
@@ -1187,7 +1195,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
 //   written to shared memory in four stages of 32 rows (two stage buffers).
 // * Roles: warps 0-5 (digits, 192 threads) run the exponent pass and write the stages;
 //   warp 14 (one thread) issues each full stage's MMAs; warps 6-13 (epilogue: two per
-//   lane quarter, each half of the column groups) form every G(m, n) of the window,
+//   lane quarter, alternate 8-column chunks) form every G(m, n) of the window,
 //   round it once (tc_round96) and add it to an FP64 accumulator in shared memory that
 //   the thread owns.  At the end the CTA's complex partial C goes to
 //   partial[blockIdx.x][j wy + l].  15 warps: 128 registers per thread.
@@ -1460,14 +1468,14 @@ __global__ void __launch_bounds__(TW_THREADS, 1) tc_gram_wide_kernel(TcGramWArgs
       const int Em = vm ? sE[slot][m] : 0;
       const int bm = vm ? sBad[slot][m] : 0;
       const uint32_t tb = tmem + lane_base + (uint32_t)(b * TC_DIAG * np);
-      for (int nb = 4 * eh; nb < np; nb += 8) {
-        uint32_t acc[TC_DIAG][4];
+      for (int nb = 8 * eh; nb < np; nb += 16) {  // 8-column chunks: the 8 diagonals in one round trip
+        uint32_t acc[TC_DIAG][8];
 #pragma unroll
-        for (int d = 0; d < TC_DIAG; ++d) tmem_ld4(tb + (uint32_t)(d * np + nb), acc[d]);
+        for (int d = 0; d < TC_DIAG; ++d) tmem_ld8(tb + (uint32_t)(d * np + nb), acc[d]);
         tmem_wait_ld();
         if (!vm) continue;
 #pragma unroll
-        for (int uu = 0; uu < 4; ++uu) {
+        for (int uu = 0; uu < 8; ++uu) {
           const int nn = nb + uu;
           if (nn >= NY) continue;
           const int cy = ta.self ? nn : MX + nn;
