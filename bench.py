@@ -40,11 +40,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "s to k eigenpairs @1e-8 resid (FP64 vs mixed); SpMM+Gram HBM GB/s vs peak"
 FP64_PEAK_GFLOPS = 1250.0   # GB300 dense FP64 (profiling recipe table); probe measured 1203
-# DRAM bytes per launch (means over one iteration's launches) of this workload in FP64, from
-# one-pass ncu captures (profiles/gram_traffic_convdiff3d_64cubed.md)
-GRAM_TRAFFIC_64CUBED = 52.6e6        # gram_partial_kernel (DFMA), 46 launches
-COMBINE_TC_TRAFFIC_64CUBED = 68.6e6  # tc_combine_kernel, 31 launches
-KCLASSES = ["spmm", "gram", "combine", "precond", "chol", "other", "gram_tc", "combine_tc"]
+# DRAM bytes per launch of this workload in FP64 (mean over one iteration's launches of the
+# kernel class), from one-pass ncu captures (profiles/gram_traffic_convdiff3d_64cubed.md)
+TRAFFIC_64CUBED = {
+    "gram_tc": 62.3e6,     # tc_gram_narrow_kernel / tc_gram_wide_kernel, 27 launches
+    "combine_tc": 68.3e6,  # tc_combine_kernel, 31 launches
+}
 TENSOR_CLASSES = ("gram_tc", "combine_tc")   # FP64 by integer digits on the tensor cores
 
 
@@ -238,7 +239,7 @@ def main():
         roofline = {
             "kernel": dom, "bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved_gbs / hbm_peak,
-            "traffic": COMBINE_TC_TRAFFIC_64CUBED if dom == "combine_tc" and default_full else None,
+            "traffic": TRAFFIC_64CUBED.get(dom) if default_full else None,
             "note": (f"FP64 by integer digits on the tensor cores: algorithmic bytes / event time of the "
                      f"{d['launches']} {dom} launches (of measured copy bandwidth); the kernel is bound by "
                      f"its integer work (digit split, exact rounding), the tensor pipe is mostly idle; "
@@ -252,8 +253,6 @@ def main():
                      f"{d['launches']} {dom} launches; its algorithmic bytes give {achieved_gbs:.0f} GB/s "
                      f"= {achieved_gbs / hbm_peak:.3f} of the measured HBM copy bandwidth"),
         }
-        if dom == "gram" and default_full:
-            roofline["traffic"] = GRAM_TRAFFIC_64CUBED
     spmm, gram = per_class["spmm"], per_class["gram"]
     hbm = {c: {"GB/s": (per_class[c]["gbyte"] / (per_class[c]["ms"] / 1e3)) if per_class[c]["ms"] else 0.0}
            for c in ("spmm", "gram", "combine", "gram_tc", "combine_tc")}

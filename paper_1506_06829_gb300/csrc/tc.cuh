@@ -1337,50 +1337,61 @@ __global__ void __launch_bounds__(TW_THREADS, 1) tc_gram_wide_kernel(TcGramWArgs
         }
         uint16_t* sA = reinterpret_cast<uint16_t*>(tw_smem + st * stage);
         uint16_t* sB = sA + (size_t)TC_DIGITS * 128 * TW_STAGE;
-        // tasks: (row pair, complex column), 16 W of them
-        for (int t = tid; t < (TW_STAGE / 2) * W; t += DT) {
-          const int rp = t / W, j = t - rp * W;
-          const int kk = 2 * rp, r = r0 + sc * TW_STAGE + kk;
-          double vv[4];
-          {
-            const double2* base;
-            size_t ld;
-            if (j < wx) {
-              base = ta.X + j;
-              ld = (size_t)ta.ldx;
-            } else if (j - wx < ta.wy0) {
-              base = ta.Y0 + (j - wx);
-              ld = (size_t)ta.ldy0;
-            } else {
-              base = ta.Y1 + (j - wx - ta.wy0);
-              ld = (size_t)ta.ldy1;
-            }
+        // tasks: (row pair, complex column), 16 W of them, four at a time: the loads of a
+        // batch are all in flight before its digits are formed
+        constexpr int TB = 4;
+        for (int t0 = tid; t0 < (TW_STAGE / 2) * W; t0 += TB * DT) {
+          double vv[TB][4];
+#pragma unroll
+          for (int q = 0; q < TB; ++q) {
+            const int t = t0 + q * DT, rp = t / W, j = t - rp * W;
+            const int r = r0 + sc * TW_STAGE + 2 * rp;
             double2 x0 = make_double2(0.0, 0.0), x1 = x0;
-            if (r < n) x0 = base[(size_t)r * ld];
-            if (r + 1 < n) x1 = base[(size_t)(r + 1) * ld];
-            vv[0] = x0.x;
-            vv[1] = x1.x;
-            vv[2] = x0.y;
-            vv[3] = x1.y;
+            if (t < (TW_STAGE / 2) * W) {
+              const double2* base;
+              size_t ld;
+              if (j < wx) {
+                base = ta.X + j;
+                ld = (size_t)ta.ldx;
+              } else if (j - wx < ta.wy0) {
+                base = ta.Y0 + (j - wx);
+                ld = (size_t)ta.ldy0;
+              } else {
+                base = ta.Y1 + (j - wx - ta.wy0);
+                ld = (size_t)ta.ldy1;
+              }
+              if (r < n) x0 = base[(size_t)r * ld];
+              if (r + 1 < n) x1 = base[(size_t)(r + 1) * ld];
+            }
+            vv[q][0] = x0.x;
+            vv[q][1] = x1.x;
+            vv[q][2] = x0.y;
+            vv[q][3] = x1.y;
           }
 #pragma unroll
-          for (int p = 0; p < 2; ++p) {
-            const int c = (j < wx ? 2 * j : MX + 2 * (j - wx)) + p;
-            float d0[TC_DIGITS], d1[TC_DIGITS];
-            const int T = sE[slot][c];
-            tc_digits(vv[2 * p], T, d0);
-            tc_digits(vv[2 * p + 1], T, d1);
-            if (j < wx) {
+          for (int q = 0; q < TB; ++q) {
+            const int t = t0 + q * DT, rp = t / W, j = t - rp * W;
+            if (t >= (TW_STAGE / 2) * W) break;
+            const int kk = 2 * rp;
 #pragma unroll
-              for (int a = 0; a < TC_DIGITS; ++a)
-                *reinterpret_cast<uint32_t*>(sA + (size_t)a * 128 * TW_STAGE + tc_off(c, kk, TW_STAGE / 8)) =
-                    tc_pack2(d0[a], d1[a]);
-            }
-            if (j >= wx || ta.self) {
-              const int nn = j < wx ? c : c - MX;
+            for (int p = 0; p < 2; ++p) {
+              const int c = (j < wx ? 2 * j : MX + 2 * (j - wx)) + p;
+              float d0[TC_DIGITS], d1[TC_DIGITS];
+              const int T = sE[slot][c];
+              tc_digits(vv[q][2 * p], T, d0);
+              tc_digits(vv[q][2 * p + 1], T, d1);
+              if (j < wx) {
 #pragma unroll
-              for (int b = 0; b < TC_DIGITS; ++b)
-                *reinterpret_cast<uint32_t*>(sB + tc_off(b * np + nn, kk, TW_STAGE / 8)) = tc_pack2(d0[b], d1[b]);
+                for (int a = 0; a < TC_DIGITS; ++a)
+                  *reinterpret_cast<uint32_t*>(sA + (size_t)a * 128 * TW_STAGE + tc_off(c, kk, TW_STAGE / 8)) =
+                      tc_pack2(d0[a], d1[a]);
+              }
+              if (j >= wx || ta.self) {
+                const int nn = j < wx ? c : c - MX;
+#pragma unroll
+                for (int b = 0; b < TC_DIGITS; ++b)
+                  *reinterpret_cast<uint32_t*>(sB + tc_off(b * np + nn, kk, TW_STAGE / 8)) = tc_pack2(d0[b], d1[b]);
+              }
             }
           }
         }
