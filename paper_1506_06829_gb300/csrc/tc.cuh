@@ -177,10 +177,18 @@ __device__ __forceinline__ double tc_round96(long long hi, long long lo, int p) 
 // The eight digit diagonals D_0..D_7 of the combination (FP32 accumulators holding
 // integers of magnitude <= 7 2^20, K' <= 64) as Z = hi 2^32 + lo = sum_d D_d 256^(7 - d):
 // pairs first in 32 bits (|256 D_2k + D_2k+1| < 2^31), then two 48-bit halves.
+// SMALL: |D_d| < 2^22 (K' <= 32), so 1.5 2^23 + D_d is exact in FP32 and its low bits give
+// D_d + 2^22 (an FP32 addition and an integer one instead of a conversion).
+template <bool SMALL>
 __device__ __forceinline__ void tc_diag_sum(const uint32_t (&D)[TC_DIAG], long long& hi, long long& lo) {
+  int I[TC_DIAG];
+#pragma unroll
+  for (int d = 0; d < TC_DIAG; ++d)
+    I[d] = SMALL ? __float_as_int(__uint_as_float(D[d]) + 12582912.0f) - 0x4B400000
+                 : __float2int_rn(__uint_as_float(D[d]));
   int P[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) P[k] = __float2int_rn(__uint_as_float(D[2 * k])) * 256 + __float2int_rn(__uint_as_float(D[2 * k + 1]));
+  for (int k = 0; k < 4; ++k) P[k] = I[2 * k] * 256 + I[2 * k + 1];
   hi = (long long)P[0] * 65536ll + (long long)P[1];
   lo = (long long)P[2] * 65536ll + (long long)P[3];
 }
@@ -270,6 +278,25 @@ __device__ __forceinline__ double tc_cval(const CombArgs& a, int wsum, int kk, i
 constexpr int TC_DWARPS = 8, TC_EWARPS = 8;
 constexpr int TC_PIPE_THREADS = (TC_DWARPS + TC_EWARPS) * 32;
 constexpr int TC_RING = 4;
+
+// Thread (row r, half h)'s k-chunks kc = h, h + 2, ... of the stacked row: 4 complex
+// values each, as (Re, Im) pairs; zeros when the row is not valid or the column is padding.
+template <int KC>
+__device__ __forceinline__ void tc_row_load(const double2* const* colp, const int* coll, int wsum, bool valid, int r,
+                                            int h, double (&xv)[4 * KC]) {
+#pragma unroll
+  for (int i = 0; i < KC / 2; ++i) {
+    const int kc = 2 * i + h;
+#pragma unroll
+    for (int uu = 0; uu < 4; ++uu) {
+      const int j = kc * 4 + uu;
+      double2 v = make_double2(0.0, 0.0);
+      if (valid && j < wsum) v = colp[j][(size_t)r * coll[j]];
+      xv[8 * i + 2 * uu] = v.x;
+      xv[8 * i + 2 * uu + 1] = v.y;
+    }
+  }
+}
 
 template <int KC>  // K' / 8 (2, 4, 6 or 8)
 __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) tc_combine_kernel(int n, TcCombArgs ta) {
@@ -361,6 +388,8 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) tc_combine_kernel(int n, T
     int it = 0, last_b = -1;
     uint32_t last_v = 0;
     bool mma_ok = true;  // thread 0: its last wait for a buffer succeeded
+    constexpr bool PF = KC == 2;  // registers allow the next tile's values ahead at K' = 16
+    double xn[PF ? 4 * KC : 1];
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
       const int s = it % ds;
       const uint32_t u = (uint32_t)(it / ds);
@@ -385,20 +414,21 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) tc_combine_kernel(int n, T
         }
       }
       double xv[4 * KC];
+      if constexpr (PF) {  // this tile's values were loaded one tile ahead
+        if (it == 0) tc_row_load<KC>(colp, coll, wsum, valid, r, h, xv);
+        else
+#pragma unroll
+          for (int e = 0; e < 4 * KC; ++e) xv[e] = xn[e];
+        const int r2 = r + gridDim.x * TC_ROWS;
+        tc_row_load<KC>(colp, coll, wsum, r2 < n, r2, h, xn);
+      } else {
+        tc_row_load<KC>(colp, coll, wsum, valid, r, h, xv);
+      }
       int T = TC_NOEXP, bad = 0;
 #pragma unroll
-      for (int i = 0; i < KC / 2; ++i) {
-        const int kc = 2 * i + h;
-#pragma unroll
-        for (int uu = 0; uu < 4; ++uu) {
-          const int j = kc * 4 + uu;
-          double2 v = make_double2(0.0, 0.0);
-          if (valid && j < wsum) v = colp[j][(size_t)r * coll[j]];
-          xv[8 * i + 2 * uu] = v.x;
-          xv[8 * i + 2 * uu + 1] = v.y;
-          T = max(T, max(tc_top(v.x), tc_top(v.y)));
-          bad |= tc_nonfinite(v.x) | tc_nonfinite(v.y);
-        }
+      for (int e = 0; e < 4 * KC; ++e) {
+        T = max(T, tc_top(xv[e]));
+        bad |= tc_nonfinite(xv[e]);
       }
       sX[it & 1][h][rl] = T;
       sXb[it & 1][h][rl] = bad;
@@ -517,7 +547,7 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) tc_combine_kernel(int n, T
 #pragma unroll
             for (int d = 0; d < TC_DIAG; ++d) dg[d] = acc[d][uu + q];
             long long hi, lo;
-            tc_diag_sum(dg, hi, lo);
+            tc_diag_sum<(KC <= 4)>(dg, hi, lo);
             yv[q] = tc_round96(hi, lo, T + sG[nn + q] - 68);
             if (bad || sBadC[nn + q]) yv[q] = __longlong_as_double(0x7FF8000000000000ll);
           }
