@@ -777,16 +777,30 @@ gplhr_status combine_tc(gplhr_ctx* ctx, gplhr::CombArgs a, int wsum, int c, int 
   t.tmem_cols = 32;
   while (t.tmem_cols < t.ts * gplhr::TC_DIAG * t.np) t.tmem_cols <<= 1;
   t.err = ctx->d_diag + 2;
-  const size_t smem = gplhr::tc_comb_smem_bytes(t.kp, t.np, t.ds);
   const int ntiles = (ctx->n + gplhr::TC_ROWS - 1) / gplhr::TC_ROWS;
-  const int grid = std::min(ntiles, ctx->num_sms);
+  // two CTAs per SM at K' <= 32, N' = 16 (both fit in shared and tensor memory; at K' = 32
+  // with one digit stage each)
+  const bool two = t.kp <= 32 && t.np == 16 && t.ts * gplhr::TC_DIAG * t.np <= 256;
+  if (two && t.kp == 32) t.ds = 1;
+  const int grid = std::min(ntiles, (two ? 2 : 1) * ctx->num_sms);
+  const size_t smem = gplhr::tc_comb_smem_bytes(t.kp, t.np, t.ds);
   t.a.normpart = c_store < c ? ctx->norm_part : nullptr;
   const double by = 16.0 * ctx->n * (wsum + c_store * (beta_one ? 2.0 : 1.0));
   const int ph = prof_begin(ctx, KC_COMBINE_TC, count ? 8.0 * ctx->n * (double)wsum * c : 0.0, count ? by : 0.0,
                             c_store < c ? 2 : 1);
   switch (t.kp / 8) {
-    case 2: gplhr::tc_combine_kernel<2><<<grid, gplhr::TC_PIPE_THREADS, smem, ctx->stream>>>(ctx->n, t); break;
-    case 4: gplhr::tc_combine_kernel<4><<<grid, gplhr::TC_PIPE_THREADS, smem, ctx->stream>>>(ctx->n, t); break;
+    case 2:
+      if (two)
+        gplhr::tc_combine_kernel<2, 2><<<grid, gplhr::TC_PIPE_THREADS, smem, ctx->stream>>>(ctx->n, t);
+      else
+        gplhr::tc_combine_kernel<2><<<grid, gplhr::TC_PIPE_THREADS, smem, ctx->stream>>>(ctx->n, t);
+      break;
+    case 4:
+      if (two)
+        gplhr::tc_combine_kernel<4, 2><<<grid, gplhr::TC_PIPE_THREADS, smem, ctx->stream>>>(ctx->n, t);
+      else
+        gplhr::tc_combine_kernel<4><<<grid, gplhr::TC_PIPE_THREADS, smem, ctx->stream>>>(ctx->n, t);
+      break;
     case 6: gplhr::tc_combine_kernel<6><<<grid, gplhr::TC_PIPE_THREADS, smem, ctx->stream>>>(ctx->n, t); break;
     default: gplhr::tc_combine_kernel<8><<<grid, gplhr::TC_PIPE_THREADS, smem, ctx->stream>>>(ctx->n, t); break;
   }
@@ -2127,6 +2141,8 @@ gplhr_status set_smem_limits(gplhr_ctx* ctx) {
                           big));
   CK(cudaFuncSetAttribute(gplhr::invert_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::tc_combine_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::tc_combine_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(gplhr::tc_combine_kernel<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::tc_combine_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::tc_combine_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(gplhr::tc_combine_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));

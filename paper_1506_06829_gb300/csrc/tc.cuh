@@ -298,8 +298,10 @@ __device__ __forceinline__ void tc_row_load(const double2* const* colp, const in
   }
 }
 
-template <int KC>  // K' / 8 (2, 4, 6 or 8)
-__global__ void __launch_bounds__(TC_PIPE_THREADS, 1) tc_combine_kernel(int n, TcCombArgs ta) {
+// CPS: CTAs per SM (2 only at K' <= 32, N' = 16: 64 registers per thread, 4-column
+// epilogue groups; twice the warps to hide latency).
+template <int KC, int CPS = 1>  // K' / 8 (2, 4, 6 or 8)
+__global__ void __launch_bounds__(TC_PIPE_THREADS, CPS) tc_combine_kernel(int n, TcCombArgs ta) {
   const CombArgs& a = ta.a;
   if (a.skip && *a.skip == 0) return;
   extern __shared__ __align__(128) unsigned char tc_smem[];
@@ -388,7 +390,7 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) tc_combine_kernel(int n, T
     int it = 0, last_b = -1;
     uint32_t last_v = 0;
     bool mma_ok = true;  // thread 0: its last wait for a buffer succeeded
-    constexpr bool PF = KC == 2;  // registers allow the next tile's values ahead at K' = 16
+    constexpr bool PF = KC == 2 && CPS == 1;  // registers allow the next tile's values ahead
     double xn[PF ? 4 * KC : 1];
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
       const int s = it % ds;
@@ -530,14 +532,20 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) tc_combine_kernel(int n, T
       const bool valid = r < n;
       const int T = sRowT[slot][row_in], bad = sRowBad[slot][row_in];
       const uint32_t tb = tmem + lane_base + (uint32_t)(b * TC_DIAG * np);
-      for (int nb = 8 * eh; nb < np; nb += 16) {  // chunks of 8 real columns, alternating halves
-        uint32_t acc[TC_DIAG][8];
+      constexpr int CW = CPS == 1 ? 8 : 4;  // columns per chunk
+      for (int nb = CW * eh; nb < np; nb += 2 * CW) {  // chunks of CW real columns, alternating halves
+        uint32_t acc[TC_DIAG][CW];
 #pragma unroll
-        for (int d = 0; d < TC_DIAG; ++d) tmem_ld8(tb + (uint32_t)(d * np + nb), acc[d]);
+        for (int d = 0; d < TC_DIAG; ++d) {
+          if constexpr (CW == 8)
+            tmem_ld8(tb + (uint32_t)(d * np + nb), acc[d]);
+          else
+            tmem_ld4(tb + (uint32_t)(d * np + nb), acc[d]);
+        }
         tmem_wait_ld();
         if (!valid) continue;
 #pragma unroll
-        for (int uu = 0; uu < 8; uu += 2) {
+        for (int uu = 0; uu < CW; uu += 2) {
           const int nn = nb + uu, l = nn >> 1;
           if (l >= a.c) continue;
           double yv[2];
