@@ -46,6 +46,7 @@ TRAFFIC_64CUBED = {
     "gram_tc": 62.3e6,     # tc_gram_narrow_kernel / tc_gram_wide_kernel, 27 launches
     "combine_tc": 68.3e6,  # tc_combine_kernel, 31 launches
 }
+KCLASSES = ["spmm", "gram", "combine", "precond", "chol", "other", "gram_tc", "combine_tc"]
 TENSOR_CLASSES = ("gram_tc", "combine_tc")   # FP64 by integer digits on the tensor cores
 
 
