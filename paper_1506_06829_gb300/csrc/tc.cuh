@@ -934,15 +934,15 @@ __device__ __forceinline__ void tn_load1(const TcGramNArgs& ta, int r, int j, do
   v[3] = x1.y;
 }
 
-// The digits thread's tasks of the window at row r0: t = tid + 256 i -> (row pair t / W,
-// complex column t % W).
+// The digits thread's tasks of the window at row r0: task i is (row pair rp[i], complex
+// column j[i]) (rp[i] >= 64: no task).
 template <int NT>
-__device__ __forceinline__ void tn_load(const TcGramNArgs& ta, int r0, int tid, int W, double (&v)[NT][4]) {
+__device__ __forceinline__ void tn_load(const TcGramNArgs& ta, int r0, const int (&rp)[NT], const int (&j)[NT],
+                                        double (&v)[NT][4]) {
 #pragma unroll
   for (int i = 0; i < NT; ++i) {
-    const int t = tid + 256 * i, rp = t / W, j = t - rp * W;
-    if (rp < TN_WIN / 2) {
-      tn_load1(ta, r0 + 2 * rp, j, v[i]);
+    if (rp[i] < TN_WIN / 2) {
+      tn_load1(ta, r0 + 2 * rp[i], j[i], v[i]);
     } else {
 #pragma unroll
       for (int c = 0; c < 4; ++c) v[i][c] = 0.0;
@@ -997,10 +997,20 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
   if (warp < TN_DWARPS) {
     // ------------------------------------------------------------ digits role --
     int it = 0;
+    int trp[NT], tj[NT];  // this thread's tasks t = tid + 256 i: (row pair, complex column), every window
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+      const int t = tid + 256 * i;
+      trp[i] = t / W;
+      tj[i] = t - trp[i] * W;
+    }
+    // A lane a 2 wx + c of plane a lies a 2 wx 64 elements after lane c when 2 wx is a
+    // multiple of 8 (the core-matrix layout runs on across the 128-lane tiles)
+    const bool alin = (MX & 7) == 0;
     for (int win = blockIdx.x; win < nwin; win += gridDim.x, ++it) {
       const int slot = it % TN_RING, r0 = win * TN_WIN;
       double v[NT][4];  // this window's values, for the exponent pass (reloaded for the digits)
-      tn_load<NT>(ta, r0, tid, W, v);
+      tn_load<NT>(ta, r0, trp, tj, v);
       // the first stage free (the previous window's first-half products done): the
       // exponent slot of this window is then free too (its epilogue is four windows back)
       bool ok = bar_and(1, TN_DWARPS * 32, mbar_wait_bounded(&bar_dempty[0], (it & 1) ^ 1, &abort_s));
@@ -1018,7 +1028,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
       bar_and(1, TN_DWARPS * 32, true);
 #pragma unroll
       for (int i = 0; i < NT; ++i) {
-        const int t = tid + 256 * i, rp = t / W, j = t - rp * W;
+        const int rp = trp[i], j = tj[i];
         if (rp < TN_WIN / 2) {
           const int c = (j < wx ? 2 * j : MX + 2 * (j - wx));  // real columns c (Re), c + 1 (Im)
           const int tre = max(tc_top(v[i][0]), tc_top(v[i][1])), tim = max(tc_top(v[i][2]), tc_top(v[i][3]));
@@ -1039,7 +1049,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
         uint16_t* sB = sA + (size_t)mt * 128 * TN_HALF;
 #pragma unroll
         for (int i = 0; i < NT; ++i) {
-          const int t = tid + 256 * i, rp = t / W, j = t - rp * W;
+          const int rp = trp[i], j = tj[i];
           if (rp < TN_WIN / 2 && (rp >> 5) == h) {
             const int kk = 2 * (rp & 31);  // row within the half (even)
             double vv[4];
@@ -1051,19 +1061,19 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
               const int T = sE[slot][c];
               tc_digits(vv[2 * p], T, d0);
               tc_digits(vv[2 * p + 1], T, d1);
-              if (j < wx) {
+              if (j < wx) {  // lanes a 2 wx + c across the tiles: tc_off runs on past lane 127
+                const int base = tc_off(c, kk, 8);
 #pragma unroll
-                for (int a = 0; a < TC_DIGITS; ++a) {
-                  const int L = a * MX + c;
-                  *reinterpret_cast<uint32_t*>(sA + (size_t)(L >> 7) * 128 * TN_HALF + tc_off(L & 127, kk, 8)) =
+                for (int a = 0; a < TC_DIGITS; ++a)
+                  *reinterpret_cast<uint32_t*>(sA + (alin ? base + a * MX * 64 : tc_off(a * MX + c, kk, 8))) =
                       tc_pack2(d0[a], d1[a]);
-                }
               }
-              if (j >= wx || ta.self) {
+              if (j >= wx || ta.self) {  // rows b np + nn, np a multiple of 16
                 const int nn = j < wx ? c : c - MX;
+                const int base = tc_off(nn, kk, 8);
 #pragma unroll
                 for (int b = 0; b < TC_DIGITS; ++b)
-                  *reinterpret_cast<uint32_t*>(sB + tc_off(b * np + nn, kk, 8)) = tc_pack2(d0[b], d1[b]);
+                  *reinterpret_cast<uint32_t*>(sB + base + b * np * 64) = tc_pack2(d0[b], d1[b]);
               }
             }
           }
@@ -1315,6 +1325,10 @@ __global__ void __launch_bounds__(TW_THREADS, 1) tc_gram_wide_kernel(TcGramWArgs
   if (warp < TW_DWARPS) {
     // ------------------------------------------------------------ digits role --
     int it = 0;
+    // task t = tid + k DT is (row pair t / W, column t % W); when W divides DT the column is
+    // tid % W for every k and the row pair advances by DT / W
+    const bool wdiv = DT % W == 0;
+    const int jw = tid % W, rpw = tid / W, rstep = DT / W;
     for (int win = blockIdx.x; win < nwin; win += gridDim.x, ++it) {
       const int slot = it % TW_RING, r0 = win * TW_WIN, nr = min(TW_WIN, n - r0);
       // the exponent slot is free once the previous window's first stage was consumed
@@ -1378,11 +1392,12 @@ __global__ void __launch_bounds__(TW_THREADS, 1) tc_gram_wide_kernel(TcGramWArgs
         // tasks: (row pair, complex column), 16 W of them, four at a time: the loads of a
         // batch are all in flight before its digits are formed
         constexpr int TB = 4;
-        for (int t0 = tid; t0 < (TW_STAGE / 2) * W; t0 += TB * DT) {
+        for (int t0 = tid, kq = 0; t0 < (TW_STAGE / 2) * W; t0 += TB * DT, kq += TB) {
           double vv[TB][4];
 #pragma unroll
           for (int q = 0; q < TB; ++q) {
-            const int t = t0 + q * DT, rp = t / W, j = t - rp * W;
+            const int t = t0 + q * DT;
+            const int rp = wdiv ? rpw + (kq + q) * rstep : t / W, j = wdiv ? jw : t - rp * W;
             const int r = r0 + sc * TW_STAGE + 2 * rp;
             double2 x0 = make_double2(0.0, 0.0), x1 = x0;
             if (t < (TW_STAGE / 2) * W) {
@@ -1408,7 +1423,8 @@ __global__ void __launch_bounds__(TW_THREADS, 1) tc_gram_wide_kernel(TcGramWArgs
           }
 #pragma unroll
           for (int q = 0; q < TB; ++q) {
-            const int t = t0 + q * DT, rp = t / W, j = t - rp * W;
+            const int t = t0 + q * DT;
+            const int rp = wdiv ? rpw + (kq + q) * rstep : t / W, j = wdiv ? jw : t - rp * W;
             if (t >= (TW_STAGE / 2) * W) break;
             const int kk = 2 * rp;
 #pragma unroll
@@ -1424,11 +1440,12 @@ __global__ void __launch_bounds__(TW_THREADS, 1) tc_gram_wide_kernel(TcGramWArgs
                   *reinterpret_cast<uint32_t*>(sA + (size_t)a * 128 * TW_STAGE + tc_off(c, kk, TW_STAGE / 8)) =
                       tc_pack2(d0[a], d1[a]);
               }
-              if (j >= wx || ta.self) {
+              if (j >= wx || ta.self) {  // rows b np + nn, np a multiple of 16
                 const int nn = j < wx ? c : c - MX;
+                const int base = tc_off(nn, kk, TW_STAGE / 8);
 #pragma unroll
                 for (int b = 0; b < TC_DIGITS; ++b)
-                  *reinterpret_cast<uint32_t*>(sB + tc_off(b * np + nn, kk, TW_STAGE / 8)) = tc_pack2(d0[b], d1[b]);
+                  *reinterpret_cast<uint32_t*>(sB + base + b * np * (TW_STAGE / 8) * 8) = tc_pack2(d0[b], d1[b]);
               }
             }
           }
