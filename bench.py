@@ -315,13 +315,15 @@ def main():
 
 
 def timed_iterations(G, pr, K, W, stream, precision, barrier, local, world, dev):
-    """K timed GPLHR iterations after W warm-up ones (CUDA events on the library stream),
-    with the library's per-kernel-class event timing over the same region."""
+    """K timed GPLHR iterations after W warm-up ones (CUDA events on the library stream;
+    the iteration's device segments replayed from CUDA graphs), then K more with the
+    library's per-kernel-class event timing (which issues every kernel on its own)."""
     import torch
     import torch.distributed as dist
     extra = {"switch_tol": 1e-300, "stall_iters": -1} if precision == "mixed" else {}
     solver = G.GPLHR(pr.A, pr.B, pr.sigma, pr.k, pr.m, pr.precond, pr.block_size, tol=pr.tol,
-                     maxit=10 ** 6, stream=stream.cuda_stream, precision=precision, autotune=True, **extra)
+                     maxit=10 ** 6, stream=stream.cuda_stream, precision=precision, autotune=True, graphs=True,
+                     **extra)
     tuned = {}
     for w in sorted({pr.k, max(1, pr.k // 2), 1}):
         t, g, us, ud = G.gplhr_spmm_shape(solver.ctx, w, precision == "mixed")
@@ -334,7 +336,6 @@ def timed_iterations(G, pr, K, W, stream, precision, barrier, local, world, dev)
     time.sleep(0.3)
     barrier()
     torch.cuda.synchronize()
-    G.gplhr_profile(solver.ctx, True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     it_before = solver.iterate(0).iters
     ev0.record(stream)
@@ -353,6 +354,13 @@ def timed_iterations(G, pr, K, W, stream, precision, barrier, local, world, dev)
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+    # the same K iterations again with per-kernel-class CUDA events (the roofline's region)
+    G.gplhr_profile(solver.ctx, True)
+    it_before = solver.iterate(0).iters
+    info = solver.iterate(K)
+    torch.cuda.synchronize()
+    if info.iters - it_before != K:
+        raise RuntimeError("the profiled iterations stopped early")
     per_class = {}
     for c in KCLASSES:
         cms, nl, fl, by = G.gplhr_profile_read(solver.ctx, c)
@@ -458,7 +466,7 @@ def time_to_pairs(G, stream, precision, inner_steps=0):
     from paper_1506_06829_gb300 import problems as P
     pr = P.config3()
     s = G.GPLHR(pr.A, None, pr.sigma, pr.k, pr.m, pr.precond, pr.block_size, tol=pr.tol,
-                maxit=2000, stream=stream.cuda_stream, precision=precision, inner_steps=inner_steps)
+                maxit=2000, stream=stream.cuda_stream, precision=precision, inner_steps=inner_steps, graphs=True)
     V0 = torch.from_numpy(pr.start_block()).to("cuda")
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
