@@ -117,12 +117,13 @@ typedef struct {
                           U^*(A - sigma B)Z from the factors of U's construction (Prop. 3.2
                           and the orthonormalisation of (A - sigma B)[W S P]); 1 = both
                           U^*AZ and U^*BZ by Gram products (Alg. 2 step 24 as printed)   */
-  int32_t fp64_gemm;   /* [0]    FP64 block combinations: 0 = on the tensor cores (tcgen05,
-                          each double split into 7 balanced 8-bit integer digits, exact
-                          FP32 accumulation of digit-pair products, error at most
-                          (K'/4 + 2) 2^-53 max|x| sum|c| over K' real terms, below the
-                          DFMA bound) where the shape allows (<= 32 input and output
-                          columns, n >= 512), DFMA otherwise; 1 = DFMA only               */
+  int32_t fp64_gemm;   /* [0]    FP64 block combinations and Gram products: 0 = on the
+                          tensor cores (tcgen05, each double split into 7 balanced 8-bit
+                          integer digits, exact accumulation of digit-pair products; a
+                          combination's error is at most (K'/4 + 2) 2^-53 max|x| sum|c|
+                          over K' real terms, below the DFMA bound) where the shape allows
+                          (combinations: <= 32 input and output columns, n >= 512; Gram
+                          products: see gplhr_gram), DFMA otherwise; 1 = DFMA only       */
   int32_t graphs;      /* [0]    1 = capture the device work of each iteration between its
                           host round trips (three segments) in CUDA graphs on first use
                           and replay them afterwards: one graph launch instead of tens of
@@ -288,9 +289,12 @@ gplhr_status gplhr_precond_apply(gplhr_ctx* ctx, const void* X, int32_t ldx, int
  * into FP64 (the Cholesky-QR Grams and pencil of the bulk phase, whose blocks hold
  * FP32 values); GPLHR_GRAM_TENSOR (3) the FP64 product as the iteration forms it: on the
  * tensor cores (each double split into 7 integer digits against a per-column exponent
- * over 128-row windows, exact FP32 accumulation of digit products, one rounding per
- * window, FP64 sums of the windows) when wx <= 128, wy <= 32, wx wy >= 400, n >= 2048
- * and opts.fp64_gemm = 0, else DFMA.  EINVAL for wx > max((m+3)k, 128) or wy > 2 (m+3)k. */
+ * over 128-row windows, exact accumulation of digit products, one rounding per window,
+ * FP64 sums of the windows) when n >= 2048, opts.fp64_gemm = 0 and the shape fits one of
+ * the forms: wx <= 24, wy <= 16 and at most 32 loaded columns (wx + wy, or wx when Y is
+ * X); the same with X and Y exchanged (C formed as (Y^* X)^*); wx <= 64, wy <= 32,
+ * wx wy >= 128; wx <= 128, wy <= 32, wx wy >= 400.  Else DFMA.  EINVAL for
+ * wx > max((m+3)k, 128) or wy > 2 (m+3)k. */
 enum { GPLHR_GRAM_FP64 = 0, GPLHR_GRAM_FP32 = 1, GPLHR_GRAM_EXACT32 = 2, GPLHR_GRAM_TENSOR = 3 };
 gplhr_status gplhr_gram(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t wx, const void* Y,
                         int32_t ldy, int32_t wy, void* C, int32_t arith);
