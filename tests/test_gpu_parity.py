@@ -489,8 +489,13 @@ def _dot2_product(X, C):
 
 
 
-@pytest.mark.parametrize("n,w,c,beta", [(5000, 8, 8, False), (100003, 32, 16, True), (4099, 17, 5, False),
-                                        (2048, 32, 32, True), (777, 24, 40, False)])
+@pytest.mark.parametrize("n,w,c,beta", [
+    (5000, 8, 8, False),      # K' = 16, N' = 16: two CTAs per SM
+    (30001, 16, 8, True),     # K' = 32, N' = 16: two CTAs per SM, one digit stage each
+    (6007, 12, 16, False),    # K' = 32, N' = 32
+    (9000, 8, 12, True),      # K' = 16, N' = 32: next tile's rows loaded a tile ahead
+    (1000, 3, 2, True),       # fewer tiles than CTAs
+    (100003, 32, 16, True), (4099, 17, 5, False), (2048, 32, 32, True), (777, 24, 40, False)])
 def test_combine_tensor_and_dfma_match_fp64(n, w, c, beta):
     """Y = X C (+ Y) on the tensor cores (integer digits, FP32 accumulation) and by DFMA
     against numpy's FP64 product.  Rows span 1e-30 .. 1e30 and include zero rows, C has
