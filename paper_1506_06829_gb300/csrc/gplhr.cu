@@ -1845,8 +1845,12 @@ gplhr_status eig_run(gplhr_ctx* ctx, int niter, gplhr_info* info, bool* conv_out
 
 // ------------------------------------------------------------------ setup ----
 
-gplhr_status validate_csr(const gplhr_csr* M, int64_t n, std::string& err, std::vector<int>& rp,
-                          std::vector<int>& ci) {
+// Checks a CSR descriptor; rp / ci point at its row pointers and column indices on the host
+// (the caller's arrays, or copies in rpv / civ when they live on the device).  The rows are
+// checked in a fixed number of ranges on host threads; the lowest failing range's error is
+// the one reported.
+gplhr_status validate_csr(const gplhr_csr* M, int64_t n, std::string& err, std::vector<int>& rpv,
+                          std::vector<int>& civ, const int*& rp, const int*& ci) {
   if (!M || M->n != n || M->nnz < 0 || !M->rowptr || (M->nnz > 0 && (!M->colind || !M->vals))) {
     err = "invalid CSR descriptor";
     return GPLHR_EINVAL;
@@ -1855,41 +1859,88 @@ gplhr_status validate_csr(const gplhr_csr* M, int64_t n, std::string& err, std::
     err = "CSR dtype must be GPLHR_R64 or GPLHR_C128";
     return GPLHR_EINVAL;
   }
-  rp.resize(n + 1);
-  ci.resize(M->nnz);
   if (M->on_device) {
-    if (cudaMemcpy(rp.data(), M->rowptr, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+    rpv.resize(n + 1);
+    civ.resize(M->nnz);
+    if (cudaMemcpy(rpv.data(), M->rowptr, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
         (M->nnz > 0 &&
-         cudaMemcpy(ci.data(), M->colind, M->nnz * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)) {
+         cudaMemcpy(civ.data(), M->colind, M->nnz * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)) {
       err = "cannot read device CSR arrays";
       return GPLHR_ECUDA;
     }
+    rp = rpv.data();
+    ci = civ.data();
   } else {
-    std::memcpy(rp.data(), M->rowptr, (n + 1) * sizeof(int));
-    if (M->nnz > 0) std::memcpy(ci.data(), M->colind, M->nnz * sizeof(int));
+    rp = static_cast<const int*>(M->rowptr);
+    ci = static_cast<const int*>(M->colind);
   }
   if (rp[0] != 0 || rp[n] != M->nnz) {
     err = "CSR rowptr must start at 0 and end at nnz";
     return GPLHR_EINVAL;
   }
-  for (int64_t i = 0; i < n; ++i) {
-    if (rp[i + 1] < rp[i]) {
-      err = "CSR rowptr not monotone";
+  const int parts = M->nnz < (int64_t)1 << 20 ? 1 : 8;
+  std::vector<int> bad(parts, 0);  // 1: rowptr not monotone, 2: column indices
+  auto work = [&](int p) {
+    const int64_t r0 = n * p / parts, r1 = n * (p + 1) / parts;
+    for (int64_t i = r0; i < r1 && !bad[p]; ++i) {
+      if (rp[i + 1] < rp[i] || rp[i + 1] > M->nnz) {  // (no index beyond nnz is read)
+        bad[p] = 1;
+        break;
+      }
+      for (int j = rp[i]; j < rp[i + 1]; ++j)
+        if (ci[j] < 0 || ci[j] >= n || (j > rp[i] && ci[j] <= ci[j - 1])) {
+          bad[p] = 2;
+          break;
+        }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int p = 1; p < parts; ++p) pool.emplace_back(work, p);
+  work(0);
+  for (auto& t : pool) t.join();
+  for (int p = 0; p < parts; ++p) {
+    if (bad[p] == 1) {
+      err = "CSR rowptr not monotone or beyond nnz";
       return GPLHR_EINVAL;
     }
-    for (int j = rp[i]; j < rp[i + 1]; ++j) {
-      if (ci[j] < 0 || ci[j] >= n || (j > rp[i] && ci[j] <= ci[j - 1])) {
-        err = "CSR column indices out of range or not strictly increasing in a row";
-        return GPLHR_EINVAL;
-      }
+    if (bad[p] == 2) {
+      err = "CSR column indices out of range or not strictly increasing in a row";
+      return GPLHR_EINVAL;
     }
   }
   return GPLHR_OK;
 }
 
+// max_j sum_i |m_ij| over a CSR matrix: a fixed number of row ranges, one per host thread,
+// each summing its columns into its own array; the arrays are then added in range order, so
+// the result does not depend on the scheduling.
+double csr_onenorm(int64_t n, int64_t nnz, const int* rp, const int* ci, const double* vals, bool cplx) {
+  const int parts = nnz < (int64_t)1 << 20 ? 1 : 8;
+  std::vector<std::vector<double>> part(parts, std::vector<double>(n, 0.0));
+  auto work = [&](int p) {
+    const int64_t r0 = n * p / parts, r1 = n * (p + 1) / parts;
+    std::vector<double>& cs = part[p];
+    for (int64_t r = r0; r < r1; ++r)
+      for (int64_t e = rp[r]; e < rp[r + 1]; ++e)
+        cs[ci[e]] += cplx ? std::hypot(vals[2 * e], vals[2 * e + 1]) : std::fabs(vals[e]);
+  };
+  std::vector<std::thread> pool;
+  for (int p = 1; p < parts; ++p) pool.emplace_back(work, p);
+  work(0);
+  for (auto& t : pool) t.join();
+  double mx = 0.0;
+  for (int64_t c = 0; c < n; ++c) {
+    double v = 0.0;
+    for (int p = 0; p < parts; ++p) v += part[p][c];
+    mx = std::max(mx, v);
+  }
+  return mx;
+}
+
 gplhr_status upload_csr(gplhr_ctx* ctx, const gplhr_csr* M, DevCsr& D, double* onenorm) {
-  std::vector<int> rp, ci;
-  gplhr_status st = validate_csr(M, ctx->n, ctx->err, rp, ci);
+  std::vector<int> rpv, civ;
+  const int *rp = nullptr, *ci = nullptr;
+  gplhr_status st = validate_csr(M, ctx->n, ctx->err, rpv, civ, rp, ci);
   if (st != GPLHR_OK) return st;
   const int64_t n = ctx->n, nnz = M->nnz;
   const size_t vsz = M->dtype == GPLHR_C128 ? 16 : 8;
@@ -1898,22 +1949,20 @@ gplhr_status upload_csr(gplhr_ctx* ctx, const gplhr_csr* M, DevCsr& D, double* o
   CK(cudaMalloc(&D.rowptr, (n + 1) * sizeof(int)));
   CK(cudaMalloc(&D.col, std::max<int64_t>(nnz, 1) * sizeof(int)));
   CK(cudaMalloc(&D.val, std::max<int64_t>(nnz, 1) * vsz));
-  CK(cudaMemcpy(D.rowptr, rp.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(D.rowptr, rp, (n + 1) * sizeof(int), cudaMemcpyHostToDevice));
   if (nnz > 0) {
-    CK(cudaMemcpy(D.col, ci.data(), nnz * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(D.col, ci, nnz * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(D.val, M->vals, nnz * vsz, M->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
   }
-  if (onenorm) {  // ||M||_1 = max column sum of |m_ij|, on the host copy
-    std::vector<double> vals(nnz * (vsz / 8));
-    if (nnz > 0) CK(cudaMemcpy(vals.data(), D.val, nnz * vsz, cudaMemcpyDeviceToHost));
-    std::vector<double> colsum(n, 0.0);
-    for (int64_t j = 0; j < nnz; ++j) {
-      const double a = vsz == 16 ? std::hypot(vals[2 * j], vals[2 * j + 1]) : std::fabs(vals[j]);
-      colsum[ci[j]] += a;
+  if (onenorm) {  // ||M||_1 = max column sum of |m_ij|, on the host
+    std::vector<double> dvals;
+    const double* vals = static_cast<const double*>(M->vals);
+    if (M->on_device) {
+      dvals.resize(nnz * (vsz / 8));
+      if (nnz > 0) CK(cudaMemcpy(dvals.data(), D.val, nnz * vsz, cudaMemcpyDeviceToHost));
+      vals = dvals.data();
     }
-    double mx = 0.0;
-    for (double v : colsum) mx = std::max(mx, v);
-    *onenorm = mx;
+    *onenorm = csr_onenorm(n, nnz, rp, ci, vals, vsz == 16);
   }
   return GPLHR_OK;
 }
@@ -2164,9 +2213,14 @@ gplhr_status load_V0(gplhr_ctx* ctx, const void* V0, int where, int is_complex, 
     return GPLHR_OK;
   }
   const cudaMemcpyKind kind = where == GPLHR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if (is_complex) {
+  if (is_complex && where == GPLHR_DEVICE) {
     CK(cudaMemcpy2DAsync(ctx->Z, ctx->s_max * sizeof(double2), V0, k * sizeof(double2), k * sizeof(double2), n,
                          kind, ctx->stream));
+  } else if (is_complex) {  // one contiguous copy from the host, then spread to the row stride of Z
+    CK(cudaMemcpyAsync(ctx->Tw1, V0, (size_t)n * k * sizeof(double2), kind, ctx->stream));
+    gplhr::copy_block_kernel<<<grid_for((size_t)n * k, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+        n, k, ctx->Tw1, k, ctx->Z, ctx->s_max);
+    CK(cudaGetLastError());
   } else {
     CK(cudaMemcpyAsync(ctx->Tw1, V0, (size_t)n * k * sizeof(double), kind, ctx->stream));
     gplhr::real_to_complex_kernel<<<grid_for((size_t)n * k, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
@@ -2467,10 +2521,26 @@ gplhr_status gplhr_vectors(gplhr_ctx* ctx, double* alpha, double* beta, double* 
       lambda[2 * j + 1] = l.imag();
     }
   }
-  if (V) CK(cudaMemcpy2DAsync(V, k * sizeof(double2), ctx->Z, ctx->s_max * sizeof(double2), k * sizeof(double2), n,
-                              d2x, ctx->stream));
-  if (Q) CK(cudaMemcpy2DAsync(Q, k * sizeof(double2), ctx->U, ctx->s_max * sizeof(double2), k * sizeof(double2), n,
-                              d2x, ctx->stream));
+  // V, Q: the first k columns of Z, U (row stride s_max).  To the host they are packed into
+  // a contiguous scratch block first (a strided copy of n rows of 16 k bytes each to
+  // pageable memory is slow), then copied in one piece; the scratch is stream-ordered
+  // against the copies.
+  const struct {
+    void* dst;
+    const double2* src;
+  } outs[2] = {{V, ctx->Z}, {Q, ctx->U}};
+  for (const auto& o : outs) {
+    if (!o.dst) continue;
+    if (where == GPLHR_DEVICE) {
+      CK(cudaMemcpy2DAsync(o.dst, k * sizeof(double2), o.src, ctx->s_max * sizeof(double2), k * sizeof(double2), n,
+                           d2x, ctx->stream));
+    } else {
+      gplhr::copy_block_kernel<<<grid_for((size_t)n * k, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+          n, k, o.src, ctx->s_max, ctx->Tw1, k);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(o.dst, ctx->Tw1, (size_t)n * k * sizeof(double2), d2x, ctx->stream));
+    }
+  }
   SqMat Rout = ctx->RA, RBout = ctx->RB;
   if (!ctx->hasB) {  // B = I: R = M_A M_B^{-1} (A V M_B = V M_A, Eq. gschur2), RB = I
     SqMat Minv = SqMat::eye(k);
