@@ -1,6 +1,6 @@
-// FP64 block combination Y = beta Y + sum_t alpha_t X_t C_t on GB300's tensor cores
-// (tcgen05, bf16 operands, FP32 accumulators in tensor memory), accurate to FP64 working
-// precision by splitting every double into small integer digits.
+// FP64 block combinations Y = beta Y + sum_t alpha_t X_t C_t and Gram products C = X^* Y on
+// GB300's tensor cores (tcgen05, bf16 operands, FP32 accumulators in tensor memory),
+// accurate to FP64 working precision by splitting every double into small integer digits.
 //
 // Scheme (per tile of 128 rows; K' = 2 sum w_t real columns, N' = 2 c real columns):
 // * complex to real: a row of [X_0 X_1 ...] is the K' doubles (Re, Im, Re, Im, ...),
@@ -18,6 +18,17 @@
 //   |D_d| < 7 2^20: every FP32 partial sum is an exact integer;
 // * y = 2^(T_r + G_n - 68) Z, Z = sum_d D_d 256^(7 - d) formed exactly in 96-bit
 //   integer arithmetic and rounded once to double (nearest, ties to even).
+// The Gram products C = X^* Y use the same digits with the contraction over the rows (per-
+// column exponent bounds over 128-row windows); see the Gram kernels below.
+//
+// Kernels in this file, all persistent with one (or two) CTAs per SM and every wait on an
+// mbarrier bounded:
+// * tc_combine_kernel<K'/8, CTAs per SM>: the combination, digit warps + epilogue warps;
+// * tc_gram_narrow_kernel<tasks>: Gram products of narrow blocks (digit planes stacked
+//   along M and N, exact integer diagonal sums in shared memory), with an MMA-issue warp;
+// * tc_gram_wide_kernel: wider Gram products (the combination's layout, diagonals formed
+//   by the MMA), with an MMA-issue warp;
+// * tc_gram_kernel: the first, serial Gram form, for X up to 128 columns.
 // Error per output: input rounding <= 2^-55 (max_k |x_rk| sum_k |c_kn| + K' max_k |x_rk|
 // max_k |c_kn|), the dropped pairs a + b >= 8 (weight <= 2^-62 K' 2^(T_r + G_n) in all),
 // and the final rounding: at most (K'/4 + 2) u max_k |x_rk| sum_k |c_kn| with u = 2^-53,
