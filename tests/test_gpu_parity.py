@@ -495,6 +495,8 @@ def _dot2_product(X, C):
     (6007, 12, 16, False),    # K' = 32, N' = 32
     (9000, 8, 12, True),      # K' = 16, N' = 32: next tile's rows loaded a tile ahead
     (1000, 3, 2, True),       # fewer tiles than CTAs
+    (30011, 16, 24, True),    # N' = 48: integer final rounding
+    (5003, 8, 32, False),     # N' = 64: integer final rounding
     (100003, 32, 16, True), (4099, 17, 5, False), (2048, 32, 32, True), (777, 24, 40, False)])
 def test_combine_tensor_and_dfma_match_fp64(n, w, c, beta):
     """Y = X C (+ Y) on the tensor cores (integer digits, FP32 accumulation) and by DFMA
