@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, CPS) tc_combine_kernel(int n,
   __shared__ __align__(8) uint64_t bar_dempty[2], bar_tfull[2], bar_tempty[2], bar_row[TC_RING];
   __shared__ uint32_t taddr_s;
   __shared__ volatile int abort_s;
-  __shared__ double nsum[COMB_MAX_NORMS];
+  __shared__ double nwarp[TC_EWARPS][COMB_MAX_NORMS];  // norm columns: one partial per epilogue warp
   __shared__ const double2* colp[TC_KMAX / 2];
   __shared__ int coll[TC_KMAX / 2];
   __shared__ int sG[TC_NMAX], sBadC[TC_NMAX];
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, CPS) tc_combine_kernel(int n,
   int wsum = 0;
   for (int t = 0; t < a.nin; ++t) wsum += a.in[t].w;
   const int nnorm = a.c - a.c_store;
-  for (int e = tid; e < nnorm; e += TC_PIPE_THREADS) nsum[e] = 0.0;
+  for (int e = tid; e < TC_EWARPS * nnorm; e += TC_PIPE_THREADS) nwarp[e / nnorm][e % nnorm] = 0.0;
   if (tid < TC_KMAX / 2) {  // where input column j of the stacked row lives
     const double2* p = nullptr;
     int ld = 0;
@@ -524,6 +524,12 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, CPS) tc_combine_kernel(int n,
     const int ew = warp - TC_DWARPS, q4 = warp & 3, eh = ew >> 2;
     const int row_in = q4 * 32 + lane;
     const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
+    constexpr int CW = CPS == 1 ? 8 : 4;  // columns per chunk
+    // |y|^2 of this thread's rows in its norm columns, summed over its tiles (column
+    // index: chunk (nb - CW eh) / (2 CW), complex column within it; <= 16 at N' <= 64)
+    double nacc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) nacc[i] = 0.0;
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
       const int b = it % ts, slot = it % TC_RING;
@@ -543,7 +549,6 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, CPS) tc_combine_kernel(int n,
       const bool valid = r < n;
       const int T = sRowT[slot][row_in], bad = sRowBad[slot][row_in];
       const uint32_t tb = tmem + lane_base + (uint32_t)(b * TC_DIAG * np);
-      constexpr int CW = CPS == 1 ? 8 : 4;  // columns per chunk
       for (int nb = CW * eh; nb < np; nb += 2 * CW) {  // chunks of CW real columns, alternating halves
         uint32_t acc[TC_DIAG][CW];
 #pragma unroll
@@ -580,20 +585,33 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, CPS) tc_combine_kernel(int n,
             }
             *dst = y;
           } else {
-            atomicAdd(&nsum[l - a.c_store], y.x * y.x + y.y * y.y);
+            nacc[((nb - CW * eh) / (2 * CW)) * (CW / 2) + uu / 2] += y.x * y.x + y.y * y.y;
           }
         }
       }
       tc_fence_before();
       mbar_arrive(&bar_tempty[b]);
     }
+    // norm columns: the warp's rows summed by a fixed shuffle tree into the warp's slot
+    if (nnorm > 0)
+      for (int ci = 0; ci < 16; ++ci) {
+        const int nb = CW * eh + 2 * CW * (ci / (CW / 2)), l = (nb >> 1) + ci % (CW / 2);
+        if (nb >= np || l < a.c_store || l >= a.c) continue;  // the same in the whole warp
+        double sv = nacc[ci];
+        for (int off = 16; off > 0; off >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, off);
+        if (lane == 0) nwarp[ew][l - a.c_store] = sv;
+      }
   }
   __syncthreads();
   tc_fence_after();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ta.tmem_cols)
                               : "memory");
-  if (a.normpart)
-    for (int e = tid; e < nnorm; e += TC_PIPE_THREADS) a.normpart[(size_t)blockIdx.x * nnorm + e] = nsum[e];
+  if (a.normpart)  // the epilogue warps' partials, added in a fixed order
+    for (int e = tid; e < nnorm; e += TC_PIPE_THREADS) {
+      double sv = 0.0;
+      for (int w = 0; w < TC_EWARPS; ++w) sv += nwarp[w][e];
+      a.normpart[(size_t)blockIdx.x * nnorm + e] = sv;
+    }
 }
 
 // ------------------------------------------------ Gram products on the tensor cores --
