@@ -545,7 +545,7 @@ bool gram_tc_fits(const gplhr_ctx* ctx, int wx, int wy) {
 }
 
 gplhr_status gram_tc(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy1, double2* C, const int* skip,
-                     int nout_count, bool count) {
+                     int nout_count, bool count, int ldc) {
   gplhr::TcGramArgs t{};
   const int wy = wy0 + wy1;
   t.n = ctx->n;
@@ -574,7 +574,7 @@ gplhr_status gram_tc(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int
   CK(cudaGetLastError());
   const int nout = wx * wy;
   gplhr::gram_reduce_kernel<<<(nout + gplhr::GRED_WARPS - 1) / gplhr::GRED_WARPS, 32 * gplhr::GRED_WARPS, 0,
-                               ctx->stream>>>(grid, nout, wx, wy, 0, ctx->gram_part, C, skip);
+                               ctx->stream>>>(grid, nout, wx, wy, 0, ctx->gram_part, C, ldc, skip);
   prof_end(ctx, ph);
   CK(cudaGetLastError());
   return GPLHR_OK;
@@ -608,7 +608,7 @@ bool gram_tn_fits(const gplhr_ctx* ctx, int wx, int wy, bool self, TnShape* sh =
 
 // trans: X and Y0 were swapped by the caller (C = (Y0^* X)^*), the reduction writes C.
 gplhr_status gram_tn(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy1, double2* C, const int* skip,
-                     int nout_count, bool count, bool self, const TnShape& sh, bool trans = false) {
+                     int nout_count, bool count, bool self, const TnShape& sh, int ldc, bool trans = false) {
   gplhr::TcGramNArgs t{};
   const int wy = wy0 + wy1;
   t.n = ctx->n;
@@ -640,7 +640,7 @@ gplhr_status gram_tn(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int
   CK(cudaGetLastError());
   const int nout = wx * wy;
   gplhr::gram_reduce_kernel<<<(nout + gplhr::GRED_WARPS - 1) / gplhr::GRED_WARPS, 32 * gplhr::GRED_WARPS, 0,
-                               ctx->stream>>>(grid, nout, wx, wy, trans ? 2 : 0, ctx->gram_part, C, skip);
+                               ctx->stream>>>(grid, nout, wx, wy, trans ? 2 : 0, ctx->gram_part, C, ldc, skip);
   prof_end(ctx, ph);
   CK(cudaGetLastError());
   return GPLHR_OK;
@@ -660,8 +660,9 @@ bool gram_tw_fits(const gplhr_ctx* ctx, int wx, int wy, bool self) {
          ctx->gram_part_elems;
 }
 
+// trans: X and Y0 were swapped by the caller (C = (Y0^* X)^*), the reduction writes C.
 gplhr_status gram_tw(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy1, double2* C, const int* skip,
-                     int nout_count, bool count, bool self) {
+                     int nout_count, bool count, bool self, int ldc, bool trans = false) {
   gplhr::TcGramWArgs t{};
   const int wy = wy0 + wy1;
   t.n = ctx->n;
@@ -690,33 +691,55 @@ gplhr_status gram_tw(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int
   CK(cudaGetLastError());
   const int nout = wx * wy;
   gplhr::gram_reduce_kernel<<<(nout + gplhr::GRED_WARPS - 1) / gplhr::GRED_WARPS, 32 * gplhr::GRED_WARPS, 0,
-                               ctx->stream>>>(grid, nout, wx, wy, 0, ctx->gram_part, C, skip);
+                               ctx->stream>>>(grid, nout, wx, wy, trans ? 2 : 0, ctx->gram_part, C, ldc, skip);
   prof_end(ctx, ph);
   CK(cudaGetLastError());
   return GPLHR_OK;
 }
 
+// C (wx x wy, row stride ldc, wy when ldc < 0) = X^* [Y0 Y1].  The FP64 product (mode 0)
+// goes to the tensor cores when a form fits: narrow, narrow transposed, wide, wide
+// transposed, serial; a product with more than 32 columns of [Y0 Y1] is computed in
+// column blocks of at most 32, each into its columns of C; else DFMA.
 gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy1, double2* C,
                   const int* skip = nullptr, bool herm = false, bool count = true, bool fp32 = false,
-                  int force_mode = -1) {
+                  int force_mode = -1, int ldc = -1) {
   const int mode = force_mode >= 0 ? force_mode : (fp32 ? 1 : (ctx->bulk32 ? 2 : 0));
   const int wy = wy0 + wy1;
+  if (ldc < 0) ldc = wy;
   const bool self = X.p == Y0.p && X.ld == Y0.ld && wy0 == wx && wy1 == 0;
+  const bool tcok = mode == 0 && force_mode < 0;
   TnShape tn;
-  if (mode == 0 && force_mode < 0 && gram_tn_fits(ctx, wx, wy, self, &tn)) {
-    const bool h = herm && self;
-    return gram_tn(ctx, X, wx, Y0, wy0, Y1, wy1, C, skip, h ? wx * (wx + 1) / 2 : wx * wy, count, self, tn);
-  }
-  if (mode == 0 && force_mode < 0 && wy1 == 0 && !self && gram_tn_fits(ctx, wy0, wx, false, &tn))
-    return gram_tn(ctx, Y0, wy0, X, wx, Blk{nullptr, 0}, 0, C, skip, wx * wy, count, false, tn, true);
-  if (mode == 0 && force_mode < 0 && gram_tw_fits(ctx, wx, wy, self)) {
-    const bool h = herm && self;
-    return gram_tw(ctx, X, wx, Y0, wy0, Y1, wy1, C, skip, h ? wx * (wx + 1) / 2 : wx * wy, count, self);
-  }
-  if (mode == 0 && force_mode < 0 && gram_tc_fits(ctx, wx, wy)) {
-    // (a Hermitian request gets the full product; the algorithmic count stays the half)
-    const bool h = herm && wy1 == 0 && wy0 == wx;
-    return gram_tc(ctx, X, wx, Y0, wy0, Y1, wy1, C, skip, h ? wx * (wx + 1) / 2 : wx * wy, count);
+  // (a Hermitian request gets the full product on the tensor cores; the algorithmic count
+  // stays the half)
+  const int nout_tc = herm && self ? wx * (wx + 1) / 2 : wx * wy;
+  if (tcok && gram_tn_fits(ctx, wx, wy, self, &tn))
+    return gram_tn(ctx, X, wx, Y0, wy0, Y1, wy1, C, skip, nout_tc, count, self, tn, ldc);
+  if (tcok && wy1 == 0 && !self && gram_tn_fits(ctx, wy0, wx, false, &tn))
+    return gram_tn(ctx, Y0, wy0, X, wx, Blk{nullptr, 0}, 0, C, skip, wx * wy, count, false, tn, ldc, true);
+  if (tcok && gram_tw_fits(ctx, wx, wy, self))
+    return gram_tw(ctx, X, wx, Y0, wy0, Y1, wy1, C, skip, nout_tc, count, self, ldc);
+  if (tcok && wy1 == 0 && !self && gram_tw_fits(ctx, wy0, wx, false))
+    return gram_tw(ctx, Y0, wy0, X, wx, Blk{nullptr, 0}, 0, C, skip, wx * wy, count, false, ldc, true);
+  if (tcok && gram_tc_fits(ctx, wx, wy))
+    return gram_tc(ctx, X, wx, Y0, wy0, Y1, wy1, C, skip, nout_tc, count, ldc);
+  if (tcok && ctx->tc && wy > gplhr::TW_YMAX && ctx->n >= 2048 && wx <= gplhr::TG_AMAX) {
+    for (int c0 = 0; c0 < wy; c0 += gplhr::TW_YMAX) {  // column blocks of [Y0 Y1]
+      const int c1 = std::min(wy, c0 + gplhr::TW_YMAX);
+      // the block's columns of Y0, then of Y1 (either part may be empty)
+      const int a0 = std::min(c0, wy0), a1 = std::min(c1, wy0);
+      const int e0 = std::max(c0, wy0) - wy0, e1 = std::max(c1, wy0) - wy0;
+      Blk p0{Y0.p + a0, Y0.ld}, p1{e1 > e0 ? Y1.p + e0 : nullptr, Y1.ld};
+      int n0 = a1 - a0, n1 = e1 - e0;
+      if (n0 == 0) {
+        p0 = p1;
+        n0 = n1;
+        p1 = Blk{nullptr, 0};
+        n1 = 0;
+      }
+      TRY(gram(ctx, X, wx, p0, n0, p1, n1, C + c0, skip, false, count, fp32, -1, ldc));
+    }
+    return GPLHR_OK;
   }
   if (herm && (wy1 != 0 || wy0 != wx)) herm = false;
   const int nout = herm ? wx * (wx + 1) / 2 : wx * wy;
@@ -749,7 +772,7 @@ gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy
   }
   CK(cudaGetLastError());
   gplhr::gram_reduce_kernel<<<(nout + gplhr::GRED_WARPS - 1) / gplhr::GRED_WARPS, 32 * gplhr::GRED_WARPS, 0,
-                               ctx->stream>>>(nchunk, nout, wx, wy, herm ? 1 : 0, ctx->gram_part, C, skip);
+                               ctx->stream>>>(nchunk, nout, wx, wy, herm ? 1 : 0, ctx->gram_part, C, ldc, skip);
   prof_end(ctx, ph);
   CK(cudaGetLastError());
   return GPLHR_OK;
@@ -2848,7 +2871,7 @@ gplhr_status gplhr_gram_noalloc(int64_t n, const void* X, int32_t ldx, int32_t w
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
     gplhr::gram_reduce_kernel<<<(nout + gplhr::GRED_WARPS - 1) / gplhr::GRED_WARPS, 32 * gplhr::GRED_WARPS, 0,
-                                 strm>>>(nchunk, nout, wx, wy, 0, scratch, (double2*)C, nullptr);
+                                 strm>>>(nchunk, nout, wx, wy, 0, scratch, (double2*)C, wy, nullptr);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {

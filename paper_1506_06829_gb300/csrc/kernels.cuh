@@ -460,8 +460,10 @@ gram_partial_x32_kernel(int n, int rows_per_chunk, const double2* __restrict__ X
 // mapped back to (i, j) of the wx x wy result (row-major, ld = wy); with herm = 1 the
 // lower triangle is filled with the conjugate transpose.
 constexpr int GRED_WARPS = 8;
+// C row stride ldc (>= the row length: wy, or wx for the transposed form), so that a
+// product can fill a column block of a wider C.
 __global__ void gram_reduce_kernel(int nchunk, int nout, int wx, int wy, int herm,
-                                   const double2* __restrict__ partial, double2* __restrict__ C,
+                                   const double2* __restrict__ partial, double2* __restrict__ C, int ldc,
                                    const int* skip) {
   if (skip && *skip == 0) return;
   const int lane = threadIdx.x & 31;
@@ -473,13 +475,13 @@ __global__ void gram_reduce_kernel(int nchunk, int nout, int wx, int wy, int her
   if (lane == 0) {
     if (herm == 2) {  // the partials hold the transposed product: C(j, i) = conj(partial (i, j))
       const int i = o / wy, j = o - i * wy;
-      C[j * wx + i] = make_double2(s.x, -s.y);
+      C[(size_t)j * ldc + i] = make_double2(s.x, -s.y);
       return;
     }
     int i, j;
     gram_index(o, wx, wy, herm, i, j);
-    C[i * wy + j] = s;
-    if (herm && i != j) C[j * wy + i] = make_double2(s.x, -s.y);
+    C[(size_t)i * ldc + j] = s;
+    if (herm && i != j) C[(size_t)j * ldc + i] = make_double2(s.x, -s.y);
   }
 }
 

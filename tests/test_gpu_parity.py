@@ -654,7 +654,11 @@ def _gram_window_bound(Xh, Yh, nwin_cta):
     (4096, 8, 8, False), (100003, 8, 8, True), (20000, 24, 8, False), (30001, 16, 16, False),
     (2048, 3, 5, False), (9000, 1, 1, True), (7001, 24, 1, False), (12345, 5, 16, False), (65536, 24, 24, True),
     # narrow after swapping the operands (C = (Y^* X)^*)
-    (20000, 8, 24, False), (30001, 4, 20, False)])
+    (20000, 8, 24, False), (30001, 4, 20, False),
+    # wide after swapping the operands
+    (30001, 16, 64, False),
+    # more than 32 columns of Y: column blocks of at most 32, each by one of the forms above
+    (20000, 80, 80, False), (9000, 64, 64, True), (12000, 24, 40, False), (4096, 40, 40, True)])
 def test_gram_tensor_matches_twice_precision(n, wx, wy, self_):
     """C = X^* Y on the tensor cores (GPLHR_GRAM_TENSOR) against a twice-working-
     precision product, with rows spread over 1e-30..1e30, zero rows and a zero column,
