@@ -98,7 +98,6 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 constexpr int TC_DIGITS = 7;     // balanced base-256 digits of a 55-bit integer
 constexpr int TC_DIAG = 8;       // accumulated digit diagonals a + b = 0..7
 constexpr int TC_ROWS = 128;     // rows per tile = tensor-memory lanes (M)
-constexpr int TC_THREADS = 256;  // two threads per row: each loads half of the row
 constexpr int TC_KMAX = 64;      // K' per tile (complex inputs: 32 columns)
 constexpr int TC_NMAX = 64;      // N' (complex outputs: 32 columns)
 constexpr int TC_NOEXP = -100000;
