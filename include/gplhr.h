@@ -121,7 +121,9 @@ typedef struct {
                           tensor cores (tcgen05, each double split into 7 balanced 8-bit
                           integer digits, exact accumulation of digit-pair products; a
                           combination's error is at most (K'/4 + 2) 2^-53 max|x| sum|c|
-                          over K' real terms, below the DFMA bound) where the shape allows
+                          over K' real terms, a bound of its own: not ordered against the
+                          DFMA bound K' 2^-53 sum |x| |c|, which is smaller when a row's
+                          entries span decades) where the shape allows
                           (combinations: <= 32 input and output columns, n >= 512; Gram
                           products: see gplhr_gram), DFMA otherwise; 1 = DFMA only       */
   int32_t graphs;      /* [0]    1 = capture the device work of each iteration between its
@@ -362,9 +364,11 @@ gplhr_status gplhr_profile_read(gplhr_ctx* ctx, int32_t kclass, double* ms, int6
  * synchronisation and latency of an allocation.  The paper has no counterpart: this
  * is a library convenience around the Gram kernel of gplhr_gram.
  * X: n x wx, Y: n x wy (row-major complex, device pointers, leading dimensions in
- * elements), C: wx x wy row-major (ld = wy), device pointer; all are the caller's.
- * Needs no context.  Limits: wx * wy <= 16384 and wx + wy <= 768, else EINVAL with a
- * message in gplhr_last_error(NULL).  The kernel's scratch (partial sums over chunks
+ * elements), C: wx x wy row-major (ld = wy), device pointer; all are the caller's and
+ * must be memory of the CURRENT device (the kernels run on the current device, with
+ * its copy of the scratch array; the library cannot check where a raw pointer lives).
+ * Needs no context.  Limits: 1 <= n <= 2^30, wx * wy <= 16384 and wx + wy <= 768, else
+ * EINVAL with a message in gplhr_last_error(NULL).  The kernel's scratch (partial sums over chunks
  * of rows) is a fixed 4 MiB array in the library's device memory, held by every GPU
  * that loads the library until the process exits; every call on a device shares it
  * and leaves it holding its own partial sums, so calls that overlap on the GPU (two

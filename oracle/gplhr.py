@@ -24,8 +24,9 @@ CUDA path):
   and pair j passes when
       ||beta_j A x - alpha_j B x|| / ((|beta_j| ||A||_1 + |alpha_j| ||B||_1) ||x||) <= tol,
   i.e. ||A x - lambda B x|| / ((||A||_1 + |lambda| ||B||_1) ||x||) <= tol.
-  Locking is in order: q = number of leading pairs that pass (never decreasing).
-  The iteration stops when all k pairs pass.
+  Locking is in order (lock_update): the q locked pairs count as converged, and q
+  grows by the run of pairs q, q+1, ... that pass.  The iteration stops when all k
+  pairs are locked (without locking: when all k pass).
 * Search directions P (Sec. 3.5; the paper compares the options in Table 2):
   "thick" is P = Z Ybar_R(:, k+1:2k) (Eq. P1, the default); "lobpcg" is
   P = V^(i) - V^(i-1) C (Eq. P_lobpcg) with C = I, since the paper leaves C open and
@@ -284,6 +285,26 @@ def residuals(pen: Pencil, st: State, AV=None, BV=None) -> np.ndarray:
     return num / den
 
 
+def lock_update(res: np.ndarray, tol: float, q: int, m: int, m0: int) -> tuple[int, int]:
+    """Soft locking and the adaptation of m (Sec. 3.6), after the residuals ``res`` of
+    the k pairs of an iteration.
+
+    Locked pairs count as converged and stay locked, and locking is in order: pair j
+    can be locked only once pairs 0..j-1 are locked.  So q grows by the run of pairs
+    q, q+1, ... that meet ``tol`` (whatever the current residuals of the locked pairs
+    0..q-1).  When q grows and pairs remain, m becomes the largest integer with
+    m (k - q) <= m0 k, i.e. floor(m0 k / (k - q)), capped at MMAX = 20; otherwise m is
+    kept.  q = k means every pair is locked: the iteration has converged.
+    Returns the new (q, m)."""
+    k = len(res)
+    lead = q
+    while lead < k and res[lead] <= tol:
+        lead += 1
+    if lead > q and lead < k:
+        return lead, min(m0 * k // (k - lead), MMAX)
+    return lead, m
+
+
 @dataclasses.dataclass
 class Result:
     V: np.ndarray
@@ -328,14 +349,11 @@ def solve(A, B, sigma, V0, m: int = 1, tol: float = 1e-8, maxit: int = 500,
         hist.append(res.copy())
         if callback is not None:
             callback(st, res)
-        converged = bool(np.all(res <= tol))
-        if lock and not converged:
-            lead = 0
-            while lead < k and res[lead] <= tol:
-                lead += 1
-            if lead > st.q:
-                st.q = lead
-                st.m = min(st.m0 * k // (k - st.q), MMAX)
+        if lock:
+            st.q, st.m = lock_update(res, tol, st.q, st.m, st.m0)
+            converged = st.q == k       # every pair locked (a locked pair has converged)
+        else:
+            converged = bool(np.all(res <= tol))
     a = np.diag(st.RA).copy()
     b = np.diag(st.RB).copy()
     with np.errstate(divide="ignore", invalid="ignore"):

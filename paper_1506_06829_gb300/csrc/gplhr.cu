@@ -1323,8 +1323,8 @@ gplhr_status start_steps(gplhr_ctx* ctx) {
 
 // Mixed mode: leave the FP32 bulk phase once the largest residual is below switch_tol,
 // or, within two decades of switch_tol, has not dropped by 10 % over stall_iters
-// iterations (survey reading C14, with the stall test restricted to where FP32 could
-// be the floor).  The
+// iterations (the paper does not treat mixed precision; this switch rule is the
+// library's, with the stall test restricted to where FP32 could be the floor).  The
 // products AV, BV (and AP, BP when they are kept as combinations) are then formed again
 // in FP64, and the residuals recomputed in FP64.
 gplhr_status phase_update(gplhr_ctx* ctx) {
@@ -1352,21 +1352,29 @@ gplhr_status phase_update(gplhr_ctx* ctx) {
   return start_steps(ctx);
 }
 
-// Convergence bookkeeping after residuals(): soft locking in order and m-adaptation.
+// Convergence bookkeeping after residuals(): soft locking in order and m-adaptation
+// (Sec. 3.6).  Locked pairs count as converged and stay locked; pair j can be locked
+// only once pairs 0..j-1 are, so q grows by the run of pairs q, q+1, ... that meet tol,
+// and m becomes the largest integer with m (k - q) <= m0 k (at most 20).  The solve has
+// converged when every pair is locked (without locking: when every pair meets tol).
 // Nothing converges or locks during the FP32 bulk phase.
+int lock_lead(const gplhr_ctx* ctx) {
+  int lead = ctx->lock ? ctx->q : 0;
+  while (lead < ctx->k && lead < (int)ctx->resid.size() && ctx->resid[lead] <= ctx->tol) ++lead;
+  return lead;
+}
+
 bool converged_update(gplhr_ctx* ctx) {
   const int k = ctx->k;
   if (ctx->bulk32) return false;
-  bool all = true;
-  for (int j = 0; j < k; ++j) all = all && ctx->resid[j] <= ctx->tol;
-  if (all) return true;
-  if (ctx->lock) {
-    int lead = 0;
-    while (lead < k && ctx->resid[lead] <= ctx->tol) ++lead;
-    if (lead > ctx->q) {
-      ctx->q = lead;
-      ctx->m = std::min(ctx->m0 * k / (k - ctx->q), 20);
-    }
+  const int lead = lock_lead(ctx);
+  if (lead == k) {
+    if (ctx->lock) ctx->q = k;
+    return true;
+  }
+  if (ctx->lock && lead > ctx->q) {
+    ctx->q = lead;
+    ctx->m = std::min(ctx->m0 * k / (k - ctx->q), 20);
   }
   return false;
 }
@@ -1619,9 +1627,7 @@ void fill_info(gplhr_ctx* ctx, gplhr_info* info) {
   if (!info) return;
   std::memset(info, 0, sizeof(*info));
   info->iters = ctx->it;
-  int lead = 0;
-  while (lead < ctx->k && lead < (int)ctx->resid.size() && ctx->resid[lead] <= ctx->tol) ++lead;
-  info->nconv = lead;
+  info->nconv = ctx->bulk32 ? 0 : lock_lead(ctx);
   info->m = ctx->m;
   info->n_orth_fallback = ctx->h_diag ? ctx->h_diag[0] : 0;
   info->fp32_iters = ctx->fp32_iters;
@@ -2265,6 +2271,7 @@ bool valid_block(const void* p, int ld, int w) { return p != nullptr && w >= 0 &
 constexpr size_t kNoallocScratchElems = (size_t)1 << 18;  // double2 elements
 constexpr int kNoallocMaxOut = 16384;                     // wx * wy limit
 constexpr int kNoallocMaxCols = 768;                      // wx + wy limit (staged rows)
+constexpr int64_t kNoallocMaxRows = (int64_t)1 << 30;     // n limit (int row indices)
 static __device__ __align__(256) double2 g_noalloc_scratch[kNoallocScratchElems];
 
 constexpr int kNoallocMaxDevices = 64;
@@ -2817,8 +2824,10 @@ gplhr_status gplhr_profile_read(gplhr_ctx* ctx, int32_t kclass, double* ms, int6
 
 gplhr_status gplhr_gram_noalloc(int64_t n, const void* X, int32_t ldx, int32_t wx, const void* Y, int32_t ldy,
                                 int32_t wy, void* C, void* stream) {
-  if (n < 1 || n > INT_MAX || wx < 1 || wy < 1 || ldx < wx || ldy < wy || !X || !Y || !C) {
-    g_create_error = "gplhr_gram_noalloc: need 1 <= n < 2^31, w >= 1, ld >= w, non-null pointers";
+  // n <= 2^30: the kernels index rows in int, and the last chunk's end r0 + rows as well
+  // as its last 16-row step stay below 2^31 with that margin
+  if (n < 1 || n > kNoallocMaxRows || wx < 1 || wy < 1 || ldx < wx || ldy < wy || !X || !Y || !C) {
+    g_create_error = "gplhr_gram_noalloc: need 1 <= n <= 2^30, w >= 1, ld >= w, non-null pointers";
     return GPLHR_EINVAL;
   }
   if ((int64_t)wx * wy > kNoallocMaxOut || wx + wy > kNoallocMaxCols) {
@@ -2831,18 +2840,22 @@ gplhr_status gplhr_gram_noalloc(int64_t n, const void* X, int32_t ldx, int32_t w
   if (st != GPLHR_OK) return st;
   const int nn = (int)n;
   const int nout = wx * wy;
+  const int64_t R = gplhr::GRAM_ROWS;
   int acc = 8;
   while (acc > 1 && (nout + acc - 1) / acc < 128) acc >>= 1;
   const int groups = (nout + acc - 1) / acc;
   const int G = std::min(groups, gplhr::GRAM_THREADS);
   const int RG = gplhr::GRAM_THREADS / G;
   const int ntile = (groups + G - 1) / G;
-  int nchunk = std::max(1, (4 * std::max(nsm, 1)) / ntile);
-  nchunk = std::min(nchunk, std::max(1, (nn + gplhr::GRAM_ROWS - 1) / gplhr::GRAM_ROWS));
-  nchunk = std::min<int>(nchunk, (int)(kNoallocScratchElems / nout));
-  int rows = (nn + nchunk - 1) / nchunk;
-  rows = ((rows + gplhr::GRAM_ROWS - 1) / gplhr::GRAM_ROWS) * gplhr::GRAM_ROWS;
-  nchunk = (nn + rows - 1) / rows;
+  // row chunks (one partial sum each) in 64-bit arithmetic: at most 4 CTAs per SM, one
+  // 16-row step per chunk at least, and no more partial sums than the scratch holds
+  int64_t nch = std::max<int64_t>(1, (4 * (int64_t)std::max(nsm, 1)) / ntile);
+  nch = std::min<int64_t>(nch, std::max<int64_t>(1, (n + R - 1) / R));
+  nch = std::min<int64_t>(nch, (int64_t)(kNoallocScratchElems / nout));
+  int64_t rows64 = (n + nch - 1) / nch;
+  rows64 = ((rows64 + R - 1) / R) * R;
+  const int nchunk = (int)((n + rows64 - 1) / rows64);
+  const int rows = (int)rows64;
   const dim3 grid(nchunk, ntile);
   const size_t smem =
       std::max((size_t)gplhr::GRAM_ROWS * (wx + wy), (size_t)RG * G * acc) * sizeof(double2);

@@ -31,9 +31,10 @@
 // * tc_gram_kernel: the first, serial Gram form, for X up to 128 columns.
 // Error per output: input rounding <= 2^-55 (max_k |x_rk| sum_k |c_kn| + K' max_k |x_rk|
 // max_k |c_kn|), the dropped pairs a + b >= 8 (weight <= 2^-62 K' 2^(T_r + G_n) in all),
-// and the final rounding: at most (K'/4 + 2) u max_k |x_rk| sum_k |c_kn| with u = 2^-53,
-// a quarter of the classical bound K' u sum_k |x_rk| |c_kn| <= K' u max|x| sum|c| of a
-// DFMA dot product.  Results below 2^-1022 (subnormal) take a second rounding.
+// and the final rounding: at most (K'/4 + 2) u max_k |x_rk| sum_k |c_kn| with u = 2^-53.
+// This bound is the scheme's own: it is not ordered against the classical bound
+// K' u sum_k |x_rk| |c_kn| of a DFMA dot product, which is the smaller one when a row's
+// entries span decades.  Results below 2^-1022 (subnormal) take a second rounding.
 #pragma once
 #include <climits>
 #include <cstdint>

@@ -291,16 +291,53 @@ def gplhr_spmm_shape(ctx, w: int, fp32: bool = False):
     return t.value, g.value, us.value, ud.value
 
 
+def _gram_operands(X, Y, Cout):
+    """Refuses, before any launch, operands that the Gram kernels would read or write
+    out of bounds: the C ABI receives raw pointers and sizes only, so it cannot see a
+    wrong dtype, a transposed view or a short tensor.  X (n x wx), Y (n x wy): complex128
+    with unit column stride; Cout: contiguous complex128 wx x wy; all CUDA tensors on one
+    device.  Returns that device."""
+    import torch
+
+    def bad(msg):
+        raise GplhrError(GPLHR_EINVAL, f"Gram operands: {msg}")
+
+    for name, T in (("X", X), ("Y", Y), ("C", Cout)):
+        if not isinstance(T, torch.Tensor) or T.dim() != 2:
+            bad(f"{name} must be a 2-D torch tensor")
+        if T.dtype != torch.complex128:
+            bad(f"{name} must be complex128, got {T.dtype}")
+    if X.shape[0] != Y.shape[0]:
+        bad(f"X has {X.shape[0]} rows, Y has {Y.shape[0]}")
+    if X.shape[0] < 1 or X.shape[1] < 1 or Y.shape[1] < 1:
+        bad("empty block")
+    if X.stride(1) != 1 or Y.stride(1) != 1:
+        bad("X and Y need unit column stride (row-major rows)")
+    if tuple(Cout.shape) != (X.shape[1], Y.shape[1]) or not Cout.is_contiguous():
+        bad(f"C must be a contiguous {X.shape[1]} x {Y.shape[1]} tensor, got {tuple(Cout.shape)}")
+    if not (X.is_cuda and Y.is_cuda and Cout.is_cuda):
+        bad("X, Y and C must be CUDA tensors")
+    if not (X.device == Y.device == Cout.device):
+        bad(f"X, Y and C on different devices ({X.device}, {Y.device}, {Cout.device})")
+    return X.device
+
+
 def gplhr_gram(ctx, X, Y, Cout, arith: str = "fp64"):
+    _gram_operands(X, Y, Cout)
     _check(lib().gplhr_gram(ctx, X.data_ptr(), X.stride(0), X.shape[1], Y.data_ptr(),
                             Y.stride(0), Y.shape[1], Cout.data_ptr(), GRAM_ARITH[arith]), ctx)
 
 
 def gplhr_gram_noalloc(X, Y, Cout, stream: int = 0):
-    """C = X^* Y without any allocation (device tensors; asynchronous on `stream`)."""
-    _check(lib().gplhr_gram_noalloc(X.shape[0], X.data_ptr(), X.stride(0), X.shape[1],
-                                    Y.data_ptr(), Y.stride(0), Y.shape[1], Cout.data_ptr(),
-                                    stream or None), None)
+    """C = X^* Y without any allocation (device tensors; asynchronous on `stream`).
+    The call runs with the tensors' device current: the library launches on the
+    current device, with that device's copy of its scratch array."""
+    import torch
+    dev = _gram_operands(X, Y, Cout)
+    with torch.cuda.device(dev):
+        _check(lib().gplhr_gram_noalloc(X.shape[0], X.data_ptr(), X.stride(0), X.shape[1],
+                                        Y.data_ptr(), Y.stride(0), Y.shape[1], Cout.data_ptr(),
+                                        stream or None), None)
 
 
 def gplhr_grad(right, left, G, dA=None, dB=None):
