@@ -155,6 +155,18 @@ typedef struct {
                           projector before T, no deflation, no gplhr_grad.  gplhr_vectors
                           then fills alpha, beta, lambda, X and resid and zero-fills V, Q,
                           RA, RB.  EINVAL for other values or combinations.               */
+  int32_t wait_limit;  /* [0]    test hook of the failure path: the number of tests (each
+                          sleeping at most 20 us) after which a wait of one role of a
+                          tensor-core kernel on another role gives up; the kernel then
+                          ends all its roles, waits (with the full limit) for its own
+                          products in flight, frees its tensor memory, and the call returns
+                          GPLHR_ETIMEOUT with the context still usable.  0 = 65536 tests
+                          (~1.3 s); values above that are clamped to it; EINVAL if < 0.
+                          The paper has no counterpart.                                    */
+  int32_t wait_probe;  /* [0]    test hook: 1 = the epilogue of every tensor-core combination
+                          also waits on an mbarrier whose phase nothing completes, so the
+                          time-out path above runs deterministically (after wait_limit
+                          tests).  Never set outside tests.                                */
 } gplhr_opts;
 
 /* Per-solve report.  resid[j] (j < k) is the backward error of pair j,
@@ -244,6 +256,26 @@ gplhr_status gplhr_vectors(gplhr_ctx* ctx, double* alpha, double* beta, double* 
 gplhr_status gplhr_grad(gplhr_ctx* right, gplhr_ctx* left, const double* G, void* dA_vals,
                         void* dB_vals, int32_t where);
 
+/* gplhr_create_batched -- create nctx contexts at once: many pencils of uneven size, or
+ * many shifts over one pencil (spectrum slicing: pass the same A, B descriptors with
+ * different shifts), each with the arguments of gplhr_create (Algorithm 2 inputs,
+ * Sec. 3.6).  Arrays of nctx entries: A (required, entries non-NULL), B (NULL, or
+ * entries NULL for B = I), sigma (2 nctx doubles: re, im), k, m, T (NULL, or NULL
+ * entries for T = I), opts (NULL, or NULL entries for the defaults).  Every context
+ * copies its matrices (as gplhr_create does; slices over one pencil do not share device
+ * copies) and owns its own stream unless opts gives one.  The contexts are created
+ * concurrently by nthreads host threads (<= 0: the host's hardware threads), all on the
+ * current device.  out (nctx handles) receives them.  All or nothing: if any creation
+ * fails, the contexts already created are destroyed, every out[i] is NULL, statuses (may
+ * be NULL) holds each entry's status, the first failing status in entry order is
+ * returned and gplhr_last_error(NULL) names that entry and its message.  The handles
+ * then go to gplhr_solve_batched / gplhr_iterate_batched and are freed one by one with
+ * gplhr_destroy. */
+gplhr_status gplhr_create_batched(int32_t nctx, const gplhr_csr* const* A, const gplhr_csr* const* B,
+                                  const double* sigma, const int32_t* k, const int32_t* m,
+                                  const gplhr_precond* const* T, const gplhr_opts* const* opts, gplhr_ctx** out,
+                                  gplhr_status* statuses, int32_t nthreads);
+
 /* Batched solves (many pencils of uneven size, or many shifts over one pencil, each in
  * its own context).  The contexts are independent: each has its own stream and
  * buffers; a pool of nthreads host threads (<= 0: the host's hardware threads) runs
@@ -263,8 +295,10 @@ gplhr_status gplhr_iterate_batched(int32_t nctx, gplhr_ctx* const* ctxs, int32_t
 /* gplhr_destroy -- free everything the context owns.  NULL is a no-op. */
 void gplhr_destroy(gplhr_ctx* ctx);
 
-/* Message for the last failing call on ctx (or of the last failed gplhr_create when
- * ctx is NULL).  The string stays valid until the next call on the same context. */
+/* Message for the last failing call on ctx (or, when called with NULL, of the last failed
+ * context-free call -- gplhr_create, gplhr_create_batched, gplhr_gram_noalloc -- on the
+ * calling host thread).  The string stays valid until the next call on the same context
+ * (or the next context-free call on the same thread). */
 const char* gplhr_last_error(const gplhr_ctx* ctx);
 
 /* ---------------------------------------------------------------------------------

@@ -32,7 +32,9 @@ using gplhr::SqMat;
 
 namespace {
 
-std::string g_create_error;
+// Message of the last failed context-free call (gplhr_create, gplhr_gram_noalloc, ...),
+// per host thread: batched creation runs gplhr_create on several threads at once.
+thread_local std::string g_create_error;
 
 struct DevCsr {
   int* rowptr = nullptr;
@@ -121,6 +123,8 @@ struct gplhr_ctx {
   int* d_diag = nullptr;      // [0] shifted-Cholesky fallbacks, [1] Cholesky failures,
                               // [2] tensor-core waits that gave up
   bool tc = true;             // FP64 combinations on the tensor cores where supported
+  int tc_wait_tries = gplhr::TC_WAIT_TRIES;  // limit of the tensor-core pipelines' waits
+  bool tc_probe = false;      // test hook: combinations wait on a barrier nothing completes
   // pinned host staging
   double2* h_small = nullptr;  // coefficient uploads
   double2* h_phipsi = nullptr;
@@ -561,6 +565,7 @@ gplhr_status gram_tc(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int
   t.partial = ctx->gram_part;
   t.skip = skip;
   t.err = ctx->d_diag + 2;
+  t.wait_tries = ctx->tc_wait_tries;
   t.np = ((2 * wy + 15) / 16) * 16;
   t.mt = (2 * wx + 127) / 128;
   t.tmem_cols = 32;
@@ -625,6 +630,7 @@ gplhr_status gram_tn(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int
   t.partial = ctx->gram_part;
   t.skip = skip;
   t.err = ctx->d_diag + 2;
+  t.wait_tries = ctx->tc_wait_tries;
   t.mt = sh.mt;
   t.np = sh.np;
   t.ts = sh.ts;
@@ -679,6 +685,7 @@ gplhr_status gram_tw(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int
   t.partial = ctx->gram_part;
   t.skip = skip;
   t.err = ctx->d_diag + 2;
+  t.wait_tries = ctx->tc_wait_tries;
   t.np = ((2 * wy + 15) / 16) * 16;
   t.ts = 2 * gplhr::TC_DIAG * t.np <= 512 ? 2 : 1;
   t.tmem_cols = 32;
@@ -797,9 +804,11 @@ gplhr_status combine_tc(gplhr_ctx* ctx, gplhr::CombArgs a, int wsum, int c, int 
   t.np = ((2 * c + 15) / 16) * 16;
   t.ds = gplhr::tc_comb_smem_bytes(t.kp, t.np, 2) <= kCombSmemMax ? 2 : 1;
   t.ts = 2 * gplhr::TC_DIAG * t.np <= 512 ? 2 : 1;
+  t.probe = ctx->tc_probe ? 1 : 0;
   t.tmem_cols = 32;
   while (t.tmem_cols < t.ts * gplhr::TC_DIAG * t.np) t.tmem_cols <<= 1;
   t.err = ctx->d_diag + 2;
+  t.wait_tries = ctx->tc_wait_tries;
   const int ntiles = (ctx->n + gplhr::TC_ROWS - 1) / gplhr::TC_ROWS;
   // two CTAs per SM at K' <= 32, N' = 16 (both fit in shared and tensor memory; at K' = 32
   // with one digit stage each)
@@ -2364,6 +2373,13 @@ gplhr_status gplhr_create(const gplhr_csr* A, const gplhr_csr* B, double sigma_r
     ctx->graphs = opts->graphs != 0;
     ctx->autotune = opts->autotune != 0;
     ctx->right_proj = opts->no_right_proj == 0;
+    if (opts->wait_limit < 0) {
+      g_create_error = "opts.wait_limit must be >= 0";
+      delete ctx;
+      return GPLHR_EINVAL;
+    }
+    if (opts->wait_limit > 0) ctx->tc_wait_tries = std::min(opts->wait_limit, gplhr::TC_WAIT_TRIES);
+    ctx->tc_probe = opts->wait_probe != 0;
     if (opts->p_mode < 0 || opts->p_mode > 2) {
       g_create_error = "opts.p_mode must be 0 (thick), 1 (LOBPCG style) or 2 (none)";
       delete ctx;
@@ -2697,6 +2713,7 @@ gplhr_status gplhr_combine(gplhr_ctx* ctx, const void* X, int32_t ldx, int32_t w
       c > 2 * ctx->s_max || arith < 0 || arith > 1 || beta < 0 || beta > 1 ||
       (X == Y && (c != w || ldy != ldx || beta != 0)))
     return GPLHR_EINVAL;
+  CK(cudaMemsetAsync(ctx->d_diag + 2, 0, sizeof(int), ctx->stream));  // this call's time-out flag
   const bool tc = ctx->tc;
   ctx->tc = tc && arith == GPLHR_COMBINE_AUTO;
   const gplhr_status st = combine(ctx, {In{Blk{(double2*)X, ldx}, w, (const double2*)C, kOne}},
@@ -3034,6 +3051,56 @@ gplhr_status gplhr_iterate_batched(int32_t nctx, gplhr_ctx* const* ctxs, int32_t
   return run_batched(nctx, ctxs, nthreads, statuses, [&](int i) {
     return gplhr_iterate(ctxs[i], niter, infos ? infos + i : nullptr);
   });
+}
+
+gplhr_status gplhr_create_batched(int32_t nctx, const gplhr_csr* const* A, const gplhr_csr* const* B,
+                                  const double* sigma, const int32_t* k, const int32_t* m,
+                                  const gplhr_precond* const* T, const gplhr_opts* const* opts, gplhr_ctx** out,
+                                  gplhr_status* statuses, int32_t nthreads) {
+  if (nctx < 0 || (nctx > 0 && (!A || !sigma || !k || !m || !out))) {
+    g_create_error = "gplhr_create_batched: need nctx >= 0 and non-null A, sigma, k, m, out";
+    return GPLHR_EINVAL;
+  }
+  for (int i = 0; i < nctx; ++i) out[i] = nullptr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    g_create_error = "gplhr_create_batched: no CUDA device";
+    return GPLHR_ECUDA;
+  }
+  std::vector<gplhr_status> st(nctx, GPLHR_OK);
+  std::vector<std::string> msg(nctx);
+  std::atomic<int> next(0);
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (int i = next.fetch_add(1); i < nctx; i = next.fetch_add(1)) {
+      st[i] = gplhr_create(A[i], B ? B[i] : nullptr, sigma[2 * i], sigma[2 * i + 1], k[i], m[i], T ? T[i] : nullptr,
+                           opts ? opts[i] : nullptr, &out[i]);
+      if (st[i] != GPLHR_OK) msg[i] = g_create_error;  // this worker thread's message
+    }
+  };
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nt = std::max(1, std::min<int>(nthreads > 0 ? nthreads : hw, nctx));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& th : pool) th.join();
+  gplhr_status first = GPLHR_OK;
+  int bad = -1;
+  for (int i = 0; i < nctx; ++i) {
+    if (statuses) statuses[i] = st[i];
+    if (first == GPLHR_OK && st[i] != GPLHR_OK) {
+      first = st[i];
+      bad = i;
+    }
+  }
+  if (first != GPLHR_OK) {  // all or nothing: the contexts that were created are freed
+    for (int i = 0; i < nctx; ++i) {
+      gplhr_destroy(out[i]);
+      out[i] = nullptr;
+    }
+    g_create_error = "gplhr_create_batched: context " + std::to_string(bad) + ": " + msg[bad];
+  }
+  return first;
 }
 
 gplhr_status gplhr_solve_batched(int32_t nctx, gplhr_ctx* const* ctxs, const void* const* V0,

@@ -224,10 +224,14 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
 }
-// Bounded wait for the phase of the given parity: false after the iteration limit, or
-// as soon as another role has raised *abort.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort) {
-  for (int it = 0; it < TC_WAIT_TRIES; ++it) {
+// Bounded wait for the phase of the given parity: false after `tries` tests, or as soon
+// as another role has raised *abort.  The pipeline's waits on other roles take the
+// limit from the kernel arguments (a context option lowers it to test the time-out
+// path); the final wait for the CTA's own products before tensor memory is freed always
+// takes the full TC_WAIT_TRIES.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                                  int tries) {
+  for (int it = 0; it < tries; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
   }
@@ -242,6 +246,8 @@ struct TcCombArgs {
   int ts;          // accumulator buffers in tensor memory (1 or 2)
   int tmem_cols;   // power of two >= max(32, ts TC_DIAG np)
   int* err;        // set to 1 if a wait gave up
+  int wait_tries;    // limit of the pipeline's mbarrier waits (tests lower it)
+  int probe;         // test hook: the epilogue also waits on a barrier nothing completes
 };
 
 __host__ __device__ constexpr size_t tc_comb_smem_bytes(int kp, int np, int ds) {
@@ -321,6 +327,7 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, CPS) tc_combine_kernel(int n,
   uint16_t* sB = reinterpret_cast<uint16_t*>(tc_smem);        // 8 np x kp: plane b, column n at row b np + n
   uint16_t* sA = sB + TC_DIAG * np * kp;                       // ds stages of TC_DIGITS x 128 x kp
   __shared__ __align__(8) uint64_t bar_dempty[2], bar_tfull[2], bar_tempty[2], bar_row[TC_RING];
+  __shared__ __align__(8) uint64_t bar_never;  // test hook: nothing ever completes its phase 0
   __shared__ uint32_t taddr_s;
   __shared__ volatile int abort_s;
   __shared__ double nwarp[TC_EWARPS][COMB_MAX_NORMS];  // norm columns: one partial per epilogue warp
@@ -368,6 +375,7 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, CPS) tc_combine_kernel(int n,
       mbar_init(&bar_tempty[i], TC_EWARPS * 32);
     }
     for (int i = 0; i < TC_RING; ++i) mbar_init(&bar_row[i], TC_ROWS);
+    mbar_init(&bar_never, 1);
   }
   __syncthreads();
   for (int e = tid; e < kp * np; e += TC_PIPE_THREADS) {
@@ -449,7 +457,7 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, CPS) tc_combine_kernel(int n,
       bool ok = bar_and(1, TC_DWARPS * 32, true);
       T = max(sX[it & 1][0][rl], sX[it & 1][1][rl]);
       bad = sXb[it & 1][0][rl] | sXb[it & 1][1][rl];
-      ok = bar_and(1, TC_DWARPS * 32, mma_ok && mbar_wait_bounded(&bar_dempty[s], (u & 1) ^ 1, &abort_s));
+      ok = bar_and(1, TC_DWARPS * 32, mma_ok && mbar_wait_bounded(&bar_dempty[s], (u & 1) ^ 1, &abort_s, ta.wait_tries));
       if (!ok) {
         if (tid == 0) {
           abort_s = 1;
@@ -488,7 +496,7 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, CPS) tc_combine_kernel(int n,
       if (tid == 0) {
         const int b = it % ts;
         const uint32_t v = (uint32_t)(it / ts);
-        mma_ok = mbar_wait_bounded(&bar_tempty[b], (v & 1) ^ 1, &abort_s);
+        mma_ok = mbar_wait_bounded(&bar_tempty[b], (v & 1) ^ 1, &abort_s, ta.wait_tries);
         if (mma_ok) {
           tc_fence_after();
           const uint32_t a0 = sA_addr + (uint32_t)s * a_stage;
@@ -517,7 +525,7 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, CPS) tc_combine_kernel(int n,
     }
     if (tid == 0 && last_b >= 0) {  // the last products complete before the tensor memory is freed
       volatile int never = 0;
-      if (!mbar_wait_bounded(&bar_tfull[last_b], last_v & 1, &never)) atomicExch(ta.err, 1);
+      if (!mbar_wait_bounded(&bar_tfull[last_b], last_v & 1, &never, TC_WAIT_TRIES)) atomicExch(ta.err, 1);
     }
   } else if (warp < TC_DWARPS + TC_EWARPS) {
     // ---------------------------------------------------------- epilogue role --
@@ -534,8 +542,9 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, CPS) tc_combine_kernel(int n,
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
       const int b = it % ts, slot = it % TC_RING;
       const uint32_t v = (uint32_t)(it / ts);
-      bool ok = mbar_wait_bounded(&bar_row[slot], (uint32_t)(it / TC_RING) & 1, &abort_s) &&
-                mbar_wait_bounded(&bar_tfull[b], v & 1, &abort_s);
+      bool ok = mbar_wait_bounded(&bar_row[slot], (uint32_t)(it / TC_RING) & 1, &abort_s, ta.wait_tries) &&
+                mbar_wait_bounded(&bar_tfull[b], v & 1, &abort_s, ta.wait_tries) &&
+                (!ta.probe || mbar_wait_bounded(&bar_never, 0, &abort_s, ta.wait_tries));
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) {
         if (lane == 0) {
@@ -646,6 +655,7 @@ struct TcGramArgs {
   double2* partial;  // [gridDim.x][wx * (wy0 + wy1)]
   const int* skip;   // nothing happens when non-null and *skip == 0
   int* err;          // set to 1 if a wait on the tensor core gave up
+  int wait_tries;    // limit of the pipeline's mbarrier waits (tests lower it)
   int np;            // 2 (wy0 + wy1) rounded up to a multiple of 16 (<= 64)
   int mt;            // M tiles: 2 wx <= 128 mt (1 or 2; 2 needs np <= 32)
   int tmem_cols;     // power of two >= mt * 8 * np
@@ -915,6 +925,7 @@ struct TcGramNArgs {
   double2* partial;  // [gridDim.x][wx * (wy0 + wy1)]
   const int* skip;
   int* err;
+  int wait_tries;    // limit of the pipeline's mbarrier waits (tests lower it)
   int mt;            // M tiles: 14 wx <= 128 mt (<= 3)
   int np;            // 2 wy rounded up to 16 (16 or 32)
   int ts;            // accumulator buffers (1 or 2)
@@ -1042,7 +1053,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
       tn_load<NT>(ta, r0, trp, tj, v);
       // the first stage free (the previous window's first-half products done): the
       // exponent slot of this window is then free too (its epilogue is four windows back)
-      bool ok = bar_and(1, TN_DWARPS * 32, mbar_wait_bounded(&bar_dempty[0], (it & 1) ^ 1, &abort_s));
+      bool ok = bar_and(1, TN_DWARPS * 32, mbar_wait_bounded(&bar_dempty[0], (it & 1) ^ 1, &abort_s, ta.wait_tries));
       if (!ok) {
         if (tid == 0) {
           abort_s = 1;
@@ -1071,7 +1082,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
       mbar_arrive(&bar_exp[slot]);
       for (int h = 0; h < 2; ++h) {
         if (h == 1) {
-          ok = bar_and(1, TN_DWARPS * 32, mbar_wait_bounded(&bar_dempty[1], (it & 1) ^ 1, &abort_s));
+          ok = bar_and(1, TN_DWARPS * 32, mbar_wait_bounded(&bar_dempty[1], (it & 1) ^ 1, &abort_s, ta.wait_tries));
           if (!ok) break;
         }
         uint16_t* sA = sA0 + (size_t)h * (stage / 2);
@@ -1130,8 +1141,8 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
         const uint32_t vv = (uint32_t)(it / ts);
         bool ok = true;
         for (int h = 0; h < 2 && ok; ++h) {
-          ok = mbar_wait_bounded(&bar_dfull[h], it & 1, &abort_s) &&
-               (h == 1 || mbar_wait_bounded(&bar_tempty[b], (vv & 1) ^ 1, &abort_s));
+          ok = mbar_wait_bounded(&bar_dfull[h], it & 1, &abort_s, ta.wait_tries) &&
+               (h == 1 || mbar_wait_bounded(&bar_tempty[b], (vv & 1) ^ 1, &abort_s, ta.wait_tries));
           if (!ok) break;
           tc_fence_after();
           const uint32_t a0 = sbase + (uint32_t)(h * stage);
@@ -1156,7 +1167,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
       }
       if (last_b >= 0) {  // the last products complete before the tensor memory is freed
         volatile int never = 0;
-        if (!mbar_wait_bounded(&bar_tfull[last_b], last_v & 1, &never)) atomicExch(ta.err, 1);
+        if (!mbar_wait_bounded(&bar_tfull[last_b], last_v & 1, &never, TC_WAIT_TRIES)) atomicExch(ta.err, 1);
       }
     }
   } else {
@@ -1173,8 +1184,8 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
     for (int win = blockIdx.x; win < nwin; win += gridDim.x, ++it) {
       const int b = it % ts, slot = it % TN_RING;
       const uint32_t vv = (uint32_t)(it / ts);
-      bool ok = mbar_wait_bounded(&bar_exp[slot], (uint32_t)(it / TN_RING) & 1, &abort_s) &&
-                mbar_wait_bounded(&bar_tfull[b], vv & 1, &abort_s);
+      bool ok = mbar_wait_bounded(&bar_exp[slot], (uint32_t)(it / TN_RING) & 1, &abort_s, ta.wait_tries) &&
+                mbar_wait_bounded(&bar_tfull[b], vv & 1, &abort_s, ta.wait_tries);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) {
         if (lane == 0) {
@@ -1295,6 +1306,7 @@ struct TcGramWArgs {
   double2* partial;  // [gridDim.x][wx * (wy0 + wy1)]
   const int* skip;
   int* err;
+  int wait_tries;    // limit of the pipeline's mbarrier waits (tests lower it)
   int np;            // 2 wy rounded up to 16 (<= 64)
   int ts;            // accumulator buffers (1 or 2)
   int tmem_cols;     // power of two >= ts 8 np
@@ -1362,7 +1374,7 @@ __global__ void __launch_bounds__(TW_THREADS, 1) tc_gram_wide_kernel(TcGramWArgs
       const int slot = it % TW_RING, r0 = win * TW_WIN, nr = min(TW_WIN, n - r0);
       // the exponent slot is free once the previous window's first stage was consumed
       // (that window's MMAs began after the epilogue of the one before it had finished)
-      bool ok = bar_and(1, DT, mbar_wait_bounded(&bar_dempty[0], ((uint32_t)(2 * it) & 1u) ^ 1u, &abort_s));
+      bool ok = bar_and(1, DT, mbar_wait_bounded(&bar_dempty[0], ((uint32_t)(2 * it) & 1u) ^ 1u, &abort_s, ta.wait_tries));
       if (!ok) {
         if (tid == 0) {
           abort_s = 1;
@@ -1413,7 +1425,7 @@ __global__ void __launch_bounds__(TW_THREADS, 1) tc_gram_wide_kernel(TcGramWArgs
         const int st = sc & 1;
         const uint32_t u = (uint32_t)(2 * it + (sc >> 1));
         if (sc > 0) {
-          ok = bar_and(1, DT, mbar_wait_bounded(&bar_dempty[st], (u & 1) ^ 1, &abort_s));
+          ok = bar_and(1, DT, mbar_wait_bounded(&bar_dempty[st], (u & 1) ^ 1, &abort_s, ta.wait_tries));
           if (!ok) break;
         }
         uint16_t* sA = reinterpret_cast<uint16_t*>(tw_smem + st * stage);
@@ -1504,8 +1516,8 @@ __global__ void __launch_bounds__(TW_THREADS, 1) tc_gram_wide_kernel(TcGramWArgs
         for (int sc = 0; sc < TW_WIN / TW_STAGE && ok; ++sc) {
           const int st = sc & 1;
           const uint32_t u = (uint32_t)(2 * it + (sc >> 1));
-          ok = mbar_wait_bounded(&bar_dfull[st], u & 1, &abort_s) &&
-               (sc > 0 || mbar_wait_bounded(&bar_tempty[b], (vv & 1) ^ 1, &abort_s));
+          ok = mbar_wait_bounded(&bar_dfull[st], u & 1, &abort_s, ta.wait_tries) &&
+               (sc > 0 || mbar_wait_bounded(&bar_tempty[b], (vv & 1) ^ 1, &abort_s, ta.wait_tries));
           if (!ok) break;
           tc_fence_after();
           const uint32_t a0 = sbase + (uint32_t)(st * stage);
@@ -1536,7 +1548,7 @@ __global__ void __launch_bounds__(TW_THREADS, 1) tc_gram_wide_kernel(TcGramWArgs
       }
       if (last_b >= 0) {  // the last products complete before the tensor memory is freed
         volatile int never = 0;
-        if (!mbar_wait_bounded(&bar_tfull[last_b], last_v & 1, &never)) atomicExch(ta.err, 1);
+        if (!mbar_wait_bounded(&bar_tfull[last_b], last_v & 1, &never, TC_WAIT_TRIES)) atomicExch(ta.err, 1);
       }
     }
   } else {
@@ -1549,8 +1561,8 @@ __global__ void __launch_bounds__(TW_THREADS, 1) tc_gram_wide_kernel(TcGramWArgs
     for (int win = blockIdx.x; win < nwin; win += gridDim.x, ++it) {
       const int b = it % ts, slot = it % TW_RING;
       const uint32_t vv = (uint32_t)(it / ts);
-      bool ok = mbar_wait_bounded(&bar_exp[slot], (uint32_t)(it / TW_RING) & 1, &abort_s) &&
-                mbar_wait_bounded(&bar_tfull[b], vv & 1, &abort_s);
+      bool ok = mbar_wait_bounded(&bar_exp[slot], (uint32_t)(it / TW_RING) & 1, &abort_s, ta.wait_tries) &&
+                mbar_wait_bounded(&bar_tfull[b], vv & 1, &abort_s, ta.wait_tries);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) {
         if (lane == 0) {

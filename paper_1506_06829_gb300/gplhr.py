@@ -29,7 +29,7 @@ EXPORTED = ["gplhr_create", "gplhr_solve", "gplhr_start", "gplhr_iterate", "gplh
             "gplhr_destroy", "gplhr_last_error", "gplhr_spmm", "gplhr_precond_apply",
             "gplhr_gram", "gplhr_combine", "gplhr_orth", "gplhr_ordqz", "gplhr_mfactors", "gplhr_profile",
             "gplhr_profile_read", "gplhr_gram_noalloc", "gplhr_grad", "gplhr_solve_batched",
-            "gplhr_iterate_batched", "gplhr_spmm_shape", "gplhr_set_deflation"]
+            "gplhr_iterate_batched", "gplhr_spmm_shape", "gplhr_set_deflation", "gplhr_create_batched"]
 P_MODES = {"thick": 0, "lobpcg": 1, "none": 2}
 KCLASS = {"spmm": 0, "gram": 1, "combine": 2, "precond": 3, "chol": 4, "other": 5, "gram_tc": 6,
           "combine_tc": 7}
@@ -51,7 +51,8 @@ class Opts(C.Structure):
                 ("no_lock", C.c_int32), ("products", C.c_int32), ("stream", C.c_void_p),
                 ("switch_tol", C.c_double), ("stall_iters", C.c_int32), ("pencil", C.c_int32),
                 ("fp64_gemm", C.c_int32), ("graphs", C.c_int32), ("autotune", C.c_int32),
-                ("p_mode", C.c_int32), ("no_right_proj", C.c_int32), ("variant", C.c_int32)]
+                ("p_mode", C.c_int32), ("no_right_proj", C.c_int32), ("variant", C.c_int32),
+                ("wait_limit", C.c_int32), ("wait_probe", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -109,6 +110,10 @@ def lib():
                                       C.POINTER(C.c_int), i32]
     L.gplhr_iterate_batched.argtypes = [i32, C.POINTER(vp), i32, C.POINTER(Info),
                                         C.POINTER(C.c_int), i32]
+    L.gplhr_create_batched.argtypes = [i32, C.POINTER(C.POINTER(Csr)), C.POINTER(C.POINTER(Csr)),
+                                       C.POINTER(C.c_double), C.POINTER(i32), C.POINTER(i32),
+                                       C.POINTER(C.POINTER(Precond)), C.POINTER(C.POINTER(Opts)),
+                                       C.POINTER(vp), C.POINTER(C.c_int), i32]
     L.gplhr_profile_read.argtypes = [vp, i32, dp, C.POINTER(C.c_int64), dp, dp]
     for name in EXPORTED:
         f = getattr(L, name)
@@ -156,11 +161,26 @@ def gplhr_create(A, B, sigma: complex, k: int, m: int, precond: str = "none",
                  precision: str = "fp64", switch_tol: float = 1e-5, stall_iters: int = 5,
                  pencil: str = "factored", inner_steps: int = 0, fp64_gemm: str = "tensor",
                  graphs: bool = False, autotune: bool = False, p_mode: str = "thick",
-                 right_proj: bool = True, variant: str = "schur"):
+                 right_proj: bool = True, variant: str = "schur", wait_limit: int = 0,
+                 wait_probe: bool = False):
     """Returns an opaque context handle (int).  A, B: SciPy CSR (B None = identity).
     inner_steps > 0: T = that many block GMRES steps on (A - sigma B) W = R,
     right-preconditioned by `precond`."""
     L = lib()
+    d = _create_args(A, B, T, precond, block_size, inner_steps, tol, maxit, lock, stream, products,
+                     precision, switch_tol, stall_iters, pencil, fp64_gemm, graphs, autotune, p_mode,
+                     right_proj, variant, wait_limit, wait_probe)
+    out = C.c_void_p()
+    st = L.gplhr_create(C.byref(d["A"].desc), C.byref(d["B"].desc) if d["B"] else None, sigma.real,
+                        sigma.imag, k, m, C.byref(d["T"]), C.byref(d["opts"]), C.byref(out))
+    _check(st, None)
+    return out.value
+
+
+def _create_args(A, B, T, precond, block_size, inner_steps, tol, maxit, lock, stream, products,
+                 precision, switch_tol, stall_iters, pencil, fp64_gemm, graphs, autotune, p_mode,
+                 right_proj, variant, wait_limit=0, wait_probe=False):
+    """Host descriptors of one context's gplhr_create arguments (kept alive together)."""
     hA = _HostCsr(A)
     hB = _HostCsr(B) if B is not None else None
     hT = _HostCsr(T.astype(np.complex128)) if T is not None else None
@@ -169,12 +189,45 @@ def gplhr_create(A, B, sigma: complex, k: int, m: int, precond: str = "none",
                 PRODUCTS[products], stream or None, switch_tol, stall_iters,
                 {"factored": 0, "gram": 1}[pencil], {"tensor": 0, "dfma": 1}[fp64_gemm],
                 1 if graphs else 0, 1 if autotune else 0, P_MODES[p_mode], 0 if right_proj else 1,
-                {"schur": 0, "eig": 1}[variant])
-    out = C.c_void_p()
-    st = L.gplhr_create(C.byref(hA.desc), C.byref(hB.desc) if hB else None, sigma.real,
-                        sigma.imag, k, m, C.byref(pc), C.byref(opts), C.byref(out))
+                {"schur": 0, "eig": 1}[variant], wait_limit, 1 if wait_probe else 0)
+    return {"A": hA, "B": hB, "Tcsr": hT, "T": pc, "opts": opts}
+
+
+_CREATE_DEFAULTS = dict(B=None, precond="none", block_size=1, T=None, tol=1e-8, maxit=500, lock=True,
+                        stream=0, products="auto", precision="fp64", switch_tol=1e-5, stall_iters=5,
+                        pencil="factored", inner_steps=0, fp64_gemm="tensor", graphs=False,
+                        autotune=False, p_mode="thick", right_proj=True, variant="schur", wait_limit=0,
+                        wait_probe=False)
+
+
+def gplhr_create_batched(specs, nthreads: int = 0):
+    """Creates one context per spec (a dict with the keyword arguments of gplhr_create:
+    A, sigma, k, m required) in one call; returns the list of handles.  All or nothing:
+    on a failure no context survives and GplhrError names the failing entry."""
+    n = len(specs)
+    keep, sig, ks, ms = [], [], [], []
+    for spec in specs:
+        a = dict(_CREATE_DEFAULTS)
+        a.update(spec)
+        keep.append(_create_args(a["A"], a["B"], a["T"], a["precond"], a["block_size"], a["inner_steps"],
+                                 a["tol"], a["maxit"], a["lock"], a["stream"], a["products"],
+                                 a["precision"], a["switch_tol"], a["stall_iters"], a["pencil"],
+                                 a["fp64_gemm"], a["graphs"], a["autotune"], a["p_mode"],
+                                 a["right_proj"], a["variant"], a["wait_limit"], a["wait_probe"]))
+        sig += [complex(a["sigma"]).real, complex(a["sigma"]).imag]
+        ks.append(int(a["k"]))
+        ms.append(int(a["m"]))
+    PCsr, PPre, POpt = C.POINTER(Csr), C.POINTER(Precond), C.POINTER(Opts)
+    Aa = (PCsr * n)(*[C.pointer(d["A"].desc) for d in keep])
+    Ba = (PCsr * n)(*[C.pointer(d["B"].desc) if d["B"] else PCsr() for d in keep])
+    Ta = (PPre * n)(*[C.pointer(d["T"]) for d in keep])
+    Oa = (POpt * n)(*[C.pointer(d["opts"]) for d in keep])
+    out = (C.c_void_p * n)()
+    sts = (C.c_int * n)()
+    st = lib().gplhr_create_batched(n, Aa, Ba, (C.c_double * (2 * n))(*sig), (C.c_int32 * n)(*ks),
+                                    (C.c_int32 * n)(*ms), Ta, Oa, out, sts, nthreads)
     _check(st, None)
-    return out.value
+    return [out[i] for i in range(n)]
 
 
 def gplhr_destroy(ctx):
@@ -434,11 +487,12 @@ class GPLHR:
                  maxit=500, lock=True, stream=0, products="auto", precision="fp64",
                  switch_tol=1e-5, stall_iters=5, pencil="factored", inner_steps=0,
                  fp64_gemm="tensor", graphs=False, autotune=False, p_mode="thick", right_proj=True,
-                 variant="schur"):
+                 variant="schur", wait_limit=0, wait_probe=False):
         self.n, self.k = A.shape[0], k
         self.ctx = gplhr_create(A, B, complex(sigma), k, m, precond, block_size, T, tol, maxit,
                                 lock, stream, products, precision, switch_tol, stall_iters, pencil,
-                                inner_steps, fp64_gemm, graphs, autotune, p_mode, right_proj, variant)
+                                inner_steps, fp64_gemm, graphs, autotune, p_mode, right_proj, variant,
+                                wait_limit, wait_probe)
 
     def solve(self, V0=None, seed=0, allow_notconv=False):
         return gplhr_solve(self.ctx, V0, seed, allow_notconv)

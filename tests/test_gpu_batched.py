@@ -89,3 +89,45 @@ def test_iterate_batched_on_the_batched_workload_copy():
         assert info.iters == 5
         assert np.all(np.isfinite(s.vectors()["lam"]))
         s.close()
+
+
+def _spec(p, tol=1e-10):
+    A, B, sigma, k, m, prec, bs, V0 = p[:8]
+    d = dict(A=A, B=B, sigma=sigma, k=k, m=m, precond=prec, block_size=bs, tol=tol, maxit=400)
+    if len(p) > 8:
+        d["T"] = p[8]
+    return d
+
+
+def test_create_batched_equals_individual_creates():
+    """gplhr_create_batched (contexts created concurrently by host threads) gives contexts
+    whose batched solves equal solves of contexts created one by one."""
+    ps = _pencils()
+    solo = []
+    for p in ps:
+        s, V0 = _make(p)
+        info = s.solve(V0)
+        solo.append((info.iters, s.vectors()["lam"]))
+        s.close()
+    ctxs = G.gplhr_create_batched([_spec(p) for p in ps], nthreads=4)
+    try:
+        st, infos, sts = G.gplhr_solve_batched(ctxs, [p[7] for p in ps], nthreads=3)
+        assert st == G.GPLHR_OK and all(x == G.GPLHR_OK for x in sts)
+        for c, p, info, (it, lam) in zip(ctxs, ps, infos, solo):
+            assert info.iters == it
+            assert np.array_equal(G.gplhr_vectors(c, p[0].shape[0], p[3])["lam"], lam)
+    finally:
+        for c in ctxs:
+            G.gplhr_destroy(c)
+
+
+def test_create_batched_is_all_or_nothing():
+    """One invalid entry (k = 33) fails the whole call: EINVAL, the message names the
+    entry, and no context is left behind."""
+    ps = _pencils()
+    specs = [_spec(p) for p in ps]
+    specs[2]["k"] = 33
+    with pytest.raises(G.GplhrError) as e:
+        G.gplhr_create_batched(specs, nthreads=4)
+    assert e.value.status == G.GPLHR_EINVAL
+    assert "context 2" in str(e.value)

@@ -112,3 +112,11 @@ def test_create_rejects_bad_input_without_gpu_work(built):
         G.gplhr_create(A, None, float("nan"), 2, 1)  # sigma not finite
     with pytest.raises(G.GplhrError):
         G.gplhr_create(A, None, 0.5, 4, 1)           # (m+3) k > n
+
+
+def test_create_batched_refuses_null_arrays_without_a_gpu(built):
+    import ctypes as C
+    out = (C.c_void_p * 1)()
+    st = built.gplhr_create_batched(1, None, None, None, None, None, None, None, out, None, 0)
+    assert st == G.GPLHR_EINVAL
+    assert "non-null" in G.gplhr_last_error(None)
