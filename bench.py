@@ -41,7 +41,9 @@ sys.path.insert(0, ROOT)
 METRIC = "s to k eigenpairs @1e-8 resid (FP64 vs mixed); SpMM+Gram HBM GB/s vs peak"
 FP64_PEAK_GFLOPS = 1250.0   # GB300 dense FP64 (profiling recipe table); probe measured 1203
 # DRAM bytes per launch of this workload in FP64 (mean over one iteration's launches of the
-# kernel class), from one-pass ncu captures (profiles/gram_traffic_convdiff3d_64cubed.md)
+# kernel class), from one-pass ncu captures of the same kernels: stored values, not measured
+# by this run; the JSON line says so in "traffic_source"
+TRAFFIC_SOURCE = "stored ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), not this run"
 TRAFFIC_64CUBED = {
     "gram_tc": 62.3e6,     # tc_gram_narrow_kernel / tc_gram_wide_kernel, 27 launches
     "combine_tc": 68.3e6,  # tc_combine_kernel, 31 launches
@@ -241,6 +243,7 @@ def main():
             "kernel": dom, "bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved_gbs / hbm_peak,
             "traffic": TRAFFIC_64CUBED.get(dom) if default_full else None,
+            "traffic_source": (TRAFFIC_SOURCE if default_full and dom in TRAFFIC_64CUBED else None),
             "note": (f"FP64 by integer digits on the tensor cores: algorithmic bytes / event time of the "
                      f"{d['launches']} {dom} launches (of measured copy bandwidth); the kernel is bound by "
                      f"its integer work (digit split, exact rounding), the tensor pipe is mostly idle; "
@@ -301,6 +304,7 @@ def main():
             line["solve_gmres"] = time_to_pairs(G, stream, "fp64", args.inner_steps)
             if not args.no_mixed:
                 line["solve_gmres_mixed"] = time_to_pairs(G, stream, "mixed", args.inner_steps)
+        line.update(other_workloads(G, stream))
     if rank == 0 and not args.no_cpu:
         sample = 3
         spi = oracle_iterations(pr, sample, 0)
@@ -462,11 +466,23 @@ def batched_throughput(G, K):
 def time_to_pairs(G, stream, precision, inner_steps=0):
     """Seconds to k eigenpairs at the residual target, complex-scaled Schroedinger 256^2
     (inner_steps > 0: T = that many block GMRES steps around the block-Jacobi T0)."""
-    import torch
     from paper_1506_06829_gb300 import problems as P
     pr = P.config3()
-    s = G.GPLHR(pr.A, None, pr.sigma, pr.k, pr.m, pr.precond, pr.block_size, tol=pr.tol,
-                maxit=2000, stream=stream.cuda_stream, precision=precision, inner_steps=inner_steps, graphs=True)
+    out = solve_timed(G, stream, pr, precision, maxit=2000, inner_steps=inner_steps, graphs=True)
+    out["workload"] = (f"{pr.name} (complex-scaled Schroedinger, n = {pr.n}, k = {pr.k}, m = {pr.m}, "
+                       f"block-Jacobi {pr.block_size}, tol {pr.tol})")
+    return out
+
+
+def solve_timed(G, stream, pr, precision, maxit, **kw):
+    """One solve from the seeded start block on the device: seconds to k pairs (CUDA events
+    on the library's stream around gplhr_solve), or the time to the iteration cap when it
+    does not converge (then "converged": false, as the paper reports DNC)."""
+    import torch
+    prec = kw.pop("precond", pr.precond)
+    bs = kw.pop("block_size", pr.block_size)
+    s = G.GPLHR(pr.A, pr.B, pr.sigma, pr.k, pr.m, prec, bs, tol=pr.tol, maxit=maxit,
+                stream=stream.cuda_stream, precision=precision, **kw)
     V0 = torch.from_numpy(pr.start_block()).to("cuda")
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -476,12 +492,57 @@ def time_to_pairs(G, stream, precision, inner_steps=0):
     torch.cuda.synchronize()
     vec = s.vectors()
     s.close()
-    return {"workload": f"{pr.name} (complex-scaled Schroedinger, n = {pr.n}, k = {pr.k}, m = {pr.m}, "
-                        f"block-Jacobi {pr.block_size}, tol {pr.tol})",
-            "s_to_k_pairs": e0.elapsed_time(e1) / 1e3, "iterations": info.iters,
-            "precision": precision, "fp32_iterations": info.fp32_iters, "inner_gmres_steps": inner_steps,
-            "sparse_products": info.n_spmm, "preconditioner_applications": info.n_prec,
-            "converged": bool(info.nconv == pr.k), "max_resid": float(max(vec["resid"]))}
+    conv = bool(info.nconv == pr.k)
+    return {"s_to_k_pairs" if conv else "s_to_cap": e0.elapsed_time(e1) / 1e3, "iterations": info.iters,
+            "cap": maxit, "precision": precision, "fp32_iterations": info.fp32_iters,
+            "inner_gmres_steps": kw.get("inner_steps", 0), "sparse_products": info.n_spmm,
+            "preconditioner_applications": info.n_prec, "converged": conv,
+            "max_resid": float(max(vec["resid"])), "tol": pr.tol}
+
+
+def other_workloads(G, stream, quick=False):
+    """Seconds to k pairs (or DNC at a stated cap) on the standard, batched-pencil and
+    differentiation workloads, FP64 and mixed, with the preconditioners that reach the
+    pairs and with the ones the workloads name."""
+    import numpy as np
+    import scipy.sparse as sp
+    from paper_1506_06829_gb300 import problems as P
+    out = {}
+    # standard problem 32^2, sigma = 4/h^2: its Jacobi preconditioner is T = I (constant
+    # diagonal) and never converges; the exact shift-invert T (dense inverse as a CSR
+    # matrix) reaches the residual target at once (eigenvalue condition numbers ~1e9:
+    # sigma lies in the 1e-10 pseudospectrum)
+    pr = P.config1()
+    T1 = sp.csr_matrix(np.linalg.inv(pr.A.toarray() - pr.sigma * np.eye(pr.n)))
+    out["solve_cfg1"] = {
+        "workload": f"{pr.name} (convection-diffusion, n = {pr.n}, k = {pr.k}, m = {pr.m}, sigma = 4/h^2, "
+                    f"tol {pr.tol})",
+        "exact_shift_invert_fp64": solve_timed(G, stream, pr, "fp64", 100, precond="csr", T=T1),
+        "exact_shift_invert_mixed": solve_timed(G, stream, pr, "mixed", 100, precond="csr", T=T1),
+        "jacobi_is_identity_fp64": solve_timed(G, stream, pr, "fp64", 3000, graphs=True),
+    }
+    # batched workload: its smallest pencil (16^2, B = M x M, Jacobi = T = I) with 16 inner
+    # block GMRES steps
+    p = P.config4()[1]
+    out["solve_cfg4_pencil"] = {
+        "workload": f"{p.name} (convection-diffusion pencil, B = MxM, n = {p.n}, k = {p.k}, m = {p.m}, "
+                    f"sigma mid-spectrum, tol {p.tol})",
+        "gmres16_fp64": solve_timed(G, stream, p, "fp64", 1000, inner_steps=16),
+        "gmres16_mixed": solve_timed(G, stream, p, "mixed", 1000, inner_steps=16),
+    }
+    # differentiation workload: full size (256^2) with 32 inner block GMRES steps around
+    # block-Jacobi 32 does not converge (DNC, as the paper reports at a cap); its 32^2 copy
+    # with the exact shift-invert T converges in 3 iterations
+    p5 = P.config5()
+    p5s = P.config5(32)
+    T5 = sp.csr_matrix(np.linalg.inv(p5s.A.toarray() - p5s.sigma * np.eye(p5s.n)))
+    out["solve_cfg5"] = {
+        "workload": f"{p5.name} (per-edge convection field, n = {p5.n}, k = {p5.k}, sigma = 4/h^2, tol {p5.tol})",
+        "full_gmres32_bj32_fp64": solve_timed(G, stream, p5, "fp64", 10 if quick else 30, precond="block_jacobi",
+                                              block_size=32, inner_steps=32),
+        "copy_32x32_exact_shift_invert_fp64": solve_timed(G, stream, p5s, "fp64", 100, precond="csr", T=T5),
+    }
+    return out
 
 
 if __name__ == "__main__":

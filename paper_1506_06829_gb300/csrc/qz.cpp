@@ -9,6 +9,9 @@
 //   * reordering by swapping adjacent 1x1 diagonal blocks with one right and one
 //     left plane rotation (Van Dooren's direct swap for triangular pencils);
 //   * a final unit-phase scaling that makes the diagonal of RB real non-negative.
+// When Phi is upper triangular (the projected pencil in factored form), the QZ runs on
+// (Psi, Phi): Phi is then the triangular factor from the start, and the QR half of the
+// Hessenberg-triangular reduction is skipped.
 #include "qz.h"
 
 #include <algorithm>
@@ -24,88 +27,92 @@ const double kEps = std::numeric_limits<double>::epsilon();
 // Plane rotation G = [[c, s], [-conj(s), c]] with c real >= 0 such that
 // G [f; g] = [r; 0].
 void givens(cd f, cd g, double& c, cd& s, cd& r) {
-  const double ag = std::abs(g);
+  const double gr = g.real(), gi = g.imag(), fr = f.real(), fi = f.imag();
+  const double ag2 = gr * gr + gi * gi, af2 = fr * fr + fi * fi;
+  // squares of moduli far from over- and underflow: the plain formulas are exact to
+  // rounding; otherwise the scaled library moduli
+  const bool plain = ag2 < 1e300 && af2 < 1e300 && (ag2 == 0.0 || ag2 > 1e-300) && (af2 == 0.0 || af2 > 1e-300);
+  const double ag = plain ? std::sqrt(ag2) : std::abs(g);
   if (ag == 0.0) {
     c = 1.0;
     s = 0.0;
     r = f;
     return;
   }
-  const double af = std::abs(f);
+  const double af = plain ? std::sqrt(af2) : std::abs(f);
   if (af == 0.0) {
     c = 0.0;
     s = std::conj(g) / ag;
     r = ag;
     return;
   }
-  const double nrm = std::hypot(af, ag);
-  const cd ph = f / af;
-  c = af / nrm;
-  s = ph * std::conj(g) / nrm;
-  r = ph * nrm;
+  const double nrm = plain ? std::sqrt(af2 + ag2) : std::hypot(af, ag);
+  const double iaf = 1.0 / af, inrm = 1.0 / nrm;
+  const double phr = fr * iaf, phi = fi * iaf;  // f / |f|
+  c = af * inrm;
+  s = cd((phr * gr + phi * gi) * inrm, (phi * gr - phr * gi) * inrm);  // ph conj(g) / nrm
+  r = cd(phr * nrm, phi * nrm);
 }
 
-// The rotations below work on the interleaved (re, im) doubles directly so that the
-// compiler can vectorise them.
+// Matrices of the QZ are held split-complex (separate real and imaginary planes, row-major)
+// so that every plane rotation is a loop of real multiply-adds over contiguous doubles,
+// which the compiler vectorises.  The accumulators are held transposed (Yt(j, i) = Y(i, j))
+// so that a rotation of two columns of Y runs over two contiguous rows.
+struct ZMat {
+  int n = 0;
+  std::vector<double> re, im;
+  explicit ZMat(int n_ = 0) : n(n_), re((size_t)n_ * n_, 0.0), im((size_t)n_ * n_, 0.0) {}
+  cd get(int i, int j) const { return cd(re[(size_t)i * n + j], im[(size_t)i * n + j]); }
+  void set(int i, int j, cd v) {
+    re[(size_t)i * n + j] = v.real();
+    im[(size_t)i * n + j] = v.imag();
+  }
+  double* R(int i) { return re.data() + (size_t)i * n; }
+  double* I(int i) { return im.data() + (size_t)i * n; }
+};
 
 // M <- G M on rows (i1, i2), columns [c0, c1): x' = c x + s y, y' = -conj(s) x + c y.
-void rot_rows(SqMat& M, int i1, int i2, double c, cd s, int c0, int c1) {
-  double* a = reinterpret_cast<double*>(&M(i1, 0));
-  double* b = reinterpret_cast<double*>(&M(i2, 0));
+void rot_rows(ZMat& M, int i1, int i2, double c, cd s, int c0, int c1) {
+  double* __restrict ar = M.R(i1);
+  double* __restrict ai = M.I(i1);
+  double* __restrict br = M.R(i2);
+  double* __restrict bi = M.I(i2);
   const double sr = s.real(), si = s.imag();
   for (int j = c0; j < c1; ++j) {
-    const double xr = a[2 * j], xi = a[2 * j + 1], yr = b[2 * j], yi = b[2 * j + 1];
-    a[2 * j] = c * xr + sr * yr - si * yi;
-    a[2 * j + 1] = c * xi + sr * yi + si * yr;
-    b[2 * j] = -sr * xr - si * xi + c * yr;
-    b[2 * j + 1] = -sr * xi + si * xr + c * yi;
+    const double xr = ar[j], xi = ai[j], yr = br[j], yi = bi[j];
+    ar[j] = c * xr + sr * yr - si * yi;
+    ai[j] = c * xi + sr * yi + si * yr;
+    br[j] = -sr * xr - si * xi + c * yr;
+    bi[j] = -sr * xi + si * xr + c * yi;
   }
 }
 
-// Y <- Y G^* on columns (j1, j2): the accumulation that keeps Y (G M) = Y_old M.
-// Y is held transposed (Yt(j, i) = Y(i, j)) so the two columns are contiguous rows:
-// x' = c x + conj(s) y, y' = -s x + c y.
-void rot_left_accum(SqMat& Yt, int j1, int j2, double c, cd s) {
-  double* a = reinterpret_cast<double*>(&Yt(j1, 0));
-  double* b = reinterpret_cast<double*>(&Yt(j2, 0));
-  const double sr = s.real(), si = s.imag();
-  for (int i = 0; i < Yt.n; ++i) {
-    const double xr = a[2 * i], xi = a[2 * i + 1], yr = b[2 * i], yi = b[2 * i + 1];
-    a[2 * i] = c * xr + sr * yr + si * yi;
-    a[2 * i + 1] = c * xi + sr * yi - si * yr;
-    b[2 * i] = -sr * xr + si * xi + c * yr;
-    b[2 * i + 1] = -sr * xi - si * xr + c * yi;
-  }
-}
-
-// YR <- YR Zr on columns (j1, j2), YR held transposed like YL:
-// x' = c x - conj(s) y, y' = s x + c y.
-void rot_right_accum(SqMat& Yt, int j1, int j2, double c, cd s) {
-  double* a = reinterpret_cast<double*>(&Yt(j1, 0));
-  double* b = reinterpret_cast<double*>(&Yt(j2, 0));
-  const double sr = s.real(), si = s.imag();
-  for (int i = 0; i < Yt.n; ++i) {
-    const double xr = a[2 * i], xi = a[2 * i + 1], yr = b[2 * i], yi = b[2 * i + 1];
-    a[2 * i] = c * xr - sr * yr - si * yi;
-    a[2 * i + 1] = c * xi - sr * yi + si * yr;
-    b[2 * i] = sr * xr - si * xi + c * yr;
-    b[2 * i + 1] = sr * xi + si * xr + c * yi;
-  }
+// Y <- Y G^* on columns (j1, j2) (rows of the transposed Yt): the accumulation that keeps
+// Y (G M) = Y_old M.  x' = c x + conj(s) y, y' = -s x + c y.
+void rot_left_accum(ZMat& Yt, int j1, int j2, double c, cd s) {
+  rot_rows(Yt, j1, j2, c, std::conj(s), 0, Yt.n);
 }
 
 // M <- M Zr on columns (j1, j2), rows [r0, r1), Zr = [[c, s], [-conj(s), c]]:
 // x' = c x - conj(s) y, y' = s x + c y.
-void rot_cols(SqMat& M, int j1, int j2, double c, cd s, int r0, int r1) {
+void rot_cols(ZMat& M, int j1, int j2, double c, cd s, int r0, int r1) {
   const double sr = s.real(), si = s.imag();
+  const int n = M.n;
+  double* __restrict re = M.re.data();
+  double* __restrict im = M.im.data();
   for (int i = r0; i < r1; ++i) {
-    double* a = reinterpret_cast<double*>(&M(i, j1));
-    double* b = reinterpret_cast<double*>(&M(i, j2));
-    const double xr = a[0], xi = a[1], yr = b[0], yi = b[1];
-    a[0] = c * xr - sr * yr - si * yi;
-    a[1] = c * xi - sr * yi + si * yr;
-    b[0] = sr * xr - si * xi + c * yr;
-    b[1] = sr * xi + si * xr + c * yi;
+    const size_t p = (size_t)i * n + j1, q = (size_t)i * n + j2;
+    const double xr = re[p], xi = im[p], yr = re[q], yi = im[q];
+    re[p] = c * xr - sr * yr - si * yi;
+    im[p] = c * xi - sr * yi + si * yr;
+    re[q] = sr * xr - si * xi + c * yr;
+    im[q] = sr * xi + si * xr + c * yi;
   }
+}
+
+// YR <- YR Zr on columns (j1, j2), YR held transposed: x' = c x - conj(s) y, y' = s x + c y.
+void rot_right_accum(ZMat& Yt, int j1, int j2, double c, cd s) {
+  rot_rows(Yt, j1, j2, c, -std::conj(s), 0, Yt.n);
 }
 
 // Right rotation on columns (j1, j2) that zeroes the entry x = M(i, j1) against
@@ -115,6 +122,11 @@ void right_zeroing(cd x, cd y, double& c, cd& s) {
   givens(y, x, c, s, r);
 }
 
+double fro(const ZMat& M) {
+  double t = 0.0;
+  for (size_t i = 0; i < M.re.size(); ++i) t += M.re[i] * M.re[i] + M.im[i] * M.im[i];
+  return std::sqrt(t);
+}
 double fro(const SqMat& M) {
   double t = 0.0;
   for (const cd& v : M.a) t += std::norm(v);
@@ -140,77 +152,80 @@ cd wilkinson_shift(cd h11, cd h12, cd h21, cd h22, cd t11, cd t12, cd t22) {
 }
 
 // Reduce (H, T) to upper Hessenberg / upper triangular form, accumulating YL, YR.
-void hessenberg_triangular(SqMat& H, SqMat& T, SqMat& YL, SqMat& YR) {
+// t_triangular: T is upper triangular already (the QR phase is skipped).
+void hessenberg_triangular(ZMat& H, ZMat& T, ZMat& YL, ZMat& YR, bool t_triangular) {
   const int n = H.n;
-  // T -> upper triangular by left rotations (a Givens QR).
-  for (int j = 0; j < n; ++j) {
-    for (int i = n - 1; i > j; --i) {
-      if (T(i, j) == cd(0.0)) continue;
-      double c;
-      cd s, r;
-      givens(T(i - 1, j), T(i, j), c, s, r);
-      rot_rows(T, i - 1, i, c, s, 0, n);
-      rot_rows(H, i - 1, i, c, s, 0, n);
-      rot_left_accum(YL, i - 1, i, c, s);
-      T(i, j) = 0.0;
+  if (!t_triangular) {
+    // T -> upper triangular by left rotations (a Givens QR).
+    for (int j = 0; j < n; ++j) {
+      for (int i = n - 1; i > j; --i) {
+        if (T.get(i, j) == cd(0.0)) continue;
+        double c;
+        cd s, r;
+        givens(T.get(i - 1, j), T.get(i, j), c, s, r);
+        rot_rows(T, i - 1, i, c, s, j, n);
+        rot_rows(H, i - 1, i, c, s, 0, n);
+        rot_left_accum(YL, i - 1, i, c, s);
+        T.set(i, j, 0.0);
+      }
     }
   }
   // H -> upper Hessenberg, keeping T triangular.
   for (int j = 0; j + 2 < n; ++j) {
     for (int i = n - 1; i >= j + 2; --i) {
-      if (H(i, j) == cd(0.0)) continue;
+      if (H.get(i, j) == cd(0.0)) continue;
       double c;
       cd s, r;
-      givens(H(i - 1, j), H(i, j), c, s, r);
+      givens(H.get(i - 1, j), H.get(i, j), c, s, r);
       rot_rows(H, i - 1, i, c, s, j, n);
       rot_rows(T, i - 1, i, c, s, i - 1, n);
       rot_left_accum(YL, i - 1, i, c, s);
-      H(i, j) = 0.0;
+      H.set(i, j, 0.0);
       // fill T(i, i-1): zero it from the right on columns (i-1, i)
-      right_zeroing(T(i, i - 1), T(i, i), c, s);
+      right_zeroing(T.get(i, i - 1), T.get(i, i), c, s);
       rot_cols(T, i - 1, i, c, s, 0, i + 1);
       rot_cols(H, i - 1, i, c, s, 0, n);
       rot_right_accum(YR, i - 1, i, c, s);
-      T(i, i - 1) = 0.0;
+      T.set(i, i - 1, 0.0);
     }
   }
 }
 
 // Move a negligible T(j, j) (ilo <= j <= ihi) down to T(ihi, ihi) and deflate an
 // infinite eigenvalue by zeroing H(ihi, ihi-1).
-void chase_zero_down(SqMat& H, SqMat& T, SqMat& YL, SqMat& YR, int j, int ihi) {
+void chase_zero_down(ZMat& H, ZMat& T, ZMat& YL, ZMat& YR, int j, int ihi) {
   const int n = H.n;
-  T(j, j) = 0.0;
+  T.set(j, j, 0.0);
   for (int i = j; i < ihi; ++i) {
     double c;
     cd s, r;
-    givens(T(i, i + 1), T(i + 1, i + 1), c, s, r);
+    givens(T.get(i, i + 1), T.get(i + 1, i + 1), c, s, r);
     rot_rows(T, i, i + 1, c, s, i, n);
     rot_rows(H, i, i + 1, c, s, std::max(i - 1, 0), n);
     rot_left_accum(YL, i, i + 1, c, s);
-    T(i + 1, i + 1) = 0.0;
+    T.set(i + 1, i + 1, 0.0);
     if (i > 0) {
       // H(i+1, i-1) filled: zero it from the right on columns (i-1, i)
-      right_zeroing(H(i + 1, i - 1), H(i + 1, i), c, s);
+      right_zeroing(H.get(i + 1, i - 1), H.get(i + 1, i), c, s);
       rot_cols(H, i - 1, i, c, s, 0, std::min(i + 2, n));
       rot_cols(T, i - 1, i, c, s, 0, i + 1);
       rot_right_accum(YR, i - 1, i, c, s);
-      H(i + 1, i - 1) = 0.0;
+      H.set(i + 1, i - 1, 0.0);
     }
   }
   if (ihi > 0) {
     double c;
     cd s;
-    right_zeroing(H(ihi, ihi - 1), H(ihi, ihi), c, s);
+    right_zeroing(H.get(ihi, ihi - 1), H.get(ihi, ihi), c, s);
     rot_cols(H, ihi - 1, ihi, c, s, 0, ihi + 1);
     rot_cols(T, ihi - 1, ihi, c, s, 0, ihi + 1);
     rot_right_accum(YR, ihi - 1, ihi, c, s);
-    H(ihi, ihi - 1) = 0.0;
+    H.set(ihi, ihi - 1, 0.0);
   }
 }
 
 // Single-shift QZ iterations until (H, T) is upper triangular.
-bool qz_iterate(SqMat& H, SqMat& T, SqMat& YL, SqMat& YR) {
+bool qz_iterate(ZMat& H, ZMat& T, ZMat& YL, ZMat& YR) {
   const int n = H.n;
   const double normH = fro(H), normT = fro(T);
   const double atolH = kEps * std::max(normH, std::numeric_limits<double>::min());
@@ -223,10 +238,10 @@ bool qz_iterate(SqMat& H, SqMat& T, SqMat& YL, SqMat& YR) {
     // find the start of the active unreduced block
     int ilo = ihi;
     while (ilo > 0) {
-      const double h = std::abs(H(ilo, ilo - 1));
-      const double rel = kEps * (std::abs(H(ilo, ilo)) + std::abs(H(ilo - 1, ilo - 1)));
+      const double h = std::abs(H.get(ilo, ilo - 1));
+      const double rel = kEps * (std::abs(H.get(ilo, ilo)) + std::abs(H.get(ilo - 1, ilo - 1)));
       if (h <= atolH || h <= rel) {
-        H(ilo, ilo - 1) = 0.0;
+        H.set(ilo, ilo - 1, 0.0);
         break;
       }
       --ilo;
@@ -239,7 +254,7 @@ bool qz_iterate(SqMat& H, SqMat& T, SqMat& YL, SqMat& YR) {
     // a negligible diagonal entry of T in the active block: infinite eigenvalue
     bool chased = false;
     for (int j = ilo; j <= ihi; ++j) {
-      if (std::abs(T(j, j)) <= atolT) {
+      if (std::abs(T.get(j, j)) <= atolT) {
         chase_zero_down(H, T, YL, YR, j, ihi);
         chased = true;
         break;
@@ -251,33 +266,33 @@ bool qz_iterate(SqMat& H, SqMat& T, SqMat& YL, SqMat& YR) {
     cd mu;
     if (since_deflation % 10 == 0) {
       // exceptional shift
-      mu = H(ihi, ihi) / T(ihi, ihi) +
-           cd(0.75, 0.35) * std::abs(H(ihi, ihi - 1)) / std::abs(T(ihi - 1, ihi - 1));
+      mu = H.get(ihi, ihi) / T.get(ihi, ihi) +
+           cd(0.75, 0.35) * std::abs(H.get(ihi, ihi - 1)) / std::abs(T.get(ihi - 1, ihi - 1));
     } else {
-      mu = wilkinson_shift(H(ihi - 1, ihi - 1), H(ihi - 1, ihi), H(ihi, ihi - 1), H(ihi, ihi),
-                           T(ihi - 1, ihi - 1), T(ihi - 1, ihi), T(ihi, ihi));
+      mu = wilkinson_shift(H.get(ihi - 1, ihi - 1), H.get(ihi - 1, ihi), H.get(ihi, ihi - 1), H.get(ihi, ihi),
+                           T.get(ihi - 1, ihi - 1), T.get(ihi - 1, ihi), T.get(ihi, ihi));
     }
     // implicit single-shift sweep on [ilo, ihi]
     double c;
     cd s, r;
-    givens(H(ilo, ilo) - mu * T(ilo, ilo), H(ilo + 1, ilo), c, s, r);
+    givens(H.get(ilo, ilo) - mu * T.get(ilo, ilo), H.get(ilo + 1, ilo), c, s, r);
     rot_rows(H, ilo, ilo + 1, c, s, ilo, n);
     rot_rows(T, ilo, ilo + 1, c, s, ilo, n);
     rot_left_accum(YL, ilo, ilo + 1, c, s);
     for (int j = ilo; j < ihi; ++j) {
       // T(j+1, j) is the bulge: zero it from the right on columns (j, j+1)
-      right_zeroing(T(j + 1, j), T(j + 1, j + 1), c, s);
+      right_zeroing(T.get(j + 1, j), T.get(j + 1, j + 1), c, s);
       rot_cols(T, j, j + 1, c, s, 0, j + 2);
       rot_cols(H, j, j + 1, c, s, 0, std::min(j + 3, n));
       rot_right_accum(YR, j, j + 1, c, s);
-      T(j + 1, j) = 0.0;
+      T.set(j + 1, j, 0.0);
       if (j + 2 <= ihi) {
         // H(j+2, j) filled: zero it from the left on rows (j+1, j+2)
-        givens(H(j + 1, j), H(j + 2, j), c, s, r);
+        givens(H.get(j + 1, j), H.get(j + 2, j), c, s, r);
         rot_rows(H, j + 1, j + 2, c, s, j, n);
         rot_rows(T, j + 1, j + 2, c, s, j + 1, n);
         rot_left_accum(YL, j + 1, j + 2, c, s);
-        H(j + 2, j) = 0.0;
+        H.set(j + 2, j, 0.0);
       }
     }
   }
@@ -285,10 +300,10 @@ bool qz_iterate(SqMat& H, SqMat& T, SqMat& YL, SqMat& YR) {
 }
 
 // Swap the adjacent 1x1 diagonal pairs at (j, j+1) of the triangular pencil (A, B).
-void swap_adjacent(SqMat& A, SqMat& B, SqMat& YL, SqMat& YR, int j) {
+void swap_adjacent(ZMat& A, ZMat& B, ZMat& YL, ZMat& YR, int j) {
   const int n = A.n;
-  const cd a11 = A(j, j), a12 = A(j, j + 1), a22 = A(j + 1, j + 1);
-  const cd b11 = B(j, j), b12 = B(j, j + 1), b22 = B(j + 1, j + 1);
+  const cd a11 = A.get(j, j), a12 = A.get(j, j + 1), a22 = A.get(j + 1, j + 1);
+  const cd b11 = B.get(j, j), b12 = B.get(j, j + 1), b22 = B.get(j + 1, j + 1);
   // right eigenvector x of the 2x2 pencil for the pair (a22, b22): (b22 A - a22 B) x = 0
   const cd num = -(b22 * a12 - a22 * b12);
   const cd den = b22 * a11 - a22 * b11;
@@ -309,18 +324,18 @@ void swap_adjacent(SqMat& A, SqMat& B, SqMat& YL, SqMat& YR, int j) {
   rot_cols(B, j, j + 1, c, s, 0, j + 2);
   rot_right_accum(YR, j, j + 1, c, s);
   // first columns of A, B are now parallel in rows (j, j+1): zero row j+1 from the left
-  const double na = std::norm(A(j, j)) + std::norm(A(j + 1, j));
-  const double nb = std::norm(B(j, j)) + std::norm(B(j + 1, j));
+  const double na = std::norm(A.get(j, j)) + std::norm(A.get(j + 1, j));
+  const double nb = std::norm(B.get(j, j)) + std::norm(B.get(j + 1, j));
   cd r;
   if (na >= nb)
-    givens(A(j, j), A(j + 1, j), c, s, r);
+    givens(A.get(j, j), A.get(j + 1, j), c, s, r);
   else
-    givens(B(j, j), B(j + 1, j), c, s, r);
+    givens(B.get(j, j), B.get(j + 1, j), c, s, r);
   rot_rows(A, j, j + 1, c, s, j, n);
   rot_rows(B, j, j + 1, c, s, j, n);
   rot_left_accum(YL, j, j + 1, c, s);
-  A(j + 1, j) = 0.0;
-  B(j + 1, j) = 0.0;
+  A.set(j + 1, j, 0.0);
+  B.set(j + 1, j, 0.0);
 }
 
 bool key_less(cd a1, cd b1, cd a2, cd b2, cd sigma) {
@@ -343,20 +358,41 @@ double pair_distance(cd alpha, cd beta, cd sigma) {
 bool ordered_qz(const SqMat& Phi, const SqMat& Psi, cd sigma, SqMat& RA, SqMat& RB, SqMat& YL,
                 SqMat& YR, int nsort) {
   const int n = Phi.n;
-  RA = Phi;
-  RB = Psi;
-  SqMat YLt = SqMat::eye(n), YRt = SqMat::eye(n);  // transposed accumulators
   if (n == 0) {
-    YL = YLt;
-    YR = YRt;
+    RA = RB = YL = YR = SqMat(0);
     return true;
   }
-  hessenberg_triangular(RA, RB, YLt, YRt);
-  if (!qz_iterate(RA, RB, YLt, YRt)) return false;
+  // A triangular Phi (the factored projected pencil) is used as the triangular factor
+  // from the start: the QZ runs on (H, T) = (Psi, Phi), whose generalized Schur form is
+  // that of (Phi, Psi) with the two triangular factors exchanged, and the QR phase of the
+  // Hessenberg-triangular reduction is skipped.
+  bool phi_tri = true;
+  for (int i = 1; i < n && phi_tri; ++i)
+    for (int j = 0; j < i; ++j)
+      if (Phi(i, j) != cd(0.0)) {
+        phi_tri = false;
+        break;
+      }
+  ZMat H(n), T(n), YLt(n), YRt(n);
+  const SqMat& Hs = phi_tri ? Psi : Phi;
+  const SqMat& Ts = phi_tri ? Phi : Psi;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      H.set(i, j, Hs(i, j));
+      T.set(i, j, Ts(i, j));
+    }
+  for (int i = 0; i < n; ++i) {
+    YLt.re[(size_t)i * n + i] = 1.0;
+    YRt.re[(size_t)i * n + i] = 1.0;
+  }
+  hessenberg_triangular(H, T, YLt, YRt, phi_tri);
+  if (!qz_iterate(H, T, YLt, YRt)) return false;
+  ZMat& A = phi_tri ? T : H;  // the factor of Phi
+  ZMat& B = phi_tri ? H : T;  // the factor of Psi
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < i; ++j) {
-      RA(i, j) = 0.0;
-      RB(i, j) = 0.0;
+      A.set(i, j, 0.0);
+      B.set(i, j, 0.0);
     }
   // selection sort of the leading nsort positions: bring the nearest remaining pair to
   // position pos by adjacent swaps (positions past nsort keep the QZ's order)
@@ -364,29 +400,29 @@ bool ordered_qz(const SqMat& Phi, const SqMat& Psi, cd sigma, SqMat& RA, SqMat& 
   for (int pos = 0; pos < npos; ++pos) {
     int best = pos;
     for (int j = pos + 1; j < n; ++j)
-      if (key_less(RA(j, j), RB(j, j), RA(best, best), RB(best, best), sigma)) best = j;
-    for (int j = best - 1; j >= pos; --j) swap_adjacent(RA, RB, YLt, YRt, j);
+      if (key_less(A.get(j, j), B.get(j, j), A.get(best, best), B.get(best, best), sigma)) best = j;
+    for (int j = best - 1; j >= pos; --j) swap_adjacent(A, B, YLt, YRt, j);
   }
   // unit-phase scaling: RB(j, j) real >= 0
-  for (int j = 0; j < n; ++j) {
-    const double mag = std::abs(RB(j, j));
-    if (mag > 0.0) {
-      const cd t = std::conj(RB(j, j)) / mag;
-      for (int c = j; c < n; ++c) {
-        RA(j, c) *= t;
-        RB(j, c) *= t;
-      }
-      RB(j, j) = mag;
-      for (int i = 0; i < n; ++i) YLt(j, i) *= std::conj(t);
-    }
-  }
+  RA = SqMat(n);
+  RB = SqMat(n);
   YL = SqMat(n);
   YR = SqMat(n);
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      YL(i, j) = YLt(j, i);
-      YR(i, j) = YRt(j, i);
+  for (int j = 0; j < n; ++j) {
+    const cd bjj = B.get(j, j);
+    const double mag = std::abs(bjj);
+    const cd t = mag > 0.0 ? std::conj(bjj) / mag : cd(1.0);
+    for (int c = j; c < n; ++c) {
+      RA(j, c) = A.get(j, c) * t;
+      RB(j, c) = B.get(j, c) * t;
     }
+    if (mag > 0.0) RB(j, j) = mag;
+    const cd ct = std::conj(t);
+    for (int i = 0; i < n; ++i) {
+      YL(i, j) = YLt.get(j, i) * ct;
+      YR(i, j) = YRt.get(j, i);
+    }
+  }
   return true;
 }
 

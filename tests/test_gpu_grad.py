@@ -127,3 +127,65 @@ def test_gplhr_grad_refuses_a_degenerate_eigenvalue():
         with pytest.raises(G.GplhrError) as e:
             G.gplhr_grad(r.ctx, l.ctx, np.ones(k, dtype=complex), np.zeros(A.nnz, dtype=complex))
         assert e.value.status == G.GPLHR_EINVAL
+
+
+def test_differentiation_workload_gates_on_the_32x32_copy():
+    """The differentiation workload's checks on its 32 x 32 copy (n = 1024, sigma = 4/h^2 at
+    the centre of the spectrum, k = 8, B = I), both solves with the exact shift-invert T:
+
+    * the workload's loss L1 = sum Re lambda_i: its gradient w.r.t. the per-edge field
+      against the dense-eigendecomposition gradient.  sigma sits in the 32-fold Laplacian
+      eigenvalue split by the skew convection: the two real eigenvalues of the 8 have
+      opposite gradients and the six complex ones have real parts constant to first order,
+      so the sum nearly cancels (|grad L1| ~ 1e-10 against 0.1 per eigenvalue).  The
+      error is therefore measured against the scale of its terms, sum_i |grad Re lambda_i|;
+    * a loss without that cancellation, L2 = sum |lambda_i - sigma|^2, at 1e-6 relative
+      to the dense gradient;
+    * L2 against central differences (step 1e-6) of dense LAPACK eigenvalues on 32 seeded
+      edges: the differences carry about 1e-12 absolute rounding in each eigenvalue, i.e.
+      ~3e-5 relative noise at this gradient size; 1e-3 relative is the gate."""
+    from oracle.grad import eig_grad
+    from paper_1506_06829_gb300.autograd import eigenvalues
+    N, k = 32, 8
+    pr = P.config5(N)
+    b, sigma = pr.meta["b"], pr.sigma
+    J = P.edge_jacobian(N, pr.A)
+    pattern = (pr.A.indptr, pr.A.indices, pr.n)
+    T = _exact_T(pr.A, None, sigma)
+    L0 = torch.tensor(P.convdiff2d_edges(N, np.zeros_like(b)).data)
+    Jt = torch.tensor(J.toarray())
+    lam_d, X, Y = _dense_pairs(pr.A, None, sigma, k)
+    grads = {}
+    for name in ("L1", "L2"):
+        bt = torch.tensor(b, dtype=torch.float64, requires_grad=True)
+        lam = eigenvalues(L0 + Jt @ bt, pattern, sigma, k, 1, precond="csr", T=T, tol=1e-12, maxit=50)
+        loss = lam.real.sum() if name == "L1" else ((lam - sigma).abs() ** 2).sum()
+        g, = torch.autograd.grad(loss, bt)
+        grads[name] = g.numpy()
+        for mu in lam.detach().numpy():
+            assert np.min(np.abs(lam_d - mu)) <= 1e-9 * abs(mu)
+    # dense references: per-eigenvalue gradients of Re lambda_i, and the two losses
+    per = [J.T @ eig_grad(pr.A, None, lam_d[i:i + 1], X[:, i:i + 1], Y[:, i:i + 1], np.ones(1))[0]
+           for i in range(k)]
+    ref1 = np.sum(per, axis=0)
+    scale1 = np.sum([np.linalg.norm(p) for p in per])
+    ref2 = J.T @ eig_grad(pr.A, None, lam_d, X, Y, 2.0 * (lam_d - sigma))[0]
+    assert np.linalg.norm(grads["L1"] - ref1) <= 1e-6 * scale1
+    assert np.linalg.norm(grads["L2"] - ref2) <= 1e-6 * np.linalg.norm(ref2)
+    # central differences of L2 on 32 seeded edges
+    rng = np.random.default_rng(1005)
+    edges = rng.choice(b.size, size=32, replace=False)
+    delta = 1e-6
+
+    def L2(bb):
+        ev = sla.eigvals(P.convdiff2d_edges(N, bb).toarray())
+        near = ev[np.argsort(np.abs(ev - sigma))[:k]]
+        return float(np.sum(np.abs(near - sigma) ** 2))
+
+    fd = np.empty(edges.size)
+    for i, e in enumerate(edges):
+        bp, bm = b.copy(), b.copy()
+        bp[e] += delta
+        bm[e] -= delta
+        fd[i] = (L2(bp) - L2(bm)) / (2 * delta)
+    assert np.linalg.norm(grads["L2"][edges] - fd) <= 1e-3 * np.linalg.norm(fd)
