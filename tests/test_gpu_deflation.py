@@ -71,3 +71,51 @@ def test_two_stage_deflated_solve(generalized, precision):
         R[:k, k:] = v1["Q"].conj().T @ (M @ v2["V"]) if generalized else v1["V"].conj().T @ (A @ v2["V"])
         L = Q if generalized else V
         assert np.linalg.norm(M @ V - L @ R) < 1e-8 * OG.onenorm(A)
+
+
+@pytest.mark.parametrize("generalized", [False, True])
+def test_spectrum_slices_deflate_their_neighbours(generalized):
+    """Spectrum slicing composed with deflation (Sec. 3.6, last paragraph): three slices
+    of one pencil whose shifts are close enough that their k nearest eigenvalues overlap.
+    Slice i deflates the Schur vectors that slices 0..i-1 found, so the slices return
+    disjoint sets: together the k nearest eigenvalues of sigma_0, then of sigma_1 among
+    those not found yet, and so on (dense LAPACK), and all their Schur vectors form one
+    orthonormal basis of a partial (generalized) Schur form."""
+    if generalized:
+        # mild convection (cell Peclet 0.2, 0.1): a strongly non-normal pencil would tie the
+        # comparison with LAPACK to its eigenvalue condition numbers instead
+        A, B = P.convdiff2d_mass(14, 0.2, 0.1)
+        ev = sla.eigvals(A.toarray(), B.toarray())
+        Bd = B.toarray()
+    else:
+        A, B = P.schroedinger2d(14, 0.3), None
+        ev = sla.eigvals(A.toarray())
+        Bd = np.eye(A.shape[0])
+    n, k = A.shape[0], 3
+    near = ev[np.argsort(np.abs(ev - ev[np.argmin(np.abs(ev))]))]
+    # shifts between consecutive low eigenvalues, so neighbouring k-sets overlap
+    shifts = [complex(near[2]), complex(0.5 * (near[2] + near[4])), complex(near[4])]
+    Vs, Qs, lams = [], [], []
+    found = np.zeros(0, dtype=complex)
+    for i, sg in enumerate(shifts):
+        Tcsr = sp.csr_matrix(np.linalg.inv(A.toarray() - (sg + 1e-3) * Bd))
+        s = G.GPLHR(A, B, sg + 1e-3, k, 1, "csr", T=Tcsr, tol=1e-11, maxit=200)
+        if Vs:
+            G.gplhr_set_deflation(s.ctx, np.hstack(Vs), np.hstack(Qs) if generalized else None)
+        info = s.solve(P.start_block(n, k, 60 + i))
+        v = s.vectors()
+        s.close()
+        assert info.nconv == k
+        rest = np.array([mu for mu in ev if np.min(np.abs(found - mu), initial=np.inf) > 1e-8 * abs(mu)])
+        want = rest[np.argsort(np.abs(rest - (sg + 1e-3)))[:k]]
+        _match(v["lam"], want, 1e-9)
+        _match(want, v["lam"], 1e-9)
+        found = np.concatenate([found, v["lam"]])
+        Vs.append(v["V"])
+        Qs.append(v["Q"])
+    V = np.hstack(Vs)
+    assert np.linalg.norm(V.conj().T @ V - np.eye(V.shape[1])) < 1e-10
+    L = np.hstack(Qs) if generalized else V
+    R = L.conj().T @ (A @ V)
+    assert np.linalg.norm(np.tril(R, -1)) < 1e-8 * OG.onenorm(A)      # one triangular factor
+    assert np.linalg.norm(A @ V - L @ R) < 1e-8 * OG.onenorm(A)
