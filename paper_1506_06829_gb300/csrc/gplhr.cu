@@ -605,7 +605,8 @@ bool gram_tn_fits(const gplhr_ctx* ctx, int wx, int wy, bool self, TnShape* sh =
   while (t.cols < t.ts * buf) t.cols <<= 1;
   t.smem = gplhr::tn_smem_bytes(t.mt, t.np, wx, wy);
   if (t.smem > kCombSmemMax) return false;
-  if ((size_t)std::min(ctx->num_sms, (ctx->n + gplhr::TN_WIN - 1) / gplhr::TN_WIN) * wx * wy > ctx->gram_part_elems)
+  if ((size_t)std::min(ctx->num_sms, (ctx->n + gplhr::TN_HALF - 1) / gplhr::TN_HALF) * wx * wy >
+      ctx->gram_part_elems)
     return false;
   if (sh) *sh = t;
   return true;
@@ -635,8 +636,7 @@ gplhr_status gram_tn(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int
   t.np = sh.np;
   t.ts = sh.ts;
   t.tmem_cols = sh.cols;
-  const int nwin = (ctx->n + gplhr::TN_WIN - 1) / gplhr::TN_WIN;
-  const int grid = std::min(ctx->num_sms, nwin);
+  const int grid = std::min(ctx->num_sms, (ctx->n + gplhr::TN_HALF - 1) / gplhr::TN_HALF);
   const double by = 16.0 * ctx->n * (self ? wx : wx + wy);
   const int ph = prof_begin(ctx, KC_GRAM_TC, count ? 8.0 * ctx->n * nout_count : 0.0, count ? by : 0.0, 2);
   if ((self ? wx : wx + wy) <= 16)

@@ -889,23 +889,28 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tc_gram_kernel(TcGramArgs ta) {
 //   real column m (mt = ceil(14 wx / 128) tiles of 128 lanes); B = the 7 planes of Y'
 //   stacked along N: row b np + n.  One MMA per 16-row K step and M tile forms every
 //   plane product P_ab(m, n) = sum_r X'_a(r, m) Y'_b(r, n) at lane (a, m), column b np + n.
-// * Rows go in windows of 128 with per-column exponent bounds (a first pass over the
-//   window; |P_ab| <= 128 2^14 = 2^21, exact in FP32).  After a window the diagonals
+// * Each CTA takes a contiguous range of 64-row halves (CTA b: halves [b H / G, (b+1) H / G),
+//   H = ceil(n / 64), G CTAs) and cuts it into pieces of up to TN_PIECE = 8 halves (512
+//   rows) from its start.  A piece has per-column exponent bounds (a first pass over the
+//   piece) and accumulates every P_ab in tensor memory over all its rows (|P_ab| <=
+//   512 2^14 = 2^23, exact in FP32).  After a piece the diagonals
 //   D_d(m, n) = sum_{a+b=d} P_ab(m, n), d = 0..7, are summed across lanes in shared
 //   memory with integer additions (each P_ab taken exactly to int32), which are exact
-//   and so independent of their order; every G(m, n) is then formed and rounded once (tc_round96) and added to
-//   FP64 accumulators, and the CTA's partial C goes to partial[blockIdx.x][j wy + l].
-// * Pipeline: warps 0-7 (digits) take a window in two halves of 64 rows (one shared-
-//   memory stage each): task (row pair, complex column) = two loads, then the exponent
-//   pass (shared atomicMax over the window), then the digits of its half, and the half
-//   is marked full.  Warp 12 (one thread) issues each full half's MMAs into accumulator
+//   and so independent of their order; every G(m, n) is then formed and rounded once
+//   (tc_round96) and added to FP64 accumulators, and the CTA's partial C goes to
+//   partial[blockIdx.x][j wy + l].  One rounding per 512 rows instead of per 128: the
+//   epilogue's lane sums and roundings are what bounds this kernel.
+// * Pipeline: warps 0-7 (digits) take a piece 128 rows at a time for the exponent pass
+//   (task (row pair, complex column) = two loads, shared atomicMax), then half by half
+//   (the two shared-memory stages alternate) for the digits, and each half is marked full.  Warp 12 (one thread) issues each full half's MMAs into accumulator
 //   buffer (window % ts), so that the digit warps never wait for the issue.  Warps 8-11
 //   (epilogue) read the buffer (warp 8 + q: lanes 32 q .. 32 q + 31 of every tile), free
 //   it, and form the window's products.  X^* X (self) splits X once and writes both
 //   operands.  13 warps: at most 4 per SM sub-partition, 128 registers per thread.
 // Every wait has an iteration limit, as in the combination.
-constexpr int TN_WIN = 128;
-constexpr int TN_HALF = 64;
+constexpr int TN_WIN = 128;   // rows of one task sweep of the digit warps
+constexpr int TN_HALF = 64;   // rows per shared-memory stage
+constexpr int TN_PIECE = 8;   // halves per piece (one exponent pass, one epilogue)
 constexpr int TN_DWARPS = 8, TN_EWARPS = 4;
 constexpr int TN_THREADS = (TN_DWARPS + TN_EWARPS + 1) * 32;
 constexpr int TN_XMAX = 24, TN_YMAX = 16;
@@ -950,8 +955,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 
 // Rows r, r + 1 of complex column j of [X Y0 Y1] as (Re r, Re r+1, Im r, Im r+1); rows
-// beyond n read as zero.
-__device__ __forceinline__ void tn_load1(const TcGramNArgs& ta, int r, int j, double (&v)[4]) {
+// at or beyond rlim (the end of the piece, at most n) read as zero.
+__device__ __forceinline__ void tn_load1(const TcGramNArgs& ta, int r, int rlim, int j, double (&v)[4]) {
   const int wx = ta.wx;
   const double2* base;
   size_t ld;
@@ -966,28 +971,12 @@ __device__ __forceinline__ void tn_load1(const TcGramNArgs& ta, int r, int j, do
     ld = (size_t)ta.ldy1;
   }
   double2 x0 = make_double2(0.0, 0.0), x1 = x0;
-  if (r < ta.n) x0 = base[(size_t)r * ld];
-  if (r + 1 < ta.n) x1 = base[(size_t)(r + 1) * ld];
+  if (r < rlim) x0 = base[(size_t)r * ld];
+  if (r + 1 < rlim) x1 = base[(size_t)(r + 1) * ld];
   v[0] = x0.x;
   v[1] = x1.x;
   v[2] = x0.y;
   v[3] = x1.y;
-}
-
-// The digits thread's tasks of the window at row r0: task i is (row pair rp[i], complex
-// column j[i]) (rp[i] >= 64: no task).
-template <int NT>
-__device__ __forceinline__ void tn_load(const TcGramNArgs& ta, int r0, const int (&rp)[NT], const int (&j)[NT],
-                                        double (&v)[NT][4]) {
-#pragma unroll
-  for (int i = 0; i < NT; ++i) {
-    if (rp[i] < TN_WIN / 2) {
-      tn_load1(ta, r0 + 2 * rp[i], j[i], v[i]);
-    } else {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) v[i][c] = 0.0;
-    }
-  }
 }
 
 template <int NT>  // tasks per digits thread (4: W <= 16 loaded columns, 8: W <= 32)
@@ -1000,7 +989,8 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
   const size_t stage = tn_stage_bytes(mt, np);
   uint16_t* sA0 = reinterpret_cast<uint16_t*>(tn_smem);                       // stage h: + h stage
   int* sD = reinterpret_cast<int*>(tn_smem + 2 * stage);                      // [8][MX][SP]
-  __shared__ __align__(8) uint64_t bar_dfull[2], bar_dempty[2], bar_tfull[2], bar_tempty[2], bar_exp[TN_RING];
+  __shared__ __align__(8) uint64_t bar_dfull[2], bar_dempty[2], bar_tfull[2], bar_tempty[2], bar_exp[TN_RING],
+      bar_expfree[TN_RING];
   __shared__ uint32_t taddr_s;
   __shared__ volatile int abort_s;
   __shared__ int sE[TN_RING][2 * (TN_XMAX + TN_YMAX)], sBad[TN_RING][2 * (TN_XMAX + TN_YMAX)];
@@ -1017,7 +1007,10 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
       mbar_init(&bar_tfull[i], 1);
       mbar_init(&bar_tempty[i], TN_EWARPS * 32);
     }
-    for (int i = 0; i < TN_RING; ++i) mbar_init(&bar_exp[i], TN_DWARPS * 32);
+    for (int i = 0; i < TN_RING; ++i) {
+      mbar_init(&bar_exp[i], TN_DWARPS * 32);
+      mbar_init(&bar_expfree[i], TN_EWARPS * 32);
+    }
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
@@ -1030,14 +1023,16 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = taddr_s;
-  const int nwin = (n + TN_WIN - 1) / TN_WIN;
   const int bufcols = mt * 7 * np;
   const int ncol = ta.self ? MX : MX + NY;  // real columns with an exponent (Y' after X')
+  // this CTA's halves [h0, h1), cut into pieces of TN_PIECE halves from h0
+  const int H = (n + TN_HALF - 1) / TN_HALF;
+  const int h0 = (int)((long long)H * blockIdx.x / gridDim.x);
+  const int h1 = (int)((long long)H * (blockIdx.x + 1) / gridDim.x);
 
   if (warp < TN_DWARPS) {
     // ------------------------------------------------------------ digits role --
-    int it = 0;
-    int trp[NT], tj[NT];  // this thread's tasks t = tid + 256 i: (row pair, complex column), every window
+    int trp[NT], tj[NT];  // this thread's tasks t = tid + 256 i: (row pair of a 128-row sweep, complex column)
 #pragma unroll
     for (int i = 0; i < NT; ++i) {
       const int t = tid + 256 * i;
@@ -1047,53 +1042,68 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
     // A lane a 2 wx + c of plane a lies a 2 wx 64 elements after lane c when 2 wx is a
     // multiple of 8 (the core-matrix layout runs on across the 128-lane tiles)
     const bool alin = (MX & 7) == 0;
-    for (int win = blockIdx.x; win < nwin; win += gridDim.x, ++it) {
-      const int slot = it % TN_RING, r0 = win * TN_WIN;
-      double v[NT][4];  // this window's values, for the exponent pass (reloaded for the digits)
-      tn_load<NT>(ta, r0, trp, tj, v);
-      // the first stage free (the previous window's first-half products done): the
-      // exponent slot of this window is then free too (its epilogue is four windows back)
-      bool ok = bar_and(1, TN_DWARPS * 32, mbar_wait_bounded(&bar_dempty[0], (it & 1) ^ 1, &abort_s, ta.wait_tries));
-      if (!ok) {
-        if (tid == 0) {
-          abort_s = 1;
-          atomicExch(ta.err, 1);
-        }
-        break;
-      }
+    int it = 0, hc = 0;  // pieces, halves written
+    bool ok = true;
+    for (int ph = h0; ph < h1 && ok; ph += TN_PIECE, ++it) {
+      const int pe = min(h1, ph + TN_PIECE);
+      const int slot = it % TN_RING;
+      const int rlim = min(n, pe * TN_HALF);
+      // the exponent slot is free once the epilogue of piece it - TN_RING has rounded
+      ok = bar_and(1, TN_DWARPS * 32,
+                   mbar_wait_bounded(&bar_expfree[slot], ((uint32_t)(it / TN_RING) & 1) ^ 1, &abort_s, ta.wait_tries));
+      if (!ok) break;
       for (int c = tid; c < ncol; c += TN_DWARPS * 32) {
         sE[slot][c] = TC_NOEXP;
         sBad[slot][c] = 0;
       }
       bar_and(1, TN_DWARPS * 32, true);
+      // exponent pass over the piece, a 128-row sweep at a time (tasks four at a time)
+      for (int r0 = ph * TN_HALF; r0 < rlim; r0 += TN_WIN) {
 #pragma unroll
-      for (int i = 0; i < NT; ++i) {
-        const int rp = trp[i], j = tj[i];
-        if (rp < TN_WIN / 2) {
-          const int c = (j < wx ? 2 * j : MX + 2 * (j - wx));  // real columns c (Re), c + 1 (Im)
-          const int tre = max(tc_top(v[i][0]), tc_top(v[i][1])), tim = max(tc_top(v[i][2]), tc_top(v[i][3]));
-          if (tre > TC_NOEXP) atomicMax(&sE[slot][c], tre);
-          if (tim > TC_NOEXP) atomicMax(&sE[slot][c + 1], tim);
-          if (tc_nonfinite(v[i][0]) | tc_nonfinite(v[i][1])) sBad[slot][c] = 1;
-          if (tc_nonfinite(v[i][2]) | tc_nonfinite(v[i][3])) sBad[slot][c + 1] = 1;
+        for (int i0 = 0; i0 < NT; i0 += 4) {
+          double v[4][4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            if (trp[i0 + i] < TN_WIN / 2) {
+              tn_load1(ta, r0 + 2 * trp[i0 + i], rlim, tj[i0 + i], v[i]);
+            } else {
+#pragma unroll
+              for (int c = 0; c < 4; ++c) v[i][c] = 0.0;
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int rp = trp[i0 + i], j = tj[i0 + i];
+            if (rp < TN_WIN / 2) {
+              const int c = (j < wx ? 2 * j : MX + 2 * (j - wx));  // real columns c (Re), c + 1 (Im)
+              const int tre = max(tc_top(v[i][0]), tc_top(v[i][1])), tim = max(tc_top(v[i][2]), tc_top(v[i][3]));
+              if (tre > TC_NOEXP) atomicMax(&sE[slot][c], tre);
+              if (tim > TC_NOEXP) atomicMax(&sE[slot][c + 1], tim);
+              if (tc_nonfinite(v[i][0]) | tc_nonfinite(v[i][1])) sBad[slot][c] = 1;
+              if (tc_nonfinite(v[i][2]) | tc_nonfinite(v[i][3])) sBad[slot][c + 1] = 1;
+            }
+          }
         }
       }
       bar_and(1, TN_DWARPS * 32, true);
       mbar_arrive(&bar_exp[slot]);
-      for (int h = 0; h < 2; ++h) {
-        if (h == 1) {
-          ok = bar_and(1, TN_DWARPS * 32, mbar_wait_bounded(&bar_dempty[1], (it & 1) ^ 1, &abort_s, ta.wait_tries));
-          if (!ok) break;
-        }
-        uint16_t* sA = sA0 + (size_t)h * (stage / 2);
+      // digits, half by half, into the two stages in turn
+      for (int hh = ph; hh < pe; ++hh, ++hc) {
+        const int s = hc & 1;
+        ok = bar_and(1, TN_DWARPS * 32,
+                     mbar_wait_bounded(&bar_dempty[s], ((uint32_t)(hc >> 1) & 1) ^ 1, &abort_s, ta.wait_tries));
+        if (!ok) break;
+        uint16_t* sA = sA0 + (size_t)s * (stage / 2);
         uint16_t* sB = sA + (size_t)mt * 128 * TN_HALF;
+        const int hb = (hh - ph) & 1;                       // half of its 128-row sweep
+        const int rs = (ph + ((hh - ph) & ~1)) * TN_HALF;   // first row of that sweep
 #pragma unroll
         for (int i = 0; i < NT; ++i) {
           const int rp = trp[i], j = tj[i];
-          if (rp < TN_WIN / 2 && (rp >> 5) == h) {
+          if (rp < TN_WIN / 2 && (rp >> 5) == hb) {
             const int kk = 2 * (rp & 31);  // row within the half (even)
             double vv[4];
-            tn_load1(ta, r0 + 2 * rp, j, vv);
+            tn_load1(ta, rs + 2 * rp, rlim, j, vv);
 #pragma unroll
             for (int p = 0; p < 2; ++p) {  // Re, Im
               const int c = (j < wx ? 2 * j : MX + 2 * (j - wx)) + p;
@@ -1119,51 +1129,49 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
           }
         }
         fence_async_smem();
-        mbar_arrive(&bar_dfull[h]);
+        mbar_arrive(&bar_dfull[s]);
       }
-      if (!ok) {
-        if (tid == 0) {
-          abort_s = 1;
-          atomicExch(ta.err, 1);
-        }
-        break;
-      }
+    }
+    if (!ok && tid == 0) {
+      abort_s = 1;
+      atomicExch(ta.err, 1);
     }
   } else if (warp == TN_DWARPS + TN_EWARPS) {
     // --------------------------------------------------------------- MMA role --
     if (lane == 0) {
       const uint32_t sbase = smem_u32(tn_smem);
       const uint32_t idesc = umma_idesc_bf16(128, 7 * np);
-      int it = 0, last_b = -1;
+      int it = 0, hc = 0, last_b = -1;
       uint32_t last_v = 0;
-      for (int win = blockIdx.x; win < nwin; win += gridDim.x, ++it) {
+      bool ok = true;
+      for (int ph = h0; ph < h1 && ok; ph += TN_PIECE, ++it) {
+        const int pe = min(h1, ph + TN_PIECE);
         const int b = it % ts;
         const uint32_t vv = (uint32_t)(it / ts);
-        bool ok = true;
-        for (int h = 0; h < 2 && ok; ++h) {
-          ok = mbar_wait_bounded(&bar_dfull[h], it & 1, &abort_s, ta.wait_tries) &&
-               (h == 1 || mbar_wait_bounded(&bar_tempty[b], (vv & 1) ^ 1, &abort_s, ta.wait_tries));
+        for (int hh = ph; hh < pe; ++hh, ++hc) {
+          const int s = hc & 1;
+          ok = mbar_wait_bounded(&bar_dfull[s], (uint32_t)(hc >> 1) & 1, &abort_s, ta.wait_tries) &&
+               (hh > ph || mbar_wait_bounded(&bar_tempty[b], (vv & 1) ^ 1, &abort_s, ta.wait_tries));
           if (!ok) break;
           tc_fence_after();
-          const uint32_t a0 = sbase + (uint32_t)(h * stage);
+          const uint32_t a0 = sbase + (uint32_t)(s * stage);
           const uint32_t b0 = a0 + (uint32_t)(mt * 128 * TN_HALF * 2);
           for (int ks = 0; ks < TN_HALF / 16; ++ks)
             for (int t = 0; t < mt; ++t)
               umma_bf16(tmem + (uint32_t)(b * bufcols + t * 7 * np),
                         umma_desc(a0 + (uint32_t)(t * 128 * TN_HALF * 2) + ks * 256, 128, 8 * 128),
-                        umma_desc(b0 + ks * 256, 128, 8 * 128), idesc, (h > 0 || ks > 0) ? 1 : 0);
-          umma_commit(&bar_dempty[h]);
-          if (h == 1) {
+                        umma_desc(b0 + ks * 256, 128, 8 * 128), idesc, (hh > ph || ks > 0) ? 1 : 0);
+          umma_commit(&bar_dempty[s]);
+          if (hh == pe - 1) {
             umma_commit(&bar_tfull[b]);
             last_b = b;
             last_v = vv;
           }
         }
-        if (!ok) {
-          abort_s = 1;
-          atomicExch(ta.err, 1);
-          break;
-        }
+      }
+      if (!ok) {
+        abort_s = 1;
+        atomicExch(ta.err, 1);
       }
       if (last_b >= 0) {  // the last products complete before the tensor memory is freed
         volatile int never = 0;
@@ -1181,21 +1189,23 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[i][q] = 0.0;
     int it = 0;
-    for (int win = blockIdx.x; win < nwin; win += gridDim.x, ++it) {
+    for (int ph = h0; ph < h1; ph += TN_PIECE, ++it) {
       const int b = it % ts, slot = it % TN_RING;
       const uint32_t vv = (uint32_t)(it / ts);
-      bool ok = mbar_wait_bounded(&bar_exp[slot], (uint32_t)(it / TN_RING) & 1, &abort_s, ta.wait_tries) &&
-                mbar_wait_bounded(&bar_tfull[b], vv & 1, &abort_s, ta.wait_tries);
-      ok = __all_sync(0xffffffffu, ok);
+      // one decision for all epilogue warps (they share the named barrier below)
+      const bool ok = bar_and(
+          2, TN_EWARPS * 32,
+          mbar_wait_bounded(&bar_exp[slot], (uint32_t)(it / TN_RING) & 1, &abort_s, ta.wait_tries) &&
+              mbar_wait_bounded(&bar_tfull[b], vv & 1, &abort_s, ta.wait_tries));
       if (!ok) {
-        if (lane == 0) {
+        if (etid == 0) {
           abort_s = 1;
           atomicExch(ta.err, 1);
         }
         break;
       }
       tc_fence_after();
-      // plane products -> diagonal sums (exact integer additions)
+      // plane products -> diagonal sums (exact integer additions; |P_ab| <= 2^23)
       for (int t = 0; t < mt; ++t) {
         const int L = t * 128 + q4 * 32 + lane, a = L / MX, m = L - a * MX;
         const bool vl = a < TC_DIGITS;
@@ -1212,11 +1222,9 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
               const int bp = bp0 + e;
               if (bp < TC_DIGITS && vl && a + bp < TC_DIAG) {
                 int* dst = sD + ((size_t)(a + bp) * MX + m) * SP + n0;
-                // |P_ab| <= 2^21: 1.5 2^23 + P is exact and its low bits are P + 2^22
 #pragma unroll
                 for (int u = 0; u < 16; ++u)
-                  if (n0 + u < NY)
-                    atomicAdd(dst + u, __float_as_int(__uint_as_float(r[e][u]) + 12582912.0f) - 0x4B400000);
+                  if (n0 + u < NY) atomicAdd(dst + u, tc_f2i(r[e][u]));
               }
             }
           }
@@ -1225,7 +1233,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
       tc_fence_before();
       mbar_arrive(&bar_tempty[b]);
       bar_and(2, TN_EWARPS * 32, true);
-      // this thread's outputs: every G(m, n) of the window, rounded once, into FP64
+      // this thread's outputs: every G(m, n) of the piece, rounded once, into FP64
 #pragma unroll
       for (int i = 0; i < TN_OUT; ++i) {
         const int o = etid + TN_EWARPS * 32 * i;
@@ -1252,6 +1260,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1) tc_gram_narrow_kernel(TcGramNAr
         }
       }
       bar_and(2, TN_EWARPS * 32, true);  // the sums are zero again
+      mbar_arrive(&bar_expfree[slot]);
     }
     // G(2j, 2l) = Re x Re, (2j, 2l+1) = Re x Im, (2j+1, 2l) = Im x Re, (2j+1, 2l+1) = Im x Im
 #pragma unroll

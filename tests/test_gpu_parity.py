@@ -616,13 +616,27 @@ def test_variant_solve_with_locking(p_mode):
 
 # ------------------------------------------------------ Gram on the tensor cores (a9) --
 
-def _gram_window_bound(Xh, Yh, nwin_cta):
-    """Bound on |C - X^* Y| per real part for the tensor-core Gram: per 128-row window w
-    and real columns m of X', n of Y' the digit rounding and dropped pairs stay below
-    2^-53 (max_w|x'_m| sum_w|y'_n| + max_w|y'_n| sum_w|x'_m| + max_w|x'_m| max_w|y'_n|),
-    the window's rounding below u |G_w|; the FP64 sums over a CTA's windows and the
-    reduction over CTAs add (nwin_cta + 160) u sum_r |x'_rm||y'_rn|.  Re C and Im C each
-    add two real entries."""
+def _narrow_pieces(n, sms=152):
+    """Row intervals over which the narrow tensor-core Gram takes one exponent bound per
+    column: CTA b of G = min(152, H) takes the 64-row halves [b H / G, (b+1) H / G),
+    H = ceil(n / 64), in pieces of up to 8 halves from its first."""
+    H = -(-n // 64)
+    G = min(sms, H)
+    out = []
+    for b in range(G):
+        h0, h1 = H * b // G, H * (b + 1) // G
+        for ph in range(h0, h1, 8):
+            out.append((64 * ph, min(n, 64 * min(h1, ph + 8))))
+    return out
+
+
+def _gram_window_bound(Xh, Yh, nwin_cta, win=128, pieces=None):
+    """Bound on |C - X^* Y| per real part for the tensor-core Gram: per window w of `win`
+    rows (or per row interval of `pieces`) and real columns m of X', n of Y' the digit
+    rounding and dropped pairs stay below 2^-53 (max_w|x'_m| sum_w|y'_n| +
+    max_w|y'_n| sum_w|x'_m| + max_w|x'_m| max_w|y'_n|), the window's rounding below
+    u |G_w|; the FP64 sums over a CTA's windows and the reduction over CTAs add
+    (nwin_cta + 160) u sum_r |x'_rm||y'_rn|.  Re C and Im C each add two real entries."""
     n = Xh.shape[0]
     u = 2.0 ** -53
 
@@ -633,8 +647,8 @@ def _gram_window_bound(Xh, Yh, nwin_cta):
 
     Xr, Yr = real(Xh), real(Yh)
     Bm = np.zeros((Xr.shape[1], Yr.shape[1]))
-    for r0 in range(0, n, 128):
-        xs, ys = Xr[r0:r0 + 128], Yr[r0:r0 + 128]
+    for r0, r1 in (pieces if pieces is not None else [(r, min(n, r + win)) for r in range(0, n, win)]):
+        xs, ys = Xr[r0:r1], Yr[r0:r1]
         mx, my = xs.max(axis=0), ys.max(axis=0)
         sx, sy = xs.sum(axis=0), ys.sum(axis=0)
         Bm += 2 * u * (np.outer(mx, sy) + np.outer(sx, my) + np.outer(mx, my))
@@ -655,6 +669,8 @@ def _gram_window_bound(Xh, Yh, nwin_cta):
     (2048, 3, 5, False), (9000, 1, 1, True), (7001, 24, 1, False), (12345, 5, 16, False), (65536, 24, 24, True),
     # narrow after swapping the operands (C = (Y^* X)^*)
     (20000, 8, 24, False), (30001, 4, 20, False),
+    # narrow with several 512-row pieces per CTA
+    (233500, 16, 8, False), (467000, 8, 8, True),
     # wide after swapping the operands
     (30001, 16, 64, False),
     # more than 32 columns of Y: column blocks of at most 32, each by one of the forms above
@@ -681,6 +697,10 @@ def test_gram_tensor_matches_twice_precision(n, wx, wy, self_):
         G.gplhr_destroy(ctx)
     nwin_cta = -(-(-(-n // 128)) // 152)
     bre, bim = _gram_window_bound(Xh, Yh, nwin_cta)
+    # the narrow form takes one exponent bound per piece of up to 512 rows: its bound, where
+    # it is the larger (a valid bound whichever form ran)
+    b2re, b2im = _gram_window_bound(Xh, Yh, nwin_cta, pieces=_narrow_pieces(n))
+    bre, bim = np.maximum(bre, b2re), np.maximum(bim, b2im)
     u = 2.0 ** -53
     ere = np.abs(got.real - ref.real) - u * np.abs(ref.real)
     eim = np.abs(got.imag - ref.imag) - u * np.abs(ref.imag)
