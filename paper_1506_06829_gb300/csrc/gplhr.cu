@@ -730,23 +730,41 @@ gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy
     return gram_tw(ctx, Y0, wy0, X, wx, Blk{nullptr, 0}, 0, C, skip, wx * wy, count, false, ldc, true);
   if (tcok && gram_tc_fits(ctx, wx, wy))
     return gram_tc(ctx, X, wx, Y0, wy0, Y1, wy1, C, skip, nout_tc, count, ldc);
-  if (tcok && ctx->tc && wy > gplhr::TW_YMAX && ctx->n >= 2048 && wx <= gplhr::TG_AMAX) {
-    for (int c0 = 0; c0 < wy; c0 += gplhr::TW_YMAX) {  // column blocks of [Y0 Y1]
-      const int c1 = std::min(wy, c0 + gplhr::TW_YMAX);
-      // the block's columns of Y0, then of Y1 (either part may be empty)
-      const int a0 = std::min(c0, wy0), a1 = std::min(c1, wy0);
-      const int e0 = std::max(c0, wy0) - wy0, e1 = std::max(c1, wy0) - wy0;
-      Blk p0{Y0.p + a0, Y0.ld}, p1{e1 > e0 ? Y1.p + e0 : nullptr, Y1.ld};
-      int n0 = a1 - a0, n1 = e1 - e0;
-      if (n0 == 0) {
-        p0 = p1;
-        n0 = n1;
-        p1 = Blk{nullptr, 0};
-        n1 = 0;
+  if (tcok && ctx->tc && ctx->n >= 2048) {
+    // outside the forms' shapes (wx <= 128): column blocks of [Y0 Y1] of the widest of 32,
+    // 16, 8 columns that a form takes with all of X, each block a tensor-core product into
+    // its columns of C (the whole product's algorithmic work is booked here, the blocks'
+    // launches and times with each block)
+    int cb = 0;
+    for (int cand : {32, 16, 8}) {
+      const int w = std::min(cand, wy);
+      if (gram_tn_fits(ctx, wx, w, false) || gram_tw_fits(ctx, wx, w, false) || gram_tc_fits(ctx, wx, w)) {
+        cb = w;
+        break;
       }
-      TRY(gram(ctx, X, wx, p0, n0, p1, n1, C + c0, skip, false, count, fp32, -1, ldc));
     }
-    return GPLHR_OK;
+    if (cb > 0 && cb < wy) {
+      if (count) {
+        ctx->k_flops[KC_GRAM_TC] += 8.0 * ctx->n * nout_tc;
+        ctx->k_bytes[KC_GRAM_TC] += 16.0 * ctx->n * (self ? wx : wx + wy);
+      }
+      for (int c0 = 0; c0 < wy; c0 += cb) {
+        const int c1 = std::min(wy, c0 + cb);
+        // the block's columns of Y0, then of Y1 (either part may be empty)
+        const int a0 = std::min(c0, wy0), a1 = std::min(c1, wy0);
+        const int e0 = std::max(c0, wy0) - wy0, e1 = std::max(c1, wy0) - wy0;
+        Blk p0{Y0.p + a0, Y0.ld}, p1{e1 > e0 ? Y1.p + e0 : nullptr, Y1.ld};
+        int n0 = a1 - a0, n1 = e1 - e0;
+        if (n0 == 0) {
+          p0 = p1;
+          n0 = n1;
+          p1 = Blk{nullptr, 0};
+          n1 = 0;
+        }
+        TRY(gram(ctx, X, wx, p0, n0, p1, n1, C + c0, skip, false, false, fp32, -1, ldc));
+      }
+      return GPLHR_OK;
+    }
   }
   if (herm && (wy1 != 0 || wy0 != wx)) herm = false;
   const int nout = herm ? wx * (wx + 1) / 2 : wx * wy;
@@ -788,15 +806,16 @@ gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy
 struct In {
   Blk X;
   int w;
-  const double2* C;
+  const double2* C;  // w x c; row stride ldc (0: c)
   double2 alpha;
+  int ldc = 0;
 };
 
 // The combination on the tensor cores (FP64 by integer digits, tc.cuh): one persistent
 // pipelined CTA per SM, 128 rows per tile; two digit stages and two accumulator buffers
 // where shared and tensor memory allow.
-gplhr_status combine_tc(gplhr_ctx* ctx, gplhr::CombArgs a, int wsum, int c, int c_store, bool beta_one,
-                        bool count) {
+gplhr_status combine_tc(gplhr_ctx* ctx, gplhr::CombArgs a, int wsum, int c, int c_store, double flops,
+                        double bytes) {
   gplhr::TcCombArgs t{};
   t.a = a;
   t.a.upper = 0;
@@ -817,9 +836,7 @@ gplhr_status combine_tc(gplhr_ctx* ctx, gplhr::CombArgs a, int wsum, int c, int 
   const int grid = std::min(ntiles, (two ? 2 : 1) * ctx->num_sms);
   const size_t smem = gplhr::tc_comb_smem_bytes(t.kp, t.np, t.ds);
   t.a.normpart = c_store < c ? ctx->norm_part : nullptr;
-  const double by = 16.0 * ctx->n * (wsum + c_store * (beta_one ? 2.0 : 1.0));
-  const int ph = prof_begin(ctx, KC_COMBINE_TC, count ? 8.0 * ctx->n * (double)wsum * c : 0.0, count ? by : 0.0,
-                            c_store < c ? 2 : 1);
+  const int ph = prof_begin(ctx, KC_COMBINE_TC, flops, bytes, c_store < c ? 2 : 1);
   switch (t.kp / 8) {
     case 2:
       if (two)
@@ -846,6 +863,155 @@ gplhr_status combine_tc(gplhr_ctx* ctx, gplhr::CombArgs a, int wsum, int c, int 
   return GPLHR_OK;
 }
 
+// A combination wider than one tensor-core tile (more than 32 input or output columns)
+// as several tensor-core launches: output column blocks of at most 32 columns, each the
+// sum over chunks of at most 32 input columns; the first chunk of a block stores (beta as
+// given), the later ones add to it (beta = 1).  Every launch rounds once, so a block
+// carries one rounding per chunk, as a blocked FP64 sum does.  In place (outputs written
+// over input columns) the order keeps the inputs of every launch intact: the one block
+// that writes over inputs runs last, its chunk holding those inputs first; with upper
+// (X <- X R^{-1}, R^{-1} upper triangular) the blocks run from the last to the first, and
+// block [c0, c1) reads input columns 0 .. c1 - 1 only, its own chunk first.  Returns false,
+// launching nothing, for shapes it does not cover (norm-only columns, outputs overlapping
+// inputs in another pattern, more than COMB_MAX_IN pieces).  flops and bytes: the whole
+// combination's algorithmic counts, booked with its first launch.
+bool combine_tc_tiled(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, bool beta_one, const int* skip,
+                      Blk Y2, int c_split, bool upper, double flops, double bytes, gplhr_status* st) {
+  constexpr int KW = gplhr::TC_KMAX / 2, NW = gplhr::TC_NMAX / 2;
+  const int nin = (int)ins.size();
+  const int64_t n = ctx->n;
+  // the input column (t, j) that output column o overwrites, if any
+  std::vector<int> at(c, -1), aj(c, -1);
+  for (int o = 0; o < c; ++o) {
+    const double2* d = o < c_split ? Y.p + o : Y2.p + (o - c_split);
+    const int ld = o < c_split ? Y.ld : Y2.ld;
+    for (int t = 0; t < nin; ++t) {
+      const double2* x = ins[t].X.p;
+      const int lx = ins[t].X.ld, w = ins[t].w;
+      const bool meet = d < x + (n - 1) * lx + w && x < d + (n - 1) * ld + 1;
+      if (!meet) continue;
+      const int64_t diff = d - x;
+      if (ld != lx || diff < 0 || diff >= w) {
+        // same rows, other columns of one buffer: no overlap; anything else is not covered
+        if (ld == lx && ((diff % lx) + lx) % lx >= w && diff > -lx && diff < lx) continue;
+        return false;
+      }
+      if (at[o] >= 0) return false;
+      at[o] = t;
+      aj[o] = (int)diff;
+    }
+  }
+  struct Piece {
+    int t, j0, j1;
+  };
+  const int nbo = (c + NW - 1) / NW;
+  std::vector<int> cb(nbo + 1);
+  for (int b = 0; b <= nbo; ++b) cb[b] = (int)((int64_t)c * b / nbo);
+  // per block: the ordered list of launches, each a list of pieces of input columns
+  std::vector<std::vector<std::vector<Piece>>> plan(nbo);
+  auto pack = [&](std::vector<std::vector<Piece>>& L, int t, int j0, int j1) {
+    while (j0 < j1) {
+      int used = 0;
+      if (!L.empty())
+        for (const Piece& p : L.back()) used += p.j1 - p.j0;
+      if (L.empty() || used >= KW || (int)L.back().size() >= gplhr::COMB_MAX_IN) {
+        L.emplace_back();
+        used = 0;
+      }
+      const int e = std::min(j1, j0 + KW - used);
+      L.back().push_back(Piece{t, j0, e});
+      j0 = e;
+    }
+  };
+  std::vector<int> order(nbo);
+  if (upper) {
+    if (nin != 1 || ins[0].w != c || c_split != c) return false;
+    for (int o = 0; o < c; ++o)
+      if (at[o] >= 0 && aj[o] != o) return false;  // in place means Y = X
+    for (int b = 0; b < nbo; ++b) {
+      order[b] = nbo - 1 - b;
+      plan[b].push_back({Piece{0, cb[b], cb[b + 1]}});
+      plan[b].emplace_back();
+      pack(plan[b], 0, 0, cb[b]);
+      if (plan[b].back().empty()) plan[b].pop_back();
+    }
+  } else {
+    int ab = -1;  // the one block that writes over inputs
+    for (int o = 0; o < c; ++o)
+      if (at[o] >= 0) {
+        int b = 0;
+        while (cb[b + 1] <= o) ++b;
+        if (ab >= 0 && ab != b) return false;
+        ab = b;
+      }
+    for (int b = 0, i = 0; b < nbo; ++b)
+      if (b != ab) order[i++] = b;
+    if (ab >= 0) order[nbo - 1] = ab;
+    for (int b = 0; b < nbo; ++b) {
+      if (b == ab) {  // first launch: the overwritten input columns of each input
+        std::vector<int> lo(nin, INT32_MAX), hi(nin, -1);
+        for (int o = cb[b]; o < cb[b + 1]; ++o)
+          if (at[o] >= 0) {
+            lo[at[o]] = std::min(lo[at[o]], aj[o]);
+            hi[at[o]] = std::max(hi[at[o]], aj[o]);
+          }
+        std::vector<Piece> first;
+        int wfirst = 0;
+        for (int t = 0; t < nin; ++t)
+          if (hi[t] >= 0) {
+            first.push_back(Piece{t, lo[t], hi[t] + 1});
+            wfirst += hi[t] + 1 - lo[t];
+          }
+        if (wfirst > KW) return false;
+        plan[b].push_back(first);
+        plan[b].emplace_back();
+        for (int t = 0; t < nin; ++t) {
+          if (hi[t] < 0) {
+            pack(plan[b], t, 0, ins[t].w);
+          } else {
+            pack(plan[b], t, 0, lo[t]);
+            pack(plan[b], t, hi[t] + 1, ins[t].w);
+          }
+        }
+        if (plan[b].back().empty()) plan[b].pop_back();
+      } else {
+        for (int t = 0; t < nin; ++t) pack(plan[b], t, 0, ins[t].w);
+      }
+    }
+  }
+  bool first_launch = true;
+  for (int i = 0; i < nbo; ++i) {
+    const int b = order[i], c0 = cb[b], c1 = cb[b + 1], bw = c1 - c0;
+    for (size_t l = 0; l < plan[b].size(); ++l) {
+      gplhr::CombArgs a{};
+      a.nin = (int)plan[b][l].size();
+      int wsum = 0;
+      for (int q = 0; q < a.nin; ++q) {
+        const Piece& p = plan[b][l][q];
+        const In& in = ins[p.t];
+        const int ldc = in.ldc > 0 ? in.ldc : c;
+        a.in[q] = gplhr::CombIn{in.X.p + p.j0, in.X.ld, p.j1 - p.j0, in.C + (size_t)p.j0 * ldc + c0, ldc, in.alpha};
+        wsum += p.j1 - p.j0;
+      }
+      const int split = std::min(std::max(c_split - c0, 0), bw);
+      a.Y = split > 0 ? Y.p + c0 : nullptr;
+      a.ldy = Y.ld;
+      a.Y2 = split < bw ? Y2.p + std::max(c0 - c_split, 0) : nullptr;
+      a.ldy2 = Y2.ld;
+      a.c = bw;
+      a.c_split = split;
+      a.c_store = bw;
+      a.beta_one = (l > 0 || beta_one) ? 1 : 0;
+      a.skip = skip;
+      a.upper = 0;
+      *st = combine_tc(ctx, a, wsum, bw, bw, first_launch ? flops : 0.0, first_launch ? bytes : 0.0);
+      first_launch = false;
+      if (*st != GPLHR_OK) return true;
+    }
+  }
+  return true;
+}
+
 // Y(cols 0..c_split) / Y2 (cols c_split..c_store) = beta Y + sum alpha_t X_t C_t;
 // columns c_store..c only contribute |.|^2 sums (reduced into ctx->d_norms).
 gplhr_status combine(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, bool beta_one,
@@ -860,7 +1026,8 @@ gplhr_status combine(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, b
   a.nin = (int)ins.size();
   int wsum = 0;
   for (int t = 0; t < a.nin; ++t) {
-    a.in[t] = gplhr::CombIn{ins[t].X.p, ins[t].X.ld, ins[t].w, ins[t].C, ins[t].alpha};
+    a.in[t] = gplhr::CombIn{ins[t].X.p, ins[t].X.ld, ins[t].w, ins[t].C, ins[t].ldc > 0 ? ins[t].ldc : c,
+                            ins[t].alpha};
     wsum += ins[t].w;
   }
   a.Y = Y.p;
@@ -873,8 +1040,14 @@ gplhr_status combine(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, b
   a.beta_one = beta_one ? 1 : 0;
   a.skip = skip;
   a.upper = (upper && !use32 && a.nin == 1 && ins[0].w == c && c_store == c && c_split == c) ? 1 : 0;
-  if (!use32 && ctx->tc && wsum <= gplhr::TC_KMAX / 2 && c <= gplhr::TC_NMAX / 2 && ctx->n >= 4 * gplhr::TC_ROWS)
-    return combine_tc(ctx, a, wsum, c, c_store, beta_one, count);
+  if (!use32 && ctx->tc && ctx->n >= 4 * gplhr::TC_ROWS) {
+    const double fl = count ? 8.0 * ctx->n * (double)wsum * c : 0.0;
+    const double by = count ? 16.0 * ctx->n * (wsum + c_store * (beta_one ? 2.0 : 1.0)) : 0.0;
+    if (wsum <= gplhr::TC_KMAX / 2 && c <= gplhr::TC_NMAX / 2) return combine_tc(ctx, a, wsum, c, c_store, fl, by);
+    gplhr_status st = GPLHR_OK;
+    if (c_store == c && combine_tc_tiled(ctx, ins, Y, c, beta_one, skip, Y2, c_split, upper, fl, by, &st))
+      return st;
+  }
   int rows_tile = gplhr::comb_rows_tile(c, a.upper);
   const size_t esz = use32 ? sizeof(float2) : sizeof(double2);
   auto smem_of = [&](int rt) { return (size_t)(wsum * c + rt * wsum + rt * c) * esz; };

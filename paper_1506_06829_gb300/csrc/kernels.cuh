@@ -499,7 +499,8 @@ struct CombIn {
   const double2* X;
   int ldx;
   int w;
-  const double2* C;
+  const double2* C;  // w x c, row stride ldc
+  int ldc;
   double2 alpha;
 };
 struct CombArgs {
@@ -552,7 +553,8 @@ __global__ void combine_kernel(int n, int rows_per_cta, CombArgs a) {
     int off = 0;
     for (int t = 0; t < a.nin; ++t) {
       const int sz = a.in[t].w * a.c;
-      for (int e = threadIdx.x; e < sz; e += blockDim.x) cs[off + e] = to_t<T>(cmul(a.in[t].alpha, a.in[t].C[e]));
+      for (int e = threadIdx.x; e < sz; e += blockDim.x)
+        cs[off + e] = to_t<T>(cmul(a.in[t].alpha, a.in[t].C[(size_t)(e / a.c) * a.in[t].ldc + e % a.c]));
       off += sz;
     }
   }

@@ -267,7 +267,7 @@ __device__ __forceinline__ double tc_cval(const CombArgs& a, int wsum, int kk, i
     jj -= a.in[t].w;
     ++t;
   }
-  const double2 cv = cmul(a.in[t].alpha, a.in[t].C[(size_t)jj * a.c + l]);
+  const double2 cv = cmul(a.in[t].alpha, a.in[t].C[(size_t)jj * a.in[t].ldc + l]);
   return p == 0 ? (q == 0 ? cv.x : cv.y) : (q == 0 ? -cv.y : cv.x);
 }
 

@@ -135,9 +135,12 @@ def test_gram_parity(n, wx, wy):
         G.gplhr_destroy(ctx)
 
 
-@pytest.mark.parametrize("n,w,cond", [(3000, 8, 1e2), (20000, 24, 1e6), (4096, 16, 1e10)])
+@pytest.mark.parametrize("n,w,cond", [(3000, 8, 1e2), (20000, 24, 1e6), (4096, 16, 1e10),
+                                      (20000, 64, 1e6), (9001, 80, 1e3)])
 def test_orth_parity(n, w, cond):
-    """orth() = the unique thin QR factor with a real positive R diagonal (oracle: Householder)."""
+    """orth() = the unique thin QR factor with a real positive R diagonal (oracle: Householder).
+    w = 64, 80: the Gram products and the in-place X R^-1 run as several tensor-core launches
+    (column blocks from the last to the first)."""
     rng = np.random.default_rng(4)
     Uq, _ = np.linalg.qr(_rand_block(rng, n, w))
     Vq, _ = np.linalg.qr(_rand_block(rng, w, w))
@@ -497,15 +500,22 @@ def _dot2_product(X, C):
     (1000, 3, 2, True),       # fewer tiles than CTAs
     (30011, 16, 24, True),    # N' = 48: integer final rounding
     (5003, 8, 32, False),     # N' = 64: integer final rounding
-    (100003, 32, 16, True), (4099, 17, 5, False), (2048, 32, 32, True), (777, 24, 40, False)])
+    (100003, 32, 16, True), (4099, 17, 5, False), (2048, 32, 32, True), (777, 24, 40, False),
+    (20000, 48, 16, True),    # two input chunks (32 + 16)
+    (8192, 80, 32, False),    # three input chunks
+    (6007, 20, 64, True),     # two output blocks
+    (4099, 70, 80, False)])   # three chunks x three blocks, ragged
 def test_combine_tensor_and_dfma_match_fp64(n, w, c, beta):
     """Y = X C (+ Y) on the tensor cores (integer digits, FP32 accumulation) and by DFMA
     against numpy's FP64 product.  Rows span 1e-30 .. 1e30 and include zero rows, C has
     a zero column.  In the real form (K' = 2w terms per output, x' = Re/Im of x, c' of C)
     the digit scheme errs by at most (K'/4 + 2) u max_k |x'_rk| sum_k |c'_kn| (u = 2^-53:
     the input digits' rounding, the dropped digit pairs and one final rounding), a DFMA
-    dot product by at most (K' + 1) u (sum_k |x'_rk| |c'_kn| + |y_old|).  (777 rows,
-    40 columns: the DFMA path, outside the tensor-core shapes.)"""
+    dot product by at most (K' + 1) u (sum_k |x'_rk| |c'_kn| + |y_old|).  More than 32
+    output columns: blocks of at most 32, each its own tensor-core launches.  More than 32 input
+    columns: the tensor cores sum chunks of at most 32 (K' <= 64 each, the chunk bounds add
+    up to at most (64/4 + 2) u max|x'| sum|c'|), and each chunk after the first is added to
+    the rounded sum so far, one more rounding of at most u (max|x'| sum|c'| + |y_old|)."""
     rng = np.random.default_rng(40 + w)
     Xh = _rand_block(rng, n, w) * np.exp(rng.uniform(-69, 69, size=n))[:, None]
     Xh[::97] = 0.0
@@ -527,9 +537,11 @@ def test_combine_tensor_and_dfma_match_fp64(n, w, c, beta):
             "dfma": (K + 1) * u * y0max if beta else 0.0}
     A = sp.identity(n, format="csr")
     ctx = G.gplhr_create(A, None, 0.5, 8, 2)
+    nch = -(-w // 32)
+    chunks = 1.01 * (nch - 1) * u * (xmax * csum + (y0max if beta else 0.0))
     try:
-        for arith, fac in (("auto", K / 4 + 2), ("dfma", K + 1)):
-            bound = fac * u * xmax * csum + slack + yold[arith]
+        for arith, fac in (("auto", min(K, 64) / 4 + 2), ("dfma", K + 1)):
+            bound = fac * u * xmax * csum + slack + yold[arith] + (chunks if arith == "auto" else 0.0)
             Y = _dev(Y0)
             G.gplhr_combine(ctx, _dev(Xh), _dev(Ch), Y, beta, arith)
             got = _host(Y)
@@ -674,7 +686,9 @@ def _gram_window_bound(Xh, Yh, nwin_cta, win=128, pieces=None):
     # wide after swapping the operands
     (30001, 16, 64, False),
     # more than 32 columns of Y: column blocks of at most 32, each by one of the forms above
-    (20000, 80, 80, False), (9000, 64, 64, True), (12000, 24, 40, False), (4096, 40, 40, True)])
+    (20000, 80, 80, False), (9000, 64, 64, True), (12000, 24, 40, False), (4096, 40, 40, True),
+    # 80 x 32 and 128 x 24 fit no form: blocks of 16 columns
+    (8192, 80, 32, False), (6000, 128, 24, False), (2500, 112, 112, True)])
 def test_gram_tensor_matches_twice_precision(n, wx, wy, self_):
     """C = X^* Y on the tensor cores (GPLHR_GRAM_TENSOR) against a twice-working-
     precision product, with rows spread over 1e-30..1e30, zero rows and a zero column,
