@@ -548,10 +548,14 @@ bool gram_tc_fits(const gplhr_ctx* ctx, int wx, int wy) {
              ctx->gram_part_elems;
 }
 
+// cbw > 0: column blocks of cbw columns of [Y0 Y1], all in one launch (grid y = block),
+// the SMs shared evenly between the blocks.
 gplhr_status gram_tc(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy1, double2* C, const int* skip,
-                     int nout_count, bool count, int ldc) {
+                     int nout_count, bool count, int ldc, int cbw = 0) {
   gplhr::TcGramArgs t{};
   const int wy = wy0 + wy1;
+  if (cbw <= 0 || cbw > wy) cbw = wy;
+  const int nblk = (wy + cbw - 1) / cbw;
   t.n = ctx->n;
   t.X = X.p;
   t.ldx = X.ld;
@@ -566,20 +570,24 @@ gplhr_status gram_tc(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int
   t.skip = skip;
   t.err = ctx->d_diag + 2;
   t.wait_tries = ctx->tc_wait_tries;
-  t.np = ((2 * wy + 15) / 16) * 16;
+  t.np = ((2 * cbw + 15) / 16) * 16;
   t.mt = (2 * wx + 127) / 128;
+  t.cbw = cbw;
   t.tmem_cols = 32;
   while (t.tmem_cols < t.mt * gplhr::TC_DIAG * t.np) t.tmem_cols <<= 1;
   const int nwin = (ctx->n + gplhr::TG_WIN - 1) / gplhr::TG_WIN;
-  const int grid = std::min(ctx->num_sms, nwin);
+  const int grid = std::max(1, std::min(ctx->num_sms / nblk, nwin));
   const bool self = X.p == Y0.p && wy1 == 0;
   const double by = 16.0 * ctx->n * (self ? wx : wx + wy);
-  const int ph = prof_begin(ctx, KC_GRAM_TC, count ? 8.0 * ctx->n * nout_count : 0.0, count ? by : 0.0, 2);
-  gplhr::tc_gram_kernel<<<grid, gplhr::TG_THREADS, gplhr::tg_smem_bytes(t.mt, t.np), ctx->stream>>>(t);
+  const int ph = prof_begin(ctx, KC_GRAM_TC, count ? 8.0 * ctx->n * nout_count : 0.0, count ? by : 0.0, 1 + nblk);
+  gplhr::tc_gram_kernel<<<dim3(grid, nblk), gplhr::TG_THREADS, gplhr::tg_smem_bytes(t.mt, t.np), ctx->stream>>>(t);
   CK(cudaGetLastError());
-  const int nout = wx * wy;
-  gplhr::gram_reduce_kernel<<<(nout + gplhr::GRED_WARPS - 1) / gplhr::GRED_WARPS, 32 * gplhr::GRED_WARPS, 0,
-                               ctx->stream>>>(grid, nout, wx, wy, 0, ctx->gram_part, C, ldc, skip);
+  for (int b = 0; b < nblk; ++b) {
+    const int wyb = std::min(cbw, wy - b * cbw), nout = wx * wyb;
+    gplhr::gram_reduce_kernel<<<(nout + gplhr::GRED_WARPS - 1) / gplhr::GRED_WARPS, 32 * gplhr::GRED_WARPS, 0,
+                                 ctx->stream>>>(grid, nout, wx, wyb, 0, ctx->gram_part + (size_t)b * grid * wx * cbw,
+                                                C + b * cbw, ldc, skip);
+  }
   prof_end(ctx, ph);
   CK(cudaGetLastError());
   return GPLHR_OK;
@@ -742,6 +750,11 @@ gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy
         cb = w;
         break;
       }
+    }
+    if (cb > 0 && cb < wy && !gram_tn_fits(ctx, wx, cb, false) && !gram_tw_fits(ctx, wx, cb, false) &&
+        (size_t)ctx->num_sms * wx * cb <= ctx->gram_part_elems) {
+      // the blocks' form is tc_gram_kernel: all blocks in one launch
+      return gram_tc(ctx, X, wx, Y0, wy0, Y1, wy1, C, skip, nout_tc, count, ldc, cb);
     }
     if (cb > 0 && cb < wy) {
       if (count) {
@@ -1408,7 +1421,8 @@ gplhr_status residuals(gplhr_ctx* ctx) {
 }
 
 // Host: sorted QZ of the s x s pencil in h_phipsi, returns Ybar_R, Ybar_L, Rbar_A, Rbar_B.
-gplhr_status host_qz(gplhr_ctx* ctx, int s, SqMat& RAb, SqMat& RBb, SqMat& YLb, SqMat& YRb, int nsort = -1) {
+gplhr_status host_qz(gplhr_ctx* ctx, int s, SqMat& RAb, SqMat& RBb, SqMat& YLb, SqMat& YRb, int nsort = -1,
+                     int nyl = -1, int nyr = -1) {
   SqMat Phi(s), Psi(s);
   for (int i = 0; i < s; ++i)
     for (int j = 0; j < s; ++j) {
@@ -1422,7 +1436,7 @@ gplhr_status host_qz(gplhr_ctx* ctx, int s, SqMat& RAb, SqMat& RBb, SqMat& YLb, 
       }
     }
   ctx->n_qz += 1;
-  if (!gplhr::ordered_qz(Phi, Psi, ctx->sigma, RAb, RBb, YLb, YRb, nsort)) {
+  if (!gplhr::ordered_qz(Phi, Psi, ctx->sigma, RAb, RBb, YLb, YRb, nsort, nyl, nyr)) {
     ctx->err = "QZ iteration did not converge";
     return GPLHR_ENUMERIC;
   }
@@ -1649,7 +1663,7 @@ gplhr_status factored_pencil_qz(gplhr_ctx* ctx, int s, int sk, SqMat& RAb, SqMat
     for (int j = i; j < sk; ++j) F(k + i, k + j) = Racc(i, j);
   ctx->n_qz += 1;
   SqMat RFb;
-  if (!gplhr::ordered_qz(F, Psi, cd(0.0, 0.0), RFb, RBb, YLb, YRb, cv)) {
+  if (!gplhr::ordered_qz(F, Psi, cd(0.0, 0.0), RFb, RBb, YLb, YRb, cv, k, cv)) {
     ctx->err = "QZ iteration did not converge";
     return GPLHR_ENUMERIC;
   }
@@ -1751,7 +1765,7 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
   if (ctx->factored)
     TRY(factored_pencil_qz(ctx, s, sk, RAb, RBb, YLb, YRb, cv));
   else
-    TRY(host_qz(ctx, s, RAb, RBb, YLb, YRb, cv));
+    TRY(host_qz(ctx, s, RAb, RBb, YLb, YRb, cv, k, cv));
   // steps 25-28: V = Z Ybar_R(:, 1:k), P = Z Ybar_R(:, k+1:k+kk), Q = U Ybar_L(:, 1:k)
   double2* hy = ctx->h_small + 6 * k * k;
   double2* hl = hy + (size_t)s * cv;
@@ -2002,7 +2016,7 @@ gplhr_status eig_iterate_once(gplhr_ctx* ctx) {
                      ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   SqMat RAb, RBb, YLb, YRb;
-  TRY(host_qz(ctx, s, RAb, RBb, YLb, YRb, 2 * k));
+  TRY(host_qz(ctx, s, RAb, RBb, YLb, YRb, 2 * k, 0, 2 * k));
   SqMat RA2(2 * k), RB2(2 * k);
   for (int i = 0; i < 2 * k; ++i)
     for (int j = 0; j < 2 * k; ++j) {

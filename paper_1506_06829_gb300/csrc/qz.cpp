@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <limits>
 
 namespace gplhr {
@@ -71,14 +72,10 @@ struct ZMat {
   double* I(int i) { return im.data() + (size_t)i * n; }
 };
 
-// M <- G M on rows (i1, i2), columns [c0, c1): x' = c x + s y, y' = -conj(s) x + c y.
-void rot_rows(ZMat& M, int i1, int i2, double c, cd s, int c0, int c1) {
-  double* __restrict ar = M.R(i1);
-  double* __restrict ai = M.I(i1);
-  double* __restrict br = M.R(i2);
-  double* __restrict bi = M.I(i2);
-  const double sr = s.real(), si = s.imag();
-  for (int j = c0; j < c1; ++j) {
+// Two split-complex rows x, y of length len: x' = c x + s y, y' = -conj(s) x + c y.
+void rot_pair(double* __restrict ar, double* __restrict ai, double* __restrict br, double* __restrict bi, int len,
+              double c, double sr, double si) {
+  for (int j = 0; j < len; ++j) {
     const double xr = ar[j], xi = ai[j], yr = br[j], yi = bi[j];
     ar[j] = c * xr + sr * yr - si * yi;
     ai[j] = c * xi + sr * yi + si * yr;
@@ -87,32 +84,74 @@ void rot_rows(ZMat& M, int i1, int i2, double c, cd s, int c0, int c1) {
   }
 }
 
-// Y <- Y G^* on columns (j1, j2) (rows of the transposed Yt): the accumulation that keeps
-// Y (G M) = Y_old M.  x' = c x + conj(s) y, y' = -s x + c y.
-void rot_left_accum(ZMat& Yt, int j1, int j2, double c, cd s) {
-  rot_rows(Yt, j1, j2, c, std::conj(s), 0, Yt.n);
+// M <- G M on rows (i1, i2), columns [c0, c1): x' = c x + s y, y' = -conj(s) x + c y.
+void rot_rows(ZMat& M, int i1, int i2, double c, cd s, int c0, int c1) {
+  if (c1 > c0) rot_pair(M.R(i1) + c0, M.I(i1) + c0, M.R(i2) + c0, M.I(i2) + c0, c1 - c0, c, s.real(), s.imag());
 }
 
-// M <- M Zr on columns (j1, j2), rows [r0, r1), Zr = [[c, s], [-conj(s), c]]:
-// x' = c x - conj(s) y, y' = s x + c y.
-void rot_cols(ZMat& M, int j1, int j2, double c, cd s, int r0, int r1) {
+// The plane rotations of the reduction, each on adjacent indices (j, j + 1), in the order
+// they were applied to the pencil.  The Schur-vector accumulators are products of them;
+// only the leading columns the caller needs are formed, at the end (form_columns).
+// Left: YL <- YL K, K = [[c, -s], [conj(s), c]] (= G^*, so that YL (G M) = YL_old M);
+// right: YR <- YR Zr, Zr = [[c, s], [-conj(s), c]].  Both are logged as (j, c, s') with
+// K or Zr = [[c, s'], [-conj(s'), c]]: s' = -s on the left, s on the right.
+struct RotLog {
+  std::vector<int> j;
+  std::vector<double> c, sr, si;
+  void add(int jj, double cc, cd s) {
+    j.push_back(jj);
+    c.push_back(cc);
+    sr.push_back(s.real());
+    si.push_back(s.imag());
+  }
+};
+
+// Y <- Y G^* on columns (j1, j1 + 1): logged.
+void rot_left_accum(RotLog& YL, int j1, double c, cd s) { YL.add(j1, c, -s); }
+
+// M <- M Zr on columns (j, j + 1), rows [r0, r1), Zr = [[c, s], [-conj(s), c]]:
+// x' = c x - conj(s) y, y' = s x + c y.  The two columns' entries of a row are adjacent,
+// so a row is one pair of real parts R = (xr, yr) and one of imaginary parts I = (xi, yi):
+// R' = c R + (-sr, sr) swap(R) - si swap(I), I' = c I + (-sr, sr) swap(I) + si swap(R)
+// (generic two-lane vectors of the compiler, no target intrinsics).
+void rot_cols(ZMat& M, int j, double c, cd s, int r0, int r1) {
+  typedef double v2d __attribute__((vector_size(16)));
   const double sr = s.real(), si = s.imag();
   const int n = M.n;
   double* __restrict re = M.re.data();
   double* __restrict im = M.im.data();
+  const v2d vc = {c, c}, va = {-sr, sr}, vs = {si, si};
   for (int i = r0; i < r1; ++i) {
-    const size_t p = (size_t)i * n + j1, q = (size_t)i * n + j2;
-    const double xr = re[p], xi = im[p], yr = re[q], yi = im[q];
-    re[p] = c * xr - sr * yr - si * yi;
-    im[p] = c * xi - sr * yi + si * yr;
-    re[q] = sr * xr - si * xi + c * yr;
-    im[q] = sr * xi + si * xr + c * yi;
+    const size_t p = (size_t)i * n + j;
+    v2d R, I;
+    std::memcpy(&R, re + p, sizeof R);
+    std::memcpy(&I, im + p, sizeof I);
+    const v2d Rs = __builtin_shufflevector(R, R, 1, 0), Is = __builtin_shufflevector(I, I, 1, 0);
+    const v2d Rn = vc * R + va * Rs - vs * Is;
+    const v2d In = vc * I + va * Is + vs * Rs;
+    std::memcpy(re + p, &Rn, sizeof Rn);
+    std::memcpy(im + p, &In, sizeof In);
   }
 }
 
-// YR <- YR Zr on columns (j1, j2), YR held transposed: x' = c x - conj(s) y, y' = s x + c y.
-void rot_right_accum(ZMat& Yt, int j1, int j2, double c, cd s) {
-  rot_rows(Yt, j1, j2, c, -std::conj(s), 0, Yt.n);
+// YR <- YR Zr on columns (j1, j1 + 1): logged.
+void rot_right_accum(RotLog& YR, int j1, double c, cd s) { YR.add(j1, c, s); }
+
+// E (n x nc, split-complex rows) = M_1 M_2 ... M_m I(:, 0:nc) for the logged rotations
+// M_i = [[c, s'], [-conj(s'), c]] on rows (j, j + 1): applied to E from the last one; rows
+// below the highest one a rotation has reached so far are zero and are skipped.
+void form_columns(const RotLog& L, int n, int nc, std::vector<double>& er, std::vector<double>& ei) {
+  er.assign((size_t)n * nc, 0.0);
+  ei.assign((size_t)n * nc, 0.0);
+  for (int j = 0; j < nc; ++j) er[(size_t)j * nc + j] = 1.0;
+  int hi = nc - 1;
+  for (size_t t = L.j.size(); t-- > 0;) {
+    const int j = L.j[t];
+    if (j > hi) continue;  // both rows zero
+    if (j + 1 > hi) hi = j + 1;
+    rot_pair(er.data() + (size_t)j * nc, ei.data() + (size_t)j * nc, er.data() + (size_t)(j + 1) * nc,
+             ei.data() + (size_t)(j + 1) * nc, nc, L.c[t], L.sr[t], L.si[t]);
+  }
 }
 
 // Right rotation on columns (j1, j2) that zeroes the entry x = M(i, j1) against
@@ -120,6 +159,13 @@ void rot_right_accum(ZMat& Yt, int j1, int j2, double c, cd s) {
 void right_zeroing(cd x, cd y, double& c, cd& s) {
   cd r;
   givens(y, x, c, s, r);
+}
+
+// |z| from the sum of squares while that stays far from over- and underflow, else the
+// library modulus
+double cabs_fast(cd z) {
+  const double t = z.real() * z.real() + z.imag() * z.imag();
+  return (t < 1e300 && (t > 1e-300 || t == 0.0)) ? std::sqrt(t) : std::abs(z);
 }
 
 double fro(const ZMat& M) {
@@ -153,7 +199,7 @@ cd wilkinson_shift(cd h11, cd h12, cd h21, cd h22, cd t11, cd t12, cd t22) {
 
 // Reduce (H, T) to upper Hessenberg / upper triangular form, accumulating YL, YR.
 // t_triangular: T is upper triangular already (the QR phase is skipped).
-void hessenberg_triangular(ZMat& H, ZMat& T, ZMat& YL, ZMat& YR, bool t_triangular) {
+void hessenberg_triangular(ZMat& H, ZMat& T, RotLog& YL, RotLog& YR, bool t_triangular) {
   const int n = H.n;
   if (!t_triangular) {
     // T -> upper triangular by left rotations (a Givens QR).
@@ -165,7 +211,7 @@ void hessenberg_triangular(ZMat& H, ZMat& T, ZMat& YL, ZMat& YR, bool t_triangul
         givens(T.get(i - 1, j), T.get(i, j), c, s, r);
         rot_rows(T, i - 1, i, c, s, j, n);
         rot_rows(H, i - 1, i, c, s, 0, n);
-        rot_left_accum(YL, i - 1, i, c, s);
+        rot_left_accum(YL, i - 1, c, s);
         T.set(i, j, 0.0);
       }
     }
@@ -179,13 +225,13 @@ void hessenberg_triangular(ZMat& H, ZMat& T, ZMat& YL, ZMat& YR, bool t_triangul
       givens(H.get(i - 1, j), H.get(i, j), c, s, r);
       rot_rows(H, i - 1, i, c, s, j, n);
       rot_rows(T, i - 1, i, c, s, i - 1, n);
-      rot_left_accum(YL, i - 1, i, c, s);
+      rot_left_accum(YL, i - 1, c, s);
       H.set(i, j, 0.0);
       // fill T(i, i-1): zero it from the right on columns (i-1, i)
       right_zeroing(T.get(i, i - 1), T.get(i, i), c, s);
-      rot_cols(T, i - 1, i, c, s, 0, i + 1);
-      rot_cols(H, i - 1, i, c, s, 0, n);
-      rot_right_accum(YR, i - 1, i, c, s);
+      rot_cols(T, i - 1, c, s, 0, i + 1);
+      rot_cols(H, i - 1, c, s, 0, n);
+      rot_right_accum(YR, i - 1, c, s);
       T.set(i, i - 1, 0.0);
     }
   }
@@ -193,7 +239,7 @@ void hessenberg_triangular(ZMat& H, ZMat& T, ZMat& YL, ZMat& YR, bool t_triangul
 
 // Move a negligible T(j, j) (ilo <= j <= ihi) down to T(ihi, ihi) and deflate an
 // infinite eigenvalue by zeroing H(ihi, ihi-1).
-void chase_zero_down(ZMat& H, ZMat& T, ZMat& YL, ZMat& YR, int j, int ihi) {
+void chase_zero_down(ZMat& H, ZMat& T, RotLog& YL, RotLog& YR, int j, int ihi) {
   const int n = H.n;
   T.set(j, j, 0.0);
   for (int i = j; i < ihi; ++i) {
@@ -202,14 +248,14 @@ void chase_zero_down(ZMat& H, ZMat& T, ZMat& YL, ZMat& YR, int j, int ihi) {
     givens(T.get(i, i + 1), T.get(i + 1, i + 1), c, s, r);
     rot_rows(T, i, i + 1, c, s, i, n);
     rot_rows(H, i, i + 1, c, s, std::max(i - 1, 0), n);
-    rot_left_accum(YL, i, i + 1, c, s);
+    rot_left_accum(YL, i, c, s);
     T.set(i + 1, i + 1, 0.0);
     if (i > 0) {
       // H(i+1, i-1) filled: zero it from the right on columns (i-1, i)
       right_zeroing(H.get(i + 1, i - 1), H.get(i + 1, i), c, s);
-      rot_cols(H, i - 1, i, c, s, 0, std::min(i + 2, n));
-      rot_cols(T, i - 1, i, c, s, 0, i + 1);
-      rot_right_accum(YR, i - 1, i, c, s);
+      rot_cols(H, i - 1, c, s, 0, std::min(i + 2, n));
+      rot_cols(T, i - 1, c, s, 0, i + 1);
+      rot_right_accum(YR, i - 1, c, s);
       H.set(i + 1, i - 1, 0.0);
     }
   }
@@ -217,15 +263,15 @@ void chase_zero_down(ZMat& H, ZMat& T, ZMat& YL, ZMat& YR, int j, int ihi) {
     double c;
     cd s;
     right_zeroing(H.get(ihi, ihi - 1), H.get(ihi, ihi), c, s);
-    rot_cols(H, ihi - 1, ihi, c, s, 0, ihi + 1);
-    rot_cols(T, ihi - 1, ihi, c, s, 0, ihi + 1);
-    rot_right_accum(YR, ihi - 1, ihi, c, s);
+    rot_cols(H, ihi - 1, c, s, 0, ihi + 1);
+    rot_cols(T, ihi - 1, c, s, 0, ihi + 1);
+    rot_right_accum(YR, ihi - 1, c, s);
     H.set(ihi, ihi - 1, 0.0);
   }
 }
 
 // Single-shift QZ iterations until (H, T) is upper triangular.
-bool qz_iterate(ZMat& H, ZMat& T, ZMat& YL, ZMat& YR) {
+bool qz_iterate(ZMat& H, ZMat& T, RotLog& YL, RotLog& YR) {
   const int n = H.n;
   const double normH = fro(H), normT = fro(T);
   const double atolH = kEps * std::max(normH, std::numeric_limits<double>::min());
@@ -238,8 +284,8 @@ bool qz_iterate(ZMat& H, ZMat& T, ZMat& YL, ZMat& YR) {
     // find the start of the active unreduced block
     int ilo = ihi;
     while (ilo > 0) {
-      const double h = std::abs(H.get(ilo, ilo - 1));
-      const double rel = kEps * (std::abs(H.get(ilo, ilo)) + std::abs(H.get(ilo - 1, ilo - 1)));
+      const double h = cabs_fast(H.get(ilo, ilo - 1));
+      const double rel = kEps * (cabs_fast(H.get(ilo, ilo)) + cabs_fast(H.get(ilo - 1, ilo - 1)));
       if (h <= atolH || h <= rel) {
         H.set(ilo, ilo - 1, 0.0);
         break;
@@ -254,7 +300,7 @@ bool qz_iterate(ZMat& H, ZMat& T, ZMat& YL, ZMat& YR) {
     // a negligible diagonal entry of T in the active block: infinite eigenvalue
     bool chased = false;
     for (int j = ilo; j <= ihi; ++j) {
-      if (std::abs(T.get(j, j)) <= atolT) {
+      if (cabs_fast(T.get(j, j)) <= atolT) {
         chase_zero_down(H, T, YL, YR, j, ihi);
         chased = true;
         break;
@@ -278,20 +324,20 @@ bool qz_iterate(ZMat& H, ZMat& T, ZMat& YL, ZMat& YR) {
     givens(H.get(ilo, ilo) - mu * T.get(ilo, ilo), H.get(ilo + 1, ilo), c, s, r);
     rot_rows(H, ilo, ilo + 1, c, s, ilo, n);
     rot_rows(T, ilo, ilo + 1, c, s, ilo, n);
-    rot_left_accum(YL, ilo, ilo + 1, c, s);
+    rot_left_accum(YL, ilo, c, s);
     for (int j = ilo; j < ihi; ++j) {
       // T(j+1, j) is the bulge: zero it from the right on columns (j, j+1)
       right_zeroing(T.get(j + 1, j), T.get(j + 1, j + 1), c, s);
-      rot_cols(T, j, j + 1, c, s, 0, j + 2);
-      rot_cols(H, j, j + 1, c, s, 0, std::min(j + 3, n));
-      rot_right_accum(YR, j, j + 1, c, s);
+      rot_cols(T, j, c, s, 0, j + 2);
+      rot_cols(H, j, c, s, 0, std::min(j + 3, n));
+      rot_right_accum(YR, j, c, s);
       T.set(j + 1, j, 0.0);
       if (j + 2 <= ihi) {
         // H(j+2, j) filled: zero it from the left on rows (j+1, j+2)
         givens(H.get(j + 1, j), H.get(j + 2, j), c, s, r);
         rot_rows(H, j + 1, j + 2, c, s, j, n);
         rot_rows(T, j + 1, j + 2, c, s, j + 1, n);
-        rot_left_accum(YL, j + 1, j + 2, c, s);
+        rot_left_accum(YL, j + 1, c, s);
         H.set(j + 2, j, 0.0);
       }
     }
@@ -300,7 +346,7 @@ bool qz_iterate(ZMat& H, ZMat& T, ZMat& YL, ZMat& YR) {
 }
 
 // Swap the adjacent 1x1 diagonal pairs at (j, j+1) of the triangular pencil (A, B).
-void swap_adjacent(ZMat& A, ZMat& B, ZMat& YL, ZMat& YR, int j) {
+void swap_adjacent(ZMat& A, ZMat& B, RotLog& YL, RotLog& YR, int j) {
   const int n = A.n;
   const cd a11 = A.get(j, j), a12 = A.get(j, j + 1), a22 = A.get(j + 1, j + 1);
   const cd b11 = B.get(j, j), b12 = B.get(j, j + 1), b22 = B.get(j + 1, j + 1);
@@ -320,9 +366,9 @@ void swap_adjacent(ZMat& A, ZMat& B, ZMat& YL, ZMat& YR, int j) {
     c = nn / nrm;
     s = -ph * std::conj(den) / nrm;
   }
-  rot_cols(A, j, j + 1, c, s, 0, j + 2);
-  rot_cols(B, j, j + 1, c, s, 0, j + 2);
-  rot_right_accum(YR, j, j + 1, c, s);
+  rot_cols(A, j, c, s, 0, j + 2);
+  rot_cols(B, j, c, s, 0, j + 2);
+  rot_right_accum(YR, j, c, s);
   // first columns of A, B are now parallel in rows (j, j+1): zero row j+1 from the left
   const double na = std::norm(A.get(j, j)) + std::norm(A.get(j + 1, j));
   const double nb = std::norm(B.get(j, j)) + std::norm(B.get(j + 1, j));
@@ -333,7 +379,7 @@ void swap_adjacent(ZMat& A, ZMat& B, ZMat& YL, ZMat& YR, int j) {
     givens(B.get(j, j), B.get(j + 1, j), c, s, r);
   rot_rows(A, j, j + 1, c, s, j, n);
   rot_rows(B, j, j + 1, c, s, j, n);
-  rot_left_accum(YL, j, j + 1, c, s);
+  rot_left_accum(YL, j, c, s);
   A.set(j + 1, j, 0.0);
   B.set(j + 1, j, 0.0);
 }
@@ -356,7 +402,7 @@ double pair_distance(cd alpha, cd beta, cd sigma) {
 }
 
 bool ordered_qz(const SqMat& Phi, const SqMat& Psi, cd sigma, SqMat& RA, SqMat& RB, SqMat& YL,
-                SqMat& YR, int nsort) {
+                SqMat& YR, int nsort, int nyl, int nyr) {
   const int n = Phi.n;
   if (n == 0) {
     RA = RB = YL = YR = SqMat(0);
@@ -373,7 +419,8 @@ bool ordered_qz(const SqMat& Phi, const SqMat& Psi, cd sigma, SqMat& RA, SqMat& 
         phi_tri = false;
         break;
       }
-  ZMat H(n), T(n), YLt(n), YRt(n);
+  ZMat H(n), T(n);
+  RotLog YLt, YRt;
   const SqMat& Hs = phi_tri ? Psi : Phi;
   const SqMat& Ts = phi_tri ? Phi : Psi;
   for (int i = 0; i < n; ++i)
@@ -381,10 +428,6 @@ bool ordered_qz(const SqMat& Phi, const SqMat& Psi, cd sigma, SqMat& RA, SqMat& 
       H.set(i, j, Hs(i, j));
       T.set(i, j, Ts(i, j));
     }
-  for (int i = 0; i < n; ++i) {
-    YLt.re[(size_t)i * n + i] = 1.0;
-    YRt.re[(size_t)i * n + i] = 1.0;
-  }
   hessenberg_triangular(H, T, YLt, YRt, phi_tri);
   if (!qz_iterate(H, T, YLt, YRt)) return false;
   ZMat& A = phi_tri ? T : H;  // the factor of Phi
@@ -403,7 +446,11 @@ bool ordered_qz(const SqMat& Phi, const SqMat& Psi, cd sigma, SqMat& RA, SqMat& 
       if (key_less(A.get(j, j), B.get(j, j), A.get(best, best), B.get(best, best), sigma)) best = j;
     for (int j = best - 1; j >= pos; --j) swap_adjacent(A, B, YLt, YRt, j);
   }
-  // unit-phase scaling: RB(j, j) real >= 0
+  // the leading columns of the accumulators, then the unit-phase scaling: RB(j, j) real >= 0
+  const int ncl = nyl < 0 ? n : std::min(nyl, n), ncr = nyr < 0 ? n : std::min(nyr, n);
+  std::vector<double> lr, li, rr, ri;
+  form_columns(YLt, n, ncl, lr, li);
+  form_columns(YRt, n, ncr, rr, ri);
   RA = SqMat(n);
   RB = SqMat(n);
   YL = SqMat(n);
@@ -418,10 +465,10 @@ bool ordered_qz(const SqMat& Phi, const SqMat& Psi, cd sigma, SqMat& RA, SqMat& 
     }
     if (mag > 0.0) RB(j, j) = mag;
     const cd ct = std::conj(t);
-    for (int i = 0; i < n; ++i) {
-      YL(i, j) = YLt.get(j, i) * ct;
-      YR(i, j) = YRt.get(j, i);
-    }
+    if (j < ncl)
+      for (int i = 0; i < n; ++i) YL(i, j) = cd(lr[(size_t)i * ncl + j], li[(size_t)i * ncl + j]) * ct;
+    if (j < ncr)
+      for (int i = 0; i < n; ++i) YR(i, j) = cd(rr[(size_t)i * ncr + j], ri[(size_t)i * ncr + j]);
   }
   return true;
 }

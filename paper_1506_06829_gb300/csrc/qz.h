@@ -24,10 +24,11 @@ struct SqMat {
 
 // Ordered complex QZ (footnote to Alg. 2 step 2): Phi = YL RA YR^*, Psi = YL RB YR^*,
 // |RA(j,j)/RB(j,j) - sigma| non-decreasing over the leading nsort positions (< 0: all),
-// which hold the nsort pairs nearest sigma; RB(j,j) real >= 0.
+// which hold the nsort pairs nearest sigma; RB(j,j) real >= 0.  Only the leading nyl
+// columns of YL and nyr of YR are formed (< 0: all); the others are returned zero.
 // Returns false if the QZ iteration did not converge.
 bool ordered_qz(const SqMat& Phi, const SqMat& Psi, cd sigma, SqMat& RA, SqMat& RB, SqMat& YL,
-                SqMat& YR, int nsort = -1);
+                SqMat& YR, int nsort = -1, int nyl = -1, int nyr = -1);
 
 // Theorem 1 with Eqs. G1_fix/G2_fix: MA = G2 G^{-1} RA, MB = I - G1 G^{-1} RA.
 void m_factors(const SqMat& RA, const SqMat& RB, SqMat& MA, SqMat& MB);

@@ -258,16 +258,12 @@ __device__ __forceinline__ int tc_off(int row, int k, int KC) {  // element offs
   return ((row >> 3) * KC + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
 }
 
-// The value of C' at (kk, nn): stacked alpha_t C_t, complex entries as 2 x 2 real blocks.
-__device__ __forceinline__ double tc_cval(const CombArgs& a, int wsum, int kk, int nn) {
+// The value of C' at (kk, nn): stacked alpha_t C_t (staged in shared memory as sCv[j c + l]),
+// complex entries as 2 x 2 real blocks.
+__device__ __forceinline__ double tc_cval(const double2* sCv, int wsum, int c, int kk, int nn) {
   const int j = kk >> 1, p = kk & 1, l = nn >> 1, q = nn & 1;
-  if (j >= wsum || l >= a.c) return 0.0;
-  int t = 0, jj = j;
-  while (jj >= a.in[t].w) {
-    jj -= a.in[t].w;
-    ++t;
-  }
-  const double2 cv = cmul(a.in[t].alpha, a.in[t].C[(size_t)jj * a.in[t].ldc + l]);
+  if (j >= wsum || l >= c) return 0.0;
+  const double2 cv = sCv[j * c + l];
   return p == 0 ? (q == 0 ? cv.x : cv.y) : (q == 0 ? -cv.y : cv.x);
 }
 
@@ -356,11 +352,24 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, CPS) tc_combine_kernel(int n,
     colp[tid] = p;
     coll[tid] = ld;
   }
-  // B operand (C' digits): column exponents, then the digits of all kp x np entries
+  // B operand (C' digits): alpha_t C_t staged in shared memory (the A stages are free until
+  // the roles start; all threads load at once), column exponents, then the digits of all
+  // kp x np entries
+  double2* sCv = reinterpret_cast<double2*>(sA);
+  for (int e = tid; e < wsum * a.c; e += TC_PIPE_THREADS) {
+    const int j = e / a.c, l = e - j * a.c;
+    int t = 0, jj = j;
+    while (jj >= a.in[t].w) {
+      jj -= a.in[t].w;
+      ++t;
+    }
+    sCv[e] = cmul(a.in[t].alpha, a.in[t].C[(size_t)jj * a.in[t].ldc + l]);
+  }
+  __syncthreads();
   if (tid < np) {
     int G = TC_NOEXP, bad = 0;
     for (int kk = 0; kk < kp; ++kk) {
-      const double v = tc_cval(a, wsum, kk, tid);
+      const double v = tc_cval(sCv, wsum, a.c, kk, tid);
       G = max(G, tc_top(v));
       bad |= tc_nonfinite(v);
     }
@@ -381,7 +390,7 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, CPS) tc_combine_kernel(int n,
   for (int e = tid; e < kp * np; e += TC_PIPE_THREADS) {
     const int nn = e / kp, kk = e - nn * kp;
     float dg[TC_DIGITS];
-    tc_digits(tc_cval(a, wsum, kk, nn), sG[nn], dg);
+    tc_digits(tc_cval(sCv, wsum, a.c, kk, nn), sG[nn], dg);
 #pragma unroll
     for (int d = 0; d < TC_DIGITS; ++d)
       sB[tc_off(d * np + nn, kk, KC)] = (uint16_t)(__float_as_uint(dg[d]) >> 16);
@@ -656,13 +665,16 @@ struct TcGramArgs {
   const int* skip;   // nothing happens when non-null and *skip == 0
   int* err;          // set to 1 if a wait on the tensor core gave up
   int wait_tries;    // limit of the pipeline's mbarrier waits (tests lower it)
-  int np;            // 2 (wy0 + wy1) rounded up to a multiple of 16 (<= 64)
+  int np;            // 2 cbw rounded up to a multiple of 16 (<= 64)
   int mt;            // M tiles: 2 wx <= 128 mt (1 or 2; 2 needs np <= 32)
   int tmem_cols;     // power of two >= mt * 8 * np
+  int cbw;           // columns of [Y0 Y1] per column block: CTA (x, y) takes block y
 };
 
 // Dynamic shared memory: A digits (7 planes x mt x 128 x TG_SUB) and B digits (8 planes x
-// np x TG_SUB), bf16.
+// np x TG_SUB), bf16.  Column blocks: the grid's y index selects columns [y cbw, y cbw + cbw)
+// of [Y0 Y1], and its x CTAs share that block's windows; block y's partials lie at
+// partial + y gridDim.x wx cbw, CTA x's at x wx wyb after that (wyb = the block's width).
 __host__ __device__ constexpr size_t tg_smem_bytes(int mt, int np) {
   return (size_t)TC_DIGITS * mt * 128 * TG_SUB * 2 + (size_t)TC_DIAG * np * TG_SUB * 2;
 }
@@ -670,7 +682,8 @@ __host__ __device__ constexpr size_t tg_smem_bytes(int mt, int np) {
 __global__ void __launch_bounds__(TG_THREADS, 1) tc_gram_kernel(TcGramArgs ta) {
   if (ta.skip && *ta.skip == 0) return;
   extern __shared__ __align__(1024) unsigned char tg_smem[];
-  const int np = ta.np, mt = ta.mt, wx = ta.wx, wy = ta.wy0 + ta.wy1, n = ta.n;
+  const int c0 = blockIdx.y * ta.cbw;
+  const int np = ta.np, mt = ta.mt, wx = ta.wx, wy = min(ta.cbw, ta.wy0 + ta.wy1 - c0), n = ta.n;
   constexpr int KC = TG_SUB / 8;
   uint16_t* sA = reinterpret_cast<uint16_t*>(tg_smem);           // [7][mt][128 x TG_SUB]
   uint16_t* sB = sA + (size_t)TC_DIGITS * mt * 128 * TG_SUB;     // [8 np x TG_SUB]
@@ -681,8 +694,9 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tc_gram_kernel(TcGramArgs ta) {
   __shared__ int ldY[TG_BMAX];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid < wy) {
-    colY[tid] = tid < ta.wy0 ? ta.Y0 + tid : ta.Y1 + (tid - ta.wy0);
-    ldY[tid] = tid < ta.wy0 ? ta.ldy0 : ta.ldy1;
+    const int cc = c0 + tid;
+    colY[tid] = cc < ta.wy0 ? ta.Y0 + cc : ta.Y1 + (cc - ta.wy0);
+    ldY[tid] = cc < ta.wy0 ? ta.ldy0 : ta.ldy1;
   }
   // zero digits once: padding rows of A and B and B's zero plane are never rewritten
   {
@@ -873,7 +887,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tc_gram_kernel(TcGramArgs ta) {
     if (ev && q < CP && j < wx && l < wy) {
       double2 v = make_double2(acc[q] + o1, acc[q + 1] - o0);
       if (bad_row || pbad || ((bad_cols >> q) & 3u)) v = make_double2(qnan, qnan);
-      ta.partial[(size_t)blockIdx.x * wx * wy + (size_t)j * wy + l] = v;
+      ta.partial[((size_t)blockIdx.y * gridDim.x * ta.cbw + (size_t)blockIdx.x * wy) * wx + (size_t)j * wy + l] = v;
     }
   }
   __syncthreads();
