@@ -739,23 +739,57 @@ gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy
   if (tcok && gram_tc_fits(ctx, wx, wy))
     return gram_tc(ctx, X, wx, Y0, wy0, Y1, wy1, C, skip, nout_tc, count, ldc);
   if (tcok && ctx->tc && ctx->n >= 2048) {
-    // outside the forms' shapes (wx <= 128): column blocks of [Y0 Y1] of the widest of 32,
-    // 16, 8 columns that a form takes with all of X, each block a tensor-core product into
-    // its columns of C (the whole product's algorithmic work is booked here, the blocks'
-    // launches and times with each block)
-    int cb = 0;
-    for (int cand : {32, 16, 8}) {
-      const int w = std::min(cand, wy);
-      if (gram_tn_fits(ctx, wx, w, false) || gram_tw_fits(ctx, wx, w, false) || gram_tc_fits(ctx, wx, w)) {
-        cb = w;
-        break;
+    // outside the forms' shapes (wx <= 128): blocks, each a tensor-core product into its part
+    // of C (the whole product's algorithmic work is booked here, the blocks' launches and
+    // times with each block).  Three plans, by a cost per column read that was measured
+    // on one GB300 at n = 65536 (narrow and wide forms ~1.9 us, the serial form with its
+    // column blocks in one launch ~2.5 us):
+    //   A: column blocks of [Y0 Y1] of the widest of 32, 24, 16, 8 columns that the narrow
+    //      or wide form takes with all of X;
+    //   B: column blocks of 32, 16 or 8 columns by the serial form, in one launch;
+    //   C: X in two halves (wx > 64), each planned alike.
+    auto plan_a = [&](int ax, int& cbw) {
+      for (int cand : {32, 24, 16, 8}) {
+        const int w = std::min(cand, wy);
+        if (gram_tn_fits(ctx, ax, w, false) || gram_tw_fits(ctx, ax, w, false)) {
+          cbw = w;
+          const int nb = (wy + w - 1) / w;
+          return 1.9 * (nb * ax + wy);
+        }
       }
+      cbw = 0;
+      return 1e30;
+    };
+    auto plan_b = [&](int ax, int& cbw) {
+      for (int cand : {32, 16, 8}) {
+        const int w = std::min(cand, wy);
+        if (gram_tc_fits(ctx, ax, w) && (size_t)ctx->num_sms * ax * w <= ctx->gram_part_elems) {
+          cbw = w;
+          const int nb = (wy + w - 1) / w;
+          return 2.5 * (nb * ax + wy);
+        }
+      }
+      cbw = 0;
+      return 1e30;
+    };
+    int cba = 0, cbb = 0, tmp = 0;
+    const double ca = plan_a(wx, cba), cb_cost = plan_b(wx, cbb);
+    double cc = 1e30;
+    const int xa = (wx + 1) / 2;
+    if (wx > gplhr::TW_XMAX)
+      cc = std::min(plan_a(xa, tmp), plan_b(xa, tmp)) + std::min(plan_a(wx - xa, tmp), plan_b(wx - xa, tmp));
+    if (cc < ca && cc < cb_cost) {
+      if (count) {
+        ctx->k_flops[KC_GRAM_TC] += 8.0 * ctx->n * nout_tc;
+        ctx->k_bytes[KC_GRAM_TC] += 16.0 * ctx->n * (self ? wx : wx + wy);
+      }
+      TRY(gram(ctx, X, xa, Y0, wy0, Y1, wy1, C, skip, false, false, fp32, -1, ldc));
+      return gram(ctx, Blk{X.p + xa, X.ld}, wx - xa, Y0, wy0, Y1, wy1, C + (size_t)xa * ldc, skip, false, false,
+                  fp32, -1, ldc);
     }
-    if (cb > 0 && cb < wy && !gram_tn_fits(ctx, wx, cb, false) && !gram_tw_fits(ctx, wx, cb, false) &&
-        (size_t)ctx->num_sms * wx * cb <= ctx->gram_part_elems) {
-      // the blocks' form is tc_gram_kernel: all blocks in one launch
-      return gram_tc(ctx, X, wx, Y0, wy0, Y1, wy1, C, skip, nout_tc, count, ldc, cb);
-    }
+    if (cbb > 0 && cbb < wy && cb_cost <= ca)
+      return gram_tc(ctx, X, wx, Y0, wy0, Y1, wy1, C, skip, nout_tc, count, ldc, cbb);
+    const int cb = cba;
     if (cb > 0 && cb < wy) {
       if (count) {
         ctx->k_flops[KC_GRAM_TC] += 8.0 * ctx->n * nout_tc;
