@@ -305,6 +305,7 @@ def main():
             if not args.no_mixed:
                 line["solve_gmres_mixed"] = time_to_pairs(G, stream, "mixed", args.inner_steps)
         line.update(other_workloads(G, stream))
+        line["qz"] = qz_device_vs_host(G)
     if rank == 0 and not args.no_cpu:
         sample = 3
         spi = oracle_iterations(pr, sample, 0)
@@ -498,6 +499,38 @@ def solve_timed(G, stream, pr, precision, maxit, **kw):
             "inner_gmres_steps": kw.get("inner_steps", 0), "sparse_products": info.n_spmm,
             "preconditioner_applications": info.n_prec, "converged": conv,
             "max_resid": float(max(vec["resid"])), "tol": pr.tol}
+
+
+def qz_device_vs_host(G, sizes=(16, 32, 56, 80), reps=5):
+    """The ordered QZ of an s x s projected pencil (Phi upper triangular, as in the factored
+    form) on the host (the library's routine, all Schur-vector columns) and on the device
+    (one CTA, CUDA events on its stream), milliseconds per call."""
+    import numpy as np
+    import torch
+    out = {"pencil": "random complex, Phi upper triangular, sigma = 0.1 + 0.1i, all positions ordered"}
+    rng = np.random.default_rng(11)
+    st = torch.cuda.Stream()
+    for s in sizes:
+        Phi = np.triu(rng.standard_normal((s, s)) + 1j * rng.standard_normal((s, s)))
+        Psi = rng.standard_normal((s, s)) + 1j * rng.standard_normal((s, s))
+        sigma = 0.1 + 0.1j
+        G.gplhr_ordqz(Phi, Psi, sigma)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            G.gplhr_ordqz(Phi, Psi, sigma)
+        host = (time.perf_counter() - t0) / reps * 1e3
+        P, S = torch.from_numpy(Phi).to("cuda"), torch.from_numpy(Psi).to("cuda")
+        with torch.cuda.stream(st):
+            G.gplhr_ordqz_device(P, S, sigma, stream=st.cuda_stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                res = G.gplhr_ordqz_device(P, S, sigma, stream=st.cuda_stream)
+            e1.record(st)
+        st.synchronize()
+        out[str(s)] = {"host_ms": host, "device_ms": e0.elapsed_time(e1) / reps,
+                       "device_status": int(res[4].item())}
+    return out
 
 
 def other_workloads(G, stream, quick=False):

@@ -421,6 +421,19 @@ gplhr_status gplhr_gram_noalloc(int64_t n, const void* X, int32_t ldx, int32_t w
 gplhr_status gplhr_ordqz(int32_t s, const double* Phi, const double* Psi, double sigma_re,
                          double sigma_im, double* RA, double* RB, double* YL, double* YR);
 
+/* The same ordered QZ on the device, in one CTA (s <= 80): the host routine's steps in its
+ * order (Givens Hessenberg-triangular reduction, single-shift sweeps, adjacent swaps of the
+ * leading nsort positions (< 0: all), unit phases), each plane rotation formed by one
+ * thread and applied by all.  Phi, Psi (read) and RA, RB, YL, YR (written) are device
+ * pointers to s x s row-major complex128 matrices; *status (a device int) is set to 0,
+ * or to 1 when the sweeps did not converge.  Asynchronous on `stream` (NULL = the
+ * default stream).  It exists so that the QZ can be timed on the device against the
+ * host: an iteration of GPLHR uses the host QZ, which measured faster at every s of the
+ * workloads.  Errors: EINVAL (s outside 1..80, NULL pointers), ECUDA (launch). */
+gplhr_status gplhr_ordqz_device(int32_t s, const void* Phi, const void* Psi, double sigma_re,
+                                double sigma_im, int32_t nsort, void* RA, void* RB, void* YL,
+                                void* YR, int32_t* status, void* stream);
+
 /* Q-free factors of Theorem 1 with Eqs. G1_fix, G2_fix: M_A = G2 G^{-1} R_A,
  * M_B = I - G1 G^{-1} R_A, G = R_A G1 + R_B G2 (k x k row-major complex, host). */
 gplhr_status gplhr_mfactors(int32_t k, const double* RA, const double* RB, double* MA,

@@ -25,6 +25,7 @@
 #include "../../include/gplhr.h"
 #include "kernels.cuh"
 #include "qz.h"
+#include "qz_device.cuh"
 #include "tc.cuh"
 
 using gplhr::cd;
@@ -3347,6 +3348,27 @@ gplhr_status gplhr_ordqz(int32_t s, const double* Phi, const double* Psi, double
     RB[2 * i] = rb.a[i].real(); RB[2 * i + 1] = rb.a[i].imag();
     YL[2 * i] = yl.a[i].real(); YL[2 * i + 1] = yl.a[i].imag();
     YR[2 * i] = yr.a[i].real(); YR[2 * i + 1] = yr.a[i].imag();
+  }
+  return GPLHR_OK;
+}
+
+gplhr_status gplhr_ordqz_device(int32_t s, const void* Phi, const void* Psi, double sigma_re, double sigma_im,
+                                int32_t nsort, void* RA, void* RB, void* YL, void* YR, int32_t* status, void* stream) {
+  if (s < 1 || s > gplhr::DQZ_SMAX || !Phi || !Psi || !RA || !RB || !YL || !YR || !status) {
+    g_create_error = "gplhr_ordqz_device: need 1 <= s <= 80 and device pointers";
+    return GPLHR_EINVAL;
+  }
+  cudaError_t e = cudaFuncSetAttribute(gplhr::ordqz_device_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)gplhr::dqz_smem_bytes(gplhr::DQZ_SMAX));
+  if (e == cudaSuccess) {
+    gplhr::ordqz_device_kernel<<<1, gplhr::DQZ_THREADS, gplhr::dqz_smem_bytes(s), (cudaStream_t)stream>>>(
+        s, (const double2*)Phi, (const double2*)Psi, make_double2(sigma_re, sigma_im), nsort, (double2*)RA,
+        (double2*)RB, (double2*)YL, (double2*)YR, status);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    g_create_error = std::string("gplhr_ordqz_device: ") + cudaGetErrorString(e);
+    return GPLHR_ECUDA;
   }
   return GPLHR_OK;
 }

@@ -27,7 +27,8 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5:
 
 EXPORTED = ["gplhr_create", "gplhr_solve", "gplhr_start", "gplhr_iterate", "gplhr_vectors",
             "gplhr_destroy", "gplhr_last_error", "gplhr_spmm", "gplhr_precond_apply",
-            "gplhr_gram", "gplhr_combine", "gplhr_orth", "gplhr_ordqz", "gplhr_mfactors", "gplhr_profile",
+            "gplhr_gram", "gplhr_combine", "gplhr_orth", "gplhr_ordqz", "gplhr_ordqz_device", "gplhr_mfactors",
+            "gplhr_profile",
             "gplhr_profile_read", "gplhr_gram_noalloc", "gplhr_grad", "gplhr_solve_batched",
             "gplhr_iterate_batched", "gplhr_spmm_shape", "gplhr_set_deflation", "gplhr_create_batched"]
 P_MODES = {"thick": 0, "lobpcg": 1, "none": 2}
@@ -101,6 +102,7 @@ def lib():
     L.gplhr_spmm_shape.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(i32), dp, dp]
     L.gplhr_set_deflation.argtypes = [vp, vp, vp, i32, i32]
     L.gplhr_ordqz.argtypes = [i32, dp, dp, dbl, dbl, dp, dp, dp, dp]
+    L.gplhr_ordqz_device.argtypes = [i32, vp, vp, dbl, dbl, i32, vp, vp, vp, vp, vp, vp]
     L.gplhr_mfactors.argtypes = [i32, dp, dp, dp, dp]
     L.gplhr_profile.argtypes = [vp, i32]
     L.gplhr_gram_noalloc.argtypes = [i64, vp, i32, i32, vp, i32, i32, vp, vp]
@@ -454,6 +456,24 @@ def gplhr_ordqz(Phi: np.ndarray, Psi: np.ndarray, sigma: complex):
                            sigma.real, sigma.imag, *[_dptr(o.view(np.float64)) for o in out])
     _check(st, None)
     return tuple(out)  # RA, RB, YL, YR
+
+
+def gplhr_ordqz_device(Phi, Psi, sigma: complex, nsort: int = -1, stream: int = 0):
+    """The ordered QZ on the device (one CTA): Phi, Psi device complex128 s x s tensors;
+    returns device tensors RA, RB, YL, YR and a device int32 status (0: converged),
+    asynchronously on `stream`."""
+    import torch
+    s = Phi.shape[0]
+    for M in (Phi, Psi):
+        if (M.dtype != torch.complex128 or not M.is_cuda or tuple(M.shape) != (s, s) or not M.is_contiguous()
+                or M.device != Phi.device):
+            raise GplhrError(GPLHR_EINVAL, "Phi, Psi: contiguous s x s complex128 tensors on one device")
+    out = [torch.empty((s, s), dtype=torch.complex128, device=Phi.device) for _ in range(4)]
+    status = torch.zeros(1, dtype=torch.int32, device=Phi.device)
+    with torch.cuda.device(Phi.device):
+        _check(lib().gplhr_ordqz_device(s, Phi.data_ptr(), Psi.data_ptr(), sigma.real, sigma.imag, nsort,
+                                        *[o.data_ptr() for o in out], status.data_ptr(), stream or None), None)
+    return (*out, status)
 
 
 def gplhr_mfactors(RA: np.ndarray, RB: np.ndarray):

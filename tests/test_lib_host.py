@@ -120,3 +120,11 @@ def test_create_batched_refuses_null_arrays_without_a_gpu(built):
     st = built.gplhr_create_batched(1, None, None, None, None, None, None, None, out, None, 0)
     assert st == G.GPLHR_EINVAL
     assert "non-null" in G.gplhr_last_error(None)
+
+
+def test_device_qz_refuses_bad_sizes_without_a_gpu(built):
+    """gplhr_ordqz_device checks s and its pointers before any device call."""
+    for s in (0, 81):
+        st = built.gplhr_ordqz_device(s, None, None, 0.0, 0.0, -1, None, None, None, None, None, None)
+        assert st == G.GPLHR_EINVAL
+    assert "s <= 80" in G.gplhr_last_error(None)
