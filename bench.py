@@ -450,9 +450,43 @@ def batched_throughput(G, K):
             s.close()
         return t_batched, t_seq, int(st)
 
+    def run_persistent(precision, pool):
+        """K iterations of the whole batch by the persistent kernel (pool = False), or by
+        the thread pool with graphs (pool = True), in the given precision."""
+        solvers = [G.GPLHR(p.A, p.B, p.sigma, p.k, p.m, p.precond, p.block_size, tol=p.tol, maxit=10 ** 6,
+                           precision=precision, graphs=pool, autotune=pool) for p in ps]
+        for s, p in zip(solvers, ps):
+            s.start(p.start_block())
+        ctxs = [s.ctx for s in solvers]
+        it = (lambda n: G.gplhr_iterate_batched(ctxs, n)) if pool else (
+            lambda n: G.gplhr_iterate_persistent(ctxs, n))
+        it(2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = it(K)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        out = {"pencil_iterations_per_s": len(ps) * K / t, "status": int(r[0])}
+        if not pool:
+            st4 = r[3]
+            out.update({"launches_per_batch_iteration": st4.launches / K,
+                        "recorded_launches_per_batch_iteration": st4.ops / K,
+                        "grid_barriers_per_batch_iteration": (st4.steps - st4.launches) / K,
+                        "grid": int(st4.grid),
+                        "host_ms_per_batch_iteration": {"record": st4.record_ms / K, "build_and_issue": st4.build_ms / K,
+                                                        "qz": st4.qz_ms / K, "device_wait": st4.wait_ms / K},
+                        "ms_per_batch_iteration": 1e3 * t / K})
+        for s in solvers:
+            s.close()
+        return out
+
     units = len(ps) * K
     tb, ts, st = run(False)
     gb, gs, gst = run(True)
+    persistent = {"fp64": run_persistent("fp64", False), "mixed": run_persistent("mixed", False),
+                  "mixed_thread_pool_graphs": run_persistent("mixed", True),
+                  "kernels": "DFMA / FFMA kernels (no tensor-core pipelines) run as virtual CTAs of one "
+                             "cooperative persistent kernel per device segment"}
     return {"workload": f"{len(ps)} contexts: 64 convection-diffusion pencils (grid sides 16..96, B = MxM, k = 4) "
                         "+ 16 shifts over a 128^2 pencil (k = 8), Jacobi, FP64",
             "pencil_iterations_per_s": units / gb, "sequential_pencil_iterations_per_s": units / gs,
@@ -461,6 +495,7 @@ def batched_throughput(G, K):
                                "sequential_pencil_iterations_per_s": units / ts, "status": st},
             "graphs": "each iteration's three device segments replayed from CUDA graphs; SpMM launch shapes "
                       "autotuned per pencil",
+            "persistent": persistent,
             "threads": os.cpu_count(), "iterations": K, "status": gst}
 
 

@@ -292,6 +292,50 @@ gplhr_status gplhr_solve_batched(int32_t nctx, gplhr_ctx* const* ctxs, const voi
 gplhr_status gplhr_iterate_batched(int32_t nctx, gplhr_ctx* const* ctxs, int32_t niter,
                                    gplhr_info* infos, gplhr_status* statuses, int32_t nthreads);
 
+/* Persistent batched iteration: the same batches (many pencils of uneven size, many
+ * shifts over one pencil), with every device segment of an iteration of Algorithm 2
+ * (steps 7-24, steps 25-28, the residual with its column norms) run for ALL contexts in
+ * one launch of a persistent kernel.  The host records each context's launches (the
+ * kernels, grids and arguments gplhr_iterate would issue, on the FP64 / FP32 DFMA and
+ * FFMA kernels, not the tensor-core ones), merges them into one program and launches it
+ * cooperatively (every CTA resident); the kernel runs step j of every context's program
+ * side by side and crosses a grid barrier before step j + 1.  Per iteration of the whole
+ * batch: three launches and two host round trips (the projected pencils for the host
+ * QZ, which runs on nthreads host threads, and the residual norms for soft locking).
+ * Each barrier wait is bounded (the contexts' opts.wait_limit, in tests of 20 us); when
+ * it runs out the call returns GPLHR_ETIMEOUT (opts.wait_probe makes it run out: a test
+ * hook).  Contexts iterate in lockstep and leave the batch when they converge, fail or
+ * reach their budget.  Results match gplhr_iterate's to rounding (the Gram products'
+ * partial sums are split by the context's share of the SMs, not by all of them).
+ * Not supported (EINVAL): GPLHR-EIG contexts, inner GMRES preconditioning (its least
+ * squares runs on the host inside T), profiling.  A context must not appear twice; all
+ * contexts belong to the current device.
+ * gplhr_iterate_persistent runs up to niter iterations of each started context;
+ * gplhr_solve_persistent starts every context (steps 1-4, on host threads, as
+ * gplhr_solve_batched does) and iterates until each converges or reaches its maxit
+ * (ENOTCONV then, results readable).  Arguments as gplhr_solve_batched; stats (may be
+ * NULL) receives the launch counts.  Returns GPLHR_OK if every context succeeded, else
+ * the first failing status in context order; a message is in gplhr_last_error(NULL). */
+typedef struct gplhr_persist_stats {
+  int64_t launches;  /* persistent-kernel launches */
+  int64_t steps;     /* program steps (grid barriers + 1 per launch) over all launches */
+  int64_t ops;       /* recorded kernel launches they replaced */
+  int32_t grid;      /* CTAs of the last launch */
+  int32_t pad;
+  double record_ms;  /* host: recording the contexts' segments (on the host threads) */
+  double build_ms;   /* host: merging the programs, issuing copies and launches */
+  double qz_ms;      /* host: the sorted QZ of every pencil (on the host threads) */
+  double wait_ms;    /* host: waiting for the device at the two round trips */
+} gplhr_persist_stats;
+gplhr_status gplhr_iterate_persistent(int32_t nctx, gplhr_ctx* const* ctxs, int32_t niter,
+                                      gplhr_info* infos, gplhr_status* statuses, int32_t nthreads,
+                                      gplhr_persist_stats* stats);
+gplhr_status gplhr_solve_persistent(int32_t nctx, gplhr_ctx* const* ctxs, const void* const* V0,
+                                    const int32_t* V0_where, const int32_t* is_complex,
+                                    const uint64_t* seeds, gplhr_info* infos,
+                                    gplhr_status* statuses, int32_t nthreads,
+                                    gplhr_persist_stats* stats);
+
 /* gplhr_destroy -- free everything the context owns.  NULL is a no-op. */
 void gplhr_destroy(gplhr_ctx* ctx);
 

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <climits>
 #include <cmath>
 #include <complex>
@@ -17,6 +18,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <condition_variable>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -24,6 +26,7 @@
 
 #include "../../include/gplhr.h"
 #include "kernels.cuh"
+#include "persist.cuh"
 #include "qz.h"
 #include "qz_device.cuh"
 #include "tc.cuh"
@@ -53,6 +56,33 @@ struct Blk {  // row-major block view
 
 
 }  // namespace
+
+// Launches and copies of one device segment of an iteration, recorded instead of issued:
+// the persistent batched iteration (gplhr_iterate_persistent) runs the segments of all
+// its contexts in one kernel (persist.cuh).  Each op keeps the kernel kind, the grid the
+// launch would have had (256 threads per CTA), its dynamic shared memory and its
+// arguments (a byte range of args).  Host-to-device copies read staging the host filled
+// before the segment, so they run before the kernel; device-to-host copies after it.
+struct PkRecorder {
+  struct Op {
+    int kind, gx, gy;
+    size_t smem, off, size;
+  };
+  struct Copy {
+    void* dst;
+    const void* src;
+    size_t bytes;
+  };
+  std::vector<Op> ops;
+  std::vector<unsigned char> args;
+  std::vector<Copy> pre, post;
+  void clear() {
+    ops.clear();
+    args.clear();
+    pre.clear();
+    post.clear();
+  }
+};
 
 struct gplhr_ctx {
   // problem
@@ -168,6 +198,16 @@ struct gplhr_ctx {
   bool autotune = false;
   std::map<int, SpmmShape> spmm_shape;  // key 4 G + V
   const SpmmShape* spmm_force = nullptr;  // candidate being measured
+  PkRecorder* rec = nullptr;  // non-null: device work is recorded, not issued
+  // persistent batched iteration: recorded segments by segment key (a segment's launches
+  // are fixed by its key, as for the CUDA graphs below), with the accounting each use adds;
+  // rec_last is the recording of the segment just issued
+  struct PkCached {
+    PkRecorder rec;
+    Counters delta;
+  };
+  std::map<uint64_t, PkCached>* pk_cache = nullptr;
+  const PkRecorder* rec_last = nullptr;
   std::string err;
 };
 
@@ -199,6 +239,57 @@ int grid_for(size_t work, int per_cta, int cap) {
   if (g < 1) g = 1;
   if (g > (size_t)cap) g = cap;
   return (int)g;
+}
+
+// ------------------------------------------------ recording (persistent mode) ----
+// Record one launch (kind, gx x gy CTAs of 256 threads, smem bytes, arguments a).
+template <class A>
+void pk_rec(gplhr_ctx* ctx, int kind, int gx, int gy, size_t smem, const A& a) {
+  PkRecorder* r = ctx->rec;
+  const size_t off = (r->args.size() + 15) & ~(size_t)15;
+  r->args.resize(off + sizeof(A));
+  std::memcpy(r->args.data() + off, &a, sizeof(A));
+  r->ops.push_back(PkRecorder::Op{kind, gx, gy, smem, off, sizeof(A)});
+}
+
+// An asynchronous copy on the context's stream, or, while recording: host-to-device
+// before the segment's kernel, device-to-host after it, device-to-device as a step.
+gplhr_status copy_async(gplhr_ctx* ctx, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+  if (ctx->rec) {
+    if (kind == cudaMemcpyHostToDevice) {
+      ctx->rec->pre.push_back(PkRecorder::Copy{dst, src, bytes});
+    } else if (kind == cudaMemcpyDeviceToHost) {
+      ctx->rec->post.push_back(PkRecorder::Copy{dst, src, bytes});
+    } else {
+      if (bytes % sizeof(double2) != 0) {
+        ctx->err = "recorded device copy: size not a multiple of 16 bytes";
+        return GPLHR_EINVAL;
+      }
+      const gplhr::PkBytes a{(const double2*)src, (double2*)dst, (int64_t)(bytes / sizeof(double2))};
+      pk_rec(ctx, gplhr::PK_BYTES, grid_for(bytes / sizeof(double2), 256, 2 * ctx->num_sms), 1, 0, a);
+    }
+    return GPLHR_OK;
+  }
+  CK(cudaMemcpyAsync(dst, src, bytes, kind, ctx->stream));
+  return GPLHR_OK;
+}
+
+// Block copy Y = X (n x w) and Y = alpha X1 + beta X2, launched or recorded.
+void launch_copy_block(gplhr_ctx* ctx, int grid, int n, int w, const double2* X, int ldx, double2* Y, int ldy) {
+  if (ctx->rec) {
+    pk_rec(ctx, gplhr::PK_COPY_BLOCK, grid, 1, 0, gplhr::PkCopy{n, w, ldx, ldy, X, Y});
+    return;
+  }
+  gplhr::copy_block_kernel<<<grid, 256, 0, ctx->stream>>>(n, w, X, ldx, Y, ldy);
+}
+
+void launch_axpby(gplhr_ctx* ctx, int grid, int n, int w, double2 alpha, const double2* X1, int ld1, double2 beta,
+                  const double2* X2, int ld2, double2* Y, int ldy) {
+  if (ctx->rec) {
+    pk_rec(ctx, gplhr::PK_AXPBY, grid, 1, 0, gplhr::PkAxpby{n, w, ld1, ld2, ldy, alpha, beta, X1, X2, Y});
+    return;
+  }
+  gplhr::axpby_kernel<<<grid, 256, 0, ctx->stream>>>(n, w, alpha, X1, ld1, beta, X2, ld2, Y, ldy);
 }
 
 // ----------------------------------------------------------- accounting ----
@@ -261,8 +352,57 @@ void restore_counters(gplhr_ctx* ctx, const gplhr_ctx::Counters& c) {
 // every kernel argument of the segment must then be fixed by the key, and the small
 // coefficient matrices reach the device through pinned staging buffers that the host
 // fills before the segment runs (the graph's copies read them when it executes).
+void add_counters(gplhr_ctx* ctx, const gplhr_ctx::Counters& d) {
+  for (int i = 0; i < 8; ++i) {
+    ctx->k_flops[i] += d.k_flops[i];
+    ctx->k_bytes[i] += d.k_bytes[i];
+    ctx->k_launch[i] += d.k_launch[i];
+  }
+  ctx->n_launch += d.n_launch;
+  ctx->n_spmm += d.n_spmm;
+  ctx->n_prec += d.n_prec;
+  ctx->h2d_bytes += d.h2d;
+  ctx->d2h_bytes += d.d2h;
+}
+
+gplhr_ctx::Counters diff_counters(const gplhr_ctx::Counters& c1, const gplhr_ctx::Counters& c0) {
+  gplhr_ctx::Counters d;
+  for (int i = 0; i < 8; ++i) {
+    d.k_flops[i] = c1.k_flops[i] - c0.k_flops[i];
+    d.k_bytes[i] = c1.k_bytes[i] - c0.k_bytes[i];
+    d.k_launch[i] = c1.k_launch[i] - c0.k_launch[i];
+  }
+  d.n_launch = c1.n_launch - c0.n_launch;
+  d.n_spmm = c1.n_spmm - c0.n_spmm;
+  d.n_prec = c1.n_prec - c0.n_prec;
+  d.h2d = c1.h2d - c0.h2d;
+  d.d2h = c1.d2h - c0.d2h;
+  return d;
+}
+
 gplhr_status run_segment(gplhr_ctx* ctx, uint64_t key, const std::function<gplhr_status()>& issue) {
-  if (!ctx->graphs || ctx->prof_on || ctx->gm_steps > 0) return issue();
+  if (ctx->pk_cache) {  // persistent batch: record once per key, reuse the recording after
+    auto it = ctx->pk_cache->find(key);
+    if (it != ctx->pk_cache->end()) {
+      add_counters(ctx, it->second.delta);
+      ctx->rec_last = &it->second.rec;
+      return GPLHR_OK;
+    }
+    const gplhr_ctx::Counters c0 = snap_counters(ctx);
+    gplhr_ctx::PkCached& c = (*ctx->pk_cache)[key];
+    c.rec.clear();
+    ctx->rec = &c.rec;
+    const gplhr_status st = issue();
+    ctx->rec = nullptr;
+    if (st != GPLHR_OK) {
+      ctx->pk_cache->erase(key);
+      return st;
+    }
+    c.delta = diff_counters(snap_counters(ctx), c0);
+    ctx->rec_last = &c.rec;
+    return GPLHR_OK;
+  }
+  if (ctx->rec || !ctx->graphs || ctx->prof_on || ctx->gm_steps > 0) return issue();
   auto it = ctx->seg_graphs.find(key);
   if (it != ctx->seg_graphs.end()) {
     CK(cudaGraphLaunch(it->second.exec, ctx->stream));
@@ -343,9 +483,18 @@ void launch_spmm_g(gplhr_ctx* ctx, gplhr::CsrDev<VTA> a, gplhr::CsrDev<VTB> b, i
     const auto it = ctx->spmm_shape.find(4 * G + V);
     if (it != ctx->spmm_shape.end()) sh = it->second;
   }
+  if (ctx->rec) sh = gplhr_ctx::SpmmShape{};  // the persistent kernel runs 256 threads per CTA
   const int rows_per_cta = (sh.threads / 32) * (32 / G);
   const int grid = grid_for((size_t)ctx->n, rows_per_cta, sh.gridmul * ctx->num_sms);
   const int nt = sh.threads;
+  if (ctx->rec) {
+    constexpr bool cpa = sizeof(VTA) == 2 * sizeof(T), cpb = sizeof(VTB) == 2 * sizeof(T);
+    const int gi = G == 4 ? 0 : G == 8 ? 1 : G == 16 ? 2 : 3;
+    const gplhr::PkSpmm o{ctx->n, hasB, ldx,    w,      ldy,   ldy2, a.rowptr, a.col, a.val,
+                          b.rowptr, b.col, b.val, X, Y, Y2};
+    pk_rec(ctx, gplhr::pk_spmm_code(V == 2 ? 1 : 0, cpa ? 1 : 0, cpb ? 1 : 0, gi), grid, 1, 0, o);
+    return;
+  }
   switch (G) {
     case 4:
       gplhr::spmm_kernel<VTA, VTB, T, 4, V><<<grid, nt, 0, ctx->stream>>>(ctx->n, a, b, hasB, X, ldx, w, Y, ldy, Y2, ldy2);
@@ -410,8 +559,11 @@ gplhr_status launch_spmm_f32(gplhr_ctx* ctx, const DevCsr& M, const DevCsr* M2, 
   spmm_cost(ctx, M, w, 4.0, fl, by);
   if (M2) spmm_cost(ctx, *M2, w, 4.0, fl, by);
   const int ph = prof_begin(ctx, KC_SPMM, fl, by, 2);
-  gplhr::to_c64_kernel<<<grid_for((size_t)ctx->n * w, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-      ctx->n, w, X.p, X.ld, ctx->X32, ld32);
+  const int gconv = grid_for((size_t)ctx->n * w, 256, 8 * ctx->num_sms);
+  if (ctx->rec)
+    pk_rec(ctx, gplhr::PK_TO_C64, gconv, 1, 0, gplhr::PkToC64{ctx->n, w, X.ld, ld32, X.p, ctx->X32});
+  else
+    gplhr::to_c64_kernel<<<gconv, 256, 0, ctx->stream>>>(ctx->n, w, X.p, X.ld, ctx->X32, ld32);
   for (int c0 = 0; c0 < w; c0 += 64) {
     const int wc = std::min(64, w - c0);
     launch_spmm_types<float, 2, float, float2>(ctx, M, M2, M.val32, M2 ? M2->val32 : nullptr, ctx->X32 + c0, ld32,
@@ -524,6 +676,13 @@ gplhr_status spmm_AB(gplhr_ctx* ctx, Blk X, int w, Blk AX, Blk BX) {
 template <int ACC>
 void launch_gram_acc(gplhr_ctx* ctx, dim3 grid, size_t smem, int rows, Blk X, int wx, Blk Y0, int wy0,
                      Blk Y1, int wy1, int herm, int nout, int G, int RG, const int* skip, int mode) {
+  if (ctx->rec) {
+    const int lacc = ACC == 1 ? 0 : ACC == 2 ? 1 : ACC == 4 ? 2 : 3;
+    const gplhr::PkGram o{ctx->n, rows, X.ld, wx,  Y0.ld, wy0, Y1.ld, wy1, herm, nout,
+                          G,      RG,   X.p,  Y0.p, Y1.p, ctx->gram_part, skip};
+    pk_rec(ctx, gplhr::PK_GRAM_BASE + 4 * mode + lacc, (int)grid.x, (int)grid.y, smem, o);
+    return;
+  }
   if (mode == 2)
     gplhr::gram_partial_x32_kernel<ACC><<<grid, gplhr::GRAM_THREADS, smem, ctx->stream>>>(
         ctx->n, rows, X.p, X.ld, wx, Y0.p, Y0.ld, wy0, Y1.p, Y1.ld, wy1, herm, nout, G, RG, ctx->gram_part, skip);
@@ -844,8 +1003,13 @@ gplhr_status gram(gplhr_ctx* ctx, Blk X, int wx, Blk Y0, int wy0, Blk Y1, int wy
     default: launch_gram_acc<1>(ctx, grid, smem, rows, X, wx, Y0, wy0, Y1, wy1, herm, nout, G, RG, skip, mode); break;
   }
   CK(cudaGetLastError());
-  gplhr::gram_reduce_kernel<<<(nout + gplhr::GRED_WARPS - 1) / gplhr::GRED_WARPS, 32 * gplhr::GRED_WARPS, 0,
-                               ctx->stream>>>(nchunk, nout, wx, wy, herm ? 1 : 0, ctx->gram_part, C, ldc, skip);
+  const int gred = (nout + gplhr::GRED_WARPS - 1) / gplhr::GRED_WARPS;
+  if (ctx->rec)
+    pk_rec(ctx, gplhr::PK_GRAM_REDUCE, gred, 1, 0,
+           gplhr::PkGramRed{nchunk, nout, wx, wy, herm ? 1 : 0, ldc, ctx->gram_part, C, skip});
+  else
+    gplhr::gram_reduce_kernel<<<gred, 32 * gplhr::GRED_WARPS, 0, ctx->stream>>>(nchunk, nout, wx, wy, herm ? 1 : 0,
+                                                                                ctx->gram_part, C, ldc, skip);
   prof_end(ctx, ph);
   CK(cudaGetLastError());
   return GPLHR_OK;
@@ -1113,6 +1277,15 @@ gplhr_status combine(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, b
   const double macs = a.upper ? 0.5 * c * (c + 1.0) : (double)wsum * c;
   const int ph = prof_begin(ctx, KC_COMBINE, count ? 8.0 * ctx->n * macs : 0.0, count ? by : 0.0,
                            c_store < c ? 2 : 1);
+  if (ctx->rec) {
+    pk_rec(ctx, use32 ? gplhr::PK_COMBINE_F : gplhr::PK_COMBINE_D, grid, 1, smem, gplhr::PkComb{ctx->n, rows_per_cta, a});
+    if (c_store < c) {
+      const int nc = c - c_store;
+      pk_rec(ctx, gplhr::PK_NORM_REDUCE, (nc + 7) / 8, 1, 0, gplhr::PkNormRed{grid, nc, ctx->norm_part, ctx->d_norms});
+    }
+    prof_end(ctx, ph);
+    return GPLHR_OK;
+  }
   if (use32)
     gplhr::combine_kernel<float><<<grid, gplhr::COMB_THREADS, smem, ctx->stream>>>(ctx->n, rows_per_cta, a);
   else
@@ -1166,15 +1339,17 @@ gplhr_status precond_apply_impl(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
   switch (ctx->prec) {
     case GPLHR_PREC_NONE: {
       if (X.p != Y.p) {
-        gplhr::copy_block_kernel<<<grid_for((size_t)n * w, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-            n, w, X.p, X.ld, Y.p, Y.ld);
+        launch_copy_block(ctx, grid_for((size_t)n * w, 256, 8 * ctx->num_sms), n, w, X.p, X.ld, Y.p, Y.ld);
         CK(cudaGetLastError());
       }
       return GPLHR_OK;
     }
     case GPLHR_PREC_JACOBI: {
       const int g = grid_for((size_t)n * w, 256, 8 * ctx->num_sms);
-      if (ctx->bulk32)
+      if (ctx->rec)
+        pk_rec(ctx, ctx->bulk32 ? gplhr::PK_JACOBI_F : gplhr::PK_JACOBI_D, g, 1, 0,
+               gplhr::PkJacobi{n, w, X.ld, Y.ld, ctx->prec_data, X.p, Y.p});
+      else if (ctx->bulk32)
         gplhr::jacobi_kernel<float><<<g, 256, 0, ctx->stream>>>(n, w, ctx->prec_data, X.p, X.ld, Y.p, Y.ld);
       else
         gplhr::jacobi_kernel<double><<<g, 256, 0, ctx->stream>>>(n, w, ctx->prec_data, X.p, X.ld, Y.p, Y.ld);
@@ -1187,7 +1362,12 @@ gplhr_status precond_apply_impl(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
       const int bpc = std::max(1, 1024 / (bs * w));
       const int grid = (nblocks + bpc - 1) / bpc;
       const size_t smem = (size_t)bpc * bs * w * sizeof(double2);
-      if (ctx->bulk32 && ctx->prec32)
+      if (ctx->rec) {
+        const bool f32 = ctx->bulk32 && ctx->prec32;
+        const gplhr::PkBj o{n, bs, w, X.ld, Y.ld, bpc, f32 ? (const void*)ctx->prec32 : (const void*)ctx->prec_data,
+                            X.p, Y.p};
+        pk_rec(ctx, f32 ? gplhr::PK_BJ_FF : ctx->bulk32 ? gplhr::PK_BJ_FD : gplhr::PK_BJ_DD, grid, 1, smem, o);
+      } else if (ctx->bulk32 && ctx->prec32)
         gplhr::block_jacobi_kernel<float, float2><<<grid, gplhr::BJ_THREADS, smem, ctx->stream>>>(
             n, bs, w, ctx->prec32, X.p, X.ld, Y.p, Y.ld, bpc);
       else if (ctx->bulk32)
@@ -1202,8 +1382,7 @@ gplhr_status precond_apply_impl(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
     case GPLHR_PREC_CSR: {
       if (X.p == Y.p) {  // out of place through a scratch block
         TRY(launch_spmm_one(ctx, ctx->Tcsr, nullptr, X, w, Blk{ctx->Tw1, ctx->k}, Blk{nullptr, 0}, ctx->bulk32));
-        gplhr::copy_block_kernel<<<grid_for((size_t)n * w, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-            n, w, ctx->Tw1, ctx->k, Y.p, Y.ld);
+        launch_copy_block(ctx, grid_for((size_t)n * w, 256, 8 * ctx->num_sms), n, w, ctx->Tw1, ctx->k, Y.p, Y.ld);
         CK(cudaGetLastError());
         return GPLHR_OK;
       }
@@ -1247,8 +1426,8 @@ gplhr_status orth_against(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w, const std
     if (wl > 0) {
       TRY(gram(ctx, L, wl, X, w, none, 0, ctx->dProjC, skip, false, cnt, ctx->bulk32));
       if (track)
-        CK(cudaMemcpyAsync(ctx->dTrackC + (size_t)pass * ctx->trk, ctx->dProjC, (size_t)wl * w * sizeof(double2),
-                           cudaMemcpyDeviceToDevice, ctx->stream));
+        TRY(copy_async(ctx, ctx->dTrackC + (size_t)pass * ctx->trk, ctx->dProjC, (size_t)wl * w * sizeof(double2),
+                       cudaMemcpyDeviceToDevice));
       TRY(combine(ctx, {In{L, wl, ctx->dProjC, kMinusOne}}, X, w, true, skip, none, -1, -1, cnt));
       for (const Extra& e : ex)
         TRY(combine(ctx, {In{e.EL, wl, ctx->dProjC, kMinusOne}}, e.E, w, true, skip, none, -1, -1, cnt));
@@ -1257,9 +1436,13 @@ gplhr_status orth_against(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w, const std
     double2* Rinv = ctx->dRinv + (size_t)pass * smax2;
     const size_t smem = (size_t)2 * w * w * sizeof(double2);
     const int ph = prof_begin(ctx, KC_CHOL, 8.0 * w * w * w / 2.0, 48.0 * w * w);
-    gplhr::chol_inv_kernel<<<1, 256, smem, ctx->stream>>>(w, (int64_t)ctx->n, ctx->dGram, Rinv,
-                                                          ctx->d_status + pass, skip, ctx->d_diag,
-                                                          track ? ctx->dTrackR + (size_t)pass * smax2 : nullptr);
+    double2* Rout = track ? ctx->dTrackR + (size_t)pass * smax2 : nullptr;
+    if (ctx->rec)
+      pk_rec(ctx, gplhr::PK_CHOL, 1, 1, smem,
+             gplhr::PkChol{w, (int64_t)ctx->n, ctx->dGram, Rinv, ctx->d_status + pass, skip, ctx->d_diag, Rout});
+    else
+      gplhr::chol_inv_kernel<<<1, 256, smem, ctx->stream>>>(w, (int64_t)ctx->n, ctx->dGram, Rinv,
+                                                            ctx->d_status + pass, skip, ctx->d_diag, Rout);
     prof_end(ctx, ph);
     CK(cudaGetLastError());
     TRY(combine(ctx, {In{X, w, Rinv, kOne}}, X, w, false, skip, none, -1, -1, cnt, -1, true));
@@ -1392,8 +1575,7 @@ gplhr_status gmres_apply_impl(gplhr_ctx* ctx, Blk X, int w, Blk Y) {
 
 gplhr_status upload(gplhr_ctx* ctx, double2* dst, const double2* src, size_t elems) {
   ctx->h2d_bytes += (int64_t)(elems * sizeof(double2));
-  CK(cudaMemcpyAsync(dst, src, elems * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
-  return GPLHR_OK;
+  return copy_async(ctx, dst, src, elems * sizeof(double2), cudaMemcpyHostToDevice);
 }
 
 // Pack a host matrix M (rows x cols of a SqMat, starting at (r0, c0)) into dst (row-major).
@@ -1409,9 +1591,11 @@ Blk blkU(gplhr_ctx* c, int col) { return Blk{c->U + col, c->s_max}; }
 
 // Residual R = AV M_B - BV M_A (all k columns, into Rw) and the backward errors of
 // the pairs with x_j = V z_j (Sec. 5.1); host receives resid[].
-gplhr_status residuals(gplhr_ctx* ctx) {
+// In parts: resid_issue stages the coefficients and issues (or records) the device
+// segment, resid_post reads the norms once it completed.
+gplhr_status resid_issue(gplhr_ctx* ctx, SqMat& Ze) {
   const int k = ctx->k;
-  SqMat Ze = gplhr::tri_eigvecs(ctx->RA, ctx->RB);
+  Ze = gplhr::tri_eigvecs(ctx->RA, ctx->RB);
   double2* h1 = ctx->h_small;
   double2* h2 = ctx->h_small + 2 * k * k;
   for (int i = 0; i < k; ++i)
@@ -1427,11 +1611,15 @@ gplhr_status residuals(gplhr_ctx* ctx) {
     TRY(combine(ctx, {In{blkAZ(ctx, 0), k, ctx->dC1, kOne}, In{blkBZ(ctx, 0), k, ctx->dC2, kMinusOne}},
                 Blk{ctx->Rw, k}, 2 * k, false, nullptr, Blk{nullptr, 0}, k, k));
     ctx->d2h_bytes += k * sizeof(double) + 3 * sizeof(int);
-    CK(cudaMemcpyAsync(ctx->h_norms, ctx->d_norms, k * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->h_diag, ctx->d_diag, 3 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    TRY(copy_async(ctx, ctx->h_norms, ctx->d_norms, k * sizeof(double), cudaMemcpyDeviceToHost));
+    TRY(copy_async(ctx, ctx->h_diag, ctx->d_diag, 3 * sizeof(int), cudaMemcpyDeviceToHost));
     return GPLHR_OK;
   }));
-  CK(cudaStreamSynchronize(ctx->stream));
+  return GPLHR_OK;
+}
+
+gplhr_status resid_post(gplhr_ctx* ctx, const SqMat& Ze) {
+  const int k = ctx->k;
   ctx->resid.assign(k, 0.0);
   for (int j = 0; j < k; ++j) {
     double zn = 0.0;
@@ -1453,6 +1641,13 @@ gplhr_status residuals(gplhr_ctx* ctx) {
     return GPLHR_ETIMEOUT;
   }
   return GPLHR_OK;
+}
+
+gplhr_status residuals(gplhr_ctx* ctx) {
+  SqMat Ze;
+  TRY(resid_issue(ctx, Ze));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return resid_post(ctx, Ze);
 }
 
 // Host: sorted QZ of the s x s pencil in h_phipsi, returns Ybar_R, Ybar_L, Rbar_A, Rbar_B.
@@ -1627,15 +1822,13 @@ gplhr_status factored_pencil_issue(gplhr_ctx* ctx, int s, int sk) {
   const size_t nC = (size_t)k * sk, nR = (size_t)sk * sk;
   double2* hC = ctx->h_track;                // 3 x nC
   double2* hR = ctx->h_track + 3 * nC;       // 3 x nR
-  CK(cudaMemcpyAsync(ctx->h_phipsi, ctx->dPhiPsi, (size_t)s * s * sizeof(double2), cudaMemcpyDeviceToHost,
-                     ctx->stream));
+  TRY(copy_async(ctx, ctx->h_phipsi, ctx->dPhiPsi, (size_t)s * s * sizeof(double2), cudaMemcpyDeviceToHost));
   for (int p = 0; p < 3; ++p) {
-    CK(cudaMemcpyAsync(hC + p * nC, ctx->dTrackC + (size_t)p * ctx->trk, nC * sizeof(double2), cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    CK(cudaMemcpyAsync(hR + p * nR, ctx->dTrackR + (size_t)p * smax2, nR * sizeof(double2), cudaMemcpyDeviceToHost,
-                       ctx->stream));
+    TRY(copy_async(ctx, hC + p * nC, ctx->dTrackC + (size_t)p * ctx->trk, nC * sizeof(double2),
+                   cudaMemcpyDeviceToHost));
+    TRY(copy_async(ctx, hR + p * nR, ctx->dTrackR + (size_t)p * smax2, nR * sizeof(double2), cudaMemcpyDeviceToHost));
   }
-  CK(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  TRY(copy_async(ctx, ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   ctx->d2h_bytes += (int64_t)((size_t)s * s + 3 * (nC + nR)) * sizeof(double2) + sizeof(int);
   return GPLHR_OK;
 }
@@ -1708,34 +1901,52 @@ gplhr_status factored_pencil_qz(gplhr_ctx* ctx, int s, int sk, SqMat& RAb, SqMat
   return GPLHR_OK;
 }
 
-// One pass of the while loop of Algorithm 2 (steps 6-30).  Rw holds the residual.
-gplhr_status iterate_once(gplhr_ctx* ctx) {
-  const int k = ctx->k, q = ctx->q, kk = k - ctx->q, m = ctx->m;
-  const int sm = ctx->s_max;
-  const Blk V = blkZ(ctx, 0), Q = blkU(ctx, 0);
-  const Blk right = ctx->hasB ? Q : V;  // projector before T: (I - QQ^*), or (I - VV^*) if B = I
-  const bool withP = ctx->hasP && kk > 0 && ctx->p_mode != 2;
-  const bool lob = ctx->p_mode == 1;
-  const int poff = lob ? q : 0;  // a LOBPCG-style P keeps its columns at V's positions
-  const int pslot = k + (m + 1) * kk;
-  const int sP = withP ? kk : 0;
-  const int s = pslot + sP;
-  const int sk = s - k;
+// One pass of the while loop of Algorithm 2 (steps 6-30), in parts: the plan (sizes of
+// this iteration and the host staging of segment A), segment A (steps 7-24 up to the
+// copies of the projected pencil to the host), the sorted QZ on the host, segment B
+// (steps 25-28), and the host update of the factors (steps 29-30).  iterate_once runs
+// them in order on the context's stream; the persistent batched iteration runs the
+// device segments of many contexts in one kernel each.  Rw holds the residual.
+struct IterPlan {
+  int k, q, kk, m, sm, pslot, sP, s, sk, cv, flags, poff;
+  bool withP, lob;
+  SqMat RAb, RBb, YLb, YRb;
+};
+
+void iter_plan(gplhr_ctx* ctx, IterPlan& p) {
+  p.k = ctx->k;
+  p.q = ctx->q;
+  p.kk = p.k - p.q;
+  p.m = ctx->m;
+  p.sm = ctx->s_max;
+  p.withP = ctx->hasP && p.kk > 0 && ctx->p_mode != 2;
+  p.lob = ctx->p_mode == 1;
+  p.poff = p.lob ? p.q : 0;  // a LOBPCG-style P keeps its columns at V's positions
+  p.pslot = p.k + (p.m + 1) * p.kk;
+  p.sP = p.withP ? p.kk : 0;
+  p.s = p.pslot + p.sP;
+  p.sk = p.s - p.k;
   // only the leading k + kk positions of the ordering are used (V and a thick P)
-  const int cv = ctx->p_mode == 0 ? k + kk : k;
-  const int flags = (ctx->bulk32 ? 1 : 0) | (ctx->recompute ? 2 : 0) | (ctx->factored ? 4 : 0) | (withP ? 8 : 0) |
-                    (ctx->p_mode << 4) | (ctx->right_proj ? 0 : 64);
+  p.cv = ctx->p_mode == 0 ? p.k + p.kk : p.k;
+  p.flags = (ctx->bulk32 ? 1 : 0) | (ctx->recompute ? 2 : 0) | (ctx->factored ? 4 : 0) | (p.withP ? 8 : 0) |
+            (ctx->p_mode << 4) | (ctx->right_proj ? 0 : 64);
   // host staging of segment A: M_B, M_A of the active pairs for the S-recurrence
-  if (m > 0) {
-    double2* hm = ctx->h_small + 4 * k * k;
-    for (int i = 0; i < kk; ++i)
-      for (int j = 0; j < kk; ++j) {
-        hm[i * kk + j] = d2(ctx->MB(q + i, q + j));
-        hm[kk * kk + i * kk + j] = d2(ctx->MA(q + i, q + j));
+  if (p.m > 0) {
+    double2* hm = ctx->h_small + 4 * p.k * p.k;
+    for (int i = 0; i < p.kk; ++i)
+      for (int j = 0; j < p.kk; ++j) {
+        hm[i * p.kk + j] = d2(ctx->MB(p.q + i, p.q + j));
+        hm[p.kk * p.kk + i * p.kk + j] = d2(ctx->MA(p.q + i, p.q + j));
       }
   }
-  // segment A: steps 7-24 up to the copies of the projected pencil to the host
-  TRY(run_segment(ctx, seg_key(1, q, m, kk, s, flags), [&]() -> gplhr_status {
+}
+
+// Segment A: steps 7-24 up to the copies of the projected pencil to the host.
+gplhr_status iter_seg_a(gplhr_ctx* ctx, const IterPlan& p) {
+  const int k = p.k, q = p.q, kk = p.kk, m = p.m, sm = p.sm, pslot = p.pslot, s = p.s, sk = p.sk;
+  const Blk V = blkZ(ctx, 0), Q = blkU(ctx, 0);
+  const Blk right = ctx->hasB ? Q : V;  // projector before T: (I - QQ^*), or (I - VV^*) if B = I
+  return run_segment(ctx, seg_key(1, q, m, kk, s, p.flags), [&]() -> gplhr_status {
     // steps 7-8 / 10: W = (I - VV^*) T (I - QQ^*) R, active columns q..k-1
     Blk Ra{ctx->Rw + q, k};
     if (ctx->right_proj) TRY(project_out(ctx, right, k, Ra, kk));
@@ -1756,18 +1967,15 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
       TRY(spmm_AB(ctx, blkZ(ctx, cur), kk, blkAZ(ctx, cur), blkBZ(ctx, cur)));
     }
     // step 21: P against V, W, S and orth; AP, BP follow by the same transforms
-    if (withP) {
+    if (p.withP) {
       const size_t nw = (size_t)ctx->n;
       const int ncopy = ctx->recompute ? 1 : (ctx->hasB ? 3 : 2);
+      const int gcp = grid_for(nw * kk, 256, 8 * ctx->num_sms);
       const int ph = prof_begin(ctx, KC_OTHER, 0.0, 32.0 * ctx->n * kk * ncopy, ncopy);
-      gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-          ctx->n, kk, ctx->Pb + poff, k, ctx->Z + pslot, sm);
+      launch_copy_block(ctx, gcp, ctx->n, kk, ctx->Pb + p.poff, k, ctx->Z + pslot, sm);
       if (!ctx->recompute) {
-        gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-            ctx->n, kk, ctx->APb + poff, k, ctx->AZ + pslot, sm);
-        if (ctx->hasB)
-          gplhr::copy_block_kernel<<<grid_for(nw * kk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-              ctx->n, kk, ctx->BPb + poff, k, ctx->BZ + pslot, sm);
+        launch_copy_block(ctx, gcp, ctx->n, kk, ctx->APb + p.poff, k, ctx->AZ + pslot, sm);
+        if (ctx->hasB) launch_copy_block(ctx, gcp, ctx->n, kk, ctx->BPb + p.poff, k, ctx->BZ + pslot, sm);
       }
       prof_end(ctx, ph);
       CK(cudaGetLastError());
@@ -1782,8 +1990,8 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
     }
     // steps 23-24: Qhat = orth((A - sigma B) [W S P]) against Q;  U = [Q Qhat]
     const int ph_ax = prof_begin(ctx, KC_OTHER, 8.0 * ctx->n * sk, 48.0 * ctx->n * sk);
-    gplhr::axpby_kernel<<<grid_for((size_t)ctx->n * sk, 256, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
-        ctx->n, sk, kOne, ctx->AZ + k, sm, d2(-ctx->sigma), blkBZ(ctx, k).p, sm, ctx->U + k, sm);
+    launch_axpby(ctx, grid_for((size_t)ctx->n * sk, 256, 8 * ctx->num_sms), ctx->n, sk, kOne, ctx->AZ + k, sm,
+                 d2(-ctx->sigma), blkBZ(ctx, k).p, sm, ctx->U + k, sm);
     prof_end(ctx, ph_ax);
     CK(cudaGetLastError());
     TRY(orth_against(ctx, Q, k, blkU(ctx, k), sk, {}, ctx->factored));
@@ -1791,31 +1999,41 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
     // step 24: projected pencil (U^* A Z, U^* B Z) by two Gram products
     TRY(gram(ctx, blkU(ctx, 0), s, blkAZ(ctx, 0), s, blkBZ(ctx, 0), s, ctx->dPhiPsi));
     ctx->d2h_bytes += (int64_t)2 * s * s * sizeof(double2);
-    CK(cudaMemcpyAsync(ctx->h_phipsi, ctx->dPhiPsi, (size_t)2 * s * s * sizeof(double2), cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    return GPLHR_OK;
-  }));
-  CK(cudaStreamSynchronize(ctx->stream));
-  SqMat RAb, RBb, YLb, YRb;
+    return copy_async(ctx, ctx->h_phipsi, ctx->dPhiPsi, (size_t)2 * s * s * sizeof(double2), cudaMemcpyDeviceToHost);
+  });
+}
+
+// Host, after segment A completed: the sorted QZ and the staging of segment B.
+gplhr_status iter_qz(gplhr_ctx* ctx, IterPlan& p) {
+  const int k = p.k, s = p.s, cv = p.cv;
   if (ctx->factored)
-    TRY(factored_pencil_qz(ctx, s, sk, RAb, RBb, YLb, YRb, cv));
+    TRY(factored_pencil_qz(ctx, s, p.sk, p.RAb, p.RBb, p.YLb, p.YRb, cv));
   else
-    TRY(host_qz(ctx, s, RAb, RBb, YLb, YRb, cv, k, cv));
+    TRY(host_qz(ctx, s, p.RAb, p.RBb, p.YLb, p.YRb, cv, k, cv));
   // steps 25-28: V = Z Ybar_R(:, 1:k), P = Z Ybar_R(:, k+1:k+kk), Q = U Ybar_L(:, 1:k)
   double2* hy = ctx->h_small + 6 * k * k;
   double2* hl = hy + (size_t)s * cv;
-  pack(hy, YRb, 0, s, 0, cv);
-  pack(hl, YLb, 0, s, 0, k);
-  TRY(run_segment(ctx, seg_key(2, q, m, kk, s, flags), [&]() -> gplhr_status {
+  pack(hy, p.YRb, 0, s, 0, cv);
+  pack(hl, p.YLb, 0, s, 0, k);
+  return GPLHR_OK;
+}
+
+// Segment B: steps 25-28.
+gplhr_status iter_seg_b(gplhr_ctx* ctx, const IterPlan& p) {
+  const int k = p.k, s = p.s, cv = p.cv, sm = p.sm;
+  const bool lob = p.lob;
+  const double2* hy = ctx->h_small + 6 * k * k;
+  const double2* hl = hy + (size_t)s * cv;
+  return run_segment(ctx, seg_key(2, p.q, p.m, p.kk, s, p.flags), [&]() -> gplhr_status {
     TRY(upload(ctx, ctx->dYR, hy, (size_t)s * cv));
     TRY(upload(ctx, ctx->dYL, hl, (size_t)s * k));
     const int nb = (int)grid_for((size_t)ctx->n * k, 256, 8 * ctx->num_sms);
     if (lob) {  // V_old (and A V_old, B V_old) into the P buffers before the update
       const int ph = prof_begin(ctx, KC_OTHER, 0.0, 32.0 * ctx->n * k, 1);
-      gplhr::copy_block_kernel<<<nb, 256, 0, ctx->stream>>>(ctx->n, k, ctx->Z, sm, ctx->Pb, k);
+      launch_copy_block(ctx, nb, ctx->n, k, ctx->Z, sm, ctx->Pb, k);
       if (!ctx->recompute) {
-        gplhr::copy_block_kernel<<<nb, 256, 0, ctx->stream>>>(ctx->n, k, ctx->AZ, sm, ctx->APb, k);
-        if (ctx->hasB) gplhr::copy_block_kernel<<<nb, 256, 0, ctx->stream>>>(ctx->n, k, ctx->BZ, sm, ctx->BPb, k);
+        launch_copy_block(ctx, nb, ctx->n, k, ctx->AZ, sm, ctx->APb, k);
+        if (ctx->hasB) launch_copy_block(ctx, nb, ctx->n, k, ctx->BZ, sm, ctx->BPb, k);
       }
       prof_end(ctx, ph);
       CK(cudaGetLastError());
@@ -1834,23 +2052,33 @@ gplhr_status iterate_once(gplhr_ctx* ctx) {
     TRY(combine(ctx, {In{blkU(ctx, 0), s, ctx->dYL, kOne}}, blkU(ctx, 0), k, false));
     if (lob) {  // Eq. P_lobpcg with C = I: P = V - V_old (A P, B P likewise)
       const int ph = prof_begin(ctx, KC_OTHER, 8.0 * ctx->n * k, 48.0 * ctx->n * k, 1);
-      gplhr::axpby_kernel<<<nb, 256, 0, ctx->stream>>>(ctx->n, k, kOne, ctx->Z, sm, kMinusOne, ctx->Pb, k, ctx->Pb, k);
+      launch_axpby(ctx, nb, ctx->n, k, kOne, ctx->Z, sm, kMinusOne, ctx->Pb, k, ctx->Pb, k);
       if (!ctx->recompute) {
-        gplhr::axpby_kernel<<<nb, 256, 0, ctx->stream>>>(ctx->n, k, kOne, ctx->AZ, sm, kMinusOne, ctx->APb, k,
-                                                         ctx->APb, k);
-        if (ctx->hasB)
-          gplhr::axpby_kernel<<<nb, 256, 0, ctx->stream>>>(ctx->n, k, kOne, ctx->BZ, sm, kMinusOne, ctx->BPb, k,
-                                                           ctx->BPb, k);
+        launch_axpby(ctx, nb, ctx->n, k, kOne, ctx->AZ, sm, kMinusOne, ctx->APb, k, ctx->APb, k);
+        if (ctx->hasB) launch_axpby(ctx, nb, ctx->n, k, kOne, ctx->BZ, sm, kMinusOne, ctx->BPb, k, ctx->BPb, k);
       }
       prof_end(ctx, ph);
       CK(cudaGetLastError());
     }
     return GPLHR_OK;
-  }));
+  });
+}
+
+// Host, after segment B was issued: steps 29-30.
+void iter_finish(gplhr_ctx* ctx, const IterPlan& p) {
   ctx->hasP = ctx->p_mode != 2;
-  // steps 29-30
-  set_factors(ctx, RAb, RBb);
+  set_factors(ctx, p.RAb, p.RBb);
   ctx->it += 1;
+}
+
+gplhr_status iterate_once(gplhr_ctx* ctx) {
+  IterPlan p;
+  iter_plan(ctx, p);
+  TRY(iter_seg_a(ctx, p));
+  CK(cudaStreamSynchronize(ctx->stream));
+  TRY(iter_qz(ctx, p));
+  TRY(iter_seg_b(ctx, p));
+  iter_finish(ctx, p);
   return GPLHR_OK;
 }
 
@@ -1889,6 +2117,414 @@ gplhr_status run_iterations(gplhr_ctx* ctx, int niter, gplhr_info* info, bool* c
   fill_info(ctx, info);
   if (conv_out) *conv_out = conv;
   return GPLHR_OK;
+}
+
+// -------------------------------------------------- persistent batched iteration ----
+// Many contexts (pencils of uneven size, or shifts over one pencil) iterate in lockstep,
+// and each device segment of an iteration (A: steps 7-24, B: steps 25-28, C: the
+// residual and its norms) runs for all of them in ONE launch of the persistent kernel of
+// persist.cuh: the host records each context's launches (the same kernels, grids and
+// arguments as gplhr_iterate, on DFMA, with grids sized to the context's share of the
+// SMs), merges them into one program, and the kernel walks it with a grid barrier per
+// step.  An iteration of the whole batch is three launches and two host round trips (the
+// pencils for the host QZ, the residual norms for locking), instead of ~100 launches
+// per context.
+struct PkBuf {
+  unsigned char* host = nullptr;  // pinned staging of a program
+  unsigned char* dev = nullptr;
+  size_t cap = 0;
+};
+
+struct PkRunner {
+  int dev = 0, num_sms = 0;
+  cudaStream_t stream = nullptr;
+  PkBuf buf[3];  // one per segment kind, so a program is not overwritten while its copy is pending
+  gplhr::PkBarrier* bar = nullptr;
+  int* derr = nullptr;
+  int* herr = nullptr;
+  unsigned long long limit_ns = 0;
+  int probe = 0;
+  int64_t launches = 0, steps = 0, ops = 0;
+  int grid = 0;
+  // host time recording segments, merging and uploading programs, in the host QZ, and
+  // waiting for the device (ms)
+  double record_ms = 0.0, build_ms = 0.0, qz_ms = 0.0, wait_ms = 0.0;
+  // the last program of each segment kind: its recordings and device program
+  std::vector<const PkRecorder*> last_recs[3];
+  gplhr::PkProgram last_prog[3] = {};
+  size_t last_smem[3] = {0, 0, 0}, last_nsteps[3] = {0, 0, 0}, last_nops[3] = {0, 0, 0};
+  std::string err;
+  ~PkRunner() {
+    for (PkBuf& b : buf) {
+      if (b.host) cudaFreeHost(b.host);
+      if (b.dev) cudaFree(b.dev);
+    }
+    if (bar) cudaFree(bar);
+    if (derr) cudaFree(derr);
+    if (herr) cudaFreeHost(herr);
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
+constexpr double kPkShare = 4.0;
+
+#define PKCK(call)                                                     \
+  do {                                                                 \
+    cudaError_t e_ = (call);                                           \
+    if (e_ != cudaSuccess) {                                           \
+      R.err = std::string(#call) + ": " + cudaGetErrorString(e_);      \
+      return GPLHR_ECUDA;                                              \
+    }                                                                  \
+  } while (0)
+
+// Merge the recorded segments into one program and run it on R.stream: host-to-device
+// copies, the program's upload, the persistent kernel, device-to-host copies.
+gplhr_status pk_launch_impl(PkRunner& R, int seg, const std::vector<const PkRecorder*>& recs);
+gplhr_status pk_launch(PkRunner& R, int seg, const std::vector<const PkRecorder*>& recs) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const gplhr_status st = pk_launch_impl(R, seg, recs);
+  R.build_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return st;
+}
+
+// The persistent kernel on R.stream: its barrier zeroed, cooperative (all CTAs resident).
+gplhr_status pk_run(PkRunner& R, gplhr::PkProgram prog, size_t smem, size_t nsteps, size_t nops) {
+  if (smem > 48 * 1024)
+    PKCK(cudaFuncSetAttribute(gplhr::persistent_segment_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem));
+  int occ = 0;
+  PKCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gplhr::persistent_segment_kernel, gplhr::PK_THREADS,
+                                                     smem));
+  if (occ < 1) {
+    R.err = "persistent kernel: no CTA fits an SM with " + std::to_string(smem) + " bytes of shared memory";
+    return GPLHR_EINVAL;
+  }
+  R.grid = R.num_sms * std::min(occ, gplhr::PK_CTAS_PER_SM);
+  PKCK(cudaMemsetAsync(R.bar, 0, sizeof(gplhr::PkBarrier), R.stream));
+  void* kargs[] = {&prog, &R.bar, &R.derr, &R.limit_ns, &R.probe};
+  PKCK(cudaLaunchCooperativeKernel((const void*)gplhr::persistent_segment_kernel, dim3(R.grid),
+                                   dim3(gplhr::PK_THREADS), kargs, smem, R.stream));
+  R.launches += 1;
+  R.steps += (int64_t)nsteps;
+  R.ops += (int64_t)nops;
+  return GPLHR_OK;
+}
+
+gplhr_status pk_launch_impl(PkRunner& R, int seg, const std::vector<const PkRecorder*>& recs) {
+  // the same recordings as the last launch of this segment kind: its program is on the
+  // device already (recordings are immutable once made)
+  if (!recs.empty() && recs == R.last_recs[seg])
+    return pk_run(R, R.last_prog[seg], R.last_smem[seg], R.last_nsteps[seg], R.last_nops[seg]);
+  R.last_recs[seg].clear();
+  size_t nops = 0, nsteps = 0, argbytes = 0, smem = 0;
+  for (const PkRecorder* r : recs) {
+    nops += r->ops.size();
+    nsteps = std::max(nsteps, r->ops.size());
+    for (const PkRecorder::Op& o : r->ops) {
+      argbytes += (o.size + 15) & ~(size_t)15;
+      smem = std::max(smem, o.smem);
+    }
+  }
+  // the copies to and from pinned host memory run inside the kernel (the device reads and
+  // writes the host's pinned staging directly): the host-to-device ones as a first step,
+  // the device-to-host ones as a last step
+  size_t npre = 0, npost = 0;
+  for (const PkRecorder* r : recs) {
+    npre += r->pre.size();
+    npost += r->post.size();
+  }
+  const size_t step0 = npre ? 1 : 0;
+  nsteps += step0 + (npost ? 1 : 0);
+  nops += npre + npost;
+  argbytes += (npre + npost) * ((sizeof(gplhr::PkRaw) + 15) & ~(size_t)15);
+  if (nops > 0) {
+    auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    const size_t o_ops = 0, o_vs = al(o_ops + nops * sizeof(gplhr::PkOp)), o_sb = al(o_vs + nops * sizeof(int)),
+                 o_st = al(o_sb + (nsteps + 1) * sizeof(int)), o_args = al(o_st + nsteps * sizeof(int)),
+                 total = o_args + argbytes;
+    if (argbytes > 0xFFFFFFFFull) {
+      R.err = "persistent program: argument pool too large";
+      return GPLHR_EINVAL;
+    }
+    PkBuf& B = R.buf[seg];
+    if (B.cap < total) {
+      if (B.host) cudaFreeHost(B.host);
+      if (B.dev) cudaFree(B.dev);
+      B.host = nullptr;
+      B.dev = nullptr;
+      B.cap = 0;
+      const size_t cap = total + total / 2;
+      if (cudaMallocHost(&B.host, cap) != cudaSuccess || cudaMalloc(&B.dev, cap) != cudaSuccess) {
+        R.err = "persistent program: allocation failed";
+        return GPLHR_ENOMEM;
+      }
+      B.cap = cap;
+    }
+    gplhr::PkOp* ops = reinterpret_cast<gplhr::PkOp*>(B.host + o_ops);
+    int* vstart = reinterpret_cast<int*>(B.host + o_vs);
+    int* step_begin = reinterpret_cast<int*>(B.host + o_sb);
+    int* step_total = reinterpret_cast<int*>(B.host + o_st);
+    size_t no = 0, ao = 0;
+    int64_t v = 0;
+    auto put = [&](int kind, int gx, int gy, const void* arg, size_t size) {
+      std::memcpy(B.host + o_args + ao, arg, size);
+      ops[no] = gplhr::PkOp{kind, gx, gy, (unsigned)ao};
+      vstart[no] = (int)v;
+      v += (int64_t)gx * gy;
+      ao += (size + 15) & ~(size_t)15;
+      ++no;
+    };
+    auto put_copies = [&](bool pre) {
+      for (const PkRecorder* r : recs)
+        for (const PkRecorder::Copy& c : pre ? r->pre : r->post) {
+          const gplhr::PkRaw a{(const unsigned char*)c.src, (unsigned char*)c.dst, (int64_t)c.bytes};
+          put(gplhr::PK_COPY_RAW, (int)std::max<size_t>(1, std::min<size_t>(8, c.bytes / 4096)), 1, &a, sizeof(a));
+        }
+    };
+    for (size_t j = 0; j < nsteps; ++j) {
+      step_begin[j] = (int)no;
+      v = 0;
+      if (j < step0) {
+        put_copies(true);
+      } else if (npost && j == nsteps - 1) {
+        put_copies(false);
+      } else {
+        for (const PkRecorder* r : recs) {
+          if (j - step0 >= r->ops.size()) continue;
+          const PkRecorder::Op& o = r->ops[j - step0];
+          put(o.kind, o.gx, o.gy, r->args.data() + o.off, o.size);
+        }
+      }
+      if (v > INT_MAX) {
+        R.err = "persistent program: too many CTAs in one step";
+        return GPLHR_EINVAL;
+      }
+      step_total[j] = (int)v;
+    }
+    step_begin[nsteps] = (int)no;
+    PKCK(cudaMemcpyAsync(B.dev, B.host, total, cudaMemcpyHostToDevice, R.stream));
+    gplhr::PkProgram prog{reinterpret_cast<const gplhr::PkOp*>(B.dev + o_ops), B.dev + o_args,
+                          reinterpret_cast<const int*>(B.dev + o_sb), reinterpret_cast<const int*>(B.dev + o_vs),
+                          reinterpret_cast<const int*>(B.dev + o_st), (int)nsteps};
+    TRY(pk_run(R, prog, smem, nsteps, nops));
+    R.last_recs[seg] = recs;
+    R.last_prog[seg] = prog;
+    R.last_smem[seg] = smem;
+    R.last_nsteps[seg] = nsteps;
+    R.last_nops[seg] = nops;
+  }
+  return GPLHR_OK;
+}
+
+// Wait for R.stream; GPLHR_ETIMEOUT if a barrier wait of the kernel gave up.
+gplhr_status pk_sync(PkRunner& R) {
+  PKCK(cudaMemcpyAsync(R.herr, R.derr, sizeof(int), cudaMemcpyDeviceToHost, R.stream));
+  const auto t0 = std::chrono::steady_clock::now();
+  PKCK(cudaStreamSynchronize(R.stream));
+  R.wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (*R.herr != 0) {
+    R.err = "persistent kernel: a grid barrier wait gave up";
+    return GPLHR_ETIMEOUT;
+  }
+  return GPLHR_OK;
+}
+
+// A fixed pool of host threads for the per-context host work of the persistent batch
+// (recording, QZ, residual bookkeeping): spawning threads for each of the five parallel
+// phases of an iteration costs more than the work itself.
+class PkPool {
+ public:
+  PkPool(int nthreads, int dev) : dev_(dev) {
+    for (int t = 1; t < nthreads; ++t) th_.emplace_back([this]() { loop(); });
+  }
+  ~PkPool() {
+    {
+      std::lock_guard<std::mutex> g(m_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : th_) t.join();
+  }
+  // f(idx[j]) for every j, on the pool and the calling thread; returns when all are done.
+  void run(const std::vector<int>& idx, const std::function<void(int)>& f) {
+    if (idx.empty()) return;
+    {
+      std::lock_guard<std::mutex> g(m_);
+      idx_ = &idx;
+      f_ = &f;
+      next_ = 0;
+      done_ = 0;
+      ++gen_;
+    }
+    cv_.notify_all();
+    work();
+    std::unique_lock<std::mutex> g(m_);
+    done_cv_.wait(g, [&]() { return done_ == (int)idx.size(); });
+    idx_ = nullptr;
+    f_ = nullptr;
+  }
+
+ private:
+  void work() {
+    for (;;) {
+      int j;
+      const std::vector<int>* idx;
+      const std::function<void(int)>* f;
+      {
+        std::lock_guard<std::mutex> g(m_);
+        if (!idx_ || next_ >= (int)idx_->size()) return;
+        j = next_++;
+        idx = idx_;
+        f = f_;
+      }
+      (*f)((*idx)[j]);
+      {
+        std::lock_guard<std::mutex> g(m_);
+        if (++done_ == (int)idx->size()) done_cv_.notify_all();
+      }
+    }
+  }
+  void loop() {
+    cudaSetDevice(dev_);
+    uint64_t seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> g(m_);
+        cv_.wait(g, [&]() { return stop_ || gen_ != seen; });
+        if (stop_) return;
+        seen = gen_;
+      }
+      work();
+    }
+  }
+  int dev_;
+  std::vector<std::thread> th_;
+  std::mutex m_;
+  std::condition_variable cv_, done_cv_;
+  const std::vector<int>* idx_ = nullptr;
+  const std::function<void(int)>* f_ = nullptr;
+  int next_ = 0, done_ = 0;
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+};
+
+// The persistent batched iteration over started contexts: each runs until it converges,
+// fails, or has run its budget (iters_cap[i] total iterations).
+gplhr_status pk_iterate(int nctx, gplhr_ctx* const* ctxs, const std::vector<int>& iters_cap, int nthreads,
+                        std::vector<gplhr_status>& st, std::vector<char>& conv, PkRunner& R) {
+  st.assign(nctx, GPLHR_OK);
+  conv.assign(nctx, 0);
+  PKCK(cudaGetDevice(&R.dev));
+  PKCK(cudaDeviceGetAttribute(&R.num_sms, cudaDevAttrMultiProcessorCount, R.dev));
+  PKCK(cudaStreamCreateWithFlags(&R.stream, cudaStreamNonBlocking));
+  PKCK(cudaMalloc(&R.bar, sizeof(gplhr::PkBarrier)));
+  PKCK(cudaMalloc(&R.derr, sizeof(int)));
+  PKCK(cudaMemset(R.derr, 0, sizeof(int)));
+  PKCK(cudaMallocHost(&R.herr, sizeof(int)));
+  // the barrier's time limit: the contexts' wait limit (tests of at most 20 us each)
+  int tries = gplhr::TC_WAIT_TRIES;
+  for (int i = 0; i < nctx; ++i) {
+    tries = std::min(tries, ctxs[i]->tc_wait_tries);
+    if (ctxs[i]->tc_probe) R.probe = 1;
+  }
+  R.limit_ns = (unsigned long long)tries * 20000ull;
+  // DFMA kernels (the tensor-core pipelines keep their own CTA shape), grids sized to a
+  // share of the SMs proportional to the context's rows: kPkShare x the SM count in all,
+  // so that each step has a few virtual CTAs per persistent CTA (measured on the batched
+  // workload, 80 contexts, 2 resident CTAs per SM: share 1 / 2 / 4 / 8 / 16 -> 33.3 / 30.5 /
+  // 28.6 / 30.3 / 31.2 ms per FP64 batch iteration; with 4: 4 / 8 -> 20.6 / 22.0 ms)
+  double nsum = 0.0;
+  for (int i = 0; i < nctx; ++i) nsum += ctxs[i]->n;
+  std::vector<int> saved_sms(nctx);
+  std::vector<char> saved_tc(nctx);
+  for (int i = 0; i < nctx; ++i) {
+    gplhr_ctx* c = ctxs[i];
+    saved_sms[i] = c->num_sms;
+    saved_tc[i] = c->tc;
+    c->num_sms = std::max(1, (int)std::lround(kPkShare * R.num_sms * c->n / nsum));
+    c->tc = false;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) st[i] = GPLHR_ECUDA;
+  }
+  std::vector<int> all(nctx);
+  for (int i = 0; i < nctx; ++i) all[i] = i;
+  PkPool pool(std::max(1, std::min(nthreads, nctx)), R.dev);
+  pool.run(all, [&](int i) {
+    if (st[i] != GPLHR_OK) return;
+    st[i] = phase_update(ctxs[i]);
+    if (st[i] == GPLHR_OK) conv[i] = converged_update(ctxs[i]);
+  });
+  std::vector<IterPlan> plan(nctx);
+  std::vector<std::map<uint64_t, gplhr_ctx::PkCached>> cache(nctx);
+  std::vector<SqMat> Ze(nctx);
+  gplhr_status fatal = GPLHR_OK;
+  // record the contexts' segments on host threads (each context records into its own
+  // recorder), then keep the ones that succeeded, in context order
+  auto record = [&](std::vector<int>& act, const std::function<gplhr_status(int)>& issue) {
+    const auto t0 = std::chrono::steady_clock::now();
+    pool.run(act, [&](int i) {
+      ctxs[i]->pk_cache = &cache[i];
+      ctxs[i]->rec_last = nullptr;
+      st[i] = issue(i);
+      ctxs[i]->pk_cache = nullptr;
+      if (st[i] == GPLHR_OK && !ctxs[i]->rec_last) {
+        ctxs[i]->err = "persistent batch: a segment recorded nothing";
+        st[i] = GPLHR_EINVAL;
+      }
+    });
+    std::vector<const PkRecorder*> rs;
+    std::vector<int> keep;
+    for (int i : act)
+      if (st[i] == GPLHR_OK) {
+        rs.push_back(ctxs[i]->rec_last);
+        keep.push_back(i);
+      }
+    act.swap(keep);
+    R.record_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return rs;
+  };
+  for (;;) {
+    std::vector<int> act;
+    for (int i = 0; i < nctx; ++i)
+      if (st[i] == GPLHR_OK && !conv[i] && ctxs[i]->it < iters_cap[i]) act.push_back(i);
+    if (act.empty()) break;
+    for (int i : act) {
+      if (ctxs[i]->bulk32) ctxs[i]->fp32_iters += 1;
+      iter_plan(ctxs[i], plan[i]);
+    }
+    // segment A, then the host QZ of every pencil
+    fatal = pk_launch(R, 0, record(act, [&](int i) { return iter_seg_a(ctxs[i], plan[i]); }));
+    if (fatal == GPLHR_OK) fatal = pk_sync(R);
+    if (fatal != GPLHR_OK) break;
+    auto tq = std::chrono::steady_clock::now();
+    pool.run(act, [&](int i) { st[i] = iter_qz(ctxs[i], plan[i]); });
+    R.qz_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tq).count();
+    std::vector<int> act_b;
+    for (int i : act)
+      if (st[i] == GPLHR_OK) act_b.push_back(i);
+    // segment B, the factors, segment C
+    fatal = pk_launch(R, 1, record(act_b, [&](int i) { return iter_seg_b(ctxs[i], plan[i]); }));
+    if (fatal != GPLHR_OK) break;
+    for (int i : act_b) iter_finish(ctxs[i], plan[i]);
+    fatal = pk_launch(R, 2, record(act_b, [&](int i) { return resid_issue(ctxs[i], Ze[i]); }));
+    if (fatal == GPLHR_OK) fatal = pk_sync(R);
+    if (fatal != GPLHR_OK) break;
+    // residuals, the precision switch (on the context's own stream) and locking
+    pool.run(act_b, [&](int i) {
+      gplhr_ctx* c = ctxs[i];
+      st[i] = resid_post(c, Ze[i]);
+      if (st[i] == GPLHR_OK) st[i] = phase_update(c);
+      if (st[i] == GPLHR_OK) conv[i] = converged_update(c);
+    });
+  }
+  for (int i = 0; i < nctx; ++i) {
+    ctxs[i]->num_sms = saved_sms[i];
+    ctxs[i]->tc = saved_tc[i] != 0;
+    if (fatal != GPLHR_OK && st[i] == GPLHR_OK && !conv[i]) {
+      st[i] = fatal;
+      ctxs[i]->err = R.err;
+    }
+  }
+  return fatal;
 }
 
 // ------------------------------------------------------------ GPLHR-EIG ------
@@ -3332,6 +3968,112 @@ gplhr_status gplhr_solve_batched(int32_t nctx, gplhr_ctx* const* ctxs, const voi
     return gplhr_solve(ctxs[i], V0 ? V0[i] : nullptr, V0_where ? V0_where[i] : GPLHR_HOST,
                        is_complex ? is_complex[i] : 0, seeds ? seeds[i] : 0, infos ? infos + i : nullptr);
   });
+}
+
+// Persistent batched iteration (pk_iterate): checks shared by the two entry points.
+static gplhr_status pk_check(int32_t nctx, gplhr_ctx* const* ctxs, bool need_started) {
+  if (nctx < 0 || (nctx > 0 && !ctxs)) {
+    g_create_error = "persistent batch: need nctx >= 0 and a context array";
+    return GPLHR_EINVAL;
+  }
+  std::vector<const gplhr_ctx*> seen;
+  for (int i = 0; i < nctx; ++i) {
+    const gplhr_ctx* c = ctxs[i];
+    const char* why = nullptr;
+    if (!c) why = "null context";
+    else if (std::find(seen.begin(), seen.end(), c) != seen.end()) why = "a context appears twice";
+    else if (need_started && !c->started) why = "context not started (gplhr_start)";
+    else if (c->eig) why = "GPLHR-EIG contexts are not supported";
+    else if (c->gm_steps > 0) why = "inner GMRES preconditioning is not supported (its least squares runs on the host)";
+    else if (c->prof_on) why = "profiling is on";
+    if (why) {
+      g_create_error = "persistent batch: context " + std::to_string(i) + ": " + why;
+      return GPLHR_EINVAL;
+    }
+    seen.push_back(c);
+  }
+  return GPLHR_OK;
+}
+
+static gplhr_status pk_finish(int32_t nctx, gplhr_ctx* const* ctxs, const std::vector<gplhr_status>& st,
+                              const std::vector<char>& conv, bool need_conv, gplhr_info* infos,
+                              gplhr_status* statuses, const PkRunner& R, gplhr_persist_stats* stats) {
+  gplhr_status first = GPLHR_OK;
+  for (int i = 0; i < nctx; ++i) {
+    gplhr_status si = st[i];
+    if (si == GPLHR_OK && need_conv && !conv[i]) {
+      ctxs[i]->err = "maxit reached before all pairs met tol";
+      si = GPLHR_ENOTCONV;
+    }
+    fill_info(ctxs[i], infos ? infos + i : nullptr);
+    if (statuses) statuses[i] = si;
+    if (first == GPLHR_OK && si != GPLHR_OK) first = si;
+  }
+  if (stats) {
+    stats->launches = R.launches;
+    stats->steps = R.steps;
+    stats->ops = R.ops;
+    stats->grid = R.grid;
+    stats->record_ms = R.record_ms;
+    stats->build_ms = R.build_ms;
+    stats->qz_ms = R.qz_ms;
+    stats->wait_ms = R.wait_ms;
+  }
+  if (!R.err.empty()) g_create_error = R.err;
+  return first;
+}
+
+gplhr_status gplhr_iterate_persistent(int32_t nctx, gplhr_ctx* const* ctxs, int32_t niter, gplhr_info* infos,
+                                      gplhr_status* statuses, int32_t nthreads, gplhr_persist_stats* stats) {
+  TRY(pk_check(nctx, ctxs, true));
+  if (niter < 0) {
+    g_create_error = "persistent batch: niter < 0";
+    return GPLHR_EINVAL;
+  }
+  std::vector<int> cap(nctx);
+  for (int i = 0; i < nctx; ++i) cap[i] = ctxs[i]->it + niter;
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  PkRunner R;
+  std::vector<gplhr_status> st;
+  std::vector<char> conv;
+  pk_iterate(nctx, ctxs, cap, nthreads > 0 ? nthreads : hw, st, conv, R);
+  return pk_finish(nctx, ctxs, st, conv, false, infos, statuses, R, stats);
+}
+
+gplhr_status gplhr_solve_persistent(int32_t nctx, gplhr_ctx* const* ctxs, const void* const* V0,
+                                    const int32_t* V0_where, const int32_t* is_complex, const uint64_t* seeds,
+                                    gplhr_info* infos, gplhr_status* statuses, int32_t nthreads,
+                                    gplhr_persist_stats* stats) {
+  TRY(pk_check(nctx, ctxs, false));
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nt = nthreads > 0 ? nthreads : hw;
+  // steps 1-4 of every context on its own stream (host threads), then the iterations
+  std::vector<gplhr_status> st0(nctx, GPLHR_OK);
+  run_batched(nctx, ctxs, nt, st0.data(), [&](int i) {
+    return gplhr_start(ctxs[i], V0 ? V0[i] : nullptr, V0_where ? V0_where[i] : GPLHR_HOST,
+                       is_complex ? is_complex[i] : 0, seeds ? seeds[i] : 0);
+  });
+  std::vector<gplhr_ctx*> ok;
+  std::vector<int> where;
+  for (int i = 0; i < nctx; ++i)
+    if (st0[i] == GPLHR_OK) {
+      ok.push_back(ctxs[i]);
+      where.push_back(i);
+    }
+  std::vector<int> cap(ok.size());
+  for (size_t j = 0; j < ok.size(); ++j) cap[j] = ok[j]->maxit;
+  PkRunner R;
+  std::vector<gplhr_status> st1;
+  std::vector<char> conv1;
+  pk_iterate((int)ok.size(), ok.data(), cap, nt, st1, conv1, R);
+  std::vector<gplhr_status> st(nctx);
+  std::vector<char> conv(nctx, 0);
+  for (int i = 0; i < nctx; ++i) st[i] = st0[i];
+  for (size_t j = 0; j < ok.size(); ++j) {
+    st[where[j]] = st1[j];
+    conv[where[j]] = conv1[j];
+  }
+  return pk_finish(nctx, ctxs, st, conv, true, infos, statuses, R, stats);
 }
 
 gplhr_status gplhr_ordqz(int32_t s, const double* Phi, const double* Psi, double sigma_re, double sigma_im,

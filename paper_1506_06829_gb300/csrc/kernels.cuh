@@ -9,6 +9,16 @@
 
 namespace gplhr {
 
+// Block index of a kernel body: the hardware one, or a virtual one when the persistent
+// kernel of the batched iteration runs the body for a recorded launch (block (x, y) of a
+// gx x gy grid).  Every body here runs with 256 threads per CTA.
+struct Cta {
+  int x, y, gx, gy;
+  static __device__ __forceinline__ Cta hw() {
+    return Cta{(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x, (int)gridDim.y};
+  }
+};
+
 // ----------------------------------------------------------------- complex ----
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
@@ -150,23 +160,28 @@ template <> __device__ __forceinline__ float zero_val<float>() { return 0.0f; }
 template <> __device__ __forceinline__ float2 zero_val<float2>() { return make_float2(0.0f, 0.0f); }
 
 // V consecutive complex values of the block row at p (V = 2: one 16-byte load).
-template <typename T, int V>
-__device__ __forceinline__ void load_xv(const cplx<T>* __restrict__ p, cplx<T> (&x)[V]);
-template <> __device__ __forceinline__ void load_xv<double, 1>(const double2* __restrict__ p, double2 (&x)[1]) {
-  x[0] = __ldg(p);
-}
-template <> __device__ __forceinline__ void load_xv<float, 2>(const float2* __restrict__ p, float2 (&x)[2]) {
-  const float4 q = __ldg(reinterpret_cast<const float4*>(p));
-  x[0] = make_float2(q.x, q.y);
-  x[1] = make_float2(q.z, q.w);
+// NC: through the read-only (non-coherent) data path.  Only a kernel that never writes
+// the block during its lifetime may use it; the persistent kernel of the batched
+// iteration, which writes blocks in one step and reads them in a later one, does not.
+template <typename T, int V, bool NC>
+__device__ __forceinline__ void load_xv(const cplx<T>* p, cplx<T> (&x)[V]) {
+  if constexpr (V == 1) {
+    x[0] = NC ? __ldg(p) : *p;
+  } else {
+    static_assert(V == 2 && sizeof(cplx<T>) == 8, "V = 2 loads two complex64 values");
+    const float4* q4 = reinterpret_cast<const float4*>(p);
+    const float4 q = NC ? __ldg(q4) : *q4;
+    x[0] = make_float2(q.x, q.y);
+    x[1] = make_float2(q.z, q.w);
+  }
 }
 
 constexpr int SPMM_THREADS = 256;
 constexpr int SPMM_BATCH = 8;
 
-template <typename VT, typename T, int G, int V>
-__device__ __forceinline__ void spmm_group_row(const CsrDev<VT>& M, int r, int n, const cplx<T>* __restrict__ X,
-                                               int ldx, int w, int c, int lane, double2* __restrict__ Y, int ldy) {
+template <typename VT, typename T, int G, int V, bool NC>
+__device__ __forceinline__ void spmm_group_row(const CsrDev<VT>& M, int r, int n, const cplx<T>* X,
+                                               int ldx, int w, int c, int lane, double2* Y, int ldy) {
   constexpr int PER = 32 / G;  // (column, value) pairs each lane loads per round
   const bool active = r < n;
   const int j0 = active ? M.rowptr[r] : 0;
@@ -203,7 +218,7 @@ __device__ __forceinline__ void spmm_group_row(const CsrDev<VT>& M, int r, int n
 #pragma unroll
       for (int u = 0; u < SPMM_BATCH; ++u) {
         if (tb + u < cnt && colok) {
-          load_xv<T, V>(X + (size_t)cc[u] * ldx + c0, xv[u]);
+          load_xv<T, V, NC>(X + (size_t)cc[u] * ldx + c0, xv[u]);
         } else {
 #pragma unroll
           for (int v = 0; v < V; ++v) xv[u][v] = czero<T>();
@@ -225,20 +240,27 @@ __device__ __forceinline__ void spmm_group_row(const CsrDev<VT>& M, int r, int n
 // T is the arithmetic (double, or float in the FP32 bulk phase; X is then the
 // complex64 copy of the block); the outputs are complex128.  Requires w <= G V; with
 // V = 2 the rows of X must be 16-byte aligned (ldx even).
+template <typename VTA, typename VTB, typename T, int G, int V, bool NC = true>
+__device__ __forceinline__ void spmm_body(const Cta& cta, int n, CsrDev<VTA> A, CsrDev<VTB> B, int hasB,
+                                                            const cplx<T>* X, int ldx, int w,
+                                                            double2* AX, int ldax,
+                                                            double2* BX, int ldbx) {
+  constexpr int RPW = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / G, c = lane - g * G;
+  const int warp = (cta.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (cta.gx * blockDim.x) >> 5;
+  for (int rb = warp * RPW; rb < n; rb += nwarps * RPW) {
+    spmm_group_row<VTA, T, G, V, NC>(A, rb + g, n, X, ldx, w, c, lane, AX, ldax);
+    if (hasB) spmm_group_row<VTB, T, G, V, NC>(B, rb + g, n, X, ldx, w, c, lane, BX, ldbx);
+  }
+}
 template <typename VTA, typename VTB, typename T, int G, int V>
 __global__ void __launch_bounds__(SPMM_THREADS) spmm_kernel(int n, CsrDev<VTA> A, CsrDev<VTB> B, int hasB,
                                                             const cplx<T>* __restrict__ X, int ldx, int w,
                                                             double2* __restrict__ AX, int ldax,
                                                             double2* __restrict__ BX, int ldbx) {
-  constexpr int RPW = 32 / G;
-  const int lane = threadIdx.x & 31;
-  const int g = lane / G, c = lane - g * G;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int rb = warp * RPW; rb < n; rb += nwarps * RPW) {
-    spmm_group_row<VTA, T, G, V>(A, rb + g, n, X, ldx, w, c, lane, AX, ldax);
-    if (hasB) spmm_group_row<VTB, T, G, V>(B, rb + g, n, X, ldx, w, c, lane, BX, ldbx);
-  }
+  spmm_body<VTA, VTB, T, G, V>(Cta::hw(), n, A, B, hasB, X, ldx, w, AX, ldax, BX, ldbx);
 }
 
 // ------------------------------------------------------------------- Gram -----
@@ -273,10 +295,10 @@ __device__ __forceinline__ void gram_index(int o, int wx, int wy, int herm, int&
 }
 
 template <int ACC, typename T = double>
-__global__ void __launch_bounds__(GRAM_THREADS)
-gram_partial_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, int ldx, int wx,
-                    const double2* __restrict__ Y0, int ldy0, int wy0, const double2* __restrict__ Y1,
-                    int ldy1, int wy1, int herm, int nout, int G, int RG, double2* __restrict__ partial,
+__device__ __forceinline__ void gram_partial_body(const Cta& cta,
+    int n, int rows_per_chunk, const double2* X, int ldx, int wx,
+                    const double2* Y0, int ldy0, int wy0, const double2* Y1,
+                    int ldy1, int wy1, int herm, int nout, int G, int RG, double2* partial,
                     const int* skip) {
   if (skip && *skip == 0) return;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -287,10 +309,10 @@ gram_partial_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, in
   C2* ys = sm + GRAM_ROWS * wx;        // GRAM_ROWS x wy
   const int tid = threadIdx.x;
   const int g = tid % G, rg = tid / G;
-  const int tile0 = blockIdx.y * G * ACC;
+  const int tile0 = cta.y * G * ACC;
   const int o0 = tile0 + g * ACC;
   const bool active = rg < RG && o0 < nout;
-  const int r0 = blockIdx.x * rows_per_chunk;
+  const int r0 = cta.x * rows_per_chunk;
   const int r1 = min(n, r0 + rows_per_chunk);
   C2 acc[ACC];
   int oi[ACC], oj[ACC];
@@ -331,7 +353,7 @@ gram_partial_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, in
     for (int t = 0; t < ACC; ++t) red[rg * per + g * ACC + t] = acc[t];
   }
   __syncthreads();
-  double2* out = partial + (size_t)blockIdx.x * nout;
+  double2* out = partial + (size_t)cta.x * nout;
   for (int e = tid; e < per; e += blockDim.x) {
     const int o = tile0 + e;
     if (o >= nout) break;
@@ -339,6 +361,15 @@ gram_partial_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, in
     for (int q = 1; q < RG; ++q) s = cadd(s, to_d(red[q * per + e]));
     out[o] = s;
   }
+}
+template <int ACC, typename T = double>
+__global__ void __launch_bounds__(GRAM_THREADS)
+gram_partial_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, int ldx, int wx,
+                    const double2* __restrict__ Y0, int ldy0, int wy0, const double2* __restrict__ Y1,
+                    int ldy1, int wy1, int herm, int nout, int G, int RG, double2* __restrict__ partial,
+                    const int* skip) {
+  gram_partial_body<ACC, T>(Cta::hw(), n, rows_per_chunk, X, ldx, wx, Y0, ldy0, wy0, Y1, ldy1, wy1, herm,
+      nout, G, RG, partial, skip);
 }
 
 // Gram of FP32-valued blocks with exact products (bulk phase of the mixed mode, whose
@@ -369,10 +400,10 @@ constexpr int X32_ROWS = 32;
 constexpr int X32_FLUSH = 32;
 
 template <int ACC>
-__global__ void __launch_bounds__(GRAM_THREADS)
-gram_partial_x32_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, int ldx, int wx,
-                        const double2* __restrict__ Y0, int ldy0, int wy0, const double2* __restrict__ Y1,
-                        int ldy1, int wy1, int herm, int nout, int G, int RG, double2* __restrict__ partial,
+__device__ __forceinline__ void gram_partial_x32_body(const Cta& cta,
+    int n, int rows_per_chunk, const double2* X, int ldx, int wx,
+                        const double2* Y0, int ldy0, int wy0, const double2* Y1,
+                        int ldy1, int wy1, int herm, int nout, int G, int RG, double2* partial,
                         const int* skip) {
   if (skip && *skip == 0) return;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -381,10 +412,10 @@ gram_partial_x32_kernel(int n, int rows_per_chunk, const double2* __restrict__ X
   float2* ys = xs + X32_ROWS * wx;                 // X32_ROWS x wy
   const int tid = threadIdx.x;
   const int g = tid % G, rg = tid / G;
-  const int tile0 = blockIdx.y * G * ACC;
+  const int tile0 = cta.y * G * ACC;
   const int o0 = tile0 + g * ACC;
   const bool active = rg < RG && o0 < nout;
-  const int r0 = blockIdx.x * rows_per_chunk;
+  const int r0 = cta.x * rows_per_chunk;
   const int r1 = min(n, r0 + rows_per_chunk);
   double2 acc[ACC];
   int oi[ACC], oj[ACC];
@@ -445,7 +476,7 @@ gram_partial_x32_kernel(int n, int rows_per_chunk, const double2* __restrict__ X
     for (int t = 0; t < ACC; ++t) red[rg * per + g * ACC + t] = acc[t];
   }
   __syncthreads();
-  double2* out = partial + (size_t)blockIdx.x * nout;
+  double2* out = partial + (size_t)cta.x * nout;
   for (int e = tid; e < per; e += blockDim.x) {
     const int o = tile0 + e;
     if (o >= nout) break;
@@ -453,6 +484,15 @@ gram_partial_x32_kernel(int n, int rows_per_chunk, const double2* __restrict__ X
     for (int q = 1; q < RG; ++q) sum = cadd(sum, red[q * per + e]);
     out[o] = sum;
   }
+}
+template <int ACC>
+__global__ void __launch_bounds__(GRAM_THREADS)
+gram_partial_x32_kernel(int n, int rows_per_chunk, const double2* __restrict__ X, int ldx, int wx,
+                        const double2* __restrict__ Y0, int ldy0, int wy0, const double2* __restrict__ Y1,
+                        int ldy1, int wy1, int herm, int nout, int G, int RG, double2* __restrict__ partial,
+                        const int* skip) {
+  gram_partial_x32_body<ACC>(Cta::hw(), n, rows_per_chunk, X, ldx, wx, Y0, ldy0, wy0, Y1, ldy1, wy1, herm,
+      nout, G, RG, partial, skip);
 }
 
 // C = sum_b partial[b] (deterministic): one warp per output, lane l adds the chunks
@@ -462,12 +502,12 @@ gram_partial_x32_kernel(int n, int rows_per_chunk, const double2* __restrict__ X
 constexpr int GRED_WARPS = 8;
 // C row stride ldc (>= the row length: wy, or wx for the transposed form), so that a
 // product can fill a column block of a wider C.
-__global__ void gram_reduce_kernel(int nchunk, int nout, int wx, int wy, int herm,
-                                   const double2* __restrict__ partial, double2* __restrict__ C, int ldc,
+__device__ __forceinline__ void gram_reduce_body(const Cta& cta, int nchunk, int nout, int wx, int wy, int herm,
+                                   const double2* partial, double2* C, int ldc,
                                    const int* skip) {
   if (skip && *skip == 0) return;
   const int lane = threadIdx.x & 31;
-  const int o = blockIdx.x * GRED_WARPS + (threadIdx.x >> 5);
+  const int o = cta.x * GRED_WARPS + (threadIdx.x >> 5);
   if (o >= nout) return;
   double2 s = make_double2(0.0, 0.0);
   for (int b = lane; b < nchunk; b += 32) s = cadd(s, partial[(size_t)b * nout + o]);
@@ -483,6 +523,11 @@ __global__ void gram_reduce_kernel(int nchunk, int nout, int wx, int wy, int her
     C[(size_t)i * ldc + j] = s;
     if (herm && i != j) C[(size_t)j * ldc + i] = make_double2(s.x, -s.y);
   }
+}
+__global__ void gram_reduce_kernel(int nchunk, int nout, int wx, int wy, int herm,
+                                   const double2* __restrict__ partial, double2* __restrict__ C, int ldc,
+                                   const int* skip) {
+  gram_reduce_body(Cta::hw(), nchunk, nout, wx, wy, herm, partial, C, ldc, skip);
 }
 
 // ---------------------------------------------------------------- combine -----
@@ -535,7 +580,7 @@ __device__ __forceinline__ double2* comb_out(const CombArgs& a, int r, int cc) {
 }
 
 template <typename T = double>
-__global__ void combine_kernel(int n, int rows_per_cta, CombArgs a) {
+__device__ __forceinline__ void combine_body(const Cta& cta, int n, int rows_per_cta, CombArgs a) {
   if (a.skip && *a.skip == 0) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   using C2 = cplx<T>;
@@ -560,7 +605,7 @@ __global__ void combine_kernel(int n, int rows_per_cta, CombArgs a) {
   }
   const int nnorm = a.c - a.c_store;
   for (int e = threadIdx.x; e < nnorm; e += blockDim.x) nsum[e] = 0.0;
-  const int r0 = blockIdx.x * rows_per_cta;
+  const int r0 = cta.x * rows_per_cta;
   const int r1 = min(n, r0 + rows_per_cta);
   for (int rb = r0; rb < r1; rb += rows_tile) {
     const int nr = min(rows_tile, r1 - rb);
@@ -607,58 +652,82 @@ __global__ void combine_kernel(int n, int rows_per_cta, CombArgs a) {
   if (a.normpart) {
     __syncthreads();
     for (int e = threadIdx.x; e < nnorm; e += blockDim.x)
-      a.normpart[(size_t)blockIdx.x * nnorm + e] = nsum[e];
+      a.normpart[(size_t)cta.x * nnorm + e] = nsum[e];
   }
+}
+template <typename T = double>
+__global__ void combine_kernel(int n, int rows_per_cta, CombArgs a) {
+  combine_body<T>(Cta::hw(), n, rows_per_cta, a);
 }
 
 // normout[j] = sum_b normpart[b][j]  (fixed order)
 // one warp per column, lane-strided then a fixed shuffle tree (deterministic)
-__global__ void norm_reduce_kernel(int nb, int nc, const double* __restrict__ part,
-                                   double* __restrict__ out) {
+__device__ __forceinline__ void norm_reduce_body(const Cta& cta, int nb, int nc, const double* part,
+                                   double* out) {
   const int lane = threadIdx.x & 31;
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int j = cta.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (j >= nc) return;
   double s = 0.0;
   for (int b = lane; b < nb; b += 32) s += part[(size_t)b * nc + j];
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if (lane == 0) out[j] = s;
 }
+__global__ void norm_reduce_kernel(int nb, int nc, const double* __restrict__ part,
+                                   double* __restrict__ out) {
+  norm_reduce_body(Cta::hw(), nb, nc, part, out);
+}
 
 // Y = alpha X1 + beta X2 (elementwise, n x w)
-__global__ void axpby_kernel(int n, int w, double2 alpha, const double2* __restrict__ X1, int ld1,
-                             double2 beta, const double2* __restrict__ X2, int ld2,
-                             double2* __restrict__ Y, int ldy) {
+__device__ __forceinline__ void axpby_body(const Cta& cta,
+    int n, int w, double2 alpha, const double2* X1, int ld1,
+                             double2 beta, const double2* X2, int ld2,
+                             double2* Y, int ldy) {
   const size_t total = (size_t)n * w;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
+  for (size_t e = cta.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)cta.gx * blockDim.x) {
     const int r = (int)(e / w), c = (int)(e - (size_t)r * w);
     double2 v = cmul(alpha, X1[(size_t)r * ld1 + c]);
     v = cfma(beta, X2[(size_t)r * ld2 + c], v);
     Y[(size_t)r * ldy + c] = v;
   }
 }
+__global__ void axpby_kernel(int n, int w, double2 alpha, const double2* __restrict__ X1, int ld1,
+                             double2 beta, const double2* __restrict__ X2, int ld2,
+                             double2* __restrict__ Y, int ldy) {
+  axpby_body(Cta::hw(), n, w, alpha, X1, ld1, beta, X2, ld2, Y, ldy);
+}
 
 // Copy an n x w block (any lds)
-__global__ void copy_block_kernel(int n, int w, const double2* __restrict__ X, int ldx,
-                                  double2* __restrict__ Y, int ldy) {
+__device__ __forceinline__ void copy_block_body(const Cta& cta,
+    int n, int w, const double2* X, int ldx,
+                                  double2* Y, int ldy) {
   const size_t total = (size_t)n * w;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
+  for (size_t e = cta.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)cta.gx * blockDim.x) {
     const int r = (int)(e / w), c = (int)(e - (size_t)r * w);
     Y[(size_t)r * ldy + c] = X[(size_t)r * ldx + c];
   }
 }
+__global__ void copy_block_kernel(int n, int w, const double2* __restrict__ X, int ldx,
+                                  double2* __restrict__ Y, int ldy) {
+  copy_block_body(Cta::hw(), n, w, X, ldx, Y, ldy);
+}
 
 // complex128 block -> complex64 block (ld = w), for the FP32 sparse products.
-__global__ void to_c64_kernel(int n, int w, const double2* __restrict__ X, int ldx, float2* __restrict__ Y,
+__device__ __forceinline__ void to_c64_body(const Cta& cta,
+    int n, int w, const double2* X, int ldx, float2* Y,
                               int ldy) {
   const size_t total = (size_t)n * w;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
+  for (size_t e = cta.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)cta.gx * blockDim.x) {
     const int r = (int)(e / w), c = (int)(e - (size_t)r * w);
     const double2 v = X[(size_t)r * ldx + c];
     Y[(size_t)r * ldy + c] = make_float2((float)v.x, (float)v.y);
   }
+}
+__global__ void to_c64_kernel(int n, int w, const double2* __restrict__ X, int ldx, float2* __restrict__ Y,
+                              int ldy) {
+  to_c64_body(Cta::hw(), n, w, X, ldx, Y, ldy);
 }
 
 // Real n x w (row-major, ld = w) to complex block.
@@ -675,14 +744,20 @@ __global__ void real_to_complex_kernel(int n, int w, const double* __restrict__ 
 // --------------------------------------------------------- preconditioners ----
 // Jacobi: Y[r][c] = d[r] X[r][c]
 template <typename T = double>
-__global__ void jacobi_kernel(int n, int w, const double2* __restrict__ d, const double2* __restrict__ X,
-                              int ldx, double2* __restrict__ Y, int ldy) {
+__device__ __forceinline__ void jacobi_body(const Cta& cta,
+    int n, int w, const double2* d, const double2* X,
+                              int ldx, double2* Y, int ldy) {
   const size_t total = (size_t)n * w;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
+  for (size_t e = cta.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)cta.gx * blockDim.x) {
     const int r = (int)(e / w), c = (int)(e - (size_t)r * w);
     Y[(size_t)r * ldy + c] = to_d(cmul(to_t<T>(d[r]), to_t<T>(X[(size_t)r * ldx + c])));
   }
+}
+template <typename T = double>
+__global__ void jacobi_kernel(int n, int w, const double2* __restrict__ d, const double2* __restrict__ X,
+                              int ldx, double2* __restrict__ Y, int ldy) {
+  jacobi_body<T>(Cta::hw(), n, w, d, X, ldx, Y, ldy);
 }
 
 // Block-Jacobi: for block b (rows [b bs, b bs + nb_b)), Y_b = Tinv_b X_b with Tinv_b
@@ -691,14 +766,15 @@ __global__ void jacobi_kernel(int n, int w, const double2* __restrict__ d, const
 // so Y may equal X.
 constexpr int BJ_THREADS = 256;
 template <typename T = double, typename TT = double2>
-__global__ void block_jacobi_kernel(int n, int bs, int w, const TT* __restrict__ Tinv,
-                                    const double2* __restrict__ X, int ldx,
-                                    double2* __restrict__ Y, int ldy, int blocks_per_cta) {
+__device__ __forceinline__ void block_jacobi_body(const Cta& cta,
+    int n, int bs, int w, const TT* Tinv,
+                                    const double2* X, int ldx,
+                                    double2* Y, int ldy, int blocks_per_cta) {
   extern __shared__ __align__(16) unsigned char smraw[];
   using C2 = cplx<T>;
   C2* xs = reinterpret_cast<C2*>(smraw);  // blocks_per_cta * bs rows x w
   const int nblocks = (n + bs - 1) / bs;
-  const int b0 = blockIdx.x * blocks_per_cta;
+  const int b0 = cta.x * blocks_per_cta;
   const int b1 = min(nblocks, b0 + blocks_per_cta);
   if (b0 >= b1) return;
   const int rstart = b0 * bs;
@@ -720,6 +796,12 @@ __global__ void block_jacobi_kernel(int n, int bs, int w, const TT* __restrict__
     for (int j = 0; j < rows_in_blk; ++j) acc = cfma(to_t<T>(Tm[j]), xb[j * w + cc], acc);
     Y[(size_t)(rstart + rr) * ldy + cc] = to_d(acc);
   }
+}
+template <typename T = double, typename TT = double2>
+__global__ void block_jacobi_kernel(int n, int bs, int w, const TT* __restrict__ Tinv,
+                                    const double2* __restrict__ X, int ldx,
+                                    double2* __restrict__ Y, int ldy, int blocks_per_cta) {
+  block_jacobi_body<T, TT>(Cta::hw(), n, bs, w, Tinv, X, ldx, Y, ldy, blocks_per_cta);
 }
 
 // Setup: extract the diagonal blocks of K = A - sigma B (B = I if hasB = 0) into
@@ -871,9 +953,9 @@ __device__ __forceinline__ double rsqrt_newton(double a) {
   return __longlong_as_double(__double_as_longlong(y) - ((long long)h << 52));  // y 2^(-h)
 }
 
-__global__ void chol_inv_kernel(int w, int64_t n, const double2* __restrict__ G,
-                                double2* __restrict__ Rinv, int* status, const int* skip_if_zero,
-                                int* fallback_counter, double2* __restrict__ Rout) {
+__device__ __forceinline__ void chol_inv_body(const Cta& cta, int w, int64_t n, const double2* G,
+                                double2* Rinv, int* status, const int* skip_if_zero,
+                                int* fallback_counter, double2* Rout) {
   extern __shared__ double2 sm[];
   double2* a = sm;              // w x w working copy -> R (upper)
   double2* inv = sm + w * w;    // w x w -> R^{-1}
@@ -989,6 +1071,11 @@ __global__ void chol_inv_kernel(int w, int64_t n, const double2* __restrict__ G,
     Rinv[e] = (j >= i) ? inv[e] : make_double2(0.0, 0.0);
     if (Rout) Rout[e] = (j >= i) ? a[e] : make_double2(0.0, 0.0);
   }
+}
+__global__ void chol_inv_kernel(int w, int64_t n, const double2* __restrict__ G,
+                                double2* __restrict__ Rinv, int* status, const int* skip_if_zero,
+                                int* fallback_counter, double2* __restrict__ Rout) {
+  chol_inv_body(Cta::hw(), w, n, G, Rinv, status, skip_if_zero, fallback_counter, Rout);
 }
 
 // ------------------------------------------------------------------ adjoint ----

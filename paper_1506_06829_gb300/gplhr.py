@@ -30,7 +30,8 @@ EXPORTED = ["gplhr_create", "gplhr_solve", "gplhr_start", "gplhr_iterate", "gplh
             "gplhr_gram", "gplhr_combine", "gplhr_orth", "gplhr_ordqz", "gplhr_ordqz_device", "gplhr_mfactors",
             "gplhr_profile",
             "gplhr_profile_read", "gplhr_gram_noalloc", "gplhr_grad", "gplhr_solve_batched",
-            "gplhr_iterate_batched", "gplhr_spmm_shape", "gplhr_set_deflation", "gplhr_create_batched"]
+            "gplhr_iterate_batched", "gplhr_spmm_shape", "gplhr_set_deflation", "gplhr_create_batched",
+            "gplhr_iterate_persistent", "gplhr_solve_persistent"]
 P_MODES = {"thick": 0, "lobpcg": 1, "none": 2}
 KCLASS = {"spmm": 0, "gram": 1, "combine": 2, "precond": 3, "chol": 4, "other": 5, "gram_tc": 6,
           "combine_tc": 7}
@@ -62,6 +63,12 @@ class Info(C.Structure):
                 ("n_spmm", C.c_int64), ("n_prec", C.c_int64),
                 ("n_qz", C.c_int64), ("n_launch", C.c_int64), ("h2d_bytes", C.c_int64),
                 ("d2h_bytes", C.c_int64), ("resid", C.c_double * 64), ("n_inner", C.c_int64)]
+
+
+class PersistStats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("steps", C.c_int64), ("ops", C.c_int64), ("grid", C.c_int32),
+                ("pad", C.c_int32), ("record_ms", C.c_double), ("build_ms", C.c_double),
+                ("qz_ms", C.c_double), ("wait_ms", C.c_double)]
 
 
 class GplhrError(RuntimeError):
@@ -112,6 +119,11 @@ def lib():
                                       C.POINTER(C.c_int), i32]
     L.gplhr_iterate_batched.argtypes = [i32, C.POINTER(vp), i32, C.POINTER(Info),
                                         C.POINTER(C.c_int), i32]
+    L.gplhr_iterate_persistent.argtypes = [i32, C.POINTER(vp), i32, C.POINTER(Info), C.POINTER(C.c_int), i32,
+                                           C.POINTER(PersistStats)]
+    L.gplhr_solve_persistent.argtypes = [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(i32), C.POINTER(i32),
+                                         C.POINTER(u64), C.POINTER(Info), C.POINTER(C.c_int), i32,
+                                         C.POINTER(PersistStats)]
     L.gplhr_create_batched.argtypes = [i32, C.POINTER(C.POINTER(Csr)), C.POINTER(C.POINTER(Csr)),
                                        C.POINTER(C.c_double), C.POINTER(i32), C.POINTER(i32),
                                        C.POINTER(C.POINTER(Precond)), C.POINTER(C.POINTER(Opts)),
@@ -439,6 +451,46 @@ def gplhr_iterate_batched(ctxs, niter: int, nthreads: int = 0):
     sts = (C.c_int * n)()
     st = lib().gplhr_iterate_batched(n, cs, niter, infos, sts, nthreads)
     return st, list(infos), list(sts)
+
+
+def gplhr_solve_persistent(ctxs, V0s=None, nthreads: int = 0):
+    """Solve every context with the persistent batched iteration (each device segment of
+    an iteration run for all contexts in one persistent-kernel launch).  V0s: list of host
+    arrays (or None).  Returns (overall status, [Info], [status], PersistStats)."""
+    n = len(ctxs)
+    cs = (C.c_void_p * n)(*ctxs)
+    keep = []
+    if V0s is not None:
+        ptrs, where, cplx = [], [], []
+        for v in V0s:
+            p, w, c, k = _v0_args(v)
+            keep.append(k)
+            ptrs.append(p)
+            where.append(w)
+            cplx.append(c)
+        vp_arr = (C.c_void_p * n)(*ptrs)
+        w_arr = (C.c_int32 * n)(*where)
+        c_arr = (C.c_int32 * n)(*cplx)
+    else:
+        vp_arr = w_arr = c_arr = None
+    infos = (Info * n)()
+    sts = (C.c_int * n)()
+    stats = PersistStats()
+    st = lib().gplhr_solve_persistent(n, cs, vp_arr, w_arr, c_arr, None, infos, sts, nthreads, C.byref(stats))
+    del keep
+    return st, list(infos), list(sts), stats
+
+
+def gplhr_iterate_persistent(ctxs, niter: int, nthreads: int = 0):
+    """niter iterations of each started context through the persistent batched iteration.
+    Returns (overall status, [Info], [status], PersistStats)."""
+    n = len(ctxs)
+    cs = (C.c_void_p * n)(*ctxs)
+    infos = (Info * n)()
+    sts = (C.c_int * n)()
+    stats = PersistStats()
+    st = lib().gplhr_iterate_persistent(n, cs, niter, infos, sts, nthreads, C.byref(stats))
+    return st, list(infos), list(sts), stats
 
 
 def gplhr_orth(ctx, X, Rinv=None):
