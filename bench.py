@@ -43,10 +43,11 @@ FP64_PEAK_GFLOPS = 1250.0   # GB300 dense FP64 (profiling recipe table); probe m
 # DRAM bytes per launch of this workload in FP64 (mean over one iteration's launches of the
 # kernel class), from one-pass ncu captures of the same kernels: stored values, not measured
 # by this run; the JSON line says so in "traffic_source"
-TRAFFIC_SOURCE = "stored ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), not this run"
+TRAFFIC_SOURCE = ("stored ncu capture of the current kernels (dram__bytes_read.sum + dram__bytes_write.sum, "
+                  "mean over one iteration's launches of the class), not this run")
 TRAFFIC_64CUBED = {
     "gram_tc": 62.3e6,     # tc_gram_narrow_kernel / tc_gram_wide_kernel, 27 launches
-    "combine_tc": 68.3e6,  # tc_combine_kernel, 31 launches
+    "combine_tc": 71.2e6,  # tc_combine_kernel, 31 launches
 }
 KCLASSES = ["spmm", "gram", "combine", "precond", "chol", "other", "gram_tc", "combine_tc"]
 TENSOR_CLASSES = ("gram_tc", "combine_tc")   # FP64 by integer digits on the tensor cores
