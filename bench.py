@@ -296,6 +296,7 @@ def main():
         line["e2e"] = e2e(pr, K, stream, G)
     if rank == 0 and not args.no_batched:
         line["batched"] = batched_throughput(G, K)
+        line["batched_solve"] = batched_solve(G)
         line["small"] = small_pencil_iterations(G, K)
     if rank == 0 and not args.no_solve:
         line["solve"] = time_to_pairs(G, stream, "fp64")
@@ -472,7 +473,7 @@ def batched_throughput(G, K):
             st4 = r[3]
             out.update({"launches_per_batch_iteration": st4.launches / K,
                         "recorded_launches_per_batch_iteration": st4.ops / K,
-                        "grid_barriers_per_batch_iteration": (st4.steps - st4.launches) / K,
+                        "longest_context_launches_per_batch_iteration": st4.steps / K,
                         "grid": int(st4.grid),
                         "host_ms_per_batch_iteration": {"record": st4.record_ms / K, "build_and_issue": st4.build_ms / K,
                                                         "qz": st4.qz_ms / K, "device_wait": st4.wait_ms / K},
@@ -487,7 +488,8 @@ def batched_throughput(G, K):
     persistent = {"fp64": run_persistent("fp64", False), "mixed": run_persistent("mixed", False),
                   "mixed_thread_pool_graphs": run_persistent("mixed", True),
                   "kernels": "DFMA / FFMA kernels (no tensor-core pipelines) run as virtual CTAs of one "
-                             "cooperative persistent kernel per device segment"}
+                             "cooperative persistent kernel per device segment, each context's launches "
+                             "in order, the contexts independently"}
     return {"workload": f"{len(ps)} contexts: 64 convection-diffusion pencils (grid sides 16..96, B = MxM, k = 4) "
                         "+ 16 shifts over a 128^2 pencil (k = 8), Jacobi, FP64",
             "pencil_iterations_per_s": units / gb, "sequential_pencil_iterations_per_s": units / gs,
@@ -498,6 +500,47 @@ def batched_throughput(G, K):
                       "autotuned per pencil",
             "persistent": persistent,
             "threads": os.cpu_count(), "iterations": K, "status": gst}
+
+
+def batched_solve(G):
+    """Seconds until every context of a converging batch has its k pairs: complex-scaled
+    Schroedinger pencils of uneven size (grid sides 16, 20, ..., 64; k = 16, m = 2,
+    block-Jacobi 16, tol 1e-8) and two more shifts over the 64^2 pencil (spectrum slicing).
+    One context at a time, all at once on a host thread pool with CUDA graphs, and the
+    persistent batched iteration, in FP64 and mixed precision.  Contexts are created
+    before the clock starts; each run includes steps 1-4 and every iteration."""
+    import torch
+    from paper_1506_06829_gb300 import problems as P
+    specs = [(P.config3(N), P.config3(N).sigma) for N in range(16, 65, 4)]
+    big = P.config3(64)
+    specs += [(big, sg) for sg in (10.0 - 5.0j, 25.0 - 12.0j)]   # two more slices that converge within 400
+
+    def run(mode, precision):
+        ss = [G.GPLHR(pr.A, None, sg, pr.k, pr.m, pr.precond, pr.block_size, tol=pr.tol, maxit=400,
+                      precision=precision, graphs=(mode == "pool")) for pr, sg in specs]
+        V0s = [pr.start_block() for pr, _ in specs]
+        ctxs = [s.ctx for s in ss]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if mode == "persistent":
+            st, infos, sts, _ = G.gplhr_solve_persistent(ctxs, V0s)
+        else:
+            st, infos, sts = G.gplhr_solve_batched(ctxs, V0s, nthreads=1 if mode == "sequential" else 0)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        out = {"s_to_all_pairs": t, "converged": int(sum(1 for x in sts if x == G.GPLHR_OK)),
+               "iterations_max": int(max(i.iters for i in infos)), "iterations_sum": int(sum(i.iters for i in infos))}
+        for s in ss:
+            s.close()
+        return out
+
+    res = {"workload": f"{len(specs)} contexts: complex-scaled Schroedinger pencils, grid sides 16..64 step 4 "
+                       "(k = 16, m = 2, block-Jacobi 16, tol 1e-8) + shifts 10-5i, 25-12i over the 64^2 pencil",
+           "contexts": len(specs)}
+    for mode in ("sequential", "pool", "persistent"):
+        for precision in ("fp64", "mixed"):
+            res[f"{mode}_{precision}"] = run(mode, precision)
+    return res
 
 
 def time_to_pairs(G, stream, precision, inner_steps=0):

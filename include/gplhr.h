@@ -297,16 +297,17 @@ gplhr_status gplhr_iterate_batched(int32_t nctx, gplhr_ctx* const* ctxs, int32_t
  * (steps 7-24, steps 25-28, the residual with its column norms) run for ALL contexts in
  * one launch of a persistent kernel.  The host records each context's launches (the
  * kernels, grids and arguments gplhr_iterate would issue, on the FP64 / FP32 DFMA and
- * FFMA kernels, not the tensor-core ones), merges them into one program and launches it
- * cooperatively (every CTA resident); the kernel runs step j of every context's program
- * side by side and crosses a grid barrier before step j + 1.  Per iteration of the whole
- * batch: three launches and two host round trips (the projected pencils for the host
- * QZ, which runs on nthreads host threads, and the residual norms for soft locking).
- * Each barrier wait is bounded (the contexts' opts.wait_limit, in tests of 20 us); when
- * it runs out the call returns GPLHR_ETIMEOUT (opts.wait_probe makes it run out: a test
- * hook).  Contexts iterate in lockstep and leave the batch when they converge, fail or
- * reach their budget.  Results match gplhr_iterate's to rounding (the Gram products'
- * partial sums are split by the context's share of the SMs, not by all of them).
+ * FFMA kernels, not the tensor-core ones) and merges them into one queue; the kernel,
+ * launched cooperatively (every CTA resident), takes the queue's items (the launches'
+ * CTAs) in order, and each item waits only for the previous launch of its own context,
+ * so the contexts advance independently.  Per iteration of the whole batch: three
+ * launches and two host round trips (the projected pencils for the host QZ, which runs on
+ * nthreads host threads, and the residual norms for soft locking).  Each wait is bounded
+ * (the contexts' opts.wait_limit, in tests of 20 us); when it runs out the call returns
+ * GPLHR_ETIMEOUT (opts.wait_probe makes it run out: a test hook).  Contexts iterate in
+ * lockstep and leave the batch when they converge, fail or reach their budget.  Results
+ * match gplhr_iterate's to rounding (the Gram products' partial sums are split by the
+ * context's share of the SMs, not by all of them).
  * Not supported (EINVAL): GPLHR-EIG contexts, inner GMRES preconditioning (its least
  * squares runs on the host inside T), profiling.  A context must not appear twice; all
  * contexts belong to the current device.
@@ -318,7 +319,7 @@ gplhr_status gplhr_iterate_batched(int32_t nctx, gplhr_ctx* const* ctxs, int32_t
  * the first failing status in context order; a message is in gplhr_last_error(NULL). */
 typedef struct gplhr_persist_stats {
   int64_t launches;  /* persistent-kernel launches */
-  int64_t steps;     /* program steps (grid barriers + 1 per launch) over all launches */
+  int64_t steps;     /* queue steps (the longest context's launches) over all launches */
   int64_t ops;       /* recorded kernel launches they replaced */
   int32_t grid;      /* CTAs of the last launch */
   int32_t pad;

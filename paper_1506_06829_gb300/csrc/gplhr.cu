@@ -2125,8 +2125,9 @@ gplhr_status run_iterations(gplhr_ctx* ctx, int niter, gplhr_info* info, bool* c
 // residual and its norms) runs for all of them in ONE launch of the persistent kernel of
 // persist.cuh: the host records each context's launches (the same kernels, grids and
 // arguments as gplhr_iterate, on DFMA, with grids sized to the context's share of the
-// SMs), merges them into one program, and the kernel walks it with a grid barrier per
-// step.  An iteration of the whole batch is three launches and two host round trips (the
+// SMs), merges them into one queue, and the kernel runs each context's launches in order,
+// the contexts independently.  An iteration of the whole batch is three launches and two
+// host round trips (the
 // pencils for the host QZ, the residual norms for locking), instead of ~100 launches
 // per context.
 struct PkBuf {
@@ -2139,7 +2140,7 @@ struct PkRunner {
   int dev = 0, num_sms = 0;
   cudaStream_t stream = nullptr;
   PkBuf buf[3];  // one per segment kind, so a program is not overwritten while its copy is pending
-  gplhr::PkBarrier* bar = nullptr;
+  gplhr::PkQueue* queue = nullptr;
   int* derr = nullptr;
   int* herr = nullptr;
   unsigned long long limit_ns = 0;
@@ -2159,7 +2160,7 @@ struct PkRunner {
       if (b.host) cudaFreeHost(b.host);
       if (b.dev) cudaFree(b.dev);
     }
-    if (bar) cudaFree(bar);
+    if (queue) cudaFree(queue);
     if (derr) cudaFree(derr);
     if (herr) cudaFreeHost(herr);
     if (stream) cudaStreamDestroy(stream);
@@ -2187,7 +2188,8 @@ gplhr_status pk_launch(PkRunner& R, int seg, const std::vector<const PkRecorder*
   return st;
 }
 
-// The persistent kernel on R.stream: its barrier zeroed, cooperative (all CTAs resident).
+// The persistent kernel on R.stream: its queue and finish counts zeroed, cooperative (all
+// CTAs resident).
 gplhr_status pk_run(PkRunner& R, gplhr::PkProgram prog, size_t smem, size_t nsteps, size_t nops) {
   if (smem > 48 * 1024)
     PKCK(cudaFuncSetAttribute(gplhr::persistent_segment_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2200,8 +2202,9 @@ gplhr_status pk_run(PkRunner& R, gplhr::PkProgram prog, size_t smem, size_t nste
     return GPLHR_EINVAL;
   }
   R.grid = R.num_sms * std::min(occ, gplhr::PK_CTAS_PER_SM);
-  PKCK(cudaMemsetAsync(R.bar, 0, sizeof(gplhr::PkBarrier), R.stream));
-  void* kargs[] = {&prog, &R.bar, &R.derr, &R.limit_ns, &R.probe};
+  PKCK(cudaMemsetAsync(R.queue, 0, sizeof(gplhr::PkQueue), R.stream));
+  PKCK(cudaMemsetAsync(prog.done, 0, (size_t)prog.nops * sizeof(int), R.stream));
+  void* kargs[] = {&prog, &R.queue, &R.derr, &R.limit_ns, &R.probe};
   PKCK(cudaLaunchCooperativeKernel((const void*)gplhr::persistent_segment_kernel, dim3(R.grid),
                                    dim3(gplhr::PK_THREADS), kargs, smem, R.stream));
   R.launches += 1;
@@ -2216,114 +2219,105 @@ gplhr_status pk_launch_impl(PkRunner& R, int seg, const std::vector<const PkReco
   if (!recs.empty() && recs == R.last_recs[seg])
     return pk_run(R, R.last_prog[seg], R.last_smem[seg], R.last_nsteps[seg], R.last_nops[seg]);
   R.last_recs[seg].clear();
+  // each context's sequence: its host-to-device copies, its recorded launches, its
+  // device-to-host copies (the copies run inside the kernel: the device reads and writes
+  // the host's pinned staging directly); the queue takes the j-th element of every
+  // sequence before the (j+1)-th
   size_t nops = 0, nsteps = 0, argbytes = 0, smem = 0;
+  const size_t rawsz = (sizeof(gplhr::PkRaw) + 15) & ~(size_t)15;
   for (const PkRecorder* r : recs) {
-    nops += r->ops.size();
-    nsteps = std::max(nsteps, r->ops.size());
+    const size_t len = r->pre.size() + r->ops.size() + r->post.size();
+    nops += len;
+    nsteps = std::max(nsteps, len);
+    argbytes += (r->pre.size() + r->post.size()) * rawsz;
     for (const PkRecorder::Op& o : r->ops) {
       argbytes += (o.size + 15) & ~(size_t)15;
       smem = std::max(smem, o.smem);
     }
   }
-  // the copies to and from pinned host memory run inside the kernel (the device reads and
-  // writes the host's pinned staging directly): the host-to-device ones as a first step,
-  // the device-to-host ones as a last step
-  size_t npre = 0, npost = 0;
-  for (const PkRecorder* r : recs) {
-    npre += r->pre.size();
-    npost += r->post.size();
+  if (nops == 0) return GPLHR_OK;
+  if (argbytes > 0xFFFFFFFFull || nops > (size_t)INT_MAX / 2) {
+    R.err = "persistent program: too large";
+    return GPLHR_EINVAL;
   }
-  const size_t step0 = npre ? 1 : 0;
-  nsteps += step0 + (npost ? 1 : 0);
-  nops += npre + npost;
-  argbytes += (npre + npost) * ((sizeof(gplhr::PkRaw) + 15) & ~(size_t)15);
-  if (nops > 0) {
-    auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
-    const size_t o_ops = 0, o_vs = al(o_ops + nops * sizeof(gplhr::PkOp)), o_sb = al(o_vs + nops * sizeof(int)),
-                 o_st = al(o_sb + (nsteps + 1) * sizeof(int)), o_args = al(o_st + nsteps * sizeof(int)),
-                 total = o_args + argbytes;
-    if (argbytes > 0xFFFFFFFFull) {
-      R.err = "persistent program: argument pool too large";
-      return GPLHR_EINVAL;
+  auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  const size_t o_ops = 0, o_vs = al(o_ops + nops * sizeof(gplhr::PkOp)), o_prev = al(o_vs + (nops + 1) * sizeof(int)),
+               o_done = al(o_prev + nops * sizeof(int)), o_args = al(o_done + nops * sizeof(int)),
+               total = o_args + argbytes;
+  PkBuf& B = R.buf[seg];
+  if (B.cap < total) {
+    if (B.host) cudaFreeHost(B.host);
+    if (B.dev) cudaFree(B.dev);
+    B.host = nullptr;
+    B.dev = nullptr;
+    B.cap = 0;
+    const size_t cap = total + total / 2;
+    if (cudaMallocHost(&B.host, cap) != cudaSuccess || cudaMalloc(&B.dev, cap) != cudaSuccess) {
+      R.err = "persistent program: allocation failed";
+      return GPLHR_ENOMEM;
     }
-    PkBuf& B = R.buf[seg];
-    if (B.cap < total) {
-      if (B.host) cudaFreeHost(B.host);
-      if (B.dev) cudaFree(B.dev);
-      B.host = nullptr;
-      B.dev = nullptr;
-      B.cap = 0;
-      const size_t cap = total + total / 2;
-      if (cudaMallocHost(&B.host, cap) != cudaSuccess || cudaMalloc(&B.dev, cap) != cudaSuccess) {
-        R.err = "persistent program: allocation failed";
-        return GPLHR_ENOMEM;
-      }
-      B.cap = cap;
-    }
-    gplhr::PkOp* ops = reinterpret_cast<gplhr::PkOp*>(B.host + o_ops);
-    int* vstart = reinterpret_cast<int*>(B.host + o_vs);
-    int* step_begin = reinterpret_cast<int*>(B.host + o_sb);
-    int* step_total = reinterpret_cast<int*>(B.host + o_st);
-    size_t no = 0, ao = 0;
-    int64_t v = 0;
-    auto put = [&](int kind, int gx, int gy, const void* arg, size_t size) {
-      std::memcpy(B.host + o_args + ao, arg, size);
-      ops[no] = gplhr::PkOp{kind, gx, gy, (unsigned)ao};
-      vstart[no] = (int)v;
-      v += (int64_t)gx * gy;
-      ao += (size + 15) & ~(size_t)15;
-      ++no;
-    };
-    auto put_copies = [&](bool pre) {
-      for (const PkRecorder* r : recs)
-        for (const PkRecorder::Copy& c : pre ? r->pre : r->post) {
-          const gplhr::PkRaw a{(const unsigned char*)c.src, (unsigned char*)c.dst, (int64_t)c.bytes};
-          put(gplhr::PK_COPY_RAW, (int)std::max<size_t>(1, std::min<size_t>(8, c.bytes / 4096)), 1, &a, sizeof(a));
-        }
-    };
-    for (size_t j = 0; j < nsteps; ++j) {
-      step_begin[j] = (int)no;
-      v = 0;
-      if (j < step0) {
-        put_copies(true);
-      } else if (npost && j == nsteps - 1) {
-        put_copies(false);
-      } else {
-        for (const PkRecorder* r : recs) {
-          if (j - step0 >= r->ops.size()) continue;
-          const PkRecorder::Op& o = r->ops[j - step0];
-          put(o.kind, o.gx, o.gy, r->args.data() + o.off, o.size);
-        }
-      }
-      if (v > INT_MAX) {
-        R.err = "persistent program: too many CTAs in one step";
-        return GPLHR_EINVAL;
-      }
-      step_total[j] = (int)v;
-    }
-    step_begin[nsteps] = (int)no;
-    PKCK(cudaMemcpyAsync(B.dev, B.host, total, cudaMemcpyHostToDevice, R.stream));
-    gplhr::PkProgram prog{reinterpret_cast<const gplhr::PkOp*>(B.dev + o_ops), B.dev + o_args,
-                          reinterpret_cast<const int*>(B.dev + o_sb), reinterpret_cast<const int*>(B.dev + o_vs),
-                          reinterpret_cast<const int*>(B.dev + o_st), (int)nsteps};
-    TRY(pk_run(R, prog, smem, nsteps, nops));
-    R.last_recs[seg] = recs;
-    R.last_prog[seg] = prog;
-    R.last_smem[seg] = smem;
-    R.last_nsteps[seg] = nsteps;
-    R.last_nops[seg] = nops;
+    B.cap = cap;
   }
+  gplhr::PkOp* ops = reinterpret_cast<gplhr::PkOp*>(B.host + o_ops);
+  int* vstart = reinterpret_cast<int*>(B.host + o_vs);
+  int* prev = reinterpret_cast<int*>(B.host + o_prev);
+  std::vector<int> last(recs.size(), -1);  // each context's latest op in the queue
+  size_t no = 0, ao = 0;
+  int64_t v = 0;
+  auto put = [&](size_t ci, int kind, int gx, int gy, const void* arg, size_t size) {
+    std::memcpy(B.host + o_args + ao, arg, size);
+    ops[no] = gplhr::PkOp{kind, gx, gy, (unsigned)ao};
+    vstart[no] = (int)v;
+    prev[no] = last[ci];
+    last[ci] = (int)no;
+    v += (int64_t)gx * gy;
+    ao += (size + 15) & ~(size_t)15;
+    ++no;
+  };
+  auto put_copy = [&](size_t ci, const PkRecorder::Copy& c) {
+    const gplhr::PkRaw a{(const unsigned char*)c.src, (unsigned char*)c.dst, (int64_t)c.bytes};
+    put(ci, gplhr::PK_COPY_RAW, (int)std::max<size_t>(1, std::min<size_t>(8, c.bytes / 4096)), 1, &a, sizeof(a));
+  };
+  for (size_t j = 0; j < nsteps; ++j)
+    for (size_t ci = 0; ci < recs.size(); ++ci) {
+      const PkRecorder* r = recs[ci];
+      const size_t npre = r->pre.size(), nrec = r->ops.size();
+      if (j < npre) {
+        put_copy(ci, r->pre[j]);
+      } else if (j < npre + nrec) {
+        const PkRecorder::Op& o = r->ops[j - npre];
+        put(ci, o.kind, o.gx, o.gy, r->args.data() + o.off, o.size);
+      } else if (j < npre + nrec + r->post.size()) {
+        put_copy(ci, r->post[j - npre - nrec]);
+      }
+    }
+  if (v > INT_MAX) {
+    R.err = "persistent program: too many virtual CTAs";
+    return GPLHR_EINVAL;
+  }
+  vstart[no] = (int)v;
+  PKCK(cudaMemcpyAsync(B.dev, B.host, o_done, cudaMemcpyHostToDevice, R.stream));  // ops, vstart, prev
+  PKCK(cudaMemcpyAsync(B.dev + o_args, B.host + o_args, argbytes, cudaMemcpyHostToDevice, R.stream));
+  gplhr::PkProgram prog{reinterpret_cast<const gplhr::PkOp*>(B.dev + o_ops), B.dev + o_args,
+                        reinterpret_cast<const int*>(B.dev + o_vs), reinterpret_cast<const int*>(B.dev + o_prev),
+                        reinterpret_cast<int*>(B.dev + o_done), (int)nops};
+  TRY(pk_run(R, prog, smem, nsteps, nops));
+  R.last_recs[seg] = recs;
+  R.last_prog[seg] = prog;
+  R.last_smem[seg] = smem;
+  R.last_nsteps[seg] = nsteps;
+  R.last_nops[seg] = nops;
   return GPLHR_OK;
 }
 
-// Wait for R.stream; GPLHR_ETIMEOUT if a barrier wait of the kernel gave up.
+// Wait for R.stream; GPLHR_ETIMEOUT if a wait of the kernel gave up.
 gplhr_status pk_sync(PkRunner& R) {
   PKCK(cudaMemcpyAsync(R.herr, R.derr, sizeof(int), cudaMemcpyDeviceToHost, R.stream));
   const auto t0 = std::chrono::steady_clock::now();
   PKCK(cudaStreamSynchronize(R.stream));
   R.wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (*R.herr != 0) {
-    R.err = "persistent kernel: a grid barrier wait gave up";
+    R.err = "persistent kernel: a wait for a context's previous launch gave up";
     return GPLHR_ETIMEOUT;
   }
   return GPLHR_OK;
@@ -2417,11 +2411,11 @@ gplhr_status pk_iterate(int nctx, gplhr_ctx* const* ctxs, const std::vector<int>
   PKCK(cudaGetDevice(&R.dev));
   PKCK(cudaDeviceGetAttribute(&R.num_sms, cudaDevAttrMultiProcessorCount, R.dev));
   PKCK(cudaStreamCreateWithFlags(&R.stream, cudaStreamNonBlocking));
-  PKCK(cudaMalloc(&R.bar, sizeof(gplhr::PkBarrier)));
+  PKCK(cudaMalloc(&R.queue, sizeof(gplhr::PkQueue)));
   PKCK(cudaMalloc(&R.derr, sizeof(int)));
   PKCK(cudaMemset(R.derr, 0, sizeof(int)));
   PKCK(cudaMallocHost(&R.herr, sizeof(int)));
-  // the barrier's time limit: the contexts' wait limit (tests of at most 20 us each)
+  // the kernel's wait limit: the contexts' wait limit (tests of at most 20 us each)
   int tries = gplhr::TC_WAIT_TRIES;
   for (int i = 0; i < nctx; ++i) {
     tries = std::min(tries, ctxs[i]->tc_wait_tries);

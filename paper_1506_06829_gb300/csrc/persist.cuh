@@ -3,16 +3,19 @@
 // norms) for every context of a batch.
 //
 // The host records each context's segment as the list of launches it would make (kernel,
-// grid, arguments), in program order.  Step j of the program is the j-th recorded launch
-// of every context that has one; the kernel walks the steps, spreads the CTAs of each
-// step's launches (their "virtual" CTAs) over its own CTAs, runs each virtual CTA with
-// the body of the recorded kernel, and crosses a grid-wide barrier before the next step.
-// A launch depends only on the earlier launches of its own context, so one barrier per
-// step keeps every context's order while the contexts' launches run side by side.
+// grid, arguments), in program order, and merges the lists into one queue: the j-th
+// launches of all contexts, then the (j+1)-th, and so on, each launch as its grid's
+// "virtual" CTAs.  The kernel's CTAs take queue items in order from a global counter; an
+// item first waits until the previous launch of its own context has finished (a count of
+// its finished virtual CTAs), then runs the recorded kernel's body for its virtual CTA and
+// counts itself finished.  A launch depends only on the earlier launches of its context,
+// so the contexts advance independently: a slow step of one (a Cholesky factorisation, a
+// large Gram product) does not hold up the others.  Every item waits only on items earlier
+// in the queue, which are held by running CTAs, so the waits always end.
 //
-// Launched cooperatively (all CTAs resident), so the barrier always completes; its wait
-// is bounded all the same (a time limit on the global timer), after which the kernel
-// records GPLHR_ETIMEOUT and every CTA returns at its next barrier.
+// Launched cooperatively (all CTAs resident); every wait is bounded all the same (a time
+// limit on the global timer), after which the kernel records GPLHR_ETIMEOUT and every CTA
+// returns.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -150,23 +153,24 @@ struct PkOp {
   unsigned argoff;
 };
 
-// Device program: ops sorted by step; step j holds ops [step_begin[j], step_begin[j+1]);
-// vstart[o] = first virtual CTA of op o within its step, step_total[j] = the step's count.
+// Device program: ops in queue order (the j-th launches of all contexts before the
+// (j+1)-th); op o owns queue items vstart[o] .. vstart[o+1] - 1 (its virtual CTAs), waits
+// for op prev[o] (its context's previous launch, -1 for none), and counts its finished
+// items in done[o] (zeroed before each launch).
 struct PkProgram {
   const PkOp* ops;
   const unsigned char* args;
-  const int* step_begin;
-  const int* vstart;
-  const int* step_total;
-  int nsteps;
+  const int* vstart;  // nops + 1 entries
+  const int* prev;
+  int* done;
+  int nops;
 };
 
-// Barrier state, zeroed by the host before each launch.
-struct PkBarrier {
-  unsigned count;
-  unsigned gen;
+// Queue state, zeroed by the host before each launch.
+struct PkQueue {
+  unsigned next;
   int abort;
-  int pad;
+  int pad[2];
 };
 
 __device__ __forceinline__ unsigned long long pk_globaltimer() {
@@ -175,42 +179,28 @@ __device__ __forceinline__ unsigned long long pk_globaltimer() {
   return t;
 }
 
-// Grid-wide barrier (sense by generation count).  Thread 0 of each CTA publishes the
-// CTA's writes (fence), arrives, and waits for the generation to move on; the last
-// arrival opens it.  The wait is bounded by limit_ns of global time: then the abort flag
-// is raised, err records GPLHR_ETIMEOUT (7) and every CTA leaves at this or its next
-// barrier.  probe (test hook): the last arrival does not open the barrier, so the wait
-// runs out.  Returns false when the kernel must end.
-__device__ __forceinline__ bool pk_grid_barrier(PkBarrier* b, unsigned nblocks, int* err,
-                                                unsigned long long limit_ns, int probe) {
-  __shared__ int pk_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &b->gen;
-    volatile int* vabort = &b->abort;
-    const unsigned g = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&b->count, 1u);
-    if (arrived == nblocks - 1 && !probe) {
-      atomicExch(&b->count, 0u);
-      __threadfence();
-      atomicAdd(&b->gen, 1u);
-    } else {
-      const unsigned long long t0 = pk_globaltimer();
-      while (*vgen == g && !*vabort) {
-        if (pk_globaltimer() - t0 > limit_ns) {
-          atomicExch(&b->abort, 1);
-          atomicCAS(err, 0, 7);
-          break;
-        }
-        __nanosleep(128);
+// Thread 0 of the CTA: wait until op d has finished `need` virtual CTAs.  Bounded by
+// limit_ns of global time: then the abort flag is raised, err records GPLHR_ETIMEOUT (7),
+// and false is returned (also when another CTA has aborted).  The fence after the wait
+// orders the CTA's later reads after the producers' writes (they fence before counting).
+__device__ __forceinline__ bool pk_wait_done(const int* done, int need, PkQueue* q, int* err,
+                                             unsigned long long limit_ns) {
+  volatile const int* vd = done;
+  volatile int* vabort = &q->abort;
+  if (*vd < need) {
+    const unsigned long long t0 = pk_globaltimer();
+    while (*vd < need) {
+      if (*vabort) return false;
+      if (pk_globaltimer() - t0 > limit_ns) {
+        atomicExch(&q->abort, 1);
+        atomicCAS(err, 0, 7);
+        return false;
       }
+      __nanosleep(64);
     }
-    __threadfence();
-    pk_ok = *vabort ? 0 : 1;
   }
-  __syncthreads();
-  return pk_ok != 0;
+  __threadfence();
+  return true;
 }
 
 template <bool F32, bool AC, bool BC, int G>
@@ -368,26 +358,42 @@ __device__ __forceinline__ void pk_run(int kind, const unsigned char* arg, const
   }
 }
 
-// The persistent kernel: one program, every step's virtual CTAs over this grid, a bounded
-// grid barrier between steps.
+// The persistent kernel: CTAs take queue items in order, wait for their context's previous
+// launch, run the item's virtual CTA and count it finished.  probe (test hook): every wait
+// asks for one virtual CTA more than its op has, so the first wait runs out.
 __global__ void __launch_bounds__(PK_THREADS, PK_CTAS_PER_SM)
-persistent_segment_kernel(PkProgram p, PkBarrier* bar, int* err, unsigned long long limit_ns, int probe) {
-  for (int j = 0; j < p.nsteps; ++j) {
-    const int o0 = p.step_begin[j], o1 = p.step_begin[j + 1];
-    const int total = p.step_total[j];
-    for (int v = blockIdx.x; v < total; v += gridDim.x) {
-      int lo = o0, hi = o1 - 1;  // last op of the step whose first virtual CTA is <= v
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (p.vstart[mid] <= v) lo = mid; else hi = mid - 1;
-      }
-      const PkOp op = p.ops[lo];
-      const int local = v - p.vstart[lo];
-      const Cta c{local % op.gx, local / op.gx, op.gx, op.gy};
-      pk_run(op.kind, p.args + op.argoff, c);
-      __syncthreads();  // the next virtual CTA reuses shared memory
+persistent_segment_kernel(PkProgram p, PkQueue* q, int* err, unsigned long long limit_ns, int probe) {
+  __shared__ int s_item, s_ok;
+  const int total = p.vstart[p.nops];
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const volatile int* vabort = &q->abort;
+      s_item = *vabort ? total : (int)atomicAdd(&q->next, 1u);
     }
-    if (j + 1 < p.nsteps && !pk_grid_barrier(bar, gridDim.x, err, limit_ns, probe)) return;
+    __syncthreads();
+    const int v = s_item;
+    if (v >= total) return;
+    int lo = 0, hi = p.nops - 1;  // the op owning item v: last op with vstart <= v
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (p.vstart[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    if (threadIdx.x == 0) {
+      const int d = p.prev[lo];
+      s_ok = d < 0 ? 1 : (pk_wait_done(p.done + d, p.vstart[d + 1] - p.vstart[d] + (probe ? 1 : 0), q, err,
+                                       limit_ns) ? 1 : 0);
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const PkOp op = p.ops[lo];
+    const int local = v - p.vstart[lo];
+    const Cta c{local % op.gx, local / op.gx, op.gx, op.gy};
+    pk_run(op.kind, p.args + op.argoff, c);
+    __syncthreads();  // the item's writes are done (and the next item reuses shared memory)
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(p.done + lo, 1);
+    }
   }
 }
 

@@ -1,14 +1,15 @@
 """GPU tests of the persistent batched iteration (gplhr_solve_persistent /
 gplhr_iterate_persistent): every device segment of an iteration runs for all contexts of
-a batch in one launch of the persistent kernel, with a bounded grid barrier between the
-recorded launches.
+a batch in one launch of the persistent kernel, which runs each context's recorded
+launches in order (each waits, bounded, for its context's previous launch) and the
+contexts independently.
 
 Checks: whole solves of pencils of uneven size (standard and generalized, block-Jacobi
 and an explicit sparse T, FP64 and mixed precision, soft locking) give the eigenvalues
 that per-context solves and dense LAPACK give; lockstep iterations of a copy of the
 batched workload (pencils and slices of one pencil) track per-context iterations; one
 pencil of the batch against the CPU oracle; three launches per iteration of the whole
-batch; a barrier wait that runs out returns ETIMEOUT and leaves the GPU usable; contexts
+batch; a wait that runs out returns ETIMEOUT and leaves the GPU usable; contexts
 the kernel cannot run are refused before any launch."""
 import numpy as np
 import pytest
@@ -173,10 +174,11 @@ def test_persistent_iterations_track_per_context_iterations():
         s.close()
 
 
-def test_persistent_barrier_timeout_then_gpu_usable():
-    """opts.wait_probe keeps the first grid barrier closed: its bounded wait (wait_limit =
-    64 tests, ~1.3 ms) runs out, the call returns ETIMEOUT and nothing hangs; a fresh batch
-    then iterates normally on the same GPU."""
+def test_persistent_wait_timeout_then_gpu_usable():
+    """opts.wait_probe makes every wait for a previous launch ask for one CTA more than it
+    has, so the first such wait (wait_limit = 64 tests, ~1.3 ms) runs out, the call
+    returns ETIMEOUT and nothing hangs; a fresh batch then iterates normally on the same
+    GPU."""
     ps = _pencils()[:2]
     probe = [_solver(p, wait_limit=64, wait_probe=True) for p in ps]
     for s, p in zip(probe, ps):
