@@ -208,6 +208,7 @@ struct gplhr_ctx {
   };
   std::map<uint64_t, PkCached>* pk_cache = nullptr;
   const PkRecorder* rec_last = nullptr;
+  double2* pk_work = nullptr;  // 2 s_max^2 values: global work of a wide Cholesky (persistent batch)
   std::string err;
 };
 
@@ -1437,12 +1438,15 @@ gplhr_status orth_against(gplhr_ctx* ctx, Blk L, int wl, Blk X, int w, const std
     const size_t smem = (size_t)2 * w * w * sizeof(double2);
     const int ph = prof_begin(ctx, KC_CHOL, 8.0 * w * w * w / 2.0, 48.0 * w * w);
     double2* Rout = track ? ctx->dTrackR + (size_t)pass * smax2 : nullptr;
-    if (ctx->rec)
-      pk_rec(ctx, gplhr::PK_CHOL, 1, 1, smem,
-             gplhr::PkChol{w, (int64_t)ctx->n, ctx->dGram, Rinv, ctx->d_status + pass, skip, ctx->d_diag, Rout});
-    else
+    if (ctx->rec) {
+      const bool glob = smem > gplhr::PK_CHOL_SMEM_MAX && ctx->pk_work;
+      pk_rec(ctx, gplhr::PK_CHOL, 1, 1, glob ? 0 : smem,
+             gplhr::PkChol{w, (int64_t)ctx->n, ctx->dGram, Rinv, ctx->d_status + pass, skip, ctx->d_diag, Rout,
+                           glob ? ctx->pk_work : nullptr});
+    } else {
       gplhr::chol_inv_kernel<<<1, 256, smem, ctx->stream>>>(w, (int64_t)ctx->n, ctx->dGram, Rinv,
                                                             ctx->d_status + pass, skip, ctx->d_diag, Rout);
+    }
     prof_end(ctx, ph);
     CK(cudaGetLastError());
     TRY(combine(ctx, {In{X, w, Rinv, kOne}}, X, w, false, skip, none, -1, -1, cnt, -1, true));
@@ -2150,6 +2154,7 @@ struct PkRunner {
   // host time recording segments, merging and uploading programs, in the host QZ, and
   // waiting for the device (ms)
   double record_ms = 0.0, build_ms = 0.0, qz_ms = 0.0, wait_ms = 0.0;
+  std::vector<double2*> work;  // per context: global work of its wide Cholesky factorisations
   // the last program of each segment kind: its recordings and device program
   std::vector<const PkRecorder*> last_recs[3];
   gplhr::PkProgram last_prog[3] = {};
@@ -2161,6 +2166,8 @@ struct PkRunner {
       if (b.dev) cudaFree(b.dev);
     }
     if (queue) cudaFree(queue);
+    for (double2* w : work)
+      if (w) cudaFree(w);
     if (derr) cudaFree(derr);
     if (herr) cudaFreeHost(herr);
     if (stream) cudaStreamDestroy(stream);
@@ -2203,7 +2210,7 @@ gplhr_status pk_run(PkRunner& R, gplhr::PkProgram prog, size_t smem, size_t nste
   }
   R.grid = R.num_sms * std::min(occ, gplhr::PK_CTAS_PER_SM);
   PKCK(cudaMemsetAsync(R.queue, 0, sizeof(gplhr::PkQueue), R.stream));
-  PKCK(cudaMemsetAsync(prog.done, 0, (size_t)prog.nops * sizeof(int), R.stream));
+  PKCK(cudaMemsetAsync(prog.claimed, 0, (size_t)(2 * prog.nops + prog.nctx) * sizeof(int), R.stream));
   void* kargs[] = {&prog, &R.queue, &R.derr, &R.limit_ns, &R.probe};
   PKCK(cudaLaunchCooperativeKernel((const void*)gplhr::persistent_segment_kernel, dim3(R.grid),
                                    dim3(gplhr::PK_THREADS), kargs, smem, R.stream));
@@ -2221,9 +2228,9 @@ gplhr_status pk_launch_impl(PkRunner& R, int seg, const std::vector<const PkReco
   R.last_recs[seg].clear();
   // each context's sequence: its host-to-device copies, its recorded launches, its
   // device-to-host copies (the copies run inside the kernel: the device reads and writes
-  // the host's pinned staging directly); the queue takes the j-th element of every
-  // sequence before the (j+1)-th
+  // the host's pinned staging directly); contexts in the given (priority) order
   size_t nops = 0, nsteps = 0, argbytes = 0, smem = 0;
+  const size_t nctx = recs.size();
   const size_t rawsz = (sizeof(gplhr::PkRaw) + 15) & ~(size_t)15;
   for (const PkRecorder* r : recs) {
     const size_t len = r->pre.size() + r->ops.size() + r->post.size();
@@ -2241,9 +2248,9 @@ gplhr_status pk_launch_impl(PkRunner& R, int seg, const std::vector<const PkReco
     return GPLHR_EINVAL;
   }
   auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
-  const size_t o_ops = 0, o_vs = al(o_ops + nops * sizeof(gplhr::PkOp)), o_prev = al(o_vs + (nops + 1) * sizeof(int)),
-               o_done = al(o_prev + nops * sizeof(int)), o_args = al(o_done + nops * sizeof(int)),
-               total = o_args + argbytes;
+  const size_t o_ops = 0, o_vc = al(o_ops + nops * sizeof(gplhr::PkOp)), o_cf = al(o_vc + nops * sizeof(int)),
+               o_cn = al(o_cf + nctx * sizeof(int)), o_zero = al(o_cn + nctx * sizeof(int)),
+               zbytes = (2 * nops + nctx) * sizeof(int), o_args = al(o_zero + zbytes), total = o_args + argbytes;
   PkBuf& B = R.buf[seg];
   if (B.cap < total) {
     if (B.host) cudaFreeHost(B.host);
@@ -2259,48 +2266,42 @@ gplhr_status pk_launch_impl(PkRunner& R, int seg, const std::vector<const PkReco
     B.cap = cap;
   }
   gplhr::PkOp* ops = reinterpret_cast<gplhr::PkOp*>(B.host + o_ops);
-  int* vstart = reinterpret_cast<int*>(B.host + o_vs);
-  int* prev = reinterpret_cast<int*>(B.host + o_prev);
-  std::vector<int> last(recs.size(), -1);  // each context's latest op in the queue
+  int* vcount = reinterpret_cast<int*>(B.host + o_vc);
+  int* ctx_first = reinterpret_cast<int*>(B.host + o_cf);
+  int* ctx_nops = reinterpret_cast<int*>(B.host + o_cn);
   size_t no = 0, ao = 0;
-  int64_t v = 0;
-  auto put = [&](size_t ci, int kind, int gx, int gy, const void* arg, size_t size) {
+  auto put = [&](int kind, int gx, int gy, const void* arg, size_t size) {
     std::memcpy(B.host + o_args + ao, arg, size);
     ops[no] = gplhr::PkOp{kind, gx, gy, (unsigned)ao};
-    vstart[no] = (int)v;
-    prev[no] = last[ci];
-    last[ci] = (int)no;
-    v += (int64_t)gx * gy;
+    vcount[no] = gx * gy;
     ao += (size + 15) & ~(size_t)15;
     ++no;
   };
-  auto put_copy = [&](size_t ci, const PkRecorder::Copy& c) {
+  auto put_copy = [&](const PkRecorder::Copy& c) {
     const gplhr::PkRaw a{(const unsigned char*)c.src, (unsigned char*)c.dst, (int64_t)c.bytes};
-    put(ci, gplhr::PK_COPY_RAW, (int)std::max<size_t>(1, std::min<size_t>(8, c.bytes / 4096)), 1, &a, sizeof(a));
+    put(gplhr::PK_COPY_RAW, (int)std::max<size_t>(1, std::min<size_t>(8, c.bytes / 4096)), 1, &a, sizeof(a));
   };
-  for (size_t j = 0; j < nsteps; ++j)
-    for (size_t ci = 0; ci < recs.size(); ++ci) {
-      const PkRecorder* r = recs[ci];
-      const size_t npre = r->pre.size(), nrec = r->ops.size();
-      if (j < npre) {
-        put_copy(ci, r->pre[j]);
-      } else if (j < npre + nrec) {
-        const PkRecorder::Op& o = r->ops[j - npre];
-        put(ci, o.kind, o.gx, o.gy, r->args.data() + o.off, o.size);
-      } else if (j < npre + nrec + r->post.size()) {
-        put_copy(ci, r->post[j - npre - nrec]);
-      }
-    }
-  if (v > INT_MAX) {
-    R.err = "persistent program: too many virtual CTAs";
-    return GPLHR_EINVAL;
+  for (size_t ci = 0; ci < nctx; ++ci) {
+    const PkRecorder* r = recs[ci];
+    ctx_first[ci] = (int)no;
+    for (const PkRecorder::Copy& c : r->pre) put_copy(c);
+    for (const PkRecorder::Op& o : r->ops) put(o.kind, o.gx, o.gy, r->args.data() + o.off, o.size);
+    for (const PkRecorder::Copy& c : r->post) put_copy(c);
+    ctx_nops[ci] = (int)no - ctx_first[ci];
   }
-  vstart[no] = (int)v;
-  PKCK(cudaMemcpyAsync(B.dev, B.host, o_done, cudaMemcpyHostToDevice, R.stream));  // ops, vstart, prev
+  PKCK(cudaMemcpyAsync(B.dev, B.host, o_zero, cudaMemcpyHostToDevice, R.stream));  // ops, counts, contexts
   PKCK(cudaMemcpyAsync(B.dev + o_args, B.host + o_args, argbytes, cudaMemcpyHostToDevice, R.stream));
-  gplhr::PkProgram prog{reinterpret_cast<const gplhr::PkOp*>(B.dev + o_ops), B.dev + o_args,
-                        reinterpret_cast<const int*>(B.dev + o_vs), reinterpret_cast<const int*>(B.dev + o_prev),
-                        reinterpret_cast<int*>(B.dev + o_done), (int)nops};
+  int* zero = reinterpret_cast<int*>(B.dev + o_zero);
+  gplhr::PkProgram prog{reinterpret_cast<const gplhr::PkOp*>(B.dev + o_ops),
+                        B.dev + o_args,
+                        reinterpret_cast<const int*>(B.dev + o_vc),
+                        reinterpret_cast<const int*>(B.dev + o_cf),
+                        reinterpret_cast<const int*>(B.dev + o_cn),
+                        zero,
+                        zero + nops,
+                        zero + 2 * nops,
+                        (int)nops,
+                        (int)nctx};
   TRY(pk_run(R, prog, smem, nsteps, nops));
   R.last_recs[seg] = recs;
   R.last_prog[seg] = prog;
@@ -2431,8 +2432,13 @@ gplhr_status pk_iterate(int nctx, gplhr_ctx* const* ctxs, const std::vector<int>
   for (int i = 0; i < nctx; ++i) nsum += ctxs[i]->n;
   std::vector<int> saved_sms(nctx);
   std::vector<char> saved_tc(nctx);
+  R.work.assign(nctx, nullptr);
+  for (int i = 0; i < nctx; ++i)  // (before any context is changed: an early return leaves them as they were)
+    if (gplhr::PK_CHOL_SMEM_MAX < (size_t)2 * ctxs[i]->s_max * ctxs[i]->s_max * sizeof(double2))
+      PKCK(cudaMalloc(&R.work[i], (size_t)2 * ctxs[i]->s_max * ctxs[i]->s_max * sizeof(double2)));
   for (int i = 0; i < nctx; ++i) {
     gplhr_ctx* c = ctxs[i];
+    c->pk_work = R.work[i];
     saved_sms[i] = c->num_sms;
     saved_tc[i] = c->tc;
     c->num_sms = std::max(1, (int)std::lround(kPkShare * R.num_sms * c->n / nsum));
@@ -2481,6 +2487,9 @@ gplhr_status pk_iterate(int nctx, gplhr_ctx* const* ctxs, const std::vector<int>
     for (int i = 0; i < nctx; ++i)
       if (st[i] == GPLHR_OK && !conv[i] && ctxs[i]->it < iters_cap[i]) act.push_back(i);
     if (act.empty()) break;
+    // the persistent kernel serves contexts in this order when several are ready: the
+    // largest first (their chains of launches are the longest)
+    std::stable_sort(act.begin(), act.end(), [&](int x, int y) { return ctxs[x]->n > ctxs[y]->n; });
     for (int i : act) {
       if (ctxs[i]->bulk32) ctxs[i]->fp32_iters += 1;
       iter_plan(ctxs[i], plan[i]);
@@ -2513,6 +2522,7 @@ gplhr_status pk_iterate(int nctx, gplhr_ctx* const* ctxs, const std::vector<int>
   for (int i = 0; i < nctx; ++i) {
     ctxs[i]->num_sms = saved_sms[i];
     ctxs[i]->tc = saved_tc[i] != 0;
+    ctxs[i]->pk_work = nullptr;
     if (fatal != GPLHR_OK && st[i] == GPLHR_OK && !conv[i]) {
       st[i] = fatal;
       ctxs[i]->err = R.err;

@@ -953,12 +953,15 @@ __device__ __forceinline__ double rsqrt_newton(double a) {
   return __longlong_as_double(__double_as_longlong(y) - ((long long)h << 52));  // y 2^(-h)
 }
 
+// work: null = the two w x w work arrays in dynamic shared memory; else 2 w^2 values of
+// global memory owned by the caller (the persistent kernel, whose CTAs cannot all hold
+// 32 w^2 bytes of shared memory for a wide block).
 __device__ __forceinline__ void chol_inv_body(const Cta& cta, int w, int64_t n, const double2* G,
                                 double2* Rinv, int* status, const int* skip_if_zero,
-                                int* fallback_counter, double2* Rout) {
+                                int* fallback_counter, double2* Rout, double2* work = nullptr) {
   extern __shared__ double2 sm[];
-  double2* a = sm;              // w x w working copy -> R (upper)
-  double2* inv = sm + w * w;    // w x w -> R^{-1}
+  double2* a = work ? work : sm;  // w x w working copy -> R (upper)
+  double2* inv = a + w * w;       // w x w -> R^{-1}
   __shared__ int fail;
   __shared__ double shift, piv_r, piv_ri;
   const int tid = threadIdx.x, nt = blockDim.x;

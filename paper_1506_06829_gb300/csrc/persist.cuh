@@ -3,19 +3,18 @@
 // norms) for every context of a batch.
 //
 // The host records each context's segment as the list of launches it would make (kernel,
-// grid, arguments), in program order, and merges the lists into one queue: the j-th
-// launches of all contexts, then the (j+1)-th, and so on, each launch as its grid's
-// "virtual" CTAs.  The kernel's CTAs take queue items in order from a global counter; an
-// item first waits until the previous launch of its own context has finished (a count of
-// its finished virtual CTAs), then runs the recorded kernel's body for its virtual CTA and
-// counts itself finished.  A launch depends only on the earlier launches of its context,
-// so the contexts advance independently: a slow step of one (a Cholesky factorisation, a
-// large Gram product) does not hold up the others.  Every item waits only on items earlier
-// in the queue, which are held by running CTAs, so the waits always end.
+// grid, arguments), in program order.  A launch's CTAs become "virtual" CTAs (items) of
+// the persistent kernel.  A launch is ready once its context's previous launch has
+// finished all its items; the kernel's CTAs look for work among the contexts' current
+// launches (one warp tests 32 contexts at once, in the host's priority order: the
+// largest contexts, whose chains of launches are the longest, first), claim an item of
+// a ready launch with an atomic counter, run the recorded kernel's body for it and count
+// it finished.  The contexts thus advance independently and no CTA waits behind work
+// that is not ready while other work is.
 //
-// Launched cooperatively (all CTAs resident); every wait is bounded all the same (a time
-// limit on the global timer), after which the kernel records GPLHR_ETIMEOUT and every CTA
-// returns.
+// Launched cooperatively (all CTAs resident).  A CTA that finds no ready work sleeps
+// briefly and looks again; if nothing becomes ready within a time limit on the global
+// timer the kernel records GPLHR_ETIMEOUT and every CTA returns.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -108,7 +107,11 @@ struct PkChol {
   const int* skip;
   int* fallback;
   double2* Rout;
+  double2* work;  // null: shared memory; else 2 w^2 values of global memory
 };
+// Dynamic shared memory above which a Cholesky runs on global work memory instead, so
+// that wide blocks (32 w^2 bytes: 131 KB at w = 64) do not cut the kernel's residency.
+constexpr size_t PK_CHOL_SMEM_MAX = 48 * 1024;
 struct PkComb {
   int n, rows_per_cta;
   CombArgs a;
@@ -153,24 +156,26 @@ struct PkOp {
   unsigned argoff;
 };
 
-// Device program: ops in queue order (the j-th launches of all contexts before the
-// (j+1)-th); op o owns queue items vstart[o] .. vstart[o+1] - 1 (its virtual CTAs), waits
-// for op prev[o] (its context's previous launch, -1 for none), and counts its finished
-// items in done[o] (zeroed before each launch).
+// Device program, context-major: context c (in priority order) owns ops
+// ctx_first[c] .. ctx_first[c] + ctx_nops[c] - 1 in program order; op o has vcount[o]
+// items.  Zeroed before each launch: claimed[o] (items handed out), done[o] (items
+// finished), cur[c] (the context's current op).
 struct PkProgram {
   const PkOp* ops;
   const unsigned char* args;
-  const int* vstart;  // nops + 1 entries
-  const int* prev;
+  const int* vcount;
+  const int* ctx_first;
+  const int* ctx_nops;
+  int* claimed;
   int* done;
-  int nops;
+  int* cur;
+  int nops, nctx;
 };
 
-// Queue state, zeroed by the host before each launch.
+// Kernel state, zeroed by the host before each launch.
 struct PkQueue {
-  unsigned next;
   int abort;
-  int pad[2];
+  int pad[3];
 };
 
 __device__ __forceinline__ unsigned long long pk_globaltimer() {
@@ -179,28 +184,50 @@ __device__ __forceinline__ unsigned long long pk_globaltimer() {
   return t;
 }
 
-// Thread 0 of the CTA: wait until op d has finished `need` virtual CTAs.  Bounded by
-// limit_ns of global time: then the abort flag is raised, err records GPLHR_ETIMEOUT (7),
-// and false is returned (also when another CTA has aborted).  The fence after the wait
-// orders the CTA's later reads after the producers' writes (they fence before counting).
-__device__ __forceinline__ bool pk_wait_done(const int* done, int need, PkQueue* q, int* err,
-                                             unsigned long long limit_ns) {
-  volatile const int* vd = done;
-  volatile int* vabort = &q->abort;
-  if (*vd < need) {
-    const unsigned long long t0 = pk_globaltimer();
-    while (*vd < need) {
-      if (*vabort) return false;
-      if (pk_globaltimer() - t0 > limit_ns) {
-        atomicExch(&q->abort, 1);
-        atomicCAS(err, 0, 7);
-        return false;
+__device__ __forceinline__ int pk_ld(const int* p) { return *(volatile const int*)p; }
+
+// Warp 0 of the CTA: claim an item of a ready op.  Lane l tests the contexts c = base + l
+// (their current op: claimable items left, previous op finished; probe, a test hook,
+// asks the previous op for one item more than it has, so nothing after a context's first
+// op is ever ready); the lowest ready context (highest priority) is tried first.  Returns
+// the op (>= 0, *item set), -1 if nothing is ready now, -2 if every context has finished.
+__device__ __forceinline__ int pk_claim(const PkProgram& p, int probe, int* item) {
+  const int lane = threadIdx.x & 31;
+  bool all_finished = true;
+  for (int base = 0; base < p.nctx; base += 32) {
+    const int c = base + lane;
+    int o = -1, j = 0;
+    bool ready = false;
+    if (c < p.nctx) {
+      j = pk_ld(p.cur + c);
+      if (j < p.ctx_nops[c]) {
+        o = p.ctx_first[c] + j;
+        ready = pk_ld(p.claimed + o) < p.vcount[o] &&
+                (j == 0 || pk_ld(p.done + o - 1) >= p.vcount[o - 1] + probe);
       }
-      __nanosleep(64);
+    }
+    if (__any_sync(0xffffffffu, c < p.nctx && j < p.ctx_nops[c])) all_finished = false;
+    unsigned ballot = __ballot_sync(0xffffffffu, ready);
+    while (ballot) {
+      const int src = __ffs(ballot) - 1;
+      const int oc = __shfl_sync(0xffffffffu, o, src);
+      const int jc = __shfl_sync(0xffffffffu, j, src);
+      int got = -1;
+      if (lane == 0) {
+        const int it = atomicAdd(p.claimed + oc, 1);
+        const int cnt = p.vcount[oc];
+        if (it >= cnt - 1) atomicMax(p.cur + base + src, jc + 1);  // the op is fully handed out
+        if (it < cnt) {
+          got = oc;
+          *item = it;
+        }
+      }
+      got = __shfl_sync(0xffffffffu, got, 0);
+      if (got >= 0) return got;
+      ballot &= ballot - 1;
     }
   }
-  __threadfence();
-  return true;
+  return all_finished ? -2 : -1;
 }
 
 template <bool F32, bool AC, bool BC, int G>
@@ -316,7 +343,7 @@ __device__ __forceinline__ void pk_run(int kind, const unsigned char* arg, const
     }
     case PK_CHOL: {
       const PkChol& o = *reinterpret_cast<const PkChol*>(arg);
-      chol_inv_body(c, o.w, o.n, o.G, o.Rinv, o.status, o.skip, o.fallback, o.Rout);
+      chol_inv_body(c, o.w, o.n, o.G, o.Rinv, o.status, o.skip, o.fallback, o.Rout, o.work);
       break;
     }
     case PK_COMBINE_D: {
@@ -358,41 +385,48 @@ __device__ __forceinline__ void pk_run(int kind, const unsigned char* arg, const
   }
 }
 
-// The persistent kernel: CTAs take queue items in order, wait for their context's previous
-// launch, run the item's virtual CTA and count it finished.  probe (test hook): every wait
-// asks for one virtual CTA more than its op has, so the first wait runs out.
+// The persistent kernel: claim a ready item, run it, count it finished; sleep when nothing
+// is ready; return when every context has finished or a wait ran out.
 __global__ void __launch_bounds__(PK_THREADS, PK_CTAS_PER_SM)
 persistent_segment_kernel(PkProgram p, PkQueue* q, int* err, unsigned long long limit_ns, int probe) {
-  __shared__ int s_item, s_ok;
-  const int total = p.vstart[p.nops];
+  __shared__ int s_op, s_item;
+  unsigned long long idle_since = 0;
   for (;;) {
-    if (threadIdx.x == 0) {
-      const volatile int* vabort = &q->abort;
-      s_item = *vabort ? total : (int)atomicAdd(&q->next, 1u);
+    if (threadIdx.x < 32) {
+      int item = 0;
+      int op = *(volatile int*)&q->abort ? -2 : pk_claim(p, probe, &item);
+      if (threadIdx.x == 0) {
+        if (op >= 0) {
+          __threadfence();  // the previous op's writes (its items fence before counting) before ours
+          idle_since = 0;
+        } else if (op == -1) {
+          const unsigned long long t = pk_globaltimer();
+          if (idle_since == 0) idle_since = t;
+          if (t - idle_since > limit_ns) {
+            atomicExch(&q->abort, 1);
+            atomicCAS(err, 0, 7);
+            op = -2;
+          }
+        }
+        s_op = op;
+        s_item = item;
+      }
     }
     __syncthreads();
-    const int v = s_item;
-    if (v >= total) return;
-    int lo = 0, hi = p.nops - 1;  // the op owning item v: last op with vstart <= v
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (p.vstart[mid] <= v) lo = mid; else hi = mid - 1;
+    const int o = s_op, it = s_item;
+    if (o == -2) return;
+    if (o == -1) {
+      if (threadIdx.x == 0) __nanosleep(256);
+      __syncthreads();
+      continue;
     }
-    if (threadIdx.x == 0) {
-      const int d = p.prev[lo];
-      s_ok = d < 0 ? 1 : (pk_wait_done(p.done + d, p.vstart[d + 1] - p.vstart[d] + (probe ? 1 : 0), q, err,
-                                       limit_ns) ? 1 : 0);
-    }
-    __syncthreads();
-    if (!s_ok) return;
-    const PkOp op = p.ops[lo];
-    const int local = v - p.vstart[lo];
-    const Cta c{local % op.gx, local / op.gx, op.gx, op.gy};
+    const PkOp op = p.ops[o];
+    const Cta c{it % op.gx, it / op.gx, op.gx, op.gy};
     pk_run(op.kind, p.args + op.argoff, c);
     __syncthreads();  // the item's writes are done (and the next item reuses shared memory)
     if (threadIdx.x == 0) {
       __threadfence();
-      atomicAdd(p.done + lo, 1);
+      atomicAdd(p.done + o, 1);
     }
   }
 }
