@@ -1264,6 +1264,15 @@ gplhr_status combine(gplhr_ctx* ctx, const std::vector<In>& ins, Blk Y, int c, b
   int rows_tile = gplhr::comb_rows_tile(c, a.upper);
   const size_t esz = use32 ? sizeof(float2) : sizeof(double2);
   auto smem_of = [&](int rt) { return (size_t)(wsum * c + rt * wsum + rt * c) * esz; };
+  // FP32 arithmetic is cheap next to the row loads: tiles of up to 4 outputs per thread
+  // keep more loads in flight between the tile's two barriers (each output's sum is the
+  // same, in the same order, whatever the tile)
+  if (use32 && !a.upper)
+    for (int f = 4; f > 1; f /= 2)
+      if (smem_of(f * rows_tile) <= 48 * 1024) {
+        rows_tile *= f;
+        break;
+      }
   while (!a.upper && rows_tile > 1 && smem_of(rows_tile) > kCombSmemMax) rows_tile /= 2;
   if (smem_of(rows_tile) > kCombSmemMax) {
     ctx->err = "combine: coefficient block too large for shared memory";
