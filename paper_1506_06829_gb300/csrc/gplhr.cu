@@ -2327,7 +2327,7 @@ gplhr_status pk_sync(PkRunner& R) {
   PKCK(cudaStreamSynchronize(R.stream));
   R.wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (*R.herr != 0) {
-    R.err = "persistent kernel: a wait for a context's previous launch gave up";
+    R.err = "persistent kernel: no launch became ready within the wait limit";
     return GPLHR_ETIMEOUT;
   }
   return GPLHR_OK;
