@@ -128,3 +128,33 @@ def test_device_qz_refuses_bad_sizes_without_a_gpu(built):
         st = built.gplhr_ordqz_device(s, None, None, 0.0, 0.0, -1, None, None, None, None, None, None)
         assert st == G.GPLHR_EINVAL
     assert "s <= 80" in G.gplhr_last_error(None)
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding passes through the C ABI has the header's size and field
+    offsets (a C program compiled against include/gplhr.h prints them)."""
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    import ctypes as C
+    structs = {"gplhr_csr": G.Csr, "gplhr_precond": G.Precond, "gplhr_opts": G.Opts, "gplhr_info": G.Info,
+               "gplhr_persist_stats": G.PersistStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gplhr.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        cname, field, value = line.split()
+        got[(cname, field)] = int(value)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
